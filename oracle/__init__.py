@@ -1,0 +1,267 @@
+"""CPU oracle of the ego-motion-reduced SGM hot path (arXiv 1708.06301), for tests only.
+
+TEST INFRASTRUCTURE: only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package. The product path (the CUDA library and its binding) never
+imports, links or runs it, and this package imports nothing from the product package.
+
+The arithmetic lives in `tsgm_oracle.cpp` (plain C++17, built with `-O2 -ffp-contract=off`);
+this module compiles it, marshals numpy arrays through ctypes, and composes the per-stage
+functions into the per-frame pipeline of the paper (Sec. 2: prediction, matching, update).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tsgm_oracle.cpp")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (g++, no SIMD intrinsics, no FP contraction)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                        "-shared", "-o", tmp, _SRC], check=True)
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_OUT)
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ----------------------------------------------------------------------------------------------
+# Parameters (defaults are the readings listed in the design notes)
+# ----------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Params:
+    width: int
+    height: int
+    d_max: int = 63            # D = d_max + 1 labels
+    census_w: int = 5
+    census_h: int = 5
+    n_paths: int = 4
+    P1: int = 8
+    P2: int = 32
+    sigma_mult: float = 3.0    # Sec. 2.3, +-3 sigma window
+    q: float = 0.25            # Sec. 2.2, constant ego-motion variance (value not given)
+    S_max: float = 10.0        # Sec. 2.3, Eq. 9 threshold per path
+    r_min: float = 0.5
+    lr_tol: int = 1
+
+    @property
+    def D(self) -> int:
+        return self.d_max + 1
+
+    @property
+    def Bc(self) -> int:
+        return self.census_w * self.census_h - 1
+
+    @property
+    def s_thr(self) -> float:
+        return float(np.float32(self.S_max) * np.float32(self.n_paths))
+
+
+# ----------------------------------------------------------------------------------------------
+# Per-stage wrappers
+# ----------------------------------------------------------------------------------------------
+
+def build_H(R, t, f: float, b: float):
+    """Eq. 4 in binary64; returns (H64, H32) row-major 4x4."""
+    lib = _load()
+    R64 = _c(np.asarray(R, dtype=np.float64).reshape(9), np.float64)
+    t64 = _c(np.asarray(t, dtype=np.float64).reshape(3), np.float64)
+    H = np.zeros(16, dtype=np.float64)
+    lib.oracle_build_H(_p(R64), _p(t64), ctypes.c_double(f), ctypes.c_double(b), _p(H))
+    return H.reshape(4, 4), H.astype(np.float32).reshape(4, 4)
+
+
+def warp_predict(Dprev, Pprev, H32, cx: float, cy: float, q: float):
+    lib = _load()
+    Hh, W = Dprev.shape
+    Dprev = _c(Dprev, np.float32)
+    Pprev = _c(Pprev, np.float32)
+    Hm = _c(H32, np.float32).reshape(16)
+    Dp = np.empty((Hh, W), np.float32)
+    Pp = np.empty((Hh, W), np.float32)
+    win = np.empty((Hh, W), np.int32)
+    lib.oracle_warp_predict(W, Hh, _p(Dprev), _p(Pprev), _p(Hm), ctypes.c_float(cx),
+                            ctypes.c_float(cy), ctypes.c_float(q), _p(Dp), _p(Pp), _p(win))
+    return Dp, Pp, win
+
+
+def windows(Dp, Pp, D: int, sigma_mult: float):
+    lib = _load()
+    Hh, W = Dp.shape
+    Dp = _c(Dp, np.float32)
+    Pp = _c(Pp, np.float32)
+    lo = np.empty((Hh, W), np.int16)
+    hi = np.empty((Hh, W), np.int16)
+    off = np.empty(W * Hh + 1, np.uint32)
+    lib.oracle_windows.restype = ctypes.c_int64
+    n = lib.oracle_windows(W, Hh, D, ctypes.c_float(sigma_mult), _p(Dp), _p(Pp), _p(lo), _p(hi),
+                           _p(off))
+    return lo, hi, off, int(n)
+
+
+def offsets(lo, hi):
+    """Exclusive prefix sum of the window lengths (row-major), length n+1."""
+    w = (np.asarray(hi, np.int64) - np.asarray(lo, np.int64) + 1).reshape(-1)
+    off = np.zeros(w.size + 1, np.uint64)
+    np.cumsum(w, out=off[1:])
+    return off.astype(np.uint32)
+
+
+def census(img, cw: int, ch: int):
+    lib = _load()
+    Hh, W = img.shape
+    img = _c(img, np.uint8)
+    codes = np.empty((Hh, W), np.uint64)
+    lib.oracle_census(W, Hh, cw, ch, _p(img), _p(codes))
+    return codes
+
+
+def cost(cl, cr, lo, hi, off, Bc: int):
+    lib = _load()
+    Hh, W = cl.shape
+    C = np.empty(int(off[-1]), np.uint8)
+    lib.oracle_cost(W, Hh, Bc, _p(_c(cl, np.uint64)), _p(_c(cr, np.uint64)), _p(_c(lo, np.int16)),
+                    _p(_c(hi, np.int16)), _p(_c(off, np.uint32)), _p(C))
+    return C
+
+
+def sgm_path(C, lo, hi, off, direction: int, P1: int, P2: int):
+    lib = _load()
+    Hh, W = lo.shape
+    L = np.empty(int(off[-1]), np.uint16)
+    lib.oracle_sgm_path(W, Hh, direction, P1, P2, _p(_c(C, np.uint8)), _p(_c(lo, np.int16)),
+                        _p(_c(hi, np.int16)), _p(_c(off, np.uint32)), _p(L))
+    return L
+
+
+def sgm(C, lo, hi, off, n_paths: int, P1: int, P2: int):
+    lib = _load()
+    Hh, W = lo.shape
+    S = np.empty(int(off[-1]), np.uint16)
+    lib.oracle_sgm(W, Hh, n_paths, P1, P2, _p(_c(C, np.uint8)), _p(_c(lo, np.int16)),
+                   _p(_c(hi, np.int16)), _p(_c(off, np.uint32)), _p(S))
+    return S
+
+
+def select(S, lo, hi, off, s_thr: float, r_min: float):
+    lib = _load()
+    Hh, W = lo.shape
+    dstar = np.empty((Hh, W), np.int32)
+    Dz = np.empty((Hh, W), np.float32)
+    rz = np.empty((Hh, W), np.float32)
+    lib.oracle_select(W, Hh, _p(_c(S, np.uint16)), _p(_c(lo, np.int16)), _p(_c(hi, np.int16)),
+                      _p(_c(off, np.uint32)), ctypes.c_float(s_thr), ctypes.c_float(r_min),
+                      _p(dstar), _p(Dz), _p(rz))
+    return dstar, Dz, rz
+
+
+def lr_check(S, lo, hi, off, dstar, D: int, tol: int, Dz, rz):
+    """Returns (dright, valid, Dz_masked, rz_masked); inputs Dz, rz are not modified."""
+    lib = _load()
+    Hh, W = lo.shape
+    dright = np.empty((Hh, W), np.int32)
+    valid = np.empty((Hh, W), np.uint8)
+    Dz = np.array(Dz, dtype=np.float32, copy=True)
+    rz = np.array(rz, dtype=np.float32, copy=True)
+    lib.oracle_lr_check(W, Hh, D, _p(_c(S, np.uint16)), _p(_c(lo, np.int16)), _p(_c(hi, np.int16)),
+                        _p(_c(off, np.uint32)), _p(_c(dstar, np.int32)), tol, _p(dright),
+                        _p(valid), _p(Dz), _p(rz))
+    return dright, valid, Dz, rz
+
+
+def kalman(Dp, Pp, Dz, rz):
+    lib = _load()
+    shape = np.shape(Dp)
+    n = int(np.prod(shape))
+    D = np.empty(shape, np.float32)
+    P = np.empty(shape, np.float32)
+    lib.oracle_kalman(n, _p(_c(Dp, np.float32)), _p(_c(Pp, np.float32)), _p(_c(Dz, np.float32)),
+                      _p(_c(rz, np.float32)), _p(D), _p(P))
+    return D, P
+
+
+# ----------------------------------------------------------------------------------------------
+# Composite stages (Sec. 2: steps 2-4 of the per-frame algorithm)
+# ----------------------------------------------------------------------------------------------
+
+def match(left, right, lo, hi, prm: Params, keep: bool = False):
+    """Stereo matching in the given windows: census, ragged cost, SGM, WTA + sub-pixel + r,
+    left-right check. Returns (Dz, rz) or, with keep=True, a dict of every intermediate."""
+    off = offsets(lo, hi)
+    cl = census(left, prm.census_w, prm.census_h)
+    cr = census(right, prm.census_w, prm.census_h)
+    C = cost(cl, cr, lo, hi, off, prm.Bc)
+    S = sgm(C, lo, hi, off, prm.n_paths, prm.P1, prm.P2)
+    dstar, Dz0, rz0 = select(S, lo, hi, off, prm.s_thr, prm.r_min)
+    dright, valid, Dz, rz = lr_check(S, lo, hi, off, dstar, prm.D, prm.lr_tol, Dz0, rz0)
+    if not keep:
+        return Dz, rz
+    return dict(off=off, cl=cl, cr=cr, C=C, S=S, dstar=dstar, Dz_raw=Dz0, rz_raw=rz0,
+                dright=dright, valid=valid, Dz=Dz, rz=rz)
+
+
+def K_fbc(K):
+    K = np.asarray(K, dtype=np.float64).reshape(3, 3)
+    return float(K[0, 0]), float(K[0, 2]), float(K[1, 2])
+
+
+class Tracker:
+    """Per-frame loop of Sec. 2 on the CPU: predict (warp + variance), reduce the search space,
+    match, update. The first frame has no prediction and searches the whole range."""
+
+    def __init__(self, prm: Params):
+        self.prm = prm
+        self.D = None
+        self.P = None
+
+    def frame(self, left, right, R, t, K, baseline: float, keep: bool = False):
+        prm = self.prm
+        Hh, W = prm.height, prm.width
+        out = {}
+        if self.D is None:
+            Dp = np.full((Hh, W), -1.0, np.float32)
+            Pp = np.full((Hh, W), -1.0, np.float32)
+        else:
+            f, cx, cy = K_fbc(K)
+            _, H32 = build_H(R, t, f, baseline)
+            Dp, Pp, win = warp_predict(self.D, self.P, H32, np.float32(cx), np.float32(cy), prm.q)
+            out["winner"] = win
+            out["H32"] = H32
+        lo, hi, off, n_cells = windows(Dp, Pp, prm.D, prm.sigma_mult)
+        m = match(left, right, lo, hi, prm, keep=True)
+        D, P = kalman(Dp, Pp, m["Dz"], m["rz"])
+        self.D, self.P = D, P
+        if keep:
+            out.update(m)
+            out.update(Dpred=Dp, Ppred=Pp, lo=lo, hi=hi, n_cells=n_cells, D=D, P=P)
+            return out
+        return D, P

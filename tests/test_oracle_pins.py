@@ -1,0 +1,567 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test checks one oracle function against something other than itself: a geometric
+construction, a closed form, a hand-worked case, a textbook formulation written independently
+here, or brute force on tiny inputs. They are chosen so that a dropped term, a wrong sign or
+index, or a transposed operand in the oracle fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_06301_gb300 import synth
+
+F, B = 721.0, 0.54
+
+
+# ----------------------------------------------------------------------------------------------
+# Eq. 1-4: disparity-space homography
+# ----------------------------------------------------------------------------------------------
+
+def _geometric_transfer(R, t, f, b, x, y, d):
+    """Back-project (x, y, d) to Euclidean space, apply M' = R M + t (Eq. 2), project again."""
+    Z = f * b / d
+    M = np.array([x * Z / f, y * Z / f, Z])
+    Mp = R @ M + t
+    return f * Mp[0] / Mp[2], f * Mp[1] / Mp[2], f * b / Mp[2]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_H_matches_geometric_transfer(seed):
+    R, t = synth.random_pose(100 + seed, max_t=1.5, max_rot_deg=3.0)
+    R = R.astype(np.float64)
+    t = t.astype(np.float64)
+    H64, H32 = oracle.build_H(R, t, F, B)
+    rs = synth.Stream(seed, 1)
+    for _ in range(50):
+        x, y, d = rs.uniform(-600, 600), rs.uniform(-180, 180), rs.uniform(1, 127)
+        w = H64 @ np.array([x, y, d, 1.0])
+        got = w[:3] / w[3]  # Eq. 3: divide by the fourth component
+        exp = _geometric_transfer(R, t, F, B, x, y, d)
+        np.testing.assert_allclose(got, exp, rtol=1e-10, atol=1e-9)
+    assert np.array_equal(H32, H64.astype(np.float32))
+
+
+def test_H_identity_pose_is_identity():
+    H64, _ = oracle.build_H(np.eye(3), np.zeros(3), F, B)
+    np.testing.assert_allclose(H64, np.eye(4), atol=1e-15)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. 2.2: warp, z-buffer, variance prediction (Eq. 3, 5, 6)
+# ----------------------------------------------------------------------------------------------
+
+def _cxcy(W, H):
+    return np.float32((W - 1) / 2.0), np.float32((H - 1) / 2.0)
+
+
+def test_warp_identity_pose_leaves_maps_unchanged():
+    W, H = 57, 23
+    D, P = synth.random_maps(7, W, H, invalid_frac=0.2)
+    _, H32 = oracle.build_H(np.eye(3), np.zeros(3), F, B)
+    cx, cy = _cxcy(W, H)
+    q = 0.25
+    Dp, Pp, win = oracle.warp_predict(D, P, H32, cx, cy, q)
+    valid = D > 0
+    assert np.array_equal(Dp[valid], D[valid])  # bit-exact
+    assert np.array_equal(Pp[valid], (P[valid] + np.float32(q)).astype(np.float32))  # Phi = 1
+    assert np.all(Dp[~valid] == -1) and np.all(Pp[~valid] == -1)
+    idx = np.arange(W * H).reshape(H, W)
+    assert np.array_equal(win[valid], idx[valid])
+
+
+def test_warp_lateral_shift_and_zbuffer_bruteforce():
+    """t = (3b/8, 0, 0): points at d = 8 move 3 px right, d = 16 move 6 px (x' = x + d t_x / b),
+    disparity unchanged. Collisions are resolved by brute force: highest d, then lowest index."""
+    W, H = 40, 9
+    rs = synth.uniform01(3, np.arange(W * H)).reshape(H, W)
+    D = np.where(rs < 0.5, 8.0, 16.0).astype(np.float32)
+    D[rs > 0.9] = -1.0
+    P = (0.1 + synth.uniform01(4, np.arange(W * H)).reshape(H, W)).astype(np.float32)
+    P[D < 0] = -1.0
+    t = np.array([3 * B / 8, 0, 0], dtype=np.float32)
+    _, H32 = oracle.build_H(np.eye(3), t.astype(np.float64), F, B)
+    cx, cy = _cxcy(W, H)
+    Dp, Pp, win = oracle.warp_predict(D, P, H32, cx, cy, 0.5)
+    # brute force
+    expD = np.full((H, W), -1.0, np.float32)
+    expW = np.full((H, W), -1, np.int64)
+    for v in range(H):
+        cands = {}
+        for u in range(W):
+            if D[v, u] <= 0:
+                continue
+            tu = u + (3 if D[v, u] == 8 else 6)
+            if tu < W:
+                cands.setdefault(tu, []).append((D[v, u], v * W + u))
+        for tu, lst in cands.items():
+            best = max(d for d, _ in lst)
+            src = min(i for d, i in lst if d == best)
+            expD[v, tu] = best
+            expW[v, tu] = src
+    assert np.array_equal(Dp, expD)
+    assert np.array_equal(win, expW)
+    ok = expW >= 0
+    assert np.array_equal(Pp[ok], (P.reshape(-1)[expW[ok]] + np.float32(0.5)).astype(np.float32))
+
+
+def test_warp_forward_motion_fronto_parallel_wall():
+    """A wall at Z = 20 m seen after moving forward s: every prediction is f b/(Z - s) and
+    Phi = Z/(Z - s), so p' = Phi^2 p + q (Eq. 5-6); checked in binary64 within 1e-6 rel."""
+    W, H, Z, s, q = 64, 32, 20.0, 1.3, 0.25
+    D = np.full((H, W), F * B / Z, np.float32)
+    P = (0.1 + 3.9 * synth.uniform01(9, np.arange(W * H)).reshape(H, W)).astype(np.float32)
+    _, H32 = oracle.build_H(np.eye(3), np.array([0, 0, -s]), F, B)
+    cx, cy = _cxcy(W, H)
+    Dp, Pp, win = oracle.warp_predict(D, P, H32, cx, cy, q)
+    hit = win >= 0
+    assert hit.mean() > 0.5  # zooming in leaves gaps (Sec. 2.2) but most pixels are reached
+    np.testing.assert_allclose(Dp[hit], F * B / (Z - s), rtol=1e-6)
+    phi = (Dp[hit].astype(np.float64)) / D.reshape(-1)[win[hit]].astype(np.float64)
+    exp = phi ** 2 * P.reshape(-1)[win[hit]].astype(np.float64) + q
+    np.testing.assert_allclose(Pp[hit], exp, rtol=1e-6)
+    np.testing.assert_allclose(phi, Z / (Z - s), rtol=1e-6)
+    # zooming: sources spread outwards from the principal point, so the image centre is reached
+    assert hit[H // 2, W // 2]
+    # each winner lands (x~ Z/(Z-s), y~ Z/(Z-s)) from the principal point; the target pixel is
+    # the nearest one (round to nearest, not truncation)
+    src = win[hit]
+    su, sv = src % W, src // W
+    x_land = (su - float(cx)) * Z / (Z - s) + float(cx)
+    y_land = (sv - float(cy)) * Z / (Z - s) + float(cy)
+    tv, tu = np.nonzero(hit)
+    assert np.all(np.abs(x_land - tu) <= 0.5 + 1e-4)
+    assert np.all(np.abs(y_land - tv) <= 0.5 + 1e-4)
+
+
+def test_warp_zbuffer_tie_goes_to_lowest_source():
+    """Moving backwards from a fronto-parallel wall shrinks the image: several sources with the
+    same predicted disparity land on one target; the lowest source index must win. Landing
+    pixels come from the geometric construction (binary64), keeping only sources that land at
+    least 1e-3 px away from a rounding boundary."""
+    W, H, Z, s = 48, 24, 10.0, 4.0
+    D = np.full((H, W), F * B / Z, np.float32)
+    P = np.ones((H, W), np.float32)
+    _, H32 = oracle.build_H(np.eye(3), np.array([0, 0, +s]), F, B)
+    cx, cy = _cxcy(W, H)
+    _, _, win = oracle.warp_predict(D, P, H32, cx, cy, 0.0)
+    uu, vv = np.meshgrid(np.arange(W), np.arange(H))
+    xl = (uu - float(cx)) * Z / (Z + s) + float(cx) + 0.5
+    yl = (vv - float(cy)) * Z / (Z + s) + float(cy) + 0.5
+    sure = (np.abs(xl - np.round(xl)) > 1e-3) & (np.abs(yl - np.round(yl)) > 1e-3)
+    tx, ty = np.floor(xl).astype(int), np.floor(yl).astype(int)
+    idx = vv * W + uu
+    n_ties = 0
+    for t in set(zip(ty[sure].tolist(), tx[sure].tolist())):
+        srcs = idx[(ty == t[0]) & (tx == t[1])]
+        if np.all(sure.reshape(-1)[srcs]):
+            assert win[t] == srcs.min()
+            n_ties += len(srcs) > 1
+    assert n_ties > 20
+
+
+def test_warp_ground_plane_against_renderer():
+    """Forward translation over a ground plane: the predicted disparity at every reached pixel
+    is the ground-plane disparity of a point landing within half a pixel of that row, and agrees
+    with the next frame's rendered ground truth up to the plane's disparity slope b/h per row."""
+    W, H, h, s = 160, 80, 1.65, 0.8
+    cam = synth.Camera(W, H, F, B)
+    scene = synth.Scene(ground_y=h, far_z=1e7, boxes=np.zeros((0, 4)), tex_seed=1)
+    _, Z0 = synth.render(scene, cam, np.eye(3), np.zeros(3))
+    _, Z1 = synth.render(scene, cam, np.eye(3), np.array([0, 0, s]))
+    D0 = (F * B / Z0).astype(np.float32)
+    D1 = (F * B / Z1).astype(np.float32)
+    ground = np.arange(H)[:, None] > cam.cy + 2
+    D0 = np.where(ground, D0, -1.0).astype(np.float32)
+    P0 = np.where(ground, 1.0, -1.0).astype(np.float32)
+    _, H32 = oracle.build_H(np.eye(3), np.array([0, 0, -s]), F, B)
+    Dp, Pp, win = oracle.warp_predict(D0, P0, H32, np.float32(cam.cx), np.float32(cam.cy), 0.0)
+    hit = win >= 0
+    assert hit.sum() > 0.3 * ground.sum()
+    rows = np.nonzero(hit)[0]
+    y_land = cam.cy + h * Dp[hit].astype(np.float64) / B  # ground plane: d = b (y - cy) / h
+    assert np.all(np.abs(y_land - rows) <= 0.5 + 1e-3)
+    assert np.all(np.abs(Dp[hit] - D1[hit]) <= 0.5 * B / h + 1e-3)
+    # each winner's predicted disparity is its source point seen s metres closer: f b / (Z - s)
+    # (the plane maps onto itself either way, so this is what tells forward from backward)
+    Zsrc = F * B / D0.reshape(-1)[win[hit]].astype(np.float64)
+    np.testing.assert_allclose(Dp[hit], F * B / (Zsrc - s), rtol=2e-5)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. 2.3: reduced window
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,p,D,exp", [
+    (10.0, 1.0, 64, (7, 13)),        # 10 -+ 3
+    (10.5, 0.25, 64, (9, 12)),       # 10.5 -+ 1.5
+    (10.2, 0.25, 64, (8, 12)),       # [8.7, 11.7] rounded outwards
+    (2.0, 4.0, 64, (0, 8)),          # clipped at 0
+    (62.0, 4.0, 64, (56, 63)),       # clipped at D-1
+    (10.0, 0.0, 64, (10, 10)),       # zero variance: one label
+    (-1.0, -1.0, 64, (0, 63)),       # no prediction: whole range
+    (10.0, float("nan"), 64, (0, 63)),
+    (10.0, float("inf"), 64, (0, 63)),
+    (100.0, 1.0, 64, (0, 63)),       # interval entirely above the range: whole range
+    (0.0, 0.01, 64, (0, 1)),
+])
+def test_window_hand_cases(d, p, D, exp):
+    lo, hi, off, n = oracle.windows(np.array([[d]], np.float32), np.array([[p]], np.float32), D, 3.0)
+    assert (int(lo[0, 0]), int(hi[0, 0])) == exp
+    assert n == exp[1] - exp[0] + 1 and off[0] == 0 and off[1] == n
+
+
+def test_window_offsets_are_exclusive_scan():
+    W, H = 33, 7
+    D, P = synth.random_maps(5, W, H, d_range=(0, 70), p_range=(0, 9), invalid_frac=0.3)
+    lo, hi, off, n = oracle.windows(D, P, 64, 3.0)
+    w = (hi.astype(np.int64) - lo + 1).reshape(-1)
+    assert np.all(w >= 1) and np.all(lo >= 0) and np.all(hi <= 63)
+    assert n == w.sum() and off[0] == 0
+    assert np.array_equal(off[1:].astype(np.int64), np.cumsum(w))
+    # an invalid prediction searches the whole range
+    assert np.all(lo[D < 0] == 0) and np.all(hi[D < 0] == 63)
+
+
+# ----------------------------------------------------------------------------------------------
+# Census + Hamming cost
+# ----------------------------------------------------------------------------------------------
+
+def test_census_hand_example():
+    img = np.array([[1, 2, 3], [4, 5, 6], [7, 8, 9]], np.uint8)
+    c = oracle.census(img, 3, 3)
+    # centre 5: neighbours in row-major order 1,2,3,4,6,7,8,9 -> bits 0..3 set
+    assert c[1, 1] == 0b00001111
+    # corner (0,0) value 1 with border clamp: nothing is smaller
+    assert c[0, 0] == 0
+    # corner (2,2) value 9, window clamped to the border: the 8 neighbours in row-major order
+    # read 5, 6, 6, 8, 9, 8, 9, 9 -> bits 0, 1, 2, 3 and 5 are set
+    exp = 0
+    bit = 0
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dx == 0 and dy == 0:
+                continue
+            qy, qx = min(max(2 + dy, 0), 2), min(max(2 + dx, 0), 2)
+            if img[qy, qx] < 9:
+                exp |= 1 << bit
+            bit += 1
+    assert c[2, 2] == exp == 0b00101111
+
+
+def test_census_bruteforce_and_constant():
+    img, _ = synth.random_images(11, 13, 9)
+    for cw, ch in ((5, 5), (9, 7), (3, 3)):
+        c = oracle.census(img, cw, ch)
+        H, W = img.shape
+        for y in range(H):
+            for x in range(W):
+                bits = []
+                for dy in range(-(ch // 2), ch // 2 + 1):
+                    for dx in range(-(cw // 2), cw // 2 + 1):
+                        if dx or dy:
+                            q = img[min(max(y + dy, 0), H - 1), min(max(x + dx, 0), W - 1)]
+                            bits.append(int(q < img[y, x]))
+                assert int(c[y, x]) == sum(b << i for i, b in enumerate(bits))
+    assert not oracle.census(np.full((8, 8), 77, np.uint8), 9, 7).any()
+
+
+def _popcount(v):
+    return bin(int(v)).count("1")
+
+
+def test_cost_hamming_and_border():
+    a, b = synth.random_images(12, 21, 6)
+    D = 8
+    cl, cr = oracle.census(a, 9, 7), oracle.census(b, 9, 7)
+    lo = np.zeros((6, 21), np.int16)
+    hi = np.full((6, 21), D - 1, np.int16)
+    off = oracle.offsets(lo, hi)
+    C = oracle.cost(cl, cr, lo, hi, off, 62)
+    for y in range(6):
+        for x in range(21):
+            for d in range(D):
+                exp = 62 if x - d < 0 else _popcount(int(cl[y, x]) ^ int(cr[y, x - d]))
+                assert C[off[y * 21 + x] + d] == exp
+    # identical images: zero cost at d = 0
+    C0 = oracle.cost(cl, cl, lo, hi, off, 62)
+    assert np.all(C0[off[:-1]] == 0)
+
+
+# ----------------------------------------------------------------------------------------------
+# SGM aggregation (Sec. 2.3)
+# ----------------------------------------------------------------------------------------------
+
+DIRS = [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (-1, 1), (1, -1)]
+
+
+def _textbook_sgm_dense(Cd, n_paths, P1, P2):
+    """Full-range SGM on a dense (H, W, D) volume, written independently of the oracle:
+    vectorised over d, each path swept with numpy."""
+    H, W, D = Cd.shape
+    Cd = Cd.astype(np.int64)
+    S = np.zeros_like(Cd)
+    for dx, dy in DIRS[:n_paths]:
+        L = np.zeros_like(Cd)
+        ys = range(H) if dy >= 0 else range(H - 1, -1, -1)
+        xs = list(range(W)) if dx >= 0 else list(range(W - 1, -1, -1))
+        for y in ys:
+            for x in xs:
+                qx, qy = x - dx, y - dy
+                if not (0 <= qx < W and 0 <= qy < H):
+                    L[y, x] = Cd[y, x]
+                    continue
+                Lq = L[qy, qx]
+                m = Lq.min()
+                up = np.concatenate([[np.iinfo(np.int64).max // 4], Lq[:-1]]) + P1
+                dn = np.concatenate([Lq[1:], [np.iinfo(np.int64).max // 4]]) + P1
+                L[y, x] = Cd[y, x] + np.minimum(np.minimum(Lq, up), np.minimum(dn, m + P2)) - m
+        S += L
+    return S
+
+
+@pytest.mark.parametrize("n_paths", [4, 8])
+def test_sgm_full_windows_equal_textbook(n_paths):
+    H, W, D = 11, 17, 12
+    a, b = synth.random_images(21, W, H)
+    cl, cr = oracle.census(a, 5, 5), oracle.census(b, 5, 5)
+    lo = np.zeros((H, W), np.int16)
+    hi = np.full((H, W), D - 1, np.int16)
+    off = oracle.offsets(lo, hi)
+    C = oracle.cost(cl, cr, lo, hi, off, 24)
+    S = oracle.sgm(C, lo, hi, off, n_paths, 8, 32)
+    S_tb = _textbook_sgm_dense(C.reshape(H, W, D), n_paths, 8, 32)
+    assert np.array_equal(S.reshape(H, W, D).astype(np.int64), S_tb)
+
+
+def _pen(a, b, P1, P2):
+    return 0 if a == b else (P1 if abs(a - b) == 1 else P2)
+
+
+def _line(W, H, dx, dy, start):
+    x, y = start
+    pts = []
+    while 0 <= x < W and 0 <= y < H:
+        pts.append((x, y))
+        x, y = x + dx, y + dy
+    return pts
+
+
+def _line_starts(W, H, dx, dy):
+    return [(x, y) for y in range(H) for x in range(W)
+            if not (0 <= x - dx < W and 0 <= y - dy < H)]
+
+
+@pytest.mark.parametrize("direction", range(8))
+def test_sgm_path_equals_bruteforce_min_energy(direction):
+    """Each path is exact 1-D dynamic programming: the normalised L_r equals the minimum, over
+    every labelling of the path prefix inside the windows, of data cost plus P1/P2 penalties,
+    up to a per-pixel constant."""
+    H, W, D, P1, P2 = 4, 6, 4, 3, 7
+    rs = synth.uniform01(31, direction, np.arange(W * H * D)).reshape(H, W, D)
+    Cd = np.floor(rs * 20).astype(np.uint8)
+    lo_l = np.floor(synth.uniform01(32, direction, np.arange(W * H)) * D).astype(np.int64)
+    hi_l = lo_l + np.floor(synth.uniform01(33, direction, np.arange(W * H)) * (D - lo_l)).astype(np.int64)
+    lo = lo_l.astype(np.int16).reshape(H, W)
+    hi = hi_l.astype(np.int16).reshape(H, W)
+    off = oracle.offsets(lo, hi)
+    C = np.concatenate([Cd[i // W, i % W, lo_l[i]:hi_l[i] + 1] for i in range(W * H)])
+    L = oracle.sgm_path(C, lo, hi, off, direction, P1, P2).astype(np.int64)
+    dx, dy = DIRS[direction]
+    checked = 0
+    for st in _line_starts(W, H, dx, dy):
+        pts = _line(W, H, dx, dy, st)
+        for k in range(len(pts)):
+            prefix = pts[:k + 1]
+            doms = [range(lo[y, x], hi[y, x] + 1) for x, y in prefix]
+            best = {}
+            for lab in itertools.product(*doms):
+                e = sum(int(Cd[y, x, l]) for (x, y), l in zip(prefix, lab))
+                e += sum(_pen(lab[i - 1], lab[i], P1, P2) for i in range(1, len(lab)))
+                best[lab[-1]] = min(best.get(lab[-1], 1 << 60), e)
+            x, y = prefix[-1]
+            i = y * W + x
+            Lp = {d: L[off[i] + d - lo[y, x]] for d in range(lo[y, x], hi[y, x] + 1)}
+            eb = min(best.values())
+            lb = min(Lp.values())
+            assert {d: v - eb for d, v in best.items()} == {d: v - lb for d, v in Lp.items()}
+            checked += 1
+    assert checked == W * H
+
+
+def test_sgm_bound_and_reduced_equals_restricted_dense():
+    """S <= P (Bc + P2); and shrinking windows never changes costs inside a window
+    (the ragged cost is the dense cost restricted to the window)."""
+    H, W, D = 9, 23, 16
+    a, b = synth.random_images(41, W, H)
+    cl, cr = oracle.census(a, 9, 7), oracle.census(b, 9, 7)
+    lo, hi = synth.random_windows(42, W, H, D, 1, 9, full_frac=0.2)
+    off = oracle.offsets(lo, hi)
+    C = oracle.cost(cl, cr, lo, hi, off, 62)
+    S = oracle.sgm(C, lo, hi, off, 8, 8, 32)
+    assert S.max() <= 8 * (62 + 32)
+    lof = np.zeros_like(lo)
+    hif = np.full_like(hi, D - 1)
+    offf = oracle.offsets(lof, hif)
+    Cf = oracle.cost(cl, cr, lof, hif, offf, 62).reshape(H, W, D)
+    for i in range(W * H):
+        y, x = divmod(i, W)
+        assert np.array_equal(C[off[i]:off[i + 1]], Cf[y, x, lo[y, x]:hi[y, x] + 1])
+
+
+# ----------------------------------------------------------------------------------------------
+# WTA, sub-pixel, matching variance (Eq. 9)
+# ----------------------------------------------------------------------------------------------
+
+def _select_one(s, lo=0, s_thr=8.0, r_min=0.0):
+    s = np.asarray(s, np.uint16)
+    loa = np.array([[lo]], np.int16)
+    hia = np.array([[lo + len(s) - 1]], np.int16)
+    off = np.array([0, len(s)], np.uint32)
+    d, Dz, rz = oracle.select(s, loa, hia, off, s_thr, r_min)
+    return int(d[0, 0]), float(Dz[0, 0]), float(rz[0, 0])
+
+
+def test_select_parabola_vertex_exact():
+    # S(d) = (2d - 21)^2 = 4 (d - 10.5)^2: tie at 10/11 -> d* = 10, vertex 10.5
+    s = [(2 * d - 21) ** 2 for d in range(20)]
+    assert _select_one(s)[:2] == (10, 10.5)
+    # S(d) = 3 (4d - 29)^2 = 48 (d - 7.25)^2: vertex 7.25
+    s = [3 * (4 * d - 29) ** 2 for d in range(16)]
+    assert _select_one(s)[:2] == (7, 7.25)
+    # same curve in a window starting at 5: disparities are absolute
+    assert _select_one(s[5:12], lo=5)[:2] == (7, 7.25)
+    # minimum on the window edge: no sub-pixel step
+    assert _select_one([4, 9, 12], lo=3)[:2] == (3, 3.0)
+
+
+def test_select_matching_variance_hand_cases():
+    # S = [10, 5, 3, 4, 9, 20], d* = 2; left: +2 (count), +7 -> 9 >= 8 stop; right: +1, +6 -> 7
+    # (count both), +17 stop  ->  r = 1 + 2 = 3
+    # sub-pixel delta = (5 - 4) / (2 (5 - 6 + 4)) = 1/6, rounded to binary32
+    exp_dz = float(np.float32(2) + np.float32(1) / np.float32(6))
+    assert _select_one([10, 5, 3, 4, 9, 20], s_thr=8.0) == (2, exp_dz, 3.0)
+    # flat bottom: equal neighbours count while the sum stays below the threshold (the case the
+    # paper's extension of the slope measure is made for)
+    d, _, r = _select_one([50, 3, 3, 3, 3, 50], s_thr=8.0)
+    assert d == 1 and r == 3.0
+    # a running sum equal to the threshold is not below it: S = [20, 8, 0, 8, 20], thr 8 -> r = 0
+    assert _select_one([20, 8, 0, 8, 20], s_thr=8.0)[2] == 0.0
+    assert _select_one([20, 7, 0, 8, 20], s_thr=8.0)[2] == 1.0
+    # r floored at r_min
+    assert _select_one([9, 0, 9], s_thr=8.0, r_min=0.5)[2] == 0.5
+
+
+def test_select_argmin_bruteforce():
+    H, W, D = 5, 7, 10
+    lo, hi = synth.random_windows(51, W, H, D, 1, 10)
+    off = oracle.offsets(lo, hi)
+    S = np.floor(synth.uniform01(52, np.arange(off[-1])) * 30).astype(np.uint16)
+    d, _, _ = oracle.select(S, lo, hi, off, 40.0, 0.5)
+    for i in range(W * H):
+        y, x = divmod(i, W)
+        assert d[y, x] == lo[y, x] + int(np.argmin(S[off[i]:off[i + 1]]))
+
+
+# ----------------------------------------------------------------------------------------------
+# Left-right check (Sec. 2.4)
+# ----------------------------------------------------------------------------------------------
+
+def test_lr_check_bruteforce():
+    H, W, D = 4, 19, 8
+    lo, hi = synth.random_windows(61, W, H, D, 1, 8, full_frac=0.3)
+    off = oracle.offsets(lo, hi)
+    S = np.floor(synth.uniform01(62, np.arange(off[-1])) * 25).astype(np.uint16)
+    dstar, Dz, rz = oracle.select(S, lo, hi, off, 40.0, 0.5)
+    dright, valid, Dzm, rzm = oracle.lr_check(S, lo, hi, off, dstar, D, 1, Dz, rz)
+    for y in range(H):
+        for xr in range(W):
+            cands = []
+            for x in range(W):
+                d = x - xr
+                i = y * W + x
+                if 0 <= d < D and lo[y, x] <= d <= hi[y, x]:
+                    cands.append((int(S[off[i] + d - lo[y, x]]), d))
+            exp = min(cands)[1] if cands else -1
+            assert dright[y, xr] == exp
+        for x in range(W):
+            d = dstar[y, x]
+            ok = x - d >= 0 and dright[y, x - d] >= 0 and abs(d - dright[y, x - d]) <= 1
+            assert valid[y, x] == ok
+            if ok:
+                assert Dzm[y, x] == Dz[y, x] and rzm[y, x] == rz[y, x]
+            else:
+                assert Dzm[y, x] == -1 and rzm[y, x] == -1
+
+
+def test_lr_check_consistent_pair_passes():
+    """A left view whose costs are minimal exactly on a constant disparity passes everywhere it
+    has a right correspondence, and fails where x - d* < 0 (no right pixel)."""
+    H, W, D, d0 = 2, 16, 6, 3
+    lo = np.zeros((H, W), np.int16)
+    hi = np.full((H, W), D - 1, np.int16)
+    off = oracle.offsets(lo, hi)
+    S = np.array([[0 if d == d0 else 10 + d for d in range(D)] for _ in range(W * H)],
+                 np.uint16).reshape(-1)
+    dstar, Dz, rz = oracle.select(S, lo, hi, off, 8.0, 0.5)
+    _, valid, _, _ = oracle.lr_check(S, lo, hi, off, dstar, D, 1, Dz, rz)
+    assert np.all(valid[:, d0:] == 1) and np.all(valid[:, :d0] == 0)
+
+
+# ----------------------------------------------------------------------------------------------
+# Kalman update (Eq. 10-12)
+# ----------------------------------------------------------------------------------------------
+
+def test_kalman_information_form():
+    n = 5000
+    dp = (1 + 126 * synth.uniform01(71, np.arange(n))).astype(np.float32)
+    pp = (0.1 + 3.9 * synth.uniform01(72, np.arange(n))).astype(np.float32)
+    dz = (1 + 126 * synth.uniform01(73, np.arange(n))).astype(np.float32)
+    rz = (0.5 + 4 * synth.uniform01(74, np.arange(n))).astype(np.float32)
+    D, P = oracle.kalman(dp, pp, dz, rz)
+    p64, r64 = pp.astype(np.float64), rz.astype(np.float64)
+    expD = (r64 * dp + p64 * dz) / (p64 + r64)     # information-form fusion
+    expP = p64 * r64 / (p64 + r64)
+    np.testing.assert_allclose(D, expD, rtol=1e-6, atol=1e-5)
+    np.testing.assert_allclose(P, expP, rtol=1e-6)
+
+
+def test_kalman_limits_and_missing_sides():
+    dp = np.array([10, 10, 10, -1, 10, -1], np.float32)
+    pp = np.array([1, 1e30, 1, -1, 2, -1], np.float32)
+    dz = np.array([12, 12, -1, 12, 12, -1], np.float32)
+    rz = np.array([0, 1, -1, 3, 2, -1], np.float32)
+    D, P = oracle.kalman(dp, pp, dz, rz)
+    assert D[0] == 12 and P[0] == 0          # r -> 0: take the measurement
+    assert abs(D[1] - 12) < 1e-5             # p -> inf: take the measurement
+    assert D[2] == 10 and P[2] == 1          # no measurement: keep the prediction
+    assert D[3] == 12 and P[3] == 3          # no prediction: take the measurement
+    assert D[4] == 11 and P[4] == 1          # equal variances: midpoint, half variance
+    assert D[5] == -1 and P[5] == -1
+
+
+# ----------------------------------------------------------------------------------------------
+# Whole pipeline properties
+# ----------------------------------------------------------------------------------------------
+
+def test_pipeline_small_pair_reduced_vs_full():
+    """Frame 2 of the 320x96 pair: the reduced search considers a fraction of the cells and is at
+    least as accurate (bad-3px over ground truth) as full-range SGM on the same frame."""
+    seq = synth.small_pair(1)
+    prm = oracle.Params(320, 96)
+    tr = oracle.Tracker(prm)
+    tr.frame(seq.left[0], seq.right[0], seq.R[0], seq.t[0], seq.K, B)
+    o = tr.frame(seq.left[1], seq.right[1], seq.R[1], seq.t[1], seq.K, B, keep=True)
+    assert o["n_cells"] < 0.5 * 320 * 96 * 64
+    lo = np.zeros((96, 320), np.int16)
+    hi = np.full((96, 320), 63, np.int16)
+    Dz_full, _ = oracle.match(seq.left[1], seq.right[1], lo, hi, prm)
+    gt = seq.gt_disp[1]
+
+    def bad(d):
+        return float(np.mean((d < 0) | (np.abs(d - gt) > 3)))
+
+    assert bad(o["D"]) <= bad(Dz_full)
