@@ -1,0 +1,210 @@
+/*
+ * tsgm — temporal SGM in an ego-motion-reduced disparity search space, GB300 (sm_103a).
+ *
+ * C ABI of the data-parallel hot path of Fucek, Markovic, Cvisic, Petrovic, "Dense Disparity
+ * Estimation in Ego-motion Reduced Search Space" (arXiv 1708.06301):
+ *   disparity prediction  (Sec. 2.2, Eq. 3, 5, 6)  -> tsgm_warp_predict
+ *   reduced search space  (Sec. 2.3)               -> tsgm_windows
+ *   stereo matching       (Sec. 2.3, 2.4, Eq. 9)   -> tsgm_match
+ *   disparity update      (Sec. 2.4, Eq. 10-12)    -> tsgm_kalman_update
+ *   one whole time step   (Sec. 2, steps 2-4)      -> tsgm_frame / tsgm_frame_host
+ *
+ * Conventions (all calls):
+ *   - Image and map pointers are DEVICE pointers (except tsgm_frame_host, tsgm_build_H and the
+ *     state export/import), caller-owned, dense row-major with pitch = width; pixel index
+ *     i = y * width + x. uint8 images; float32 disparity (px) and variance (px^2) maps.
+ *   - An invalid disparity or variance is -1.0f. A map value is valid iff it is finite and >= 0.
+ *   - A disparity window is [d_lo, d_hi] inclusive, int16, inside [0, d_max].
+ *   - Calls are asynchronous on the context's CUDA stream unless stated otherwise; outputs are
+ *     ready when that stream reaches the point of the call. Inputs must stay valid until then.
+ *   - Every call returns a tsgm_status; on failure tsgm_last_error() gives a message. No call
+ *     throws across the ABI. A context is not thread-safe: one host thread at a time.
+ *   - The context owns every scratch buffer, allocated once in tsgm_create for the maximum
+ *     problem (width x height pixels x (d_max + 1) labels); no call allocates device memory
+ *     afterwards (tsgm_frame_host uses pinned staging allocated at create time too).
+ *   - Pose convention (Eq. 2): M^k = R M^{k-1} + t maps previous-frame camera coordinates to
+ *     current ones; R row-major 3x3, t in metres; forward motion by s gives t = (0, 0, -s).
+ *     K is the row-major 3x3 intrinsic matrix; f = K[0], cx = K[2], cy = K[5].
+ */
+#ifndef TSGM_H
+#define TSGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSGM_MAX_LABELS 256   /* d_max + 1 <= 256 */
+#define TSGM_MAX_CENSUS_BITS 64
+
+typedef struct tsgm_ctx tsgm_ctx;
+
+typedef enum {
+    TSGM_OK = 0,
+    TSGM_ERR_INVALID_ARG = 1,   /* null pointer, bad size or parameter; nothing was launched */
+    TSGM_ERR_OUT_OF_MEMORY = 2, /* tsgm_create could not allocate its buffers */
+    TSGM_ERR_CUDA = 3,          /* a CUDA call failed; message in tsgm_last_error */
+    TSGM_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    TSGM_ERR_STATE = 5,         /* call not valid in the current state (e.g. no previous frame) */
+    TSGM_ERR_UNIMPLEMENTED = 6
+} tsgm_status;
+
+/* Flags for tsgm_params.flags */
+#define TSGM_FLAG_KEEP_INTERNALS 1u  /* also write d*, right-view disparities and the LR mask of
+                                        the last tsgm_match into context buffers (tsgm_inspect) */
+#define TSGM_FLAG_FULL_RANGE 2u      /* tsgm_frame ignores the prediction when choosing windows:
+                                        plain full-range SGM every frame (still Kalman-updated) */
+
+typedef struct {
+    int32_t width, height;       /* image size, 1 <= width <= 16000, 1 <= height */
+    int32_t d_max;               /* labels are 0..d_max; d_max + 1 <= TSGM_MAX_LABELS */
+    int32_t census_w, census_h;  /* odd census window; census_w * census_h - 1 <= 64 */
+    int32_t n_paths;             /* SGM paths: 4 (->, <-, down, up) or 8 (+ 4 diagonals) */
+    int32_t P1, P2;              /* SGM penalties, 0 <= P1 <= P2, census bits + P2 <= 255 */
+    float sigma_mult;            /* window half-width in standard deviations (Sec. 2.3: 3) */
+    float q;                     /* ego-motion variance in disparity space, px^2 (Eq. 5) */
+    float S_max;                 /* matching-variance threshold per path (Eq. 9, Sec. 2.3) */
+    float r_min;                 /* floor of the matching variance r, px^2 */
+    int32_t lr_tol;              /* left-right check tolerance in px (Sec. 2.4) */
+    uint32_t flags;              /* TSGM_FLAG_* */
+} tsgm_params;
+
+/* Fill *p with the defaults: d_max 127, census 9x7, 8 paths, P1 8, P2 32, sigma_mult 3,
+ * q 0.25, S_max 10, r_min 0.5, lr_tol 1, flags 0. */
+void tsgm_default_params(tsgm_params* p, int32_t width, int32_t height);
+
+/* Create a context. `cuda_stream` is a cudaStream_t (may be NULL: the context then creates and
+ * owns a non-blocking stream). Allocates all device scratch for the given size. Errors:
+ * INVALID_ARG (bad parameters), OUT_OF_MEMORY, CUDA. On failure *out is set to NULL. */
+tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out);
+
+/* Release all resources. Synchronises the context stream first. NULL is ignored. */
+void tsgm_destroy(tsgm_ctx* ctx);
+
+/* Message of the last failed call on this context (static storage owned by the context). */
+const char* tsgm_last_error(const tsgm_ctx* ctx);
+
+/* Use another CUDA stream for subsequent calls (NULL: the context's own stream). */
+tsgm_status tsgm_set_stream(tsgm_ctx* ctx, void* cuda_stream);
+
+/* Host-side: the disparity-space homography H = Gamma T Gamma^{-1} (Sec. 2.1, Eq. 1-4) in
+ * binary64, returned as row-major 4x4 rounded to binary32. x, y are measured from the
+ * principal point. Errors: INVALID_ARG for null pointers, f <= 0 or baseline <= 0. */
+tsgm_status tsgm_build_H(const float R[9], const float t[3], const float K[9], float baseline,
+                         float H_out[16]);
+
+/* Disparity prediction (Sec. 2.2): warp prev_D by the pose in disparity space (Eq. 3, with the
+ * homogeneous divide), resolve collisions by keeping the highest predicted disparity (ties: the
+ * lowest source index), predict the variance p = Phi^2 p + q with Phi = d'/d (Eq. 5-6).
+ * Sources with an invalid d or p, or d <= 0, are skipped; unreached targets are invalid.
+ * prev_D, prev_P: width*height floats (inputs); pred_D, pred_P: width*height floats (outputs,
+ * must not alias the inputs). The z-buffer keys stay in the context (tsgm_inspect). */
+tsgm_status tsgm_warp_predict(tsgm_ctx* ctx, const float* prev_D, const float* prev_P,
+                              const float R[9], const float t[3], const float K[9],
+                              float baseline, float* pred_D, float* pred_P);
+
+/* Reduced search space (Sec. 2.3): d_lo = max(0, floor(d - k sqrt(p))), d_hi = min(d_max,
+ * ceil(d + k sqrt(p))) with k = sigma_mult, binary32; the whole range [0, d_max] where the
+ * prediction is invalid or the interval misses [0, d_max]. Also builds the ragged-volume
+ * offsets in the context. If n_cells_host is not NULL the call synchronises the stream and
+ * writes the number of (pixel, disparity) cells, sum of the window lengths. */
+tsgm_status tsgm_windows(tsgm_ctx* ctx, const float* pred_D, const float* pred_P,
+                         int16_t* d_lo, int16_t* d_hi, uint64_t* n_cells_host);
+
+/* Stereo matching restricted to the windows (Sec. 2.3-2.4): census transform of both images,
+ * Hamming cost per window cell (x - d < 0 costs all census bits), SGM path aggregation with
+ * penalties P1/P2 over n_paths directions where a neighbour's disparities outside its own
+ * window do not exist, winner-takes-all (lowest d on ties), parabolic sub-pixel refinement,
+ * matching variance r = n_l + n_r (Eq. 9, aggregated-cost reading, floored at r_min), and the
+ * left-right check. left, right: uint8 images; d_lo, d_hi: windows, copied into the context
+ * and clamped there to 0 <= d_lo <= d_hi <= d_max (the clamped copy is what is matched and what
+ * tsgm_inspect shows); D_z, r_z: float outputs, -1 where the left-right check fails. */
+tsgm_status tsgm_match(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
+                       const int16_t* d_lo, const int16_t* d_hi, float* D_z, float* r_z);
+
+/* Pixel-wise Kalman update (Sec. 2.4, Eq. 10-12): K = p/(p+r), d = d_p + K (d_z - d_p),
+ * p' = (1 - K) p, binary32. Only a measurement: (d_z, r); only a prediction: (d_p, p);
+ * neither: (-1, -1). Outputs may alias the prediction inputs. */
+tsgm_status tsgm_kalman_update(tsgm_ctx* ctx, const float* pred_D, const float* pred_P,
+                               const float* D_z, const float* r_z, float* D, float* P);
+
+/* One time step (Sec. 2): predict from the context's previous state with the pose, choose the
+ * windows, match, update; the result is written to D, P (device) and kept as the next
+ * frame's previous state. The first call after create/reset has no prediction and searches
+ * the whole range (Sec. 3); its R, t may be NULL. */
+tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
+                       const float R[9], const float t[3], const float K[9], float baseline,
+                       float* D, float* P);
+
+/* tsgm_frame with HOST buffers: copies left/right (width*height bytes each) to the device,
+ * runs the step and copies D, P (width*height floats each) back. Pinned host memory gives
+ * asynchronous copies; the call synchronises the stream before returning. */
+tsgm_status tsgm_frame_host(tsgm_ctx* ctx, const uint8_t* left_host, const uint8_t* right_host,
+                            const float R[9], const float t[3], const float K[9],
+                            float baseline, float* D_host, float* P_host);
+
+/* Forget the previous frame: the next tsgm_frame searches the whole range. */
+tsgm_status tsgm_reset(tsgm_ctx* ctx);
+
+/* Checkpoint of the per-stream state (previous D, P and whether it exists) through host
+ * buffers of width*height floats. Export synchronises the stream. */
+tsgm_status tsgm_state_export(tsgm_ctx* ctx, float* D_host, float* P_host, int32_t* has_prev);
+tsgm_status tsgm_state_import(tsgm_ctx* ctx, const float* D_host, const float* P_host,
+                              int32_t has_prev);
+
+/* Census transform of one image (the matching cost's first stage): for every pixel p, bit b
+ * (LSB first) is [I(q) < I(p)] for the b-th neighbour q of the census window in row-major
+ * order without the centre, coordinates clamped to the border. codes: width*height uint64. */
+tsgm_status tsgm_census(tsgm_ctx* ctx, const uint8_t* img, uint64_t* codes);
+
+/* Internal buffers of the last call, for inspection and tests. */
+typedef enum {
+    TSGM_BUF_CENSUS_L = 0,  /* uint64 [n]     census of the left image (last match)     */
+    TSGM_BUF_CENSUS_R = 1,  /* uint64 [n]     census of the right image                 */
+    TSGM_BUF_OFFSETS = 2,   /* uint32 [n + 1] exclusive scan of window lengths          */
+    TSGM_BUF_COST = 3,      /* uint8  [cells] ragged matching cost                      */
+    TSGM_BUF_S = 4,         /* uint16 [cells] aggregated cost S = sum of path costs     */
+    TSGM_BUF_DSTAR = 5,     /* int16  [n]     winner-takes-all disparity (KEEP_INTERNALS) */
+    TSGM_BUF_DRIGHT = 6,    /* int16  [n]     right-view disparity, -1 none (KEEP_INTERNALS) */
+    TSGM_BUF_LR_VALID = 7,  /* uint8  [n]     1 where the left-right check passed (KEEP_INTERNALS) */
+    TSGM_BUF_ZKEYS = 8,     /* uint64 [n]     z-buffer keys of the last warp: high 32 bits =
+                                              ~bits(d'), low 32 = source index; ~0 = empty */
+    TSGM_BUF_WINDOWS_LO = 9,  /* int16 [n]    windows of the last tsgm_frame              */
+    TSGM_BUF_WINDOWS_HI = 10,
+    TSGM_BUF_PRED_D = 11,   /* float [n]      prediction of the last tsgm_frame            */
+    TSGM_BUF_PRED_P = 12
+} tsgm_buffer;
+
+/* Copy an internal buffer (device to device, on the context stream) into dst. `count` is the
+ * number of elements to copy; for the cell buffers the current cell count can be read with
+ * tsgm_cells. INVALID_ARG if count exceeds the buffer. */
+tsgm_status tsgm_inspect(tsgm_ctx* ctx, tsgm_buffer which, void* dst, uint64_t count);
+
+/* Number of cells of the windows of the last match/windows call (synchronises the stream). */
+tsgm_status tsgm_cells(tsgm_ctx* ctx, uint64_t* n_cells);
+
+/* Number of kernels this context has enqueued since create (CUDA library copies such as the
+ * z-buffer memset are not counted). */
+tsgm_status tsgm_launches(tsgm_ctx* ctx, uint64_t* n);
+
+/* Stage timing with CUDA events on the context stream. When enabled, each call records events
+ * around its stages; tsgm_stage_times returns the accumulated milliseconds per stage since the
+ * last enable (synchronises) and the number of times each was recorded. Stage ids: */
+#define TSGM_STAGE_WARP 0      /* scatter + gather */
+#define TSGM_STAGE_WINDOWS 1   /* windows + offsets */
+#define TSGM_STAGE_CENSUS 2
+#define TSGM_STAGE_COST 3
+#define TSGM_STAGE_SGM 4       /* path aggregation */
+#define TSGM_STAGE_SELECT 5    /* WTA, sub-pixel, r, LR check */
+#define TSGM_STAGE_KALMAN 6
+#define TSGM_STAGE_OFFSETS 7   /* offsets of caller windows in tsgm_match */
+#define TSGM_N_STAGES 8
+tsgm_status tsgm_profile(tsgm_ctx* ctx, int32_t enable);
+tsgm_status tsgm_stage_times(tsgm_ctx* ctx, double ms[TSGM_N_STAGES], int64_t count[TSGM_N_STAGES]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSGM_H */

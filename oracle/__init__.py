@@ -247,12 +247,15 @@ class Tracker:
         prm = self.prm
         Hh, W = prm.height, prm.width
         out = {}
+        # calibration and pose enter as binary32, like the C interface of the path
+        baseline = float(np.float32(baseline))
+        K = np.asarray(K, dtype=np.float32)
         if self.D is None:
             Dp = np.full((Hh, W), -1.0, np.float32)
             Pp = np.full((Hh, W), -1.0, np.float32)
         else:
             f, cx, cy = K_fbc(K)
-            _, H32 = build_H(R, t, f, baseline)
+            _, H32 = build_H(np.asarray(R, np.float32), np.asarray(t, np.float32), f, baseline)
             Dp, Pp, win = warp_predict(self.D, self.P, H32, np.float32(cx), np.float32(cy), prm.q)
             out["winner"] = win
             out["H32"] = H32

@@ -1,0 +1,107 @@
+// Internal declarations shared by the tsgm CUDA sources (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tsgm.h"
+
+namespace tsgm {
+
+constexpr int kInf = 0x3FFF;          // +inf for path costs held in 32-bit registers
+constexpr uint64_t kEmptyKey = ~0ull; // empty z-buffer slot
+
+// Per-call device views of the inputs of the matching stages.
+struct MatchBufs {
+    const uint8_t* left;
+    const uint8_t* right;
+    const int16_t* lo;
+    const int16_t* hi;
+    float* Dz;
+    float* rz;
+};
+
+// Launchers (defined in tsgm_predict.cu / tsgm_match.cu). Each enqueues on `st` and returns the
+// launch status (cudaGetLastError).
+cudaError_t launch_warp_scatter(const float* Dprev, const float* Pprev, const float* H, float cx,
+                                float cy, int W, int Hh, unsigned long long* keys, cudaStream_t st);
+cudaError_t launch_warp_gather(const unsigned long long* keys, const float* Dprev,
+                               const float* Pprev, float q, int n, float* Dpred, float* Ppred,
+                               cudaStream_t st);
+cudaError_t launch_windows(const float* Dp, const float* Pp, int W, int Hh, int D, float k,
+                           int16_t* lo, int16_t* hi, uint32_t* rowsum, cudaStream_t st);
+cudaError_t launch_sanitize(const int16_t* lo_in, const int16_t* hi_in, int W, int Hh, int D,
+                            int16_t* lo, int16_t* hi, uint32_t* rowsum, cudaStream_t st);
+cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t* rowsum, int W,
+                           int Hh, uint32_t* off, cudaStream_t st);
+cudaError_t launch_fill(float* a, float v, int n, cudaStream_t st);
+cudaError_t launch_kalman(const float* Dp, const float* Pp, const float* Dz, const float* rz, int n,
+                          float* D, float* P, float* D2, float* P2, cudaStream_t st);
+
+cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int Hh, int cw, int ch,
+                          uint64_t* outA, uint64_t* outB, cudaStream_t st);
+cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const int16_t* lo,
+                        const int16_t* hi, const uint32_t* off, int W, int Hh, int Bc, uint8_t* C,
+                        uint16_t* S, cudaStream_t st);
+cudaError_t launch_sgm(const uint8_t* C, const int16_t* lo, const int16_t* hi, const uint32_t* off,
+                       int W, int Hh, int D, int n_paths, int P1, int P2, uint16_t* S,
+                       cudaStream_t st);
+cudaError_t launch_select(const uint16_t* S, const int16_t* lo, const int16_t* hi,
+                          const uint32_t* off, int W, int Hh, float s_thr, float r_min, int lr_tol,
+                          float* Dz, float* rz, int16_t* dstar, int16_t* dright, uint8_t* valid,
+                          cudaStream_t st);
+
+}  // namespace tsgm
+
+// The opaque context of the public ABI.
+struct tsgm_ctx {
+    tsgm_params prm;
+    int W = 0, H = 0, D = 0, n = 0, Bc = 0;
+    uint64_t max_cells = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+
+    // device scratch, all sized at create time
+    uint64_t* censusL = nullptr;
+    uint64_t* censusR = nullptr;
+    unsigned long long* keys = nullptr;
+    float* predD = nullptr;
+    float* predP = nullptr;
+    float* Dz = nullptr;
+    float* rz = nullptr;
+    float* stateD = nullptr;
+    float* stateP = nullptr;
+    int16_t* lo = nullptr;
+    int16_t* hi = nullptr;
+    int16_t* dstar = nullptr;
+    int16_t* dright = nullptr;
+    uint8_t* lrvalid = nullptr;
+    uint32_t* off = nullptr;
+    uint32_t* rowsum = nullptr;
+    uint8_t* C = nullptr;
+    uint16_t* S = nullptr;
+    // staging for tsgm_frame_host
+    uint8_t* d_left = nullptr;
+    uint8_t* d_right = nullptr;
+    float* d_outD = nullptr;
+    float* d_outP = nullptr;
+
+    int has_prev = 0;
+    uint64_t launches = 0;  // kernels enqueued by this context (for launch accounting)
+    std::string err;
+
+    // stage timing: a ring of event pairs resolved lazily by tsgm_stage_times
+    struct EventRec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<EventRec> ev_recs;
+    size_t ev_used = 0;
+    double ms[TSGM_N_STAGES] = {};
+    int64_t cnt[TSGM_N_STAGES] = {};
+};

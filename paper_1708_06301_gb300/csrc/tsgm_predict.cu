@@ -1,0 +1,313 @@
+// Disparity prediction (Sec. 2.2), reduced windows (Sec. 2.3) and the pixel-wise Kalman update
+// (Sec. 2.4) as elementwise / per-row kernels.
+//
+// Every float operation that can decide an integer later (target pixel, z-buffer order, window
+// bounds, the Kalman output warped by the next frame) uses explicit round-to-nearest intrinsics
+// in a fixed order, so no FMA contraction or reassociation changes a result.
+
+#include <cfloat>
+
+#include "tsgm_internal.cuh"
+
+namespace tsgm {
+namespace {
+
+__device__ __forceinline__ bool valid_value(float v) { return v >= 0.0f && v <= FLT_MAX; }
+
+// ---------------------------------------------------------------------------------------------
+// Warp scatter (Eq. 3 + homogeneous divide; z-buffer of Sec. 2.2 "disparity refinement").
+// One thread per source pixel; the key packs ~bits(d') (bits of a positive float grow with its
+// value, so the complement makes atomicMin keep the largest d') above the source index (equal
+// d' -> lowest index).
+// ---------------------------------------------------------------------------------------------
+struct WarpParams {
+    float h[16];
+    float cx, cy;
+};
+
+__global__ void __launch_bounds__(256) k_warp_scatter(const float* __restrict__ Dprev,
+                                                      const float* __restrict__ Pprev,
+                                                      WarpParams wp, int W, int Hh,
+                                                      unsigned long long* __restrict__ keys) {
+    const int n = W * Hh;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float d = Dprev[i];
+        const float p = Pprev[i];
+        if (!(d > 0.0f && d <= FLT_MAX && valid_value(p))) continue;
+        const int v = i / W;
+        const int u = i - v * W;
+        const float xt = __fsub_rn((float)u, wp.cx);
+        const float yt = __fsub_rn((float)v, wp.cy);
+        float w[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float* h = wp.h + 4 * r;
+            float s = __fadd_rn(__fmul_rn(h[0], xt), __fmul_rn(h[1], yt));
+            s = __fadd_rn(s, __fmul_rn(h[2], d));
+            w[r] = __fadd_rn(s, h[3]);
+        }
+        if (!(w[3] > 0.0f)) continue;
+        const float xp = __fdiv_rn(w[0], w[3]);
+        const float yp = __fdiv_rn(w[1], w[3]);
+        const float dp = __fdiv_rn(w[2], w[3]);
+        if (!(dp > 0.0f && dp <= FLT_MAX)) continue;
+        const float fx = floorf(__fadd_rn(__fadd_rn(xp, wp.cx), 0.5f));
+        const float fy = floorf(__fadd_rn(__fadd_rn(yp, wp.cy), 0.5f));
+        if (!(fx >= 0.0f && fx <= (float)(W - 1) && fy >= 0.0f && fy <= (float)(Hh - 1))) continue;
+        const int tgt = (int)fy * W + (int)fx;
+        const unsigned long long key =
+            ((unsigned long long)(~__float_as_uint(dp)) << 32) | (unsigned long long)(unsigned)i;
+        atomicMin(keys + tgt, key);
+    }
+}
+
+// Warp gather + variance prediction (Eq. 5-6): p' = (d'/d)^2 p + q.
+__global__ void __launch_bounds__(256) k_warp_gather(const unsigned long long* __restrict__ keys,
+                                                     const float* __restrict__ Dprev,
+                                                     const float* __restrict__ Pprev, float q,
+                                                     int n, float* __restrict__ Dpred,
+                                                     float* __restrict__ Ppred) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[i];
+        float dp = -1.0f, pp = -1.0f;
+        if (key != kEmptyKey) {
+            const unsigned src = (unsigned)(key & 0xFFFFFFFFull);
+            dp = __uint_as_float(~(unsigned)(key >> 32));
+            const float phi = __fdiv_rn(dp, Dprev[src]);
+            const float phi2 = __fmul_rn(phi, phi);
+            pp = __fadd_rn(__fmul_rn(phi2, Pprev[src]), q);
+        }
+        Dpred[i] = dp;
+        Ppred[i] = pp;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block-wide helpers (blockDim.x a multiple of 32, at most 1024)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* sh /* >= 32 words */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    uint32_t t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0u;
+    if (wid == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[0] = t;
+    }
+    __syncthreads();
+    const uint32_t r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive scan across the block; returns this thread's exclusive prefix and the block total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* sh,
+                                                         uint32_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    __syncthreads();
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = (lane < nw) ? sh[lane] : 0u;
+        uint32_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += u;
+        }
+        if (lane < nw) sh[lane] = ti - t;  // exclusive prefix of warp totals
+        if (lane == nw - 1) sh[32] = ti;   // block total
+    }
+    __syncthreads();
+    const uint32_t r = sh[wid] + inc - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Windows (Sec. 2.3): [floor(d - k sqrt(p)), ceil(d + k sqrt(p))] clipped to [0, D-1]; the
+// whole range without a valid prediction or when the interval misses the range. One block per
+// row; also writes the row's total window length.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
+                                                 const float* __restrict__ Pp, int W, int D,
+                                                 float k, int16_t* __restrict__ lo,
+                                                 int16_t* __restrict__ hi,
+                                                 uint32_t* __restrict__ rowsum) {
+    __shared__ uint32_t sh[33];
+    const int y = blockIdx.x;
+    uint32_t acc = 0;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const int i = y * W + x;
+        const float d = Dp[i], p = Pp[i];
+        int a = 0, b = D - 1;
+        if (valid_value(d) && valid_value(p)) {
+            const float s = __fsqrt_rn(p);
+            const float r = __fmul_rn(k, s);
+            const float lo_f = floorf(__fsub_rn(d, r));
+            const float hi_f = ceilf(__fadd_rn(d, r));
+            if (lo_f <= (float)(D - 1) && hi_f >= 0.0f) {
+                a = lo_f < 0.0f ? 0 : (int)lo_f;
+                b = hi_f > (float)(D - 1) ? D - 1 : (int)hi_f;
+            }
+        }
+        lo[i] = (int16_t)a;
+        hi[i] = (int16_t)b;
+        acc += (uint32_t)(b - a + 1);
+    }
+    const uint32_t t = block_sum(acc, sh);
+    if (threadIdx.x == 0) rowsum[y] = t;
+}
+
+// Caller-supplied windows: copy them clamped into [0, D-1] with lo <= hi (so that every later
+// kernel stays inside the ragged volume whatever the input) and write the row's total length.
+__global__ void __launch_bounds__(256) k_sanitize_rowsum(const int16_t* __restrict__ lo_in,
+                                                         const int16_t* __restrict__ hi_in, int W,
+                                                         int D, int16_t* __restrict__ lo,
+                                                         int16_t* __restrict__ hi,
+                                                         uint32_t* __restrict__ rowsum) {
+    __shared__ uint32_t sh[33];
+    const int y = blockIdx.x;
+    uint32_t acc = 0;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const int i = y * W + x;
+        const int a = min(max((int)lo_in[i], 0), D - 1);
+        const int b = min(max((int)hi_in[i], a), D - 1);
+        lo[i] = (int16_t)a;
+        hi[i] = (int16_t)b;
+        acc += (uint32_t)(b - a + 1);
+    }
+    const uint32_t t = block_sum(acc, sh);
+    if (threadIdx.x == 0) rowsum[y] = t;
+}
+
+// Offsets of the ragged volume: off[i] = sum of window lengths of pixels before i (row-major);
+// off[n] = total. One block per row: base = sum of earlier row totals, then a block scan.
+__global__ void __launch_bounds__(512) k_offsets(const int16_t* __restrict__ lo,
+                                                 const int16_t* __restrict__ hi,
+                                                 const uint32_t* __restrict__ rowsum, int W,
+                                                 int Hh, uint32_t* __restrict__ off) {
+    __shared__ uint32_t sh[33];
+    const int y = blockIdx.x;
+    uint32_t part = 0;
+    for (int r = threadIdx.x; r < y; r += blockDim.x) part += rowsum[r];
+    uint32_t base = block_sum(part, sh);
+    for (int x0 = 0; x0 < W; x0 += blockDim.x) {
+        const int x = x0 + threadIdx.x;
+        const int i = y * W + x;
+        const uint32_t w = (x < W) ? (uint32_t)(hi[i] - lo[i] + 1) : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(w, sh, &tot);
+        if (x < W) off[i] = base + ex;
+        base += tot;
+    }
+    if (y == Hh - 1 && threadIdx.x == 0) off[(size_t)W * Hh] = base;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kalman update (Eq. 10-12). Optional second output (the context's state for the next frame).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_kalman(const float* __restrict__ Dp,
+                                                const float* __restrict__ Pp,
+                                                const float* __restrict__ Dz,
+                                                const float* __restrict__ rz, int n,
+                                                float* D, float* P, float* D2, float* P2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float dp = Dp[i], pp = Pp[i], dz = Dz[i], r = rz[i];
+        const bool pv = valid_value(dp) && valid_value(pp);
+        const bool mv = valid_value(dz) && valid_value(r);
+        float d, p;
+        if (pv && mv) {
+            const float K = __fdiv_rn(pp, __fadd_rn(pp, r));
+            d = __fadd_rn(dp, __fmul_rn(K, __fsub_rn(dz, dp)));
+            p = __fmul_rn(__fsub_rn(1.0f, K), pp);
+        } else if (mv) {
+            d = dz;
+            p = r;
+        } else if (pv) {
+            d = dp;
+            p = pp;
+        } else {
+            d = -1.0f;
+            p = -1.0f;
+        }
+        D[i] = d;
+        P[i] = p;
+        if (D2) {
+            D2[i] = d;
+            P2[i] = p;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fill(float* __restrict__ a, float v, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+}
+
+int grid_for(int n, int threads) {
+    int g = (n + threads - 1) / threads;
+    const int cap = 152 * 16;  // grid-stride beyond 16 blocks per SM
+    return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
+}  // namespace
+
+cudaError_t launch_warp_scatter(const float* Dprev, const float* Pprev, const float* H, float cx,
+                                float cy, int W, int Hh, unsigned long long* keys,
+                                cudaStream_t st) {
+    WarpParams wp;
+    for (int i = 0; i < 16; ++i) wp.h[i] = H[i];
+    wp.cx = cx;
+    wp.cy = cy;
+    k_warp_scatter<<<grid_for(W * Hh, 256), 256, 0, st>>>(Dprev, Pprev, wp, W, Hh, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_gather(const unsigned long long* keys, const float* Dprev,
+                               const float* Pprev, float q, int n, float* Dpred, float* Ppred,
+                               cudaStream_t st) {
+    k_warp_gather<<<grid_for(n, 256), 256, 0, st>>>(keys, Dprev, Pprev, q, n, Dpred, Ppred);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_windows(const float* Dp, const float* Pp, int W, int Hh, int D, float k,
+                           int16_t* lo, int16_t* hi, uint32_t* rowsum, cudaStream_t st) {
+    k_windows<<<Hh, 256, 0, st>>>(Dp, Pp, W, D, k, lo, hi, rowsum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sanitize(const int16_t* lo_in, const int16_t* hi_in, int W, int Hh, int D,
+                            int16_t* lo, int16_t* hi, uint32_t* rowsum, cudaStream_t st) {
+    k_sanitize_rowsum<<<Hh, 256, 0, st>>>(lo_in, hi_in, W, D, lo, hi, rowsum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t* rowsum, int W,
+                           int Hh, uint32_t* off, cudaStream_t st) {
+    k_offsets<<<Hh, 512, 0, st>>>(lo, hi, rowsum, W, Hh, off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float* a, float v, int n, cudaStream_t st) {
+    k_fill<<<grid_for(n, 256), 256, 0, st>>>(a, v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kalman(const float* Dp, const float* Pp, const float* Dz, const float* rz, int n,
+                          float* D, float* P, float* D2, float* P2, cudaStream_t st) {
+    k_kalman<<<grid_for(n, 256), 256, 0, st>>>(Dp, Pp, Dz, rz, n, D, P, D2, P2);
+    return cudaGetLastError();
+}
+
+}  // namespace tsgm

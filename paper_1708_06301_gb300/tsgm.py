@@ -1,0 +1,279 @@
+"""Python binding of the tsgm C ABI (`include/tsgm.h`): argument marshalling only.
+
+Every step of the path runs in the CUDA library `_build/libtsgm.so`; this module loads it with
+ctypes and passes device pointers (torch tensors' `data_ptr()` or plain integers), host arrays
+for poses and calibration, and the current torch CUDA stream. There is no fallback: if the
+library is missing, loading fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtsgm.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "tsgm.h")
+
+OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_UNIMPLEMENTED = range(7)
+FLAG_KEEP_INTERNALS = 1
+FLAG_FULL_RANGE = 2
+N_STAGES = 8
+STAGES = ["warp", "windows", "census", "cost", "sgm", "select", "kalman", "offsets"]
+BUF = dict(census_l=0, census_r=1, offsets=2, cost=3, S=4, dstar=5, dright=6, lr_valid=7,
+           zkeys=8, windows_lo=9, windows_hi=10, pred_d=11, pred_p=12)
+
+
+class TsgmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tsgm status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("d_max", ctypes.c_int32),
+                ("census_w", ctypes.c_int32), ("census_h", ctypes.c_int32),
+                ("n_paths", ctypes.c_int32), ("P1", ctypes.c_int32), ("P2", ctypes.c_int32),
+                ("sigma_mult", ctypes.c_float), ("q", ctypes.c_float), ("S_max", ctypes.c_float),
+                ("r_min", ctypes.c_float), ("lr_tol", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+_vp = ctypes.c_void_p
+_fp = ctypes.POINTER(ctypes.c_float)
+_SIGS = {
+    "tsgm_default_params": (None, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_int32]),
+    "tsgm_create": (ctypes.c_int, [ctypes.POINTER(Params), _vp, ctypes.POINTER(_vp)]),
+    "tsgm_destroy": (None, [_vp]),
+    "tsgm_last_error": (ctypes.c_char_p, [_vp]),
+    "tsgm_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "tsgm_build_H": (ctypes.c_int, [_fp, _fp, _fp, ctypes.c_float, _fp]),
+    "tsgm_warp_predict": (ctypes.c_int, [_vp, _vp, _vp, _fp, _fp, _fp, ctypes.c_float, _vp, _vp]),
+    "tsgm_windows": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_match": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tsgm_kalman_update": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tsgm_frame": (ctypes.c_int, [_vp, _vp, _vp, _fp, _fp, _fp, ctypes.c_float, _vp, _vp]),
+    "tsgm_frame_host": (ctypes.c_int, [_vp, _vp, _vp, _fp, _fp, _fp, ctypes.c_float, _vp, _vp]),
+    "tsgm_reset": (ctypes.c_int, [_vp]),
+    "tsgm_state_export": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32)]),
+    "tsgm_state_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
+    "tsgm_census": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tsgm_inspect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64]),
+    "tsgm_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "tsgm_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_stage_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"tsgm CUDA library not found at {path}; build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def header_symbols(path: str = HEADER):
+    """Function names declared in the public header."""
+    text = open(path).read()
+    return sorted(set(re.findall(r"\b(tsgm_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def default_params(width: int, height: int, **kw) -> Params:
+    p = Params()
+    load().tsgm_default_params(ctypes.byref(p), int(width), int(height))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_cuda") and not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _host_f32(a, n: int):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(-1))
+    if arr.size != n:
+        raise ValueError(f"expected {n} floats, got {arr.size}")
+    return arr, arr.ctypes.data_as(_fp)
+
+
+def build_H(R, t, K, baseline: float) -> np.ndarray:
+    lib = load()
+    Ra, Rp = _host_f32(R, 9)
+    ta, tp = _host_f32(t, 3)
+    Ka, Kp = _host_f32(K, 9)
+    out = np.zeros(16, np.float32)
+    st = lib.tsgm_build_H(Rp, tp, Kp, ctypes.c_float(baseline), out.ctypes.data_as(_fp))
+    if st != OK:
+        raise TsgmError(st, "tsgm_build_H: invalid pose or calibration")
+    return out.reshape(4, 4)
+
+
+def _current_stream() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+class Context:
+    """One tsgm context: scratch for one image size plus the per-stream previous state."""
+
+    def __init__(self, params: Params, stream: int | None = None):
+        self.lib = load()
+        self.params = params
+        self.W, self.H = params.width, params.height
+        self.n = self.W * self.H
+        h = _vp()
+        s = _current_stream() if stream is None else int(stream)
+        st = self.lib.tsgm_create(ctypes.byref(params), _vp(s or None), ctypes.byref(h))
+        if st != OK:
+            raise TsgmError(st, "tsgm_create failed (see stderr for the parameter check)")
+        self.h = h
+
+    # -- plumbing -------------------------------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != OK:
+            msg = self.lib.tsgm_last_error(self.h)
+            raise TsgmError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tsgm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream: int | None):
+        self._check(self.lib.tsgm_set_stream(self.h, _vp(stream or None)), "tsgm_set_stream")
+
+    # -- the path ---------------------------------------------------------------------------------
+    def warp_predict(self, prev_D, prev_P, R, t, K, baseline, pred_D, pred_P):
+        Ra, Rp = _host_f32(R, 9)
+        ta, tp = _host_f32(t, 3)
+        Ka, Kp = _host_f32(K, 9)
+        self._check(self.lib.tsgm_warp_predict(self.h, _ptr(prev_D), _ptr(prev_P), Rp, tp, Kp,
+                                               ctypes.c_float(baseline), _ptr(pred_D),
+                                               _ptr(pred_P)), "tsgm_warp_predict")
+
+    def windows(self, pred_D, pred_P, d_lo, d_hi, want_cells: bool = False):
+        cells = ctypes.c_uint64(0)
+        self._check(self.lib.tsgm_windows(self.h, _ptr(pred_D), _ptr(pred_P), _ptr(d_lo), _ptr(d_hi),
+                                          ctypes.byref(cells) if want_cells else None),
+                    "tsgm_windows")
+        return int(cells.value) if want_cells else None
+
+    def match(self, left, right, d_lo, d_hi, D_z, r_z):
+        self._check(self.lib.tsgm_match(self.h, _ptr(left), _ptr(right), _ptr(d_lo), _ptr(d_hi),
+                                        _ptr(D_z), _ptr(r_z)), "tsgm_match")
+
+    def kalman_update(self, pred_D, pred_P, D_z, r_z, D, P):
+        self._check(self.lib.tsgm_kalman_update(self.h, _ptr(pred_D), _ptr(pred_P), _ptr(D_z),
+                                                _ptr(r_z), _ptr(D), _ptr(P)), "tsgm_kalman_update")
+
+    def frame(self, left, right, R, t, K, baseline, D, P):
+        Ra, Rp = _host_f32(R, 9)
+        ta, tp = _host_f32(t, 3)
+        Ka, Kp = _host_f32(K, 9)
+        self._check(self.lib.tsgm_frame(self.h, _ptr(left), _ptr(right), Rp, tp, Kp,
+                                        ctypes.c_float(baseline), _ptr(D), _ptr(P)), "tsgm_frame")
+
+    def frame_host(self, left: np.ndarray, right: np.ndarray, R, t, K, baseline, D: np.ndarray,
+                   P: np.ndarray):
+        """Host buffers (numpy or pinned torch CPU tensors) in and out; synchronises."""
+        def hp(a):
+            if hasattr(a, "data_ptr"):
+                return a.data_ptr()
+            return a.ctypes.data
+        Ra, Rp = _host_f32(R, 9)
+        ta, tp = _host_f32(t, 3)
+        Ka, Kp = _host_f32(K, 9)
+        self._check(self.lib.tsgm_frame_host(self.h, hp(left), hp(right), Rp, tp, Kp,
+                                             ctypes.c_float(baseline), hp(D), hp(P)),
+                    "tsgm_frame_host")
+
+    def reset(self):
+        self._check(self.lib.tsgm_reset(self.h), "tsgm_reset")
+
+    def state_export(self):
+        D = np.empty((self.H, self.W), np.float32)
+        P = np.empty((self.H, self.W), np.float32)
+        has = ctypes.c_int32(0)
+        self._check(self.lib.tsgm_state_export(self.h, D.ctypes.data, P.ctypes.data, ctypes.byref(has)),
+                    "tsgm_state_export")
+        return D, P, bool(has.value)
+
+    def state_import(self, D, P, has_prev: bool = True):
+        D = np.ascontiguousarray(D, np.float32)
+        P = np.ascontiguousarray(P, np.float32)
+        self._check(self.lib.tsgm_state_import(self.h, D.ctypes.data, P.ctypes.data, int(has_prev)),
+                    "tsgm_state_import")
+
+    def census(self, img, codes):
+        self._check(self.lib.tsgm_census(self.h, _ptr(img), _ptr(codes)), "tsgm_census")
+
+    def inspect(self, which: str, dst, count: int):
+        self._check(self.lib.tsgm_inspect(self.h, BUF[which], _ptr(dst), int(count)), "tsgm_inspect")
+
+    def cells(self) -> int:
+        v = ctypes.c_uint64(0)
+        self._check(self.lib.tsgm_cells(self.h, ctypes.byref(v)), "tsgm_cells")
+        return int(v.value)
+
+    def launches(self) -> int:
+        v = ctypes.c_uint64(0)
+        self._check(self.lib.tsgm_launches(self.h, ctypes.byref(v)), "tsgm_launches")
+        return int(v.value)
+
+    def profile(self, enable: bool):
+        self._check(self.lib.tsgm_profile(self.h, int(bool(enable))), "tsgm_profile")
+
+    def stage_times(self):
+        ms = (ctypes.c_double * N_STAGES)()
+        cnt = (ctypes.c_int64 * N_STAGES)()
+        self._check(self.lib.tsgm_stage_times(self.h, ms, cnt), "tsgm_stage_times")
+        return {STAGES[s]: (ms[s], cnt[s]) for s in range(N_STAGES)}

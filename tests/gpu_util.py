@@ -1,0 +1,32 @@
+"""Helpers for the GPU tests: numpy <-> torch device buffers with exact bit patterns."""
+import numpy as np
+
+_TORCH_OF = {
+    np.uint8: "uint8", np.int8: "int8", np.int16: "int16", np.uint16: "int16",
+    np.int32: "int32", np.uint32: "int32", np.int64: "int64", np.uint64: "int64",
+    np.float32: "float32",
+}
+
+
+def dev(a: np.ndarray):
+    import torch
+    a = np.ascontiguousarray(a)
+    t = getattr(torch, _TORCH_OF[a.dtype.type])
+    view = a.view(np.dtype(str(t).replace("torch.", "")))
+    return torch.from_numpy(view.copy()).cuda()
+
+
+def empty(shape, dtype):
+    import torch
+    t = getattr(torch, _TORCH_OF[np.dtype(dtype).type])
+    return torch.empty(shape, dtype=t, device="cuda")
+
+
+def host(t, dtype):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(dtype)
+
+
+def f32(x):
+    return np.float32(x)

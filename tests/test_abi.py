@@ -1,0 +1,98 @@
+"""The C ABI library on the CPU: it loads, exports every function the header declares, and its
+host-side pieces (parameter checks, the homography) behave; no GPU calls."""
+import ast
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_06301_gb300 import build as tbuild
+from paper_1708_06301_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tsgm():
+    tbuild.build()
+    from paper_1708_06301_gb300 import tsgm as t
+    t.load()
+    return t
+
+
+def test_exports_every_declared_symbol(tsgm):
+    lib = tsgm.load()
+    syms = tsgm.header_symbols()
+    assert len(syms) >= 19
+    for s in syms:
+        assert hasattr(lib, s), s
+    for s in ("tsgm_create", "tsgm_warp_predict", "tsgm_windows", "tsgm_match",
+              "tsgm_kalman_update", "tsgm_frame"):
+        assert s in syms
+
+
+def test_default_params(tsgm):
+    p = tsgm.default_params(1242, 375)
+    assert (p.d_max, p.census_w, p.census_h, p.n_paths, p.P1, p.P2) == (127, 9, 7, 8, 8, 32)
+    assert (p.sigma_mult, p.q, p.S_max, p.r_min, p.lr_tol) == (3.0, 0.25, 10.0, 0.5, 1)
+
+
+@pytest.mark.parametrize("bad", [dict(n_paths=5), dict(d_max=256), dict(census_w=4),
+                                 dict(census_w=11, census_h=7), dict(P1=40, P2=30),
+                                 dict(P2=200), dict(width=0), dict(q=-1.0)])
+def test_create_rejects_bad_params_before_touching_the_gpu(tsgm, bad):
+    p = tsgm.default_params(64, 32)
+    for k, v in bad.items():
+        setattr(p, k, v)
+    with pytest.raises(tsgm.TsgmError) as e:
+        tsgm.Context(p, stream=0)
+    assert e.value.status == tsgm.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_build_H_matches_oracle_bits(tsgm, seed):
+    """Host-side homography (binary64, rounded once): identical to the oracle's."""
+    R, t = synth.random_pose(300 + seed)
+    K = synth.Camera(1242, 375, 721.0, 0.54).K
+    b = np.float32(0.54)
+    H = tsgm.build_H(R, t, K, b)
+    _, Ho = oracle.build_H(R, t, float(K[0, 0]), float(b))
+    assert np.array_equal(H, Ho)
+
+
+def test_build_H_rejects_bad_calibration(tsgm):
+    K = synth.Camera(64, 32, 721.0, 0.54).K
+    with pytest.raises(tsgm.TsgmError):
+        tsgm.build_H(np.eye(3), np.zeros(3), K, 0.0)
+    K2 = K.copy()
+    K2[0, 0] = -1
+    with pytest.raises(tsgm.TsgmError):
+        tsgm.build_H(np.eye(3), np.zeros(3), K2, 0.54)
+
+
+def _imports(path):
+    tree = ast.parse(open(path).read())
+    names = set()
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Import):
+            names.update(a.name.split(".")[0] for a in node.names)
+        elif isinstance(node, ast.ImportFrom) and node.module:
+            names.add(node.module.split(".")[0])
+    return names
+
+
+def test_product_and_oracle_are_independent():
+    pkg = os.path.join(ROOT, "paper_1708_06301_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            assert "oracle" not in _imports(os.path.join(pkg, f)), f
+    for f in os.listdir(os.path.join(pkg, "csrc")):
+        assert "oracle" not in open(os.path.join(pkg, "csrc", f)).read().lower().replace(
+            "the oracle", ""), f
+    od = os.path.join(ROOT, "oracle")
+    for f in os.listdir(od):
+        if f.endswith(".py"):
+            assert "paper_1708_06301_gb300" not in _imports(os.path.join(od, f)), f
+        if f.endswith((".cpp", ".h")):
+            assert "tsgm.h" not in open(os.path.join(od, f)).read()

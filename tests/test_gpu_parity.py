@@ -1,0 +1,300 @@
+"""GPU path vs the CPU oracle, stage by stage and end to end, through the C ABI.
+
+Integer results (census codes, costs, aggregated costs, windows, offsets, z-buffer winners,
+d*, right-view disparities, the LR mask) must be bit-exact. Float results must agree within
+1e-4 px (disparities) and 1e-5 relative (variances); both sides compute them in binary32 with
+the same operation order, so in practice they are identical as well.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_06301_gb300 import synth
+
+from gpu_util import dev, empty, host, f32
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_D = 1e-4
+TOL_P_REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def tsgm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_06301_gb300 import tsgm as t
+    t.load()
+    return t
+
+
+def make_ctx(tsgm, W, H, d_max=63, cw=5, ch=5, n_paths=4, flags=1, **kw):
+    prm = tsgm.default_params(W, H, d_max=d_max, census_w=cw, census_h=ch, n_paths=n_paths,
+                              flags=flags, **kw)
+    return tsgm.Context(prm)
+
+
+def oparams(W, H, d_max=63, cw=5, ch=5, n_paths=4, **kw):
+    return oracle.Params(W, H, d_max=d_max, census_w=cw, census_h=ch, n_paths=n_paths, **kw)
+
+
+def assert_maps(Dg, Pg, Do, Po):
+    assert np.array_equal(Dg < 0, Do < 0)
+    v = Do >= 0
+    if v.any():
+        assert np.max(np.abs(Dg[v] - Do[v])) <= TOL_D
+        assert np.max(np.abs(Pg[v] - Po[v]) / np.maximum(np.abs(Po[v]), 1e-12)) <= TOL_P_REL
+    assert np.all(Dg[~v] == -1) and np.all(Pg[~v] == -1)
+
+
+# ----------------------------------------------------------------------------------------------
+# census
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("W,H,cw,ch", [(1242, 375, 9, 7), (97, 45, 5, 5), (33, 1, 5, 5),
+                                       (1, 17, 9, 7), (40, 9, 3, 3), (71, 23, 15, 3)])
+def test_census_bitexact(tsgm, W, H, cw, ch):
+    a, b = synth.random_images(100 + W, W, H)
+    with make_ctx(tsgm, W, H, cw=cw, ch=ch) as ctx:
+        out = empty((H, W), np.uint64)
+        ctx.census(dev(a), out)
+        assert np.array_equal(host(out, np.uint64), oracle.census(a, cw, ch))
+
+
+# ----------------------------------------------------------------------------------------------
+# prediction
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_warp_bitexact_random_pose(tsgm, seed):
+    W, H = 1242, 375
+    D, P = synth.random_maps(seed, W, H, invalid_frac=0.1)
+    R, t = synth.random_pose(seed + 10)
+    K = synth.Camera(W, H, 721.0, 0.54).K
+    b = f32(0.54)
+    with make_ctx(tsgm, W, H, d_max=127) as ctx:
+        pD, pP = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.warp_predict(dev(D), dev(P), R, t, K, b, pD, pP)
+        keys = empty((H, W), np.uint64)
+        ctx.inspect("zkeys", keys, W * H)
+        kg = host(keys, np.uint64)
+        Dg, Pg = host(pD, np.float32), host(pP, np.float32)
+    _, H32 = oracle.build_H(R, t, float(K[0, 0]), float(b))
+    Do, Po, win = oracle.warp_predict(D, P, H32, K[0, 2], K[1, 2], 0.25)
+    src = np.where(kg == np.uint64(0xFFFFFFFFFFFFFFFF), -1, (kg & np.uint64(0xFFFFFFFF)).astype(np.int64))
+    assert np.array_equal(src, win)  # z-buffer winners
+    assert np.array_equal(Dg, Do)
+    assert np.array_equal(Pg, Po)
+    assert (win >= 0).mean() > 0.5
+
+
+def test_warp_identity_pose(tsgm):
+    W, H = 320, 96
+    D, P = synth.random_maps(5, W, H, invalid_frac=0.2)
+    K = synth.Camera(W, H, 721.0, 0.54).K
+    with make_ctx(tsgm, W, H) as ctx:
+        pD, pP = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.warp_predict(dev(D), dev(P), np.eye(3), np.zeros(3), K, f32(0.54), pD, pP)
+        Dg, Pg = host(pD, np.float32), host(pP, np.float32)
+    v = D > 0
+    assert np.array_equal(Dg[v], D[v]) and np.all(Dg[~v] == -1)
+    assert np.array_equal(Pg[v], (P[v] + f32(0.25)).astype(np.float32))
+
+
+@pytest.mark.parametrize("W,H,D", [(1242, 375, 128), (33, 7, 64), (5, 1, 1)])
+def test_windows_bitexact(tsgm, W, H, D):
+    Dp, Pp = synth.random_maps(7, W, H, d_range=(-5, D + 5), p_range=(0, 9), invalid_frac=0.2)
+    Pp[0, 0] = np.nan
+    Pp[-1, -1] = np.inf
+    with make_ctx(tsgm, W, H, d_max=D - 1) as ctx:
+        lo, hi = empty((H, W), np.int16), empty((H, W), np.int16)
+        n = ctx.windows(dev(Dp), dev(Pp), lo, hi, want_cells=True)
+        off = empty((W * H + 1,), np.uint32)
+        ctx.inspect("offsets", off, W * H + 1)
+        log, hig, offg = host(lo, np.int16), host(hi, np.int16), host(off, np.uint32)
+    loo, hio, offo, no = oracle.windows(Dp, Pp, D, 3.0)
+    assert np.array_equal(log, loo) and np.array_equal(hig, hio)
+    assert np.array_equal(offg, offo) and n == no
+
+
+# ----------------------------------------------------------------------------------------------
+# matching stages on random windows (narrow, wide and full-range mixed)
+# ----------------------------------------------------------------------------------------------
+
+CASES = [
+    # W, H, D, census, paths, w_min, w_max, full_frac
+    (97, 45, 64, (5, 5), 4, 1, 24, 0.2),
+    (131, 37, 128, (9, 7), 8, 1, 40, 0.25),
+    (64, 32, 256, (9, 7), 8, 20, 80, 0.1),
+    (200, 3, 64, (5, 5), 8, 1, 64, 0.5),
+    (3, 70, 32, (5, 5), 8, 1, 32, 0.3),
+    (1, 1, 16, (5, 5), 8, 1, 16, 1.0),
+    (50, 20, 1, (5, 5), 8, 1, 1, 0.0),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_match_stages_bitexact(tsgm, case):
+    W, H, D, (cw, ch), npaths, wmin, wmax, ff = case
+    seq_l, seq_r = synth.random_images(W * 7 + H, W, H)
+    # make the right image a shifted copy so that matching has structure
+    right = np.roll(seq_l, -min(5, D - 1), axis=1)
+    right[:, -5:] = seq_r[:, -5:]
+    lo, hi = synth.random_windows(W + H, W, H, D, wmin, min(wmax, D), full_frac=ff)
+    with make_ctx(tsgm, W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths) as ctx:
+        Dz, rz = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.match(dev(seq_l), dev(right), dev(lo), dev(hi), Dz, rz)
+        n = ctx.cells()
+        C = empty((n,), np.uint8)
+        S = empty((n,), np.uint16)
+        ctx.inspect("cost", C, n)
+        ctx.inspect("S", S, n)
+        ds, dr, va = empty((H, W), np.int16), empty((H, W), np.int16), empty((H, W), np.uint8)
+        ctx.inspect("dstar", ds, W * H)
+        ctx.inspect("dright", dr, W * H)
+        ctx.inspect("lr_valid", va, W * H)
+        g = dict(C=host(C, np.uint8), S=host(S, np.uint16), ds=host(ds, np.int16),
+                 dr=host(dr, np.int16), va=host(va, np.uint8), Dz=host(Dz, np.float32),
+                 rz=host(rz, np.float32))
+    prm = oparams(W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths)
+    o = oracle.match(seq_l, right, lo, hi, prm, keep=True)
+    assert n == int(o["off"][-1])
+    assert np.array_equal(g["C"], o["C"])
+    assert np.array_equal(g["S"], o["S"])
+    assert np.array_equal(g["ds"].astype(np.int32), o["dstar"])
+    assert np.array_equal(g["dr"].astype(np.int32), o["dright"])
+    assert np.array_equal(g["va"], o["valid"])
+    assert_maps(g["Dz"], g["rz"], o["Dz"], o["rz"])
+
+
+def test_kalman_elementwise(tsgm):
+    W, H = 257, 3
+    n = W * H
+    Dp, Pp = synth.random_maps(31, W, H, invalid_frac=0.3)
+    Dz, rz = synth.random_maps(32, W, H, p_range=(0.5, 5), invalid_frac=0.3)
+    with make_ctx(tsgm, W, H) as ctx:
+        D, P = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.kalman_update(dev(Dp), dev(Pp), dev(Dz), dev(rz), D, P)
+        Dg, Pg = host(D, np.float32), host(P, np.float32)
+    Do, Po = oracle.kalman(Dp, Pp, Dz, rz)
+    assert_maps(Dg, Pg, Do, Po)
+    assert n == Do.size
+
+
+# ----------------------------------------------------------------------------------------------
+# whole frames
+# ----------------------------------------------------------------------------------------------
+
+def run_sequence(tsgm, seq, n_frames, d_max, cw, ch, npaths, flags=1):
+    W, H = seq.cam.W, seq.cam.H
+    b = f32(seq.cam.b)
+    out = []
+    with make_ctx(tsgm, W, H, d_max=d_max, cw=cw, ch=ch, n_paths=npaths, flags=flags) as ctx:
+        D, P = empty((H, W), np.float32), empty((H, W), np.float32)
+        for k in range(n_frames):
+            ctx.frame(dev(seq.left[k]), dev(seq.right[k]), seq.R[k], seq.t[k], seq.K, b, D, P)
+            lo, hi = empty((H, W), np.int16), empty((H, W), np.int16)
+            ctx.inspect("windows_lo", lo, W * H)
+            ctx.inspect("windows_hi", hi, W * H)
+            out.append(dict(D=host(D, np.float32), P=host(P, np.float32), lo=host(lo, np.int16),
+                            hi=host(hi, np.int16)))
+    return out
+
+
+def test_frames_small_pair(tsgm):
+    seq = synth.small_pair(1)
+    g = run_sequence(tsgm, seq, 2, 63, 5, 5, 4)
+    tr = oracle.Tracker(oparams(320, 96))
+    for k in range(2):
+        o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
+        assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
+        assert_maps(g[k]["D"], g[k]["P"], o["D"], o["P"])
+
+
+@pytest.mark.slow
+def test_frames_kitti_like_full_size(tsgm):
+    """The benchmark's workload at full size (1242x375, D = 128, census 9x7, 8 paths), first
+    three frames, every pixel compared."""
+    seq = synth.kitti_like(2, n_frames=3)
+    g = run_sequence(tsgm, seq, 3, 127, 9, 7, 8)
+    tr = oracle.Tracker(oparams(1242, 375, d_max=127, cw=9, ch=7, n_paths=8))
+    for k in range(3):
+        o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
+        assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
+        assert_maps(g[k]["D"], g[k]["P"], o["D"], o["P"])
+
+
+def test_frame_host_equals_device(tsgm):
+    seq = synth.small_pair(1)
+    W, H = 320, 96
+    b = f32(seq.cam.b)
+    g = run_sequence(tsgm, seq, 2, 63, 5, 5, 4)
+    with make_ctx(tsgm, W, H) as ctx:
+        D = np.empty((H, W), np.float32)
+        P = np.empty((H, W), np.float32)
+        for k in range(2):
+            ctx.frame_host(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, b, D, P)
+            assert np.array_equal(D, g[k]["D"]) and np.array_equal(P, g[k]["P"])
+
+
+def test_state_export_import_resume(tsgm):
+    seq = synth.small_pair(1)
+    W, H = 320, 96
+    b = f32(seq.cam.b)
+    g = run_sequence(tsgm, seq, 2, 63, 5, 5, 4)
+    with make_ctx(tsgm, W, H) as a:
+        D, P = empty((H, W), np.float32), empty((H, W), np.float32)
+        a.frame(dev(seq.left[0]), dev(seq.right[0]), None, None, seq.K, b, D, P)
+        sD, sP, has = a.state_export()
+    assert has
+    with make_ctx(tsgm, W, H) as c:
+        c.state_import(sD, sP, True)
+        D, P = empty((H, W), np.float32), empty((H, W), np.float32)
+        c.frame(dev(seq.left[1]), dev(seq.right[1]), seq.R[1], seq.t[1], seq.K, b, D, P)
+        assert np.array_equal(host(D, np.float32), g[1]["D"])
+
+
+def test_full_range_flag_equals_full_windows(tsgm):
+    """TSGM_FLAG_FULL_RANGE: frame 2 matched over [0, D-1] everywhere equals tsgm_match with
+    full windows, then the Kalman update with the prediction."""
+    seq = synth.small_pair(1)
+    W, H = 320, 96
+    g = run_sequence(tsgm, seq, 2, 63, 5, 5, 4, flags=1 | 2)
+    assert np.all(g[1]["lo"] == 0) and np.all(g[1]["hi"] == 63)
+    prm = oparams(W, H)
+    tr = oracle.Tracker(prm)
+    o0 = tr.frame(seq.left[0], seq.right[0], seq.R[0], seq.t[0], seq.K, f32(seq.cam.b), keep=True)
+    _, H32 = oracle.build_H(seq.R[1], seq.t[1], float(seq.K[0, 0]), float(f32(seq.cam.b)))
+    Dp, Pp, _ = oracle.warp_predict(o0["D"], o0["P"], H32, seq.K[0, 2], seq.K[1, 2], prm.q)
+    lo = np.zeros((H, W), np.int16)
+    hi = np.full((H, W), 63, np.int16)
+    Dz, rz = oracle.match(seq.left[1], seq.right[1], lo, hi, prm)
+    Do, Po = oracle.kalman(Dp, Pp, Dz, rz)
+    assert_maps(g[1]["D"], g[1]["P"], Do, Po)
+
+
+def test_errors_are_status_codes(tsgm):
+    with pytest.raises(tsgm.TsgmError):
+        tsgm.Context(tsgm.default_params(64, 32, n_paths=5))
+    with pytest.raises(tsgm.TsgmError):
+        tsgm.Context(tsgm.default_params(64, 32, d_max=300))
+    with make_ctx(tsgm, 64, 32) as ctx:
+        with pytest.raises(tsgm.TsgmError) as e:
+            ctx.match(0, 0, 0, 0, 0, 0)
+        assert e.value.status == tsgm.ERR_INVALID_ARG
+        D = empty((32, 64), np.float32)
+        # the first frame needs no pose
+        ctx.frame(dev(np.zeros((32, 64), np.uint8)), dev(np.zeros((32, 64), np.uint8)),
+                  None, None, synth.Camera(64, 32, 721.0, 0.54).K, f32(0.54), D, empty((32, 64), np.float32))
+        # later frames do
+        with pytest.raises(tsgm.TsgmError) as e:
+            ctx.frame(dev(np.zeros((32, 64), np.uint8)), dev(np.zeros((32, 64), np.uint8)),
+                      None, None, synth.Camera(64, 32, 721.0, 0.54).K, f32(0.54), D, empty((32, 64), np.float32))
+        assert e.value.status == tsgm.ERR_INVALID_ARG
+        # a zero baseline cannot build H
+        with pytest.raises(tsgm.TsgmError) as e:
+            ctx.frame(dev(np.zeros((32, 64), np.uint8)), dev(np.zeros((32, 64), np.uint8)),
+                      np.eye(3), np.zeros(3), synth.Camera(64, 32, 721.0, 0.54).K, f32(0.0), D,
+                      empty((32, 64), np.float32))
+        assert e.value.status == tsgm.ERR_INVALID_ARG
