@@ -75,8 +75,8 @@ typedef struct {
  * q 0.25, S_max 10, r_min 0.5, lr_tol 1, flags 0. */
 void tsgm_default_params(tsgm_params* p, int32_t width, int32_t height);
 
-/* Create a context. `cuda_stream` is a cudaStream_t (may be NULL: the context then creates and
- * owns a non-blocking stream). Allocates all device scratch for the given size. Errors:
+/* Create a context. `cuda_stream` is the cudaStream_t every call of the context is enqueued on
+ * (NULL: the legacy default stream). Allocates all device scratch for the given size. Errors:
  * INVALID_ARG (bad parameters), OUT_OF_MEMORY, CUDA. On failure *out is set to NULL. */
 tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out);
 
@@ -86,7 +86,7 @@ void tsgm_destroy(tsgm_ctx* ctx);
 /* Message of the last failed call on this context (static storage owned by the context). */
 const char* tsgm_last_error(const tsgm_ctx* ctx);
 
-/* Use another CUDA stream for subsequent calls (NULL: the context's own stream). */
+/* Use another CUDA stream for subsequent calls (NULL: the legacy default stream). */
 tsgm_status tsgm_set_stream(tsgm_ctx* ctx, void* cuda_stream);
 
 /* Host-side: the disparity-space homography H = Gamma T Gamma^{-1} (Sec. 2.1, Eq. 1-4) in
@@ -163,9 +163,12 @@ tsgm_status tsgm_census(tsgm_ctx* ctx, const uint8_t* img, uint64_t* codes);
 typedef enum {
     TSGM_BUF_CENSUS_L = 0,  /* uint64 [n]     census of the left image (last match)     */
     TSGM_BUF_CENSUS_R = 1,  /* uint64 [n]     census of the right image                 */
-    TSGM_BUF_OFFSETS = 2,   /* uint32 [n + 1] exclusive scan of window lengths          */
-    TSGM_BUF_COST = 3,      /* uint8  [cells] ragged matching cost                      */
-    TSGM_BUF_S = 4,         /* uint16 [cells] aggregated cost S = sum of path costs     */
+    TSGM_BUF_OFFSETS = 2,   /* uint32 [n + 1] start of each pixel's block in the ragged volume:
+                               exclusive scan of the window lengths rounded up to even; [n] is
+                               the storage size. Pixel i's cell j (disparity d_lo + j) is at
+                               offsets[i] + j.                                              */
+    TSGM_BUF_COST = 3,      /* uint8  [storage] ragged matching cost                     */
+    TSGM_BUF_S = 4,         /* uint16 [storage] aggregated cost S = sum of path costs    */
     TSGM_BUF_DSTAR = 5,     /* int16  [n]     winner-takes-all disparity (KEEP_INTERNALS) */
     TSGM_BUF_DRIGHT = 6,    /* int16  [n]     right-view disparity, -1 none (KEEP_INTERNALS) */
     TSGM_BUF_LR_VALID = 7,  /* uint8  [n]     1 where the left-right check passed (KEEP_INTERNALS) */
@@ -178,11 +181,12 @@ typedef enum {
 } tsgm_buffer;
 
 /* Copy an internal buffer (device to device, on the context stream) into dst. `count` is the
- * number of elements to copy; for the cell buffers the current cell count can be read with
- * tsgm_cells. INVALID_ARG if count exceeds the buffer. */
+ * number of elements to copy; for the cell buffers the storage size is offsets[n].
+ * INVALID_ARG if count exceeds the buffer. */
 tsgm_status tsgm_inspect(tsgm_ctx* ctx, tsgm_buffer which, void* dst, uint64_t count);
 
-/* Number of cells of the windows of the last match/windows call (synchronises the stream). */
+/* Number of (pixel, disparity) cells of the windows of the last match/windows call: the sum of
+ * the window lengths (synchronises the stream). */
 tsgm_status tsgm_cells(tsgm_ctx* ctx, uint64_t* n_cells);
 
 /* Number of kernels this context has enqueued since create (CUDA library copies such as the

@@ -12,7 +12,7 @@ using namespace tsgm;
 
 namespace {
 
-constexpr size_t kEventPool = 1024;  // events (pairs) kept for stage timing
+constexpr size_t kEventPool = 8192;  // events kept for stage timing (two per record)
 
 tsgm_status fail(tsgm_ctx* c, tsgm_status s, const char* msg) {
     if (c) c->err = msg;
@@ -132,6 +132,7 @@ void free_all(tsgm_ctx* c) {
     void* bufs[] = {c->censusL, c->censusR, c->keys,   c->predD,  c->predP,   c->Dz,
                     c->rz,      c->stateD,  c->stateP, c->lo,     c->hi,      c->dstar,
                     c->dright,  c->lrvalid, c->off,    c->rowsum, c->C,       c->S,
+                    c->rowcells, c->cells,  c->desc,
                     c->d_left,  c->d_right, c->d_outD, c->d_outP};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -185,9 +186,11 @@ tsgm_status windows_stage(tsgm_ctx* ctx, const float* pD, const float* pP, int16
                           int16_t* hi) {
     stage_begin(ctx, TSGM_STAGE_WINDOWS);
     TSGM_LAUNCH(launch_windows(pD, pP, ctx->W, ctx->H, ctx->D, ctx->prm.sigma_mult, lo, hi, ctx->rowsum,
-                           ctx->stream),
-            "windows");
-    TSGM_LAUNCH(launch_offsets(lo, hi, ctx->rowsum, ctx->W, ctx->H, ctx->off, ctx->stream), "offsets");
+                               ctx->rowcells, ctx->stream),
+                "windows");
+    TSGM_LAUNCH(launch_offsets(lo, hi, ctx->rowsum, ctx->rowcells, ctx->W, ctx->H, ctx->off, ctx->desc,
+                               ctx->cells, ctx->stream),
+                "offsets");
     stage_end(ctx, TSGM_STAGE_WINDOWS);
     return TSGM_OK;
 }
@@ -202,19 +205,19 @@ tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* righ
             "census");
     stage_end(ctx, TSGM_STAGE_CENSUS);
     stage_begin(ctx, TSGM_STAGE_COST);
-    TSGM_LAUNCH(launch_cost(ctx->censusL, ctx->censusR, lo, hi, ctx->off, ctx->W, ctx->H, ctx->Bc, ctx->C,
-                        ctx->S, ctx->stream),
-            "cost");
+    TSGM_LAUNCH(launch_cost(ctx->censusL, ctx->censusR, ctx->desc, ctx->W, ctx->H, ctx->Bc, ctx->C, ctx->S,
+                            ctx->stream),
+                "cost");
     stage_end(ctx, TSGM_STAGE_COST);
     stage_begin(ctx, TSGM_STAGE_SGM);
-    TSGM_LAUNCH(launch_sgm(ctx->C, lo, hi, ctx->off, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->S,
-                       ctx->stream),
-            "sgm");
+    TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->S,
+                           ctx->stream),
+                "sgm");
     stage_end(ctx, TSGM_STAGE_SGM);
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;
     const float s_thr = p.S_max * (float)p.n_paths;
     stage_begin(ctx, TSGM_STAGE_SELECT);
-    TSGM_LAUNCH(launch_select(ctx->S, lo, hi, ctx->off, ctx->W, ctx->H, s_thr, p.r_min, p.lr_tol, Dz, rz,
+    TSGM_LAUNCH(launch_select(ctx->S, ctx->desc, ctx->W, ctx->H, s_thr, p.r_min, p.lr_tol, Dz, rz,
                           keep ? ctx->dstar : nullptr, keep ? ctx->dright : nullptr,
                           keep ? ctx->lrvalid : nullptr, ctx->stream),
             "select");
@@ -263,15 +266,7 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ctx->n = p->width * p->height;
     ctx->Bc = p->census_w * p->census_h - 1;
     ctx->max_cells = (uint64_t)ctx->n * (uint64_t)ctx->D;
-    if (cuda_stream) {
-        ctx->stream = (cudaStream_t)cuda_stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
-            delete ctx;
-            return TSGM_ERR_CUDA;
-        }
-        ctx->stream = ctx->own_stream;
-    }
+    ctx->stream = (cudaStream_t)cuda_stream;  // NULL: the legacy default stream
     const size_t n = (size_t)ctx->n;
     bool ok = true;
     ok = ok && alloc(&ctx->censusL, n) == cudaSuccess;
@@ -290,6 +285,9 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ok = ok && alloc(&ctx->lrvalid, n) == cudaSuccess;
     ok = ok && alloc(&ctx->off, n + 1) == cudaSuccess;
     ok = ok && alloc(&ctx->rowsum, (size_t)ctx->H) == cudaSuccess;
+    ok = ok && alloc(&ctx->rowcells, (size_t)ctx->H) == cudaSuccess;
+    ok = ok && alloc(&ctx->cells, 1) == cudaSuccess;
+    ok = ok && alloc(&ctx->desc, n) == cudaSuccess;
     ok = ok && alloc(&ctx->C, (size_t)ctx->max_cells + 64) == cudaSuccess;
     ok = ok && alloc(&ctx->S, (size_t)ctx->max_cells + 64) == cudaSuccess;
     ok = ok && alloc(&ctx->d_left, n) == cudaSuccess;
@@ -299,7 +297,6 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     if (!ok) {
         cudaGetLastError();
         free_all(ctx);
-        if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
         delete ctx;
         return TSGM_ERR_OUT_OF_MEMORY;
     }
@@ -311,7 +308,6 @@ void tsgm_destroy(tsgm_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     free_all(ctx);
-    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
 
@@ -319,14 +315,7 @@ const char* tsgm_last_error(const tsgm_ctx* ctx) { return ctx ? ctx->err.c_str()
 
 tsgm_status tsgm_set_stream(tsgm_ctx* ctx, void* cuda_stream) {
     if (!ctx) return TSGM_ERR_INVALID_ARG;
-    if (cuda_stream) {
-        ctx->stream = (cudaStream_t)cuda_stream;
-        return TSGM_OK;
-    }
-    if (!ctx->own_stream &&
-        cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess)
-        return fail(ctx, TSGM_ERR_CUDA, "stream creation failed");
-    ctx->stream = ctx->own_stream;
+    ctx->stream = (cudaStream_t)cuda_stream;
     return TSGM_OK;
 }
 
@@ -375,9 +364,10 @@ tsgm_status tsgm_match(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
     // the caller's windows are copied, clamped into [0, d_max], into the context's buffers
     stage_begin(ctx, TSGM_STAGE_OFFSETS);
     TSGM_LAUNCH(launch_sanitize(d_lo, d_hi, ctx->W, ctx->H, ctx->D, ctx->lo, ctx->hi, ctx->rowsum,
-                                ctx->stream),
+                                ctx->rowcells, ctx->stream),
                 "windows copy");
-    TSGM_LAUNCH(launch_offsets(ctx->lo, ctx->hi, ctx->rowsum, ctx->W, ctx->H, ctx->off, ctx->stream),
+    TSGM_LAUNCH(launch_offsets(ctx->lo, ctx->hi, ctx->rowsum, ctx->rowcells, ctx->W, ctx->H, ctx->off,
+                               ctx->desc, ctx->cells, ctx->stream),
                 "offsets");
     stage_end(ctx, TSGM_STAGE_OFFSETS);
     return match_stages(ctx, left, right, ctx->lo, ctx->hi, D_z, r_z);
@@ -517,7 +507,7 @@ tsgm_status tsgm_cells(tsgm_ctx* ctx, uint64_t* n_cells) {
     if (!ctx) return TSGM_ERR_INVALID_ARG;
     if (!n_cells) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_cells: null pointer");
     uint32_t v = 0;
-    TSGM_CK(cudaMemcpyAsync(&v, ctx->off + ctx->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream),
+    TSGM_CK(cudaMemcpyAsync(&v, ctx->cells, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream),
             "read cell count");
     TSGM_CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     *n_cells = v;

@@ -32,27 +32,27 @@ cudaError_t launch_warp_gather(const unsigned long long* keys, const float* Dpre
                                const float* Pprev, float q, int n, float* Dpred, float* Ppred,
                                cudaStream_t st);
 cudaError_t launch_windows(const float* Dp, const float* Pp, int W, int Hh, int D, float k,
-                           int16_t* lo, int16_t* hi, uint32_t* rowsum, cudaStream_t st);
+                           int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
+                           cudaStream_t st);
 cudaError_t launch_sanitize(const int16_t* lo_in, const int16_t* hi_in, int W, int Hh, int D,
-                            int16_t* lo, int16_t* hi, uint32_t* rowsum, cudaStream_t st);
-cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t* rowsum, int W,
-                           int Hh, uint32_t* off, cudaStream_t st);
+                            int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
+                            cudaStream_t st);
+cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t* rowsum,
+                           const uint32_t* rowcells, int W, int Hh, uint32_t* off, uint2* desc,
+                           uint32_t* cells_total, cudaStream_t st);
 cudaError_t launch_fill(float* a, float v, int n, cudaStream_t st);
 cudaError_t launch_kalman(const float* Dp, const float* Pp, const float* Dz, const float* rz, int n,
                           float* D, float* P, float* D2, float* P2, cudaStream_t st);
 
 cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int Hh, int cw, int ch,
                           uint64_t* outA, uint64_t* outB, cudaStream_t st);
-cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const int16_t* lo,
-                        const int16_t* hi, const uint32_t* off, int W, int Hh, int Bc, uint8_t* C,
-                        uint16_t* S, cudaStream_t st);
-cudaError_t launch_sgm(const uint8_t* C, const int16_t* lo, const int16_t* hi, const uint32_t* off,
-                       int W, int Hh, int D, int n_paths, int P1, int P2, uint16_t* S,
-                       cudaStream_t st);
-cudaError_t launch_select(const uint16_t* S, const int16_t* lo, const int16_t* hi,
-                          const uint32_t* off, int W, int Hh, float s_thr, float r_min, int lr_tol,
-                          float* Dz, float* rz, int16_t* dstar, int16_t* dright, uint8_t* valid,
-                          cudaStream_t st);
+cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* desc, int W, int Hh,
+                        int Bc, uint8_t* C, uint16_t* S, cudaStream_t st);
+cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
+                       int P1, int P2, uint16_t* S, cudaStream_t st);
+cudaError_t launch_select(const uint16_t* S, const uint2* desc, int W, int Hh, float s_thr,
+                          float r_min, int lr_tol, float* Dz, float* rz, int16_t* dstar,
+                          int16_t* dright, uint8_t* valid, cudaStream_t st);
 
 }  // namespace tsgm
 
@@ -62,7 +62,6 @@ struct tsgm_ctx {
     int W = 0, H = 0, D = 0, n = 0, Bc = 0;
     uint64_t max_cells = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t own_stream = nullptr;
 
     // device scratch, all sized at create time
     uint64_t* censusL = nullptr;
@@ -79,8 +78,11 @@ struct tsgm_ctx {
     int16_t* dstar = nullptr;
     int16_t* dright = nullptr;
     uint8_t* lrvalid = nullptr;
-    uint32_t* off = nullptr;
-    uint32_t* rowsum = nullptr;
+    uint32_t* off = nullptr;       // block start of each pixel (+ storage size at [n])
+    uint2* desc = nullptr;         // {off, lo | w << 16} per pixel
+    uint32_t* rowsum = nullptr;    // storage cells per row
+    uint32_t* rowcells = nullptr;  // true window cells per row
+    uint32_t* cells = nullptr;     // true window cells of the whole image (device scalar)
     uint8_t* C = nullptr;
     uint16_t* S = nullptr;
     // staging for tsgm_frame_host

@@ -2,9 +2,11 @@
 //   census transform -> ragged Hamming cost -> SGM path aggregation -> WTA / sub-pixel /
 //   matching variance (Eq. 9) -> left-right check.
 //
-// Ragged volume: the cells of pixel i are off[i] .. off[i+1]-1, cell j <-> disparity lo[i] + j.
-// C is uint8 (Hamming distance), S is uint16 (sum of the path costs, accumulated with packed
-// 32-bit reductions: two neighbouring cells per word, no carry since S <= P (Bc + P2) < 2^16).
+// Ragged volume: pixel i owns cells off[i] .. off[i] + w_i - 1, cell j <-> disparity lo[i] + j,
+// in a block of w_i rounded up to even (so every block starts 4-byte aligned in the uint16
+// aggregate). C is uint8 (Hamming distance); S is uint16, the sum of the path costs, built with
+// packed 32-bit reductions of two neighbouring cells (no carry: S <= P (Bc + P2) <= 2040).
+// Each pixel's {off, lo | w << 16} descriptor is read once per pixel.
 
 #include <cfloat>
 
@@ -56,13 +58,11 @@ __global__ void __launch_bounds__(kCtW* kCtH) k_census(const uint8_t* __restrict
 
 // ---------------------------------------------------------------------------------------------
 // Ragged cost: C(p, d) = popcount(cL(x,y) ^ cR(x-d,y)), x - d < 0 -> Bc. Groups of 8 lanes walk
-// one pixel's window; the same pass zeroes S for the aggregation that follows.
+// one pixel's window; the same pass zeroes the pixel's S block for the aggregation.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
                                               const uint64_t* __restrict__ cr,
-                                              const int16_t* __restrict__ lo,
-                                              const int16_t* __restrict__ hi,
-                                              const uint32_t* __restrict__ off, int W, int n,
+                                              const uint2* __restrict__ desc, int W, int n,
                                               int Bc, uint8_t* __restrict__ C,
                                               uint16_t* __restrict__ S) {
     const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
@@ -71,68 +71,74 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
     for (int i = g; i < n; i += ngroups) {
         const int y = i / W;
         const int x = i - y * W;
-        const int a = lo[i];
-        const int w = hi[i] - a + 1;
-        const uint32_t o = off[i];
+        const uint2 dsc = desc[i];
+        const uint32_t o = dsc.x;
+        const int a = (int)(dsc.y & 0xFFFFu);
+        const int w = (int)(dsc.y >> 16);
         const uint64_t c0 = cl[i];
         const uint64_t* row = cr + (size_t)y * W;
         for (int j = sub; j < w; j += 8) {
             const int xr = x - (a + j);
             const int c = xr >= 0 ? __popcll(c0 ^ row[xr]) : Bc;
             C[o + j] = (uint8_t)c;
-            S[o + j] = 0;
         }
+        uint32_t* S32 = reinterpret_cast<uint32_t*>(S + o);
+        for (int j = sub; 2 * j < w; j += 8) S32[j] = 0u;
     }
 }
 
 // ---------------------------------------------------------------------------------------------
-// SGM path aggregation. One warp walks one path line (all lines of all directions in one
-// launch, horizontal ones first since they are the longest). Along direction r with
+// SGM path aggregation. One warp walks one path line; all lines of all directions are in one
+// launch, horizontal ones first since they are the longest chains. Along direction r with
 // predecessor q:
 //   L(p,d) = C(p,d) + min(L(q,d), L(q,d-1)+P1, L(q,d+1)+P1, m+P2) - m,  m = min_k L(q,k)
 // where L(q,.) outside q's window is +inf and the first pixel of a line has L = C.
-// Narrow windows (<= 32 labels) keep L in a register, lane j <-> label lo + j, and fetch the
-// predecessor's values with shuffles by the window offset. Wider windows go through a
-// per-warp shared-memory buffer indexed by absolute disparity. Each lane adds its L to S with
-// a packed 32-bit reduction covering two neighbouring cells.
+// Three step kinds, by the window of the current pixel p:
+//   N  (w <= 32): lane j <-> label lo + j, one register; the predecessor's values come by
+//      shuffles at the window offset (from registers) or from shared memory;
+//   F  (w == D > 32): dense labels, lane j <-> labels LPL*j .. LPL*j+LPL-1 packed two per
+//      32-bit register and updated with min.u16x2; the predecessor comes from the dense
+//      registers (full-range run) or from shared memory;
+//   G  (otherwise): per-warp shared-memory buffer indexed by absolute disparity.
+// Whenever the representation changes, the predecessor is written to shared memory first.
+// Every lane adds its L to S with packed 32-bit reductions of aligned cell pairs.
 // Direction codes: 0 (+1,0) 1 (-1,0) 2 (0,+1) 3 (0,-1) 4 (+1,+1) 5 (-1,-1) 6 (-1,+1) 7 (+1,-1)
 // ---------------------------------------------------------------------------------------------
 struct SgmLines {
-    int start[9];   // prefix sums of line counts per slot
-    int code[8];    // direction code per slot
+    int start[9];  // prefix sums of line counts per slot
+    int code[8];   // direction code per slot
     int nslots;
 };
 
 constexpr int kSgmWarps = 8;
+constexpr uint32_t kInf2 = ((uint32_t)kInf << 16) | (uint32_t)kInf;
 
 __device__ __forceinline__ void dir_of(int code, int& dx, int& dy) {
-    // 0 (+1,0) 1 (-1,0) 2 (0,+1) 3 (0,-1) 4 (+1,+1) 5 (-1,-1) 6 (-1,+1) 7 (+1,-1)
     dx = (code == 0 || code == 4 || code == 7) ? 1 : ((code == 1 || code == 5 || code == 6) ? -1 : 0);
     dy = (code == 2 || code == 4 || code == 6) ? 1 : ((code == 3 || code == 5 || code == 7) ? -1 : 0);
 }
 
-// Adds L (this lane's cell g = o + j, active if `act`) to S with packed pairs. Cells at even g
-// carry their right neighbour (next lane, same chunk); a cell at odd g is sent alone (high
-// half) only by the first lane of a chunk, otherwise the previous lane already covered it.
-__device__ __forceinline__ void emit_pair(uint32_t* S32, uint32_t g, int L, bool act,
-                                          bool next_act, int lane) {
-    const int Ln = __shfl_down_sync(kFull, L, 1);
-    if (!act) return;
-    if ((g & 1u) == 0u) {
-        const uint32_t v = (uint32_t)L | ((next_act && lane < 31) ? ((uint32_t)Ln << 16) : 0u);
-        atomicAdd(S32 + (g >> 1), v);
-    } else if (lane == 0) {
-        atomicAdd(S32 + (g >> 1), (uint32_t)L << 16);
-    }
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
 }
 
+// packed pair of 16-bit labels (e, e+1) kept only where inside [lo, hi], +inf elsewhere
+__device__ __forceinline__ uint32_t mask_pair(uint32_t v, int e, int lo, int hi) {
+    const uint32_t l = (e >= lo && e <= hi) ? (v & 0xFFFFu) : (uint32_t)kInf;
+    const uint32_t h = (e + 1 >= lo && e + 1 <= hi) ? (v >> 16) : (uint32_t)kInf;
+    return l | (h << 16);
+}
+
+template <int LPL>
 __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restrict__ C,
-                                                        const int16_t* __restrict__ lo_,
-                                                        const int16_t* __restrict__ hi_,
-                                                        const uint32_t* __restrict__ off,
-                                                        int W, int Hh, int D, int P1, int P2,
+                                                        const uint2* __restrict__ desc, int W,
+                                                        int Hh, int D, int P1, int P2,
                                                         SgmLines lines, uint32_t* S32) {
-    extern __shared__ uint16_t sgm_smem[];
+    constexpr int NP = LPL / 2;       // packed pairs per lane in the dense representation
+    constexpr int DP = 32 * LPL;      // labels covered by the dense representation (>= D)
+    extern __shared__ uint32_t sgm_smem32[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kSgmWarps + wib;
@@ -161,108 +167,210 @@ __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restric
     const int ny = dy > 0 ? Hh - y0 : (dy < 0 ? y0 + 1 : 0x7fffffff);
     const int len = min(nx, ny);
     const int step = dy * W + dx;
+    const int i0 = y0 * W + x0;
 
-    uint16_t* buf0 = sgm_smem + wib * 2 * D;
-    uint16_t* buf1 = buf0 + D;
+    // two shared-memory buffers of DP labels (uint16) per warp, viewed as uint32 pairs
+    uint32_t* const buf0 = sgm_smem32 + wib * DP;  // DP/2 pairs per buffer
+    constexpr int kBufPairs = DP / 2;
 
+    // dense-label masks: lanes' pairs beyond D hold +inf and contribute nothing
+    uint32_t keep[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int e = LPL * lane + 2 * k;
+        keep[k] = (e < D ? 0xFFFFu : 0u) | (e + 1 < D ? 0xFFFF0000u : 0u);
+    }
+
+    const uint32_t P1P1 = ((uint32_t)P1 << 16) | (uint32_t)P1;
     int qlo = 0, qw = 0, m = 0;
-    int Lreg = kInf;
-    bool q_in_reg = true;
-    int qb = 0;
+    int loc = 0;  // where the predecessor lives: 0 narrow registers, 1 dense registers, 2 smem
+    int qb = 0;   // smem buffer holding the predecessor when loc == 2
+    int Nreg = kInf;
+    uint32_t Dreg[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) Dreg[k] = kInf2;
 
-    int i = y0 * W + x0;
-    // software pipeline: window of the current pixel loaded one step ahead
-    int lo = __ldg(lo_ + i);
-    int w = __ldg(hi_ + i) - lo + 1;
-    uint32_t o = __ldg(off + i);
-    for (int k = 0; k < len; ++k) {
-        int lo_n = 0, w_n = 0;
-        uint32_t o_n = 0;
-        if (k + 1 < len) {
-            const int in = i + step;
-            lo_n = __ldg(lo_ + in);
-            w_n = __ldg(hi_ + in) - lo_n + 1;
-            o_n = __ldg(off + in);
+    // Descriptors of the line, 32 pixels per lane-wide load, two blocks kept (current, next),
+    // and the costs of the next pixel loaded one step ahead (they do not depend on L).
+    uint2 dc0 = lane < len ? __ldg(desc + (i0 + lane * step)) : make_uint2(0u, 0u);
+    uint2 dc1 = 32 + lane < len ? __ldg(desc + (i0 + (32 + lane) * step)) : make_uint2(0u, 0u);
+    uint32_t o_n = __shfl_sync(kFull, dc0.x, 0);
+    uint32_t lw_n = __shfl_sync(kFull, dc0.y, 0);
+    int cN_n = 0;
+    uint32_t cD_n[NP];
+    auto prefetch = [&](uint32_t o, uint32_t lw) {
+        const int w = (int)(lw >> 16);
+        cN_n = (lane < w) ? (int)__ldg(C + o + lane) : 0;
+        const uint16_t* C16 = reinterpret_cast<const uint16_t*>(C + o);
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+            const int e = LPL * lane + 2 * k2;
+            const uint32_t b = (w == D && w > 32 && e < D) ? (uint32_t)__ldg(C16 + (e >> 1)) : 0u;
+            cD_n[k2] = __byte_perm(b, 0u, 0x4140);  // bytes (c0, c1) -> u16x2
         }
-        int lmin = kInf;
-        if (w <= 32 && (k == 0 || q_in_reg)) {
-            const bool act = lane < w;
-            const int c = act ? (int)__ldg(C + o + lane) : 0;
-            int L;
-            if (k == 0) {
-                L = c;
-            } else {
-                const int s = lane + (lo - qlo);
-                int vc = __shfl_sync(kFull, Lreg, s & 31);
-                int vl = __shfl_sync(kFull, Lreg, (s - 1) & 31);
-                int vr = __shfl_sync(kFull, Lreg, (s + 1) & 31);
-                vc = ((unsigned)s < (unsigned)qw) ? vc : kInf;
-                vl = ((unsigned)(s - 1) < (unsigned)qw) ? vl : kInf;
-                vr = ((unsigned)(s + 1) < (unsigned)qw) ? vr : kInf;
-                const int t = min(min(min(vl, vr) + P1, vc), m + P2);
-                L = c + t - m;
-            }
-            L = act ? L : kInf;
-            emit_pair(S32, o + lane, L, act, lane + 1 < w, lane);
-            Lreg = L;
-            lmin = L;
-            q_in_reg = true;
-        } else {
-            if (k > 0 && q_in_reg) {
-                if (lane < qw) buf0[qlo + lane] = (uint16_t)Lreg;
+    };
+    prefetch(o_n, lw_n);
+
+    for (int k = 0; k < len; ++k) {
+        const uint32_t o = o_n;
+        const int lo = (int)(lw_n & 0xFFFFu);
+        const int w = (int)(lw_n >> 16);
+        const int cN = cN_n;
+        uint32_t c2[NP];
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) c2[k2] = cD_n[k2];
+        const bool first = (k == 0);
+
+        // next pixel: descriptor and costs
+        const int kn = k + 1;
+        if ((kn & 31) == 0) {
+            dc0 = dc1;
+            const int kk = kn + 32 + lane;
+            dc1 = kk < len ? __ldg(desc + (i0 + kk * step)) : make_uint2(0u, 0u);
+        }
+        if (kn < len) {
+            o_n = __shfl_sync(kFull, dc0.x, kn & 31);
+            lw_n = __shfl_sync(kFull, dc0.y, kn & 31);
+            prefetch(o_n, lw_n);
+        }
+
+        // make the predecessor available in the representation this step reads
+        const bool p_narrow = w <= 32;
+        const bool p_full = !p_narrow && w == D;
+        if (!first) {
+            const bool need_smem = (p_narrow && loc != 0) || (p_full && loc != 1) ||
+                                   (!p_narrow && !p_full);
+            if (need_smem && loc != 2) {
+                if (loc == 0) {
+                    if (lane < qw) reinterpret_cast<uint16_t*>(buf0)[qlo + lane] = (uint16_t)Nreg;
+                } else {
+#pragma unroll
+                    for (int k2 = 0; k2 < NP; ++k2) buf0[(LPL * lane) / 2 + k2] = Dreg[k2];
+                }
                 qb = 0;
+                loc = 2;
                 __syncwarp();
             }
-            const uint16_t* src = qb ? buf1 : buf0;
-            uint16_t* dst = qb ? buf0 : buf1;
-            const int qhi = qlo + qw - 1;
-            if (w <= 32) {
-                // narrow pixel after a wide one: read shared memory, keep the result in a register
-                const bool act = lane < w;
-                const int d = lo + lane;
-                const int c = act ? (int)__ldg(C + o + lane) : 0;
-                const int vc = (d >= qlo && d <= qhi) ? (int)src[d] : kInf;
-                const int vl = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src[d - 1] : kInf;
-                const int vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src[d + 1] : kInf;
-                const int t = min(min(min(vl, vr) + P1, vc), m + P2);
-                int L = act ? c + t - m : kInf;
-                emit_pair(S32, o + lane, L, act, lane + 1 < w, lane);
-                Lreg = L;
-                lmin = L;
-                q_in_reg = true;
+        }
+        const uint32_t* srcp = buf0 + qb * kBufPairs;
+        const uint16_t* src16 = reinterpret_cast<const uint16_t*>(srcp);
+        int lmin;
+        if (p_narrow) {
+            const bool act = lane < w;
+            int L;
+            if (first) {
+                L = cN;
             } else {
-                for (int j0 = 0; j0 < w; j0 += 32) {
-                    const int j = j0 + lane;
-                    const bool act = j < w;
-                    const int d = lo + j;
-                    const int c = act ? (int)__ldg(C + o + j) : 0;
-                    int L;
-                    if (k == 0) {
-                        L = c;
-                    } else {
-                        const int vc = (d >= qlo && d <= qhi) ? (int)src[d] : kInf;
-                        const int vl = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src[d - 1] : kInf;
-                        const int vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src[d + 1] : kInf;
-                        const int t = min(min(min(vl, vr) + P1, vc), m + P2);
-                        L = c + t - m;
-                    }
-                    L = act ? L : kInf;
-                    if (act) dst[d] = (uint16_t)L;
-                    lmin = min(lmin, L);
-                    emit_pair(S32, o + j, L, act, j + 1 < w, lane);
+                int vc, vl, vr;
+                if (loc == 0) {
+                    const int s = lane + (lo - qlo);
+                    vc = __shfl_sync(kFull, Nreg, s & 31);
+                    vl = __shfl_sync(kFull, Nreg, (s - 1) & 31);
+                    vr = __shfl_sync(kFull, Nreg, (s + 1) & 31);
+                    vc = ((unsigned)s < (unsigned)qw) ? vc : kInf;
+                    vl = ((unsigned)(s - 1) < (unsigned)qw) ? vl : kInf;
+                    vr = ((unsigned)(s + 1) < (unsigned)qw) ? vr : kInf;
+                } else {
+                    const int d = lo + lane;
+                    const int qhi = qlo + qw - 1;
+                    vc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
+                    vl = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
+                    vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
                 }
-                q_in_reg = false;
-                qb ^= 1;
+                const int t = min(min(min(vl, vr) + P1, vc), m + P2);
+                L = cN + t - m;
             }
+            L = act ? L : kInf;
+            const int Ln = __shfl_down_sync(kFull, L, 1);
+            if (act && !(lane & 1))
+                atomicAdd(S32 + ((o + lane) >> 1),
+                          (uint32_t)L | ((lane + 1 < w) ? ((uint32_t)Ln << 16) : 0u));
+            Nreg = L;
+            lmin = L;
+            loc = 0;
+        } else if (p_full) {
+            uint32_t Lq[NP];
+            if (!first) {
+                if (loc == 1) {
+#pragma unroll
+                    for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[k2];
+                } else {
+                    const int qhi = qlo + qw - 1;
+#pragma unroll
+                    for (int k2 = 0; k2 < NP; ++k2)
+                        Lq[k2] = mask_pair(srcp[(LPL * lane) / 2 + k2], LPL * lane + 2 * k2, qlo, qhi);
+                }
+            }
+            uint32_t pmin = kInf2;
+            if (first) {
+#pragma unroll
+                for (int k2 = 0; k2 < NP; ++k2) {
+                    Dreg[k2] = (c2[k2] & keep[k2]) | (kInf2 & ~keep[k2]);
+                    pmin = vmin2(pmin, Dreg[k2]);
+                }
+            } else {
+                uint32_t left_in = __shfl_up_sync(kFull, Lq[NP - 1], 1);
+                uint32_t right_in = __shfl_down_sync(kFull, Lq[0], 1);
+                if (lane == 0) left_in = kInf2;
+                if (lane == 31) right_in = kInf2;
+                const uint32_t mm = ((uint32_t)m << 16) | (uint32_t)m;
+                const uint32_t mP2 = mm + (((uint32_t)P2 << 16) | (uint32_t)P2);
+#pragma unroll
+                for (int k2 = 0; k2 < NP; ++k2) {
+                    const uint32_t prev = (k2 == 0) ? left_in : Lq[k2 - 1];
+                    const uint32_t next = (k2 == NP - 1) ? right_in : Lq[k2 + 1];
+                    const uint32_t lm1 = __byte_perm(prev, Lq[k2], 0x5432);  // (d-1) values
+                    const uint32_t lp1 = __byte_perm(Lq[k2], next, 0x5432);  // (d+1) values
+                    uint32_t t = vmin2(lm1, lp1) + P1P1;
+                    t = vmin2(vmin2(t, Lq[k2]), mP2);
+                    const uint32_t Lnew = (c2[k2] + t) - mm;
+                    Dreg[k2] = (Lnew & keep[k2]) | (kInf2 & ~keep[k2]);
+                    pmin = vmin2(pmin, Dreg[k2]);
+                }
+            }
+            // packed reductions: the lane's pairs are 4-byte aligned (even block start, LPL even)
+#pragma unroll
+            for (int k2 = 0; k2 < NP; ++k2) {
+                const int e = LPL * lane + 2 * k2;
+                if (e < D) atomicAdd(S32 + ((o + e) >> 1), Dreg[k2] & keep[k2]);
+            }
+            lmin = (int)min(pmin & 0xFFFFu, pmin >> 16);
+            loc = 1;
+        } else {
+            // general window: shared memory indexed by absolute disparity
+            uint16_t* dst16 = reinterpret_cast<uint16_t*>(buf0 + (qb ^ 1) * kBufPairs);
+            const int qhi = qlo + qw - 1;
+            lmin = kInf;
+            for (int j0 = 0; j0 < w; j0 += 32) {
+                const int j = j0 + lane;
+                const bool act = j < w;
+                const int d = lo + j;
+                const int c = (j0 == 0) ? cN : (act ? (int)__ldg(C + o + j) : 0);
+                int L;
+                if (first) {
+                    L = c;
+                } else {
+                    const int vc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
+                    const int vl = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
+                    const int vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
+                    const int t = min(min(min(vl, vr) + P1, vc), m + P2);
+                    L = c + t - m;
+                }
+                L = act ? L : kInf;
+                if (act) dst16[d] = (uint16_t)L;
+                lmin = min(lmin, L);
+                const int Ln = __shfl_down_sync(kFull, L, 1);
+                if (act && !(j & 1))
+                    atomicAdd(S32 + ((o + j) >> 1),
+                              (uint32_t)L | ((j + 1 < w) ? ((uint32_t)Ln << 16) : 0u));
+            }
+            qb ^= 1;
+            loc = 2;
         }
         m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
         qlo = lo;
         qw = w;
         __syncwarp();
-        i += step;
-        lo = lo_n;
-        w = w_n;
-        o = o_n;
     }
 }
 
@@ -277,7 +385,6 @@ __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restric
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ int count_side(const uint16_t* __restrict__ s, int start, int dirn,
                                           int lo_idx, int hi_idx, int s0, float thr, int lane) {
-    // labels start, start+dirn, ... inside [lo_idx, hi_idx]; returns how many are counted
     int carry = 0, count = 0;
     for (int t0 = 0;; t0 += 32) {
         const int jj = start + dirn * (t0 + lane);
@@ -299,19 +406,17 @@ __device__ __forceinline__ int count_side(const uint16_t* __restrict__ s, int st
 }
 
 __global__ void __launch_bounds__(1024) k_select(const uint16_t* __restrict__ S,
-                                                 const int16_t* __restrict__ lo_,
-                                                 const int16_t* __restrict__ hi_,
-                                                 const uint32_t* __restrict__ off, int W,
+                                                 const uint2* __restrict__ desc, int W,
                                                  float s_thr, float r_min, int lr_tol,
                                                  float* __restrict__ Dz, float* __restrict__ rz,
                                                  int16_t* __restrict__ dstar_out,
                                                  int16_t* __restrict__ dright_out,
                                                  uint8_t* __restrict__ valid_out) {
     extern __shared__ uint32_t sel_smem[];
-    uint32_t* drk = sel_smem;                      // W keys
-    float* dzs = (float*)(drk + W);                // W
-    float* rzs = dzs + W;                          // W
-    int16_t* ds = (int16_t*)(rzs + W);             // W
+    uint32_t* drk = sel_smem;            // W keys
+    float* dzs = (float*)(drk + W);      // W
+    float* rzs = dzs + W;                // W
+    int16_t* ds = (int16_t*)(rzs + W);   // W
     const int y = blockIdx.x;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -319,9 +424,10 @@ __global__ void __launch_bounds__(1024) k_select(const uint16_t* __restrict__ S,
     __syncthreads();
     for (int x = wid; x < W; x += nw) {
         const int i = y * W + x;
-        const int a = lo_[i];
-        const int w = hi_[i] - a + 1;
-        const uint16_t* s = S + off[i];
+        const uint2 dsc = desc[i];
+        const int a = (int)(dsc.y & 0xFFFFu);
+        const int w = (int)(dsc.y >> 16);
+        const uint16_t* s = S + dsc.x;
         unsigned best = 0xFFFFFFFFu;
         for (int j = lane; j < w; j += 32) {
             const unsigned sv = s[j];
@@ -379,51 +485,55 @@ cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int H
     return cudaGetLastError();
 }
 
-cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const int16_t* lo,
-                        const int16_t* hi, const uint32_t* off, int W, int Hh, int Bc, uint8_t* C,
-                        uint16_t* S, cudaStream_t st) {
+cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* desc, int W, int Hh,
+                        int Bc, uint8_t* C, uint16_t* S, cudaStream_t st) {
     const int n = W * Hh;
     int blocks = (n * 8 + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_cost<<<blocks, 256, 0, st>>>(cl, cr, lo, hi, off, W, n, Bc, C, S);
+    k_cost<<<blocks, 256, 0, st>>>(cl, cr, desc, W, n, Bc, C, S);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sgm(const uint8_t* C, const int16_t* lo, const int16_t* hi, const uint32_t* off,
-                       int W, int Hh, int D, int n_paths, int P1, int P2, uint16_t* S,
-                       cudaStream_t st) {
+template <int LPL>
+static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int Hh, int D,
+                                int P1, int P2, const SgmLines& L, uint32_t* S32, cudaStream_t st) {
+    const int nlines = L.start[L.nslots];
+    const int blocks = (nlines + kSgmWarps - 1) / kSgmWarps;
+    const size_t smem = (size_t)kSgmWarps * 2 * (32 * LPL) * sizeof(uint16_t);  // 2 buffers/warp
+    k_sgm<LPL><<<blocks, kSgmWarps * 32, smem, st>>>(C, desc, W, Hh, D, P1, P2, L, S32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
+                       int P1, int P2, uint16_t* S, cudaStream_t st) {
     // slots ordered longest lines first: horizontal, vertical, then diagonals
-    static const int order8[8] = {0, 1, 2, 3, 4, 5, 6, 7};
     SgmLines L;
     L.nslots = n_paths;
     L.start[0] = 0;
     for (int s = 0; s < n_paths; ++s) {
-        const int code = order8[s];
+        const int code = s;
         L.code[s] = code;
         const int cnt = code <= 1 ? Hh : (code <= 3 ? W : W + Hh - 1);
         L.start[s + 1] = L.start[s] + cnt;
     }
-    const int nlines = L.start[n_paths];
-    const int blocks = (nlines + kSgmWarps - 1) / kSgmWarps;
-    const size_t smem = (size_t)kSgmWarps * 2 * D * sizeof(uint16_t);
-    k_sgm<<<blocks, kSgmWarps * 32, smem, st>>>(C, lo, hi, off, W, Hh, D, P1, P2, L,
-                                                 reinterpret_cast<uint32_t*>(S));
-    return cudaGetLastError();
+    uint32_t* S32 = reinterpret_cast<uint32_t*>(S);
+    if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, D, P1, P2, L, S32, st);
+    if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, D, P1, P2, L, S32, st);
+    if (D <= 192) return launch_sgm_t<6>(C, desc, W, Hh, D, P1, P2, L, S32, st);
+    return launch_sgm_t<8>(C, desc, W, Hh, D, P1, P2, L, S32, st);
 }
 
-cudaError_t launch_select(const uint16_t* S, const int16_t* lo, const int16_t* hi,
-                          const uint32_t* off, int W, int Hh, float s_thr, float r_min, int lr_tol,
-                          float* Dz, float* rz, int16_t* dstar, int16_t* dright, uint8_t* valid,
-                          cudaStream_t st) {
+cudaError_t launch_select(const uint16_t* S, const uint2* desc, int W, int Hh, float s_thr,
+                          float r_min, int lr_tol, float* Dz, float* rz, int16_t* dstar,
+                          int16_t* dright, uint8_t* valid, cudaStream_t st) {
     const size_t smem = (size_t)W * (4 + 4 + 4 + 2);
     if (smem > 48 * 1024) {
         const cudaError_t e =
             cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int threads = 1024;
-    k_select<<<Hh, threads, smem, st>>>(S, lo, hi, off, W, s_thr, r_min, lr_tol, Dz, rz, dstar,
-                                        dright, valid);
+    k_select<<<Hh, 1024, smem, st>>>(S, desc, W, s_thr, r_min, lr_tol, Dz, rz, dstar, dright,
+                                     valid);
     return cudaGetLastError();
 }
 

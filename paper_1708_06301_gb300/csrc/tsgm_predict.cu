@@ -14,6 +14,10 @@ namespace {
 
 __device__ __forceinline__ bool valid_value(float v) { return v >= 0.0f && v <= FLT_MAX; }
 
+// Storage of one pixel's window in the ragged volume: rounded up to an even number of cells so
+// that every block starts 4-byte aligned in the uint16 aggregate (packed pair updates).
+__device__ __forceinline__ uint32_t block_cells(int w) { return (uint32_t)(w + (w & 1)); }
+
 // ---------------------------------------------------------------------------------------------
 // Warp scatter (Eq. 3 + homogeneous divide; z-buffer of Sec. 2.2 "disparity refinement").
 // One thread per source pixel; the key packs ~bits(d') (bits of a positive float grow with its
@@ -144,10 +148,11 @@ __global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
                                                  const float* __restrict__ Pp, int W, int D,
                                                  float k, int16_t* __restrict__ lo,
                                                  int16_t* __restrict__ hi,
-                                                 uint32_t* __restrict__ rowsum) {
+                                                 uint32_t* __restrict__ rowsum,
+                                                 uint32_t* __restrict__ rowcells) {
     __shared__ uint32_t sh[33];
     const int y = blockIdx.x;
-    uint32_t acc = 0;
+    uint32_t acc = 0, acc_true = 0;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int i = y * W + x;
         const float d = Dp[i], p = Pp[i];
@@ -164,10 +169,15 @@ __global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
         }
         lo[i] = (int16_t)a;
         hi[i] = (int16_t)b;
-        acc += (uint32_t)(b - a + 1);
+        acc_true += (uint32_t)(b - a + 1);
+        acc += block_cells(b - a + 1);
     }
     const uint32_t t = block_sum(acc, sh);
-    if (threadIdx.x == 0) rowsum[y] = t;
+    const uint32_t tt = block_sum(acc_true, sh);
+    if (threadIdx.x == 0) {
+        rowsum[y] = t;
+        rowcells[y] = tt;
+    }
 }
 
 // Caller-supplied windows: copy them clamped into [0, D-1] with lo <= hi (so that every later
@@ -176,28 +186,39 @@ __global__ void __launch_bounds__(256) k_sanitize_rowsum(const int16_t* __restri
                                                          const int16_t* __restrict__ hi_in, int W,
                                                          int D, int16_t* __restrict__ lo,
                                                          int16_t* __restrict__ hi,
-                                                         uint32_t* __restrict__ rowsum) {
+                                                         uint32_t* __restrict__ rowsum,
+                                                         uint32_t* __restrict__ rowcells) {
     __shared__ uint32_t sh[33];
     const int y = blockIdx.x;
-    uint32_t acc = 0;
+    uint32_t acc = 0, acc_true = 0;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int i = y * W + x;
         const int a = min(max((int)lo_in[i], 0), D - 1);
         const int b = min(max((int)hi_in[i], a), D - 1);
         lo[i] = (int16_t)a;
         hi[i] = (int16_t)b;
-        acc += (uint32_t)(b - a + 1);
+        acc_true += (uint32_t)(b - a + 1);
+        acc += block_cells(b - a + 1);
     }
     const uint32_t t = block_sum(acc, sh);
-    if (threadIdx.x == 0) rowsum[y] = t;
+    const uint32_t tt = block_sum(acc_true, sh);
+    if (threadIdx.x == 0) {
+        rowsum[y] = t;
+        rowcells[y] = tt;
+    }
 }
 
-// Offsets of the ragged volume: off[i] = sum of window lengths of pixels before i (row-major);
-// off[n] = total. One block per row: base = sum of earlier row totals, then a block scan.
+// Offsets of the ragged volume: pixel i's block starts at off[i] = sum of the (2-aligned) block
+// sizes of the pixels before it (row-major); off[n] = storage size. One block per row: base =
+// sum of earlier row totals, then a block scan. Also writes the per-pixel descriptor
+// {off, lo | w << 16} used by the matching kernels, and (last row) the number of true cells.
 __global__ void __launch_bounds__(512) k_offsets(const int16_t* __restrict__ lo,
                                                  const int16_t* __restrict__ hi,
-                                                 const uint32_t* __restrict__ rowsum, int W,
-                                                 int Hh, uint32_t* __restrict__ off) {
+                                                 const uint32_t* __restrict__ rowsum,
+                                                 const uint32_t* __restrict__ rowcells, int W,
+                                                 int Hh, uint32_t* __restrict__ off,
+                                                 uint2* __restrict__ desc,
+                                                 uint32_t* __restrict__ cells_total) {
     __shared__ uint32_t sh[33];
     const int y = blockIdx.x;
     uint32_t part = 0;
@@ -206,13 +227,29 @@ __global__ void __launch_bounds__(512) k_offsets(const int16_t* __restrict__ lo,
     for (int x0 = 0; x0 < W; x0 += blockDim.x) {
         const int x = x0 + threadIdx.x;
         const int i = y * W + x;
-        const uint32_t w = (x < W) ? (uint32_t)(hi[i] - lo[i] + 1) : 0u;
+        int a = 0, w = 0;
+        if (x < W) {
+            a = lo[i];
+            w = hi[i] - a + 1;
+        }
+        const uint32_t bw = (x < W) ? block_cells(w) : 0u;
         uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(w, sh, &tot);
-        if (x < W) off[i] = base + ex;
+        const uint32_t ex = block_exclusive_scan(bw, sh, &tot);
+        if (x < W) {
+            off[i] = base + ex;
+            desc[i] = make_uint2(base + ex, (uint32_t)a | ((uint32_t)w << 16));
+        }
         base += tot;
     }
-    if (y == Hh - 1 && threadIdx.x == 0) off[(size_t)W * Hh] = base;
+    if (y == Hh - 1) {
+        uint32_t c = 0;
+        for (int r = threadIdx.x; r < Hh; r += blockDim.x) c += rowcells[r];
+        c = block_sum(c, sh);
+        if (threadIdx.x == 0) {
+            off[(size_t)W * Hh] = base;
+            *cells_total = c;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -282,20 +319,23 @@ cudaError_t launch_warp_gather(const unsigned long long* keys, const float* Dpre
 }
 
 cudaError_t launch_windows(const float* Dp, const float* Pp, int W, int Hh, int D, float k,
-                           int16_t* lo, int16_t* hi, uint32_t* rowsum, cudaStream_t st) {
-    k_windows<<<Hh, 256, 0, st>>>(Dp, Pp, W, D, k, lo, hi, rowsum);
+                           int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
+                           cudaStream_t st) {
+    k_windows<<<Hh, 256, 0, st>>>(Dp, Pp, W, D, k, lo, hi, rowsum, rowcells);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sanitize(const int16_t* lo_in, const int16_t* hi_in, int W, int Hh, int D,
-                            int16_t* lo, int16_t* hi, uint32_t* rowsum, cudaStream_t st) {
-    k_sanitize_rowsum<<<Hh, 256, 0, st>>>(lo_in, hi_in, W, D, lo, hi, rowsum);
+                            int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
+                            cudaStream_t st) {
+    k_sanitize_rowsum<<<Hh, 256, 0, st>>>(lo_in, hi_in, W, D, lo, hi, rowsum, rowcells);
     return cudaGetLastError();
 }
 
-cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t* rowsum, int W,
-                           int Hh, uint32_t* off, cudaStream_t st) {
-    k_offsets<<<Hh, 512, 0, st>>>(lo, hi, rowsum, W, Hh, off);
+cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t* rowsum,
+                           const uint32_t* rowcells, int W, int Hh, uint32_t* off, uint2* desc,
+                           uint32_t* cells_total, cudaStream_t st) {
+    k_offsets<<<Hh, 512, 0, st>>>(lo, hi, rowsum, rowcells, W, Hh, off, desc, cells_total);
     return cudaGetLastError();
 }
 

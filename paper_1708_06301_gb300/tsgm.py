@@ -141,9 +141,10 @@ def build_H(R, t, K, baseline: float) -> np.ndarray:
 
 
 def _current_stream() -> int:
+    """Handle of torch's current CUDA stream (0 is the legacy default stream)."""
     try:
         import torch
-        if torch.cuda.is_available() and torch.cuda.is_initialized():
+        if torch.cuda.is_available():
             return int(torch.cuda.current_stream().cuda_stream)
     except Exception:
         pass

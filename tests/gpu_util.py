@@ -30,3 +30,18 @@ def host(t, dtype):
 
 def f32(x):
     return np.float32(x)
+
+
+def compact(buf: np.ndarray, off: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    """Cells of a ragged buffer laid out with per-pixel block starts `off` (the GPU layout, blocks
+    rounded up to even) gathered into the compact order (window after window, no gaps)."""
+    w = (hi.astype(np.int64) - lo.astype(np.int64) + 1).reshape(-1)
+    start = np.repeat(off[:-1].astype(np.int64), w)
+    pos = np.arange(int(w.sum()), dtype=np.int64) - np.repeat(np.concatenate([[0], np.cumsum(w)[:-1]]), w)
+    return buf[start + pos]
+
+
+def padded_offsets(lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    """Block starts of the GPU layout: exclusive scan of the window lengths rounded up to even."""
+    w = (hi.astype(np.int64) - lo.astype(np.int64) + 1).reshape(-1)
+    return np.concatenate([[0], np.cumsum(w + (w & 1))]).astype(np.uint32)
