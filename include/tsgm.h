@@ -58,7 +58,7 @@ typedef enum {
                                         plain full-range SGM every frame (still Kalman-updated) */
 
 typedef struct {
-    int32_t width, height;       /* image size, 1 <= width <= 16000, 1 <= height */
+    int32_t width, height;       /* image size, 1 <= width <= 13000, 1 <= height */
     int32_t d_max;               /* labels are 0..d_max; d_max + 1 <= TSGM_MAX_LABELS */
     int32_t census_w, census_h;  /* odd census window; census_w * census_h - 1 <= 64 */
     int32_t n_paths;             /* SGM paths: 4 (->, <-, down, up) or 8 (+ 4 diagonals) */

@@ -53,8 +53,8 @@ tsgm_status check_params(const tsgm_params* p, std::string& why) {
         why = "width/height out of range";
         return TSGM_ERR_INVALID_ARG;
     }
-    if (p->width > 16000) {
-        why = "width must be <= 16000 (per-column state of one row is kept in shared memory)";
+    if (p->width > 13000) {
+        why = "width must be <= 13000 (per-column state of one row is kept in shared memory)";
         return TSGM_ERR_INVALID_ARG;
     }
     if (p->d_max < 0 || p->d_max + 1 > TSGM_MAX_LABELS) {
@@ -78,7 +78,7 @@ tsgm_status check_params(const tsgm_params* p, std::string& why) {
         why = buf;
         return TSGM_ERR_INVALID_ARG;
     }
-    const uint64_t cells = (uint64_t)p->width * p->height * (uint64_t)(p->d_max + 1);
+    const uint64_t cells = (uint64_t)p->width * p->height * (uint64_t)(p->d_max + 4);
     if (cells + 64 >= (1ull << 32)) {
         why = "width * height * (d_max + 1) must stay below 2^32 cells";
         return TSGM_ERR_INVALID_ARG;
@@ -132,7 +132,7 @@ void free_all(tsgm_ctx* c) {
     void* bufs[] = {c->censusL, c->censusR, c->keys,   c->predD,  c->predP,   c->Dz,
                     c->rz,      c->stateD,  c->stateP, c->lo,     c->hi,      c->dstar,
                     c->dright,  c->lrvalid, c->off,    c->rowsum, c->C,       c->S,
-                    c->rowcells, c->cells,  c->desc,
+                    c->rowcells, c->cells,  c->desc,  c->Lvol,
                     c->d_left,  c->d_right, c->d_outD, c->d_outP};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -205,21 +205,22 @@ tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* righ
             "census");
     stage_end(ctx, TSGM_STAGE_CENSUS);
     stage_begin(ctx, TSGM_STAGE_COST);
-    TSGM_LAUNCH(launch_cost(ctx->censusL, ctx->censusR, ctx->desc, ctx->W, ctx->H, ctx->Bc, ctx->C, ctx->S,
+    TSGM_LAUNCH(launch_cost(ctx->censusL, ctx->censusR, ctx->desc, ctx->W, ctx->H, ctx->Bc, ctx->C,
                             ctx->stream),
                 "cost");
     stage_end(ctx, TSGM_STAGE_COST);
     stage_begin(ctx, TSGM_STAGE_SGM);
-    TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->S,
-                           ctx->stream),
+    TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->Lvol,
+                           ctx->max_cells, ctx->stream),
                 "sgm");
     stage_end(ctx, TSGM_STAGE_SGM);
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;
     const float s_thr = p.S_max * (float)p.n_paths;
     stage_begin(ctx, TSGM_STAGE_SELECT);
-    TSGM_LAUNCH(launch_select(ctx->S, ctx->desc, ctx->W, ctx->H, s_thr, p.r_min, p.lr_tol, Dz, rz,
-                          keep ? ctx->dstar : nullptr, keep ? ctx->dright : nullptr,
-                          keep ? ctx->lrvalid : nullptr, ctx->stream),
+    TSGM_LAUNCH(launch_select(ctx->Lvol, ctx->max_cells, p.n_paths, ctx->desc, ctx->W, ctx->H, s_thr,
+                              p.r_min, p.lr_tol, Dz, rz, keep ? ctx->S : nullptr,
+                              keep ? ctx->dstar : nullptr, keep ? ctx->dright : nullptr,
+                              keep ? ctx->lrvalid : nullptr, ctx->stream),
             "select");
     stage_end(ctx, TSGM_STAGE_SELECT);
     return TSGM_OK;
@@ -265,7 +266,8 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ctx->D = p->d_max + 1;
     ctx->n = p->width * p->height;
     ctx->Bc = p->census_w * p->census_h - 1;
-    ctx->max_cells = (uint64_t)ctx->n * (uint64_t)ctx->D;
+    // storage of the ragged volumes: every pixel's block is its window rounded up to 4 cells
+    ctx->max_cells = (uint64_t)ctx->n * (uint64_t)((ctx->D + 3) & ~3);
     ctx->stream = (cudaStream_t)cuda_stream;  // NULL: the legacy default stream
     const size_t n = (size_t)ctx->n;
     bool ok = true;
@@ -290,6 +292,7 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ok = ok && alloc(&ctx->desc, n) == cudaSuccess;
     ok = ok && alloc(&ctx->C, (size_t)ctx->max_cells + 64) == cudaSuccess;
     ok = ok && alloc(&ctx->S, (size_t)ctx->max_cells + 64) == cudaSuccess;
+    ok = ok && alloc(&ctx->Lvol, (size_t)ctx->max_cells * (size_t)p->n_paths + 64) == cudaSuccess;
     ok = ok && alloc(&ctx->d_left, n) == cudaSuccess;
     ok = ok && alloc(&ctx->d_right, n) == cudaSuccess;
     ok = ok && alloc(&ctx->d_outD, n) == cudaSuccess;

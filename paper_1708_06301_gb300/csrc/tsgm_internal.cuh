@@ -47,12 +47,13 @@ cudaError_t launch_kalman(const float* Dp, const float* Pp, const float* Dz, con
 cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int Hh, int cw, int ch,
                           uint64_t* outA, uint64_t* outB, cudaStream_t st);
 cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* desc, int W, int Hh,
-                        int Bc, uint8_t* C, uint16_t* S, cudaStream_t st);
+                        int Bc, uint8_t* C, cudaStream_t st);
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
-                       int P1, int P2, uint16_t* S, cudaStream_t st);
-cudaError_t launch_select(const uint16_t* S, const uint2* desc, int W, int Hh, float s_thr,
-                          float r_min, int lr_tol, float* Dz, float* rz, int16_t* dstar,
-                          int16_t* dright, uint8_t* valid, cudaStream_t st);
+                       int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, cudaStream_t st);
+cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
+                          int W, int Hh, float s_thr, float r_min, int lr_tol, float* Dz, float* rz,
+                          uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
+                          cudaStream_t st);
 
 }  // namespace tsgm
 
@@ -83,8 +84,9 @@ struct tsgm_ctx {
     uint32_t* rowsum = nullptr;    // storage cells per row
     uint32_t* rowcells = nullptr;  // true window cells per row
     uint32_t* cells = nullptr;     // true window cells of the whole image (device scalar)
-    uint8_t* C = nullptr;
-    uint16_t* S = nullptr;
+    uint8_t* C = nullptr;          // ragged matching cost
+    uint16_t* S = nullptr;         // aggregated cost, written only with TSGM_FLAG_KEEP_INTERNALS
+    uint8_t* Lvol = nullptr;       // one ragged uint8 volume of path costs per SGM direction
     // staging for tsgm_frame_host
     uint8_t* d_left = nullptr;
     uint8_t* d_right = nullptr;

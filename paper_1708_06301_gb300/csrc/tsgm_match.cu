@@ -2,10 +2,10 @@
 //   census transform -> ragged Hamming cost -> SGM path aggregation -> WTA / sub-pixel /
 //   matching variance (Eq. 9) -> left-right check.
 //
-// Ragged volume: pixel i owns cells off[i] .. off[i] + w_i - 1, cell j <-> disparity lo[i] + j,
-// in a block of w_i rounded up to even (so every block starts 4-byte aligned in the uint16
-// aggregate). C is uint8 (Hamming distance); S is uint16, the sum of the path costs, built with
-// packed 32-bit reductions of two neighbouring cells (no carry: S <= P (Bc + P2) <= 2040).
+// Ragged volumes: pixel i owns cells off[i] .. off[i] + w_i - 1 (cell j <-> disparity lo[i] + j)
+// of a block of w_i rounded up to a multiple of 4 cells, so blocks start 4-byte aligned. C is the
+// uint8 Hamming cost; each SGM direction r writes its path cost L_r (<= census bits + P2 <= 255)
+// to its own uint8 volume with plain stores, and the selection kernel forms S = sum_r L_r.
 // Each pixel's {off, lo | w << 16} descriptor is read once per pixel.
 
 #include <cfloat>
@@ -58,13 +58,12 @@ __global__ void __launch_bounds__(kCtW* kCtH) k_census(const uint8_t* __restrict
 
 // ---------------------------------------------------------------------------------------------
 // Ragged cost: C(p, d) = popcount(cL(x,y) ^ cR(x-d,y)), x - d < 0 -> Bc. Groups of 8 lanes walk
-// one pixel's window; the same pass zeroes the pixel's S block for the aggregation.
+// one pixel's window.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
                                               const uint64_t* __restrict__ cr,
                                               const uint2* __restrict__ desc, int W, int n,
-                                              int Bc, uint8_t* __restrict__ C,
-                                              uint16_t* __restrict__ S) {
+                                              int Bc, uint8_t* __restrict__ C) {
     const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     const int sub = threadIdx.x & 7;
     const int ngroups = (gridDim.x * blockDim.x) >> 3;
@@ -82,8 +81,6 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
             const int c = xr >= 0 ? __popcll(c0 ^ row[xr]) : Bc;
             C[o + j] = (uint8_t)c;
         }
-        uint32_t* S32 = reinterpret_cast<uint32_t*>(S + o);
-        for (int j = sub; 2 * j < w; j += 8) S32[j] = 0u;
     }
 }
 
@@ -101,7 +98,7 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
 //      registers (full-range run) or from shared memory;
 //   G  (otherwise): per-warp shared-memory buffer indexed by absolute disparity.
 // Whenever the representation changes, the predecessor is written to shared memory first.
-// Every lane adds its L to S with packed 32-bit reductions of aligned cell pairs.
+// Every step stores the pixel's L values into the direction's own uint8 volume.
 // Direction codes: 0 (+1,0) 1 (-1,0) 2 (0,+1) 3 (0,-1) 4 (+1,+1) 5 (-1,-1) 6 (-1,+1) 7 (+1,-1)
 // ---------------------------------------------------------------------------------------------
 struct SgmLines {
@@ -135,7 +132,8 @@ template <int LPL>
 __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restrict__ C,
                                                         const uint2* __restrict__ desc, int W,
                                                         int Hh, int D, int P1, int P2,
-                                                        SgmLines lines, uint32_t* S32) {
+                                                        SgmLines lines, uint8_t* __restrict__ Lvol,
+                                                        uint64_t vol_stride) {
     constexpr int NP = LPL / 2;       // packed pairs per lane in the dense representation
     constexpr int DP = 32 * LPL;      // labels covered by the dense representation (>= D)
     extern __shared__ uint32_t sgm_smem32[];
@@ -146,6 +144,7 @@ __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restric
     int slot = 0;
     while (gw >= lines.start[slot + 1]) ++slot;
     const int l = gw - lines.start[slot];
+    uint8_t* __restrict__ Lv = Lvol + (size_t)lines.code[slot] * vol_stride;
     int dx, dy;
     dir_of(lines.code[slot], dx, dy);
     int x0, y0;
@@ -180,8 +179,9 @@ __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restric
         const int e = LPL * lane + 2 * k;
         keep[k] = (e < D ? 0xFFFFu : 0u) | (e + 1 < D ? 0xFFFF0000u : 0u);
     }
-
     const uint32_t P1P1 = ((uint32_t)P1 << 16) | (uint32_t)P1;
+    const uint32_t P2P2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
+
     int qlo = 0, qw = 0, m = 0;
     int loc = 0;  // where the predecessor lives: 0 narrow registers, 1 dense registers, 2 smem
     int qb = 0;   // smem buffer holding the predecessor when loc == 2
@@ -190,199 +190,246 @@ __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restric
 #pragma unroll
     for (int k = 0; k < NP; ++k) Dreg[k] = kInf2;
 
-    // Descriptors of the line, 32 pixels per lane-wide load, two blocks kept (current, next),
-    // and the costs of the next pixel loaded one step ahead (they do not depend on L).
+    // Descriptors of the line: block `blk` of 32 pixels (one per lane) in dc0, the next in dc1.
+    int blk = 0;
     uint2 dc0 = lane < len ? __ldg(desc + (i0 + lane * step)) : make_uint2(0u, 0u);
     uint2 dc1 = 32 + lane < len ? __ldg(desc + (i0 + (32 + lane) * step)) : make_uint2(0u, 0u);
-    uint32_t o_n = __shfl_sync(kFull, dc0.x, 0);
-    uint32_t lw_n = __shfl_sync(kFull, dc0.y, 0);
-    int cN_n = 0;
-    uint32_t cD_n[NP];
-    auto prefetch = [&](uint32_t o, uint32_t lw) {
-        const int w = (int)(lw >> 16);
-        cN_n = (lane < w) ? (int)__ldg(C + o + lane) : 0;
+    // descriptor of pixel kk of the line; kk never decreases and advances by at most one
+    auto fetch = [&](int kk, uint32_t& o_, uint32_t& lw_) {
+        if ((kk >> 5) != blk) {
+            dc0 = dc1;
+            ++blk;
+            const int t = ((blk + 1) << 5) + lane;
+            dc1 = t < len ? __ldg(desc + (i0 + t * step)) : make_uint2(0u, 0u);
+        }
+        o_ = __shfl_sync(kFull, dc0.x, kk & 31);
+        lw_ = __shfl_sync(kFull, dc0.y, kk & 31);
+    };
+    // write the predecessor into smem buffer 0 if it is held in registers
+    auto spill = [&]() {
+        if (loc != 2) __syncwarp();  // earlier reads of buffer 0 are done before it is rewritten
+        if (loc == 0) {
+            if (lane < qw) reinterpret_cast<uint16_t*>(buf0)[qlo + lane] = (uint16_t)Nreg;
+        } else if (loc == 1) {
+#pragma unroll
+            for (int k2 = 0; k2 < NP; ++k2) buf0[(LPL * lane) / 2 + k2] = Dreg[k2];
+        }
+        if (loc != 2) {
+            qb = 0;
+            loc = 2;
+            __syncwarp();
+        }
+    };
+    auto emit_narrow = [&](uint32_t o, int L, int w) {
+        if (lane < w) Lv[o + lane] = (uint8_t)L;
+    };
+    auto load_dense_cost = [&](uint32_t o, uint32_t (&c2)[NP]) {
         const uint16_t* C16 = reinterpret_cast<const uint16_t*>(C + o);
 #pragma unroll
         for (int k2 = 0; k2 < NP; ++k2) {
             const int e = LPL * lane + 2 * k2;
-            const uint32_t b = (w == D && w > 32 && e < D) ? (uint32_t)__ldg(C16 + (e >> 1)) : 0u;
-            cD_n[k2] = __byte_perm(b, 0u, 0x4140);  // bytes (c0, c1) -> u16x2
+            const uint32_t b = (e < D) ? (uint32_t)__ldg(C16 + (e >> 1)) : 0u;
+            c2[k2] = __byte_perm(b, 0u, 0x4140);  // bytes (c0, c1) -> u16x2
         }
     };
-    prefetch(o_n, lw_n);
-
-    for (int k = 0; k < len; ++k) {
-        const uint32_t o = o_n;
-        const int lo = (int)(lw_n & 0xFFFFu);
-        const int w = (int)(lw_n >> 16);
-        const int cN = cN_n;
-        uint32_t c2[NP];
+    // one dense step from the predecessor values Lq (labels LPL*lane + ..), result in Dreg
+    auto dense_step = [&](const uint32_t (&Lq)[NP], const uint32_t (&c2)[NP]) -> int {
+        uint32_t left_in = __shfl_up_sync(kFull, Lq[NP - 1], 1);
+        uint32_t right_in = __shfl_down_sync(kFull, Lq[0], 1);
+        if (lane == 0) left_in = kInf2;
+        if (lane == 31) right_in = kInf2;
+        const uint32_t mm = ((uint32_t)m << 16) | (uint32_t)m;
+        const uint32_t mP2 = mm + P2P2;
+        uint32_t pmin = kInf2;
 #pragma unroll
-        for (int k2 = 0; k2 < NP; ++k2) c2[k2] = cD_n[k2];
-        const bool first = (k == 0);
-
-        // next pixel: descriptor and costs
-        const int kn = k + 1;
-        if ((kn & 31) == 0) {
-            dc0 = dc1;
-            const int kk = kn + 32 + lane;
-            dc1 = kk < len ? __ldg(desc + (i0 + kk * step)) : make_uint2(0u, 0u);
+        for (int k2 = 0; k2 < NP; ++k2) {
+            const uint32_t prev = (k2 == 0) ? left_in : Lq[k2 - 1];
+            const uint32_t next = (k2 == NP - 1) ? right_in : Lq[k2 + 1];
+            const uint32_t lm1 = __byte_perm(prev, Lq[k2], 0x5432);  // (d-1) values
+            const uint32_t lp1 = __byte_perm(Lq[k2], next, 0x5432);  // (d+1) values
+            uint32_t t = vmin2(lm1, lp1) + P1P1;
+            t = vmin2(vmin2(t, Lq[k2]), mP2);
+            const uint32_t Lnew = (c2[k2] + t) - mm;
+            Dreg[k2] = (Lnew & keep[k2]) | (kInf2 & ~keep[k2]);
+            pmin = vmin2(pmin, Dreg[k2]);
         }
-        if (kn < len) {
-            o_n = __shfl_sync(kFull, dc0.x, kn & 31);
-            lw_n = __shfl_sync(kFull, dc0.y, kn & 31);
-            prefetch(o_n, lw_n);
-        }
-
-        // make the predecessor available in the representation this step reads
-        const bool p_narrow = w <= 32;
-        const bool p_full = !p_narrow && w == D;
-        if (!first) {
-            const bool need_smem = (p_narrow && loc != 0) || (p_full && loc != 1) ||
-                                   (!p_narrow && !p_full);
-            if (need_smem && loc != 2) {
-                if (loc == 0) {
-                    if (lane < qw) reinterpret_cast<uint16_t*>(buf0)[qlo + lane] = (uint16_t)Nreg;
-                } else {
+        return (int)min(pmin & 0xFFFFu, pmin >> 16);
+    };
+    // dense store: the low byte of every 16-bit label, four labels per 32-bit store when the
+    // lane's labels start 4-aligned (LPL a multiple of 4), otherwise two per 16-bit store
+    auto emit_dense = [&](uint32_t o) {
+        if constexpr (LPL % 4 == 0) {
 #pragma unroll
-                    for (int k2 = 0; k2 < NP; ++k2) buf0[(LPL * lane) / 2 + k2] = Dreg[k2];
-                }
-                qb = 0;
-                loc = 2;
-                __syncwarp();
+            for (int k4 = 0; k4 < NP / 2; ++k4) {
+                const int e = LPL * lane + 4 * k4;
+                if (e < D)
+                    *reinterpret_cast<uint32_t*>(Lv + o + e) =
+                        __byte_perm(Dreg[2 * k4], Dreg[2 * k4 + 1], 0x6420);
+            }
+        } else {
+#pragma unroll
+            for (int k2 = 0; k2 < NP; ++k2) {
+                const int e = LPL * lane + 2 * k2;
+                if (e < D)
+                    *reinterpret_cast<uint16_t*>(Lv + o + e) =
+                        (uint16_t)__byte_perm(Dreg[k2], 0u, 0x0020);
             }
         }
-        const uint32_t* srcp = buf0 + qb * kBufPairs;
-        const uint16_t* src16 = reinterpret_cast<const uint16_t*>(srcp);
-        int lmin;
-        if (p_narrow) {
-            const bool act = lane < w;
+    };
+
+    uint32_t o, lw;
+    fetch(0, o, lw);
+    int k = 0;
+    while (k < len) {
+        int lo = (int)(lw & 0xFFFFu);
+        int w = (int)(lw >> 16);
+        if (w <= 32) {
+            // ------------------------------------------------------------ narrow run
+            int c = lane < w ? (int)__ldg(C + o + lane) : 0;
             int L;
-            if (first) {
-                L = cN;
+            if (k == 0) {
+                L = c;
             } else {
-                int vc, vl, vr;
-                if (loc == 0) {
-                    const int s = lane + (lo - qlo);
-                    vc = __shfl_sync(kFull, Nreg, s & 31);
-                    vl = __shfl_sync(kFull, Nreg, (s - 1) & 31);
-                    vr = __shfl_sync(kFull, Nreg, (s + 1) & 31);
-                    vc = ((unsigned)s < (unsigned)qw) ? vc : kInf;
-                    vl = ((unsigned)(s - 1) < (unsigned)qw) ? vl : kInf;
-                    vr = ((unsigned)(s + 1) < (unsigned)qw) ? vr : kInf;
-                } else {
-                    const int d = lo + lane;
-                    const int qhi = qlo + qw - 1;
-                    vc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
-                    vl = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
-                    vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
-                }
-                const int t = min(min(min(vl, vr) + P1, vc), m + P2);
-                L = cN + t - m;
+                spill();
+                const uint16_t* src16 = reinterpret_cast<const uint16_t*>(buf0 + qb * kBufPairs);
+                const int d = lo + lane;
+                const int qhi = qlo + qw - 1;
+                const int vc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
+                const int vl = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
+                const int vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
+                L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
             }
-            L = act ? L : kInf;
-            const int Ln = __shfl_down_sync(kFull, L, 1);
-            if (act && !(lane & 1))
-                atomicAdd(S32 + ((o + lane) >> 1),
-                          (uint32_t)L | ((lane + 1 < w) ? ((uint32_t)Ln << 16) : 0u));
-            Nreg = L;
-            lmin = L;
-            loc = 0;
-        } else if (p_full) {
-            uint32_t Lq[NP];
-            if (!first) {
-                if (loc == 1) {
-#pragma unroll
-                    for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[k2];
-                } else {
-                    const int qhi = qlo + qw - 1;
-#pragma unroll
-                    for (int k2 = 0; k2 < NP; ++k2)
-                        Lq[k2] = mask_pair(srcp[(LPL * lane) / 2 + k2], LPL * lane + 2 * k2, qlo, qhi);
+            for (;;) {
+                // look one pixel ahead: its descriptor and (if narrow) its costs
+                const bool more = k + 1 < len;
+                uint32_t o_n = 0, lw_n = 0;
+                int c_n = 0;
+                if (more) {
+                    fetch(k + 1, o_n, lw_n);
+                    const int w_n = (int)(lw_n >> 16);
+                    c_n = (w_n <= 32 && lane < w_n) ? (int)__ldg(C + o_n + lane) : 0;
                 }
+                L = lane < w ? L : kInf;
+                emit_narrow(o, L, w);
+                m = (int)__reduce_min_sync(kFull, (unsigned)L);
+                Nreg = L;
+                qlo = lo;
+                qw = w;
+                loc = 0;
+                ++k;
+                if (!more) break;
+                o = o_n;
+                lw = lw_n;
+                lo = (int)(lw & 0xFFFFu);
+                w = (int)(lw >> 16);
+                if (w > 32) break;
+                const int s_ = lane + (lo - qlo);
+                int vc = __shfl_sync(kFull, Nreg, s_ & 31);
+                int vl = __shfl_sync(kFull, Nreg, (s_ - 1) & 31);
+                int vr = __shfl_sync(kFull, Nreg, (s_ + 1) & 31);
+                vc = ((unsigned)s_ < (unsigned)qw) ? vc : kInf;
+                vl = ((unsigned)(s_ - 1) < (unsigned)qw) ? vl : kInf;
+                vr = ((unsigned)(s_ + 1) < (unsigned)qw) ? vr : kInf;
+                L = c_n + min(min(min(vl, vr) + P1, vc), m + P2) - m;
             }
-            uint32_t pmin = kInf2;
-            if (first) {
+        } else if (w == D) {
+            // ------------------------------------------------------------ full-range run
+            uint32_t c2[NP];
+            load_dense_cost(o, c2);
+            int lmin;
+            if (k == 0) {
+                uint32_t pmin = kInf2;
 #pragma unroll
                 for (int k2 = 0; k2 < NP; ++k2) {
                     Dreg[k2] = (c2[k2] & keep[k2]) | (kInf2 & ~keep[k2]);
                     pmin = vmin2(pmin, Dreg[k2]);
                 }
+                lmin = (int)min(pmin & 0xFFFFu, pmin >> 16);
             } else {
-                uint32_t left_in = __shfl_up_sync(kFull, Lq[NP - 1], 1);
-                uint32_t right_in = __shfl_down_sync(kFull, Lq[0], 1);
-                if (lane == 0) left_in = kInf2;
-                if (lane == 31) right_in = kInf2;
-                const uint32_t mm = ((uint32_t)m << 16) | (uint32_t)m;
-                const uint32_t mP2 = mm + (((uint32_t)P2 << 16) | (uint32_t)P2);
+                spill();
+                const uint32_t* srcp = buf0 + qb * kBufPairs;
+                const int qhi = qlo + qw - 1;
+                uint32_t Lq[NP];
 #pragma unroll
-                for (int k2 = 0; k2 < NP; ++k2) {
-                    const uint32_t prev = (k2 == 0) ? left_in : Lq[k2 - 1];
-                    const uint32_t next = (k2 == NP - 1) ? right_in : Lq[k2 + 1];
-                    const uint32_t lm1 = __byte_perm(prev, Lq[k2], 0x5432);  // (d-1) values
-                    const uint32_t lp1 = __byte_perm(Lq[k2], next, 0x5432);  // (d+1) values
-                    uint32_t t = vmin2(lm1, lp1) + P1P1;
-                    t = vmin2(vmin2(t, Lq[k2]), mP2);
-                    const uint32_t Lnew = (c2[k2] + t) - mm;
-                    Dreg[k2] = (Lnew & keep[k2]) | (kInf2 & ~keep[k2]);
-                    pmin = vmin2(pmin, Dreg[k2]);
+                for (int k2 = 0; k2 < NP; ++k2)
+                    Lq[k2] = mask_pair(srcp[(LPL * lane) / 2 + k2], LPL * lane + 2 * k2, qlo, qhi);
+                lmin = dense_step(Lq, c2);
+            }
+            for (;;) {
+                const bool more = k + 1 < len;
+                uint32_t o_n = 0, lw_n = 0;
+                if (more) {
+                    fetch(k + 1, o_n, lw_n);
+                    if ((int)(lw_n >> 16) == D) load_dense_cost(o_n, c2);
                 }
-            }
-            // packed reductions: the lane's pairs are 4-byte aligned (even block start, LPL even)
+                emit_dense(o);
+                m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
+                qlo = 0;
+                qw = D;
+                loc = 1;
+                ++k;
+                if (!more) break;
+                o = o_n;
+                lw = lw_n;
+                if ((int)(lw >> 16) != D) break;
+                uint32_t Lq[NP];
 #pragma unroll
-            for (int k2 = 0; k2 < NP; ++k2) {
-                const int e = LPL * lane + 2 * k2;
-                if (e < D) atomicAdd(S32 + ((o + e) >> 1), Dreg[k2] & keep[k2]);
+                for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[k2];
+                lmin = dense_step(Lq, c2);
             }
-            lmin = (int)min(pmin & 0xFFFFu, pmin >> 16);
-            loc = 1;
         } else {
-            // general window: shared memory indexed by absolute disparity
+            // ------------------------------------------------------------ general window
+            if (k > 0) spill();
+            __syncwarp();
+            const uint16_t* src16 = reinterpret_cast<const uint16_t*>(buf0 + qb * kBufPairs);
             uint16_t* dst16 = reinterpret_cast<uint16_t*>(buf0 + (qb ^ 1) * kBufPairs);
             const int qhi = qlo + qw - 1;
-            lmin = kInf;
+            int lmin = kInf;
             for (int j0 = 0; j0 < w; j0 += 32) {
                 const int j = j0 + lane;
                 const bool act = j < w;
                 const int d = lo + j;
-                const int c = (j0 == 0) ? cN : (act ? (int)__ldg(C + o + j) : 0);
+                const int c = act ? (int)__ldg(C + o + j) : 0;
                 int L;
-                if (first) {
+                if (k == 0) {
                     L = c;
                 } else {
                     const int vc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
                     const int vl = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
                     const int vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
-                    const int t = min(min(min(vl, vr) + P1, vc), m + P2);
-                    L = c + t - m;
+                    L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
                 }
                 L = act ? L : kInf;
                 if (act) dst16[d] = (uint16_t)L;
                 lmin = min(lmin, L);
-                const int Ln = __shfl_down_sync(kFull, L, 1);
-                if (act && !(j & 1))
-                    atomicAdd(S32 + ((o + j) >> 1),
-                              (uint32_t)L | ((j + 1 < w) ? ((uint32_t)Ln << 16) : 0u));
+                if (act) Lv[o + j] = (uint8_t)L;
             }
+            m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
             qb ^= 1;
             loc = 2;
+            qlo = lo;
+            qw = w;
+            __syncwarp();
+            if (++k < len) fetch(k, o, lw);
         }
-        m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
-        qlo = lo;
-        qw = w;
-        __syncwarp();
     }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Selection + left-right check. One block per image row; one warp per pixel at a time.
-//  * d* = argmin S (lowest d on ties), packed key (S << 16 | j) reduced over the warp;
-//  * sub-pixel parabola when d*-1 and d*+1 are in the window;
-//  * r = n_l + n_r (Eq. 9): prefix sums of S(d) - S(d*) walking away from d*, counted while
-//    below s_thr (the rise is >= 0, so the counted labels form a run next to d*);
+// Selection + left-right check. One block per image row.
+//  * S(p, d) = sum over the directions of L_r(p, d), read 4 labels at a time (32-bit loads);
+//  * d* = argmin S (lowest d on ties); sub-pixel parabola when d*-1 and d*+1 are in the window;
+//  * r = n_l + n_r (Eq. 9): walking away from d*, a neighbour counts while the running sum of
+//    S(d) - S(d*) stays below s_thr; the rise is >= 0, so the running sums grow with the distance
+//    and the count is the number of labels whose sum from d* outwards is below s_thr;
 //  * right-view disparity D_R(xr) = argmin over cells with x - d = xr of (S, d), built in shared
 //    memory with atomicMin on (S << 9 | d); after the row, |d* - D_R(x - d*)| <= tol passes.
+// Pixels with at most kSelNarrow labels are handled by one thread each with S in registers;
+// wider windows are queued and handled by a whole warp each.
 // ---------------------------------------------------------------------------------------------
+constexpr int kSelThreads = 512;
+constexpr int kSelNarrow = 16;
+
 __device__ __forceinline__ int count_side(const uint16_t* __restrict__ s, int start, int dirn,
                                           int lo_idx, int hi_idx, int s0, float thr, int lane) {
     int carry = 0, count = 0;
@@ -405,47 +452,157 @@ __device__ __forceinline__ int count_side(const uint16_t* __restrict__ s, int st
     return count;
 }
 
-__global__ void __launch_bounds__(1024) k_select(const uint16_t* __restrict__ S,
-                                                 const uint2* __restrict__ desc, int W,
-                                                 float s_thr, float r_min, int lr_tol,
-                                                 float* __restrict__ Dz, float* __restrict__ rz,
-                                                 int16_t* __restrict__ dstar_out,
-                                                 int16_t* __restrict__ dright_out,
-                                                 uint8_t* __restrict__ valid_out) {
+// sum of the path volumes for labels j .. j+3 of the block at o: two u16x2 words
+template <int NPATHS>
+__device__ __forceinline__ void sum_paths(const uint8_t* __restrict__ Lvol, uint64_t stride,
+                                          uint32_t o, int j, uint32_t& p0, uint32_t& p1) {
+    uint32_t v[NPATHS];
+#pragma unroll
+    for (int r = 0; r < NPATHS; ++r)
+        v[r] = __ldg(reinterpret_cast<const uint32_t*>(Lvol + r * stride + o + j));
+    p0 = 0u;
+    p1 = 0u;
+#pragma unroll
+    for (int r = 0; r < NPATHS; ++r) {
+        p0 += __byte_perm(v[r], 0u, 0x4140);
+        p1 += __byte_perm(v[r], 0u, 0x4342);
+    }
+}
+
+template <int NPATHS>
+__global__ void __launch_bounds__(kSelThreads) k_select(
+    const uint8_t* __restrict__ Lvol, uint64_t vol_stride, const uint2* __restrict__ desc, int W,
+    int DP, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz, float* __restrict__ rz,
+    uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
+    int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out) {
     extern __shared__ uint32_t sel_smem[];
-    uint32_t* drk = sel_smem;            // W keys
-    float* dzs = (float*)(drk + W);      // W
-    float* rzs = dzs + W;                // W
-    int16_t* ds = (int16_t*)(rzs + W);   // W
+    __shared__ int n_wide;
+    uint32_t* drk = sel_smem;                    // W keys
+    float* dzs = (float*)(drk + W);              // W
+    float* rzs = dzs + W;                        // W
+    int16_t* ds = (int16_t*)(rzs + W);           // W
+    int16_t* wideq = ds + W;                     // W queued wide pixels
+    // per-warp scratch of DP labels, 8-byte aligned for the 4-label stores
+    uint16_t* scr_all = (uint16_t*)(sel_smem + ((3 * W + W + 1) & ~1));
     const int y = blockIdx.x;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int x = threadIdx.x; x < W; x += blockDim.x) drk[x] = 0xFFFFFFFFu;
+    if (threadIdx.x == 0) n_wide = 0;
     __syncthreads();
-    for (int x = wid; x < W; x += nw) {
+
+    // ---- narrow windows: one thread per pixel
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int i = y * W + x;
         const uint2 dsc = desc[i];
+        const uint32_t o = dsc.x;
         const int a = (int)(dsc.y & 0xFFFFu);
         const int w = (int)(dsc.y >> 16);
-        const uint16_t* s = S + dsc.x;
-        unsigned best = 0xFFFFFFFFu;
-        for (int j = lane; j < w; j += 32) {
-            const unsigned sv = s[j];
-            best = min(best, (sv << 16) | (unsigned)j);
-            const int xr = x - (a + j);
-            if (xr >= 0) atomicMin(drk + xr, (sv << 9) | (unsigned)(a + j));
+        if (w > kSelNarrow) {
+            wideq[atomicAdd(&n_wide, 1)] = (int16_t)x;
+            continue;
         }
+        uint32_t sp[kSelNarrow / 2];  // S as u16x2 pairs
+#pragma unroll
+        for (int q = 0; q < kSelNarrow / 4; ++q) {
+            if (4 * q < w) {
+                sum_paths<NPATHS>(Lvol, vol_stride, o, 4 * q, sp[2 * q], sp[2 * q + 1]);
+                if (S_out) *reinterpret_cast<uint2*>(S_out + o + 4 * q) = make_uint2(sp[2 * q], sp[2 * q + 1]);
+            } else {
+                sp[2 * q] = 0xFFFFFFFFu;
+                sp[2 * q + 1] = 0xFFFFFFFFu;
+            }
+        }
+        int sv[kSelNarrow];
+#pragma unroll
+        for (int j = 0; j < kSelNarrow; ++j)
+            sv[j] = (j < w) ? (int)((j & 1) ? (sp[j >> 1] >> 16) : (sp[j >> 1] & 0xFFFFu)) : 0x7FFFFFFF;
+        int js = 0, s0 = sv[0];
+#pragma unroll
+        for (int j = 1; j < kSelNarrow; ++j)
+            if (sv[j] < s0) {
+                s0 = sv[j];
+                js = j;
+            }
+        int sm = 0, spv = 0;
+#pragma unroll
+        for (int j = 0; j < kSelNarrow; ++j) {
+            if (j == js - 1) sm = sv[j];
+            if (j == js + 1) spv = sv[j];
+            if (j < w) {
+                const int xr = x - (a + j);
+                if (xr >= 0) atomicMin(drk + xr, ((uint32_t)sv[j] << 9) | (uint32_t)(a + j));
+            }
+        }
+        float delta = 0.0f;
+        if (js >= 1 && js + 1 < w) {
+            const int den = 2 * (sm - 2 * s0 + spv);
+            if (den > 0) delta = __fdiv_rn((float)(sm - spv), (float)den);
+        }
+        // counts: running sums outwards from d*; walking labels in order of distance keeps the
+        // sums growing, so every label whose sum is below the threshold is in the counted run
+        int nl = 0, nr = 0, acc = 0;
+#pragma unroll
+        for (int j = kSelNarrow - 1; j >= 0; --j) {
+            if (j < js) {
+                acc += sv[j] - s0;
+                nl += ((float)acc < s_thr) ? 1 : 0;
+            }
+        }
+        acc = 0;
+#pragma unroll
+        for (int j = 0; j < kSelNarrow; ++j) {
+            if (j > js && j < w) {
+                acc += sv[j] - s0;
+                nr += ((float)acc < s_thr) ? 1 : 0;
+            }
+        }
+        float r = (float)(nl + nr);
+        if (r < r_min) r = r_min;
+        ds[x] = (int16_t)(a + js);
+        dzs[x] = __fadd_rn((float)(a + js), delta);
+        rzs[x] = r;
+    }
+    __syncthreads();
+
+    // ---- wide windows: one warp per pixel
+    uint16_t* scr = scr_all + wid * DP;
+    const int nwide = n_wide;
+    for (int q = wid; q < nwide; q += nw) {
+        const int x = wideq[q];
+        const int i = y * W + x;
+        const uint2 dsc = desc[i];
+        const uint32_t o = dsc.x;
+        const int a = (int)(dsc.y & 0xFFFFu);
+        const int w = (int)(dsc.y >> 16);
+        unsigned best = 0xFFFFFFFFu;
+        for (int j = 4 * lane; j < w; j += 128) {
+            uint32_t p0, p1;
+            sum_paths<NPATHS>(Lvol, vol_stride, o, j, p0, p1);
+            *reinterpret_cast<uint2*>(scr + j) = make_uint2(p0, p1);
+            if (S_out) *reinterpret_cast<uint2*>(S_out + o + j) = make_uint2(p0, p1);
+            const unsigned sv[4] = {p0 & 0xFFFFu, p0 >> 16, p1 & 0xFFFFu, p1 >> 16};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (j + t < w) {
+                    best = min(best, (sv[t] << 16) | (unsigned)(j + t));
+                    const int xr = x - (a + j + t);
+                    if (xr >= 0) atomicMin(drk + xr, (sv[t] << 9) | (unsigned)(a + j + t));
+                }
+            }
+        }
+        __syncwarp();
         best = __reduce_min_sync(kFull, best);
         const int js = (int)(best & 0xFFFFu);
         const int s0 = (int)(best >> 16);
         float delta = 0.0f;
         if (js >= 1 && js + 1 < w) {
-            const int sm = s[js - 1], sp = s[js + 1];
-            const int den = 2 * (sm - 2 * s0 + sp);
-            if (den > 0) delta = __fdiv_rn((float)(sm - sp), (float)den);
+            const int smv = scr[js - 1], spv = scr[js + 1];
+            const int den = 2 * (smv - 2 * s0 + spv);
+            if (den > 0) delta = __fdiv_rn((float)(smv - spv), (float)den);
         }
-        const int nl = count_side(s, js - 1, -1, 0, w - 1, s0, s_thr, lane);
-        const int nr = count_side(s, js + 1, +1, 0, w - 1, s0, s_thr, lane);
+        const int nl = count_side(scr, js - 1, -1, 0, w - 1, s0, s_thr, lane);
+        const int nr = count_side(scr, js + 1, +1, 0, w - 1, s0, s_thr, lane);
         float r = (float)(nl + nr);
         if (r < r_min) r = r_min;
         if (lane == 0) {
@@ -453,6 +610,7 @@ __global__ void __launch_bounds__(1024) k_select(const uint16_t* __restrict__ S,
             dzs[x] = __fadd_rn((float)(a + js), delta);
             rzs[x] = r;
         }
+        __syncwarp();
     }
     __syncthreads();
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
@@ -486,26 +644,27 @@ cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int H
 }
 
 cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* desc, int W, int Hh,
-                        int Bc, uint8_t* C, uint16_t* S, cudaStream_t st) {
+                        int Bc, uint8_t* C, cudaStream_t st) {
     const int n = W * Hh;
     int blocks = (n * 8 + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_cost<<<blocks, 256, 0, st>>>(cl, cr, desc, W, n, Bc, C, S);
+    k_cost<<<blocks, 256, 0, st>>>(cl, cr, desc, W, n, Bc, C);
     return cudaGetLastError();
 }
 
 template <int LPL>
 static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int Hh, int D,
-                                int P1, int P2, const SgmLines& L, uint32_t* S32, cudaStream_t st) {
+                                int P1, int P2, const SgmLines& L, uint8_t* Lvol,
+                                uint64_t vol_stride, cudaStream_t st) {
     const int nlines = L.start[L.nslots];
     const int blocks = (nlines + kSgmWarps - 1) / kSgmWarps;
     const size_t smem = (size_t)kSgmWarps * 2 * (32 * LPL) * sizeof(uint16_t);  // 2 buffers/warp
-    k_sgm<LPL><<<blocks, kSgmWarps * 32, smem, st>>>(C, desc, W, Hh, D, P1, P2, L, S32);
+    k_sgm<LPL><<<blocks, kSgmWarps * 32, smem, st>>>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
-                       int P1, int P2, uint16_t* S, cudaStream_t st) {
+                       int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, cudaStream_t st) {
     // slots ordered longest lines first: horizontal, vertical, then diagonals
     SgmLines L;
     L.nslots = n_paths;
@@ -516,24 +675,28 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
         const int cnt = code <= 1 ? Hh : (code <= 3 ? W : W + Hh - 1);
         L.start[s + 1] = L.start[s] + cnt;
     }
-    uint32_t* S32 = reinterpret_cast<uint32_t*>(S);
-    if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, D, P1, P2, L, S32, st);
-    if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, D, P1, P2, L, S32, st);
-    if (D <= 192) return launch_sgm_t<6>(C, desc, W, Hh, D, P1, P2, L, S32, st);
-    return launch_sgm_t<8>(C, desc, W, Hh, D, P1, P2, L, S32, st);
+    if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
+    if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
+    if (D <= 192) return launch_sgm_t<6>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
+    return launch_sgm_t<8>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
 }
 
-cudaError_t launch_select(const uint16_t* S, const uint2* desc, int W, int Hh, float s_thr,
-                          float r_min, int lr_tol, float* Dz, float* rz, int16_t* dstar,
-                          int16_t* dright, uint8_t* valid, cudaStream_t st) {
-    const size_t smem = (size_t)W * (4 + 4 + 4 + 2);
+cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
+                          int W, int Hh, float s_thr, float r_min, int lr_tol, float* Dz, float* rz,
+                          uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
+                          cudaStream_t st) {
+    // per-warp scratch for the wide windows: up to 256 labels
+    const int DP = 256;
+    const size_t smem = (size_t)((3 * W + W + 1) & ~1) * 4 +
+                        (size_t)(kSelThreads / 32) * DP * sizeof(uint16_t);
+    auto kern = n_paths == 8 ? k_select<8> : k_select<4>;
     if (smem > 48 * 1024) {
         const cudaError_t e =
-            cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_select<<<Hh, 1024, smem, st>>>(S, desc, W, s_thr, r_min, lr_tol, Dz, rz, dstar, dright,
-                                     valid);
+    kern<<<Hh, kSelThreads, smem, st>>>(Lvol, vol_stride, desc, W, DP, s_thr, r_min, lr_tol, Dz, rz,
+                                        S, dstar, dright, valid);
     return cudaGetLastError();
 }
 

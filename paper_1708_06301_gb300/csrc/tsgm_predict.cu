@@ -14,9 +14,9 @@ namespace {
 
 __device__ __forceinline__ bool valid_value(float v) { return v >= 0.0f && v <= FLT_MAX; }
 
-// Storage of one pixel's window in the ragged volume: rounded up to an even number of cells so
-// that every block starts 4-byte aligned in the uint16 aggregate (packed pair updates).
-__device__ __forceinline__ uint32_t block_cells(int w) { return (uint32_t)(w + (w & 1)); }
+// Storage of one pixel's window in the ragged volumes: rounded up to a multiple of 4 cells so that
+// every block starts 4-byte aligned in the uint8 volumes (32-bit loads and stores of 4 labels).
+__device__ __forceinline__ uint32_t block_cells(int w) { return (uint32_t)((w + 3) & ~3); }
 
 // ---------------------------------------------------------------------------------------------
 // Warp scatter (Eq. 3 + homogeneous divide; z-buffer of Sec. 2.2 "disparity refinement").
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) k_sanitize_rowsum(const int16_t* __restri
     }
 }
 
-// Offsets of the ragged volume: pixel i's block starts at off[i] = sum of the (2-aligned) block
+// Offsets of the ragged volume: pixel i's block starts at off[i] = sum of the (4-aligned) block
 // sizes of the pixels before it (row-major); off[n] = storage size. One block per row: base =
 // sum of earlier row totals, then a block scan. Also writes the per-pixel descriptor
 // {off, lo | w << 16} used by the matching kernels, and (last row) the number of true cells.

@@ -34,7 +34,7 @@ def f32(x):
 
 def compact(buf: np.ndarray, off: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
     """Cells of a ragged buffer laid out with per-pixel block starts `off` (the GPU layout, blocks
-    rounded up to even) gathered into the compact order (window after window, no gaps)."""
+    rounded up to a multiple of 4 cells) gathered into the compact order (no gaps)."""
     w = (hi.astype(np.int64) - lo.astype(np.int64) + 1).reshape(-1)
     start = np.repeat(off[:-1].astype(np.int64), w)
     pos = np.arange(int(w.sum()), dtype=np.int64) - np.repeat(np.concatenate([[0], np.cumsum(w)[:-1]]), w)
@@ -42,6 +42,6 @@ def compact(buf: np.ndarray, off: np.ndarray, lo: np.ndarray, hi: np.ndarray) ->
 
 
 def padded_offsets(lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
-    """Block starts of the GPU layout: exclusive scan of the window lengths rounded up to even."""
+    """Block starts of the GPU layout: exclusive scan of the window lengths rounded up to 4."""
     w = (hi.astype(np.int64) - lo.astype(np.int64) + 1).reshape(-1)
-    return np.concatenate([[0], np.cumsum(w + (w & 1))]).astype(np.uint32)
+    return np.concatenate([[0], np.cumsum((w + 3) & ~3)]).astype(np.uint32)
