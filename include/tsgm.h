@@ -208,6 +208,32 @@ tsgm_status tsgm_launches(tsgm_ctx* ctx, uint64_t* n);
 tsgm_status tsgm_profile(tsgm_ctx* ctx, int32_t enable);
 tsgm_status tsgm_stage_times(tsgm_ctx* ctx, double ms[TSGM_N_STAGES], int64_t count[TSGM_N_STAGES]);
 
+/* Disparity prediction that allocates nothing (the paper has no counterpart: this is a
+ * deployment variant of tsgm_warp_predict).
+ *
+ * Some callers cannot allocate device memory: a process whose GPU memory is owned by another
+ * framework's caching allocator, where a cudaMalloc outside it can fail once the pool holds the
+ * free memory, or a real-time loop that must not call cudaMalloc because it can block on the
+ * device. This call does what tsgm_warp_predict does, without a context: its z-buffer is a
+ * fixed array of TSGM_NOALLOC_MAX_PIXELS 64-bit keys (16 MiB) in the library's device memory,
+ * held by every GPU that loads the library until the process exits. It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   prev_D, prev_P, pred_D, pred_P: device maps of width*height floats, as in tsgm_warp_predict;
+ *   q: variance added by the prediction (Eq. 5); cuda_stream: stream to enqueue on (NULL: the
+ *   legacy default stream); errbuf: optional buffer of errbuf_len bytes for a message.
+ * Returns INVALID_ARG (nothing launched) for null pointers, a bad pose or calibration, or
+ * width * height > TSGM_NOALLOC_MAX_PIXELS; CUDA if a launch fails.
+ * The first call on a device looks up the array's device address on that device (a one-time
+ * set-up); make that first call before any stream capture. Every call shares the one array and
+ * resets the keys it uses, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+#define TSGM_NOALLOC_MAX_PIXELS 2097152
+tsgm_status tsgm_warp_predict_noalloc(const float* prev_D, const float* prev_P, int32_t width,
+                                      int32_t height, const float R[9], const float t[3],
+                                      const float K[9], float baseline, float q, float* pred_D,
+                                      float* pred_P, void* cuda_stream, char* errbuf,
+                                      size_t errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif
