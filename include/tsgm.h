@@ -208,6 +208,26 @@ tsgm_status tsgm_launches(tsgm_ctx* ctx, uint64_t* n);
 tsgm_status tsgm_profile(tsgm_ctx* ctx, int32_t enable);
 tsgm_status tsgm_stage_times(tsgm_ctx* ctx, double ms[TSGM_N_STAGES], int64_t count[TSGM_N_STAGES]);
 
+/* Adjoint of the float stages (training/fitting form): prediction (Sec. 2.2, Eq. 3, 5, 6) then
+ * the Kalman update (Sec. 2.4, Eq. 10-12) as a function of the pose, q and a measurement-variance
+ * scale s_r (r = s_r * r_z).
+ *   pose6 = (w0, w1, w2, t0, t1, t2): R = exp([w]x) (Rodrigues, binary64 then rounded to
+ *   binary32 for the warp), t in metres, convention of Eq. 2.
+ * tsgm_adjoint_forward writes D, P (device, width*height floats) and keeps the z-buffer winners
+ * in the context. tsgm_adjoint_backward must follow it with the same inputs: given the upstream
+ * gradients grad_D, grad_P (device), it recomputes every quantity except the winners (target
+ * pixels are roundings, piecewise constant in the pose) and writes dL/d(w0, w1, w2, t0, t1, t2,
+ * q, s_r) to the host array grad_out[8] (binary64; synchronises the stream). dL/dt0 and dL/dt1
+ * are 0: with the winners fixed, lateral translation does not change any predicted depth. */
+tsgm_status tsgm_adjoint_forward(tsgm_ctx* ctx, const float* prev_D, const float* prev_P,
+                                 const double pose6[6], const float K[9], float baseline, float q,
+                                 float r_scale, const float* D_z, const float* r_z, float* D,
+                                 float* P);
+tsgm_status tsgm_adjoint_backward(tsgm_ctx* ctx, const float* prev_D, const float* prev_P,
+                                  const double pose6[6], const float K[9], float baseline, float q,
+                                  float r_scale, const float* D_z, const float* r_z,
+                                  const float* grad_D, const float* grad_P, double grad_out[8]);
+
 /* Disparity prediction that allocates nothing (the paper has no counterpart: this is a
  * deployment variant of tsgm_warp_predict).
  *

@@ -268,3 +268,132 @@ class Tracker:
             out.update(Dpred=Dp, Ppred=Pp, lo=lo, hi=hi, n_cells=n_cells, D=D, P=P)
             return out
         return D, P
+
+
+# ----------------------------------------------------------------------------------------------
+# Adjoint references (float stages: prediction Eq. 3, 5, 6 then Kalman Eq. 10-12), binary64
+# ----------------------------------------------------------------------------------------------
+
+def rodrigues(w):
+    """R = exp([w]x) for a rotation vector w (binary64)."""
+    w = np.asarray(w, np.float64).reshape(3)
+    th = float(np.linalg.norm(w))
+    if th == 0.0:
+        return np.eye(3)
+    k = w / th
+    Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + np.sin(th) * Kx + (1 - np.cos(th)) * (Kx @ Kx)
+
+
+def warp_kalman_f64(prevD, prevP, winner, pose6, K, b, q, s_r, Dz, rz):
+    """Prediction and update in binary64 with the z-buffer winners held fixed (`winner`: source
+    index per target or -1). Returns (D, P) as float64 maps."""
+    pose6 = np.asarray(pose6, np.float64)
+    f, cx, cy = K_fbc(K)
+    H64, _ = build_H(rodrigues(pose6[:3]), pose6[3:], f, float(b))
+    Hh, W = prevD.shape
+    win = np.asarray(winner).reshape(-1)
+    has = win >= 0
+    s = win[has]
+    d = prevD.reshape(-1)[s].astype(np.float64)
+    p = prevP.reshape(-1)[s].astype(np.float64)
+    u = (s % W).astype(np.float64) - float(np.float32(cx))
+    v = (s // W).astype(np.float64) - float(np.float32(cy))
+    w = H64 @ np.stack([u, v, d, np.ones_like(d)])
+    dp = w[2] / w[3]                       # Eq. 3: divide by the fourth component
+    pp = (dp / d) ** 2 * p + q             # Eq. 5-6
+    n = W * Hh
+    Dp = np.full(n, -1.0)
+    Pp = np.full(n, -1.0)
+    Dp[has] = dp
+    Pp[has] = pp
+    dz = Dz.reshape(-1).astype(np.float64)
+    rr = rz.reshape(-1).astype(np.float64)
+    mv = (dz >= 0) & (rr >= 0) & np.isfinite(dz) & np.isfinite(rr)
+    r = s_r * rr
+    D = np.full(n, -1.0)
+    P = np.full(n, -1.0)
+    both = has & mv
+    Kg = Pp[both] / (Pp[both] + r[both])   # Eq. 10
+    D[both] = Dp[both] + Kg * (dz[both] - Dp[both])  # Eq. 11
+    P[both] = (1 - Kg) * Pp[both]          # Eq. 12
+    mo = mv & ~has
+    D[mo], P[mo] = dz[mo], r[mo]
+    po = has & ~mv
+    D[po], P[po] = Dp[po], Pp[po]
+    return D.reshape(Hh, W), P.reshape(Hh, W)
+
+
+def adjoint_fd(prevD, prevP, winner, pose6, K, b, q, s_r, Dz, rz, gD, gP, h=1e-4):
+    """Central finite differences (binary64) of L = sum(gD * D + gP * P) with respect to
+    (w0, w1, w2, t0, t1, t2, q, s_r)."""
+    th = np.concatenate([np.asarray(pose6, np.float64), [q, s_r]])
+    gD = gD.astype(np.float64)
+    gP = gP.astype(np.float64)
+
+    def loss(x):
+        D, P = warp_kalman_f64(prevD, prevP, winner, x[:6], K, b, x[6], x[7], Dz, rz)
+        return float(np.sum(gD * D) + np.sum(gP * P))
+
+    g = np.zeros(8)
+    for i in range(8):
+        e = np.zeros(8)
+        e[i] = h
+        g[i] = (loss(th + e) - loss(th - e)) / (2 * h)
+    return g
+
+
+def adjoint_grad_f64(prevD, prevP, winner, pose6, K, b, q, s_r, Dz, rz, gD, gP):
+    """Analytic gradient of L = sum(gD * D + gP * P) in binary64, written from the forward
+    definitions above; dR/dw by central differences of `rodrigues` (step 1e-6)."""
+    pose6 = np.asarray(pose6, np.float64)
+    f, cx, cy = K_fbc(K)
+    R = rodrigues(pose6[:3])
+    t = pose6[3:]
+    Hh, W = prevD.shape
+    win = np.asarray(winner).reshape(-1)
+    has = win >= 0
+    s = win[has]
+    d = prevD.reshape(-1)[s].astype(np.float64)
+    p = prevP.reshape(-1)[s].astype(np.float64)
+    u = (s % W).astype(np.float64) - float(np.float32(cx))
+    v = (s // W).astype(np.float64) - float(np.float32(cy))
+    # fourth row of H = Gamma T Gamma^{-1}: (R20/f, R21/f, t2/(f b), R22)
+    w3 = R[2, 0] * u / f + R[2, 1] * v / f + t[2] * d / (f * b) + R[2, 2]
+    dp = d / w3
+    pp = (dp / d) ** 2 * p + q
+    dz = Dz.reshape(-1)[has].astype(np.float64)
+    rr = rz.reshape(-1)[has].astype(np.float64)
+    mv = (dz >= 0) & (rr >= 0)
+    gd = gD.reshape(-1)[has].astype(np.float64)
+    gp = gP.reshape(-1)[has].astype(np.float64)
+    r = s_r * rr
+    den = pp + r
+    dD_ddp = np.where(mv, r / den, 1.0)
+    dD_dpp = np.where(mv, (dz - dp) * r / den ** 2, 0.0)
+    dP_dpp = np.where(mv, (r / den) ** 2, 1.0)
+    dD_dr = np.where(mv, -(dz - dp) * pp / den ** 2, 0.0)
+    dP_dr = np.where(mv, (pp / den) ** 2, 0.0)
+    dL_dpp = gd * dD_dpp + gp * dP_dpp
+    dL_ddp = gd * dD_ddp + dL_dpp * 2 * p * dp / d ** 2
+    dL_dw3 = dL_ddp * (-d / w3 ** 2)
+    g_R2 = np.array([np.sum(dL_dw3 * u / f), np.sum(dL_dw3 * v / f), np.sum(dL_dw3)])
+    g_t2 = np.sum(dL_dw3 * d / (f * b))
+    g_q = np.sum(dL_dpp)
+    g_sr = np.sum((gd * dD_dr + gp * dP_dr) * rr)
+    # measurement-only targets: P = s_r r_z
+    dzall = Dz.reshape(-1).astype(np.float64)
+    rall = rz.reshape(-1).astype(np.float64)
+    mo = (~has) & (dzall >= 0) & (rall >= 0)
+    g_sr += np.sum(gP.reshape(-1)[mo].astype(np.float64) * rall[mo])
+    g = np.zeros(8)
+    hstep = 1e-6
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = hstep
+        dR = (rodrigues(pose6[:3] + e) - rodrigues(pose6[:3] - e)) / (2 * hstep)
+        g[i] = float(np.dot(g_R2, dR[2]))
+    g[5] = g_t2
+    g[6] = g_q
+    g[7] = g_sr
+    return g

@@ -132,7 +132,7 @@ void free_all(tsgm_ctx* c) {
     void* bufs[] = {c->censusL, c->censusR, c->keys,   c->predD,  c->predP,   c->Dz,
                     c->rz,      c->stateD,  c->stateP, c->lo,     c->hi,      c->dstar,
                     c->dright,  c->lrvalid, c->off,    c->rowsum, c->C,       c->S,
-                    c->rowcells, c->cells,  c->desc,  c->Lvol,
+                    c->rowcells, c->cells,  c->desc,  c->Lvol,  c->adj_partials,
                     c->d_left,  c->d_right, c->d_outD, c->d_outP};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -293,6 +293,7 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ok = ok && alloc(&ctx->C, (size_t)ctx->max_cells + 64) == cudaSuccess;
     ok = ok && alloc(&ctx->S, (size_t)ctx->max_cells + 64) == cudaSuccess;
     ok = ok && alloc(&ctx->Lvol, (size_t)ctx->max_cells * (size_t)p->n_paths + 64) == cudaSuccess;
+    ok = ok && alloc(&ctx->adj_partials, (size_t)kAdjointBlocks * 6) == cudaSuccess;
     ok = ok && alloc(&ctx->d_left, n) == cudaSuccess;
     ok = ok && alloc(&ctx->d_right, n) == cudaSuccess;
     ok = ok && alloc(&ctx->d_outD, n) == cudaSuccess;

@@ -13,6 +13,7 @@ namespace tsgm {
 
 constexpr int kInf = 0x3FFF;          // +inf for path costs held in 32-bit registers
 constexpr uint64_t kEmptyKey = ~0ull; // empty z-buffer slot
+constexpr int kAdjointBlocks = 152 * 4;  // blocks of the adjoint reduction (one partial each)
 
 // Per-call device views of the inputs of the matching stages.
 struct MatchBufs {
@@ -87,6 +88,7 @@ struct tsgm_ctx {
     uint8_t* C = nullptr;          // ragged matching cost
     uint16_t* S = nullptr;         // aggregated cost, written only with TSGM_FLAG_KEEP_INTERNALS
     uint8_t* Lvol = nullptr;       // one ragged uint8 volume of path costs per SGM direction
+    double* adj_partials = nullptr;  // per-block partial sums of the adjoint (6 per block)
     // staging for tsgm_frame_host
     uint8_t* d_left = nullptr;
     uint8_t* d_right = nullptr;

@@ -68,6 +68,12 @@ _SIGS = {
     "tsgm_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "tsgm_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_adjoint_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _fp,
+                                            ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp,
+                                            _vp, _vp, _vp]),
+    "tsgm_adjoint_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _fp,
+                                             ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp,
+                                             _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "tsgm_stage_times": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -264,6 +270,26 @@ class Context:
         v = ctypes.c_uint64(0)
         self._check(self.lib.tsgm_cells(self.h, ctypes.byref(v)), "tsgm_cells")
         return int(v.value)
+
+    def adjoint_forward(self, prev_D, prev_P, pose6, K, baseline, q, r_scale, D_z, r_z, D, P):
+        p6 = (ctypes.c_double * 6)(*[float(v) for v in np.asarray(pose6, np.float64).reshape(6)])
+        Ka, Kp = _host_f32(K, 9)
+        self._check(self.lib.tsgm_adjoint_forward(self.h, _ptr(prev_D), _ptr(prev_P), p6, Kp,
+                                                  ctypes.c_float(baseline), ctypes.c_float(q),
+                                                  ctypes.c_float(r_scale), _ptr(D_z), _ptr(r_z),
+                                                  _ptr(D), _ptr(P)), "tsgm_adjoint_forward")
+
+    def adjoint_backward(self, prev_D, prev_P, pose6, K, baseline, q, r_scale, D_z, r_z, grad_D,
+                         grad_P) -> np.ndarray:
+        p6 = (ctypes.c_double * 6)(*[float(v) for v in np.asarray(pose6, np.float64).reshape(6)])
+        Ka, Kp = _host_f32(K, 9)
+        g = (ctypes.c_double * 8)()
+        self._check(self.lib.tsgm_adjoint_backward(self.h, _ptr(prev_D), _ptr(prev_P), p6, Kp,
+                                                   ctypes.c_float(baseline), ctypes.c_float(q),
+                                                   ctypes.c_float(r_scale), _ptr(D_z), _ptr(r_z),
+                                                   _ptr(grad_D), _ptr(grad_P), g),
+                    "tsgm_adjoint_backward")
+        return np.array(list(g), dtype=np.float64)
 
     def launches(self) -> int:
         v = ctypes.c_uint64(0)
