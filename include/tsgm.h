@@ -228,6 +228,48 @@ tsgm_status tsgm_adjoint_backward(tsgm_ctx* ctx, const float* prev_D, const floa
                                   float r_scale, const float* D_z, const float* r_z,
                                   const float* grad_D, const float* grad_P, double grad_out[8]);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched matching over many camera streams of different sizes and disparity ranges (the
+ * tsgm_match step of every stream, Sec. 2.3-2.4). One call runs one CUDA graph: every stage is a
+ * single launch over the work of all streams, and the path aggregation is a persistent kernel
+ * whose warps take path lines of any stream from one queue.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct tsgm_batch tsgm_batch;
+
+/* streams[i] gives width, height and d_max of stream i (n_streams <= 128); the matching
+ * parameters (census window, paths, P1, P2, S_max, r_min, lr_tol) must be equal across streams.
+ * max_labels > 0 sizes every stream's ragged volumes for windows of that many labels on average
+ * (0: d_max + 1, never too small); a call whose windows need more cells than a stream's storage
+ * skips that stream and writes -1 to its outputs (reported by tsgm_batch_cells). The batch works
+ * on its own CUDA stream, ordered after and before `cuda_stream` (NULL: legacy default stream)
+ * with events. Errors: INVALID_ARG, OUT_OF_MEMORY. */
+tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int32_t max_labels,
+                              void* cuda_stream, tsgm_batch** out);
+void tsgm_batch_destroy(tsgm_batch* b);
+const char* tsgm_batch_last_error(const tsgm_batch* b);
+
+/* One step: host arrays of n_streams device pointers (images, windows, outputs as in
+ * tsgm_match). The first call captures the graph; later calls update the pointer table and
+ * replay it. A call waits until the previous step of this batch has finished on the GPU. */
+tsgm_status tsgm_batch_match(tsgm_batch* b, const uint8_t* const* left,
+                             const uint8_t* const* right, const int16_t* const* d_lo,
+                             const int16_t* const* d_hi, float* const* D_z, float* const* r_z);
+
+/* Time every candidate launch shape of the path aggregation (warps per block x blocks per SM)
+ * on these inputs, `reps` steps each, keep the fastest and re-capture the graph. Outputs the
+ * best mean step time (ms) and the chosen shape index. Synchronises. */
+tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
+                                const uint8_t* const* right, const int16_t* const* d_lo,
+                                const int16_t* const* d_hi, float* const* D_z, float* const* r_z,
+                                int32_t reps, double* best_ms, int32_t* best_shape);
+
+/* Total window cells of the last step over all streams, and how many streams were skipped for
+ * lack of storage. Synchronises. */
+tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed);
+
+/* Kernels launched by this batch (graph steps count their kernels). */
+tsgm_status tsgm_batch_launches(tsgm_batch* b, uint64_t* n);
+
 /* Disparity prediction that allocates nothing (the paper has no counterpart: this is a
  * deployment variant of tsgm_warp_predict).
  *

@@ -1,0 +1,490 @@
+// Batched matching over many camera streams of different sizes and disparity ranges (Sec. 2.3-2.4
+// applied to every stream): every stage is one launch over the work units of all streams (rows,
+// census tiles, pixels, path lines); the path aggregation is a persistent kernel whose warps pull
+// path lines from one global queue, ordered direction-major so that the long horizontal chains of
+// every stream start first and large and small streams balance; the whole step is captured once
+// in a CUDA graph and replayed. The launch shape of the aggregation is chosen by an autotuner that
+// times the candidates on the caller's data.
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tsgm_kernels.cuh"
+
+namespace {
+
+using namespace tsgm;
+using namespace tsgm::dev;
+
+constexpr int kMaxStreams = 128;
+
+// Device-side view of one stream.
+struct BStream {
+    int W, H, D, n;
+    // per-call inputs and outputs, rewritten before every replay
+    const uint8_t* left;
+    const uint8_t* right;
+    const int16_t* lo_in;
+    const int16_t* hi_in;
+    float* Dz;
+    float* rz;
+    // scratch owned by the batch
+    int16_t* lo;
+    int16_t* hi;
+    uint64_t* censusL;
+    uint64_t* censusR;
+    uint2* desc;
+    uint32_t* off;
+    uint32_t* rowsum;
+    uint32_t* rowcells;
+    uint32_t* cells;
+    uint32_t* status;  // 0 ok, 1: the windows need more cells than the stream's storage
+    uint8_t* C;
+    uint8_t* Lvol;
+    uint64_t capacity;  // cells of storage per volume (C and each direction of Lvol)
+};
+
+struct BTable {
+    int ns;
+    int row_base[kMaxStreams + 1];   // prefix of image rows
+    int tile_base[kMaxStreams + 1];  // prefix of census tiles (one image)
+    int px_base[kMaxStreams + 1];    // prefix of pixels
+    int tiles_x[kMaxStreams];
+    // path lines, direction-major: items of stream i in slot s are
+    // [slot_base[s][i], slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]
+    int slot_base[8][kMaxStreams + 1];
+    int total_lines;
+};
+
+__device__ __forceinline__ int find_stream(const int* base, int ns, int item) {
+    int lo = 0, hi = ns - 1;  // largest i with base[i] <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) kb_sanitize(const BStream* __restrict__ st,
+                                                   const BTable* __restrict__ tb) {
+    const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
+    const BStream& b = st[s];
+    sanitize_row(b.lo_in, b.hi_in, b.W, b.D, blockIdx.x - tb->row_base[s], b.lo, b.hi, b.rowsum,
+                 b.rowcells);
+}
+
+__global__ void __launch_bounds__(512) kb_offsets(const BStream* __restrict__ st,
+                                                  const BTable* __restrict__ tb) {
+    const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
+    const BStream& b = st[s];
+    const int y = blockIdx.x - tb->row_base[s];
+    offsets_row(b.lo, b.hi, b.rowsum, b.rowcells, b.W, b.H, y, b.off, b.desc, b.cells);
+    if (y == b.H - 1 && threadIdx.x == 0)
+        *b.status = (uint64_t)b.off[(size_t)b.W * b.H] > b.capacity ? 1u : 0u;
+}
+
+__global__ void __launch_bounds__(kCtW* kCtH) kb_census(const BStream* __restrict__ st,
+                                                         const BTable* __restrict__ tb, int cw,
+                                                         int ch) {
+    const int s = find_stream(tb->tile_base, tb->ns, blockIdx.x);
+    const BStream& b = st[s];
+    const int t = blockIdx.x - tb->tile_base[s];
+    const int tx = t % tb->tiles_x[s], ty = t / tb->tiles_x[s];
+    census_tile(blockIdx.z ? b.right : b.left, b.W, b.H, cw, ch, tx * kCtW, ty * kCtH,
+                blockIdx.z ? b.censusR : b.censusL);
+}
+
+__global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
+                                               const BTable* __restrict__ tb, int Bc) {
+    const int ngroups = (gridDim.x * blockDim.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    const int total = tb->px_base[tb->ns];
+    for (int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 3; gi < total; gi += ngroups) {
+        const int s = find_stream(tb->px_base, tb->ns, gi);
+        const BStream& b = st[s];
+        if (*b.status != 0u) continue;
+        cost_pixels(b.censusL, b.censusR, b.desc, b.W, b.n, Bc, b.C, gi - tb->px_base[s], sub, b.n);
+    }
+}
+
+// persistent path aggregation: warps take path lines from a global counter until none is left
+template <int LPL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__ st,
+                                                     const BTable* __restrict__ tb, int n_paths,
+                                                     int P1, int P2, int* __restrict__ counter) {
+    extern __shared__ uint32_t sgm_smem32[];
+    uint32_t* buf = sgm_smem32 + (threadIdx.x >> 5) * (32 * LPL);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= tb->total_lines) return;
+        int slot = 0;
+        while (slot + 1 < n_paths && item >= tb->slot_base[slot + 1][0]) ++slot;
+        const int s = find_stream(tb->slot_base[slot], tb->ns, item);
+        const BStream& b = st[s];
+        if (*b.status != 0u) continue;
+        sgm_line<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, slot, item - tb->slot_base[slot][s],
+                      b.Lvol + (size_t)slot * b.capacity, buf);
+        __syncwarp();
+    }
+}
+
+template <int NPATHS>
+__global__ void __launch_bounds__(kSelThreads) kb_select(const BStream* __restrict__ st,
+                                                         const BTable* __restrict__ tb, int DP,
+                                                         float s_thr, float r_min, int lr_tol) {
+    extern __shared__ uint32_t sel_smem[];
+    __shared__ int n_wide;
+    const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
+    const BStream& b = st[s];
+    const int y = blockIdx.x - tb->row_base[s];
+    if (*b.status != 0u) {
+        for (int x = threadIdx.x; x < b.W; x += blockDim.x) {
+            b.Dz[y * b.W + x] = -1.0f;
+            b.rz[y * b.W + x] = -1.0f;
+        }
+        return;
+    }
+    select_row<NPATHS>(b.Lvol, b.capacity, b.desc, b.W, y, DP, s_thr, r_min, lr_tol, b.Dz, b.rz,
+                       nullptr, nullptr, nullptr, nullptr, sel_smem, n_wide);
+}
+
+struct SgmShape {
+    int warps;   // warps per block
+    int blocks;  // blocks per SM
+};
+const SgmShape kShapes[] = {{4, 4}, {4, 8}, {8, 2}, {8, 4}, {8, 6}, {16, 2}, {16, 3}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+}  // namespace
+
+struct tsgm_batch {
+    tsgm_params prm;  // common parameters (width/height/d_max of stream 0)
+    int ns = 0;
+    std::vector<int> W, H, D;
+    int maxW = 0, maxD = 0, sms = 152;
+    cudaStream_t user = nullptr;
+    cudaStream_t exec = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<void*> allocs;
+    BStream* h_streams = nullptr;  // pinned host copy of the stream table
+    BStream* d_streams = nullptr;
+    BTable* h_table = nullptr;
+    BTable* d_table = nullptr;
+    int* d_counter = nullptr;
+    int shape = 3;  // index into kShapes
+    cudaGraphExec_t graph = nullptr;
+    uint64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+tsgm_status bfail(tsgm_batch* b, tsgm_status s, const std::string& msg) {
+    if (b) b->err = msg;
+    return s;
+}
+
+tsgm_status bcuda(tsgm_batch* b, cudaError_t e, const char* where) {
+    return bfail(b, TSGM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+bool balloc(tsgm_batch* b, T** p, size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T) + 64) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    b->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return true;
+}
+
+// enqueue every stage of one batched step on b->exec (used for capture and for tuning)
+cudaError_t enqueue_step(tsgm_batch* b, int shape) {
+    const tsgm_params& p = b->prm;
+    cudaStream_t st = b->exec;
+    const BTable& t = *b->h_table;
+    cudaError_t e = cudaMemcpyAsync(b->d_streams, b->h_streams, sizeof(BStream) * b->ns,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    const int rows = t.row_base[b->ns];
+    kb_sanitize<<<rows, 256, 0, st>>>(b->d_streams, b->d_table);
+    kb_offsets<<<rows, 512, 0, st>>>(b->d_streams, b->d_table);
+    kb_census<<<dim3(t.tile_base[b->ns], 1, 2), dim3(kCtW, kCtH), 0, st>>>(b->d_streams, b->d_table,
+                                                                           p.census_w, p.census_h);
+    kb_cost<<<b->sms * 8, 256, 0, st>>>(b->d_streams, b->d_table, p.census_w * p.census_h - 1);
+    if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+    const SgmShape sh = kShapes[shape];
+    const int LPL = b->maxD <= 64 ? 2 : (b->maxD <= 128 ? 4 : (b->maxD <= 192 ? 6 : 8));
+    const size_t smem = (size_t)sh.warps * 2 * 32 * LPL * sizeof(uint16_t);
+    const int grid = b->sms * sh.blocks;
+#define TSGM_SGM_CASE(L, Wp)                                                                   \
+    if (LPL == L && sh.warps == Wp)                                                            \
+        kb_sgm<L, Wp><<<grid, Wp * 32, smem, st>>>(b->d_streams, b->d_table, p.n_paths, p.P1, \
+                                                   p.P2, b->d_counter);
+    TSGM_SGM_CASE(2, 4) TSGM_SGM_CASE(2, 8) TSGM_SGM_CASE(2, 16)
+    TSGM_SGM_CASE(4, 4) TSGM_SGM_CASE(4, 8) TSGM_SGM_CASE(4, 16)
+    TSGM_SGM_CASE(6, 4) TSGM_SGM_CASE(6, 8) TSGM_SGM_CASE(6, 16)
+    TSGM_SGM_CASE(8, 4) TSGM_SGM_CASE(8, 8) TSGM_SGM_CASE(8, 16)
+#undef TSGM_SGM_CASE
+    const int DP = 256;
+    const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * DP * 2;
+    const float s_thr = p.S_max * (float)p.n_paths;
+    if (p.n_paths == 8)
+        kb_select<8><<<rows, kSelThreads, sel_smem, st>>>(b->d_streams, b->d_table, DP, s_thr,
+                                                          p.r_min, p.lr_tol);
+    else
+        kb_select<4><<<rows, kSelThreads, sel_smem, st>>>(b->d_streams, b->d_table, DP, s_thr,
+                                                          p.r_min, p.lr_tol);
+    return cudaGetLastError();
+}
+
+tsgm_status capture(tsgm_batch* b) {
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->exec, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "begin capture");
+    cudaError_t e2 = enqueue_step(b, b->shape);
+    e = cudaStreamEndCapture(b->exec, &g);
+    if (e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bcuda(b, e2, "capture step");
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "end capture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bcuda(b, e, "instantiate graph");
+    return TSGM_OK;
+}
+
+tsgm_status set_io(tsgm_batch* b, const uint8_t* const* left, const uint8_t* const* right,
+                   const int16_t* const* d_lo, const int16_t* const* d_hi, float* const* D_z,
+                   float* const* r_z) {
+    if (!left || !right || !d_lo || !d_hi || !D_z || !r_z)
+        return bfail(b, TSGM_ERR_INVALID_ARG, "tsgm_batch_match: null pointer array");
+    for (int i = 0; i < b->ns; ++i) {
+        if (!left[i] || !right[i] || !d_lo[i] || !d_hi[i] || !D_z[i] || !r_z[i])
+            return bfail(b, TSGM_ERR_INVALID_ARG, "tsgm_batch_match: null pointer for stream " +
+                                                      std::to_string(i));
+        BStream& s = b->h_streams[i];
+        s.left = left[i];
+        s.right = right[i];
+        s.lo_in = d_lo[i];
+        s.hi_in = d_hi[i];
+        s.Dz = D_z[i];
+        s.rz = r_z[i];
+    }
+    return TSGM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int32_t max_labels,
+                              void* cuda_stream, tsgm_batch** out) {
+    if (!out) return TSGM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!streams || n_streams < 1 || n_streams > kMaxStreams) return TSGM_ERR_INVALID_ARG;
+    const tsgm_params& p0 = streams[0];
+    for (int i = 0; i < n_streams; ++i) {
+        const tsgm_params& p = streams[i];
+        if (p.census_w != p0.census_w || p.census_h != p0.census_h || p.n_paths != p0.n_paths ||
+            p.P1 != p0.P1 || p.P2 != p0.P2 || p.S_max != p0.S_max || p.r_min != p0.r_min ||
+            p.lr_tol != p0.lr_tol)
+            return TSGM_ERR_INVALID_ARG;  // matching parameters must be shared by the batch
+        if (p.width < 1 || p.height < 1 || p.width > 13000 || p.d_max < 0 || p.d_max > 255)
+            return TSGM_ERR_INVALID_ARG;
+        if (p.census_w * p.census_h - 1 + p.P2 > 255 || p.P1 < 0 || p.P2 < p.P1)
+            return TSGM_ERR_INVALID_ARG;
+        if (p.census_w < 1 || p.census_h < 1 || !(p.census_w & 1) || !(p.census_h & 1) ||
+            p.census_w > 15 || p.census_h > 15 || p.census_w * p.census_h - 1 > 64 ||
+            (p.n_paths != 4 && p.n_paths != 8))
+            return TSGM_ERR_INVALID_ARG;
+    }
+    tsgm_batch* b = new (std::nothrow) tsgm_batch();
+    if (!b) return TSGM_ERR_OUT_OF_MEMORY;
+    b->prm = p0;
+    b->ns = n_streams;
+    b->user = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    bool ok = cudaStreamCreateWithFlags(&b->exec, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_streams, sizeof(BStream) * n_streams) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_table, sizeof(BTable)) == cudaSuccess;
+    ok = ok && balloc(b, &b->d_streams, n_streams) && balloc(b, &b->d_table, 1) &&
+         balloc(b, &b->d_counter, 1);
+    if (ok) {
+        std::memset(b->h_streams, 0, sizeof(BStream) * n_streams);
+        std::memset(b->h_table, 0, sizeof(BTable));
+        BTable& t = *b->h_table;
+        t.ns = n_streams;
+        for (int i = 0; i < n_streams && ok; ++i) {
+            const tsgm_params& p = streams[i];
+            BStream& s = b->h_streams[i];
+            s.W = p.width;
+            s.H = p.height;
+            s.D = p.d_max + 1;
+            s.n = p.width * p.height;
+            const int lab = (max_labels > 0 && max_labels < s.D) ? max_labels : s.D;
+            s.capacity = (uint64_t)s.n * (uint64_t)((lab + 3) & ~3);
+            b->W.push_back(s.W);
+            b->H.push_back(s.H);
+            b->D.push_back(s.D);
+            b->maxW = std::max(b->maxW, s.W);
+            b->maxD = std::max(b->maxD, s.D);
+            const size_t n = (size_t)s.n;
+            ok = balloc(b, &s.lo, n) && balloc(b, &s.hi, n) && balloc(b, &s.censusL, n) &&
+                 balloc(b, &s.censusR, n) && balloc(b, &s.desc, n) && balloc(b, &s.off, n + 1) &&
+                 balloc(b, &s.rowsum, (size_t)s.H) && balloc(b, &s.rowcells, (size_t)s.H) &&
+                 balloc(b, &s.cells, 1) && balloc(b, &s.status, 1) &&
+                 balloc(b, &s.C, (size_t)s.capacity + 64) &&
+                 balloc(b, &s.Lvol, (size_t)s.capacity * p0.n_paths + 64);
+            t.row_base[i + 1] = t.row_base[i] + s.H;
+            t.tiles_x[i] = (s.W + kCtW - 1) / kCtW;
+            t.tile_base[i + 1] = t.tile_base[i] + t.tiles_x[i] * ((s.H + kCtH - 1) / kCtH);
+            t.px_base[i + 1] = t.px_base[i] + s.n;
+        }
+        // direction-major line order: every stream's horizontal lines first
+        int item = 0;
+        for (int slot = 0; slot < p0.n_paths; ++slot) {
+            for (int i = 0; i < n_streams; ++i) {
+                t.slot_base[slot][i] = item;
+                const BStream& s = b->h_streams[i];
+                item += slot <= 1 ? s.H : (slot <= 3 ? s.W : s.W + s.H - 1);
+            }
+            t.slot_base[slot][n_streams] = item;
+        }
+        t.total_lines = item;
+        ok = ok && cudaMemcpy(b->d_table, b->h_table, sizeof(BTable), cudaMemcpyHostToDevice) == cudaSuccess;
+        const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * 256 * 2;
+        if (ok && sel_smem > 48 * 1024) {
+            ok = cudaFuncSetAttribute(kb_select<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sel_smem) == cudaSuccess &&
+                 cudaFuncSetAttribute(kb_select<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sel_smem) == cudaSuccess;
+        }
+    }
+    if (!ok) {
+        cudaGetLastError();
+        tsgm_batch_destroy(b);
+        return TSGM_ERR_OUT_OF_MEMORY;
+    }
+    *out = b;
+    return TSGM_OK;
+}
+
+void tsgm_batch_destroy(tsgm_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaStreamSynchronize(b->exec);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (void* q : b->allocs) cudaFree(q);
+    if (b->h_streams) cudaFreeHost(b->h_streams);
+    if (b->h_table) cudaFreeHost(b->h_table);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->exec) cudaStreamDestroy(b->exec);
+    delete b;
+}
+
+const char* tsgm_batch_last_error(const tsgm_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+tsgm_status tsgm_batch_match(tsgm_batch* b, const uint8_t* const* left,
+                             const uint8_t* const* right, const int16_t* const* d_lo,
+                             const int16_t* const* d_hi, float* const* D_z, float* const* r_z) {
+    if (!b) return TSGM_ERR_INVALID_ARG;
+    tsgm_status s = set_io(b, left, right, d_lo, d_hi, D_z, r_z);
+    if (s != TSGM_OK) return s;
+    // the graph reads the pinned table when it runs: wait for the previous replay first
+    cudaError_t e = cudaEventSynchronize(b->ev_out);
+    if (e != cudaSuccess) return bcuda(b, e, "previous batch step");
+    if (!b->graph && (s = capture(b)) != TSGM_OK) return s;
+    if ((e = cudaEventRecord(b->ev_in, b->user)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->exec, b->ev_in, 0)) != cudaSuccess ||
+        (e = cudaGraphLaunch(b->graph, b->exec)) != cudaSuccess ||
+        (e = cudaEventRecord(b->ev_out, b->exec)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->user, b->ev_out, 0)) != cudaSuccess)
+        return bcuda(b, e, "batch step");
+    b->launches += 6;
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
+                                const uint8_t* const* right, const int16_t* const* d_lo,
+                                const int16_t* const* d_hi, float* const* D_z, float* const* r_z,
+                                int32_t reps, double* best_ms, int32_t* best_shape) {
+    if (!b) return TSGM_ERR_INVALID_ARG;
+    tsgm_status s = set_io(b, left, right, d_lo, d_hi, D_z, r_z);
+    if (s != TSGM_OK) return s;
+    if (reps < 1) reps = 3;
+    cudaError_t e = cudaEventSynchronize(b->ev_out);
+    if (e != cudaSuccess) return bcuda(b, e, "previous batch step");
+    cudaEvent_t a = nullptr, z = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&z);
+    double best = 1e30;
+    int best_i = b->shape;
+    for (int i = 0; i < kNumShapes; ++i) {
+        e = enqueue_step(b, i);  // warm-up
+        if (e != cudaSuccess) break;
+        cudaEventRecord(a, b->exec);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue_step(b, i);
+        cudaEventRecord(z, b->exec);
+        if (e == cudaSuccess) e = cudaEventSynchronize(z);
+        float ms = 0.0f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, z);
+        if (e == cudaSuccess && ms / reps < best) {
+            best = ms / reps;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    if (e != cudaSuccess) return bcuda(b, e, "autotune");
+    b->shape = best_i;
+    if ((s = capture(b)) != TSGM_OK) return s;
+    if (best_ms) *best_ms = best;
+    if (best_shape) *best_shape = best_i;
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed) {
+    if (!b || !cells) return TSGM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->exec);
+    if (e != cudaSuccess) return bcuda(b, e, "synchronize");
+    uint64_t tot = 0;
+    int32_t over = 0;
+    for (int i = 0; i < b->ns; ++i) {
+        uint32_t c = 0, st = 0;
+        if (cudaMemcpy(&c, b->h_streams[i].cells, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&st, b->h_streams[i].status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bfail(b, TSGM_ERR_CUDA, "tsgm_batch_cells: copy");
+        tot += c;
+        over += st != 0u;
+    }
+    *cells = tot;
+    if (overflowed) *overflowed = over;
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_batch_launches(tsgm_batch* b, uint64_t* n) {
+    if (!b || !n) return TSGM_ERR_INVALID_ARG;
+    *n = b->launches;
+    return TSGM_OK;
+}
+
+}  // extern "C"

@@ -7,16 +7,12 @@
 
 #include <cfloat>
 
-#include "tsgm_internal.cuh"
+#include "tsgm_kernels.cuh"
 
 namespace tsgm {
 namespace {
 
-__device__ __forceinline__ bool valid_value(float v) { return v >= 0.0f && v <= FLT_MAX; }
-
-// Storage of one pixel's window in the ragged volumes: rounded up to a multiple of 4 cells so that
-// every block starts 4-byte aligned in the uint8 volumes (32-bit loads and stores of 4 labels).
-__device__ __forceinline__ uint32_t block_cells(int w) { return (uint32_t)((w + 3) & ~3); }
+using namespace dev;
 
 // ---------------------------------------------------------------------------------------------
 // Warp scatter (Eq. 3 + homogeneous divide; z-buffer of Sec. 2.2 "disparity refinement").
@@ -87,59 +83,6 @@ __global__ void __launch_bounds__(256) k_warp_gather(const unsigned long long* _
 }
 
 // ---------------------------------------------------------------------------------------------
-// Block-wide helpers (blockDim.x a multiple of 32, at most 1024)
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* sh /* >= 32 words */) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    uint32_t t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0u;
-    if (wid == 0) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) sh[0] = t;
-    }
-    __syncthreads();
-    const uint32_t r = sh[0];
-    __syncthreads();
-    return r;
-}
-
-// Exclusive scan across the block; returns this thread's exclusive prefix and the block total.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* sh,
-                                                         uint32_t* total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    __syncthreads();
-    if (lane == 31) sh[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t t = (lane < nw) ? sh[lane] : 0u;
-        uint32_t ti = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, ti, o);
-            if (lane >= o) ti += u;
-        }
-        if (lane < nw) sh[lane] = ti - t;  // exclusive prefix of warp totals
-        if (lane == nw - 1) sh[32] = ti;   // block total
-    }
-    __syncthreads();
-    const uint32_t r = sh[wid] + inc - v;
-    *total = sh[32];
-    __syncthreads();
-    return r;
-}
-
-// ---------------------------------------------------------------------------------------------
 // Windows (Sec. 2.3): [floor(d - k sqrt(p)), ceil(d + k sqrt(p))] clipped to [0, D-1]; the
 // whole range without a valid prediction or when the interval misses the range. One block per
 // row; also writes the row's total window length.
@@ -180,38 +123,17 @@ __global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
     }
 }
 
-// Caller-supplied windows: copy them clamped into [0, D-1] with lo <= hi (so that every later
-// kernel stays inside the ragged volume whatever the input) and write the row's total length.
+// Caller-supplied windows, clamped copies and row totals (see sanitize_row).
 __global__ void __launch_bounds__(256) k_sanitize_rowsum(const int16_t* __restrict__ lo_in,
                                                          const int16_t* __restrict__ hi_in, int W,
                                                          int D, int16_t* __restrict__ lo,
                                                          int16_t* __restrict__ hi,
                                                          uint32_t* __restrict__ rowsum,
                                                          uint32_t* __restrict__ rowcells) {
-    __shared__ uint32_t sh[33];
-    const int y = blockIdx.x;
-    uint32_t acc = 0, acc_true = 0;
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const int i = y * W + x;
-        const int a = min(max((int)lo_in[i], 0), D - 1);
-        const int b = min(max((int)hi_in[i], a), D - 1);
-        lo[i] = (int16_t)a;
-        hi[i] = (int16_t)b;
-        acc_true += (uint32_t)(b - a + 1);
-        acc += block_cells(b - a + 1);
-    }
-    const uint32_t t = block_sum(acc, sh);
-    const uint32_t tt = block_sum(acc_true, sh);
-    if (threadIdx.x == 0) {
-        rowsum[y] = t;
-        rowcells[y] = tt;
-    }
+    sanitize_row(lo_in, hi_in, W, D, blockIdx.x, lo, hi, rowsum, rowcells);
 }
 
-// Offsets of the ragged volume: pixel i's block starts at off[i] = sum of the (4-aligned) block
-// sizes of the pixels before it (row-major); off[n] = storage size. One block per row: base =
-// sum of earlier row totals, then a block scan. Also writes the per-pixel descriptor
-// {off, lo | w << 16} used by the matching kernels, and (last row) the number of true cells.
+// Block starts and descriptors of the ragged volume, one block per row (see offsets_row).
 __global__ void __launch_bounds__(512) k_offsets(const int16_t* __restrict__ lo,
                                                  const int16_t* __restrict__ hi,
                                                  const uint32_t* __restrict__ rowsum,
@@ -219,37 +141,7 @@ __global__ void __launch_bounds__(512) k_offsets(const int16_t* __restrict__ lo,
                                                  int Hh, uint32_t* __restrict__ off,
                                                  uint2* __restrict__ desc,
                                                  uint32_t* __restrict__ cells_total) {
-    __shared__ uint32_t sh[33];
-    const int y = blockIdx.x;
-    uint32_t part = 0;
-    for (int r = threadIdx.x; r < y; r += blockDim.x) part += rowsum[r];
-    uint32_t base = block_sum(part, sh);
-    for (int x0 = 0; x0 < W; x0 += blockDim.x) {
-        const int x = x0 + threadIdx.x;
-        const int i = y * W + x;
-        int a = 0, w = 0;
-        if (x < W) {
-            a = lo[i];
-            w = hi[i] - a + 1;
-        }
-        const uint32_t bw = (x < W) ? block_cells(w) : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(bw, sh, &tot);
-        if (x < W) {
-            off[i] = base + ex;
-            desc[i] = make_uint2(base + ex, (uint32_t)a | ((uint32_t)w << 16));
-        }
-        base += tot;
-    }
-    if (y == Hh - 1) {
-        uint32_t c = 0;
-        for (int r = threadIdx.x; r < Hh; r += blockDim.x) c += rowcells[r];
-        c = block_sum(c, sh);
-        if (threadIdx.x == 0) {
-            off[(size_t)W * Hh] = base;
-            *cells_total = c;
-        }
-    }
+    offsets_row(lo, hi, rowsum, rowcells, W, Hh, blockIdx.x, off, desc, cells_total);
 }
 
 // ---------------------------------------------------------------------------------------------

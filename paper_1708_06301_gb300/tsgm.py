@@ -68,6 +68,17 @@ _SIGS = {
     "tsgm_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "tsgm_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_batch_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_int32,
+                                         _vp, ctypes.POINTER(_vp)]),
+    "tsgm_batch_destroy": (None, [_vp]),
+    "tsgm_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "tsgm_batch_match": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tsgm_batch_autotune": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "tsgm_batch_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "tsgm_batch_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_adjoint_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _fp,
                                             ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp,
                                             _vp, _vp, _vp]),
@@ -304,3 +315,71 @@ class Context:
         cnt = (ctypes.c_int64 * N_STAGES)()
         self._check(self.lib.tsgm_stage_times(self.h, ms, cnt), "tsgm_stage_times")
         return {STAGES[s]: (ms[s], cnt[s]) for s in range(N_STAGES)}
+
+
+class Batch:
+    """Batched matching over streams of different sizes (tsgm_batch_* of the C ABI)."""
+
+    def __init__(self, params_list, max_labels: int = 0, stream: int | None = None):
+        self.lib = load()
+        self.params = list(params_list)
+        self.n = len(self.params)
+        arr = (Params * self.n)(*self.params)
+        h = _vp()
+        s = _current_stream() if stream is None else int(stream)
+        st = self.lib.tsgm_batch_create(arr, self.n, int(max_labels), _vp(s or None), ctypes.byref(h))
+        if st != OK:
+            raise TsgmError(st, "tsgm_batch_create failed")
+        self.h = h
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self.lib.tsgm_batch_last_error(self.h)
+            raise TsgmError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    @staticmethod
+    def _arr(xs):
+        return (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+
+    def match(self, lefts, rights, los, his, Dzs, rzs):
+        self._check(self.lib.tsgm_batch_match(self.h, self._arr(lefts), self._arr(rights),
+                                              self._arr(los), self._arr(his), self._arr(Dzs),
+                                              self._arr(rzs)), "tsgm_batch_match")
+
+    def autotune(self, lefts, rights, los, his, Dzs, rzs, reps: int = 3):
+        ms = ctypes.c_double(0)
+        shape = ctypes.c_int32(0)
+        self._check(self.lib.tsgm_batch_autotune(self.h, self._arr(lefts), self._arr(rights),
+                                                 self._arr(los), self._arr(his), self._arr(Dzs),
+                                                 self._arr(rzs), int(reps), ctypes.byref(ms),
+                                                 ctypes.byref(shape)), "tsgm_batch_autotune")
+        return float(ms.value), int(shape.value)
+
+    def cells(self):
+        c = ctypes.c_uint64(0)
+        o = ctypes.c_int32(0)
+        self._check(self.lib.tsgm_batch_cells(self.h, ctypes.byref(c), ctypes.byref(o)),
+                    "tsgm_batch_cells")
+        return int(c.value), int(o.value)
+
+    def launches(self) -> int:
+        v = ctypes.c_uint64(0)
+        self._check(self.lib.tsgm_batch_launches(self.h, ctypes.byref(v)), "tsgm_batch_launches")
+        return int(v.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tsgm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
