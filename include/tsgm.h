@@ -270,6 +270,35 @@ tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed
 /* Kernels launched by this batch (graph steps count their kernels). */
 tsgm_status tsgm_batch_launches(tsgm_batch* b, uint64_t* n);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving: many camera streams each sending frames at their own rate. The per-stream state
+ * (previous D, P) stays on the device. A scheduler thread admits a frame as soon as its stream
+ * has no frame in flight and an execution slot of its image size is free (continuous batching:
+ * frames arriving while others run start on their own CUDA stream and overlap with them).
+ * Slots hold a context's scratch; they are created per image size, at least one each and more
+ * while the HBM budget allows, never more than that size has streams.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct tsgm_server tsgm_server;
+
+/* streams[i]: parameters of camera stream i (frames of a stream must have its size). */
+tsgm_status tsgm_server_create(const tsgm_params* streams, int32_t n_streams,
+                               uint64_t hbm_budget_bytes, tsgm_server** out);
+/* Finishes every submitted frame, then releases everything. */
+void tsgm_server_destroy(tsgm_server* s);
+/* Queue one frame of `stream` (host images of its size, copied at once; pose as in tsgm_frame,
+ * NULL for the stream's first frame). D_host, P_host receive the result and must stay valid until
+ * tsgm_server_wait returns for the ticket. Frames of one stream run in submission order. */
+tsgm_status tsgm_server_submit(tsgm_server* s, int32_t stream, const uint8_t* left_host,
+                               const uint8_t* right_host, const float R[9], const float t[3],
+                               const float K[9], float baseline, float* D_host, float* P_host,
+                               uint64_t* ticket);
+/* Block until the ticket's frame is done; returns its status and its latency (submit to result). */
+tsgm_status tsgm_server_wait(tsgm_server* s, uint64_t ticket, double* latency_ms);
+/* Latency percentiles over all finished frames, their number, the number of slots and the
+ * largest number of frames that were on the GPU at once. */
+tsgm_status tsgm_server_stats(tsgm_server* s, double* p50_ms, double* p99_ms, uint64_t* completed,
+                              int32_t* n_slots, uint64_t* max_in_flight);
+
 /* Disparity prediction that allocates nothing (the paper has no counterpart: this is a
  * deployment variant of tsgm_warp_predict).
  *

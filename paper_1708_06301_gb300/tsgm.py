@@ -79,6 +79,17 @@ _SIGS = {
     "tsgm_batch_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_int32)]),
     "tsgm_batch_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_server_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_uint64,
+                                          ctypes.POINTER(_vp)]),
+    "tsgm_server_destroy": (None, [_vp]),
+    "tsgm_server_submit": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _fp, _fp, _fp,
+                                          ctypes.c_float, _vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "tsgm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_adjoint_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _fp,
                                             ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp,
                                             _vp, _vp, _vp]),
@@ -370,6 +381,72 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             self.lib.tsgm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Serving loop of the C ABI (tsgm_server_*): submit frames per camera stream, wait for them."""
+
+    def __init__(self, params_list, hbm_budget_bytes: int):
+        self.lib = load()
+        self.params = list(params_list)
+        arr = (Params * len(self.params))(*self.params)
+        h = _vp()
+        st = self.lib.tsgm_server_create(arr, len(self.params), int(hbm_budget_bytes), ctypes.byref(h))
+        if st != OK:
+            raise TsgmError(st, "tsgm_server_create failed")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, stream: int, left: np.ndarray, right: np.ndarray, R, t, K, baseline,
+               D_out: np.ndarray, P_out: np.ndarray) -> int:
+        """Queue a frame; D_out/P_out (float32 numpy, the stream's size) receive the result."""
+        left = np.ascontiguousarray(left, np.uint8)
+        right = np.ascontiguousarray(right, np.uint8)
+        Ra, Rp = _host_f32(R, 9)
+        ta, tp = _host_f32(t, 3)
+        Ka, Kp = _host_f32(K, 9)
+        tk = ctypes.c_uint64(0)
+        st = self.lib.tsgm_server_submit(self.h, int(stream), left.ctypes.data, right.ctypes.data,
+                                         Rp, tp, Kp, ctypes.c_float(baseline), D_out.ctypes.data,
+                                         P_out.ctypes.data, ctypes.byref(tk))
+        if st != OK:
+            raise TsgmError(st, "tsgm_server_submit failed")
+        self._keep[int(tk.value)] = (D_out, P_out)
+        return int(tk.value)
+
+    def wait(self, ticket: int) -> float:
+        lat = ctypes.c_double(0)
+        st = self.lib.tsgm_server_wait(self.h, int(ticket), ctypes.byref(lat))
+        self._keep.pop(int(ticket), None)
+        if st != OK:
+            raise TsgmError(st, "tsgm_server_wait: frame failed")
+        return float(lat.value)
+
+    def stats(self):
+        p50, p99 = ctypes.c_double(0), ctypes.c_double(0)
+        done, fl = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        slots = ctypes.c_int32(0)
+        self.lib.tsgm_server_stats(self.h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(done),
+                                   ctypes.byref(slots), ctypes.byref(fl))
+        return dict(p50_ms=p50.value, p99_ms=p99.value, completed=int(done.value),
+                    slots=int(slots.value), max_in_flight=int(fl.value))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tsgm_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
