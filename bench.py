@@ -186,6 +186,194 @@ def run_reference(args, ws, rank):
 # GPU arm
 # ----------------------------------------------------------------------------------------------
 
+def mix_shape(i: int):
+    """Stream i of the multi-stream workloads: 640x480 D=64, 1242x375 D=128, 1920x1080 D=256."""
+    return [(640, 480, 64), (1242, 375, 128), (1920, 1080, 256)][i % 3]
+
+
+def render_mix(n_frames: int):
+    """One rendered driving-shaped sequence per image size (focal length scaled with the width)."""
+    from paper_1708_06301_gb300 import synth
+    out = {}
+    for k in range(3):
+        W, H, D = mix_shape(k)
+        out[(W, H)] = synth.make_sequence(100 + k, W, H, 721.0 * W / 1242.0, 0.54,
+                                          n_frames=n_frames, n_boxes=20, noise_sigma=2.0)
+    return out
+
+
+def bench_adjoint(dev, steps: int):
+    """Adjoint of prediction + Kalman at 1242x375 (random maps D 1-127, P 0.1-4, random 6-DoF pose
+    with |t| <= 1.5 m and angles within 3 deg): device time of forward and backward."""
+    import torch
+    from paper_1708_06301_gb300 import synth, tsgm
+    W, H = 1242, 375
+    D, P = synth.random_maps(5, W, H, d_range=(1, 127), p_range=(0.1, 4.0))
+    Dz, rz = synth.random_maps(6, W, H, d_range=(1, 127), p_range=(0.5, 4.0), invalid_frac=0.1)
+    _, t = synth.random_pose(7, max_t=1.5)
+    pose6 = np.concatenate([np.radians([1.5, -2.0, 0.7]), t.astype(np.float64)])
+    K = synth.Camera(W, H, 721.0, 0.54).K
+    b = np.float32(0.54)
+    dD, dP, dDz, drz = (torch.from_numpy(x).to(dev) for x in (D, P, Dz, rz))
+    gD = torch.randn((H, W), device=dev)
+    gP = torch.randn((H, W), device=dev)
+    oD, oP = torch.empty_like(dD), torch.empty_like(dP)
+    with tsgm.Context(tsgm.default_params(W, H), stream=torch.cuda.current_stream(dev).cuda_stream) as c:
+        for _ in range(3):
+            c.adjoint_forward(dD, dP, pose6, K, b, 0.25, 1.0, dDz, drz, oD, oP)
+            c.adjoint_backward(dD, dP, pose6, K, b, 0.25, 1.0, dDz, drz, gD, gP)
+        fwd, bwd = [], []
+        st = torch.cuda.current_stream(dev)
+        for _ in range(steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(st)
+            c.adjoint_forward(dD, dP, pose6, K, b, 0.25, 1.0, dDz, drz, oD, oP)
+            e1.record(st)
+            c.adjoint_backward(dD, dP, pose6, K, b, 0.25, 1.0, dDz, drz, gD, gP)
+            e2.record(st)
+            torch.cuda.synchronize()
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e1.elapsed_time(e2))
+    return {"workload": "1242x375 random maps, random 6-DoF pose, gradients w.r.t. pose, q, r-scale",
+            "forward_ms": float(np.median(fwd)),
+            "backward_ms_incl_host_reduction": float(np.median(bwd))}
+
+
+def bench_batched(dev, steps: int, warmup: int):
+    """32 streams (i mod 3 -> 640x480 D=64, 1242x375 D=128, 1920x1080 D=256), per-pixel windows of
+    4-24 labels around the ground truth, one graph replay per step."""
+    import torch
+    from paper_1708_06301_gb300 import synth, tsgm
+    seqs = render_mix(1)
+    NS = 32
+    params, L, R, LO, HI, DZ, RZ = [], [], [], [], [], [], []
+    px = 0
+    for i in range(NS):
+        W, H, D = mix_shape(i)
+        sq = seqs[(W, H)]
+        params.append(tsgm.default_params(W, H, d_max=D - 1))
+        gt = np.clip(np.floor(sq.gt_disp[0] + 0.5), 0, D - 1).astype(np.int64).reshape(-1)
+        n = W * H
+        w = 4 + np.floor(synth.uniform01(200 + i, np.arange(n)) * 21).astype(np.int64)
+        lo = np.clip(gt - w // 2, 0, D - w)
+        hi = lo + w - 1
+        L.append(torch.from_numpy(sq.left[0]).to(dev))
+        R.append(torch.from_numpy(sq.right[0]).to(dev))
+        LO.append(torch.from_numpy(lo.astype(np.int16).reshape(H, W)).to(dev))
+        HI.append(torch.from_numpy(hi.astype(np.int16).reshape(H, W)).to(dev))
+        DZ.append(torch.empty((H, W), dtype=torch.float32, device=dev))
+        RZ.append(torch.empty((H, W), dtype=torch.float32, device=dev))
+        px += n
+    st = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with tsgm.Batch(params, max_labels=24, stream=st.cuda_stream) as bt:
+        tune_ms, shape = bt.autotune(L, R, LO, HI, DZ, RZ, reps=2)
+        for _ in range(warmup):
+            bt.match(L, R, LO, HI, DZ, RZ)
+        torch.cuda.synchronize()
+        cells, over = bt.cells()
+        ms, sgm_ms, prof_step = [], [], []
+        l0 = bt.launches()
+        for s_ in range(steps):
+            flush.fill_(float(s_))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            bt.match(L, R, LO, HI, DZ, RZ)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        launches = bt.launches() - l0
+        for s_ in range(steps):  # aggregation kernel alone: direct launches with events around it
+            flush.fill_(float(s_))
+            torch.cuda.synchronize()
+            a_ms, z_ms = bt.profile(L, R, LO, HI, DZ, RZ)
+            sgm_ms.append(a_ms)
+            prof_step.append(z_ms)
+    step_s = float(np.mean(ms)) / 1000.0
+    sgm_s = float(np.mean(sgm_ms)) / 1000.0
+    peak, kind = peaks()
+    agg_bytes = algorithmic_sgm_bytes(cells, px)
+    # whole-step algorithmic bytes: images 2, census 16 (write+read), windows 4 read + 4 copy,
+    # descriptors 8 + offsets 4, outputs 8 per pixel; C 1 write + 1 read, S 2 per cell
+    step_bytes = 46 * px + 4 * cells
+    return {"workload": "32 streams: 11x 640x480 D=64, 11x 1242x375 D=128, 10x 1920x1080 D=256; "
+                        "windows 4-24 labels around ground truth; inputs larger than L2",
+            "px_per_step": px, "cells_per_step": cells, "overflowed_streams": over,
+            "ms_per_step": step_s * 1000.0, "gcells_per_s": cells / step_s / 1e9,
+            "frames_per_s": NS / step_s, "autotuned_shape": shape, "autotune_ms": tune_ms,
+            "kernels_per_step": launches / max(steps, 1),
+            "ms_per_step_direct_launches": float(np.mean(prof_step)),
+            "roofline_sgm": {"bound": "hbm", "achieved": agg_bytes / sgm_s / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": agg_bytes / sgm_s / 1e9 / peak,
+                             "peak_kind": kind, "avg_launch_us": sgm_s * 1e6,
+                             "algorithmic_bytes_per_launch": agg_bytes},
+            "step_hbm_frac": step_bytes / step_s / 1e9 / peak}
+
+
+def bench_serving(duration_s: float, budget_gb: float):
+    """64 camera streams (same size mix), each sending frames as a Poisson process at 10-30 Hz for
+    `duration_s` seconds; latency from submission to result, aggregate frames/s."""
+    import queue
+    from paper_1708_06301_gb300 import synth, tsgm
+    F = 6
+    seqs = render_mix(F)
+    NS = 64
+    params = []
+    for i in range(NS):
+        W, H, D = mix_shape(i)
+        params.append(tsgm.default_params(W, H, d_max=D - 1))
+    rs = synth.Stream(11, 0x5E7)
+    events = []
+    for i in range(NS):
+        rate = rs.uniform(10.0, 30.0)
+        tcur = rs.uniform(0.0, 1.0 / rate)
+        k = 0
+        while tcur < duration_s:
+            events.append((tcur, i, k))
+            k += 1
+            tcur += -np.log(max(rs.uniform(), 1e-12)) / rate
+    events.sort()
+    done_q = queue.Queue()
+    lat = []
+
+    def waiter(srv):
+        while True:
+            item = done_q.get()
+            if item is None:
+                return
+            lat.append(srv.wait(item[0]))
+
+    with tsgm.Server(params, hbm_budget_bytes=int(budget_gb * (1 << 30))) as srv:
+        th = threading.Thread(target=waiter, args=(srv,), daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        for (ta, i, k) in events:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            W, H, D = mix_shape(i)
+            sq = seqs[(W, H)]
+            f = k % F
+            if k == 0:
+                Rm, tv = None, None
+            else:
+                Rm, tv = sq.pose_between((k - 1) % F, f)
+            Dout = np.empty((H, W), np.float32)
+            Pout = np.empty((H, W), np.float32)
+            tk = srv.submit(i, sq.left[f], sq.right[f], Rm, tv, sq.K, np.float32(sq.cam.b), Dout, Pout)
+            done_q.put((tk, Dout, Pout))
+        done_q.put(None)
+        th.join()
+        t_end = time.perf_counter() - t0
+        st = srv.stats()
+    return {"workload": "64 camera streams (11/11/10 mix x2: 640x480 D=64, 1242x375 D=128, "
+                        "1920x1080 D=256), Poisson frame arrivals at 10-30 Hz per stream",
+            "duration_s": duration_s, "frames": len(events), "frames_per_s": len(events) / t_end,
+            "offered_frames_per_s": len(events) / duration_s,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "slots": st["slots"],
+            "max_in_flight": st["max_in_flight"], "hbm_budget_gb": budget_gb}
+
+
 def algorithmic_sgm_bytes(cells: int, px: int) -> int:
     """Bytes the aggregation kernel must move once: the ragged cost C read (1 B/cell), the
     aggregated S written (2 B/cell), window bounds and offsets read (8 B/px)."""
@@ -334,6 +522,11 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     achieved = bytes_per_launch / agg_avg_s / 1e9
     peak, peak_kind = peaks()
 
+    extra = {}
+    if not args.skip_forms:
+        extra["adjoint"] = bench_adjoint(dev, 10)
+        extra["batched"] = bench_batched(dev, max(3, args.steps // 2), 2)
+        extra["serving"] = bench_serving(args.serving_seconds, 64.0)
     cpu_s = sum(oracle_frames(seq, list(range(N_FRAMES))))
     line = {
         "metric": METRIC,
@@ -372,6 +565,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
                 "h2d_bytes_per_step": N_FRAMES * 2 * n,
                 "d2h_bytes_per_step": N_FRAMES * 2 * 4 * n},
         "gpu_launches": launches,
+        **extra,
         "wall_s_timed_region": wall_red,
         "clocks": clocks,
     }
@@ -386,6 +580,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true",
                     help="run only the reduced-window steps (for profiler captures)")
+    ap.add_argument("--skip-forms", action="store_true",
+                    help="skip the adjoint, batched and serving measurements")
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -267,6 +267,13 @@ tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
  * lack of storage. Synchronises. */
 tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed);
 
+/* One step run with direct launches instead of the graph, timed with CUDA events on the batch's
+ * stream: device time of the path aggregation kernel and of the whole step (ms). Synchronises. */
+tsgm_status tsgm_batch_profile(tsgm_batch* b, const uint8_t* const* left,
+                               const uint8_t* const* right, const int16_t* const* d_lo,
+                               const int16_t* const* d_hi, float* const* D_z, float* const* r_z,
+                               float* sgm_ms, float* step_ms);
+
 /* Kernels launched by this batch (graph steps count their kernels). */
 tsgm_status tsgm_batch_launches(tsgm_batch* b, uint64_t* n);
 

@@ -180,6 +180,7 @@ struct tsgm_batch {
     int* d_counter = nullptr;
     int shape = 3;  // index into kShapes
     cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev_sgm_a = nullptr, ev_sgm_b = nullptr;  // around the aggregation (profiled steps)
     uint64_t launches = 0;
     std::string err;
 };
@@ -208,7 +209,7 @@ bool balloc(tsgm_batch* b, T** p, size_t count) {
 }
 
 // enqueue every stage of one batched step on b->exec (used for capture and for tuning)
-cudaError_t enqueue_step(tsgm_batch* b, int shape) {
+cudaError_t enqueue_step(tsgm_batch* b, int shape, bool timed = false) {
     const tsgm_params& p = b->prm;
     cudaStream_t st = b->exec;
     const BTable& t = *b->h_table;
@@ -222,6 +223,7 @@ cudaError_t enqueue_step(tsgm_batch* b, int shape) {
                                                                            p.census_w, p.census_h);
     kb_cost<<<b->sms * 8, 256, 0, st>>>(b->d_streams, b->d_table, p.census_w * p.census_h - 1);
     if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecord(b->ev_sgm_a, st)) != cudaSuccess) return e;
     const SgmShape sh = kShapes[shape];
     const int LPL = b->maxD <= 64 ? 2 : (b->maxD <= 128 ? 4 : (b->maxD <= 192 ? 6 : 8));
     const size_t smem = (size_t)sh.warps * 2 * 32 * LPL * sizeof(uint16_t);
@@ -235,6 +237,7 @@ cudaError_t enqueue_step(tsgm_batch* b, int shape) {
     TSGM_SGM_CASE(6, 4) TSGM_SGM_CASE(6, 8) TSGM_SGM_CASE(6, 16)
     TSGM_SGM_CASE(8, 4) TSGM_SGM_CASE(8, 8) TSGM_SGM_CASE(8, 16)
 #undef TSGM_SGM_CASE
+    if (timed && (e = cudaEventRecord(b->ev_sgm_b, st)) != cudaSuccess) return e;
     const int DP = 256;
     const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * DP * 2;
     const float s_thr = p.S_max * (float)p.n_paths;
@@ -324,6 +327,7 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
     bool ok = cudaStreamCreateWithFlags(&b->exec, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreate(&b->ev_sgm_a) == cudaSuccess && cudaEventCreate(&b->ev_sgm_b) == cudaSuccess &&
               cudaMallocHost((void**)&b->h_streams, sizeof(BStream) * n_streams) == cudaSuccess &&
               cudaMallocHost((void**)&b->h_table, sizeof(BTable)) == cudaSuccess;
     ok = ok && balloc(b, &b->d_streams, n_streams) && balloc(b, &b->d_table, 1) &&
@@ -397,6 +401,8 @@ void tsgm_batch_destroy(tsgm_batch* b) {
     if (b->h_table) cudaFreeHost(b->h_table);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_sgm_a) cudaEventDestroy(b->ev_sgm_a);
+    if (b->ev_sgm_b) cudaEventDestroy(b->ev_sgm_b);
     if (b->exec) cudaStreamDestroy(b->exec);
     delete b;
 }
@@ -478,6 +484,30 @@ tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed
     }
     *cells = tot;
     if (overflowed) *overflowed = over;
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_batch_profile(tsgm_batch* b, const uint8_t* const* left,
+                               const uint8_t* const* right, const int16_t* const* d_lo,
+                               const int16_t* const* d_hi, float* const* D_z, float* const* r_z,
+                               float* sgm_ms, float* step_ms) {
+    if (!b || !sgm_ms || !step_ms) return TSGM_ERR_INVALID_ARG;
+    tsgm_status s = set_io(b, left, right, d_lo, d_hi, D_z, r_z);
+    if (s != TSGM_OK) return s;
+    cudaError_t e = cudaEventSynchronize(b->ev_out);
+    cudaEvent_t a = nullptr, z = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&z);
+    if (e == cudaSuccess) e = cudaEventRecord(a, b->exec);
+    if (e == cudaSuccess) e = enqueue_step(b, b->shape, true);
+    if (e == cudaSuccess) e = cudaEventRecord(z, b->exec);
+    if (e == cudaSuccess) e = cudaEventSynchronize(z);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(sgm_ms, b->ev_sgm_a, b->ev_sgm_b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(step_ms, a, z);
+    if (a) cudaEventDestroy(a);
+    if (z) cudaEventDestroy(z);
+    if (e != cudaSuccess) return bcuda(b, e, "tsgm_batch_profile");
+    b->launches += 6;
     return TSGM_OK;
 }
 

@@ -213,6 +213,14 @@ class Sequence:
     R: list             # float32 (3,3) relative pose frame k-1 -> k, index k (R[0] = identity)
     t: list             # float32 (3,)
     scene: Scene
+    R_wc: list = None   # camera-to-world rotation of every frame
+    c_w: list = None    # camera centre of every frame
+
+    def pose_between(self, i: int, j: int):
+        """Relative pose (R, t) mapping frame i camera coordinates to frame j's (Eq. 2 form)."""
+        R = self.R_wc[j].T @ self.R_wc[i]
+        t = self.R_wc[j].T @ (self.c_w[i] - self.c_w[j])
+        return R.astype(np.float32), t.astype(np.float32)
 
     @property
     def K(self) -> np.ndarray:
@@ -270,7 +278,7 @@ def make_sequence(seed: int, W: int, H: int, f: float, b: float, n_frames: int, 
             trel = R_wc[k].T @ (c_w[k - 1] - c_w[k])
             Rs.append(Rrel.astype(np.float32))
             ts.append(trel.astype(np.float32))
-    return Sequence(cam, left, right, gt, Rs, ts, scene)
+    return Sequence(cam, left, right, gt, Rs, ts, scene, R_wc, c_w)
 
 
 # ----------------------------------------------------------------------------------------------

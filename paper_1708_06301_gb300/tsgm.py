@@ -79,6 +79,9 @@ _SIGS = {
     "tsgm_batch_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_int32)]),
     "tsgm_batch_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_batch_profile": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                          ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float)]),
     "tsgm_server_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_uint64,
                                           ctypes.POINTER(_vp)]),
     "tsgm_server_destroy": (None, [_vp]),
@@ -377,6 +380,15 @@ class Batch:
         v = ctypes.c_uint64(0)
         self._check(self.lib.tsgm_batch_launches(self.h, ctypes.byref(v)), "tsgm_batch_launches")
         return int(v.value)
+
+    def profile(self, lefts, rights, los, his, Dzs, rzs):
+        """(aggregation ms, whole step ms) of one step with direct launches."""
+        a, z = ctypes.c_float(0), ctypes.c_float(0)
+        self._check(self.lib.tsgm_batch_profile(self.h, self._arr(lefts), self._arr(rights),
+                                                self._arr(los), self._arr(his), self._arr(Dzs),
+                                                self._arr(rzs), ctypes.byref(a), ctypes.byref(z)),
+                    "tsgm_batch_profile")
+        return float(a.value), float(z.value)
 
     def close(self):
         if getattr(self, "h", None):
