@@ -35,7 +35,8 @@ if ROOT not in sys.path:
 METRIC = "reduced-range SGM Gcells/s and fps vs full-range on same GB300; % HBM roofline"
 WORKLOAD = ("kitti-shaped synthetic sequence: 10 frames 1242x375 uint8 stereo, f=721, b=0.54, "
             "ground + 20 boxes, noise sigma 2, census 9x7, 8 paths, P1=8, P2=32, D=128; frame 1 "
-            "full range, frames 2-10 +-3 sigma windows")
+            "full range, frames 2-10 +-3 sigma windows around the warped prediction with its "
+            "one-pixel gaps filled (Eq. 7-8, gamma_f = 1 px)")
 N_FRAMES = 10
 L2_FLUSH_BYTES = 256 << 20
 
@@ -144,7 +145,7 @@ def oracle_frames(seq, frames):
     tracker that restarts (no prediction) whenever frame 0 comes up."""
     import oracle
     oracle.build()
-    prm = oracle.Params(1242, 375, d_max=127, census_w=9, census_h=7, n_paths=8)
+    prm = oracle.Params(1242, 375, d_max=127, census_w=9, census_h=7, n_paths=8, fill_gaps=True)
     tr = oracle.Tracker(prm)
     b = np.float32(seq.cam.b)
     times = []
@@ -410,8 +411,9 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     def make(flags):
         return tsgm.Context(tsgm.default_params(W, H, flags=flags), stream=stream.cuda_stream)
 
-    ctx = make(0)
+    ctx = make(tsgm.FLAG_FILL_GAPS)
     ctx_full = make(tsgm.FLAG_FULL_RANGE)
+    ctx_plain = make(0)  # the prediction without gap filling, for comparison
     Dout = torch.empty((H, W), dtype=torch.float32, device=dev)
     Pout = torch.empty_like(Dout)
 
@@ -443,6 +445,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
         return
     cells_red, bad_red = characterise(ctx)
     cells_full, bad_full = characterise(ctx_full)
+    cells_plain, bad_plain = characterise(ctx_plain)
 
     def timed(c, K_steps, W_steps, profile):
         for _ in range(W_steps):
@@ -477,6 +480,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     t_full, _, _, stages_full = timed(ctx_full, max(1, args.steps // 2), max(3, args.warmup // 2),
                                       profile=True)
     k_full = max(1, args.steps // 2)
+    t_plain, _, _, stages_plain = timed(ctx_plain, k_full, 3, profile=True)
 
     # end to end through the host-buffer entry point (pinned host memory)
     hl = [torch.from_numpy(x).pin_memory() for x in seq.left]
@@ -549,6 +553,9 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
                        "ms_per_step": t_full_max / k_full,
                        "ms_sgm_stages_per_step": ms_sgm_full},
         "speedup_vs_full_range": fps / fps_full,
+        "without_gap_fill": {"fps": N_FRAMES * k_full / (t_plain / 1000.0),
+                             "search_space_frac": [c / (n * 128) for c in cells_plain],
+                             "bad3px_updated": bad_plain},
         "search_space_frac": [c / (n * 128) for c in cells_red],
         "bad3px": {"reduced_updated": bad_red, "full_range_updated": bad_full},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},

@@ -56,6 +56,8 @@ typedef enum {
                                         the last tsgm_match into context buffers (tsgm_inspect) */
 #define TSGM_FLAG_FULL_RANGE 2u      /* tsgm_frame ignores the prediction when choosing windows:
                                         plain full-range SGM every frame (still Kalman-updated) */
+#define TSGM_FLAG_FILL_GAPS 4u       /* tsgm_frame fills one-pixel gaps of the prediction
+                                        (Sec. 2.2, Eq. 7-8) before choosing the windows */
 
 typedef struct {
     int32_t width, height;       /* image size, 1 <= width <= 13000, 1 <= height */
@@ -69,10 +71,11 @@ typedef struct {
     float r_min;                 /* floor of the matching variance r, px^2 */
     int32_t lr_tol;              /* left-right check tolerance in px (Sec. 2.4) */
     uint32_t flags;              /* TSGM_FLAG_* */
+    float gamma_f;               /* similarity threshold of the gap filling (Eq. 8), px */
 } tsgm_params;
 
 /* Fill *p with the defaults: d_max 127, census 9x7, 8 paths, P1 8, P2 32, sigma_mult 3,
- * q 0.25, S_max 10, r_min 0.5, lr_tol 1, flags 0. */
+ * q 0.25, S_max 10, r_min 0.5, lr_tol 1, flags 0, gamma_f 1. */
 void tsgm_default_params(tsgm_params* p, int32_t width, int32_t height);
 
 /* Create a context. `cuda_stream` is the cudaStream_t every call of the context is enqueued on
@@ -104,6 +107,12 @@ tsgm_status tsgm_build_H(const float R[9], const float t[3], const float K[9], f
 tsgm_status tsgm_warp_predict(tsgm_ctx* ctx, const float* prev_D, const float* prev_P,
                               const float R[9], const float t[3], const float K[9],
                               float baseline, float* pred_D, float* pred_P);
+
+/* Gap filling of a prediction (Sec. 2.2, Eq. 7-8), in place: an invalid pixel whose two
+ * horizontal neighbours are valid with |d_l - d_r| < gamma_f takes their mean disparity and mean
+ * variance; then the same with the vertical neighbours on the horizontally filled map. Each pass
+ * reads the map as it was before the pass. Uses the context's D_z/r_z buffers as scratch. */
+tsgm_status tsgm_fill_gaps(tsgm_ctx* ctx, float* pred_D, float* pred_P);
 
 /* Reduced search space (Sec. 2.3): d_lo = max(0, floor(d - k sqrt(p))), d_hi = min(d_max,
  * ceil(d + k sqrt(p))) with k = sigma_mult, binary32; the whole range [0, d_max] where the

@@ -72,6 +72,8 @@ class Params:
     S_max: float = 10.0        # Sec. 2.3, Eq. 9 threshold per path
     r_min: float = 0.5
     lr_tol: int = 1
+    fill_gaps: bool = False    # Sec. 2.2, Eq. 7-8 on the prediction
+    gamma_f: float = 1.0       # Eq. 8 similarity threshold (value not given)
 
     @property
     def D(self) -> int:
@@ -112,6 +114,16 @@ def warp_predict(Dprev, Pprev, H32, cx: float, cy: float, q: float):
     lib.oracle_warp_predict(W, Hh, _p(Dprev), _p(Pprev), _p(Hm), ctypes.c_float(cx),
                             ctypes.c_float(cy), ctypes.c_float(q), _p(Dp), _p(Pp), _p(win))
     return Dp, Pp, win
+
+
+def fill_gaps(Dp, Pp, gamma_f: float):
+    """Eq. 7-8: horizontal then vertical one-pixel gap filling of a prediction (copies)."""
+    lib = _load()
+    Hh, W = Dp.shape
+    D = np.array(Dp, dtype=np.float32, copy=True)
+    P = np.array(Pp, dtype=np.float32, copy=True)
+    lib.oracle_fill_gaps(W, Hh, ctypes.c_float(gamma_f), _p(D), _p(P))
+    return D, P
 
 
 def windows(Dp, Pp, D: int, sigma_mult: float):
@@ -259,6 +271,8 @@ class Tracker:
             Dp, Pp, win = warp_predict(self.D, self.P, H32, np.float32(cx), np.float32(cy), prm.q)
             out["winner"] = win
             out["H32"] = H32
+            if prm.fill_gaps:
+                Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)
         lo, hi, off, n_cells = windows(Dp, Pp, prm.D, prm.sigma_mult)
         m = match(left, right, lo, hi, prm, keep=True)
         D, P = kalman(Dp, Pp, m["Dz"], m["rz"])

@@ -131,6 +131,47 @@ void oracle_warp_predict(int W, int Hh, const float* Dprev, const float* Pprev, 
 }
 
 // ------------------------------------------------------------------------------------------
+// Sec. 2.2, Eq. 7-8: filling the gaps that forward motion leaves in the prediction ("zooming").
+// An invalid predicted pixel whose two horizontal neighbours are valid and similar,
+// |d_{i-1} - d_{i+1}| < gamma_f (f_s of Eq. 8), takes their mean (Eq. 7); then the same with the
+// vertical neighbours on the horizontally filled map. Each pass reads the map as it was before
+// that pass (a pixel filled in a pass does not serve as a neighbour in the same pass). The variance
+// of a filled pixel is the mean of its two neighbours' variances. In place on D, P.
+// ------------------------------------------------------------------------------------------
+void oracle_fill_gaps(int W, int Hh, float gamma_f, float* D, float* P) {
+    const int n = W * Hh;
+    std::vector<float> d0(D, D + n), p0(P, P + n);
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int y = 0; y < Hh; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int i = y * W + x;
+                if (finite_nonneg(d0[i]) && finite_nonneg(p0[i])) continue;
+                int a, b;
+                if (pass == 0) {
+                    if (x == 0 || x == W - 1) continue;
+                    a = i - 1;
+                    b = i + 1;
+                } else {
+                    if (y == 0 || y == Hh - 1) continue;
+                    a = i - W;
+                    b = i + W;
+                }
+                if (!(finite_nonneg(d0[a]) && finite_nonneg(p0[a]) && finite_nonneg(d0[b]) &&
+                      finite_nonneg(p0[b])))
+                    continue;
+                const float diff = std::fabs(d0[a] - d0[b]);
+                if (!(diff < gamma_f)) continue;
+                const float ds = d0[a] + d0[b];
+                const float ps = p0[a] + p0[b];
+                D[i] = ds * 0.5f;
+                P[i] = ps * 0.5f;
+            }
+        std::copy(D, D + n, d0.begin());
+        std::copy(P, P + n, p0.begin());
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Sec. 2.3: reduced search interval [d - 3 sqrt(p), d + 3 sqrt(p)] (multiplier k = sigma_mult),
 // rounded outwards to integers and clipped to [0, D-1]. A pixel without a valid prediction
 // (d < 0, p < 0, NaN or inf), or whose interval misses [0, D-1], is searched over the whole

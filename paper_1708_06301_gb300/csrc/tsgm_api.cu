@@ -83,6 +83,10 @@ tsgm_status check_params(const tsgm_params* p, std::string& why) {
         why = "width * height * (d_max + 1) must stay below 2^32 cells";
         return TSGM_ERR_INVALID_ARG;
     }
+    if (!(p->gamma_f >= 0.0f) || !std::isfinite(p->gamma_f)) {
+        why = "gamma_f must be finite and >= 0";
+        return TSGM_ERR_INVALID_ARG;
+    }
     if (!(p->sigma_mult >= 0.0f) || !(p->q >= 0.0f) || !(p->S_max >= 0.0f) || !(p->r_min >= 0.0f) ||
         p->lr_tol < 0 || !std::isfinite(p->sigma_mult) || !std::isfinite(p->q) ||
         !std::isfinite(p->S_max) || !std::isfinite(p->r_min)) {
@@ -182,6 +186,17 @@ tsgm_status warp_stage(tsgm_ctx* ctx, const float* prevD, const float* prevP, co
     return TSGM_OK;
 }
 
+// Eq. 7-8, in place on (D, P): horizontal pass into the D_z/r_z scratch, vertical pass back.
+tsgm_status fill_gaps_stage(tsgm_ctx* ctx, float* D, float* P) {
+    stage_begin(ctx, TSGM_STAGE_WARP);
+    TSGM_LAUNCH(launch_fill_gaps(D, P, ctx->W, ctx->H, ctx->prm.gamma_f, 0, ctx->Dz, ctx->rz, ctx->stream),
+                "fill gaps");
+    TSGM_LAUNCH(launch_fill_gaps(ctx->Dz, ctx->rz, ctx->W, ctx->H, ctx->prm.gamma_f, 1, D, P, ctx->stream),
+                "fill gaps");
+    stage_end(ctx, TSGM_STAGE_WARP);
+    return TSGM_OK;
+}
+
 tsgm_status windows_stage(tsgm_ctx* ctx, const float* pD, const float* pP, int16_t* lo,
                           int16_t* hi) {
     stage_begin(ctx, TSGM_STAGE_WINDOWS);
@@ -247,6 +262,7 @@ void tsgm_default_params(tsgm_params* p, int32_t width, int32_t height) {
     p->r_min = 0.5f;
     p->lr_tol = 1;
     p->flags = 0;
+    p->gamma_f = 1.0f;
 }
 
 tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out) {
@@ -350,6 +366,14 @@ tsgm_status tsgm_warp_predict(tsgm_ctx* ctx, const float* prev_D, const float* p
     return warp_stage(ctx, prev_D, prev_P, R, t, K, baseline, pred_D, pred_P);
 }
 
+tsgm_status tsgm_fill_gaps(tsgm_ctx* ctx, float* pred_D, float* pred_P) {
+    if (!ctx) return TSGM_ERR_INVALID_ARG;
+    if (!pred_D || !pred_P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_fill_gaps: null pointer");
+    if (pred_D == ctx->Dz || pred_P == ctx->rz || pred_D == ctx->rz || pred_P == ctx->Dz)
+        return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_fill_gaps: maps alias the context scratch");
+    return fill_gaps_stage(ctx, pred_D, pred_P);
+}
+
 tsgm_status tsgm_windows(tsgm_ctx* ctx, const float* pred_D, const float* pred_P, int16_t* d_lo,
                          int16_t* d_hi, uint64_t* n_cells_host) {
     if (!ctx) return TSGM_ERR_INVALID_ARG;
@@ -399,6 +423,7 @@ tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
         return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: pose required after the first frame");
     if (ctx->has_prev) {
         TSGM_TRY(warp_stage(ctx, ctx->stateD, ctx->stateP, R, t, K, baseline, ctx->predD, ctx->predP));
+        if (ctx->prm.flags & TSGM_FLAG_FILL_GAPS) TSGM_TRY(fill_gaps_stage(ctx, ctx->predD, ctx->predP));
     } else {
         TSGM_LAUNCH(launch_fill(ctx->predD, -1.0f, ctx->n, ctx->stream), "fill");
         TSGM_LAUNCH(launch_fill(ctx->predP, -1.0f, ctx->n, ctx->stream), "fill");

@@ -180,6 +180,35 @@ __global__ void __launch_bounds__(256) k_kalman(const float* __restrict__ Dp,
     }
 }
 
+// Gap filling (Eq. 7-8), one pass: horizontal (vertical == 0) or vertical neighbours, reading
+// the input maps and writing the output maps (distinct buffers).
+__global__ void __launch_bounds__(256) k_fill_gaps(const float* __restrict__ Din,
+                                                   const float* __restrict__ Pin, int W, int Hh,
+                                                   float gamma_f, int vertical,
+                                                   float* __restrict__ Dout,
+                                                   float* __restrict__ Pout) {
+    const int n = W * Hh;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float d = Din[i], p = Pin[i];
+        if (!(valid_value(d) && valid_value(p))) {
+            const int y = i / W, x = i - y * W;
+            const bool inner = vertical ? (y > 0 && y < Hh - 1) : (x > 0 && x < W - 1);
+            if (inner) {
+                const int a = vertical ? i - W : i - 1;
+                const int b = vertical ? i + W : i + 1;
+                const float da = Din[a], db = Din[b], pa = Pin[a], pb = Pin[b];
+                if (valid_value(da) && valid_value(pa) && valid_value(db) && valid_value(pb) &&
+                    fabsf(__fsub_rn(da, db)) < gamma_f) {
+                    d = __fmul_rn(__fadd_rn(da, db), 0.5f);
+                    p = __fmul_rn(__fadd_rn(pa, pb), 0.5f);
+                }
+            }
+        }
+        Dout[i] = d;
+        Pout[i] = p;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_fill(float* __restrict__ a, float v, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
 }
@@ -228,6 +257,12 @@ cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t*
                            const uint32_t* rowcells, int W, int Hh, uint32_t* off, uint2* desc,
                            uint32_t* cells_total, cudaStream_t st) {
     k_offsets<<<Hh, 512, 0, st>>>(lo, hi, rowsum, rowcells, W, Hh, off, desc, cells_total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_gaps(const float* Din, const float* Pin, int W, int Hh, float gamma_f,
+                             int vertical, float* Dout, float* Pout, cudaStream_t st) {
+    k_fill_gaps<<<grid_for(W * Hh, 256), 256, 0, st>>>(Din, Pin, W, Hh, gamma_f, vertical, Dout, Pout);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "tsgm.h")
 OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_UNIMPLEMENTED = range(7)
 FLAG_KEEP_INTERNALS = 1
 FLAG_FULL_RANGE = 2
+FLAG_FILL_GAPS = 4
 N_STAGES = 8
 STAGES = ["warp", "windows", "census", "cost", "sgm", "select", "kalman", "offsets"]
 BUF = dict(census_l=0, census_r=1, offsets=2, cost=3, S=4, dstar=5, dright=6, lr_valid=7,
@@ -37,7 +38,8 @@ class Params(ctypes.Structure):
                 ("census_w", ctypes.c_int32), ("census_h", ctypes.c_int32),
                 ("n_paths", ctypes.c_int32), ("P1", ctypes.c_int32), ("P2", ctypes.c_int32),
                 ("sigma_mult", ctypes.c_float), ("q", ctypes.c_float), ("S_max", ctypes.c_float),
-                ("r_min", ctypes.c_float), ("lr_tol", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("r_min", ctypes.c_float), ("lr_tol", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("gamma_f", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -64,6 +66,7 @@ _SIGS = {
     "tsgm_state_export": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32)]),
     "tsgm_state_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
     "tsgm_census": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tsgm_fill_gaps": (ctypes.c_int, [_vp, _vp, _vp]),
     "tsgm_inspect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64]),
     "tsgm_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -284,6 +287,9 @@ class Context:
         P = np.ascontiguousarray(P, np.float32)
         self._check(self.lib.tsgm_state_import(self.h, D.ctypes.data, P.ctypes.data, int(has_prev)),
                     "tsgm_state_import")
+
+    def fill_gaps(self, pred_D, pred_P):
+        self._check(self.lib.tsgm_fill_gaps(self.h, _ptr(pred_D), _ptr(pred_P)), "tsgm_fill_gaps")
 
     def census(self, img, codes):
         self._check(self.lib.tsgm_census(self.h, _ptr(img), _ptr(codes)), "tsgm_census")

@@ -305,3 +305,40 @@ def test_errors_are_status_codes(tsgm):
                       np.eye(3), np.zeros(3), synth.Camera(64, 32, 721.0, 0.54).K, f32(0.0), D,
                       empty((32, 64), np.float32))
         assert e.value.status == tsgm.ERR_INVALID_ARG
+
+
+# ----------------------------------------------------------------------------------------------
+# gap filling of the prediction (Sec. 2.2, Eq. 7-8)
+# ----------------------------------------------------------------------------------------------
+
+def test_fill_gaps_bitexact(tsgm):
+    """Forward motion opens one-pixel gaps in a warped map; the GPU fill equals the oracle's."""
+    W, H = 1242, 375
+    D, P = synth.random_maps(41, W, H, d_range=(20, 40), invalid_frac=0.05)
+    K = synth.Camera(W, H, 721.0, 0.54).K
+    b = f32(0.54)
+    R, t = np.eye(3, dtype=np.float32), np.array([0, 0, -1.0], np.float32)
+    with make_ctx(tsgm, W, H, d_max=127, gamma_f=1.5) as ctx:
+        pD, pP = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.warp_predict(dev(D), dev(P), R, t, K, b, pD, pP)
+        Dw, Pw = host(pD, np.float32), host(pP, np.float32)
+        ctx.fill_gaps(pD, pP)
+        Dg, Pg = host(pD, np.float32), host(pP, np.float32)
+    Do, Po = oracle.fill_gaps(Dw, Pw, 1.5)
+    assert np.array_equal(Dg, Do) and np.array_equal(Pg, Po)
+    assert (Do >= 0).sum() > (Dw >= 0).sum()  # something was filled
+
+
+@pytest.mark.parametrize("slow_case", [False, pytest.param(True, marks=pytest.mark.slow)])
+def test_frames_with_gap_filling(tsgm, slow_case):
+    if slow_case:
+        seq, n, dm, cw, ch, npaths = synth.kitti_like(2, n_frames=3), 3, 127, 9, 7, 8
+    else:
+        seq, n, dm, cw, ch, npaths = synth.small_pair(1), 2, 63, 5, 5, 4
+    W, H = seq.cam.W, seq.cam.H
+    g = run_sequence(tsgm, seq, n, dm, cw, ch, npaths, flags=1 | 4)
+    tr = oracle.Tracker(oparams(W, H, d_max=dm, cw=cw, ch=ch, n_paths=npaths, fill_gaps=True))
+    for k in range(n):
+        o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
+        assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
+        assert_maps(g[k]["D"], g[k]["P"], o["D"], o["P"])

@@ -565,3 +565,39 @@ def test_pipeline_small_pair_reduced_vs_full():
         return float(np.mean((d < 0) | (np.abs(d - gt) > 3)))
 
     assert bad(o["D"]) <= bad(Dz_full)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. 2.2, Eq. 7-8: gap filling
+# ----------------------------------------------------------------------------------------------
+
+def test_fill_gaps_hand_cases():
+    I = -1.0
+    D = np.array([[5, I, 5.5, I, 9, I, I, 3],
+                  [1, 1, 1, 1, 1, 1, 1, 1],
+                  [2, 2, 2, I, 2, 2, 2, 2]], np.float32)
+    P = np.where(D >= 0, 1.0, -1.0).astype(np.float32)
+    P[0, 0], P[0, 2] = 2.0, 4.0
+    Df, Pf = oracle.fill_gaps(D, P, 1.0)
+    assert Df[0, 1] == 5.25 and Pf[0, 1] == 3.0        # similar neighbours: mean (Eq. 7)
+    assert Df[0, 3] == -1                              # |5.5 - 9| >= gamma_f (Eq. 8): invalid
+    assert Df[0, 5] == -1 and Df[0, 6] == -1           # two-pixel gap: no immediate pair
+    assert Df[2, 3] == 2.0 and Pf[2, 3] == 1.0
+    # vertical pass
+    D2 = np.array([[4, 4, 4], [I, I, I], [4.5, 9, 4.2]], np.float32)
+    P2 = np.where(D2 >= 0, 1.0, -1.0).astype(np.float32)
+    Df2, _ = oracle.fill_gaps(D2, P2, 1.0)
+    assert Df2[1, 0] == 4.25
+    assert Df2[1, 1] == -1                             # |4 - 9| >= gamma_f
+    assert Df2[1, 2] == np.float32((np.float32(4) + np.float32(4.2)) * np.float32(0.5))
+
+
+def test_fill_gaps_horizontal_pass_comes_first():
+    """(1, 1) has dissimilar horizontal neighbours (0 and 20) and an invalid upper neighbour that
+    only the horizontal pass fills: it is filled iff the horizontal pass runs before the vertical
+    one (Sec. 2.2 describes the horizontal filling, then 'the same approach' vertically)."""
+    I = -1.0
+    D = np.array([[3, I, 3], [0, I, 20], [3, 3, 3]], np.float32)
+    P = np.where(D >= 0, 1.0, -1.0).astype(np.float32)
+    Df, _ = oracle.fill_gaps(D, P, 1.0)
+    assert Df[0, 1] == 3 and Df[1, 1] == 3
