@@ -173,9 +173,9 @@ typedef enum {
     TSGM_BUF_CENSUS_L = 0,  /* uint64 [n]     census of the left image (last match)     */
     TSGM_BUF_CENSUS_R = 1,  /* uint64 [n]     census of the right image                 */
     TSGM_BUF_OFFSETS = 2,   /* uint32 [n + 1] start of each pixel's block in the ragged volume:
-                               exclusive scan of the window lengths rounded up to even; [n] is
-                               the storage size. Pixel i's cell j (disparity d_lo + j) is at
-                               offsets[i] + j.                                              */
+                               exclusive scan of the window lengths rounded up to a multiple
+                               of 4; [n] is the storage size. Pixel i's cell j (disparity
+                               d_lo + j) is at offsets[i] + j.                              */
     TSGM_BUF_COST = 3,      /* uint8  [storage] ragged matching cost                     */
     TSGM_BUF_S = 4,         /* uint16 [storage] aggregated cost S = sum of path costs    */
     TSGM_BUF_DSTAR = 5,     /* int16  [n]     winner-takes-all disparity (KEEP_INTERNALS) */
@@ -186,7 +186,11 @@ typedef enum {
     TSGM_BUF_WINDOWS_LO = 9,  /* int16 [n]    windows of the last tsgm_frame              */
     TSGM_BUF_WINDOWS_HI = 10,
     TSGM_BUF_PRED_D = 11,   /* float [n]      prediction of the last tsgm_frame            */
-    TSGM_BUF_PRED_P = 12
+    TSGM_BUF_PRED_P = 12,
+    TSGM_BUF_COUNTS = 13    /* uint32 [2]     of the last match: [0] true window cells, [1] lanes
+                                              that walked one SGM path line (8, 16 or 32: the
+                                              work layout chosen from the windows; results do
+                                              not depend on it)                              */
 } tsgm_buffer;
 
 /* Copy an internal buffer (device to device, on the context stream) into dst. `count` is the

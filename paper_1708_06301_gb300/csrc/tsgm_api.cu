@@ -226,8 +226,9 @@ tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* righ
     stage_end(ctx, TSGM_STAGE_COST);
     stage_begin(ctx, TSGM_STAGE_SGM);
     TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->Lvol,
-                           ctx->max_cells, ctx->stream),
+                           ctx->max_cells, ctx->cells + 1, ctx->stream),
                 "sgm");
+    ++ctx->launches;  // the aggregation is two kernels (one per layout, one returns at once)
     stage_end(ctx, TSGM_STAGE_SGM);
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;
     const float s_thr = p.S_max * (float)p.n_paths;
@@ -303,8 +304,8 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ok = ok && alloc(&ctx->lrvalid, n) == cudaSuccess;
     ok = ok && alloc(&ctx->off, n + 1) == cudaSuccess;
     ok = ok && alloc(&ctx->rowsum, (size_t)ctx->H) == cudaSuccess;
-    ok = ok && alloc(&ctx->rowcells, (size_t)ctx->H) == cudaSuccess;
-    ok = ok && alloc(&ctx->cells, 1) == cudaSuccess;
+    ok = ok && alloc(&ctx->rowcells, 2 * (size_t)ctx->H) == cudaSuccess;
+    ok = ok && alloc(&ctx->cells, 2) == cudaSuccess;
     ok = ok && alloc(&ctx->desc, n) == cudaSuccess;
     ok = ok && alloc(&ctx->C, (size_t)ctx->max_cells + 64) == cudaSuccess;
     ok = ok && alloc(&ctx->S, (size_t)ctx->max_cells + 64) == cudaSuccess;
@@ -524,6 +525,7 @@ tsgm_status tsgm_inspect(tsgm_ctx* ctx, tsgm_buffer which, void* dst, uint64_t c
         case TSGM_BUF_WINDOWS_HI: src = ctx->hi; cap = n; esz = 2; break;
         case TSGM_BUF_PRED_D: src = ctx->predD; cap = n; esz = 4; break;
         case TSGM_BUF_PRED_P: src = ctx->predP; cap = n; esz = 4; break;
+        case TSGM_BUF_COUNTS: src = ctx->cells; cap = 2; esz = 4; break;
         default: return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_inspect: unknown buffer");
     }
     if (count > cap) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_inspect: count exceeds buffer");

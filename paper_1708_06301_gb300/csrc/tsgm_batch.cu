@@ -40,8 +40,8 @@ struct BStream {
     uint2* desc;
     uint32_t* off;
     uint32_t* rowsum;
-    uint32_t* rowcells;
-    uint32_t* cells;
+    uint32_t* rowcells;  // true cells per row, then (at + H) pixels wider than kNarrow8 per row
+    uint32_t* cells;     // [0] true cells, [1] aggregation layout (sgm_mode)
     uint32_t* status;  // 0 ok, 1: the windows need more cells than the stream's storage
     uint8_t* C;
     uint8_t* Lvol;
@@ -55,9 +55,10 @@ struct BTable {
     int px_base[kMaxStreams + 1];    // prefix of pixels
     int tiles_x[kMaxStreams];
     // path lines, direction-major: items of stream i in slot s are
-    // [slot_base[s][i], slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]
+    // [slot_base[s][i], slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]; an item is
+    // one line of a horizontal direction, else a quad of 4 consecutive lines
     int slot_base[8][kMaxStreams + 1];
-    int total_lines;
+    int total_lines;  // items (quads) of all slots
 };
 
 __device__ __forceinline__ int find_stream(const int* base, int ns, int item) {
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(256) kb_sanitize(const BStream* __restrict__ s
     const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
     const BStream& b = st[s];
     sanitize_row(b.lo_in, b.hi_in, b.W, b.D, blockIdx.x - tb->row_base[s], b.lo, b.hi, b.rowsum,
-                 b.rowcells);
+                 b.rowcells, b.rowcells + b.H);
 }
 
 __global__ void __launch_bounds__(512) kb_offsets(const BStream* __restrict__ st,
@@ -82,7 +83,8 @@ __global__ void __launch_bounds__(512) kb_offsets(const BStream* __restrict__ st
     const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
     const BStream& b = st[s];
     const int y = blockIdx.x - tb->row_base[s];
-    offsets_row(b.lo, b.hi, b.rowsum, b.rowcells, b.W, b.H, y, b.off, b.desc, b.cells);
+    offsets_row(b.lo, b.hi, b.rowsum, b.rowcells, b.rowcells + b.H, b.W, b.H, y, b.off, b.desc,
+                b.cells);
     if (y == b.H - 1 && threadIdx.x == 0)
         *b.status = (uint64_t)b.off[(size_t)b.W * b.H] > b.capacity ? 1u : 0u;
 }
@@ -111,13 +113,15 @@ __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
     }
 }
 
-// persistent path aggregation: warps take path lines from a global counter until none is left
+// persistent path aggregation: warps take items from a global counter until none is left; an item
+// is one horizontal line (walked by the whole warp) or a quad of 4 lines of another direction of
+// one stream, walked in the stream's layout (sgm_mode)
 template <int LPL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__ st,
                                                      const BTable* __restrict__ tb, int n_paths,
                                                      int P1, int P2, int* __restrict__ counter) {
     extern __shared__ uint32_t sgm_smem32[];
-    uint32_t* buf = sgm_smem32 + (threadIdx.x >> 5) * (32 * LPL);
+    uint32_t* wsm = sgm_smem32 + (threadIdx.x >> 5) * sgm_mixed_words<LPL>();
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
@@ -129,9 +133,15 @@ __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__
         const int s = find_stream(tb->slot_base[slot], tb->ns, item);
         const BStream& b = st[s];
         if (*b.status != 0u) continue;
-        sgm_line<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, slot, item - tb->slot_base[slot][s],
-                      b.Lvol + (size_t)slot * b.capacity, buf);
-        __syncwarp();
+        const int idx = item - tb->slot_base[slot][s];
+        uint8_t* Lv = b.Lvol + (size_t)slot * b.capacity;
+        if (slot <= 1) {  // horizontal: one line per item, one warp per line
+            sgm_line<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, slot, idx, Lv, wsm);
+        } else {
+            const int nl = slot <= 3 ? b.W : b.W + b.H - 1;
+            sgm_line_quad<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, slot, 4 * idx, nl, b.cells[1],
+                               Lv, wsm);
+        }
     }
 }
 
@@ -161,6 +171,29 @@ struct SgmShape {
 };
 const SgmShape kShapes[] = {{4, 4}, {4, 8}, {8, 2}, {8, 4}, {8, 6}, {16, 2}, {16, 3}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+using SgmKernel = void (*)(const BStream*, const BTable*, int, int, int, int*);
+
+int lpl_for(int maxD) { return maxD <= 64 ? 2 : (maxD <= 128 ? 4 : 8); }
+
+template <int LPL>
+SgmKernel sgm_kernel_l(int warps) {
+    return warps == 4 ? kb_sgm<LPL, 4> : (warps == 8 ? kb_sgm<LPL, 8> : kb_sgm<LPL, 16>);
+}
+
+SgmKernel sgm_kernel(int maxD, int warps) {
+    switch (lpl_for(maxD)) {
+        case 2: return sgm_kernel_l<2>(warps);
+        case 4: return sgm_kernel_l<4>(warps);
+        default: return sgm_kernel_l<8>(warps);
+    }
+}
+
+size_t sgm_smem_bytes(int maxD, int warps) {
+    const int L = lpl_for(maxD);
+    const int words = L == 2 ? sgm_mixed_words<2>() : (L == 4 ? sgm_mixed_words<4>() : sgm_mixed_words<8>());
+    return (size_t)warps * words * sizeof(uint32_t);
+}
 
 }  // namespace
 
@@ -225,18 +258,9 @@ cudaError_t enqueue_step(tsgm_batch* b, int shape, bool timed = false) {
     if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecord(b->ev_sgm_a, st)) != cudaSuccess) return e;
     const SgmShape sh = kShapes[shape];
-    const int LPL = b->maxD <= 64 ? 2 : (b->maxD <= 128 ? 4 : (b->maxD <= 192 ? 6 : 8));
-    const size_t smem = (size_t)sh.warps * 2 * 32 * LPL * sizeof(uint16_t);
     const int grid = b->sms * sh.blocks;
-#define TSGM_SGM_CASE(L, Wp)                                                                   \
-    if (LPL == L && sh.warps == Wp)                                                            \
-        kb_sgm<L, Wp><<<grid, Wp * 32, smem, st>>>(b->d_streams, b->d_table, p.n_paths, p.P1, \
-                                                   p.P2, b->d_counter);
-    TSGM_SGM_CASE(2, 4) TSGM_SGM_CASE(2, 8) TSGM_SGM_CASE(2, 16)
-    TSGM_SGM_CASE(4, 4) TSGM_SGM_CASE(4, 8) TSGM_SGM_CASE(4, 16)
-    TSGM_SGM_CASE(6, 4) TSGM_SGM_CASE(6, 8) TSGM_SGM_CASE(6, 16)
-    TSGM_SGM_CASE(8, 4) TSGM_SGM_CASE(8, 8) TSGM_SGM_CASE(8, 16)
-#undef TSGM_SGM_CASE
+    sgm_kernel(b->maxD, sh.warps)<<<grid, sh.warps * 32, sgm_smem_bytes(b->maxD, sh.warps), st>>>(
+        b->d_streams, b->d_table, p.n_paths, p.P1, p.P2, b->d_counter);
     if (timed && (e = cudaEventRecord(b->ev_sgm_b, st)) != cudaSuccess) return e;
     const int DP = 256;
     const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * DP * 2;
@@ -354,8 +378,8 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
             const size_t n = (size_t)s.n;
             ok = balloc(b, &s.lo, n) && balloc(b, &s.hi, n) && balloc(b, &s.censusL, n) &&
                  balloc(b, &s.censusR, n) && balloc(b, &s.desc, n) && balloc(b, &s.off, n + 1) &&
-                 balloc(b, &s.rowsum, (size_t)s.H) && balloc(b, &s.rowcells, (size_t)s.H) &&
-                 balloc(b, &s.cells, 1) && balloc(b, &s.status, 1) &&
+                 balloc(b, &s.rowsum, (size_t)s.H) && balloc(b, &s.rowcells, 2 * (size_t)s.H) &&
+                 balloc(b, &s.cells, 2) && balloc(b, &s.status, 1) &&
                  balloc(b, &s.C, (size_t)s.capacity + 64) &&
                  balloc(b, &s.Lvol, (size_t)s.capacity * p0.n_paths + 64);
             t.row_base[i + 1] = t.row_base[i] + s.H;
@@ -363,18 +387,25 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
             t.tile_base[i + 1] = t.tile_base[i] + t.tiles_x[i] * ((s.H + kCtH - 1) / kCtH);
             t.px_base[i + 1] = t.px_base[i] + s.n;
         }
-        // direction-major line order: every stream's horizontal lines first
+        // direction-major order of line quads: every stream's horizontal lines first
         int item = 0;
         for (int slot = 0; slot < p0.n_paths; ++slot) {
             for (int i = 0; i < n_streams; ++i) {
                 t.slot_base[slot][i] = item;
                 const BStream& s = b->h_streams[i];
-                item += slot <= 1 ? s.H : (slot <= 3 ? s.W : s.W + s.H - 1);
+                item += slot <= 1 ? s.H : ((slot <= 3 ? s.W : s.W + s.H - 1) + 3) / 4;
             }
             t.slot_base[slot][n_streams] = item;
         }
         t.total_lines = item;
         ok = ok && cudaMemcpy(b->d_table, b->h_table, sizeof(BTable), cudaMemcpyHostToDevice) == cudaSuccess;
+        for (int k = 0; ok && k < kNumShapes; ++k) {
+            const size_t sm = sgm_smem_bytes(b->maxD, kShapes[k].warps);
+            if (sm > 48 * 1024)
+                ok = cudaFuncSetAttribute(sgm_kernel(b->maxD, kShapes[k].warps),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm) == cudaSuccess;
+        }
         const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * 256 * 2;
         if (ok && sel_smem > 48 * 1024) {
             ok = cudaFuncSetAttribute(kb_select<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -72,15 +72,36 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
     return r;
 }
 
+// Windows wider than this many labels leave the two-labels-per-lane fast path of an 8-lane line
+// group (sgm_line_group<8>); their count per row picks the aggregation layout (sgm_mode).
+constexpr int kNarrow8 = 16;
+
+// Row statistics written next to the windows: storage cells, true cells, pixels wider than
+// kNarrow8 (rowwide).
+__device__ __forceinline__ void row_totals(uint32_t acc, uint32_t acc_true, uint32_t acc_wide,
+                                           int y, uint32_t* sh, uint32_t* __restrict__ rowsum,
+                                           uint32_t* __restrict__ rowcells,
+                                           uint32_t* __restrict__ rowwide) {
+    const uint32_t t = block_sum(acc, sh);
+    const uint32_t tt = block_sum(acc_true, sh);
+    const uint32_t tw = block_sum(acc_wide, sh);
+    if (threadIdx.x == 0) {
+        rowsum[y] = t;
+        rowcells[y] = tt;
+        rowwide[y] = tw;
+    }
+}
+
 // Caller-supplied windows: copy them clamped into [0, D-1] with lo <= hi (so that every later
-// kernel stays inside the ragged volume whatever the input) and write the row's total length.
+// kernel stays inside the ragged volume whatever the input) and write the row's totals.
 __device__ __forceinline__ void sanitize_row(const int16_t* __restrict__ lo_in,
                                              const int16_t* __restrict__ hi_in, int W, int D, int y,
                                              int16_t* __restrict__ lo, int16_t* __restrict__ hi,
                                              uint32_t* __restrict__ rowsum,
-                                             uint32_t* __restrict__ rowcells) {
+                                             uint32_t* __restrict__ rowcells,
+                                             uint32_t* __restrict__ rowwide) {
     __shared__ uint32_t sh[33];
-    uint32_t acc = 0, acc_true = 0;
+    uint32_t acc = 0, acc_true = 0, acc_wide = 0;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int i = y * W + x;
         const int a = min(max((int)lo_in[i], 0), D - 1);
@@ -89,23 +110,31 @@ __device__ __forceinline__ void sanitize_row(const int16_t* __restrict__ lo_in,
         hi[i] = (int16_t)b;
         acc_true += (uint32_t)(b - a + 1);
         acc += block_cells(b - a + 1);
+        acc_wide += (b - a + 1 > kNarrow8) ? 1u : 0u;
     }
-    const uint32_t t = block_sum(acc, sh);
-    const uint32_t tt = block_sum(acc_true, sh);
-    if (threadIdx.x == 0) {
-        rowsum[y] = t;
-        rowcells[y] = tt;
-    }
+    row_totals(acc, acc_true, acc_wide, y, sh, rowsum, rowcells, rowwide);
+}
+
+// Lanes per path line for the aggregation of one image, from the storage cells, the pixel count
+// and the pixels wider than kNarrow8: 32 (one line per warp, labels packed up to 16 per lane)
+// when the windows average more than 24 cells of storage, else 8 when at most one pixel in 16
+// is wider than kNarrow8 labels, else 16. It decides only the work layout, never a result.
+__host__ __device__ __forceinline__ uint32_t sgm_mode(uint64_t storage, uint64_t n,
+                                                      uint64_t wide) {
+    if (storage > 24 * n) return 32u;
+    return wide * 16 <= n ? 8u : 16u;
 }
 
 // Offsets of the ragged volume: pixel i's block starts at off[i] = sum of the (4-aligned) block
 // sizes of the pixels before it (row-major); off[n] = storage size. One block per row: base =
 // sum of earlier row totals, then a block scan. Also writes the per-pixel descriptor
-// {off, lo | w << 16} used by the matching kernels, and (last row) the number of true cells.
+// {off, lo | w << 16} used by the matching kernels, and (last row) the number of true cells in
+// cells_total[0] and the aggregation layout (sgm_mode) in cells_total[1].
 __device__ __forceinline__ void offsets_row(const int16_t* __restrict__ lo,
                                             const int16_t* __restrict__ hi,
                                             const uint32_t* __restrict__ rowsum,
-                                            const uint32_t* __restrict__ rowcells, int W, int Hh,
+                                            const uint32_t* __restrict__ rowcells,
+                                            const uint32_t* __restrict__ rowwide, int W, int Hh,
                                             int y, uint32_t* __restrict__ off,
                                             uint2* __restrict__ desc,
                                             uint32_t* __restrict__ cells_total) {
@@ -131,12 +160,17 @@ __device__ __forceinline__ void offsets_row(const int16_t* __restrict__ lo,
         base += tot;
     }
     if (y == Hh - 1) {
-        uint32_t c = 0;
-        for (int r = threadIdx.x; r < Hh; r += blockDim.x) c += rowcells[r];
+        uint32_t c = 0, wd = 0;
+        for (int r = threadIdx.x; r < Hh; r += blockDim.x) {
+            c += rowcells[r];
+            wd += rowwide[r];
+        }
         c = block_sum(c, sh);
+        wd = block_sum(wd, sh);
         if (threadIdx.x == 0) {
             off[(size_t)W * Hh] = base;
-            *cells_total = c;
+            cells_total[0] = c;
+            cells_total[1] = sgm_mode(base, (uint64_t)W * Hh, wd);
         }
     }
 }
@@ -224,16 +258,9 @@ __device__ __forceinline__ uint32_t mask_pair(uint32_t v, int e, int lo, int hi)
     return l | (h << 16);
 }
 
-// One path line: direction `code`, line index `l` of that direction; Lv is the direction's
-// volume, buf0 this warp's two shared buffers of 32*LPL labels.
-template <int LPL>
-__device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
-                                         const uint2* __restrict__ desc, int W, int Hh, int D,
-                                         int P1, int P2, int code, int l, uint8_t* __restrict__ Lv,
-                                         uint32_t* const buf0) {
-    constexpr int NP = LPL / 2;       // packed pairs per lane in the dense representation
-    constexpr int DP = 32 * LPL;      // labels covered by the dense representation (>= D)
-    const int lane = threadIdx.x & 31;
+// Start pixel, step and length of line l of direction `code` in a W x Hh image.
+__device__ __forceinline__ void line_geometry(int code, int l, int W, int Hh, int& i0, int& step,
+                                              int& len) {
     int dx, dy;
     dir_of(code, dx, dy);
     int x0, y0;
@@ -253,19 +280,75 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
     }
     const int nx = dx > 0 ? W - x0 : (dx < 0 ? x0 + 1 : 0x7fffffff);
     const int ny = dy > 0 ? Hh - y0 : (dy < 0 ? y0 + 1 : 0x7fffffff);
-    const int len = min(nx, ny);
-    const int step = dy * W + dx;
-    const int i0 = y0 * W + x0;
+    len = min(nx, ny);
+    step = dy * W + dx;
+    i0 = y0 * W + x0;
+}
 
-    constexpr int kBufPairs = DP / 2;  // two buffers of DP uint16 labels, viewed as pairs
+// 4-byte asynchronous copy global -> shared (completion tracked by commit groups, not by the
+// issuing thread's registers, so that many copies can be in flight per warp).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared memory of one warp of the aggregation kernels, in 32-bit words, for labels up to
+// DP = 32 * LPL. A warp walking one line: two label buffers (2 x DP uint16) and a ring of
+// kRingW slots of DP cost bytes. Groups of G lanes: per group two label buffers and a ring of
+// kRingG slots of DP cost bytes.
+constexpr int kRingW = 8, kPrefW = 6;  // ring slots and prefetch distance, one line per warp
+constexpr int kRingG = 4, kPrefG = 3;  // the same for a group of 8 or 16 lanes
+template <int LPL>
+__host__ __device__ constexpr int sgm_warp_words() { return (32 * LPL) * (1 + kRingW / 4); }
+template <int LPL, int G>
+__host__ __device__ constexpr int sgm_group_words() { return (32 * LPL) * (1 + kRingG / 4); }
+template <int LPL>
+__host__ __device__ constexpr int sgm_mixed_words() {
+    return (32 / 8) * sgm_group_words<LPL, 8>() > sgm_warp_words<LPL>()
+               ? (32 / 8) * sgm_group_words<LPL, 8>()
+               : sgm_warp_words<LPL>();
+}
+
+// One path line walked by a whole warp: direction `code`, line index `l` of that direction; Lv is
+// the direction's volume, wsm this warp's shared memory (sgm_warp_words).
+//
+// Three representations of the predecessor's path costs: narrow (w <= 32, lane j <-> label lo + j,
+// neighbours by three shuffles at the window offset), dense (w == D, LPL labels per lane packed as
+// 16-bit pairs, min.u16x2 arithmetic, neighbours by two shuffles) and shared memory (absolute
+// label index), which also carries every change between the first two. The costs of the pixels
+// 1 .. kPrefW ahead are in flight into a ring of shared-memory slots (cp.async), so a step never
+// waits for memory; descriptors come 32 pixels at a time, two blocks ahead.
+template <int LPL>
+__device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
+                                         const uint2* __restrict__ desc, int W, int Hh, int D,
+                                         int P1, int P2, int code, int l, uint8_t* __restrict__ Lv,
+                                         uint32_t* const wsm) {
+    static_assert(LPL == 2 || LPL == 4 || LPL == 8, "labels per lane");
+    constexpr int NP = LPL / 2;        // packed pairs per lane in the dense form
+    constexpr int DP = 32 * LPL;       // labels covered by the dense form (>= D)
+    constexpr int kBufPairs = DP / 2;  // two buffers of DP uint16 labels, as pairs
+    constexpr int R = kRingW, PF = kPrefW;
+    uint32_t* const buf0 = wsm;
+    uint8_t* const ring = reinterpret_cast<uint8_t*>(wsm + DP);
+    const int lane = threadIdx.x & 31;
+    int i0, step, len;
+    line_geometry(code, l, W, Hh, i0, step, len);
 
     // dense-label masks: lanes' pairs beyond D hold +inf and contribute nothing
     uint32_t keep[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        const int e = LPL * lane + 2 * k;
-        keep[k] = (e < D ? 0xFFFFu : 0u) | (e + 1 < D ? 0xFFFF0000u : 0u);
+    for (int k2 = 0; k2 < NP; ++k2) {
+        const int e = LPL * lane + 2 * k2;
+        keep[k2] = (e < D ? 0xFFFFu : 0u) | (e + 1 < D ? 0xFFFF0000u : 0u);
     }
+    const bool dense_lane = LPL * lane < D;
     const uint32_t P1P1 = ((uint32_t)P1 << 16) | (uint32_t)P1;
     const uint32_t P2P2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
 
@@ -275,23 +358,34 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
     int Nreg = kInf;
     uint32_t Dreg[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) Dreg[k] = kInf2;
+    for (int k2 = 0; k2 < NP; ++k2) Dreg[k2] = kInf2;
 
-    // Descriptors of the line: block `blk` of 32 pixels (one per lane) in dc0, the next in dc1.
-    int blk = 0;
-    uint2 dc0 = lane < len ? __ldg(desc + (i0 + lane * step)) : make_uint2(0u, 0u);
-    uint2 dc1 = 32 + lane < len ? __ldg(desc + (i0 + (32 + lane) * step)) : make_uint2(0u, 0u);
-    // descriptor of pixel kk of the line; kk never decreases and advances by at most one
-    auto fetch = [&](int kk, uint32_t& o_, uint32_t& lw_) {
-        if ((kk >> 5) != blk) {
-            dc0 = dc1;
-            ++blk;
-            const int t = ((blk + 1) << 5) + lane;
-            dc1 = t < len ? __ldg(desc + (i0 + t * step)) : make_uint2(0u, 0u);
-        }
-        o_ = __shfl_sync(kFull, dc0.x, kk & 31);
-        lw_ = __shfl_sync(kFull, dc0.y, kk & 31);
+    // descriptors in blocks of 32 pixels (one per lane): dc0 block blk, dc1 the next, dc2 the one
+    // after (in flight)
+    auto ldesc = [&](int kk) -> uint2 {
+        return kk < len ? __ldg(desc + (i0 + kk * step)) : make_uint2(0u, 0u);
     };
+    uint2 dc0 = ldesc(lane), dc1 = ldesc(32 + lane), dc2 = ldesc(64 + lane);
+    int blk = 0;
+    auto desc_at = [&](int kk, uint32_t& o_, uint32_t& lw_) {  // kk in block blk or blk + 1
+        const bool first = (kk >> 5) == blk;
+        o_ = __shfl_sync(kFull, first ? dc0.x : dc1.x, kk & 31);
+        lw_ = __shfl_sync(kFull, first ? dc0.y : dc1.y, kk & 31);
+    };
+    // start the copy of pixel kk's costs (its whole window, whole 4-byte words) into its slot
+    auto issue = [&](int kk) {
+        uint32_t o_, lw_;
+        desc_at(kk, o_, lw_);
+        const int w_ = kk < len ? (int)(lw_ >> 16) : 0;
+        uint8_t* slot = ring + (kk & (R - 1)) * DP;
+#pragma unroll
+        for (int t = 0; t < (DP + 127) / 128; ++t) {
+            const int j = lane + 32 * t;
+            if (4 * j < w_) cp_async4(slot + 4 * j, C + o_ + 4 * j);
+        }
+        cp_async_commit();
+    };
+
     // write the predecessor into smem buffer 0 if it is held in registers
     auto spill = [&]() {
         if (loc != 2) __syncwarp();  // earlier reads of buffer 0 are done before it is rewritten
@@ -305,18 +399,6 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
             qb = 0;
             loc = 2;
             __syncwarp();
-        }
-    };
-    auto emit_narrow = [&](uint32_t o, int L, int w) {
-        if (lane < w) Lv[o + lane] = (uint8_t)L;
-    };
-    auto load_dense_cost = [&](uint32_t o, uint32_t (&c2)[NP]) {
-        const uint16_t* C16 = reinterpret_cast<const uint16_t*>(C + o);
-#pragma unroll
-        for (int k2 = 0; k2 < NP; ++k2) {
-            const int e = LPL * lane + 2 * k2;
-            const uint32_t b = (e < D) ? (uint32_t)__ldg(C16 + (e >> 1)) : 0u;
-            c2[k2] = __byte_perm(b, 0u, 0x4140);  // bytes (c0, c1) -> u16x2
         }
     };
     // one dense step from the predecessor values Lq (labels LPL*lane + ..), result in Dreg
@@ -345,37 +427,53 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
     // dense store: the low byte of every 16-bit label, four labels per 32-bit store when the
     // lane's labels start 4-aligned (LPL a multiple of 4), otherwise two per 16-bit store
     auto emit_dense = [&](uint32_t o) {
+        if (!dense_lane) return;
         if constexpr (LPL % 4 == 0) {
 #pragma unroll
-            for (int k4 = 0; k4 < NP / 2; ++k4) {
-                const int e = LPL * lane + 4 * k4;
-                if (e < D)
-                    *reinterpret_cast<uint32_t*>(Lv + o + e) =
+            for (int k4 = 0; k4 < NP / 2; ++k4)
+                if (LPL * lane + 4 * k4 < D)
+                    *reinterpret_cast<uint32_t*>(Lv + o + LPL * lane + 4 * k4) =
                         __byte_perm(Dreg[2 * k4], Dreg[2 * k4 + 1], 0x6420);
-            }
         } else {
-#pragma unroll
-            for (int k2 = 0; k2 < NP; ++k2) {
-                const int e = LPL * lane + 2 * k2;
-                if (e < D)
-                    *reinterpret_cast<uint16_t*>(Lv + o + e) =
-                        (uint16_t)__byte_perm(Dreg[k2], 0u, 0x0020);
-            }
+            *reinterpret_cast<uint16_t*>(Lv + o + LPL * lane) =
+                (uint16_t)__byte_perm(Dreg[0], 0u, 0x0020);
         }
     };
 
-    uint32_t o, lw;
-    fetch(0, o, lw);
-    int k = 0;
-    while (k < len) {
-        int lo = (int)(lw & 0xFFFFu);
-        int w = (int)(lw >> 16);
+    for (int u = 0; u < PF; ++u) issue(u);
+    // unrolled so that consecutive steps use different registers: a store or copy still reading
+    // its operands does not hold up the next step
+#pragma unroll 4
+    for (int k = 0; k < len; ++k) {
+        if (k > 0 && (k & 31) == 0) {
+            dc0 = dc1;
+            dc1 = dc2;
+            ++blk;
+            dc2 = ldesc(((blk + 2) << 5) + lane);
+        }
+        uint32_t o, lw;
+        desc_at(k, o, lw);
+        const int lo = (int)(lw & 0xFFFFu);
+        const int w = (int)(lw >> 16);
+        cp_async_wait<PF - 1>();  // this pixel's copy (the oldest in flight) has landed
+        __syncwarp();             // ... for every lane's part of it
+        const uint8_t* cs = ring + (k & (R - 1)) * DP;
+        issue(k + PF);  // into the slot read two steps ago
         if (w <= 32) {
-            // ------------------------------------------------------------ narrow run
-            int c = lane < w ? (int)__ldg(C + o + lane) : 0;
+            // ------------------------------------------------------------ narrow step
+            const int c = lane < w ? (int)cs[lane] : 0;
             int L;
             if (k == 0) {
                 L = c;
+            } else if (loc == 0) {
+                const int s_ = lane + (lo - qlo);
+                int vc = __shfl_sync(kFull, Nreg, s_ & 31);
+                int vl = __shfl_sync(kFull, Nreg, (s_ - 1) & 31);
+                int vr = __shfl_sync(kFull, Nreg, (s_ + 1) & 31);
+                vc = ((unsigned)s_ < (unsigned)qw) ? vc : kInf;
+                vl = ((unsigned)(s_ - 1) < (unsigned)qw) ? vl : kInf;
+                vr = ((unsigned)(s_ + 1) < (unsigned)qw) ? vr : kInf;
+                L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
             } else {
                 spill();
                 const uint16_t* src16 = reinterpret_cast<const uint16_t*>(buf0 + qb * kBufPairs);
@@ -386,43 +484,24 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
                 const int vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
                 L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
             }
-            for (;;) {
-                // look one pixel ahead: its descriptor and (if narrow) its costs
-                const bool more = k + 1 < len;
-                uint32_t o_n = 0, lw_n = 0;
-                int c_n = 0;
-                if (more) {
-                    fetch(k + 1, o_n, lw_n);
-                    const int w_n = (int)(lw_n >> 16);
-                    c_n = (w_n <= 32 && lane < w_n) ? (int)__ldg(C + o_n + lane) : 0;
-                }
-                L = lane < w ? L : kInf;
-                emit_narrow(o, L, w);
-                m = (int)__reduce_min_sync(kFull, (unsigned)L);
-                Nreg = L;
-                qlo = lo;
-                qw = w;
-                loc = 0;
-                ++k;
-                if (!more) break;
-                o = o_n;
-                lw = lw_n;
-                lo = (int)(lw & 0xFFFFu);
-                w = (int)(lw >> 16);
-                if (w > 32) break;
-                const int s_ = lane + (lo - qlo);
-                int vc = __shfl_sync(kFull, Nreg, s_ & 31);
-                int vl = __shfl_sync(kFull, Nreg, (s_ - 1) & 31);
-                int vr = __shfl_sync(kFull, Nreg, (s_ + 1) & 31);
-                vc = ((unsigned)s_ < (unsigned)qw) ? vc : kInf;
-                vl = ((unsigned)(s_ - 1) < (unsigned)qw) ? vl : kInf;
-                vr = ((unsigned)(s_ + 1) < (unsigned)qw) ? vr : kInf;
-                L = c_n + min(min(min(vl, vr) + P1, vc), m + P2) - m;
-            }
+            L = lane < w ? L : kInf;
+            if (lane < w) Lv[o + lane] = (uint8_t)L;
+            m = (int)__reduce_min_sync(kFull, (unsigned)L);
+            Nreg = L;
+            loc = 0;
         } else if (w == D) {
-            // ------------------------------------------------------------ full-range run
+            // ------------------------------------------------------------ full-range step
             uint32_t c2[NP];
-            load_dense_cost(o, c2);
+            if constexpr (LPL == 2) {
+                c2[0] = __byte_perm(*reinterpret_cast<const uint16_t*>(cs + 2 * lane), 0u, 0x4140);
+            } else {
+#pragma unroll
+                for (int r = 0; r < LPL / 4; ++r) {
+                    const uint32_t wd = *reinterpret_cast<const uint32_t*>(cs + LPL * lane + 4 * r);
+                    c2[2 * r] = __byte_perm(wd, 0u, 0x4140);
+                    c2[2 * r + 1] = __byte_perm(wd, 0u, 0x4342);
+                }
+            }
             int lmin;
             if (k == 0) {
                 uint32_t pmin = kInf2;
@@ -432,6 +511,11 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
                     pmin = vmin2(pmin, Dreg[k2]);
                 }
                 lmin = (int)min(pmin & 0xFFFFu, pmin >> 16);
+            } else if (loc == 1) {
+                uint32_t Lq[NP];
+#pragma unroll
+                for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[k2];
+                lmin = dense_step(Lq, c2);
             } else {
                 spill();
                 const uint32_t* srcp = buf0 + qb * kBufPairs;
@@ -442,30 +526,11 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
                     Lq[k2] = mask_pair(srcp[(LPL * lane) / 2 + k2], LPL * lane + 2 * k2, qlo, qhi);
                 lmin = dense_step(Lq, c2);
             }
-            for (;;) {
-                const bool more = k + 1 < len;
-                uint32_t o_n = 0, lw_n = 0;
-                if (more) {
-                    fetch(k + 1, o_n, lw_n);
-                    if ((int)(lw_n >> 16) == D) load_dense_cost(o_n, c2);
-                }
-                emit_dense(o);
-                m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
-                qlo = 0;
-                qw = D;
-                loc = 1;
-                ++k;
-                if (!more) break;
-                o = o_n;
-                lw = lw_n;
-                if ((int)(lw >> 16) != D) break;
-                uint32_t Lq[NP];
-#pragma unroll
-                for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[k2];
-                lmin = dense_step(Lq, c2);
-            }
+            emit_dense(o);
+            m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
+            loc = 1;
         } else {
-            // ------------------------------------------------------------ general window
+            // ------------------------------------------------------------ other widths (smem)
             if (k > 0) spill();
             __syncwarp();
             const uint16_t* src16 = reinterpret_cast<const uint16_t*>(buf0 + qb * kBufPairs);
@@ -476,7 +541,7 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
                 const int j = j0 + lane;
                 const bool act = j < w;
                 const int d = lo + j;
-                const int c = act ? (int)__ldg(C + o + j) : 0;
+                const int c = act ? (int)cs[j] : 0;
                 int L;
                 if (k == 0) {
                     L = c;
@@ -487,19 +552,242 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
                     L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
                 }
                 L = act ? L : kInf;
-                if (act) dst16[d] = (uint16_t)L;
+                if (act) {
+                    dst16[d] = (uint16_t)L;
+                    Lv[o + j] = (uint8_t)L;
+                }
                 lmin = min(lmin, L);
-                if (act) Lv[o + j] = (uint8_t)L;
             }
             m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
             qb ^= 1;
             loc = 2;
-            qlo = lo;
-            qw = w;
             __syncwarp();
-            if (++k < len) fetch(k, o, lw);
         }
+        qlo = lo;
+        qw = w;
     }
+    cp_async_wait<0>();  // the copies past the line end (empty groups) are retired
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------------------------
+// One path line walked by a group of G lanes (G = 8 or 16; 32 / G lines per warp), for the short
+// lines of images whose windows are mostly narrow. Lane j of the group holds the path costs of
+// labels lo + 2j and lo + 2j + 1 packed as 16-bit halves, so windows of up to 2G labels take one
+// step of packed arithmetic: the predecessor's values at d - 1 .. d + 2 come from three shuffles
+// of the predecessor's pairs at a group-uniform offset and a byte permutation chosen by the
+// offset's parity. Labels outside a window carry at least kInf. Wider windows walk their labels in
+// chunks of 2G through the group's two label buffers (absolute disparity index, ping-pong).
+// Costs arrive through the group's ring of kRingG shared-memory slots, kPrefG pixels ahead. The
+// groups of a warp step together (a group with a shorter line, or none, idles to the end) and take
+// their minima by full-warp reductions; shuffles and the wide path synchronise the group alone.
+// gsm is the group's shared memory (sgm_group_words); l < 0: no line for this group.
+// ---------------------------------------------------------------------------------------------
+template <int LPL, int G>
+__device__ __forceinline__ void sgm_line_group(const uint8_t* __restrict__ C,
+                                               const uint2* __restrict__ desc, int W, int Hh,
+                                               int D, int P1, int P2, int code, int l,
+                                               uint8_t* __restrict__ Lv, uint32_t* const gsm) {
+    static_assert(G == 8 || G == 16, "group of 8 or 16 lanes");
+    constexpr int DP = 32 * LPL;
+    constexpr int NW = 2 * G;  // widest window of the packed fast path
+    constexpr int R = kRingG, PF = kPrefG;
+    uint16_t* const sbuf = reinterpret_cast<uint16_t*>(gsm);          // 2 x DP labels
+    uint8_t* const ring = reinterpret_cast<uint8_t*>(gsm + DP);       // R slots of DP bytes
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int gi = lane / G;
+    const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
+    int i0 = 0, step = 0, len = 0;  // l < 0: this group has no line and only keeps step
+    if (l >= 0) line_geometry(code, l, W, Hh, i0, step, len);
+    // the groups of the warp step together (the per-group minimum is taken by full-warp
+    // reductions, far faster than a reduction over a partial mask): as many steps as the longest
+    const int steps = (int)__reduce_max_sync(kFull, (unsigned)len);
+
+    const uint32_t P1P1 = ((uint32_t)P1 << 16) | (uint32_t)P1;
+    const uint32_t P2P2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
+
+    // descriptors: dA holds pixels [G*blk, G*blk + G) (one per lane), dB the next block, dC the
+    // one after (in flight)
+    auto ldesc = [&](int kk) -> uint2 {
+        return kk < len ? __ldg(desc + (i0 + kk * step)) : make_uint2(0u, 0u);
+    };
+    uint2 dA = ldesc(gl), dB = ldesc(G + gl), dC = ldesc(2 * G + gl);
+    int blk = 0;
+    auto desc_at = [&](int kk, uint32_t& o_, uint32_t& lw_) {  // kk in block blk or blk + 1
+        const bool first = (kk / G) == blk;
+        o_ = __shfl_sync(gmask, first ? dA.x : dB.x, kk & (G - 1), G);
+        lw_ = __shfl_sync(gmask, first ? dA.y : dB.y, kk & (G - 1), G);
+    };
+    auto issue = [&](int kk) {
+        uint32_t o_, lw_;
+        desc_at(kk, o_, lw_);
+        const int w_ = kk < len ? (int)(lw_ >> 16) : 0;
+        uint8_t* slot = ring + (kk & (R - 1)) * DP;
+#pragma unroll
+        for (int t = 0; t < (DP + 4 * G - 1) / (4 * G); ++t) {
+            const int j = gl + G * t;
+            if (4 * j < w_) cp_async4(slot + 4 * j, C + o_ + 4 * j);
+        }
+        cp_async_commit();
+    };
+    // (c(d), c(d+1)) as 16-bit halves, kInf for labels at or beyond w (j = first label's index)
+    auto cost_pair = [&](uint32_t raw, int j, int w_) -> uint32_t {
+        const uint32_t c2 = __byte_perm(raw, 0u, 0x4140);
+        return j >= w_ ? kInf2 : (j + 1 >= w_ ? (c2 | ((uint32_t)kInf << 16)) : c2);
+    };
+    auto relax = [&](uint32_t prev, uint32_t cen, uint32_t nxt, uint32_t c2, uint32_t mm,
+                     uint32_t mP2) -> uint32_t {
+        uint32_t t = vmin2(prev, nxt) + P1P1;
+        t = vmin2(vmin2(t, cen), mP2);
+        return (c2 + t) - mm;  // every half of t is >= m: no borrow between the halves
+    };
+
+    uint32_t Q = kInf2;  // predecessor pair (labels qlo + 2gl, +1) while held in registers
+    int qlo = 0, qw = 0, qb = 0;
+    bool in_regs = true;
+    uint32_t mm = 0, mP2 = 0;
+
+    for (int u = 0; u < PF; ++u) issue(u);
+#pragma unroll 2
+    for (int k = 0; k < steps; ++k) {
+        if (k > 0 && (k & (G - 1)) == 0) {
+            dA = dB;
+            dB = dC;
+            ++blk;
+            dC = ldesc((blk + 2) * G + gl);
+        }
+        uint32_t o, lw;
+        desc_at(k, o, lw);  // past the line's end: 0 (an empty window, nothing stored)
+        const int lo = (int)(lw & 0xFFFFu);
+        const int w = (int)(lw >> 16);
+        cp_async_wait<PF - 1>();
+        __syncwarp(gmask);
+        const uint8_t* cs = ring + (k & (R - 1)) * DP;
+        issue(k + PF);  // into the slot read the step before
+        uint32_t pm;
+        if (w <= NW) {
+            // ------------------------------------------------------------ packed narrow step
+            const uint32_t raw =
+                2 * gl < w ? (uint32_t)*reinterpret_cast<const uint16_t*>(cs + 2 * gl) : 0u;
+            const uint32_t c2 = cost_pair(raw, 2 * gl, w);
+            uint32_t L;
+            if (k == 0) {
+                L = c2;
+            } else {
+                uint32_t prev, cen, nxt;
+                const int r0 = lo - qlo - 1;  // predecessor index of label lo - 1
+                if (in_regs) {
+                    const int a = gl + (r0 >> 1);
+                    uint32_t A = __shfl_sync(gmask, Q, a, G);
+                    uint32_t B = __shfl_sync(gmask, Q, a + 1, G);
+                    uint32_t E = __shfl_sync(gmask, Q, a + 2, G);
+                    A = (unsigned)a < (unsigned)G ? A : kInf2;
+                    B = (unsigned)(a + 1) < (unsigned)G ? B : kInf2;
+                    E = (unsigned)(a + 2) < (unsigned)G ? E : kInf2;
+                    const bool odd = (r0 & 1) != 0;
+                    const uint32_t s1 = odd ? 0x5432u : 0x3210u;
+                    prev = __byte_perm(A, B, s1);
+                    cen = __byte_perm(A, B, odd ? 0x7654u : 0x5432u);
+                    nxt = __byte_perm(B, E, s1);
+                } else {
+                    const uint16_t* src = sbuf + qb * DP;
+                    const int d0 = lo + 2 * gl, qhi = qlo + qw - 1;
+                    const uint32_t v0 = (d0 - 1 >= qlo && d0 - 1 <= qhi) ? src[d0 - 1] : kInf;
+                    const uint32_t v1 = (d0 >= qlo && d0 <= qhi) ? src[d0] : kInf;
+                    const uint32_t v2 = (d0 + 1 >= qlo && d0 + 1 <= qhi) ? src[d0 + 1] : kInf;
+                    const uint32_t v3 = (d0 + 2 >= qlo && d0 + 2 <= qhi) ? src[d0 + 2] : kInf;
+                    prev = v0 | (v1 << 16);
+                    cen = v1 | (v2 << 16);
+                    nxt = v2 | (v3 << 16);
+                }
+                L = relax(prev, cen, nxt, c2, mm, mP2);
+            }
+            if (2 * gl < w)
+                *reinterpret_cast<uint16_t*>(Lv + o + 2 * gl) = (uint16_t)__byte_perm(L, 0u, 0x0020);
+            pm = min(L & 0xFFFFu, L >> 16);
+            Q = L;
+            in_regs = true;
+        } else {
+            // ------------------------------------------------------------ wide step (chunks)
+            if (k > 0 && in_regs) {
+                __syncwarp(gmask);  // earlier reads of buffer qb are done
+                const int d0 = qlo + 2 * gl;
+                if (2 * gl < qw) sbuf[qb * DP + d0] = (uint16_t)(Q & 0xFFFFu);
+                if (2 * gl + 1 < qw) sbuf[qb * DP + d0 + 1] = (uint16_t)(Q >> 16);
+                __syncwarp(gmask);
+            }
+            const uint16_t* src = sbuf + qb * DP;
+            uint16_t* dst = sbuf + (qb ^ 1) * DP;
+            const int qhi = qlo + qw - 1;
+            pm = (uint32_t)kInf;
+            for (int j0 = 0; j0 < w; j0 += NW) {
+                const int j = j0 + 2 * gl;
+                const int d0 = lo + j;
+                const uint32_t raw = j < w ? (uint32_t)*reinterpret_cast<const uint16_t*>(cs + j) : 0u;
+                const uint32_t c2 = cost_pair(raw, j, w);
+                uint32_t L;
+                if (k == 0) {
+                    L = c2;
+                } else {
+                    const uint32_t v0 = (d0 - 1 >= qlo && d0 - 1 <= qhi) ? src[d0 - 1] : kInf;
+                    const uint32_t v1 = (d0 >= qlo && d0 <= qhi) ? src[d0] : kInf;
+                    const uint32_t v2 = (d0 + 1 >= qlo && d0 + 1 <= qhi) ? src[d0 + 1] : kInf;
+                    const uint32_t v3 = (d0 + 2 >= qlo && d0 + 2 <= qhi) ? src[d0 + 2] : kInf;
+                    L = relax(v0 | (v1 << 16), v1 | (v2 << 16), v2 | (v3 << 16), c2, mm, mP2);
+                }
+                if (j < w) {
+                    dst[d0] = (uint16_t)(L & 0xFFFFu);
+                    if (j + 1 < w) dst[d0 + 1] = (uint16_t)(L >> 16);
+                    *reinterpret_cast<uint16_t*>(Lv + o + j) = (uint16_t)__byte_perm(L, 0u, 0x0020);
+                }
+                pm = min(pm, min(L & 0xFFFFu, L >> 16));
+            }
+            __syncwarp(gmask);  // dst complete, src reads done
+            qb ^= 1;
+            in_regs = false;
+        }
+        // the minimum over each group, from one full-warp reduction per group
+        uint32_t m = 0;
+#pragma unroll
+        for (int g = 0; g < 32 / G; ++g) {
+            const uint32_t mg = __reduce_min_sync(kFull, gi == g ? pm : 0xFFFFFFFFu);
+            m = gi == g ? mg : m;
+        }
+        mm = (m << 16) | m;
+        mP2 = mm + P2P2;
+        qlo = lo;
+        qw = w;
+    }
+    cp_async_wait<0>();
+    __syncwarp();  // the group's buffers may be reused by its next line
+}
+
+// The lines [l0, l0 + 4) of direction `code` (those below nl) of one image, walked by one warp in
+// the layout `mode` (lanes per line, sgm_mode). `wsm` is the warp's shared memory
+// (sgm_mixed_words).
+template <int LPL>
+__device__ __forceinline__ void sgm_line_quad(const uint8_t* __restrict__ C,
+                                              const uint2* __restrict__ desc, int W, int Hh, int D,
+                                              int P1, int P2, int code, int l0, int nl,
+                                              uint32_t mode, uint8_t* __restrict__ Lv,
+                                              uint32_t* wsm) {
+    const int lane = threadIdx.x & 31;
+    if (mode == 8u) {
+        const int l = l0 + (lane >> 3);
+        sgm_line_group<LPL, 8>(C, desc, W, Hh, D, P1, P2, code, l < nl ? l : -1, Lv,
+                               wsm + (lane >> 3) * sgm_group_words<LPL, 8>());
+    } else if (mode == 16u) {
+        for (int r = 0; r < 2; ++r) {
+            const int l = l0 + 2 * r + (lane >> 4);
+            sgm_line_group<LPL, 16>(C, desc, W, Hh, D, P1, P2, code, l < nl ? l : -1, Lv,
+                                    wsm + (lane >> 4) * sgm_group_words<LPL, 16>());
+        }
+    } else {
+        for (int r = 0; r < 4 && l0 + r < nl; ++r) sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code,
+                                                                 l0 + r, Lv, wsm);
+    }
+    __syncwarp();
 }
 
 constexpr int kSelThreads = 512;

@@ -92,10 +92,11 @@ __global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
                                                  float k, int16_t* __restrict__ lo,
                                                  int16_t* __restrict__ hi,
                                                  uint32_t* __restrict__ rowsum,
-                                                 uint32_t* __restrict__ rowcells) {
+                                                 uint32_t* __restrict__ rowcells,
+                                                 uint32_t* __restrict__ rowwide) {
     __shared__ uint32_t sh[33];
     const int y = blockIdx.x;
-    uint32_t acc = 0, acc_true = 0;
+    uint32_t acc = 0, acc_true = 0, acc_wide = 0;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int i = y * W + x;
         const float d = Dp[i], p = Pp[i];
@@ -114,13 +115,9 @@ __global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
         hi[i] = (int16_t)b;
         acc_true += (uint32_t)(b - a + 1);
         acc += block_cells(b - a + 1);
+        acc_wide += (b - a + 1 > kNarrow8) ? 1u : 0u;
     }
-    const uint32_t t = block_sum(acc, sh);
-    const uint32_t tt = block_sum(acc_true, sh);
-    if (threadIdx.x == 0) {
-        rowsum[y] = t;
-        rowcells[y] = tt;
-    }
+    row_totals(acc, acc_true, acc_wide, y, sh, rowsum, rowcells, rowwide);
 }
 
 // Caller-supplied windows, clamped copies and row totals (see sanitize_row).
@@ -130,7 +127,7 @@ __global__ void __launch_bounds__(256) k_sanitize_rowsum(const int16_t* __restri
                                                          int16_t* __restrict__ hi,
                                                          uint32_t* __restrict__ rowsum,
                                                          uint32_t* __restrict__ rowcells) {
-    sanitize_row(lo_in, hi_in, W, D, blockIdx.x, lo, hi, rowsum, rowcells);
+    sanitize_row(lo_in, hi_in, W, D, blockIdx.x, lo, hi, rowsum, rowcells, rowcells + gridDim.x);
 }
 
 // Block starts and descriptors of the ragged volume, one block per row (see offsets_row).
@@ -141,7 +138,7 @@ __global__ void __launch_bounds__(512) k_offsets(const int16_t* __restrict__ lo,
                                                  int Hh, uint32_t* __restrict__ off,
                                                  uint2* __restrict__ desc,
                                                  uint32_t* __restrict__ cells_total) {
-    offsets_row(lo, hi, rowsum, rowcells, W, Hh, blockIdx.x, off, desc, cells_total);
+    offsets_row(lo, hi, rowsum, rowcells, rowcells + Hh, W, Hh, blockIdx.x, off, desc, cells_total);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -242,7 +239,7 @@ cudaError_t launch_warp_gather(const unsigned long long* keys, const float* Dpre
 cudaError_t launch_windows(const float* Dp, const float* Pp, int W, int Hh, int D, float k,
                            int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
                            cudaStream_t st) {
-    k_windows<<<Hh, 256, 0, st>>>(Dp, Pp, W, D, k, lo, hi, rowsum, rowcells);
+    k_windows<<<Hh, 256, 0, st>>>(Dp, Pp, W, D, k, lo, hi, rowsum, rowcells, rowcells + Hh);
     return cudaGetLastError();
 }
 

@@ -346,3 +346,30 @@ def random_windows(seed: int, W: int, H: int, D: int, w_min: int = 1, w_max: int
         lo[full] = 0
         hi[full] = D - 1
     return lo.astype(np.int16).reshape(H, W), hi.astype(np.int16).reshape(H, W)
+
+
+def mixed_windows(seed: int, W: int, H: int, D: int, narrow=(1, 16), wide=(17, 40),
+                  wide_frac: float = 0.0, full_frac: float = 0.0):
+    """Windows centred on a smooth disparity surface, so that neighbouring windows overlap and
+    shift by a few labels like windows around a prediction: widths uniform in `narrow`, a fraction
+    `wide_frac` uniform in `wide`, a fraction `full_frac` the full range (int16 lo, hi)."""
+    n = W * H
+    idx = np.arange(n, dtype=np.int64)
+    x = (idx % W).astype(np.float64)
+    y = (idx // W).astype(np.float64)
+    phase = 6.2831853 * uniform01(seed, 0x31, np.zeros(1, np.int64))[0]
+    centre = (D - 1) * (0.5 + 0.35 * np.sin(6.2831853 * x / 97.0 + phase) *
+                        np.cos(6.2831853 * y / 53.0))
+    u = uniform01(seed, 0x32, idx)
+    w = narrow[0] + np.floor(u * (narrow[1] - narrow[0] + 1)).astype(np.int64)
+    pick = uniform01(seed, 0x33, idx)
+    wide_w = wide[0] + np.floor(uniform01(seed, 0x34, idx) * (wide[1] - wide[0] + 1)).astype(np.int64)
+    w = np.where(pick < wide_frac, wide_w, w)
+    w = np.clip(w, 1, D)
+    lo = np.clip(np.round(centre - w / 2.0).astype(np.int64), 0, D - w)
+    hi = lo + w - 1
+    full = (pick >= wide_frac) & (pick < wide_frac + full_frac)
+    lo[full] = 0
+    hi[full] = D - 1
+    return lo.astype(np.int16).reshape(H, W), hi.astype(np.int16).reshape(H, W)
+

@@ -24,7 +24,7 @@ FLAG_FILL_GAPS = 4
 N_STAGES = 8
 STAGES = ["warp", "windows", "census", "cost", "sgm", "select", "kalman", "offsets"]
 BUF = dict(census_l=0, census_r=1, offsets=2, cost=3, S=4, dstar=5, dright=6, lr_valid=7,
-           zkeys=8, windows_lo=9, windows_hi=10, pred_d=11, pred_p=12)
+           zkeys=8, windows_lo=9, windows_hi=10, pred_d=11, pred_p=12, counts=13)
 
 
 class TsgmError(RuntimeError):

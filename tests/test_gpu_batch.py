@@ -32,7 +32,12 @@ def inputs(seed):
         a, b = synth.random_images(seed * 100 + k, W, H)
         right = np.roll(a, -min(3, D - 1), axis=1)
         right[:, -3:] = b[:, -3:]
-        lo, hi = synth.random_windows(seed * 100 + k + 50, W, H, D, 4, min(24, D), full_frac=0.1)
+        if W >= 1000:  # windows around a smooth surface, mostly narrow (8 lanes per path line)
+            lo, hi = synth.mixed_windows(seed * 100 + k + 50, W, H, D, (1, 16), (17, 40), 0.02,
+                                         0.02)
+        else:
+            lo, hi = synth.random_windows(seed * 100 + k + 50, W, H, D, 4, min(24, D),
+                                          full_frac=0.1)
         out.append((a, right, lo, hi))
     return out
 

@@ -123,26 +123,41 @@ def test_windows_bitexact(tsgm, W, H, D):
 # matching stages on random windows (narrow, wide and full-range mixed)
 # ----------------------------------------------------------------------------------------------
 
+# W, H, D, census, paths, windows, lanes per path line the aggregation must pick
+#   ("rand", w_min, w_max, full_frac): independent random windows (neighbours rarely overlap)
+#   ("mixed", narrow, wide, wide_frac, full_frac): windows around a smooth surface (overlapping)
 CASES = [
-    # W, H, D, census, paths, w_min, w_max, full_frac
-    (97, 45, 64, (5, 5), 4, 1, 24, 0.2),
-    (131, 37, 128, (9, 7), 8, 1, 40, 0.25),
-    (64, 32, 256, (9, 7), 8, 20, 80, 0.1),
-    (200, 3, 64, (5, 5), 8, 1, 64, 0.5),
-    (3, 70, 32, (5, 5), 8, 1, 32, 0.3),
-    (1, 1, 16, (5, 5), 8, 1, 16, 1.0),
-    (50, 20, 1, (5, 5), 8, 1, 1, 0.0),
+    (97, 45, 64, (5, 5), 4, ("rand", 1, 24, 0.2), 16),
+    (131, 37, 128, (9, 7), 8, ("rand", 1, 40, 0.25), 32),
+    (64, 32, 256, (9, 7), 8, ("rand", 20, 80, 0.1), 32),
+    (200, 3, 64, (5, 5), 8, ("rand", 1, 64, 0.5), 32),
+    (3, 70, 32, (5, 5), 8, ("rand", 1, 32, 0.3), 16),
+    (1, 1, 16, (5, 5), 8, ("rand", 1, 16, 1.0), 8),
+    (50, 20, 1, (5, 5), 8, ("rand", 1, 1, 0.0), 8),
+    (211, 29, 128, (9, 7), 8, ("mixed", (1, 16), (17, 40), 0.02, 0.03), 8),
+    (173, 31, 64, (5, 5), 4, ("mixed", (4, 24), (25, 40), 0.0, 0.02), 16),
+    (97, 41, 256, (9, 7), 8, ("mixed", (1, 16), (17, 60), 0.02, 0.02), 8),
+    (160, 24, 128, (9, 7), 8, ("mixed", (3, 12), (17, 32), 0.0, 0.0), 8),
+    (77, 50, 64, (5, 5), 8, ("mixed", (4, 24), (17, 64), 0.05, 0.05), 16),
 ]
+
+
+def case_windows(W, H, D, spec):
+    if spec[0] == "rand":
+        _, wmin, wmax, ff = spec
+        return synth.random_windows(W + H, W, H, D, wmin, min(wmax, D), full_frac=ff)
+    _, narrow, wide, wf, ff = spec
+    return synth.mixed_windows(W * 3 + H, W, H, D, narrow, wide, wf, ff)
 
 
 @pytest.mark.parametrize("case", CASES)
 def test_match_stages_bitexact(tsgm, case):
-    W, H, D, (cw, ch), npaths, wmin, wmax, ff = case
+    W, H, D, (cw, ch), npaths, spec, lanes = case
     seq_l, seq_r = synth.random_images(W * 7 + H, W, H)
     # make the right image a shifted copy so that matching has structure
     right = np.roll(seq_l, -min(5, D - 1), axis=1)
     right[:, -5:] = seq_r[:, -5:]
-    lo, hi = synth.random_windows(W + H, W, H, D, wmin, min(wmax, D), full_frac=ff)
+    lo, hi = case_windows(W, H, D, spec)
     with make_ctx(tsgm, W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths) as ctx:
         Dz, rz = empty((H, W), np.float32), empty((H, W), np.float32)
         ctx.match(dev(seq_l), dev(right), dev(lo), dev(hi), Dz, rz)
@@ -159,13 +174,17 @@ def test_match_stages_bitexact(tsgm, case):
         ctx.inspect("dstar", ds, W * H)
         ctx.inspect("dright", dr, W * H)
         ctx.inspect("lr_valid", va, W * H)
+        counts = empty((2,), np.uint32)
+        ctx.inspect("counts", counts, 2)
+        counts = host(counts, np.uint32)
         g = dict(C=compact(host(C, np.uint8), offg, lo, hi), S=compact(host(S, np.uint16), offg, lo, hi),
                  ds=host(ds, np.int16),
                  dr=host(dr, np.int16), va=host(va, np.uint8), Dz=host(Dz, np.float32),
                  rz=host(rz, np.float32))
     prm = oparams(W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths)
     o = oracle.match(seq_l, right, lo, hi, prm, keep=True)
-    assert n == int(o["off"][-1])
+    assert n == int(o["off"][-1]) == int(counts[0])
+    assert int(counts[1]) == lanes
     assert np.array_equal(offg, padded_offsets(lo, hi))
     assert np.array_equal(g["C"], o["C"])
     assert np.array_equal(g["S"], o["S"])
