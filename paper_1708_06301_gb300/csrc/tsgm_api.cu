@@ -228,7 +228,6 @@ tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* righ
     TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->Lvol,
                            ctx->max_cells, ctx->cells + 1, ctx->stream),
                 "sgm");
-    ++ctx->launches;  // the aggregation is two kernels (one per layout, one returns at once)
     stage_end(ctx, TSGM_STAGE_SGM);
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;
     const float s_thr = p.S_max * (float)p.n_paths;

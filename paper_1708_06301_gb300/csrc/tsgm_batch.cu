@@ -40,7 +40,7 @@ struct BStream {
     uint2* desc;
     uint32_t* off;
     uint32_t* rowsum;
-    uint32_t* rowcells;  // true cells per row, then (at + H) pixels wider than kNarrow8 per row
+    uint32_t* rowcells;  // true cells per row, then (at + H) pixels wider than kNarrowMax per row
     uint32_t* cells;     // [0] true cells, [1] aggregation layout (sgm_mode)
     uint32_t* status;  // 0 ok, 1: the windows need more cells than the stream's storage
     uint8_t* C;
@@ -55,10 +55,9 @@ struct BTable {
     int px_base[kMaxStreams + 1];    // prefix of pixels
     int tiles_x[kMaxStreams];
     // path lines, direction-major: items of stream i in slot s are
-    // [slot_base[s][i], slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]; an item is
-    // one line of a horizontal direction, else a quad of 4 consecutive lines
+    // [slot_base[s][i], slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]
     int slot_base[8][kMaxStreams + 1];
-    int total_lines;  // items (quads) of all slots
+    int total_lines;
 };
 
 __device__ __forceinline__ int find_stream(const int* base, int ns, int item) {
@@ -113,15 +112,14 @@ __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
     }
 }
 
-// persistent path aggregation: warps take items from a global counter until none is left; an item
-// is one horizontal line (walked by the whole warp) or a quad of 4 lines of another direction of
-// one stream, walked in the stream's layout (sgm_mode)
+// persistent path aggregation: warps take path lines from a global counter until none is left;
+// each line picks its walker from its windows unless its stream is mostly wide (sgm_mode)
 template <int LPL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__ st,
                                                      const BTable* __restrict__ tb, int n_paths,
                                                      int P1, int P2, int* __restrict__ counter) {
     extern __shared__ uint32_t sgm_smem32[];
-    uint32_t* wsm = sgm_smem32 + (threadIdx.x >> 5) * sgm_mixed_words<LPL>();
+    uint32_t* wsm = sgm_smem32 + (threadIdx.x >> 5) * sgm_warp_words<LPL>();
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
@@ -133,15 +131,8 @@ __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__
         const int s = find_stream(tb->slot_base[slot], tb->ns, item);
         const BStream& b = st[s];
         if (*b.status != 0u) continue;
-        const int idx = item - tb->slot_base[slot][s];
-        uint8_t* Lv = b.Lvol + (size_t)slot * b.capacity;
-        if (slot <= 1) {  // horizontal: one line per item, one warp per line
-            sgm_line<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, slot, idx, Lv, wsm);
-        } else {
-            const int nl = slot <= 3 ? b.W : b.W + b.H - 1;
-            sgm_line_quad<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, slot, 4 * idx, nl, b.cells[1],
-                               Lv, wsm);
-        }
+        sgm_line_any<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, slot, item - tb->slot_base[slot][s],
+                          b.Lvol + (size_t)slot * b.capacity, wsm, b.cells[1] == 2u);
     }
 }
 
@@ -191,7 +182,7 @@ SgmKernel sgm_kernel(int maxD, int warps) {
 
 size_t sgm_smem_bytes(int maxD, int warps) {
     const int L = lpl_for(maxD);
-    const int words = L == 2 ? sgm_mixed_words<2>() : (L == 4 ? sgm_mixed_words<4>() : sgm_mixed_words<8>());
+    const int words = L == 2 ? sgm_warp_words<2>() : (L == 4 ? sgm_warp_words<4>() : sgm_warp_words<8>());
     return (size_t)warps * words * sizeof(uint32_t);
 }
 
@@ -387,13 +378,13 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
             t.tile_base[i + 1] = t.tile_base[i] + t.tiles_x[i] * ((s.H + kCtH - 1) / kCtH);
             t.px_base[i + 1] = t.px_base[i] + s.n;
         }
-        // direction-major order of line quads: every stream's horizontal lines first
+        // direction-major line order: every stream's horizontal lines first
         int item = 0;
         for (int slot = 0; slot < p0.n_paths; ++slot) {
             for (int i = 0; i < n_streams; ++i) {
                 t.slot_base[slot][i] = item;
                 const BStream& s = b->h_streams[i];
-                item += slot <= 1 ? s.H : ((slot <= 3 ? s.W : s.W + s.H - 1) + 3) / 4;
+                item += slot <= 1 ? s.H : (slot <= 3 ? s.W : s.W + s.H - 1);
             }
             t.slot_base[slot][n_streams] = item;
         }

@@ -72,12 +72,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
     return r;
 }
 
-// Windows wider than this many labels leave the two-labels-per-lane fast path of an 8-lane line
-// group (sgm_line_group<8>); their count per row picks the aggregation layout (sgm_mode).
-constexpr int kNarrow8 = 16;
+// Windows wider than this many labels leave the narrow representation of the path aggregation;
+// their count per row is kept with the row totals (rowwide).
+constexpr int kNarrowMax = 32;
 
 // Row statistics written next to the windows: storage cells, true cells, pixels wider than
-// kNarrow8 (rowwide).
+// kNarrowMax (rowwide).
 __device__ __forceinline__ void row_totals(uint32_t acc, uint32_t acc_true, uint32_t acc_wide,
                                            int y, uint32_t* sh, uint32_t* __restrict__ rowsum,
                                            uint32_t* __restrict__ rowcells,
@@ -110,19 +110,18 @@ __device__ __forceinline__ void sanitize_row(const int16_t* __restrict__ lo_in,
         hi[i] = (int16_t)b;
         acc_true += (uint32_t)(b - a + 1);
         acc += block_cells(b - a + 1);
-        acc_wide += (b - a + 1 > kNarrow8) ? 1u : 0u;
+        acc_wide += (b - a + 1 > kNarrowMax) ? 1u : 0u;
     }
     row_totals(acc, acc_true, acc_wide, y, sh, rowsum, rowcells, rowwide);
 }
 
-// Lanes per path line for the aggregation of one image, from the storage cells, the pixel count
-// and the pixels wider than kNarrow8: 32 (one line per warp, labels packed up to 16 per lane)
-// when the windows average more than 24 cells of storage, else 8 when at most one pixel in 16
-// is wider than kNarrow8 labels, else 16. It decides only the work layout, never a result.
-__host__ __device__ __forceinline__ uint32_t sgm_mode(uint64_t storage, uint64_t n,
-                                                      uint64_t wide) {
-    if (storage > 24 * n) return 32u;
-    return wide * 16 <= n ? 8u : 16u;
+// Aggregation layout of one image, from the storage cells and the pixel count: 2 when the windows
+// average more than 24 cells of storage (every line takes the general walker), else 1 (each line
+// picks the narrow or the general walker from its own windows). It decides only the work layout,
+// never a result.
+__host__ __device__ __forceinline__ uint32_t sgm_mode(uint64_t storage, uint64_t n, uint64_t wide) {
+    (void)wide;
+    return storage > 24 * n ? 2u : 1u;
 }
 
 // Offsets of the ragged volume: pixel i's block starts at off[i] = sum of the (4-aligned) block
@@ -300,20 +299,14 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Shared memory of one warp of the aggregation kernels, in 32-bit words, for labels up to
-// DP = 32 * LPL. A warp walking one line: two label buffers (2 x DP uint16) and a ring of
-// kRingW slots of DP cost bytes. Groups of G lanes: per group two label buffers and a ring of
-// kRingG slots of DP cost bytes.
-constexpr int kRingW = 8, kPrefW = 6;  // ring slots and prefetch distance, one line per warp
-constexpr int kRingG = 4, kPrefG = 3;  // the same for a group of 8 or 16 lanes
+// DP = 32 * LPL: two label buffers (2 x DP uint16) shared by both walkers, then either the ring of
+// kRingW cost slots of DP bytes (sgm_line) or two blocks of 32 narrow cost slots of 32 bytes
+// (sgm_line_narrow).
+constexpr int kRingW = 8, kPrefW = 6;  // ring slots and prefetch distance of sgm_line
 template <int LPL>
-__host__ __device__ constexpr int sgm_warp_words() { return (32 * LPL) * (1 + kRingW / 4); }
-template <int LPL, int G>
-__host__ __device__ constexpr int sgm_group_words() { return (32 * LPL) * (1 + kRingG / 4); }
-template <int LPL>
-__host__ __device__ constexpr int sgm_mixed_words() {
-    return (32 / 8) * sgm_group_words<LPL, 8>() > sgm_warp_words<LPL>()
-               ? (32 / 8) * sgm_group_words<LPL, 8>()
-               : sgm_warp_words<LPL>();
+__host__ __device__ constexpr int sgm_warp_words() {
+    return (32 * LPL) + ((32 * LPL) * kRingW / 4 > 2 * 32 * 32 / 4 ? (32 * LPL) * kRingW / 4
+                                                                     : 2 * 32 * 32 / 4);
 }
 
 // One path line walked by a whole warp: direction `code`, line index `l` of that direction; Lv is
@@ -440,36 +433,121 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
         }
     };
 
+    // Software pipeline: at the top of step k the descriptor of pixel k and (narrow pixels) this
+    // lane's cost byte are in registers, prepared during step k - 1. A step first starts the
+    // neighbour shuffles of the narrow recurrence (the head of the dependent chain), then, while
+    // they are in flight, starts the copy of pixel k + PF, waits for pixel k + 1's copy and reads
+    // its descriptor and cost byte, and only then finishes pixel k. Runs of narrow pixels take a
+    // tight loop of their own.
     for (int u = 0; u < PF; ++u) issue(u);
-    // unrolled so that consecutive steps use different registers: a store or copy still reading
-    // its operands does not hold up the next step
-#pragma unroll 4
-    for (int k = 0; k < len; ++k) {
-        if (k > 0 && (k & 31) == 0) {
+    cp_async_wait<PF - 1>();
+    __syncwarp();
+    uint32_t o, lw;
+    desc_at(0, o, lw);
+    int c = (lane < (int)(lw >> 16)) ? (int)ring[lane] : 0;
+    // prepare pixel k + 1 (its copy landed, descriptor and cost byte in registers)
+    auto prepare_next = [&](int k, uint32_t& o_n, uint32_t& lw_n, int& c_n) {
+        issue(k + PF);  // into the slot of pixel k + PF - R, read two steps ago
+        cp_async_wait<PF - 1>();  // pixel k + 1's copy has landed ...
+        __syncwarp();             // ... for every lane's part of it
+        if (((k + 1) & 31) == 0) {
             dc0 = dc1;
             dc1 = dc2;
             ++blk;
             dc2 = ldesc(((blk + 2) << 5) + lane);
         }
-        uint32_t o, lw;
-        desc_at(k, o, lw);
-        const int lo = (int)(lw & 0xFFFFu);
-        const int w = (int)(lw >> 16);
-        cp_async_wait<PF - 1>();  // this pixel's copy (the oldest in flight) has landed
-        __syncwarp();             // ... for every lane's part of it
-        const uint8_t* cs = ring + (k & (R - 1)) * DP;
-        issue(k + PF);  // into the slot read two steps ago
-        if (w <= 32) {
-            // ------------------------------------------------------------ narrow step
-            const int c = lane < w ? (int)cs[lane] : 0;
-            int L;
-            if (k == 0) {
-                L = c;
-            } else if (loc == 0) {
+        desc_at(k + 1, o_n, lw_n);
+        c_n = (lane < (int)(lw_n >> 16)) ? (int)ring[((k + 1) & (R - 1)) * DP + lane] : 0;
+    };
+    int k = 0;
+    while (k < len) {
+        // ---------------------------------------------------------------- narrow runs
+        // consecutive narrow pixels after a narrow one: a tight loop without dispatch, unrolled so
+        // that consecutive steps use different registers (a store or copy still reading its
+        // operands does not hold up the next step)
+        if (k > 0 && loc == 0) {
+#pragma unroll 4
+            while (k < len && (int)(lw >> 16) <= 32) {
+                const int lo = (int)(lw & 0xFFFFu);
+                const int w = (int)(lw >> 16);
                 const int s_ = lane + (lo - qlo);
                 int vc = __shfl_sync(kFull, Nreg, s_ & 31);
                 int vl = __shfl_sync(kFull, Nreg, (s_ - 1) & 31);
                 int vr = __shfl_sync(kFull, Nreg, (s_ + 1) & 31);
+                uint32_t o_n, lw_n;
+                int c_n;
+                prepare_next(k, o_n, lw_n, c_n);
+                vc = ((unsigned)s_ < (unsigned)qw) ? vc : kInf;
+                vl = ((unsigned)(s_ - 1) < (unsigned)qw) ? vl : kInf;
+                vr = ((unsigned)(s_ + 1) < (unsigned)qw) ? vr : kInf;
+                int L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
+                L = lane < w ? L : kInf;
+                if (lane < w) Lv[o + lane] = (uint8_t)L;
+                m = (int)__reduce_min_sync(kFull, (unsigned)L);
+                Nreg = L;
+                qlo = lo;
+                qw = w;
+                o = o_n;
+                lw = lw_n;
+                c = c_n;
+                ++k;
+            }
+            if (k >= len) break;
+        }
+        // ---------------------------------------------------------------- full-range runs
+        // consecutive full-range pixels after a full-range one: the same, for the dense form
+        if (k > 0 && loc == 1) {
+#pragma unroll 2
+            while (k < len && (int)(lw >> 16) == D) {
+                uint32_t o_n, lw_n;
+                int c_n;
+                prepare_next(k, o_n, lw_n, c_n);
+                const uint8_t* cs = ring + (k & (R - 1)) * DP;
+                uint32_t c2[NP];
+                if constexpr (LPL == 2) {
+                    c2[0] = __byte_perm(*reinterpret_cast<const uint16_t*>(cs + 2 * lane), 0u,
+                                        0x4140);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < LPL / 4; ++r) {
+                        const uint32_t wd =
+                            *reinterpret_cast<const uint32_t*>(cs + LPL * lane + 4 * r);
+                        c2[2 * r] = __byte_perm(wd, 0u, 0x4140);
+                        c2[2 * r + 1] = __byte_perm(wd, 0u, 0x4342);
+                    }
+                }
+                uint32_t Lq[NP];
+#pragma unroll
+                for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[k2];
+                const int lmin = dense_step(Lq, c2);
+                emit_dense(o);
+                m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
+                o = o_n;
+                lw = lw_n;
+                c = c_n;
+                ++k;
+            }
+            qlo = 0;
+            qw = D;
+            if (k >= len) break;
+        }
+        // ---------------------------------------------------------------- any other step
+        const int lo = (int)(lw & 0xFFFFu);
+        const int w = (int)(lw >> 16);
+        const int s_ = lane + (lo - qlo);
+        int vc = __shfl_sync(kFull, Nreg, s_ & 31);
+        int vl = __shfl_sync(kFull, Nreg, (s_ - 1) & 31);
+        int vr = __shfl_sync(kFull, Nreg, (s_ + 1) & 31);
+        uint32_t o_n, lw_n;
+        int c_n;
+        prepare_next(k, o_n, lw_n, c_n);
+        const uint8_t* cs = ring + (k & (R - 1)) * DP;
+        if (w <= 32) {
+            // ------------------------------------------------------------ narrow step
+            int L;
+            if (k == 0) {
+                L = c;
+            } else if (loc == 0) {
                 vc = ((unsigned)s_ < (unsigned)qw) ? vc : kInf;
                 vl = ((unsigned)(s_ - 1) < (unsigned)qw) ? vl : kInf;
                 vr = ((unsigned)(s_ + 1) < (unsigned)qw) ? vr : kInf;
@@ -479,10 +557,10 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
                 const uint16_t* src16 = reinterpret_cast<const uint16_t*>(buf0 + qb * kBufPairs);
                 const int d = lo + lane;
                 const int qhi = qlo + qw - 1;
-                const int vc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
-                const int vl = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
-                const int vr = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
-                L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
+                const int uc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
+                const int ul = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
+                const int ur = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
+                L = c + min(min(min(ul, ur) + P1, uc), m + P2) - m;
             }
             L = lane < w ? L : kInf;
             if (lane < w) Lv[o + lane] = (uint8_t)L;
@@ -565,229 +643,170 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
         }
         qlo = lo;
         qw = w;
+        o = o_n;
+        lw = lw_n;
+        c = c_n;
+        ++k;
     }
     cp_async_wait<0>();  // the copies past the line end (empty groups) are retired
     __syncwarp();
 }
 
 // ---------------------------------------------------------------------------------------------
-// One path line walked by a group of G lanes (G = 8 or 16; 32 / G lines per warp), for the short
-// lines of images whose windows are mostly narrow. Lane j of the group holds the path costs of
-// labels lo + 2j and lo + 2j + 1 packed as 16-bit halves, so windows of up to 2G labels take one
-// step of packed arithmetic: the predecessor's values at d - 1 .. d + 2 come from three shuffles
-// of the predecessor's pairs at a group-uniform offset and a byte permutation chosen by the
-// offset's parity. Labels outside a window carry at least kInf. Wider windows walk their labels in
-// chunks of 2G through the group's two label buffers (absolute disparity index, ping-pong).
-// Costs arrive through the group's ring of kRingG shared-memory slots, kPrefG pixels ahead. The
-// groups of a warp step together (a group with a shorter line, or none, idles to the end) and take
-// their minima by full-warp reductions; shuffles and the wide path synchronise the group alone.
-// gsm is the group's shared memory (sgm_group_words); l < 0: no line for this group.
+// One path line of narrow windows walked by a whole warp (lane j <-> label lo + j, as the narrow
+// representation of sgm_line), with the prefetch done 32 pixels at a time: at the start of each
+// block of 32 pixels every lane fetches the descriptor of one pixel two blocks ahead and copies
+// the costs of one pixel of the next block into its 32-byte slot (cp.async), so that a step is
+// the recurrence alone: two shuffles for its descriptor, one shared load for its cost, three
+// shuffles for the predecessor, the min chain, one store and one reduction. Windows wider than 32
+// take a slow step (costs read straight from global memory, predecessor through the label
+// buffers). For lines with few such pixels.
 // ---------------------------------------------------------------------------------------------
-template <int LPL, int G>
-__device__ __forceinline__ void sgm_line_group(const uint8_t* __restrict__ C,
-                                               const uint2* __restrict__ desc, int W, int Hh,
-                                               int D, int P1, int P2, int code, int l,
-                                               uint8_t* __restrict__ Lv, uint32_t* const gsm) {
-    static_assert(G == 8 || G == 16, "group of 8 or 16 lanes");
+template <int LPL>
+__device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
+                                                const uint2* __restrict__ desc, int W, int Hh,
+                                                int D, int P1, int P2, int code, int l,
+                                                uint8_t* __restrict__ Lv, uint32_t* const wsm) {
     constexpr int DP = 32 * LPL;
-    constexpr int NW = 2 * G;  // widest window of the packed fast path
-    constexpr int R = kRingG, PF = kPrefG;
-    uint16_t* const sbuf = reinterpret_cast<uint16_t*>(gsm);          // 2 x DP labels
-    uint8_t* const ring = reinterpret_cast<uint8_t*>(gsm + DP);       // R slots of DP bytes
+    uint16_t* const buf16 = reinterpret_cast<uint16_t*>(wsm);       // 2 x DP labels
+    uint8_t* const cblk = reinterpret_cast<uint8_t*>(wsm + DP);     // 2 blocks x 32 x 32 bytes
     const int lane = threadIdx.x & 31;
-    const int gl = lane & (G - 1);
-    const int gi = lane / G;
-    const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
-    int i0 = 0, step = 0, len = 0;  // l < 0: this group has no line and only keeps step
-    if (l >= 0) line_geometry(code, l, W, Hh, i0, step, len);
-    // the groups of the warp step together (the per-group minimum is taken by full-warp
-    // reductions, far faster than a reduction over a partial mask): as many steps as the longest
-    const int steps = (int)__reduce_max_sync(kFull, (unsigned)len);
+    int i0, step, len;
+    line_geometry(code, l, W, Hh, i0, step, len);
+    (void)D;
 
-    const uint32_t P1P1 = ((uint32_t)P1 << 16) | (uint32_t)P1;
-    const uint32_t P2P2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
-
-    // descriptors: dA holds pixels [G*blk, G*blk + G) (one per lane), dB the next block, dC the
-    // one after (in flight)
     auto ldesc = [&](int kk) -> uint2 {
         return kk < len ? __ldg(desc + (i0 + kk * step)) : make_uint2(0u, 0u);
     };
-    uint2 dA = ldesc(gl), dB = ldesc(G + gl), dC = ldesc(2 * G + gl);
-    int blk = 0;
-    auto desc_at = [&](int kk, uint32_t& o_, uint32_t& lw_) {  // kk in block blk or blk + 1
-        const bool first = (kk / G) == blk;
-        o_ = __shfl_sync(gmask, first ? dA.x : dB.x, kk & (G - 1), G);
-        lw_ = __shfl_sync(gmask, first ? dA.y : dB.y, kk & (G - 1), G);
-    };
-    auto issue = [&](int kk) {
-        uint32_t o_, lw_;
-        desc_at(kk, o_, lw_);
-        const int w_ = kk < len ? (int)(lw_ >> 16) : 0;
-        uint8_t* slot = ring + (kk & (R - 1)) * DP;
-#pragma unroll
-        for (int t = 0; t < (DP + 4 * G - 1) / (4 * G); ++t) {
-            const int j = gl + G * t;
-            if (4 * j < w_) cp_async4(slot + 4 * j, C + o_ + 4 * j);
+    // this lane copies the costs of its pixel of block b (narrow windows only) into its slot
+    auto copy_block = [&](int b, uint2 d) {
+        const int w_ = (int)(d.y >> 16);
+        if (w_ <= 32) {
+            uint8_t* dst = cblk + (b & 1) * 1024 + lane * 32;
+            const uint8_t* src = C + d.x;
+            for (int i = 0; 4 * i < w_; ++i) cp_async4(dst + 4 * i, src + 4 * i);
         }
         cp_async_commit();
     };
-    // (c(d), c(d+1)) as 16-bit halves, kInf for labels at or beyond w (j = first label's index)
-    auto cost_pair = [&](uint32_t raw, int j, int w_) -> uint32_t {
-        const uint32_t c2 = __byte_perm(raw, 0u, 0x4140);
-        return j >= w_ ? kInf2 : (j + 1 >= w_ ? (c2 | ((uint32_t)kInf << 16)) : c2);
-    };
-    auto relax = [&](uint32_t prev, uint32_t cen, uint32_t nxt, uint32_t c2, uint32_t mm,
-                     uint32_t mP2) -> uint32_t {
-        uint32_t t = vmin2(prev, nxt) + P1P1;
-        t = vmin2(vmin2(t, cen), mP2);
-        return (c2 + t) - mm;  // every half of t is >= m: no borrow between the halves
-    };
 
-    uint32_t Q = kInf2;  // predecessor pair (labels qlo + 2gl, +1) while held in registers
-    int qlo = 0, qw = 0, qb = 0;
-    bool in_regs = true;
-    uint32_t mm = 0, mP2 = 0;
+    const int nblk = (len + 31) >> 5;
+    uint2 dA = ldesc(lane), dB = ldesc(32 + lane);
+    copy_block(0, dA);
+    int qlo = 0, qw = 0, m = 0, Nreg = kInf, qb = 0;
+    bool in_regs = true;  // predecessor in Nreg (else in label buffer qb, absolute index)
 
-    for (int u = 0; u < PF; ++u) issue(u);
-#pragma unroll 2
-    for (int k = 0; k < steps; ++k) {
-        if (k > 0 && (k & (G - 1)) == 0) {
-            dA = dB;
-            dB = dC;
-            ++blk;
-            dC = ldesc((blk + 2) * G + gl);
-        }
-        uint32_t o, lw;
-        desc_at(k, o, lw);  // past the line's end: 0 (an empty window, nothing stored)
-        const int lo = (int)(lw & 0xFFFFu);
-        const int w = (int)(lw >> 16);
-        cp_async_wait<PF - 1>();
-        __syncwarp(gmask);
-        const uint8_t* cs = ring + (k & (R - 1)) * DP;
-        issue(k + PF);  // into the slot read the step before
-        uint32_t pm;
-        if (w <= NW) {
-            // ------------------------------------------------------------ packed narrow step
-            const uint32_t raw =
-                2 * gl < w ? (uint32_t)*reinterpret_cast<const uint16_t*>(cs + 2 * gl) : 0u;
-            const uint32_t c2 = cost_pair(raw, 2 * gl, w);
-            uint32_t L;
-            if (k == 0) {
-                L = c2;
-            } else {
-                uint32_t prev, cen, nxt;
-                const int r0 = lo - qlo - 1;  // predecessor index of label lo - 1
-                if (in_regs) {
-                    const int a = gl + (r0 >> 1);
-                    uint32_t A = __shfl_sync(gmask, Q, a, G);
-                    uint32_t B = __shfl_sync(gmask, Q, a + 1, G);
-                    uint32_t E = __shfl_sync(gmask, Q, a + 2, G);
-                    A = (unsigned)a < (unsigned)G ? A : kInf2;
-                    B = (unsigned)(a + 1) < (unsigned)G ? B : kInf2;
-                    E = (unsigned)(a + 2) < (unsigned)G ? E : kInf2;
-                    const bool odd = (r0 & 1) != 0;
-                    const uint32_t s1 = odd ? 0x5432u : 0x3210u;
-                    prev = __byte_perm(A, B, s1);
-                    cen = __byte_perm(A, B, odd ? 0x7654u : 0x5432u);
-                    nxt = __byte_perm(B, E, s1);
-                } else {
-                    const uint16_t* src = sbuf + qb * DP;
-                    const int d0 = lo + 2 * gl, qhi = qlo + qw - 1;
-                    const uint32_t v0 = (d0 - 1 >= qlo && d0 - 1 <= qhi) ? src[d0 - 1] : kInf;
-                    const uint32_t v1 = (d0 >= qlo && d0 <= qhi) ? src[d0] : kInf;
-                    const uint32_t v2 = (d0 + 1 >= qlo && d0 + 1 <= qhi) ? src[d0 + 1] : kInf;
-                    const uint32_t v3 = (d0 + 2 >= qlo && d0 + 2 <= qhi) ? src[d0 + 2] : kInf;
-                    prev = v0 | (v1 << 16);
-                    cen = v1 | (v2 << 16);
-                    nxt = v2 | (v3 << 16);
-                }
-                L = relax(prev, cen, nxt, c2, mm, mP2);
-            }
-            if (2 * gl < w)
-                *reinterpret_cast<uint16_t*>(Lv + o + 2 * gl) = (uint16_t)__byte_perm(L, 0u, 0x0020);
-            pm = min(L & 0xFFFFu, L >> 16);
-            Q = L;
-            in_regs = true;
-        } else {
-            // ------------------------------------------------------------ wide step (chunks)
-            if (k > 0 && in_regs) {
-                __syncwarp(gmask);  // earlier reads of buffer qb are done
-                const int d0 = qlo + 2 * gl;
-                if (2 * gl < qw) sbuf[qb * DP + d0] = (uint16_t)(Q & 0xFFFFu);
-                if (2 * gl + 1 < qw) sbuf[qb * DP + d0 + 1] = (uint16_t)(Q >> 16);
-                __syncwarp(gmask);
-            }
-            const uint16_t* src = sbuf + qb * DP;
-            uint16_t* dst = sbuf + (qb ^ 1) * DP;
-            const int qhi = qlo + qw - 1;
-            pm = (uint32_t)kInf;
-            for (int j0 = 0; j0 < w; j0 += NW) {
-                const int j = j0 + 2 * gl;
-                const int d0 = lo + j;
-                const uint32_t raw = j < w ? (uint32_t)*reinterpret_cast<const uint16_t*>(cs + j) : 0u;
-                const uint32_t c2 = cost_pair(raw, j, w);
-                uint32_t L;
+    for (int b = 0; b < nblk; ++b) {
+        __syncwarp();  // reads of the buffer about to be refilled are done
+        copy_block(b + 1, dB);
+        const uint2 dC = ldesc(((b + 2) << 5) + lane);
+        cp_async_wait<1>();  // this block's copies have landed ...
+        __syncwarp();        // ... for every lane
+        const uint8_t* cb = cblk + (b & 1) * 1024;
+        const int kend = min(32, len - (b << 5));
+#pragma unroll 4
+        for (int u = 0; u < kend; ++u) {
+            const int k = (b << 5) + u;
+            const uint32_t o = __shfl_sync(kFull, dA.x, u);
+            const uint32_t lw = __shfl_sync(kFull, dA.y, u);
+            const int lo = (int)(lw & 0xFFFFu);
+            const int w = (int)(lw >> 16);
+            if (w <= 32) {
+                const int c = lane < w ? (int)cb[u * 32 + lane] : 0;
+                int L;
                 if (k == 0) {
-                    L = c2;
+                    L = c;
+                } else if (in_regs) {
+                    const int s_ = lane + (lo - qlo);
+                    int vc = __shfl_sync(kFull, Nreg, s_ & 31);
+                    int vl = __shfl_sync(kFull, Nreg, (s_ - 1) & 31);
+                    int vr = __shfl_sync(kFull, Nreg, (s_ + 1) & 31);
+                    vc = ((unsigned)s_ < (unsigned)qw) ? vc : kInf;
+                    vl = ((unsigned)(s_ - 1) < (unsigned)qw) ? vl : kInf;
+                    vr = ((unsigned)(s_ + 1) < (unsigned)qw) ? vr : kInf;
+                    L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
                 } else {
-                    const uint32_t v0 = (d0 - 1 >= qlo && d0 - 1 <= qhi) ? src[d0 - 1] : kInf;
-                    const uint32_t v1 = (d0 >= qlo && d0 <= qhi) ? src[d0] : kInf;
-                    const uint32_t v2 = (d0 + 1 >= qlo && d0 + 1 <= qhi) ? src[d0 + 1] : kInf;
-                    const uint32_t v3 = (d0 + 2 >= qlo && d0 + 2 <= qhi) ? src[d0 + 2] : kInf;
-                    L = relax(v0 | (v1 << 16), v1 | (v2 << 16), v2 | (v3 << 16), c2, mm, mP2);
+                    const uint16_t* src16 = buf16 + qb * DP;
+                    const int d = lo + lane, qhi = qlo + qw - 1;
+                    const int uc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
+                    const int ul = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
+                    const int ur = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
+                    L = c + min(min(min(ul, ur) + P1, uc), m + P2) - m;
                 }
-                if (j < w) {
-                    dst[d0] = (uint16_t)(L & 0xFFFFu);
-                    if (j + 1 < w) dst[d0 + 1] = (uint16_t)(L >> 16);
-                    *reinterpret_cast<uint16_t*>(Lv + o + j) = (uint16_t)__byte_perm(L, 0u, 0x0020);
+                L = lane < w ? L : kInf;
+                if (lane < w) Lv[o + lane] = (uint8_t)L;
+                m = (int)__reduce_min_sync(kFull, (unsigned)L);
+                Nreg = L;
+                in_regs = true;
+            } else {
+                // ---------------------------------------------------- slow step: wide window
+                if (k > 0 && in_regs) {
+                    __syncwarp();  // earlier reads of buffer qb are done
+                    if (lane < qw) buf16[qb * DP + qlo + lane] = (uint16_t)Nreg;
+                    __syncwarp();
                 }
-                pm = min(pm, min(L & 0xFFFFu, L >> 16));
+                const uint16_t* src16 = buf16 + qb * DP;
+                uint16_t* dst16 = buf16 + (qb ^ 1) * DP;
+                const int qhi = qlo + qw - 1;
+                int lmin = kInf;
+                for (int j0 = 0; j0 < w; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool act = j < w;
+                    const int d = lo + j;
+                    const int c = act ? (int)__ldg(C + o + j) : 0;
+                    int L;
+                    if (k == 0) {
+                        L = c;
+                    } else {
+                        const int uc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
+                        const int ul = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
+                        const int ur = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
+                        L = c + min(min(min(ul, ur) + P1, uc), m + P2) - m;
+                    }
+                    L = act ? L : kInf;
+                    if (act) {
+                        dst16[d] = (uint16_t)L;
+                        Lv[o + j] = (uint8_t)L;
+                    }
+                    lmin = min(lmin, L);
+                }
+                m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
+                qb ^= 1;
+                in_regs = false;
+                __syncwarp();
             }
-            __syncwarp(gmask);  // dst complete, src reads done
-            qb ^= 1;
-            in_regs = false;
+            qlo = lo;
+            qw = w;
         }
-        // the minimum over each group, from one full-warp reduction per group
-        uint32_t m = 0;
-#pragma unroll
-        for (int g = 0; g < 32 / G; ++g) {
-            const uint32_t mg = __reduce_min_sync(kFull, gi == g ? pm : 0xFFFFFFFFu);
-            m = gi == g ? mg : m;
-        }
-        mm = (m << 16) | m;
-        mP2 = mm + P2P2;
-        qlo = lo;
-        qw = w;
+        dA = dB;
+        dB = dC;
     }
     cp_async_wait<0>();
-    __syncwarp();  // the group's buffers may be reused by its next line
+    __syncwarp();
 }
 
-// The lines [l0, l0 + 4) of direction `code` (those below nl) of one image, walked by one warp in
-// the layout `mode` (lanes per line, sgm_mode). `wsm` is the warp's shared memory
-// (sgm_mixed_words).
+// One path line of one image: lines with at most one pixel in 8 wider than 32 labels take the
+// narrow walker, the others the general one (the choice changes the work, never the result).
+// `dense_image`: the image's windows are mostly wide (skip the scan).
 template <int LPL>
-__device__ __forceinline__ void sgm_line_quad(const uint8_t* __restrict__ C,
-                                              const uint2* __restrict__ desc, int W, int Hh, int D,
-                                              int P1, int P2, int code, int l0, int nl,
-                                              uint32_t mode, uint8_t* __restrict__ Lv,
-                                              uint32_t* wsm) {
-    const int lane = threadIdx.x & 31;
-    if (mode == 8u) {
-        const int l = l0 + (lane >> 3);
-        sgm_line_group<LPL, 8>(C, desc, W, Hh, D, P1, P2, code, l < nl ? l : -1, Lv,
-                               wsm + (lane >> 3) * sgm_group_words<LPL, 8>());
-    } else if (mode == 16u) {
-        for (int r = 0; r < 2; ++r) {
-            const int l = l0 + 2 * r + (lane >> 4);
-            sgm_line_group<LPL, 16>(C, desc, W, Hh, D, P1, P2, code, l < nl ? l : -1, Lv,
-                                    wsm + (lane >> 4) * sgm_group_words<LPL, 16>());
+__device__ __forceinline__ void sgm_line_any(const uint8_t* __restrict__ C,
+                                             const uint2* __restrict__ desc, int W, int Hh, int D,
+                                             int P1, int P2, int code, int l,
+                                             uint8_t* __restrict__ Lv, uint32_t* const wsm,
+                                             bool dense_image) {
+    if (!dense_image) {
+        const int lane = threadIdx.x & 31;
+        int i0, step, len;
+        line_geometry(code, l, W, Hh, i0, step, len);
+        int wide = 0;
+        for (int kk = lane; kk < len; kk += 32)
+            wide += (int)(__ldg(desc + (i0 + kk * step)).y >> 16) > 32 ? 1 : 0;
+        wide = (int)__reduce_add_sync(kFull, (unsigned)wide);
+        if (wide * 8 <= len) {
+            sgm_line_narrow<LPL>(C, desc, W, Hh, D, P1, P2, code, l, Lv, wsm);
+            return;
         }
-    } else {
-        for (int r = 0; r < 4 && l0 + r < nl; ++r) sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code,
-                                                                 l0 + r, Lv, wsm);
     }
-    __syncwarp();
+    sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code, l, Lv, wsm);
 }
 
 constexpr int kSelThreads = 512;

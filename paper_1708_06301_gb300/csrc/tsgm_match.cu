@@ -34,75 +34,27 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
                 threadIdx.x & 7, (gridDim.x * blockDim.x) >> 3);
 }
 
-// Path aggregation of one image: all lines of all directions. The layout word written with the
-// offsets (sgm_mode) picks one of two kernels, both launched, the other one returning at once:
-//   k_sgm_warp   (layout 32): one warp per line;
-//   k_sgm_mixed  (layouts 8, 16): the horizontal lines (the longest, whose chains bound the
-//                launch) one warp each, the lines of the other directions 32 / G per warp, one
-//                group of G lanes each.
+// Path aggregation of one image: all lines of all directions in one launch, one warp per line
+// (horizontal lines first: they are the longest chains). Each line picks its walker from its
+// windows unless the layout word written with the offsets (sgm_mode) says the image is mostly
+// wide.
 template <int LPL>
-__global__ void __launch_bounds__(kSgmWarps * 32) k_sgm_warp(const uint8_t* __restrict__ C,
-                                                             const uint2* __restrict__ desc, int W,
-                                                             int Hh, int D, int P1, int P2,
-                                                             SgmLines lines,
-                                                             uint8_t* __restrict__ Lvol,
-                                                             uint64_t vol_stride,
-                                                             const uint32_t* __restrict__ mode_word) {
+__global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restrict__ C,
+                                                        const uint2* __restrict__ desc, int W,
+                                                        int Hh, int D, int P1, int P2,
+                                                        SgmLines lines, uint8_t* __restrict__ Lvol,
+                                                        uint64_t vol_stride,
+                                                        const uint32_t* __restrict__ mode_word) {
     extern __shared__ uint32_t sgm_smem32[];
-    if (__ldg(mode_word) != 32u) return;
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kSgmWarps + wib;
     if (gw >= lines.start[lines.nslots]) return;
     int slot = 0;
     while (gw >= lines.start[slot + 1]) ++slot;
     const int code = lines.code[slot];
-    sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code, gw - lines.start[slot],
-                  Lvol + (size_t)code * vol_stride, sgm_smem32 + wib * sgm_warp_words<LPL>());
-}
-
-template <int LPL>
-__global__ void __launch_bounds__(kSgmWarps * 32) k_sgm_mixed(const uint8_t* __restrict__ C,
-                                                              const uint2* __restrict__ desc, int W,
-                                                              int Hh, int D, int P1, int P2,
-                                                              SgmLines lines,
-                                                              uint8_t* __restrict__ Lvol,
-                                                              uint64_t vol_stride,
-                                                              const uint32_t* __restrict__ mode_word) {
-    extern __shared__ uint32_t sgm_smem32[];
-    const uint32_t mode = __ldg(mode_word);
-    if (mode == 32u) return;
-    const int wib = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    uint32_t* wsm = sgm_smem32 + wib * sgm_mixed_words<LPL>();
-    int item = blockIdx.x * kSgmWarps + wib;
-    for (int slot = 0; slot < lines.nslots; ++slot) {
-        const int code = lines.code[slot];
-        const int cnt = lines.start[slot + 1] - lines.start[slot];
-        uint8_t* Lv = Lvol + (size_t)code * vol_stride;
-        if (code <= 1) {
-            if (item < cnt) {
-                sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code, item, Lv, wsm);
-                return;
-            }
-            item -= cnt;
-            continue;
-        }
-        const int per = mode == 16u ? 2 : 4;
-        const int nit = (cnt + per - 1) / per;
-        if (item < nit) {
-            if (mode == 16u) {
-                const int l = item * 2 + (lane >> 4);
-                sgm_line_group<LPL, 16>(C, desc, W, Hh, D, P1, P2, code, l < cnt ? l : -1, Lv,
-                                        wsm + (lane >> 4) * sgm_group_words<LPL, 16>());
-            } else {
-                const int l = item * 4 + (lane >> 3);
-                sgm_line_group<LPL, 8>(C, desc, W, Hh, D, P1, P2, code, l < cnt ? l : -1, Lv,
-                                       wsm + (lane >> 3) * sgm_group_words<LPL, 8>());
-            }
-            return;
-        }
-        item -= nit;
-    }
+    sgm_line_any<LPL>(C, desc, W, Hh, D, P1, P2, code, gw - lines.start[slot],
+                      Lvol + (size_t)code * vol_stride, sgm_smem32 + wib * sgm_warp_words<LPL>(),
+                      __ldg(mode_word) == 2u);
 }
 
 template <int NPATHS>
@@ -141,24 +93,8 @@ static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int 
                                 int P1, int P2, const SgmLines& L, uint8_t* Lvol,
                                 uint64_t vol_stride, const uint32_t* mode, cudaStream_t st) {
     const int nlines = L.start[L.nslots];
-    const size_t smem_w = (size_t)kSgmWarps * sgm_warp_words<LPL>() * sizeof(uint32_t);
-    const size_t smem_m = (size_t)kSgmWarps * sgm_mixed_words<LPL>() * sizeof(uint32_t);
-    if (smem_w > 48 * 1024) {  // opt in to more than 48 KB of dynamic shared memory
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_sgm_warp<LPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w);
-        if (e != cudaSuccess) return e;
-    }
-    if (smem_m > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_sgm_mixed<LPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
-        if (e != cudaSuccess) return e;
-    }
-    // items of the mixed layout: every horizontal line, and pairs (layout 16) of the other lines
-    const int horiz = L.start[2 < L.nslots ? 2 : L.nslots];
-    const int items_m = horiz + (nlines - horiz + 1) / 2;
-    k_sgm_warp<LPL><<<(nlines + kSgmWarps - 1) / kSgmWarps, kSgmWarps * 32, smem_w, st>>>(
-        C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, mode);
-    k_sgm_mixed<LPL><<<(items_m + kSgmWarps - 1) / kSgmWarps, kSgmWarps * 32, smem_m, st>>>(
+    const size_t smem = (size_t)kSgmWarps * sgm_warp_words<LPL>() * sizeof(uint32_t);
+    k_sgm<LPL><<<(nlines + kSgmWarps - 1) / kSgmWarps, kSgmWarps * 32, smem, st>>>(
         C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, mode);
     return cudaGetLastError();
 }

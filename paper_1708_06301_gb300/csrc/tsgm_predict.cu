@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
         hi[i] = (int16_t)b;
         acc_true += (uint32_t)(b - a + 1);
         acc += block_cells(b - a + 1);
-        acc_wide += (b - a + 1 > kNarrow8) ? 1u : 0u;
+        acc_wide += (b - a + 1 > kNarrowMax) ? 1u : 0u;
     }
     row_totals(acc, acc_true, acc_wide, y, sh, rowsum, rowcells, rowwide);
 }

@@ -123,22 +123,27 @@ def test_windows_bitexact(tsgm, W, H, D):
 # matching stages on random windows (narrow, wide and full-range mixed)
 # ----------------------------------------------------------------------------------------------
 
-# W, H, D, census, paths, windows, lanes per path line the aggregation must pick
+# W, H, D, census, paths, windows, aggregation layout the image must get (1: each line picks the
+# narrow or the general walker, 2: every line takes the general walker)
 #   ("rand", w_min, w_max, full_frac): independent random windows (neighbours rarely overlap)
 #   ("mixed", narrow, wide, wide_frac, full_frac): windows around a smooth surface (overlapping)
+#   ("border", narrow, cols): narrow windows around a smooth surface, full range in the first and
+#                             last `cols` columns
 CASES = [
-    (97, 45, 64, (5, 5), 4, ("rand", 1, 24, 0.2), 16),
-    (131, 37, 128, (9, 7), 8, ("rand", 1, 40, 0.25), 32),
-    (64, 32, 256, (9, 7), 8, ("rand", 20, 80, 0.1), 32),
-    (200, 3, 64, (5, 5), 8, ("rand", 1, 64, 0.5), 32),
-    (3, 70, 32, (5, 5), 8, ("rand", 1, 32, 0.3), 16),
-    (1, 1, 16, (5, 5), 8, ("rand", 1, 16, 1.0), 8),
-    (50, 20, 1, (5, 5), 8, ("rand", 1, 1, 0.0), 8),
-    (211, 29, 128, (9, 7), 8, ("mixed", (1, 16), (17, 40), 0.02, 0.03), 8),
-    (173, 31, 64, (5, 5), 4, ("mixed", (4, 24), (25, 40), 0.0, 0.02), 16),
-    (97, 41, 256, (9, 7), 8, ("mixed", (1, 16), (17, 60), 0.02, 0.02), 8),
-    (160, 24, 128, (9, 7), 8, ("mixed", (3, 12), (17, 32), 0.0, 0.0), 8),
-    (77, 50, 64, (5, 5), 8, ("mixed", (4, 24), (17, 64), 0.05, 0.05), 16),
+    (97, 45, 64, (5, 5), 4, ("rand", 1, 24, 0.2), 1),
+    (131, 37, 128, (9, 7), 8, ("rand", 1, 40, 0.25), 2),
+    (64, 32, 256, (9, 7), 8, ("rand", 20, 80, 0.1), 2),
+    (200, 3, 64, (5, 5), 8, ("rand", 1, 64, 0.5), 2),
+    (3, 70, 32, (5, 5), 8, ("rand", 1, 32, 0.3), 1),
+    (1, 1, 16, (5, 5), 8, ("rand", 1, 16, 1.0), 1),
+    (50, 20, 1, (5, 5), 8, ("rand", 1, 1, 0.0), 1),
+    (211, 29, 128, (9, 7), 8, ("mixed", (1, 16), (17, 40), 0.02, 0.03), 1),
+    (173, 31, 64, (5, 5), 4, ("mixed", (4, 24), (25, 40), 0.0, 0.02), 1),
+    (97, 41, 256, (9, 7), 8, ("mixed", (1, 16), (17, 60), 0.02, 0.02), 1),
+    (160, 24, 128, (9, 7), 8, ("mixed", (3, 12), (17, 32), 0.0, 0.0), 1),
+    # full range in the border columns: those columns' lines take the general walker
+    (150, 40, 128, (9, 7), 8, ("border", (3, 12), 6), 1),
+    (77, 50, 64, (5, 5), 8, ("mixed", (4, 24), (17, 64), 0.05, 0.05), 1),
 ]
 
 
@@ -146,13 +151,21 @@ def case_windows(W, H, D, spec):
     if spec[0] == "rand":
         _, wmin, wmax, ff = spec
         return synth.random_windows(W + H, W, H, D, wmin, min(wmax, D), full_frac=ff)
+    if spec[0] == "border":
+        _, narrow, cols = spec
+        lo, hi = synth.mixed_windows(W * 3 + H, W, H, D, narrow, (17, 32), 0.0, 0.0)
+        lo, hi = lo.copy(), hi.copy()
+        for sl in (slice(0, cols), slice(W - cols, W)):
+            lo[:, sl] = 0
+            hi[:, sl] = D - 1
+        return lo, hi
     _, narrow, wide, wf, ff = spec
     return synth.mixed_windows(W * 3 + H, W, H, D, narrow, wide, wf, ff)
 
 
 @pytest.mark.parametrize("case", CASES)
 def test_match_stages_bitexact(tsgm, case):
-    W, H, D, (cw, ch), npaths, spec, lanes = case
+    W, H, D, (cw, ch), npaths, spec, layout = case
     seq_l, seq_r = synth.random_images(W * 7 + H, W, H)
     # make the right image a shifted copy so that matching has structure
     right = np.roll(seq_l, -min(5, D - 1), axis=1)
@@ -184,7 +197,7 @@ def test_match_stages_bitexact(tsgm, case):
     prm = oparams(W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths)
     o = oracle.match(seq_l, right, lo, hi, prm, keep=True)
     assert n == int(o["off"][-1]) == int(counts[0])
-    assert int(counts[1]) == lanes
+    assert int(counts[1]) == layout
     assert np.array_equal(offg, padded_offsets(lo, hi))
     assert np.array_equal(g["C"], o["C"])
     assert np.array_equal(g["S"], o["S"])
