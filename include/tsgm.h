@@ -187,11 +187,8 @@ typedef enum {
     TSGM_BUF_WINDOWS_HI = 10,
     TSGM_BUF_PRED_D = 11,   /* float [n]      prediction of the last tsgm_frame            */
     TSGM_BUF_PRED_P = 12,
-    TSGM_BUF_COUNTS = 13    /* uint32 [2]     of the last match: [0] true window cells, [1] the
-                                              aggregation layout chosen from the windows: 1 each
-                                              path line picks a walker for narrow or for any
-                                              windows, 2 every line takes the latter (results
-                                              do not depend on it)                           */
+    TSGM_BUF_COUNTS = 13    /* uint32 [2]     of the last match: [0] true window cells, [1] pixels
+                                              whose window is wider than 32 labels          */
 } tsgm_buffer;
 
 /* Copy an internal buffer (device to device, on the context stream) into dst. `count` is the

@@ -226,7 +226,7 @@ tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* righ
     stage_end(ctx, TSGM_STAGE_COST);
     stage_begin(ctx, TSGM_STAGE_SGM);
     TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->Lvol,
-                           ctx->max_cells, ctx->cells + 1, ctx->stream),
+                           ctx->max_cells, ctx->stream),
                 "sgm");
     stage_end(ctx, TSGM_STAGE_SGM);
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;

@@ -41,7 +41,7 @@ struct BStream {
     uint32_t* off;
     uint32_t* rowsum;
     uint32_t* rowcells;  // true cells per row, then (at + H) pixels wider than kNarrowMax per row
-    uint32_t* cells;     // [0] true cells, [1] aggregation layout (sgm_mode)
+    uint32_t* cells;     // [0] true cells, [1] pixels wider than kNarrowMax
     uint32_t* status;  // 0 ok, 1: the windows need more cells than the stream's storage
     uint8_t* C;
     uint8_t* Lvol;
@@ -54,9 +54,10 @@ struct BTable {
     int tile_base[kMaxStreams + 1];  // prefix of census tiles (one image)
     int px_base[kMaxStreams + 1];    // prefix of pixels
     int tiles_x[kMaxStreams];
-    // path lines, direction-major: items of stream i in slot s are
-    // [slot_base[s][i], slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]
-    int slot_base[8][kMaxStreams + 1];
+    // pairs of opposite path lines, direction-major: slot s holds the lines of directions 2s and
+    // 2s + 1; items of stream i in slot s are [slot_base[s][i], slot_base[s][i+1]);
+    // slot_base[s][ns] == slot_base[s+1][0]
+    int slot_base[4][kMaxStreams + 1];
     int total_lines;
 };
 
@@ -112,27 +113,30 @@ __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
     }
 }
 
-// persistent path aggregation: warps take path lines from a global counter until none is left;
-// each line picks its walker from its windows unless its stream is mostly wide (sgm_mode)
+// persistent path aggregation: warps take items from a global counter until none is left; each
+// pair of opposite path lines (one geometric line) is two items, its twins (see sgm_pair)
 template <int LPL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__ st,
-                                                     const BTable* __restrict__ tb, int n_paths,
+                                                     const BTable* __restrict__ tb, int n_pairs,
                                                      int P1, int P2, int* __restrict__ counter) {
     extern __shared__ uint32_t sgm_smem32[];
-    uint32_t* wsm = sgm_smem32 + (threadIdx.x >> 5) * sgm_warp_words<LPL>();
+    uint32_t* wsm = sgm_smem32 + (threadIdx.x >> 5) * sgm_pair_words<LPL>();
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(counter, 1);
         item = __shfl_sync(kFull, item, 0);
-        if (item >= tb->total_lines) return;
+        if (item >= 2 * tb->total_lines) return;
+        const int pitem = item >> 1;  // two items (twins) per pair of lines
         int slot = 0;
-        while (slot + 1 < n_paths && item >= tb->slot_base[slot + 1][0]) ++slot;
-        const int s = find_stream(tb->slot_base[slot], tb->ns, item);
+        while (slot + 1 < n_pairs && pitem >= tb->slot_base[slot + 1][0]) ++slot;
+        const int s = find_stream(tb->slot_base[slot], tb->ns, pitem);
         const BStream& b = st[s];
         if (*b.status != 0u) continue;
-        sgm_line_any<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, slot, item - tb->slot_base[slot][s],
-                          b.Lvol + (size_t)slot * b.capacity, wsm, b.cells[1] == 2u);
+        const int code = 2 * slot;
+        sgm_pair<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, code, pitem - tb->slot_base[slot][s],
+                      b.Lvol + (size_t)code * b.capacity, b.Lvol + (size_t)(code + 1) * b.capacity,
+                      wsm, item & 1);
     }
 }
 
@@ -182,7 +186,7 @@ SgmKernel sgm_kernel(int maxD, int warps) {
 
 size_t sgm_smem_bytes(int maxD, int warps) {
     const int L = lpl_for(maxD);
-    const int words = L == 2 ? sgm_warp_words<2>() : (L == 4 ? sgm_warp_words<4>() : sgm_warp_words<8>());
+    const int words = L == 2 ? sgm_pair_words<2>() : (L == 4 ? sgm_pair_words<4>() : sgm_pair_words<8>());
     return (size_t)warps * words * sizeof(uint32_t);
 }
 
@@ -251,7 +255,7 @@ cudaError_t enqueue_step(tsgm_batch* b, int shape, bool timed = false) {
     const SgmShape sh = kShapes[shape];
     const int grid = b->sms * sh.blocks;
     sgm_kernel(b->maxD, sh.warps)<<<grid, sh.warps * 32, sgm_smem_bytes(b->maxD, sh.warps), st>>>(
-        b->d_streams, b->d_table, p.n_paths, p.P1, p.P2, b->d_counter);
+        b->d_streams, b->d_table, p.n_paths / 2, p.P1, p.P2, b->d_counter);
     if (timed && (e = cudaEventRecord(b->ev_sgm_b, st)) != cudaSuccess) return e;
     const int DP = 256;
     const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * DP * 2;
@@ -380,11 +384,12 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
         }
         // direction-major line order: every stream's horizontal lines first
         int item = 0;
-        for (int slot = 0; slot < p0.n_paths; ++slot) {
+        for (int slot = 0; slot < p0.n_paths / 2; ++slot) {
             for (int i = 0; i < n_streams; ++i) {
                 t.slot_base[slot][i] = item;
                 const BStream& s = b->h_streams[i];
-                item += slot <= 1 ? s.H : (slot <= 3 ? s.W : s.W + s.H - 1);
+                const int code = 2 * slot;
+                item += code <= 1 ? s.H : (code <= 3 ? s.W : s.W + s.H - 1);
             }
             t.slot_base[slot][n_streams] = item;
         }

@@ -52,8 +52,7 @@ cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int H
 cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* desc, int W, int Hh,
                         int Bc, uint8_t* C, cudaStream_t st);
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
-                       int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, const uint32_t* mode,
-                       cudaStream_t st);
+                       int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, cudaStream_t st);
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
                           int W, int Hh, float s_thr, float r_min, int lr_tol, float* Dz, float* rz,
                           uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
@@ -87,7 +86,7 @@ struct tsgm_ctx {
     uint2* desc = nullptr;         // {off, lo | w << 16} per pixel
     uint32_t* rowsum = nullptr;    // storage cells per row
     uint32_t* rowcells = nullptr;  // true window cells per row, then (at + H) wide pixels per row
-    uint32_t* cells = nullptr;     // [0] true window cells of the image, [1] aggregation layout
+    uint32_t* cells = nullptr;     // [0] true window cells of the image, [1] pixels wider than 32
     uint8_t* C = nullptr;          // ragged matching cost
     uint16_t* S = nullptr;         // aggregated cost, written only with TSGM_FLAG_KEEP_INTERNALS
     uint8_t* Lvol = nullptr;       // one ragged uint8 volume of path costs per SGM direction

@@ -72,8 +72,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
     return r;
 }
 
-// Windows wider than this many labels leave the narrow representation of the path aggregation;
-// their count per row is kept with the row totals (rowwide).
+// Windows wider than this many labels leave the narrow representation of the path aggregation
+// (one label per lane); their count per row is kept with the row totals (rowwide).
 constexpr int kNarrowMax = 32;
 
 // Row statistics written next to the windows: storage cells, true cells, pixels wider than
@@ -115,20 +115,11 @@ __device__ __forceinline__ void sanitize_row(const int16_t* __restrict__ lo_in,
     row_totals(acc, acc_true, acc_wide, y, sh, rowsum, rowcells, rowwide);
 }
 
-// Aggregation layout of one image, from the storage cells and the pixel count: 2 when the windows
-// average more than 24 cells of storage (every line takes the general walker), else 1 (each line
-// picks the narrow or the general walker from its own windows). It decides only the work layout,
-// never a result.
-__host__ __device__ __forceinline__ uint32_t sgm_mode(uint64_t storage, uint64_t n, uint64_t wide) {
-    (void)wide;
-    return storage > 24 * n ? 2u : 1u;
-}
-
 // Offsets of the ragged volume: pixel i's block starts at off[i] = sum of the (4-aligned) block
 // sizes of the pixels before it (row-major); off[n] = storage size. One block per row: base =
 // sum of earlier row totals, then a block scan. Also writes the per-pixel descriptor
 // {off, lo | w << 16} used by the matching kernels, and (last row) the number of true cells in
-// cells_total[0] and the aggregation layout (sgm_mode) in cells_total[1].
+// cells_total[0] and the number of pixels wider than kNarrowMax in cells_total[1].
 __device__ __forceinline__ void offsets_row(const int16_t* __restrict__ lo,
                                             const int16_t* __restrict__ hi,
                                             const uint32_t* __restrict__ rowsum,
@@ -169,7 +160,7 @@ __device__ __forceinline__ void offsets_row(const int16_t* __restrict__ lo,
         if (threadIdx.x == 0) {
             off[(size_t)W * Hh] = base;
             cells_total[0] = c;
-            cells_total[1] = sgm_mode(base, (uint64_t)W * Hh, wd);
+            cells_total[1] = wd;
         }
     }
 }
@@ -298,16 +289,11 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Shared memory of one warp of the aggregation kernels, in 32-bit words, for labels up to
-// DP = 32 * LPL: two label buffers (2 x DP uint16) shared by both walkers, then either the ring of
-// kRingW cost slots of DP bytes (sgm_line) or two blocks of 32 narrow cost slots of 32 bytes
-// (sgm_line_narrow).
+// Shared memory of sgm_line, in 32-bit words, for labels up to DP = 32 * LPL: two label buffers
+// (2 x DP uint16) and a ring of kRingW cost slots of DP bytes.
 constexpr int kRingW = 8, kPrefW = 6;  // ring slots and prefetch distance of sgm_line
 template <int LPL>
-__host__ __device__ constexpr int sgm_warp_words() {
-    return (32 * LPL) + ((32 * LPL) * kRingW / 4 > 2 * 32 * 32 / 4 ? (32 * LPL) * kRingW / 4
-                                                                     : 2 * 32 * 32 / 4);
-}
+__host__ __device__ constexpr int sgm_warp_words() { return (32 * LPL) * (1 + kRingW / 4); }
 
 // One path line walked by a whole warp: direction `code`, line index `l` of that direction; Lv is
 // the direction's volume, wsm this warp's shared memory (sgm_warp_words).
@@ -662,7 +648,7 @@ __device__ __forceinline__ void sgm_line(const uint8_t* __restrict__ C,
 // take a slow step (costs read straight from global memory, predecessor through the label
 // buffers). For lines with few such pixels.
 // ---------------------------------------------------------------------------------------------
-template <int LPL>
+template <int LPL, bool kPure>
 __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
                                                 const uint2* __restrict__ desc, int W, int Hh,
                                                 int D, int P1, int P2, int code, int l,
@@ -703,8 +689,35 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
         __syncwarp();        // ... for every lane
         const uint8_t* cb = cblk + (b & 1) * 1024;
         const int kend = min(32, len - (b << 5));
-#pragma unroll 4
-        for (int u = 0; u < kend; ++u) {
+        // pixels of this block whose window is narrow (past the line's end: w = 0, narrow)
+        const uint32_t nmask = kPure ? ~0u : __ballot_sync(kFull, (int)(dA.y >> 16) <= 32);
+        // a narrow step after a narrow one: straight-line code (the first pixel is a select, not
+        // a branch), so that the steps of a group of four interleave
+        auto fast_step = [&](int u) {
+            const int k = (b << 5) + u;
+            const uint32_t o = __shfl_sync(kFull, dA.x, u);
+            const uint32_t lw = __shfl_sync(kFull, dA.y, u);
+            const int lo = (int)(lw & 0xFFFFu);
+            const int w = (int)(lw >> 16);
+            const int c = lane < w ? (int)cb[u * 32 + lane] : 0;
+            const int s_ = lane + (lo - qlo);
+            int vc = __shfl_sync(kFull, Nreg, s_ & 31);
+            int vl = __shfl_sync(kFull, Nreg, (s_ - 1) & 31);
+            int vr = __shfl_sync(kFull, Nreg, (s_ + 1) & 31);
+            vc = ((unsigned)s_ < (unsigned)qw) ? vc : kInf;
+            vl = ((unsigned)(s_ - 1) < (unsigned)qw) ? vl : kInf;
+            vr = ((unsigned)(s_ + 1) < (unsigned)qw) ? vr : kInf;
+            int L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
+            L = k == 0 ? c : L;
+            L = lane < w ? L : kInf;
+            if (lane < w) Lv[o + lane] = (uint8_t)L;
+            m = (int)__reduce_min_sync(kFull, (unsigned)L);
+            Nreg = L;
+            qlo = lo;
+            qw = w;
+        };
+        // any step (wide windows, or a narrow one after a wide one)
+        auto slow_step = [&](int u) {
             const int k = (b << 5) + u;
             const uint32_t o = __shfl_sync(kFull, dA.x, u);
             const uint32_t lw = __shfl_sync(kFull, dA.y, u);
@@ -776,6 +789,21 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
             }
             qlo = lo;
             qw = w;
+        };
+        for (int u0 = 0; u0 < kend; u0 += 4) {
+            if ((kPure || in_regs) && u0 + 4 <= kend && ((nmask >> u0) & 15u) == 15u) {
+                fast_step(u0);
+                fast_step(u0 + 1);
+                fast_step(u0 + 2);
+                fast_step(u0 + 3);
+            } else {
+                for (int u = u0; u < u0 + 4 && u < kend; ++u) {
+                    if (kPure)
+                        fast_step(u);
+                    else
+                        slow_step(u);
+                }
+            }
         }
         dA = dB;
         dB = dC;
@@ -784,29 +812,238 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
     __syncwarp();
 }
 
-// One path line of one image: lines with at most one pixel in 8 wider than 32 labels take the
-// narrow walker, the others the general one (the choice changes the work, never the result).
-// `dense_image`: the image's windows are mostly wide (skip the scan).
+// ---------------------------------------------------------------------------------------------
+// Pairs of lines. Directions come in opposite pairs (codes 2s and 2s + 1) that walk the same
+// geometric lines from their two ends; one warp walks both lines of a pair step by step, the two
+// independent recurrences interleaved (a lone recurrence leaves the warp waiting on its own
+// dependent chain most of the time).
+// ---------------------------------------------------------------------------------------------
+
+// Line index, in direction codeB (the opposite of the direction of line lA of codeA), of the same
+// geometric line.
+__device__ __forceinline__ int partner_line(int codeA, int lA, int codeB, int W, int Hh) {
+    int dx, dy;
+    dir_of(codeA, dx, dy);
+    if (dx == 0 || dy == 0) return lA;
+    int i0, step, len;
+    line_geometry(codeA, lA, W, Hh, i0, step, len);
+    const int e = i0 + (len - 1) * step;  // codeB starts where line lA ends
+    const int xs = e % W, ys = e / W;
+    int dxB, dyB;
+    dir_of(codeB, dxB, dyB);
+    if (xs == (dxB > 0 ? 0 : W - 1)) return ys;
+    return Hh + (dxB > 0 ? xs - 1 : xs);
+}
+
+// Smem words of one warp of the aggregation kernels: the largest of the narrow walker (label
+// buffers and two cost blocks), the general walker and the paired full-range walker (two rings).
+constexpr int kRingP = 8, kPrefP = 6;  // ring slots and prefetch distance of the full-range pair
 template <int LPL>
-__device__ __forceinline__ void sgm_line_any(const uint8_t* __restrict__ C,
-                                             const uint2* __restrict__ desc, int W, int Hh, int D,
-                                             int P1, int P2, int code, int l,
-                                             uint8_t* __restrict__ Lv, uint32_t* const wsm,
-                                             bool dense_image) {
-    if (!dense_image) {
-        const int lane = threadIdx.x & 31;
-        int i0, step, len;
-        line_geometry(code, l, W, Hh, i0, step, len);
-        int wide = 0;
-        for (int kk = lane; kk < len; kk += 32)
-            wide += (int)(__ldg(desc + (i0 + kk * step)).y >> 16) > 32 ? 1 : 0;
-        wide = (int)__reduce_add_sync(kFull, (unsigned)wide);
-        if (wide * 8 <= len) {
-            sgm_line_narrow<LPL>(C, desc, W, Hh, D, P1, P2, code, l, Lv, wsm);
-            return;
+__host__ __device__ constexpr int sgm_narrow_words() { return 32 * LPL + 2 * 32 * 32 / 4; }
+// (the narrow walker's layout: DP words of label buffers, then 2 x 32 x 32 cost bytes)
+template <int LPL>
+__host__ __device__ constexpr int sgm_dense_slot() { return 32 * LPL > 128 ? 32 * LPL : 128; }
+template <int LPL>
+__host__ __device__ constexpr int sgm_pair_words() {
+    return sgm_narrow_words<LPL>() > 2 * kRingP * sgm_dense_slot<LPL>() / 4
+               ? (sgm_narrow_words<LPL>() > sgm_warp_words<LPL>() ? sgm_narrow_words<LPL>()
+                                                                   : sgm_warp_words<LPL>())
+               : (2 * kRingP * sgm_dense_slot<LPL>() / 4 > sgm_warp_words<LPL>()
+                      ? 2 * kRingP * sgm_dense_slot<LPL>() / 4
+                      : sgm_warp_words<LPL>());
+}
+
+// Two lines whose windows are all the full range (the dense form of sgm_line, interleaved). Each
+// lane copies its own cost bytes of the pixel kPrefP ahead into its own part of a ring slot, so
+// no warp synchronisation is needed per step.
+template <int LPL>
+__device__ __forceinline__ void sgm_pair_dense(const uint8_t* __restrict__ C,
+                                               const uint2* __restrict__ desc, int W, int Hh,
+                                               int D, int P1, int P2, const int (&code)[2],
+                                               const int (&l)[2], uint8_t* const (&Lv)[2],
+                                               uint32_t* const wsm) {
+    constexpr int NP = LPL / 2;
+    constexpr int SL = sgm_dense_slot<LPL>();  // ring slot bytes
+    constexpr int R = kRingP, PF = kPrefP;
+    const int lane = threadIdx.x & 31;
+    int i0[2], step[2], len = 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) line_geometry(code[i], l[i], W, Hh, i0[i], step[i], len);
+    uint32_t keep[NP];
+#pragma unroll
+    for (int k2 = 0; k2 < NP; ++k2) {
+        const int e = LPL * lane + 2 * k2;
+        keep[k2] = (e < D ? 0xFFFFu : 0u) | (e + 1 < D ? 0xFFFF0000u : 0u);
+    }
+    const bool dense_lane = LPL * lane < D;
+    const uint32_t P1P1 = ((uint32_t)P1 << 16) | (uint32_t)P1;
+    const uint32_t P2P2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
+    auto ldesc = [&](int i, int kk) -> uint32_t {
+        return kk < len ? __ldg(&desc[i0[i] + kk * step[i]].x) : 0u;
+    };
+    auto ring = [&](int i) { return reinterpret_cast<uint8_t*>(wsm) + i * R * SL; };
+    // this lane's cost words of pixel kk of line i, from offset o_, into its part of the slot
+    auto issue = [&](int i, int kk, uint32_t o_) {
+        if (kk >= len) return;
+        uint8_t* slot = ring(i) + (kk & (R - 1)) * SL;
+        if constexpr (LPL == 2) {
+            if (4 * (lane >> 1) < D) cp_async4(slot + 4 * lane, C + o_ + 4 * (lane >> 1));
+        } else {
+#pragma unroll
+            for (int r = 0; r < LPL / 4; ++r)
+                if (LPL * lane + 4 * r < D)
+                    cp_async4(slot + LPL * lane + 4 * r, C + o_ + LPL * lane + 4 * r);
+        }
+    };
+    uint32_t dc0[2], dc1[2], dc2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        dc0[i] = ldesc(i, lane);
+        dc1[i] = ldesc(i, 32 + lane);
+        dc2[i] = ldesc(i, 64 + lane);
+    }
+    int blk = 0;
+    auto off_at = [&](int i, int kk) -> uint32_t {  // kk in block blk or blk + 1
+        const bool first = (kk >> 5) == blk;
+        return __shfl_sync(kFull, first ? dc0[i] : dc1[i], kk & 31);
+    };
+    for (int u = 0; u < PF; ++u) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) issue(i, u, off_at(i, u));
+        cp_async_commit();
+    }
+    uint32_t Dreg[2][NP];
+    int m[2] = {0, 0};
+#pragma unroll 2
+    for (int k = 0; k < len; ++k) {
+        if (k > 0 && (k & 31) == 0) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                dc0[i] = dc1[i];
+                dc1[i] = dc2[i];
+                dc2[i] = ldesc(i, ((blk + 3) << 5) + lane);
+            }
+            ++blk;
+        }
+        uint32_t o[2], on[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            o[i] = off_at(i, k);
+            on[i] = off_at(i, k + PF);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) issue(i, k + PF, on[i]);
+        cp_async_commit();
+        cp_async_wait<PF>();  // pixel k's copies (this lane's part) have landed
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const uint8_t* cs = ring(i) + (k & (R - 1)) * SL;
+            uint32_t c2[NP];
+            if constexpr (LPL == 2) {
+                const uint32_t wd = *reinterpret_cast<const uint32_t*>(cs + 4 * lane);
+                c2[0] = __byte_perm(wd, 0u, (lane & 1) ? 0x4342 : 0x4140);
+            } else {
+#pragma unroll
+                for (int r = 0; r < LPL / 4; ++r) {
+                    const uint32_t wd = *reinterpret_cast<const uint32_t*>(cs + LPL * lane + 4 * r);
+                    c2[2 * r] = __byte_perm(wd, 0u, 0x4140);
+                    c2[2 * r + 1] = __byte_perm(wd, 0u, 0x4342);
+                }
+            }
+            uint32_t pmin = kInf2;
+            if (k == 0) {
+#pragma unroll
+                for (int k2 = 0; k2 < NP; ++k2) {
+                    Dreg[i][k2] = (c2[k2] & keep[k2]) | (kInf2 & ~keep[k2]);
+                    pmin = vmin2(pmin, Dreg[i][k2]);
+                }
+            } else {
+                uint32_t left_in = __shfl_up_sync(kFull, Dreg[i][NP - 1], 1);
+                uint32_t right_in = __shfl_down_sync(kFull, Dreg[i][0], 1);
+                if (lane == 0) left_in = kInf2;
+                if (lane == 31) right_in = kInf2;
+                const uint32_t mm = ((uint32_t)m[i] << 16) | (uint32_t)m[i];
+                const uint32_t mP2 = mm + P2P2;
+                uint32_t Lq[NP];
+#pragma unroll
+                for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[i][k2];
+#pragma unroll
+                for (int k2 = 0; k2 < NP; ++k2) {
+                    const uint32_t prev = (k2 == 0) ? left_in : Lq[k2 - 1];
+                    const uint32_t next = (k2 == NP - 1) ? right_in : Lq[k2 + 1];
+                    const uint32_t lm1 = __byte_perm(prev, Lq[k2], 0x5432);
+                    const uint32_t lp1 = __byte_perm(Lq[k2], next, 0x5432);
+                    uint32_t t = vmin2(lm1, lp1) + P1P1;
+                    t = vmin2(vmin2(t, Lq[k2]), mP2);
+                    const uint32_t Lnew = (c2[k2] + t) - mm;
+                    Dreg[i][k2] = (Lnew & keep[k2]) | (kInf2 & ~keep[k2]);
+                    pmin = vmin2(pmin, Dreg[i][k2]);
+                }
+            }
+            if (dense_lane) {
+                if constexpr (LPL % 4 == 0) {
+#pragma unroll
+                    for (int k4 = 0; k4 < NP / 2; ++k4)
+                        if (LPL * lane + 4 * k4 < D)
+                            *reinterpret_cast<uint32_t*>(Lv[i] + o[i] + LPL * lane + 4 * k4) =
+                                __byte_perm(Dreg[i][2 * k4], Dreg[i][2 * k4 + 1], 0x6420);
+                } else {
+                    *reinterpret_cast<uint16_t*>(Lv[i] + o[i] + LPL * lane) =
+                        (uint16_t)__byte_perm(Dreg[i][0], 0u, 0x0020);
+                }
+            }
+            m[i] = (int)__reduce_min_sync(kFull, min(pmin & 0xFFFFu, pmin >> 16));
         }
     }
-    sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code, l, Lv, wsm);
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+// One pair of lines of one image: scan the windows of the (common) geometric line once. Lines
+// whose windows are all the full range are walked together by twin 0 with the paired full-range
+// walker (two interleaved recurrences per warp); other lines are walked one per twin, line A by
+// twin 0 and line B by twin 1, with the narrow walker (at most one pixel in 8 wider than 32
+// labels) or the general one. twin < 0: this warp walks the whole pair alone. The choice changes
+// the work, never the result.
+template <int LPL>
+__device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
+                                         const uint2* __restrict__ desc, int W, int Hh, int D,
+                                         int P1, int P2, int codeA, int lA, uint8_t* __restrict__ LvA,
+                                         uint8_t* __restrict__ LvB, uint32_t* const wsm, int twin) {
+    const int lane = threadIdx.x & 31;
+    const int codeB = codeA + 1;
+    const int lB = partner_line(codeA, lA, codeB, W, Hh);
+    int i0, step, len;
+    line_geometry(codeA, lA, W, Hh, i0, step, len);
+    int wide = 0, full = 0;
+    for (int kk = lane; kk < len; kk += 32) {
+        const int w_ = (int)(__ldg(&desc[i0 + kk * step].y) >> 16);
+        wide += w_ > 32 ? 1 : 0;
+        full += w_ == D ? 1 : 0;
+    }
+    wide = (int)__reduce_add_sync(kFull, (unsigned)wide);
+    full = (int)__reduce_add_sync(kFull, (unsigned)full);
+    if (full == len && D > 32) {
+        if (twin == 1) return;
+        const int code[2] = {codeA, codeB};
+        const int l[2] = {lA, lB};
+        uint8_t* const Lv[2] = {LvA, LvB};
+        sgm_pair_dense<LPL>(C, desc, W, Hh, D, P1, P2, code, l, Lv, wsm);
+        return;
+    }
+    const bool narrow = wide * 8 <= len;
+    for (int t = 0; t < 2; ++t) {
+        if (twin >= 0 && twin != t) continue;
+        const int code = t ? codeB : codeA;
+        const int li = t ? lB : lA;
+        uint8_t* const Lv = t ? LvB : LvA;
+        if (wide == 0)
+            sgm_line_narrow<LPL, true>(C, desc, W, Hh, D, P1, P2, code, li, Lv, wsm);
+        else if (narrow)
+            sgm_line_narrow<LPL, false>(C, desc, W, Hh, D, P1, P2, code, li, Lv, wsm);
+        else
+            sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code, li, Lv, wsm);
+    }
 }
 
 constexpr int kSelThreads = 512;

@@ -34,27 +34,27 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
                 threadIdx.x & 7, (gridDim.x * blockDim.x) >> 3);
 }
 
-// Path aggregation of one image: all lines of all directions in one launch, one warp per line
-// (horizontal lines first: they are the longest chains). Each line picks its walker from its
-// windows unless the layout word written with the offsets (sgm_mode) says the image is mostly
-// wide.
+// Path aggregation of one image: all lines of all directions in one launch, two twin warps per
+// pair of opposite directions on one geometric line (see sgm_pair; horizontal pairs first: they
+// are the longest chains). `lines` lists the first direction of each pair (codes 0, 2, 4, 6) and
+// its line counts.
 template <int LPL>
 __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restrict__ C,
                                                         const uint2* __restrict__ desc, int W,
                                                         int Hh, int D, int P1, int P2,
                                                         SgmLines lines, uint8_t* __restrict__ Lvol,
-                                                        uint64_t vol_stride,
-                                                        const uint32_t* __restrict__ mode_word) {
+                                                        uint64_t vol_stride) {
     extern __shared__ uint32_t sgm_smem32[];
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kSgmWarps + wib;
-    if (gw >= lines.start[lines.nslots]) return;
+    const int pair = gw >> 1;
+    if (pair >= lines.start[lines.nslots]) return;
     int slot = 0;
-    while (gw >= lines.start[slot + 1]) ++slot;
+    while (pair >= lines.start[slot + 1]) ++slot;
     const int code = lines.code[slot];
-    sgm_line_any<LPL>(C, desc, W, Hh, D, P1, P2, code, gw - lines.start[slot],
-                      Lvol + (size_t)code * vol_stride, sgm_smem32 + wib * sgm_warp_words<LPL>(),
-                      __ldg(mode_word) == 2u);
+    sgm_pair<LPL>(C, desc, W, Hh, D, P1, P2, code, pair - lines.start[slot],
+                  Lvol + (size_t)code * vol_stride, Lvol + (size_t)(code + 1) * vol_stride,
+                  sgm_smem32 + wib * sgm_pair_words<LPL>(), gw & 1);
 }
 
 template <int NPATHS>
@@ -91,30 +91,34 @@ cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* des
 template <int LPL>
 static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int Hh, int D,
                                 int P1, int P2, const SgmLines& L, uint8_t* Lvol,
-                                uint64_t vol_stride, const uint32_t* mode, cudaStream_t st) {
-    const int nlines = L.start[L.nslots];
-    const size_t smem = (size_t)kSgmWarps * sgm_warp_words<LPL>() * sizeof(uint32_t);
-    k_sgm<LPL><<<(nlines + kSgmWarps - 1) / kSgmWarps, kSgmWarps * 32, smem, st>>>(
-        C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, mode);
+                                uint64_t vol_stride, cudaStream_t st) {
+    const int nwarps = 2 * L.start[L.nslots];  // twin warps per pair
+    const size_t smem = (size_t)kSgmWarps * sgm_pair_words<LPL>() * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_sgm<LPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_sgm<LPL><<<(nwarps + kSgmWarps - 1) / kSgmWarps, kSgmWarps * 32, smem, st>>>(
+        C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
-                       int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, const uint32_t* mode,
-                       cudaStream_t st) {
-    // slots ordered longest lines first: horizontal, vertical, then diagonals
+                       int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, cudaStream_t st) {
+    // pairs of opposite directions, longest lines first: horizontal, vertical, then diagonals
     SgmLines L;
-    L.nslots = n_paths;
+    L.nslots = n_paths / 2;
     L.start[0] = 0;
-    for (int s = 0; s < n_paths; ++s) {
-        const int code = s;
+    for (int s = 0; s < L.nslots; ++s) {
+        const int code = 2 * s;
         L.code[s] = code;
         const int cnt = code <= 1 ? Hh : (code <= 3 ? W : W + Hh - 1);
         L.start[s + 1] = L.start[s] + cnt;
     }
-    if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, mode, st);
-    if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, mode, st);
-    return launch_sgm_t<8>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, mode, st);
+    if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
+    if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
+    return launch_sgm_t<8>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
 }
 
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
