@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(512) kb_offsets(const BStream* __restrict__ st
         *b.status = (uint64_t)b.off[(size_t)b.W * b.H] > b.capacity ? 1u : 0u;
 }
 
+template <int CW, int CH>
 __global__ void __launch_bounds__(kCtW* kCtH) kb_census(const BStream* __restrict__ st,
                                                          const BTable* __restrict__ tb, int cw,
                                                          int ch) {
@@ -96,8 +97,8 @@ __global__ void __launch_bounds__(kCtW* kCtH) kb_census(const BStream* __restric
     const BStream& b = st[s];
     const int t = blockIdx.x - tb->tile_base[s];
     const int tx = t % tb->tiles_x[s], ty = t / tb->tiles_x[s];
-    census_tile(blockIdx.z ? b.right : b.left, b.W, b.H, cw, ch, tx * kCtW, ty * kCtH,
-                blockIdx.z ? b.censusR : b.censusL);
+    census_tile<CW, CH>(blockIdx.z ? b.right : b.left, b.W, b.H, cw, ch, tx * kCtW, ty * kCtH,
+                        blockIdx.z ? b.censusR : b.censusL);
 }
 
 __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
@@ -247,8 +248,15 @@ cudaError_t enqueue_step(tsgm_batch* b, int shape, bool timed = false) {
     const int rows = t.row_base[b->ns];
     kb_sanitize<<<rows, 256, 0, st>>>(b->d_streams, b->d_table);
     kb_offsets<<<rows, 512, 0, st>>>(b->d_streams, b->d_table);
-    kb_census<<<dim3(t.tile_base[b->ns], 1, 2), dim3(kCtW, kCtH), 0, st>>>(b->d_streams, b->d_table,
-                                                                           p.census_w, p.census_h);
+    {
+        const dim3 cg(t.tile_base[b->ns], 1, 2), cb(kCtW, kCtH);
+        if (p.census_w == 9 && p.census_h == 7)
+            kb_census<9, 7><<<cg, cb, 0, st>>>(b->d_streams, b->d_table, p.census_w, p.census_h);
+        else if (p.census_w == 5 && p.census_h == 5)
+            kb_census<5, 5><<<cg, cb, 0, st>>>(b->d_streams, b->d_table, p.census_w, p.census_h);
+        else
+            kb_census<0, 0><<<cg, cb, 0, st>>>(b->d_streams, b->d_table, p.census_w, p.census_h);
+    }
     kb_cost<<<b->sms * 8, 256, 0, st>>>(b->d_streams, b->d_table, p.census_w * p.census_h - 1);
     if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecord(b->ev_sgm_a, st)) != cudaSuccess) return e;

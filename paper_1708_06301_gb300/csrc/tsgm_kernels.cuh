@@ -171,17 +171,25 @@ __device__ __forceinline__ void offsets_row(const int16_t* __restrict__ lo,
 // ---------------------------------------------------------------------------------------------
 constexpr int kCtW = 32, kCtH = 8, kCmax = 15;
 
-// one 32 x 8 tile whose top-left output pixel is (bx, by); block of kCtW x kCtH threads
+// one 32 x 8 tile whose top-left output pixel is (bx, by); block of kCtW x kCtH threads.
+// CW x CH > 0: the window size is a compile-time constant and the comparisons unroll into
+// constant bit positions; 0 x 0: any size given at run time (cw, ch).
+template <int CW, int CH>
 __device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int W, int Hh, int cw,
                                             int ch, int bx, int by, uint64_t* __restrict__ out) {
     __shared__ uint8_t tile[kCtH + kCmax][kCtW + kCmax];
+    if constexpr (CW > 0) {
+        cw = CW;
+        ch = CH;
+    }
     const int rx = cw / 2, ry = ch / 2;
     const int tw = kCtW + 2 * rx, th = kCtH + 2 * ry;
-    for (int t = threadIdx.y * kCtW + threadIdx.x; t < tw * th; t += kCtW * kCtH) {
-        const int ty = t / tw, tx = t - ty * tw;
-        const int gx = min(max(bx + tx - rx, 0), W - 1);
+    for (int ty = threadIdx.y; ty < th; ty += kCtH) {
         const int gy = min(max(by + ty - ry, 0), Hh - 1);
-        tile[ty][tx] = img[gy * W + gx];
+        for (int tx = threadIdx.x; tx < tw; tx += kCtW) {
+            const int gx = min(max(bx + tx - rx, 0), W - 1);
+            tile[ty][tx] = img[gy * W + gx];
+        }
     }
     __syncthreads();
     const int x = bx + threadIdx.x, y = by + threadIdx.y;
@@ -189,13 +197,25 @@ __device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int
     const int cx = threadIdx.x + rx, cy = threadIdx.y + ry;
     const uint8_t c = tile[cy][cx];
     uint64_t code = 0;
-    int bit = 0;
-    for (int dy = -ry; dy <= ry; ++dy)
-        for (int dx = -rx; dx <= rx; ++dx) {
-            if (dx == 0 && dy == 0) continue;
-            code |= (uint64_t)(tile[cy + dy][cx + dx] < c) << bit;
-            ++bit;
-        }
+    if constexpr (CW > 0) {
+        constexpr int RX = CW / 2, RY = CH / 2;
+#pragma unroll
+        for (int dy = -RY; dy <= RY; ++dy)
+#pragma unroll
+            for (int dx = -RX; dx <= RX; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                const int bit = (dy + RY) * CW + (dx + RX) - ((dy > 0 || (dy == 0 && dx > 0)) ? 1 : 0);
+                code |= (uint64_t)(tile[cy + dy][cx + dx] < c) << bit;
+            }
+    } else {
+        int bit = 0;
+        for (int dy = -ry; dy <= ry; ++dy)
+            for (int dx = -rx; dx <= rx; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                code |= (uint64_t)(tile[cy + dy][cx + dx] < c) << bit;
+                ++bit;
+            }
+    }
     out[y * W + x] = code;
 }
 
@@ -292,6 +312,8 @@ __device__ __forceinline__ void cp_async_wait() {
 // Shared memory of sgm_line, in 32-bit words, for labels up to DP = 32 * LPL: two label buffers
 // (2 x DP uint16) and a ring of kRingW cost slots of DP bytes.
 constexpr int kRingW = 8, kPrefW = 6;  // ring slots and prefetch distance of sgm_line
+// narrow walker: predecessor rows of 32 labels with kInf pads on both sides (see sgm_line_narrow)
+constexpr int kRowPad = 3, kRowLen = 32 + 2 * kRowPad;
 template <int LPL>
 __host__ __device__ constexpr int sgm_warp_words() { return (32 * LPL) * (1 + kRingW / 4); }
 
@@ -656,7 +678,11 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
     constexpr int DP = 32 * LPL;
     uint16_t* const buf16 = reinterpret_cast<uint16_t*>(wsm);       // 2 x DP labels
     uint8_t* const cblk = reinterpret_cast<uint8_t*>(wsm + DP);     // 2 blocks x 32 x 32 bytes
+    // two rows (ping-pong by step parity) holding the path costs of a narrow pixel, label
+    // qlo + j at position kRowPad + j, kInf in the pads and past its window
+    int* const rows = reinterpret_cast<int*>(wsm + DP + 2 * 32 * 32 / 4);
     const int lane = threadIdx.x & 31;
+    for (int t = lane; t < 2 * kRowLen; t += 32) rows[t] = kInf;
     int i0, step, len;
     line_geometry(code, l, W, Hh, i0, step, len);
     (void)D;
@@ -693,6 +719,8 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
         const uint32_t nmask = kPure ? ~0u : __ballot_sync(kFull, (int)(dA.y >> 16) <= 32);
         // a narrow step after a narrow one: straight-line code (the first pixel is a select, not
         // a branch), so that the steps of a group of four interleave
+        // the predecessor's labels d - 1 .. d + 1 come from its padded row: the offset clamped to
+        // [-2, 33] reads only pads when out of range, so no range checks are needed
         auto fast_step = [&](int u) {
             const int k = (b << 5) + u;
             const uint32_t o = __shfl_sync(kFull, dA.x, u);
@@ -700,18 +728,16 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
             const int lo = (int)(lw & 0xFFFFu);
             const int w = (int)(lw >> 16);
             const int c = lane < w ? (int)cb[u * 32 + lane] : 0;
-            const int s_ = lane + (lo - qlo);
-            int vc = __shfl_sync(kFull, Nreg, s_ & 31);
-            int vl = __shfl_sync(kFull, Nreg, (s_ - 1) & 31);
-            int vr = __shfl_sync(kFull, Nreg, (s_ + 1) & 31);
-            vc = ((unsigned)s_ < (unsigned)qw) ? vc : kInf;
-            vl = ((unsigned)(s_ - 1) < (unsigned)qw) ? vl : kInf;
-            vr = ((unsigned)(s_ + 1) < (unsigned)qw) ? vr : kInf;
+            const int* prow = rows + ((k + 1) & 1) * kRowLen;
+            const int sc = min(max(lane + (lo - qlo), -2), 33) + kRowPad;
+            const int vl = prow[sc - 1], vc = prow[sc], vr = prow[sc + 1];
             int L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
             L = k == 0 ? c : L;
             L = lane < w ? L : kInf;
+            rows[(k & 1) * kRowLen + kRowPad + lane] = L;
             if (lane < w) Lv[o + lane] = (uint8_t)L;
             m = (int)__reduce_min_sync(kFull, (unsigned)L);
+            __syncwarp();  // this row is complete for the next step
             Nreg = L;
             qlo = lo;
             qw = w;
@@ -746,8 +772,10 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
                     L = c + min(min(min(ul, ur) + P1, uc), m + P2) - m;
                 }
                 L = lane < w ? L : kInf;
+                rows[(k & 1) * kRowLen + kRowPad + lane] = L;
                 if (lane < w) Lv[o + lane] = (uint8_t)L;
                 m = (int)__reduce_min_sync(kFull, (unsigned)L);
+                __syncwarp();  // this row is complete for the next step
                 Nreg = L;
                 in_regs = true;
             } else {
@@ -839,8 +867,10 @@ __device__ __forceinline__ int partner_line(int codeA, int lA, int codeB, int W,
 // buffers and two cost blocks), the general walker and the paired full-range walker (two rings).
 constexpr int kRingP = 8, kPrefP = 6;  // ring slots and prefetch distance of the full-range pair
 template <int LPL>
-__host__ __device__ constexpr int sgm_narrow_words() { return 32 * LPL + 2 * 32 * 32 / 4; }
-// (the narrow walker's layout: DP words of label buffers, then 2 x 32 x 32 cost bytes)
+__host__ __device__ constexpr int sgm_narrow_words() {
+    return 32 * LPL + 2 * 32 * 32 / 4 + 2 * kRowLen;
+}
+// (the narrow walker's layout: DP words of label buffers, 2 x 32 x 32 cost bytes, two padded rows)
 template <int LPL>
 __host__ __device__ constexpr int sgm_dense_slot() { return 32 * LPL > 128 ? 32 * LPL : 128; }
 template <int LPL>

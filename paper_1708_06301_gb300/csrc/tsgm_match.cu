@@ -17,13 +17,14 @@ namespace {
 
 using namespace dev;
 
+template <int CW, int CH>
 __global__ void __launch_bounds__(kCtW* kCtH) k_census(const uint8_t* __restrict__ imgA,
                                                         const uint8_t* __restrict__ imgB, int W,
                                                         int Hh, int cw, int ch,
                                                         uint64_t* __restrict__ outA,
                                                         uint64_t* __restrict__ outB) {
-    census_tile(blockIdx.z ? imgB : imgA, W, Hh, cw, ch, blockIdx.x * kCtW, blockIdx.y * kCtH,
-                blockIdx.z ? outB : outA);
+    census_tile<CW, CH>(blockIdx.z ? imgB : imgA, W, Hh, cw, ch, blockIdx.x * kCtW,
+                        blockIdx.y * kCtH, blockIdx.z ? outB : outA);
 }
 
 __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
@@ -75,7 +76,12 @@ cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int H
                           uint64_t* outA, uint64_t* outB, cudaStream_t st) {
     dim3 blk(kCtW, kCtH);
     dim3 grd((W + kCtW - 1) / kCtW, (Hh + kCtH - 1) / kCtH, imgB ? 2 : 1);
-    k_census<<<grd, blk, 0, st>>>(imgA, imgB, W, Hh, cw, ch, outA, outB);
+    if (cw == 9 && ch == 7)
+        k_census<9, 7><<<grd, blk, 0, st>>>(imgA, imgB, W, Hh, cw, ch, outA, outB);
+    else if (cw == 5 && ch == 5)
+        k_census<5, 5><<<grd, blk, 0, st>>>(imgA, imgB, W, Hh, cw, ch, outA, outB);
+    else
+        k_census<0, 0><<<grd, blk, 0, st>>>(imgA, imgB, W, Hh, cw, ch, outA, outB);
     return cudaGetLastError();
 }
 
