@@ -232,8 +232,8 @@ tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* righ
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;
     const float s_thr = p.S_max * (float)p.n_paths;
     stage_begin(ctx, TSGM_STAGE_SELECT);
-    TSGM_LAUNCH(launch_select(ctx->Lvol, ctx->max_cells, p.n_paths, ctx->desc, ctx->W, ctx->H, s_thr,
-                              p.r_min, p.lr_tol, Dz, rz, keep ? ctx->S : nullptr,
+    TSGM_LAUNCH(launch_select(ctx->Lvol, ctx->max_cells, p.n_paths, ctx->desc, ctx->W, ctx->H, ctx->D,
+                              s_thr, p.r_min, p.lr_tol, Dz, rz, keep ? ctx->S : nullptr,
                               keep ? ctx->dstar : nullptr, keep ? ctx->dright : nullptr,
                               keep ? ctx->lrvalid : nullptr, ctx->stream),
             "select");

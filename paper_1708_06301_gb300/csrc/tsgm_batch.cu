@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__
 }
 
 template <int NPATHS>
-__global__ void __launch_bounds__(kSelThreads) kb_select(const BStream* __restrict__ st,
+__global__ void __launch_bounds__(kSelThreads, 2) kb_select(const BStream* __restrict__ st,
                                                          const BTable* __restrict__ tb, int DP,
                                                          float s_thr, float r_min, int lr_tol) {
     extern __shared__ uint32_t sel_smem[];

@@ -1118,37 +1118,43 @@ __device__ __forceinline__ void sum_paths(const uint8_t* __restrict__ Lvol, uint
     }
 }
 
-// One image row y of one image; a whole block works on it. `smem` holds the per-column state of
-// the row followed by the per-warp scratch; `n_wide` is a block-shared counter.
-template <int NPATHS>
-__device__ __forceinline__ void select_row(
+// Selection of the pixels [x0, x1) of image row y (Eq. 9 and the left-right check), by one block.
+// The right-view keys of the row (per column xr, the (S << 9 | d) minimum over the pixels
+// x = xr + d whose window holds d) are reached through `part`: keymin(xr, key) (an atomic minimum
+// from one of this block's pixels), key(xr) (the row's final key, after sync()), own_keys() and
+// nkeys (this block's key array, to initialise) and sync() (every block working on the row).
+// `smem` holds this block's keys and the per-pixel state of its pixels, then the per-warp scratch;
+// `n_wide` is block-shared.
+template <int NPATHS, int NCH, class Part>
+__device__ __forceinline__ void select_part(
     const uint8_t* __restrict__ Lvol, uint64_t vol_stride, const uint2* __restrict__ desc, int W,
-    int y, int DP, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz,
+    int y, int x0, int x1, int DP, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz,
     float* __restrict__ rz, uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
     int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out, uint32_t* sel_smem,
-    int& n_wide) {
-    uint32_t* drk = sel_smem;                    // W keys
-    float* dzs = (float*)(drk + W);              // W
-    float* rzs = dzs + W;                        // W
-    int16_t* ds = (int16_t*)(rzs + W);           // W
-    int16_t* wideq = ds + W;                     // W queued wide pixels
+    int& n_wide, Part& part) {
+    const int npx = x1 - x0;
+    uint32_t* drk = part.own_keys();              // nkeys keys (may alias sel_smem)
+    float* dzs = (float*)(sel_smem + part.nkeys); // npx
+    float* rzs = dzs + npx;                       // npx
+    int16_t* ds = (int16_t*)(rzs + npx);          // npx
+    int16_t* wideq = ds + npx;                    // npx queued wide pixels
     // per-warp scratch of DP labels, 8-byte aligned for the 4-label stores
-    uint16_t* scr_all = (uint16_t*)(sel_smem + ((3 * W + W + 1) & ~1));
+    uint16_t* scr_all = (uint16_t*)(sel_smem + ((part.nkeys + 3 * npx + 1) & ~1));
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int x = threadIdx.x; x < W; x += blockDim.x) drk[x] = 0xFFFFFFFFu;
+    for (int t = threadIdx.x; t < part.nkeys; t += blockDim.x) drk[t] = 0xFFFFFFFFu;
     if (threadIdx.x == 0) n_wide = 0;
-    __syncthreads();
+    part.sync();
 
     // ---- narrow windows: one thread per pixel
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
         const int i = y * W + x;
         const uint2 dsc = desc[i];
         const uint32_t o = dsc.x;
         const int a = (int)(dsc.y & 0xFFFFu);
         const int w = (int)(dsc.y >> 16);
         if (w > kSelNarrow) {
-            wideq[atomicAdd(&n_wide, 1)] = (int16_t)x;
+            wideq[atomicAdd(&n_wide, 1)] = (int16_t)(x - x0);
             continue;
         }
         uint32_t sp[kSelNarrow / 2];  // S as u16x2 pairs
@@ -1180,7 +1186,7 @@ __device__ __forceinline__ void select_row(
             if (j == js + 1) spv = sv[j];
             if (j < w) {
                 const int xr = x - (a + j);
-                if (xr >= 0) atomicMin(drk + xr, ((uint32_t)sv[j] << 9) | (uint32_t)(a + j));
+                if (xr >= 0) part.keymin(xr, ((uint32_t)sv[j] << 9) | (uint32_t)(a + j));
             }
         }
         float delta = 0.0f;
@@ -1208,35 +1214,60 @@ __device__ __forceinline__ void select_row(
         }
         float r = (float)(nl + nr);
         if (r < r_min) r = r_min;
-        ds[x] = (int16_t)(a + js);
-        dzs[x] = __fadd_rn((float)(a + js), delta);
-        rzs[x] = r;
+        ds[x - x0] = (int16_t)(a + js);
+        dzs[x - x0] = __fadd_rn((float)(a + js), delta);
+        rzs[x - x0] = r;
     }
     __syncthreads();
 
-    // ---- wide windows: one warp per pixel
+    // ---- wide windows: one warp per pixel, the next pixel's path costs loaded during this one
+    // (NCH chunks of 128 labels cover the widest window)
     uint16_t* scr = scr_all + wid * DP;
     const int nwide = n_wide;
-    for (int q = wid; q < nwide; q += nw) {
-        const int x = wideq[q];
-        const int i = y * W + x;
-        const uint2 dsc = desc[i];
-        const uint32_t o = dsc.x;
-        const int a = (int)(dsc.y & 0xFFFFu);
+    auto load_wide = [&](int q, uint32_t (&v)[NCH * NPATHS], uint2& dsc) {
+        if (q >= nwide) return;
+        dsc = desc[y * W + x0 + wideq[q]];
         const int w = (int)(dsc.y >> 16);
-        unsigned best = 0xFFFFFFFFu;
-        for (int j = 4 * lane; j < w; j += 128) {
-            uint32_t p0, p1;
-            sum_paths<NPATHS>(Lvol, vol_stride, o, j, p0, p1);
-            *reinterpret_cast<uint2*>(scr + j) = make_uint2(p0, p1);
-            if (S_out) *reinterpret_cast<uint2*>(S_out + o + j) = make_uint2(p0, p1);
-            const unsigned sv[4] = {p0 & 0xFFFFu, p0 >> 16, p1 & 0xFFFFu, p1 >> 16};
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (j + t < w) {
-                    best = min(best, (sv[t] << 16) | (unsigned)(j + t));
-                    const int xr = x - (a + j + t);
-                    if (xr >= 0) atomicMin(drk + xr, (sv[t] << 9) | (unsigned)(a + j + t));
+        for (int c = 0; c < NCH; ++c) {
+            const int j = 4 * lane + 128 * c;
+#pragma unroll
+            for (int r = 0; r < NPATHS; ++r)
+                v[c * NPATHS + r] =
+                    j < w ? __ldg(reinterpret_cast<const uint32_t*>(Lvol + r * vol_stride + dsc.x + j))
+                          : 0u;
+        }
+    };
+    uint32_t vcur[NCH * NPATHS], vnext[NCH * NPATHS];
+    uint2 dcur = make_uint2(0u, 0u), dnext = make_uint2(0u, 0u);
+    load_wide(wid, vcur, dcur);
+    for (int q = wid; q < nwide; q += nw) {
+        load_wide(q + nw, vnext, dnext);
+        const int x = x0 + wideq[q];
+        const uint32_t o = dcur.x;
+        const int a = (int)(dcur.y & 0xFFFFu);
+        const int w = (int)(dcur.y >> 16);
+        unsigned best = 0xFFFFFFFFu;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int j = 4 * lane + 128 * c;
+            if (j < w) {
+                uint32_t p0 = 0u, p1 = 0u;
+#pragma unroll
+                for (int r = 0; r < NPATHS; ++r) {
+                    p0 += __byte_perm(vcur[c * NPATHS + r], 0u, 0x4140);
+                    p1 += __byte_perm(vcur[c * NPATHS + r], 0u, 0x4342);
+                }
+                *reinterpret_cast<uint2*>(scr + j) = make_uint2(p0, p1);
+                if (S_out) *reinterpret_cast<uint2*>(S_out + o + j) = make_uint2(p0, p1);
+                const unsigned sv[4] = {p0 & 0xFFFFu, p0 >> 16, p1 & 0xFFFFu, p1 >> 16};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (j + t < w) {
+                        best = min(best, (sv[t] << 16) | (unsigned)(j + t));
+                        const int xr = x - (a + j + t);
+                        if (xr >= 0) part.keymin(xr, (sv[t] << 9) | (unsigned)(a + j + t));
+                    }
                 }
             }
         }
@@ -1255,31 +1286,57 @@ __device__ __forceinline__ void select_row(
         float r = (float)(nl + nr);
         if (r < r_min) r = r_min;
         if (lane == 0) {
-            ds[x] = (int16_t)(a + js);
-            dzs[x] = __fadd_rn((float)(a + js), delta);
-            rzs[x] = r;
+            ds[x - x0] = (int16_t)(a + js);
+            dzs[x - x0] = __fadd_rn((float)(a + js), delta);
+            rzs[x - x0] = r;
         }
         __syncwarp();
+#pragma unroll
+        for (int t = 0; t < NCH * NPATHS; ++t) vcur[t] = vnext[t];
+        dcur = dnext;
     }
-    __syncthreads();
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    part.sync();  // every key of the row is final
+    for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
         const int i = y * W + x;
-        const int d = ds[x];
+        const int d = ds[x - x0];
         const int xr = x - d;
         bool ok = false;
         if (xr >= 0) {
-            const uint32_t kk = drk[xr];
+            const uint32_t kk = part.key(xr);
             ok = kk != 0xFFFFFFFFu && abs(d - (int)(kk & 0x1FFu)) <= lr_tol;
         }
-        Dz[i] = ok ? dzs[x] : -1.0f;
-        rz[i] = ok ? rzs[x] : -1.0f;
+        Dz[i] = ok ? dzs[x - x0] : -1.0f;
+        rz[i] = ok ? rzs[x - x0] : -1.0f;
         if (dstar_out) {
             dstar_out[i] = (int16_t)d;
-            const uint32_t kx = drk[x];
+            const uint32_t kx = part.key(x);
             dright_out[i] = kx == 0xFFFFFFFFu ? (int16_t)-1 : (int16_t)(kx & 0x1FFu);
             valid_out[i] = ok ? 1 : 0;
         }
     }
+    part.sync();  // no block leaves while another may still read its keys
+}
+
+// One whole row per block: the keys in this block's shared memory.
+struct RowPart {
+    uint32_t* keys;
+    int nkeys;
+    __device__ uint32_t* own_keys() const { return keys; }
+    __device__ void keymin(int xr, uint32_t k) const { atomicMin(keys + xr, k); }
+    __device__ uint32_t key(int xr) const { return keys[xr]; }
+    __device__ void sync() const { __syncthreads(); }
+};
+
+template <int NPATHS>
+__device__ __forceinline__ void select_row(
+    const uint8_t* __restrict__ Lvol, uint64_t vol_stride, const uint2* __restrict__ desc, int W,
+    int y, int DP, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz,
+    float* __restrict__ rz, uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
+    int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out, uint32_t* sel_smem,
+    int& n_wide) {
+    RowPart part{sel_smem, W};
+    select_part<NPATHS, 2>(Lvol, vol_stride, desc, W, y, 0, W, DP, s_thr, r_min, lr_tol, Dz, rz,
+                           S_out, dstar_out, dright_out, valid_out, sel_smem, n_wide, part);
 }
 
 }  // namespace dev

@@ -8,6 +8,8 @@
 // to its own uint8 volume with plain stores, and the selection kernel forms S = sum_r L_r.
 // Each pixel's {off, lo | w << 16} descriptor is read once per pixel.
 
+#include <cooperative_groups.h>
+
 #include <cfloat>
 
 #include "tsgm_kernels.cuh"
@@ -58,16 +60,47 @@ __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restric
                   sgm_smem32 + wib * sgm_pair_words<LPL>(), gw & 1);
 }
 
-template <int NPATHS>
-__global__ void __launch_bounds__(kSelThreads) k_select(
+// Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the
+// row's pixels (seg columns from x0). Every block keeps the right-view keys its own pixels can
+// reach, columns x0 - (D - 1) .. x0 + seg - 1, with atomics in its own shared memory; after the
+// cluster barrier the key of column xr is the minimum over the (at most few) blocks whose pixels
+// reach it, read through distributed shared memory.
+constexpr int kSelCluster = 4;
+constexpr int kSelThreadsCl = 256;
+
+struct ClusterPart {
+    uint32_t* keys;
+    int nkeys;   // seg + D - 1
+    int seg, D, W, base;  // base: the column of keys[0] (x0 - (D - 1))
+    __device__ uint32_t* own_keys() const { return keys; }
+    __device__ void keymin(int xr, uint32_t k) const { atomicMin(keys + (xr - base), k); }
+    __device__ uint32_t key(int xr) const {
+        // pixels x = xr + d (d < D) lie in the blocks from xr's block to (xr + D - 1)'s
+        const int b0 = xr / seg, b1 = min(W - 1, xr + D - 1) / seg;
+        uint32_t k = 0xFFFFFFFFu;
+        for (int b = b0; b <= b1; ++b)
+            k = min(k, cooperative_groups::this_cluster().map_shared_rank(keys, b)[xr - (b * seg - (D - 1))]);
+        return k;
+    }
+    __device__ void sync() const { cooperative_groups::this_cluster().sync(); }
+};
+
+template <int NPATHS, int NCH>
+__global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(kSelThreadsCl) k_select(
     const uint8_t* __restrict__ Lvol, uint64_t vol_stride, const uint2* __restrict__ desc, int W,
-    int DP, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz, float* __restrict__ rz,
-    uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
+    int DP, int DPim, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz,
+    float* __restrict__ rz, uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
     int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out) {
     extern __shared__ uint32_t sel_smem[];
     __shared__ int n_wide;
-    select_row<NPATHS>(Lvol, vol_stride, desc, W, blockIdx.x, DP, s_thr, r_min, lr_tol, Dz, rz,
-                       S_out, dstar_out, dright_out, valid_out, sel_smem, n_wide);
+    const int rank = (int)cooperative_groups::this_cluster().block_rank();
+    const int y = blockIdx.x / kSelCluster;
+    const int seg = (W + kSelCluster - 1) / kSelCluster;
+    const int x0 = min(W, rank * seg), x1 = min(W, x0 + seg);
+    const int D = DPim;
+    ClusterPart part{sel_smem, seg + D - 1, seg, D, W, rank * seg - (D - 1)};
+    select_part<NPATHS, NCH>(Lvol, vol_stride, desc, W, y, x0, x1, DP, s_thr, r_min, lr_tol, Dz, rz,
+                             S_out, dstar_out, dright_out, valid_out, sel_smem, n_wide, part);
 }
 
 }  // namespace
@@ -128,21 +161,24 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
 }
 
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
-                          int W, int Hh, float s_thr, float r_min, int lr_tol, float* Dz, float* rz,
-                          uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
+                          int W, int Hh, int D, float s_thr, float r_min, int lr_tol, float* Dz,
+                          float* rz, uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
                           cudaStream_t st) {
     // per-warp scratch for the wide windows: up to 256 labels
     const int DP = 256;
-    const size_t smem = (size_t)((3 * W + W + 1) & ~1) * 4 +
-                        (size_t)(kSelThreads / 32) * DP * sizeof(uint16_t);
-    auto kern = n_paths == 8 ? k_select<8> : k_select<4>;
+    const int seg = (W + kSelCluster - 1) / kSelCluster;
+    const size_t smem = (size_t)((seg + D - 1 + 3 * seg + 1) & ~1) * 4 +
+                        (size_t)(kSelThreadsCl / 32) * DP * sizeof(uint16_t);
+    auto kern = n_paths == 8 ? (D <= 128 ? k_select<8, 1> : k_select<8, 2>)
+                             : (D <= 128 ? k_select<4, 1> : k_select<4, 2>);
     if (smem > 48 * 1024) {
         const cudaError_t e =
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<Hh, kSelThreads, smem, st>>>(Lvol, vol_stride, desc, W, DP, s_thr, r_min, lr_tol, Dz, rz,
-                                        S, dstar, dright, valid);
+    kern<<<Hh * kSelCluster, kSelThreadsCl, smem, st>>>(Lvol, vol_stride, desc, W, DP, D, s_thr,
+                                                         r_min, lr_tol, Dz, rz, S, dstar, dright,
+                                                         valid);
     return cudaGetLastError();
 }
 
