@@ -841,6 +841,337 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
 }
 
 // ---------------------------------------------------------------------------------------------
+// One path line of narrow and full-range windows (the image-border lines of a reduced frame),
+// walked by a whole warp: the narrow walker's block copies, padded rows and straight-line groups
+// for narrow pixels, and the dense form of sgm_line (LPL labels per lane packed as uint16 pairs)
+// for full-range pixels, whose costs are copied by each lane (its own words) two groups of four
+// pixels ahead into a ring of kRingM slots, with straight-line groups of four full-range steps.
+// Changes of representation and other widths (slow step, costs read from global memory) go
+// through the two label buffers.
+// ---------------------------------------------------------------------------------------------
+constexpr int kRingM = 16;  // full-range cost slots of the mixed walker (3 groups in flight)
+template <int LPL>
+__host__ __device__ constexpr int sgm_mixed_words() {
+    return 32 * LPL + 2 * 32 * 32 / 4 + 2 * kRowLen + kRingM * (32 * LPL > 128 ? 32 * LPL : 128) / 4;
+}
+
+template <int LPL>
+__device__ __forceinline__ void sgm_line_mixed(const uint8_t* __restrict__ C,
+                                               const uint2* __restrict__ desc, int W, int Hh,
+                                               int D, int P1, int P2, int code, int l,
+                                               uint8_t* __restrict__ Lv, uint32_t* const wsm) {
+    constexpr int NP = LPL / 2;
+    constexpr int DP = 32 * LPL;
+    constexpr int kBufPairs = DP / 2;
+    constexpr int SL = DP > 128 ? DP : 128;  // dense slot bytes
+    uint32_t* const buf0 = wsm;                                          // 2 x DP labels
+    uint16_t* const buf16 = reinterpret_cast<uint16_t*>(wsm);
+    uint8_t* const cblk = reinterpret_cast<uint8_t*>(wsm + DP);          // 2 x 32 x 32 bytes
+    int* const rows = reinterpret_cast<int*>(wsm + DP + 2 * 32 * 32 / 4);  // 2 padded rows
+    uint8_t* const dring = reinterpret_cast<uint8_t*>(wsm + DP + 2 * 32 * 32 / 4 + 2 * kRowLen);
+    const int lane = threadIdx.x & 31;
+    int i0, step, len;
+    line_geometry(code, l, W, Hh, i0, step, len);
+    for (int t = lane; t < 2 * kRowLen; t += 32) rows[t] = kInf;
+
+    uint32_t keep[NP];
+#pragma unroll
+    for (int k2 = 0; k2 < NP; ++k2) {
+        const int e = LPL * lane + 2 * k2;
+        keep[k2] = (e < D ? 0xFFFFu : 0u) | (e + 1 < D ? 0xFFFF0000u : 0u);
+    }
+    const bool dense_lane = LPL * lane < D;
+    const uint32_t P1P1 = ((uint32_t)P1 << 16) | (uint32_t)P1;
+    const uint32_t P2P2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
+
+    auto ldesc = [&](int kk) -> uint2 {
+        return kk < len ? __ldg(desc + (i0 + kk * step)) : make_uint2(0u, 0u);
+    };
+    auto copy_block = [&](int b, uint2 d) {  // this lane's pixel of block b, narrow windows only
+        const int w_ = (int)(d.y >> 16);
+        if (w_ <= 32) {
+            uint8_t* dst = cblk + (b & 1) * 1024 + lane * 32;
+            const uint8_t* src = C + d.x;
+            for (int t = 0; 4 * t < w_; ++t) cp_async4(dst + 4 * t, src + 4 * t);
+        }
+    };
+    auto copy_dense = [&](int kk, uint32_t o_) {  // this lane's cost words of a full-range pixel
+        uint8_t* slot = dring + (kk & (kRingM - 1)) * SL;
+        if constexpr (LPL == 2) {
+            if (4 * (lane >> 1) < D) cp_async4(slot + 4 * lane, C + o_ + 4 * (lane >> 1));
+        } else {
+#pragma unroll
+            for (int r = 0; r < LPL / 4; ++r)
+                if (LPL * lane + 4 * r < D) cp_async4(slot + LPL * lane + 4 * r, C + o_ + LPL * lane + 4 * r);
+        }
+    };
+    auto dense_costs = [&](int kk, uint32_t (&c2)[NP]) {
+        const uint8_t* cs = dring + (kk & (kRingM - 1)) * SL;
+        if constexpr (LPL == 2) {
+            const uint32_t wd = *reinterpret_cast<const uint32_t*>(cs + 4 * lane);
+            c2[0] = __byte_perm(wd, 0u, (lane & 1) ? 0x4342 : 0x4140);
+        } else {
+#pragma unroll
+            for (int r = 0; r < LPL / 4; ++r) {
+                const uint32_t wd = *reinterpret_cast<const uint32_t*>(cs + LPL * lane + 4 * r);
+                c2[2 * r] = __byte_perm(wd, 0u, 0x4140);
+                c2[2 * r + 1] = __byte_perm(wd, 0u, 0x4342);
+            }
+        }
+    };
+
+    int qlo = 0, qw = 0, m = 0, Nreg = kInf, qb = 0;
+    int loc = 0;  // predecessor: 0 narrow (Nreg and its padded row), 1 dense (Dreg), 2 label buffer qb
+    uint32_t Dreg[NP];
+#pragma unroll
+    for (int k2 = 0; k2 < NP; ++k2) Dreg[k2] = kInf2;
+
+    auto spill = [&]() {  // the predecessor into label buffer 0 if it is in registers
+        if (loc == 2) return;
+        __syncwarp();
+        if (loc == 0) {
+            if (lane < qw) buf16[qlo + lane] = (uint16_t)Nreg;
+        } else {
+#pragma unroll
+            for (int k2 = 0; k2 < NP; ++k2) buf0[(LPL * lane) / 2 + k2] = Dreg[k2];
+        }
+        qb = 0;
+        loc = 2;
+        __syncwarp();
+    };
+    auto dense_update = [&](const uint32_t (&Lq)[NP], const uint32_t (&c2)[NP]) -> int {
+        uint32_t left_in = __shfl_up_sync(kFull, Lq[NP - 1], 1);
+        uint32_t right_in = __shfl_down_sync(kFull, Lq[0], 1);
+        if (lane == 0) left_in = kInf2;
+        if (lane == 31) right_in = kInf2;
+        const uint32_t mm = ((uint32_t)m << 16) | (uint32_t)m;
+        const uint32_t mP2 = mm + P2P2;
+        uint32_t pmin = kInf2;
+#pragma unroll
+        for (int k2 = 0; k2 < NP; ++k2) {
+            const uint32_t prev = (k2 == 0) ? left_in : Lq[k2 - 1];
+            const uint32_t next = (k2 == NP - 1) ? right_in : Lq[k2 + 1];
+            const uint32_t lm1 = __byte_perm(prev, Lq[k2], 0x5432);
+            const uint32_t lp1 = __byte_perm(Lq[k2], next, 0x5432);
+            uint32_t t = vmin2(lm1, lp1) + P1P1;
+            t = vmin2(vmin2(t, Lq[k2]), mP2);
+            const uint32_t Lnew = (c2[k2] + t) - mm;
+            Dreg[k2] = (Lnew & keep[k2]) | (kInf2 & ~keep[k2]);
+            pmin = vmin2(pmin, Dreg[k2]);
+        }
+        return (int)min(pmin & 0xFFFFu, pmin >> 16);
+    };
+    auto emit_dense = [&](uint32_t o) {
+        if (!dense_lane) return;
+        if constexpr (LPL % 4 == 0) {
+#pragma unroll
+            for (int k4 = 0; k4 < NP / 2; ++k4)
+                if (LPL * lane + 4 * k4 < D)
+                    *reinterpret_cast<uint32_t*>(Lv + o + LPL * lane + 4 * k4) =
+                        __byte_perm(Dreg[2 * k4], Dreg[2 * k4 + 1], 0x6420);
+        } else {
+            *reinterpret_cast<uint16_t*>(Lv + o + LPL * lane) =
+                (uint16_t)__byte_perm(Dreg[0], 0u, 0x0020);
+        }
+    };
+
+    const int nblk = (len + 31) >> 5;
+    uint2 dA = ldesc(lane), dB = ldesc(32 + lane);
+    uint32_t dmA = __ballot_sync(kFull, (int)(dA.y >> 16) == D);
+    uint32_t dmB = __ballot_sync(kFull, (int)(dB.y >> 16) == D);
+    copy_block(0, dA);
+    // groups 0 and 1 (pixels 0 .. 7, all in block 0)
+    for (int g = 0; g < 2; ++g) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int p = 4 * g + t;
+            if (p < len && ((dmA >> p) & 1u)) copy_dense(p, __shfl_sync(kFull, dA.x, p));
+        }
+        cp_async_commit();
+    }
+
+    for (int b = 0; b < nblk; ++b) {
+        const uint8_t* cb = cblk + (b & 1) * 1024;
+        const int kend = min(32, len - (b << 5));
+        const uint32_t nmask = __ballot_sync(kFull, (int)(dA.y >> 16) <= 32);
+        uint2 dC = make_uint2(0u, 0u);
+        uint32_t dmC = 0u;
+        for (int u0 = 0; u0 < kend; u0 += 4) {
+            // copies: at the block's first group the next block's narrow costs (its descriptors
+            // two blocks ahead too), at every group the full-range pixels two groups ahead
+            __syncwarp();  // reads of the slots about to be refilled are done
+            if (u0 == 0) {
+                copy_block(b + 1, dB);
+                dC = ldesc(((b + 2) << 5) + lane);
+                dmC = __ballot_sync(kFull, (int)(dC.y >> 16) == D);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int u = u0 + 8 + t;  // pixel (b << 5) + u, in this block or the next
+                const int p = (b << 5) + u;
+                const bool nxt = u >= 32;
+                const uint32_t dm = nxt ? dmB : dmA;
+                if (p < len && ((dm >> (u & 31)) & 1u))
+                    copy_dense(p, __shfl_sync(kFull, nxt ? dB.x : dA.x, u & 31));
+            }
+            cp_async_commit();
+            cp_async_wait<2>();  // this group's full-range copies (and this block's) have landed
+            __syncwarp();
+            const bool full4 = u0 + 4 <= kend;
+            // ---------------------------------------------------------------- group kinds
+            if (full4 && loc == 0 && ((nmask >> u0) & 15u) == 15u) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int u = u0 + t;
+                    const int k = (b << 5) + u;
+                    const uint32_t o = __shfl_sync(kFull, dA.x, u);
+                    const uint32_t lw = __shfl_sync(kFull, dA.y, u);
+                    const int lo = (int)(lw & 0xFFFFu);
+                    const int w = (int)(lw >> 16);
+                    const int c = lane < w ? (int)cb[u * 32 + lane] : 0;
+                    const int* prow = rows + ((k + 1) & 1) * kRowLen;
+                    const int sc = min(max(lane + (lo - qlo), -2), 33) + kRowPad;
+                    const int vl = prow[sc - 1], vc = prow[sc], vr = prow[sc + 1];
+                    int L = c + min(min(min(vl, vr) + P1, vc), m + P2) - m;
+                    L = k == 0 ? c : L;
+                    L = lane < w ? L : kInf;
+                    rows[(k & 1) * kRowLen + kRowPad + lane] = L;
+                    if (lane < w) Lv[o + lane] = (uint8_t)L;
+                    m = (int)__reduce_min_sync(kFull, (unsigned)L);
+                    __syncwarp();
+                    Nreg = L;
+                    qlo = lo;
+                    qw = w;
+                }
+                continue;
+            }
+            if (full4 && loc == 1 && ((dmA >> u0) & 15u) == 15u) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int u = u0 + t;
+                    const int k = (b << 5) + u;
+                    const uint32_t o = __shfl_sync(kFull, dA.x, u);
+                    uint32_t c2[NP];
+                    dense_costs(k, c2);
+                    uint32_t Lq[NP];
+#pragma unroll
+                    for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[k2];
+                    const int lmin = dense_update(Lq, c2);
+                    emit_dense(o);
+                    m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
+                }
+                continue;  // qlo = 0, qw = D already
+            }
+            // ---------------------------------------------------------------- any steps
+            for (int u = u0; u < u0 + 4 && u < kend; ++u) {
+                const int k = (b << 5) + u;
+                const uint32_t o = __shfl_sync(kFull, dA.x, u);
+                const uint32_t lw = __shfl_sync(kFull, dA.y, u);
+                const int lo = (int)(lw & 0xFFFFu);
+                const int w = (int)(lw >> 16);
+                if (w <= 32) {
+                    const int c = lane < w ? (int)cb[u * 32 + lane] : 0;
+                    int L;
+                    if (k == 0) {
+                        L = c;
+                    } else if (loc == 0) {
+                        const int* prow = rows + ((k + 1) & 1) * kRowLen;
+                        const int sc = min(max(lane + (lo - qlo), -2), 33) + kRowPad;
+                        L = c + min(min(min(prow[sc - 1], prow[sc + 1]) + P1, prow[sc]), m + P2) - m;
+                    } else {
+                        spill();
+                        const uint16_t* src16 = buf16 + qb * DP;
+                        const int d = lo + lane, qhi = qlo + qw - 1;
+                        const int uc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
+                        const int ul = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
+                        const int ur = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
+                        L = c + min(min(min(ul, ur) + P1, uc), m + P2) - m;
+                    }
+                    L = lane < w ? L : kInf;
+                    rows[(k & 1) * kRowLen + kRowPad + lane] = L;
+                    if (lane < w) Lv[o + lane] = (uint8_t)L;
+                    m = (int)__reduce_min_sync(kFull, (unsigned)L);
+                    __syncwarp();
+                    Nreg = L;
+                    loc = 0;
+                } else if (w == D) {
+                    uint32_t c2[NP];
+                    dense_costs(k, c2);
+                    int lmin;
+                    if (k == 0) {
+                        uint32_t pmin = kInf2;
+#pragma unroll
+                        for (int k2 = 0; k2 < NP; ++k2) {
+                            Dreg[k2] = (c2[k2] & keep[k2]) | (kInf2 & ~keep[k2]);
+                            pmin = vmin2(pmin, Dreg[k2]);
+                        }
+                        lmin = (int)min(pmin & 0xFFFFu, pmin >> 16);
+                    } else if (loc == 1) {
+                        uint32_t Lq[NP];
+#pragma unroll
+                        for (int k2 = 0; k2 < NP; ++k2) Lq[k2] = Dreg[k2];
+                        lmin = dense_update(Lq, c2);
+                    } else {
+                        spill();
+                        const uint32_t* srcp = buf0 + qb * kBufPairs;
+                        const int qhi = qlo + qw - 1;
+                        uint32_t Lq[NP];
+#pragma unroll
+                        for (int k2 = 0; k2 < NP; ++k2)
+                            Lq[k2] = mask_pair(srcp[(LPL * lane) / 2 + k2], LPL * lane + 2 * k2, qlo, qhi);
+                        lmin = dense_update(Lq, c2);
+                    }
+                    emit_dense(o);
+                    m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
+                    loc = 1;
+                } else {
+                    // ---------------------------------------------------- other widths
+                    if (k > 0) spill();
+                    __syncwarp();
+                    const uint16_t* src16 = buf16 + qb * DP;
+                    uint16_t* dst16 = buf16 + (qb ^ 1) * DP;
+                    const int qhi = qlo + qw - 1;
+                    int lmin = kInf;
+                    for (int j0 = 0; j0 < w; j0 += 32) {
+                        const int j = j0 + lane;
+                        const bool act = j < w;
+                        const int d = lo + j;
+                        const int c = act ? (int)__ldg(C + o + j) : 0;
+                        int L;
+                        if (k == 0) {
+                            L = c;
+                        } else {
+                            const int uc = (d >= qlo && d <= qhi) ? (int)src16[d] : kInf;
+                            const int ul = (d - 1 >= qlo && d - 1 <= qhi) ? (int)src16[d - 1] : kInf;
+                            const int ur = (d + 1 >= qlo && d + 1 <= qhi) ? (int)src16[d + 1] : kInf;
+                            L = c + min(min(min(ul, ur) + P1, uc), m + P2) - m;
+                        }
+                        L = act ? L : kInf;
+                        if (act) {
+                            dst16[d] = (uint16_t)L;
+                            Lv[o + j] = (uint8_t)L;
+                        }
+                        lmin = min(lmin, L);
+                    }
+                    m = (int)__reduce_min_sync(kFull, (unsigned)lmin);
+                    qb ^= 1;
+                    loc = 2;
+                    __syncwarp();
+                }
+                qlo = lo;
+                qw = w;
+            }
+        }
+        dA = dB;
+        dB = dC;
+        dmA = dmB;
+        dmB = dmC;
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------------------------
 // Pairs of lines. Directions come in opposite pairs (codes 2s and 2s + 1) that walk the same
 // geometric lines from their two ends; one warp walks both lines of a pair step by step, the two
 // independent recurrences interleaved (a lone recurrence leaves the warp waiting on its own
@@ -874,13 +1205,19 @@ __host__ __device__ constexpr int sgm_narrow_words() {
 template <int LPL>
 __host__ __device__ constexpr int sgm_dense_slot() { return 32 * LPL > 128 ? 32 * LPL : 128; }
 template <int LPL>
-__host__ __device__ constexpr int sgm_pair_words() {
+__host__ __device__ constexpr int sgm_pair_words0() {
     return sgm_narrow_words<LPL>() > 2 * kRingP * sgm_dense_slot<LPL>() / 4
                ? (sgm_narrow_words<LPL>() > sgm_warp_words<LPL>() ? sgm_narrow_words<LPL>()
                                                                    : sgm_warp_words<LPL>())
                : (2 * kRingP * sgm_dense_slot<LPL>() / 4 > sgm_warp_words<LPL>()
                       ? 2 * kRingP * sgm_dense_slot<LPL>() / 4
                       : sgm_warp_words<LPL>());
+}
+
+template <int LPL>
+__host__ __device__ constexpr int sgm_pair_words() {
+    return sgm_pair_words0<LPL>() > sgm_mixed_words<LPL>() ? sgm_pair_words0<LPL>()
+                                                           : sgm_mixed_words<LPL>();
 }
 
 // Two lines whose windows are all the full range (the dense form of sgm_line, interleaved). Each
@@ -1032,9 +1369,11 @@ __device__ __forceinline__ void sgm_pair_dense(const uint8_t* __restrict__ C,
 // One pair of lines of one image: scan the windows of the (common) geometric line once. Lines
 // whose windows are all the full range are walked together by twin 0 with the paired full-range
 // walker (two interleaved recurrences per warp); other lines are walked one per twin, line A by
-// twin 0 and line B by twin 1, with the narrow walker (at most one pixel in 8 wider than 32
-// labels) or the general one. twin < 0: this warp walks the whole pair alone. The choice changes
-// the work, never the result.
+// twin 0 and line B by twin 1: with the branch-free narrow walker when no window is wider than 32
+// labels; the general walker when more than one pixel in 8 has a window of 33 .. D - 1 labels;
+// the narrow walker when at most one pixel in 8 is wide and the wide ones are scattered (runs
+// shorter than 8 on average); else the mixed walker (narrow and full-range runs at full speed). twin < 0: this warp walks the
+// whole pair alone. The choice changes the work, never the result.
 template <int LPL>
 __device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
                                          const uint2* __restrict__ desc, int W, int Hh, int D,
@@ -1045,14 +1384,23 @@ __device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
     const int lB = partner_line(codeA, lA, codeB, W, Hh);
     int i0, step, len;
     line_geometry(codeA, lA, W, Hh, i0, step, len);
-    int wide = 0, full = 0;
-    for (int kk = lane; kk < len; kk += 32) {
-        const int w_ = (int)(__ldg(&desc[i0 + kk * step].y) >> 16);
-        wide += w_ > 32 ? 1 : 0;
+    int wide = 0, full = 0, runs = 0;
+    bool carry = false;  // whether the last pixel of the previous 32 was wide
+    for (int k0 = 0; k0 < len; k0 += 32) {
+        const int kk = k0 + lane;
+        const int w_ = kk < len ? (int)(__ldg(&desc[i0 + kk * step].y) >> 16) : 0;
+        const bool wd = w_ > 32;
+        const bool up = __shfl_up_sync(kFull, wd, 1) != 0;  // every lane takes part
+        const bool before = lane == 0 ? carry : up;
+        wide += wd ? 1 : 0;
         full += w_ == D ? 1 : 0;
+        runs += (wd && !before) ? 1 : 0;  // a run of wide windows starts here
+        carry = __shfl_sync(kFull, wd, 31) != 0;
     }
     wide = (int)__reduce_add_sync(kFull, (unsigned)wide);
     full = (int)__reduce_add_sync(kFull, (unsigned)full);
+    runs = (int)__reduce_add_sync(kFull, (unsigned)runs);
+    const int other = wide - (D > 32 ? full : 0);  // windows of 33 .. D - 1 labels
     if (full == len && D > 32) {
         if (twin == 1) return;
         const int code[2] = {codeA, codeB};
@@ -1061,7 +1409,6 @@ __device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
         sgm_pair_dense<LPL>(C, desc, W, Hh, D, P1, P2, code, l, Lv, wsm);
         return;
     }
-    const bool narrow = wide * 8 <= len;
     for (int t = 0; t < 2; ++t) {
         if (twin >= 0 && twin != t) continue;
         const int code = t ? codeB : codeA;
@@ -1069,10 +1416,12 @@ __device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
         uint8_t* const Lv = t ? LvB : LvA;
         if (wide == 0)
             sgm_line_narrow<LPL, true>(C, desc, W, Hh, D, P1, P2, code, li, Lv, wsm);
-        else if (narrow)
+        else if (other * 8 > len)
+            sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code, li, Lv, wsm);
+        else if (runs * 8 > wide && wide * 8 <= len)  // few wide windows, scattered
             sgm_line_narrow<LPL, false>(C, desc, W, Hh, D, P1, P2, code, li, Lv, wsm);
         else
-            sgm_line<LPL>(C, desc, W, Hh, D, P1, P2, code, li, Lv, wsm);
+            sgm_line_mixed<LPL>(C, desc, W, Hh, D, P1, P2, code, li, Lv, wsm);
     }
 }
 
