@@ -414,6 +414,8 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     ctx = make(tsgm.FLAG_FILL_GAPS)
     ctx_full = make(tsgm.FLAG_FULL_RANGE)
     ctx_plain = make(0)  # the prediction without gap filling, for comparison
+    # the prediction with its edges rejected (Sec. 2.2) before the gap filling, for comparison
+    ctx_edge = make(tsgm.FLAG_FILL_GAPS | tsgm.FLAG_EDGE_REJECT)
     Dout = torch.empty((H, W), dtype=torch.float32, device=dev)
     Pout = torch.empty_like(Dout)
 
@@ -446,6 +448,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     cells_red, bad_red = characterise(ctx)
     cells_full, bad_full = characterise(ctx_full)
     cells_plain, bad_plain = characterise(ctx_plain)
+    cells_edge, bad_edge = characterise(ctx_edge)
 
     def timed(c, K_steps, W_steps, profile):
         for _ in range(W_steps):
@@ -481,6 +484,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
                                       profile=True)
     k_full = max(1, args.steps // 2)
     t_plain, _, _, stages_plain = timed(ctx_plain, k_full, 3, profile=True)
+    t_edge, _, _, _ = timed(ctx_edge, k_full, 3, profile=False)
 
     # end to end through the host-buffer entry point (pinned host memory)
     hl = [torch.from_numpy(x).pin_memory() for x in seq.left]
@@ -556,6 +560,9 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
         "without_gap_fill": {"fps": N_FRAMES * k_full / (t_plain / 1000.0),
                              "search_space_frac": [c / (n * 128) for c in cells_plain],
                              "bad3px_updated": bad_plain},
+        "with_edge_rejection": {"fps": N_FRAMES * k_full / (t_edge / 1000.0),
+                                "search_space_frac": [c / (n * 128) for c in cells_edge],
+                                "bad3px_updated": bad_edge},
         "search_space_frac": [c / (n * 128) for c in cells_red],
         "bad3px": {"reduced_updated": bad_red, "full_range_updated": bad_full},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},

@@ -58,6 +58,9 @@ typedef enum {
                                         plain full-range SGM every frame (still Kalman-updated) */
 #define TSGM_FLAG_FILL_GAPS 4u       /* tsgm_frame fills one-pixel gaps of the prediction
                                         (Sec. 2.2, Eq. 7-8) before choosing the windows */
+#define TSGM_FLAG_EDGE_REJECT 8u     /* tsgm_frame rejects predicted pixels next to a disparity
+                                        discontinuity (Sec. 2.2, disparity refinement), before
+                                        the gap filling */
 
 typedef struct {
     int32_t width, height;       /* image size, 1 <= width <= 13000, 1 <= height */
@@ -72,10 +75,11 @@ typedef struct {
     int32_t lr_tol;              /* left-right check tolerance in px (Sec. 2.4) */
     uint32_t flags;              /* TSGM_FLAG_* */
     float gamma_f;               /* similarity threshold of the gap filling (Eq. 8), px */
+    float edge_thr;              /* discontinuity threshold of the edge rejection, px */
 } tsgm_params;
 
 /* Fill *p with the defaults: d_max 127, census 9x7, 8 paths, P1 8, P2 32, sigma_mult 3,
- * q 0.25, S_max 10, r_min 0.5, lr_tol 1, flags 0, gamma_f 1. */
+ * q 0.25, S_max 10, r_min 0.5, lr_tol 1, flags 0, gamma_f 1, edge_thr 1. */
 void tsgm_default_params(tsgm_params* p, int32_t width, int32_t height);
 
 /* Create a context. `cuda_stream` is the cudaStream_t every call of the context is enqueued on
@@ -113,6 +117,12 @@ tsgm_status tsgm_warp_predict(tsgm_ctx* ctx, const float* prev_D, const float* p
  * variance; then the same with the vertical neighbours on the horizontally filled map. Each pass
  * reads the map as it was before the pass. Uses the context's D_z/r_z buffers as scratch. */
 tsgm_status tsgm_fill_gaps(tsgm_ctx* ctx, float* pred_D, float* pred_P);
+
+/* Edge rejection of a prediction (Sec. 2.2, disparity refinement), in place: a valid pixel whose
+ * 8-neighbourhood (inside the image) holds a valid prediction differing by at least edge_thr
+ * becomes invalid (-1 in both maps); invalid neighbours do not count. The pass reads the map as it
+ * was before it. Uses the context's D_z/r_z buffers as scratch. */
+tsgm_status tsgm_edge_reject(tsgm_ctx* ctx, float* pred_D, float* pred_P);
 
 /* Reduced search space (Sec. 2.3): d_lo = max(0, floor(d - k sqrt(p))), d_hi = min(d_max,
  * ceil(d + k sqrt(p))) with k = sigma_mult, binary32; the whole range [0, d_max] where the

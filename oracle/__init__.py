@@ -74,6 +74,8 @@ class Params:
     lr_tol: int = 1
     fill_gaps: bool = False    # Sec. 2.2, Eq. 7-8 on the prediction
     gamma_f: float = 1.0       # Eq. 8 similarity threshold (value not given)
+    edge_reject: bool = False  # Sec. 2.2, reject predicted pixels near disparity discontinuities
+    edge_thr: float = 1.0      # discontinuity threshold of the edge rejection (value not given)
 
     @property
     def D(self) -> int:
@@ -123,6 +125,17 @@ def fill_gaps(Dp, Pp, gamma_f: float):
     D = np.array(Dp, dtype=np.float32, copy=True)
     P = np.array(Pp, dtype=np.float32, copy=True)
     lib.oracle_fill_gaps(W, Hh, ctypes.c_float(gamma_f), _p(D), _p(P))
+    return D, P
+
+
+def edge_reject(Dp, Pp, edge_thr: float):
+    """Sec. 2.2 disparity refinement: reject predicted pixels next to a disparity discontinuity
+    (8-neighbourhood, |d - d_n| >= edge_thr with a valid neighbour; copies)."""
+    lib = _load()
+    Hh, W = Dp.shape
+    D = np.array(Dp, dtype=np.float32, copy=True)
+    P = np.array(Pp, dtype=np.float32, copy=True)
+    lib.oracle_edge_reject(W, Hh, ctypes.c_float(edge_thr), _p(D), _p(P))
     return D, P
 
 
@@ -271,6 +284,9 @@ class Tracker:
             Dp, Pp, win = warp_predict(self.D, self.P, H32, np.float32(cx), np.float32(cy), prm.q)
             out["winner"] = win
             out["H32"] = H32
+            out["Dpred_raw"], out["Ppred_raw"] = Dp, Pp
+            if prm.edge_reject:
+                Dp, Pp = edge_reject(Dp, Pp, prm.edge_thr)
             if prm.fill_gaps:
                 Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)
         lo, hi, off, n_cells = windows(Dp, Pp, prm.D, prm.sigma_mult)

@@ -172,6 +172,37 @@ void oracle_fill_gaps(int W, int Hh, float gamma_f, float* D, float* P) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Sec. 2.2, disparity refinement: predicted pixels near a disparity discontinuity are rejected.
+// Reading (the paper gives neither the neighbourhood nor the threshold): a valid predicted pixel
+// becomes invalid (-1, -1) when one of its 8 neighbours inside the image holds a valid
+// prediction whose disparity differs by at least edge_thr (the negation of the similarity of
+// Eq. 8); invalid neighbours are holes, not edges. Reads the map as it was before the pass.
+// ------------------------------------------------------------------------------------------
+void oracle_edge_reject(int W, int Hh, float edge_thr, float* D, float* P) {
+    const int n = W * Hh;
+    std::vector<float> d0(D, D + n), p0(P, P + n);
+    for (int y = 0; y < Hh; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int i = y * W + x;
+            if (!(finite_nonneg(d0[i]) && finite_nonneg(p0[i]))) continue;
+            bool edge = false;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (dx == 0 && dy == 0) continue;
+                    const int xn = x + dx, yn = y + dy;
+                    if (xn < 0 || xn >= W || yn < 0 || yn >= Hh) continue;
+                    const int j = yn * W + xn;
+                    if (!(finite_nonneg(d0[j]) && finite_nonneg(p0[j]))) continue;
+                    if (!(std::fabs(d0[i] - d0[j]) < edge_thr)) edge = true;
+                }
+            if (edge) {
+                D[i] = -1.0f;
+                P[i] = -1.0f;
+            }
+        }
+}
+
+// ------------------------------------------------------------------------------------------
 // Sec. 2.3: reduced search interval [d - 3 sqrt(p), d + 3 sqrt(p)] (multiplier k = sigma_mult),
 // rounded outwards to integers and clipped to [0, D-1]. A pixel without a valid prediction
 // (d < 0, p < 0, NaN or inf), or whose interval misses [0, D-1], is searched over the whole

@@ -83,6 +83,10 @@ tsgm_status check_params(const tsgm_params* p, std::string& why) {
         why = "width * height * (d_max + 1) must stay below 2^32 cells";
         return TSGM_ERR_INVALID_ARG;
     }
+    if (!(p->edge_thr >= 0.0f) || !std::isfinite(p->edge_thr)) {
+        why = "edge_thr must be finite and >= 0";
+        return TSGM_ERR_INVALID_ARG;
+    }
     if (!(p->gamma_f >= 0.0f) || !std::isfinite(p->gamma_f)) {
         why = "gamma_f must be finite and >= 0";
         return TSGM_ERR_INVALID_ARG;
@@ -186,6 +190,19 @@ tsgm_status warp_stage(tsgm_ctx* ctx, const float* prevD, const float* prevP, co
     return TSGM_OK;
 }
 
+// Sec. 2.2 edge rejection, in place on (D, P) through the D_z/r_z scratch.
+tsgm_status edge_reject_stage(tsgm_ctx* ctx, float* D, float* P) {
+    stage_begin(ctx, TSGM_STAGE_WARP);
+    TSGM_LAUNCH(launch_edge_reject(D, P, ctx->W, ctx->H, ctx->prm.edge_thr, ctx->Dz, ctx->rz,
+                                   ctx->stream),
+                "edge reject");
+    const size_t bytes = sizeof(float) * (size_t)ctx->n;
+    TSGM_CK(cudaMemcpyAsync(D, ctx->Dz, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+    TSGM_CK(cudaMemcpyAsync(P, ctx->rz, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+    stage_end(ctx, TSGM_STAGE_WARP);
+    return TSGM_OK;
+}
+
 // Eq. 7-8, in place on (D, P): horizontal pass into the D_z/r_z scratch, vertical pass back.
 tsgm_status fill_gaps_stage(tsgm_ctx* ctx, float* D, float* P) {
     stage_begin(ctx, TSGM_STAGE_WARP);
@@ -263,6 +280,7 @@ void tsgm_default_params(tsgm_params* p, int32_t width, int32_t height) {
     p->lr_tol = 1;
     p->flags = 0;
     p->gamma_f = 1.0f;
+    p->edge_thr = 1.0f;
 }
 
 tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out) {
@@ -374,6 +392,14 @@ tsgm_status tsgm_fill_gaps(tsgm_ctx* ctx, float* pred_D, float* pred_P) {
     return fill_gaps_stage(ctx, pred_D, pred_P);
 }
 
+tsgm_status tsgm_edge_reject(tsgm_ctx* ctx, float* pred_D, float* pred_P) {
+    if (!ctx) return TSGM_ERR_INVALID_ARG;
+    if (!pred_D || !pred_P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_edge_reject: null pointer");
+    if (pred_D == ctx->Dz || pred_P == ctx->rz || pred_D == ctx->rz || pred_P == ctx->Dz)
+        return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_edge_reject: maps alias the context scratch");
+    return edge_reject_stage(ctx, pred_D, pred_P);
+}
+
 tsgm_status tsgm_windows(tsgm_ctx* ctx, const float* pred_D, const float* pred_P, int16_t* d_lo,
                          int16_t* d_hi, uint64_t* n_cells_host) {
     if (!ctx) return TSGM_ERR_INVALID_ARG;
@@ -423,6 +449,7 @@ tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
         return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: pose required after the first frame");
     if (ctx->has_prev) {
         TSGM_TRY(warp_stage(ctx, ctx->stateD, ctx->stateP, R, t, K, baseline, ctx->predD, ctx->predP));
+        if (ctx->prm.flags & TSGM_FLAG_EDGE_REJECT) TSGM_TRY(edge_reject_stage(ctx, ctx->predD, ctx->predP));
         if (ctx->prm.flags & TSGM_FLAG_FILL_GAPS) TSGM_TRY(fill_gaps_stage(ctx, ctx->predD, ctx->predP));
     } else {
         TSGM_LAUNCH(launch_fill(ctx->predD, -1.0f, ctx->n, ctx->stream), "fill");

@@ -42,6 +42,8 @@ cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t*
                            const uint32_t* rowcells, int W, int Hh, uint32_t* off, uint2* desc,
                            uint32_t* cells_total, cudaStream_t st);
 cudaError_t launch_fill(float* a, float v, int n, cudaStream_t st);
+cudaError_t launch_edge_reject(const float* Din, const float* Pin, int W, int Hh, float thr,
+                               float* Dout, float* Pout, cudaStream_t st);
 cudaError_t launch_fill_gaps(const float* Din, const float* Pin, int W, int Hh, float gamma_f,
                              int vertical, float* Dout, float* Pout, cudaStream_t st);
 cudaError_t launch_kalman(const float* Dp, const float* Pp, const float* Dz, const float* rz, int n,

@@ -216,6 +216,39 @@ int grid_for(int n, int threads) {
     return g < 1 ? 1 : (g > cap ? cap : g);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Edge rejection (Sec. 2.2, disparity refinement): a valid predicted pixel with a valid
+// 8-neighbour whose disparity differs by at least thr becomes invalid; one thread per pixel,
+// out of place.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_edge_reject(const float* __restrict__ Din,
+                                                     const float* __restrict__ Pin, int W, int Hh,
+                                                     float thr, float* __restrict__ Dout,
+                                                     float* __restrict__ Pout) {
+    const int n = W * Hh;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float d = Din[i], p = Pin[i];
+        bool edge = false;
+        if (valid_value(d) && valid_value(p)) {
+            const int y = i / W, x = i - y * W;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int yn = y + dy;
+                if (yn < 0 || yn >= Hh) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int xn = x + dx;
+                    if ((dx == 0 && dy == 0) || xn < 0 || xn >= W) continue;
+                    const int j = yn * W + xn;
+                    const float dn = Din[j], pn = Pin[j];
+                    if (valid_value(dn) && valid_value(pn) && !(fabsf(__fsub_rn(d, dn)) < thr))
+                        edge = true;
+                }
+            }
+        }
+        Dout[i] = edge ? -1.0f : d;
+        Pout[i] = edge ? -1.0f : p;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_warp_scatter(const float* Dprev, const float* Pprev, const float* H, float cx,
@@ -254,6 +287,15 @@ cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t*
                            const uint32_t* rowcells, int W, int Hh, uint32_t* off, uint2* desc,
                            uint32_t* cells_total, cudaStream_t st) {
     k_offsets<<<Hh, 512, 0, st>>>(lo, hi, rowsum, rowcells, W, Hh, off, desc, cells_total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_reject(const float* Din, const float* Pin, int W, int Hh, float thr,
+                               float* Dout, float* Pout, cudaStream_t st) {
+    const int n = W * Hh;
+    int blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_edge_reject<<<blocks, 256, 0, st>>>(Din, Pin, W, Hh, thr, Dout, Pout);
     return cudaGetLastError();
 }
 

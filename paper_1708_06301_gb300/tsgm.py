@@ -21,6 +21,7 @@ OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_UN
 FLAG_KEEP_INTERNALS = 1
 FLAG_FULL_RANGE = 2
 FLAG_FILL_GAPS = 4
+FLAG_EDGE_REJECT = 8
 N_STAGES = 8
 STAGES = ["warp", "windows", "census", "cost", "sgm", "select", "kalman", "offsets"]
 BUF = dict(census_l=0, census_r=1, offsets=2, cost=3, S=4, dstar=5, dright=6, lr_valid=7,
@@ -39,7 +40,8 @@ class Params(ctypes.Structure):
                 ("n_paths", ctypes.c_int32), ("P1", ctypes.c_int32), ("P2", ctypes.c_int32),
                 ("sigma_mult", ctypes.c_float), ("q", ctypes.c_float), ("S_max", ctypes.c_float),
                 ("r_min", ctypes.c_float), ("lr_tol", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("gamma_f", ctypes.c_float)]
+                ("gamma_f", ctypes.c_float),
+                ("edge_thr", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -67,6 +69,7 @@ _SIGS = {
     "tsgm_state_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
     "tsgm_census": (ctypes.c_int, [_vp, _vp, _vp]),
     "tsgm_fill_gaps": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tsgm_edge_reject": (ctypes.c_int, [_vp, _vp, _vp]),
     "tsgm_inspect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64]),
     "tsgm_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -290,6 +293,10 @@ class Context:
 
     def fill_gaps(self, pred_D, pred_P):
         self._check(self.lib.tsgm_fill_gaps(self.h, _ptr(pred_D), _ptr(pred_P)), "tsgm_fill_gaps")
+
+    def edge_reject(self, pred_D, pred_P):
+        self._check(self.lib.tsgm_edge_reject(self.h, _ptr(pred_D), _ptr(pred_P)),
+                    "tsgm_edge_reject")
 
     def census(self, img, codes):
         self._check(self.lib.tsgm_census(self.h, _ptr(img), _ptr(codes)), "tsgm_census")

@@ -379,3 +379,35 @@ def test_frames_with_gap_filling(tsgm, slow_case):
         o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
         assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
         assert_maps(g[k]["D"], g[k]["P"], o["D"], o["P"])
+
+
+@pytest.mark.parametrize("thr", [1.0, 2.5])
+def test_edge_reject_bitexact(tsgm, thr):
+    """Edge rejection of a warped prediction (objects at several depths and holes): the GPU pass
+    equals the oracle's, and it rejects something."""
+    W, H = 1242, 375
+    seq = synth.kitti_like(2, n_frames=2)
+    D = seq.gt_disp[0].astype(np.float32)
+    P = np.full_like(D, 0.5)
+    D[::97, ::13] = -1.0                             # a few holes
+    K = synth.Camera(W, H, 721.0, 0.54).K
+    with make_ctx(tsgm, W, H, d_max=127, edge_thr=thr) as ctx:
+        pD, pP = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.warp_predict(dev(D), dev(P), seq.R[1], seq.t[1], K, f32(0.54), pD, pP)
+        Dw, Pw = host(pD, np.float32), host(pP, np.float32)
+        ctx.edge_reject(pD, pP)
+        Dg, Pg = host(pD, np.float32), host(pP, np.float32)
+    Do, Po = oracle.edge_reject(Dw, Pw, thr)
+    assert np.array_equal(Dg, Do) and np.array_equal(Pg, Po)
+    assert (Do < 0).sum() > (Dw < 0).sum()
+
+
+def test_frames_with_edge_rejection_and_gap_filling(tsgm):
+    seq, n = synth.small_pair(1), 2
+    W, H = seq.cam.W, seq.cam.H
+    g = run_sequence(tsgm, seq, n, 63, 5, 5, 4, flags=1 | 4 | 8)
+    tr = oracle.Tracker(oparams(W, H, d_max=63, fill_gaps=True, edge_reject=True))
+    for k in range(n):
+        o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
+        assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
+        assert_maps(g[k]["D"], g[k]["P"], o["D"], o["P"])

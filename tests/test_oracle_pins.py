@@ -601,3 +601,63 @@ def test_fill_gaps_horizontal_pass_comes_first():
     P = np.where(D >= 0, 1.0, -1.0).astype(np.float32)
     Df, _ = oracle.fill_gaps(D, P, 1.0)
     assert Df[0, 1] == 3 and Df[1, 1] == 3
+
+
+def test_edge_reject_hand_cases():
+    """Sec. 2.2: predicted pixels next to a disparity discontinuity are rejected (reading: any
+    valid 8-neighbour differing by >= edge_thr), both sides of the edge, nothing else."""
+    I = -1.0
+    # a vertical step between columns 2 and 3: those two columns go, the rest stays
+    D = np.array([[10, 10, 10, 20, 20, 20]] * 4, np.float32)
+    P = np.full_like(D, 2.0)
+    De, Pe = oracle.edge_reject(D, P, 1.0)
+    keep = np.ones_like(D, bool)
+    keep[:, 2:4] = False
+    assert np.array_equal(De[keep], D[keep]) and np.array_equal(Pe[keep], P[keep])
+    assert np.all(De[~keep] == -1) and np.all(Pe[~keep] == -1)
+    # a ramp whose steps (0.4 px across, 0.8 px diagonally) stay below the threshold: untouched
+    y, x = np.mgrid[0:5, 0:7].astype(np.float32)
+    R = (np.float32(10) + np.float32(0.4) * x + np.float32(0.4) * y).astype(np.float32)
+    Re, _ = oracle.edge_reject(R, np.ones_like(R), 1.0)
+    assert np.array_equal(Re, R)
+    # a difference equal to the threshold is a discontinuity (the similarity of Eq. 8 is strict)
+    E = np.array([[5, 6]], np.float32)
+    Ee, _ = oracle.edge_reject(E, np.ones_like(E), 1.0)
+    assert np.all(Ee == -1)
+    Ee2, _ = oracle.edge_reject(E, np.ones_like(E), 1.5)
+    assert np.array_equal(Ee2, E)
+    # holes are not edges: a valid pixel among invalid ones (or ones with an invalid variance)
+    # stays; a diagonal neighbour counts
+    H = np.array([[I, I, I], [I, 7, 30], [I, 40, I]], np.float32)
+    HP = np.where(H >= 0, 1.0, -1.0).astype(np.float32)
+    HP[1, 2] = -1.0                                  # (1, 2) has an invalid variance: a hole
+    He, _ = oracle.edge_reject(H, HP, 1.0)
+    assert He[1, 1] == -1 and He[2, 1] == -1         # 7 vs 40 (below): both rejected
+    assert He[1, 2] == 30                            # invalid pixels are left as they are
+    G = np.array([[I, I, I], [I, 7, I], [I, I, 90]], np.float32)
+    Ge, _ = oracle.edge_reject(G, np.where(G >= 0, 1.0, -1.0).astype(np.float32), 1.0)
+    assert Ge[1, 1] == -1 and Ge[2, 2] == -1         # diagonal neighbours: an edge
+    # one pixel, one row, one column: no neighbours beyond the image
+    assert oracle.edge_reject(np.array([[3.0]], np.float32), np.array([[1.0]], np.float32), 1.0)[0][0, 0] == 3.0
+
+
+def test_edge_reject_runs_before_gap_filling_in_the_tracker():
+    """The tracker refines the prediction in the paper's order: edge rejection, then gap filling
+    (Sec. 2.2); a one-pixel hole between two rejected edge pixels stays a hole."""
+    from paper_1708_06301_gb300 import synth
+    seq = synth.small_pair(1)
+    W, H = seq.cam.W, seq.cam.H
+    base = dict(d_max=63, census_w=5, census_h=5, n_paths=4)
+    outs = {}
+    for er in (False, True):
+        prm = oracle.Params(W, H, fill_gaps=True, edge_reject=er, **base)
+        tr = oracle.Tracker(prm)
+        tr.frame(seq.left[0], seq.right[0], None, None, seq.K, seq.cam.b)
+        outs[er] = tr.frame(seq.left[1], seq.right[1], seq.R[1], seq.t[1], seq.K, seq.cam.b, keep=True)
+    pd0, pd1 = outs[False]["Dpred"], outs[True]["Dpred"]
+    assert (pd1 < 0).sum() > (pd0 < 0).sum()        # the scene's object edges lose predictions
+    raw = (outs[True]["Dpred_raw"], outs[True]["Ppred_raw"])
+    ref = oracle.fill_gaps(*oracle.edge_reject(*raw, 1.0), 1.0)
+    swapped = oracle.edge_reject(*oracle.fill_gaps(*raw, 1.0), 1.0)
+    assert np.array_equal(ref[0], pd1) and np.array_equal(ref[1], outs[True]["Ppred"])
+    assert not np.array_equal(swapped[0], pd1)       # the order matters on this scene
