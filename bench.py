@@ -240,34 +240,48 @@ def bench_adjoint(dev, steps: int):
             "backward_ms_incl_host_reduction": float(np.median(bwd))}
 
 
+BATCH_STREAMS = 32
+BATCH_MAX_LABELS = 24
+
+
+def batched_stream(seqs, i: int):
+    """Inputs of stream i of the batched workload: its size (W, H, D), the rendered left and right
+    images, and per-pixel windows of 4-24 labels (uniform, seeded) around the rounded ground
+    truth, clipped into [0, D - 1]."""
+    from paper_1708_06301_gb300 import synth
+    W, H, D = mix_shape(i)
+    sq = seqs[(W, H)]
+    gt = np.clip(np.floor(sq.gt_disp[0] + 0.5), 0, D - 1).astype(np.int64).reshape(-1)
+    n = W * H
+    w = 4 + np.floor(synth.uniform01(200 + i, np.arange(n)) * 21).astype(np.int64)
+    lo = np.clip(gt - w // 2, 0, D - w)
+    hi = lo + w - 1
+    return (W, H, D, sq.left[0], sq.right[0], lo.astype(np.int16).reshape(H, W),
+            hi.astype(np.int16).reshape(H, W))
+
+
 def bench_batched(dev, steps: int, warmup: int):
     """32 streams (i mod 3 -> 640x480 D=64, 1242x375 D=128, 1920x1080 D=256), per-pixel windows of
     4-24 labels around the ground truth, one graph replay per step."""
     import torch
-    from paper_1708_06301_gb300 import synth, tsgm
+    from paper_1708_06301_gb300 import tsgm
     seqs = render_mix(1)
-    NS = 32
+    NS = BATCH_STREAMS
     params, L, R, LO, HI, DZ, RZ = [], [], [], [], [], [], []
     px = 0
     for i in range(NS):
-        W, H, D = mix_shape(i)
-        sq = seqs[(W, H)]
+        W, H, D, left_i, right_i, lo_i, hi_i = batched_stream(seqs, i)
         params.append(tsgm.default_params(W, H, d_max=D - 1))
-        gt = np.clip(np.floor(sq.gt_disp[0] + 0.5), 0, D - 1).astype(np.int64).reshape(-1)
-        n = W * H
-        w = 4 + np.floor(synth.uniform01(200 + i, np.arange(n)) * 21).astype(np.int64)
-        lo = np.clip(gt - w // 2, 0, D - w)
-        hi = lo + w - 1
-        L.append(torch.from_numpy(sq.left[0]).to(dev))
-        R.append(torch.from_numpy(sq.right[0]).to(dev))
-        LO.append(torch.from_numpy(lo.astype(np.int16).reshape(H, W)).to(dev))
-        HI.append(torch.from_numpy(hi.astype(np.int16).reshape(H, W)).to(dev))
+        L.append(torch.from_numpy(left_i).to(dev))
+        R.append(torch.from_numpy(right_i).to(dev))
+        LO.append(torch.from_numpy(lo_i).to(dev))
+        HI.append(torch.from_numpy(hi_i).to(dev))
         DZ.append(torch.empty((H, W), dtype=torch.float32, device=dev))
         RZ.append(torch.empty((H, W), dtype=torch.float32, device=dev))
-        px += n
+        px += W * H
     st = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    with tsgm.Batch(params, max_labels=24, stream=st.cuda_stream) as bt:
+    with tsgm.Batch(params, max_labels=BATCH_MAX_LABELS, stream=st.cuda_stream) as bt:
         tune_ms, shape = bt.autotune(L, R, LO, HI, DZ, RZ, reps=2)
         for _ in range(warmup):
             bt.match(L, R, LO, HI, DZ, RZ)

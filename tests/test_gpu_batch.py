@@ -113,3 +113,40 @@ def test_batch_skips_streams_without_enough_storage(tsgm):
     assert over == len(SHAPES)
     for k in range(len(SHAPES)):
         assert np.all(Dzs[k] == -1) and np.all(rzs[k] == -1)
+
+
+@pytest.mark.slow
+def test_batch_full_size_workload_against_oracle_and_single_streams(tsgm):
+    """The batched workload as timed (32 streams of 640x480 D=64, 1242x375 D=128 and 1920x1080
+    D=256 with 4-24-label windows, storage for 24 labels, autotuned launch shape): every stream
+    equals the single-image path, and one stream of each size equals the oracle."""
+    import bench
+    seqs = bench.render_mix(1)
+    streams = [bench.batched_stream(seqs, i) for i in range(bench.BATCH_STREAMS)]
+    prm = [tsgm.default_params(W, H, d_max=D - 1) for (W, H, D, *_r) in streams]
+    data = [(a, b, lo, hi) for (_W, _H, _D, a, b, lo, hi) in streams]
+    with tsgm.Batch(prm, max_labels=bench.BATCH_MAX_LABELS) as batch:
+        dl = [dev(x[0]) for x in data]
+        dr = [dev(x[1]) for x in data]
+        lo = [dev(x[2]) for x in data]
+        hi = [dev(x[3]) for x in data]
+        Dz = [empty((H, W), np.float32) for (W, H, *_r) in streams]
+        rz = [empty((H, W), np.float32) for (W, H, *_r) in streams]
+        batch.autotune(dl, dr, lo, hi, Dz, rz, reps=1)
+        batch.match(dl, dr, lo, hi, Dz, rz)
+        Dzs = [host(d, np.float32) for d in Dz]
+        rzs = [host(r, np.float32) for r in rz]
+        _, over = batch.cells()
+    assert over == 0
+    for k, (W, H, D, *_r) in enumerate(streams):
+        Ds, rs = single(tsgm, W, H, D, data[k])
+        assert np.array_equal(Dzs[k], Ds), k
+        assert np.array_equal(rzs[k], rs), k
+    for k in range(3):
+        W, H, D, a, b, lo_k, hi_k = streams[k]
+        Do, ro = oracle.match(a, b, lo_k, hi_k, oracle.Params(W, H, d_max=D - 1, census_w=9,
+                                                               census_h=7, n_paths=8))
+        assert np.array_equal(Dzs[k] < 0, Do < 0), k
+        v = Do >= 0
+        assert np.max(np.abs(Dzs[k][v] - Do[v]), initial=0) <= 1e-4, k
+        assert np.array_equal(rzs[k][v], ro[v]), k
