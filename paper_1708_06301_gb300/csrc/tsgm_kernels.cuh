@@ -789,11 +789,19 @@ __device__ __forceinline__ void sgm_line_narrow(const uint8_t* __restrict__ C,
                 uint16_t* dst16 = buf16 + (qb ^ 1) * DP;
                 const int qhi = qlo + qw - 1;
                 int lmin = kInf;
-                for (int j0 = 0; j0 < w; j0 += 32) {
+                // every cost load first (one memory round trip), then the labels
+                int cv[LPL];
+#pragma unroll
+                for (int r = 0; r < LPL; ++r)
+                    cv[r] = 32 * r + lane < w ? (int)__ldg(C + o + 32 * r + lane) : 0;
+#pragma unroll
+                for (int r = 0; r < LPL; ++r) {
+                    const int j0 = 32 * r;
+                    if (j0 >= w) break;
                     const int j = j0 + lane;
                     const bool act = j < w;
                     const int d = lo + j;
-                    const int c = act ? (int)__ldg(C + o + j) : 0;
+                    const int c = cv[r];
                     int L;
                     if (k == 0) {
                         L = c;
@@ -1132,11 +1140,19 @@ __device__ __forceinline__ void sgm_line_mixed(const uint8_t* __restrict__ C,
                     uint16_t* dst16 = buf16 + (qb ^ 1) * DP;
                     const int qhi = qlo + qw - 1;
                     int lmin = kInf;
-                    for (int j0 = 0; j0 < w; j0 += 32) {
+                    // every cost load first (one memory round trip), then the labels
+                    int cv[LPL];
+#pragma unroll
+                    for (int r = 0; r < LPL; ++r)
+                        cv[r] = 32 * r + lane < w ? (int)__ldg(C + o + 32 * r + lane) : 0;
+#pragma unroll
+                    for (int r = 0; r < LPL; ++r) {
+                        const int j0 = 32 * r;
+                        if (j0 >= w) break;
                         const int j = j0 + lane;
                         const bool act = j < w;
                         const int d = lo + j;
-                        const int c = act ? (int)__ldg(C + o + j) : 0;
+                        const int c = cv[r];
                         int L;
                         if (k == 0) {
                             L = c;
