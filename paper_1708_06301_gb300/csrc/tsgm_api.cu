@@ -141,6 +141,7 @@ void free_all(tsgm_ctx* c) {
                     c->rz,      c->stateD,  c->stateP, c->lo,     c->hi,      c->dstar,
                     c->dright,  c->lrvalid, c->off,    c->rowsum, c->C,       c->S,
                     c->rowcells, c->cells,  c->desc,  c->Lvol,  c->adj_partials,
+                    c->wq,      c->gkeys,   c->wds,
                     c->d_left,  c->d_right, c->d_outD, c->d_outP};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -218,10 +219,10 @@ tsgm_status windows_stage(tsgm_ctx* ctx, const float* pD, const float* pP, int16
                           int16_t* hi) {
     stage_begin(ctx, TSGM_STAGE_WINDOWS);
     TSGM_LAUNCH(launch_windows(pD, pP, ctx->W, ctx->H, ctx->D, ctx->prm.sigma_mult, lo, hi, ctx->rowsum,
-                               ctx->rowcells, ctx->stream),
+                               ctx->rowcells, ctx->wq, ctx->stream),
                 "windows");
     TSGM_LAUNCH(launch_offsets(lo, hi, ctx->rowsum, ctx->rowcells, ctx->W, ctx->H, ctx->off, ctx->desc,
-                               ctx->cells, ctx->stream),
+                               ctx->cells, ctx->wq, ctx->stream),
                 "offsets");
     stage_end(ctx, TSGM_STAGE_WINDOWS);
     return TSGM_OK;
@@ -252,7 +253,8 @@ tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* righ
     TSGM_LAUNCH(launch_select(ctx->Lvol, ctx->max_cells, p.n_paths, ctx->desc, ctx->W, ctx->H, ctx->D,
                               s_thr, p.r_min, p.lr_tol, Dz, rz, keep ? ctx->S : nullptr,
                               keep ? ctx->dstar : nullptr, keep ? ctx->dright : nullptr,
-                              keep ? ctx->lrvalid : nullptr, ctx->stream),
+                              keep ? ctx->lrvalid : nullptr, ctx->wq, ctx->gkeys, ctx->wds,
+                              ctx->stream),
             "select");
     stage_end(ctx, TSGM_STAGE_SELECT);
     return TSGM_OK;
@@ -323,6 +325,12 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ok = ok && alloc(&ctx->rowsum, (size_t)ctx->H) == cudaSuccess;
     ok = ok && alloc(&ctx->rowcells, 2 * (size_t)ctx->H) == cudaSuccess;
     ok = ok && alloc(&ctx->cells, 2) == cudaSuccess;
+    ok = ok && alloc(&ctx->wq, n + 1) == cudaSuccess;
+    ok = ok && alloc(&ctx->gkeys, n) == cudaSuccess;
+    ok = ok && alloc(&ctx->wds, n) == cudaSuccess;
+    // no key yet (the selection keeps this state between images); complete before any stream
+    ok = ok && cudaMemset(ctx->gkeys, 0xFF, n * sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(nullptr) == cudaSuccess;
     ok = ok && alloc(&ctx->desc, n) == cudaSuccess;
     ok = ok && alloc(&ctx->C, (size_t)ctx->max_cells + 64) == cudaSuccess;
     ok = ok && alloc(&ctx->S, (size_t)ctx->max_cells + 64) == cudaSuccess;
@@ -418,10 +426,10 @@ tsgm_status tsgm_match(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
     // the caller's windows are copied, clamped into [0, d_max], into the context's buffers
     stage_begin(ctx, TSGM_STAGE_OFFSETS);
     TSGM_LAUNCH(launch_sanitize(d_lo, d_hi, ctx->W, ctx->H, ctx->D, ctx->lo, ctx->hi, ctx->rowsum,
-                                ctx->rowcells, ctx->stream),
+                                ctx->rowcells, ctx->wq, ctx->stream),
                 "windows copy");
     TSGM_LAUNCH(launch_offsets(ctx->lo, ctx->hi, ctx->rowsum, ctx->rowcells, ctx->W, ctx->H, ctx->off,
-                               ctx->desc, ctx->cells, ctx->stream),
+                               ctx->desc, ctx->cells, ctx->wq, ctx->stream),
                 "offsets");
     stage_end(ctx, TSGM_STAGE_OFFSETS);
     return match_stages(ctx, left, right, ctx->lo, ctx->hi, D_z, r_z);

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(512) kb_offsets(const BStream* __restrict__ st
     const BStream& b = st[s];
     const int y = blockIdx.x - tb->row_base[s];
     offsets_row(b.lo, b.hi, b.rowsum, b.rowcells, b.rowcells + b.H, b.W, b.H, y, b.off, b.desc,
-                b.cells);
+                b.cells, nullptr);
     if (y == b.H - 1 && threadIdx.x == 0)
         *b.status = (uint64_t)b.off[(size_t)b.W * b.H] > b.capacity ? 1u : 0u;
 }

@@ -34,13 +34,14 @@ cudaError_t launch_warp_gather(const unsigned long long* keys, const float* Dpre
                                cudaStream_t st);
 cudaError_t launch_windows(const float* Dp, const float* Pp, int W, int Hh, int D, float k,
                            int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
-                           cudaStream_t st);
+                           uint32_t* wq, cudaStream_t st);
 cudaError_t launch_sanitize(const int16_t* lo_in, const int16_t* hi_in, int W, int Hh, int D,
                             int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
-                            cudaStream_t st);
+                            uint32_t* wq, cudaStream_t st);
+// wq: the queue of wide pixels (see select_split), cleared by launch_windows / launch_sanitize
 cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t* rowsum,
                            const uint32_t* rowcells, int W, int Hh, uint32_t* off, uint2* desc,
-                           uint32_t* cells_total, cudaStream_t st);
+                           uint32_t* cells_total, uint32_t* wq, cudaStream_t st);
 cudaError_t launch_fill(float* a, float v, int n, cudaStream_t st);
 cudaError_t launch_edge_reject(const float* Din, const float* Pin, int W, int Hh, float thr,
                                float* Dout, float* Pout, cudaStream_t st);
@@ -58,7 +59,7 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
                           int W, int Hh, int D, float s_thr, float r_min, int lr_tol, float* Dz,
                           float* rz, uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
-                          cudaStream_t st);
+                          const uint32_t* wq, uint32_t* gkeys, int16_t* wds, cudaStream_t st);
 
 }  // namespace tsgm
 
@@ -89,6 +90,9 @@ struct tsgm_ctx {
     uint32_t* rowsum = nullptr;    // storage cells per row
     uint32_t* rowcells = nullptr;  // true window cells per row, then (at + H) wide pixels per row
     uint32_t* cells = nullptr;     // [0] true window cells of the image, [1] pixels wider than 32
+    uint32_t* wq = nullptr;        // queue of the wide pixels of the selection (n + 1 words)
+    uint32_t* gkeys = nullptr;     // right-view keys of the wide pixels (all ones between images)
+    int16_t* wds = nullptr;        // winners of the wide pixels
     uint8_t* C = nullptr;          // ragged matching cost
     uint16_t* S = nullptr;         // aggregated cost, written only with TSGM_FLAG_KEEP_INTERNALS
     uint8_t* Lvol = nullptr;       // one ragged uint8 volume of path costs per SGM direction

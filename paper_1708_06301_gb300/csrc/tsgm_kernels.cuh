@@ -76,6 +76,16 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 // (one label per lane); their count per row is kept with the row totals (rowwide).
 constexpr int kNarrowMax = 32;
 
+// Windows of at most this many labels are selected by one thread; wider ones by a warp.
+constexpr int kSelNarrow = 16;
+
+// Queue of the pixels wider than kSelNarrow: wq[0] their number, wq[1 ..] their indices. They are selected apart from their rows (select_wide) unless more than
+// a quarter of the image is wide, when every row takes its own (one decision for the whole image,
+// from wq[0], by both selection kernels).
+__host__ __device__ __forceinline__ bool select_split(uint32_t n_wide, int n) {
+    return 4ull * n_wide <= (unsigned long long)n;
+}
+
 // Row statistics written next to the windows: storage cells, true cells, pixels wider than
 // kNarrowMax (rowwide).
 __device__ __forceinline__ void row_totals(uint32_t acc, uint32_t acc_true, uint32_t acc_wide,
@@ -127,7 +137,8 @@ __device__ __forceinline__ void offsets_row(const int16_t* __restrict__ lo,
                                             const uint32_t* __restrict__ rowwide, int W, int Hh,
                                             int y, uint32_t* __restrict__ off,
                                             uint2* __restrict__ desc,
-                                            uint32_t* __restrict__ cells_total) {
+                                            uint32_t* __restrict__ cells_total,
+                                            uint32_t* __restrict__ wq) {
     __shared__ uint32_t sh[33];
     uint32_t part = 0;
     for (int r = threadIdx.x; r < y; r += blockDim.x) part += rowsum[r];
@@ -146,6 +157,23 @@ __device__ __forceinline__ void offsets_row(const int16_t* __restrict__ lo,
         if (x < W) {
             off[i] = base + ex;
             desc[i] = make_uint2(base + ex, (uint32_t)a | ((uint32_t)w << 16));
+        }
+        if (wq) {
+            // the wide pixels of this chunk of the row into the queue: places within the block by
+            // a shared counter, one global atomic per chunk
+            __shared__ uint32_t wcnt, wbase;
+            if (threadIdx.x == 0) wcnt = 0u;
+            __syncthreads();
+            const unsigned bal = __ballot_sync(kFull, x < W && w > kSelNarrow);
+            const int lane = threadIdx.x & 31;
+            uint32_t at = 0;
+            if (lane == 0 && bal) at = atomicAdd(&wcnt, (uint32_t)__popc(bal));
+            at = __shfl_sync(kFull, at, 0);
+            __syncthreads();
+            if (threadIdx.x == 0) wbase = wcnt ? atomicAdd(wq, wcnt) : 0u;
+            __syncthreads();
+            if ((bal >> lane) & 1u)
+                wq[1 + wbase + at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
         }
         base += tot;
     }
@@ -1442,7 +1470,6 @@ __device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
 }
 
 constexpr int kSelThreads = 512;
-constexpr int kSelNarrow = 16;
 
 __device__ __forceinline__ int count_side(const uint16_t* __restrict__ s, int start, int dirn,
                                           int lo_idx, int hi_idx, int s0, float thr, int lane) {
@@ -1483,6 +1510,80 @@ __device__ __forceinline__ void sum_paths(const uint8_t* __restrict__ Lvol, uint
     }
 }
 
+// One window wider than kSelNarrow by a whole warp (Eq. 9 and the right-view keys): v holds this
+// lane's words of the NPATHS path-cost volumes (labels 4 lane + 128 c .. + 3 of chunk c). The
+// aggregated costs go to the warp's scratch scr (and to S_out when given), the right-view key of
+// every label to keymin(xr, key); returns the winner, its sub-pixel disparity and the matching
+// variance.
+template <int NPATHS, int NCH, class KeyMin>
+__device__ __forceinline__ void select_wide(const uint32_t (&v)[NCH * NPATHS], uint2 dsc, int x,
+                                            float s_thr, float r_min, uint16_t* scr,
+                                            uint16_t* __restrict__ S_out, const KeyMin& keymin,
+                                            int& dstar, float& dz, float& rr) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t o = dsc.x;
+    const int a = (int)(dsc.y & 0xFFFFu);
+    const int w = (int)(dsc.y >> 16);
+    unsigned best = 0xFFFFFFFFu;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const int j = 4 * lane + 128 * c;
+        if (j < w) {
+            uint32_t p0 = 0u, p1 = 0u;
+#pragma unroll
+            for (int r = 0; r < NPATHS; ++r) {
+                p0 += __byte_perm(v[c * NPATHS + r], 0u, 0x4140);
+                p1 += __byte_perm(v[c * NPATHS + r], 0u, 0x4342);
+            }
+            *reinterpret_cast<uint2*>(scr + j) = make_uint2(p0, p1);
+            if (S_out) *reinterpret_cast<uint2*>(S_out + o + j) = make_uint2(p0, p1);
+            const unsigned sv[4] = {p0 & 0xFFFFu, p0 >> 16, p1 & 0xFFFFu, p1 >> 16};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (j + t < w) {
+                    best = min(best, (sv[t] << 16) | (unsigned)(j + t));
+                    const int xr = x - (a + j + t);
+                    if (xr >= 0) keymin(xr, (sv[t] << 9) | (unsigned)(a + j + t));
+                }
+            }
+        }
+    }
+    __syncwarp();
+    best = __reduce_min_sync(kFull, best);
+    const int js = (int)(best & 0xFFFFu);
+    const int s0 = (int)(best >> 16);
+    float delta = 0.0f;
+    if (js >= 1 && js + 1 < w) {
+        const int smv = scr[js - 1], spv = scr[js + 1];
+        const int den = 2 * (smv - 2 * s0 + spv);
+        if (den > 0) delta = __fdiv_rn((float)(smv - spv), (float)den);
+    }
+    const int nl = count_side(scr, js - 1, -1, 0, w - 1, s0, s_thr, lane);
+    const int nr = count_side(scr, js + 1, +1, 0, w - 1, s0, s_thr, lane);
+    float r = (float)(nl + nr);
+    if (r < r_min) r = r_min;
+    dstar = a + js;
+    dz = __fadd_rn((float)(a + js), delta);
+    rr = r;
+    __syncwarp();  // the scratch is free for the next pixel
+}
+
+// The path costs of a wide window (see select_wide) into this lane's words v.
+template <int NPATHS, int NCH>
+__device__ __forceinline__ void load_wide_costs(const uint8_t* __restrict__ Lvol, uint64_t stride,
+                                                uint2 dsc, uint32_t (&v)[NCH * NPATHS]) {
+    const int lane = threadIdx.x & 31;
+    const int w = (int)(dsc.y >> 16);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const int j = 4 * lane + 128 * c;
+#pragma unroll
+        for (int r = 0; r < NPATHS; ++r)
+            v[c * NPATHS + r] =
+                j < w ? __ldg(reinterpret_cast<const uint32_t*>(Lvol + r * stride + dsc.x + j)) : 0u;
+    }
+}
+
 // Selection of the pixels [x0, x1) of image row y (Eq. 9 and the left-right check), by one block.
 // The right-view keys of the row (per column xr, the (S << 9 | d) minimum over the pixels
 // x = xr + d whose window holds d) are reached through `part`: keymin(xr, key) (an atomic minimum
@@ -1496,7 +1597,11 @@ __device__ __forceinline__ void select_part(
     int y, int x0, int x1, int DP, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz,
     float* __restrict__ rz, uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
     int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out, uint32_t* sel_smem,
-    int& n_wide, Part& part) {
+    int& n_wide, Part& part, int n, const uint32_t* __restrict__ wq,
+    uint32_t* __restrict__ gkeys_row, const int16_t* __restrict__ wds) {
+    // split: the wide pixels were selected apart (select_wide over the queue wq); their winners
+    // are in wds, their keys in gkeys_row (merged here and reset for the next image)
+    const bool split = wq != nullptr && select_split(wq[0], n);
     const int npx = x1 - x0;
     uint32_t* drk = part.own_keys();              // nkeys keys (may alias sel_smem)
     float* dzs = (float*)(sel_smem + part.nkeys); // npx
@@ -1519,7 +1624,10 @@ __device__ __forceinline__ void select_part(
         const int a = (int)(dsc.y & 0xFFFFu);
         const int w = (int)(dsc.y >> 16);
         if (w > kSelNarrow) {
-            wideq[atomicAdd(&n_wide, 1)] = (int16_t)(x - x0);
+            if (split)
+                ds[x - x0] = -1;
+            else
+                wideq[atomicAdd(&n_wide, 1)] = (int16_t)(x - x0);
             continue;
         }
         uint32_t sp[kSelNarrow / 2];  // S as u16x2 pairs
@@ -1592,16 +1700,7 @@ __device__ __forceinline__ void select_part(
     auto load_wide = [&](int q, uint32_t (&v)[NCH * NPATHS], uint2& dsc) {
         if (q >= nwide) return;
         dsc = desc[y * W + x0 + wideq[q]];
-        const int w = (int)(dsc.y >> 16);
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            const int j = 4 * lane + 128 * c;
-#pragma unroll
-            for (int r = 0; r < NPATHS; ++r)
-                v[c * NPATHS + r] =
-                    j < w ? __ldg(reinterpret_cast<const uint32_t*>(Lvol + r * vol_stride + dsc.x + j))
-                          : 0u;
-        }
+        load_wide_costs<NPATHS, NCH>(Lvol, vol_stride, dsc, v);
     };
     uint32_t vcur[NCH * NPATHS], vnext[NCH * NPATHS];
     uint2 dcur = make_uint2(0u, 0u), dnext = make_uint2(0u, 0u);
@@ -1609,69 +1708,49 @@ __device__ __forceinline__ void select_part(
     for (int q = wid; q < nwide; q += nw) {
         load_wide(q + nw, vnext, dnext);
         const int x = x0 + wideq[q];
-        const uint32_t o = dcur.x;
-        const int a = (int)(dcur.y & 0xFFFFu);
-        const int w = (int)(dcur.y >> 16);
-        unsigned best = 0xFFFFFFFFu;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            const int j = 4 * lane + 128 * c;
-            if (j < w) {
-                uint32_t p0 = 0u, p1 = 0u;
-#pragma unroll
-                for (int r = 0; r < NPATHS; ++r) {
-                    p0 += __byte_perm(vcur[c * NPATHS + r], 0u, 0x4140);
-                    p1 += __byte_perm(vcur[c * NPATHS + r], 0u, 0x4342);
-                }
-                *reinterpret_cast<uint2*>(scr + j) = make_uint2(p0, p1);
-                if (S_out) *reinterpret_cast<uint2*>(S_out + o + j) = make_uint2(p0, p1);
-                const unsigned sv[4] = {p0 & 0xFFFFu, p0 >> 16, p1 & 0xFFFFu, p1 >> 16};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    if (j + t < w) {
-                        best = min(best, (sv[t] << 16) | (unsigned)(j + t));
-                        const int xr = x - (a + j + t);
-                        if (xr >= 0) part.keymin(xr, (sv[t] << 9) | (unsigned)(a + j + t));
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        best = __reduce_min_sync(kFull, best);
-        const int js = (int)(best & 0xFFFFu);
-        const int s0 = (int)(best >> 16);
-        float delta = 0.0f;
-        if (js >= 1 && js + 1 < w) {
-            const int smv = scr[js - 1], spv = scr[js + 1];
-            const int den = 2 * (smv - 2 * s0 + spv);
-            if (den > 0) delta = __fdiv_rn((float)(smv - spv), (float)den);
-        }
-        const int nl = count_side(scr, js - 1, -1, 0, w - 1, s0, s_thr, lane);
-        const int nr = count_side(scr, js + 1, +1, 0, w - 1, s0, s_thr, lane);
-        float r = (float)(nl + nr);
-        if (r < r_min) r = r_min;
+        int dsr;
+        float dzr, rr;
+        select_wide<NPATHS, NCH>(vcur, dcur, x, s_thr, r_min, scr, S_out,
+                                 [&](int xr, uint32_t k) { part.keymin(xr, k); }, dsr, dzr, rr);
         if (lane == 0) {
-            ds[x - x0] = (int16_t)(a + js);
-            dzs[x - x0] = __fadd_rn((float)(a + js), delta);
-            rzs[x - x0] = r;
+            ds[x - x0] = (int16_t)dsr;
+            dzs[x - x0] = dzr;
+            rzs[x - x0] = rr;
         }
-        __syncwarp();
 #pragma unroll
         for (int t = 0; t < NCH * NPATHS; ++t) vcur[t] = vnext[t];
         dcur = dnext;
     }
+    if (split) {
+        __syncthreads();  // this block's key atomics are done
+        const int kb = part.key_base();
+        for (int t = threadIdx.x; t < part.nkeys; t += blockDim.x) {
+            const int xr = kb + t;
+            if (xr >= 0 && xr < W) drk[t] = min(drk[t], gkeys_row[xr]);
+        }
+    }
     part.sync();  // every key of the row is final
     for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
         const int i = y * W + x;
-        const int d = ds[x - x0];
+        int d = ds[x - x0];
+        const bool wide_px = split && d < 0;
+        if (wide_px) d = wds[i];
         const int xr = x - d;
         bool ok = false;
         if (xr >= 0) {
             const uint32_t kk = part.key(xr);
             ok = kk != 0xFFFFFFFFu && abs(d - (int)(kk & 0x1FFu)) <= lr_tol;
         }
-        Dz[i] = ok ? dzs[x - x0] : -1.0f;
-        rz[i] = ok ? rzs[x - x0] : -1.0f;
+        if (wide_px) {
+            if (!ok) {
+                Dz[i] = -1.0f;
+                rz[i] = -1.0f;
+            }
+        } else {
+            Dz[i] = ok ? dzs[x - x0] : -1.0f;
+            rz[i] = ok ? rzs[x - x0] : -1.0f;
+        }
+        if (split) gkeys_row[x] = 0xFFFFFFFFu;
         if (dstar_out) {
             dstar_out[i] = (int16_t)d;
             const uint32_t kx = part.key(x);
@@ -1690,6 +1769,7 @@ struct RowPart {
     __device__ void keymin(int xr, uint32_t k) const { atomicMin(keys + xr, k); }
     __device__ uint32_t key(int xr) const { return keys[xr]; }
     __device__ void sync() const { __syncthreads(); }
+    __device__ int key_base() const { return 0; }
 };
 
 template <int NPATHS>
@@ -1698,10 +1778,12 @@ __device__ __forceinline__ void select_row(
     int y, int DP, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz,
     float* __restrict__ rz, uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
     int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out, uint32_t* sel_smem,
-    int& n_wide) {
+    int& n_wide, int n = 0, const uint32_t* __restrict__ wq = nullptr,
+    uint32_t* __restrict__ gkeys_row = nullptr, const int16_t* __restrict__ wds = nullptr) {
     RowPart part{sel_smem, W};
     select_part<NPATHS, 2>(Lvol, vol_stride, desc, W, y, 0, W, DP, s_thr, r_min, lr_tol, Dz, rz,
-                           S_out, dstar_out, dright_out, valid_out, sel_smem, n_wide, part);
+                           S_out, dstar_out, dright_out, valid_out, sel_smem, n_wide, part, n, wq,
+                           gkeys_row, wds);
 }
 
 }  // namespace dev

@@ -83,6 +83,7 @@ struct ClusterPart {
         return k;
     }
     __device__ void sync() const { cooperative_groups::this_cluster().sync(); }
+    __device__ int key_base() const { return base; }
 };
 
 template <int NPATHS, int NCH>
@@ -90,7 +91,8 @@ __global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(kSelThread
     const uint8_t* __restrict__ Lvol, uint64_t vol_stride, const uint2* __restrict__ desc, int W,
     int DP, int DPim, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz,
     float* __restrict__ rz, uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
-    int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out) {
+    int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out, int n,
+    const uint32_t* __restrict__ wq, uint32_t* __restrict__ gkeys, const int16_t* __restrict__ wds) {
     extern __shared__ uint32_t sel_smem[];
     __shared__ int n_wide;
     const int rank = (int)cooperative_groups::this_cluster().block_rank();
@@ -100,7 +102,61 @@ __global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(kSelThread
     const int D = DPim;
     ClusterPart part{sel_smem, seg + D - 1, seg, D, W, rank * seg - (D - 1)};
     select_part<NPATHS, NCH>(Lvol, vol_stride, desc, W, y, x0, x1, DP, s_thr, r_min, lr_tol, Dz, rz,
-                             S_out, dstar_out, dright_out, valid_out, sel_smem, n_wide, part);
+                             S_out, dstar_out, dright_out, valid_out, sel_smem, n_wide, part, n, wq,
+                             gkeys + (size_t)y * W, wds);
+}
+
+// The wide windows of the queue wq (see select_split), one warp per pixel (pixel t of the queue by
+// warp t mod the launch's warps, the next one's path costs loaded during the current one): winner,
+// sub-pixel disparity and matching variance into wds, Dz and rz (the row's selection clears Dz and
+// rz where the left-right check fails), right-view keys into gkeys (atomic minimum per column).
+template <int NPATHS, int NCH>
+__global__ void __launch_bounds__(256) k_select_wide(const uint8_t* __restrict__ Lvol,
+                                                     uint64_t vol_stride,
+                                                     const uint2* __restrict__ desc, int W, int n,
+                                                     float s_thr, float r_min,
+                                                     float* __restrict__ Dz, float* __restrict__ rz,
+                                                     uint16_t* __restrict__ S_out,
+                                                     int16_t* __restrict__ wds,
+                                                     uint32_t* __restrict__ gkeys,
+                                                     const uint32_t* __restrict__ wq) {
+    __shared__ __align__(16) uint16_t scr_all[8][NCH * 128];
+    const int count = (int)wq[0];
+    if (!select_split((uint32_t)count, n)) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * 8;
+    uint16_t* const scr = scr_all[wid];
+    uint32_t vcur[NCH * NPATHS], vnext[NCH * NPATHS];
+    uint2 dcur = make_uint2(0u, 0u), dnext = make_uint2(0u, 0u);
+    int t = blockIdx.x * 8 + wid;
+    int icur = 0, inext = 0;
+    if (t < count) {
+        icur = (int)wq[1 + t];
+        dcur = desc[icur];
+        load_wide_costs<NPATHS, NCH>(Lvol, vol_stride, dcur, vcur);
+    }
+    for (; t < count; t += nwarps) {
+        if (t + nwarps < count) {
+            inext = (int)wq[1 + t + nwarps];
+            dnext = desc[inext];
+            load_wide_costs<NPATHS, NCH>(Lvol, vol_stride, dnext, vnext);
+        }
+        const int y = icur / W, x = icur - y * W;
+        uint32_t* const grow = gkeys + (size_t)y * W;
+        int dsr;
+        float dzr, rr;
+        select_wide<NPATHS, NCH>(vcur, dcur, x, s_thr, r_min, scr, S_out,
+                                 [&](int xr, uint32_t k) { atomicMin(grow + xr, k); }, dsr, dzr, rr);
+        if (lane == 0) {
+            wds[icur] = (int16_t)dsr;
+            Dz[icur] = dzr;
+            rz[icur] = rr;
+        }
+#pragma unroll
+        for (int q = 0; q < NCH * NPATHS; ++q) vcur[q] = vnext[q];
+        dcur = dnext;
+        icur = inext;
+    }
 }
 
 }  // namespace
@@ -163,22 +219,28 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
                           int W, int Hh, int D, float s_thr, float r_min, int lr_tol, float* Dz,
                           float* rz, uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
-                          cudaStream_t st) {
+                          const uint32_t* wq, uint32_t* gkeys, int16_t* wds, cudaStream_t st) {
     // per-warp scratch for the wide windows: up to 256 labels
     const int DP = 256;
+    const int n = W * Hh;
     const int seg = (W + kSelCluster - 1) / kSelCluster;
     const size_t smem = (size_t)((seg + D - 1 + 3 * seg + 1) & ~1) * 4 +
                         (size_t)(kSelThreadsCl / 32) * DP * sizeof(uint16_t);
+    auto wide = n_paths == 8 ? (D <= 128 ? k_select_wide<8, 1> : k_select_wide<8, 2>)
+                             : (D <= 128 ? k_select_wide<4, 1> : k_select_wide<4, 2>);
+    wide<<<152 * 4, 256, 0, st>>>(Lvol, vol_stride, desc, W, n, s_thr, r_min, Dz, rz, S, wds,
+                                  gkeys, wq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     auto kern = n_paths == 8 ? (D <= 128 ? k_select<8, 1> : k_select<8, 2>)
                              : (D <= 128 ? k_select<4, 1> : k_select<4, 2>);
     if (smem > 48 * 1024) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     kern<<<Hh * kSelCluster, kSelThreadsCl, smem, st>>>(Lvol, vol_stride, desc, W, DP, D, s_thr,
                                                          r_min, lr_tol, Dz, rz, S, dstar, dright,
-                                                         valid);
+                                                         valid, n, wq, gkeys, wds);
     return cudaGetLastError();
 }
 

@@ -93,9 +93,11 @@ __global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
                                                  int16_t* __restrict__ hi,
                                                  uint32_t* __restrict__ rowsum,
                                                  uint32_t* __restrict__ rowcells,
-                                                 uint32_t* __restrict__ rowwide) {
+                                                 uint32_t* __restrict__ rowwide,
+                                                 uint32_t* __restrict__ wq) {
     __shared__ uint32_t sh[33];
     const int y = blockIdx.x;
+    if (y == 0 && threadIdx.x == 0) wq[0] = 0u;  // the offsets pass queues this image's wide pixels
     uint32_t acc = 0, acc_true = 0, acc_wide = 0;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const int i = y * W + x;
@@ -126,7 +128,9 @@ __global__ void __launch_bounds__(256) k_sanitize_rowsum(const int16_t* __restri
                                                          int D, int16_t* __restrict__ lo,
                                                          int16_t* __restrict__ hi,
                                                          uint32_t* __restrict__ rowsum,
-                                                         uint32_t* __restrict__ rowcells) {
+                                                         uint32_t* __restrict__ rowcells,
+                                                         uint32_t* __restrict__ wq) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) wq[0] = 0u;  // see k_windows
     sanitize_row(lo_in, hi_in, W, D, blockIdx.x, lo, hi, rowsum, rowcells, rowcells + gridDim.x);
 }
 
@@ -137,8 +141,10 @@ __global__ void __launch_bounds__(512) k_offsets(const int16_t* __restrict__ lo,
                                                  const uint32_t* __restrict__ rowcells, int W,
                                                  int Hh, uint32_t* __restrict__ off,
                                                  uint2* __restrict__ desc,
-                                                 uint32_t* __restrict__ cells_total) {
-    offsets_row(lo, hi, rowsum, rowcells, rowcells + Hh, W, Hh, blockIdx.x, off, desc, cells_total);
+                                                 uint32_t* __restrict__ cells_total,
+                                                 uint32_t* __restrict__ wq) {
+    offsets_row(lo, hi, rowsum, rowcells, rowcells + Hh, W, Hh, blockIdx.x, off, desc, cells_total,
+                wq);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -271,22 +277,22 @@ cudaError_t launch_warp_gather(const unsigned long long* keys, const float* Dpre
 
 cudaError_t launch_windows(const float* Dp, const float* Pp, int W, int Hh, int D, float k,
                            int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
-                           cudaStream_t st) {
-    k_windows<<<Hh, 256, 0, st>>>(Dp, Pp, W, D, k, lo, hi, rowsum, rowcells, rowcells + Hh);
+                           uint32_t* wq, cudaStream_t st) {
+    k_windows<<<Hh, 256, 0, st>>>(Dp, Pp, W, D, k, lo, hi, rowsum, rowcells, rowcells + Hh, wq);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sanitize(const int16_t* lo_in, const int16_t* hi_in, int W, int Hh, int D,
                             int16_t* lo, int16_t* hi, uint32_t* rowsum, uint32_t* rowcells,
-                            cudaStream_t st) {
-    k_sanitize_rowsum<<<Hh, 256, 0, st>>>(lo_in, hi_in, W, D, lo, hi, rowsum, rowcells);
+                            uint32_t* wq, cudaStream_t st) {
+    k_sanitize_rowsum<<<Hh, 256, 0, st>>>(lo_in, hi_in, W, D, lo, hi, rowsum, rowcells, wq);
     return cudaGetLastError();
 }
 
 cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t* rowsum,
                            const uint32_t* rowcells, int W, int Hh, uint32_t* off, uint2* desc,
-                           uint32_t* cells_total, cudaStream_t st) {
-    k_offsets<<<Hh, 512, 0, st>>>(lo, hi, rowsum, rowcells, W, Hh, off, desc, cells_total);
+                           uint32_t* cells_total, uint32_t* wq, cudaStream_t st) {
+    k_offsets<<<Hh, 512, 0, st>>>(lo, hi, rowsum, rowcells, W, Hh, off, desc, cells_total, wq);
     return cudaGetLastError();
 }
 
