@@ -1584,6 +1584,77 @@ __device__ __forceinline__ void load_wide_costs(const uint8_t* __restrict__ Lvol
     }
 }
 
+// One window of at most NL (a multiple of 4, <= kSelNarrow) labels by one thread: its aggregated
+// costs (to S_out when given), every label's right-view key to keymin(xr, key), the winner's index
+// js in the window, its sub-pixel offset delta and the matching variance r (Eq. 9).
+template <int NPATHS, int NL, class KeyMin>
+__device__ __forceinline__ void select_narrow(const uint8_t* __restrict__ Lvol, uint64_t vol_stride,
+                                              uint32_t o, int a, int w, int x, float s_thr,
+                                              float r_min, uint16_t* __restrict__ S_out,
+                                              const KeyMin& keymin, int& js_out, float& delta_out,
+                                              float& r_out) {
+    uint32_t sp[NL / 2];  // S as u16x2 pairs
+#pragma unroll
+    for (int q = 0; q < NL / 4; ++q) {
+        if (4 * q < w) {
+            sum_paths<NPATHS>(Lvol, vol_stride, o, 4 * q, sp[2 * q], sp[2 * q + 1]);
+            if (S_out) *reinterpret_cast<uint2*>(S_out + o + 4 * q) = make_uint2(sp[2 * q], sp[2 * q + 1]);
+        } else {
+            sp[2 * q] = 0xFFFFFFFFu;
+            sp[2 * q + 1] = 0xFFFFFFFFu;
+        }
+    }
+    int sv[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j)
+        sv[j] = (j < w) ? (int)((j & 1) ? (sp[j >> 1] >> 16) : (sp[j >> 1] & 0xFFFFu)) : 0x7FFFFFFF;
+    int js = 0, s0 = sv[0];
+#pragma unroll
+    for (int j = 1; j < NL; ++j)
+        if (sv[j] < s0) {
+            s0 = sv[j];
+            js = j;
+        }
+    int sm = 0, spv = 0;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+        if (j == js - 1) sm = sv[j];
+        if (j == js + 1) spv = sv[j];
+        if (j < w) {
+            const int xr = x - (a + j);
+            if (xr >= 0) keymin(xr, ((uint32_t)sv[j] << 9) | (uint32_t)(a + j));
+        }
+    }
+    float delta = 0.0f;
+    if (js >= 1 && js + 1 < w) {
+        const int den = 2 * (sm - 2 * s0 + spv);
+        if (den > 0) delta = __fdiv_rn((float)(sm - spv), (float)den);
+    }
+    // counts: running sums outwards from d*; walking labels in order of distance keeps the
+    // sums growing, so every label whose sum is below the threshold is in the counted run
+    int nl = 0, nr = 0, acc = 0;
+#pragma unroll
+    for (int j = NL - 1; j >= 0; --j) {
+        if (j < js) {
+            acc += sv[j] - s0;
+            nl += ((float)acc < s_thr) ? 1 : 0;
+        }
+    }
+    acc = 0;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+        if (j > js && j < w) {
+            acc += sv[j] - s0;
+            nr += ((float)acc < s_thr) ? 1 : 0;
+        }
+    }
+    float r = (float)(nl + nr);
+    if (r < r_min) r = r_min;
+    js_out = js;
+    delta_out = delta;
+    r_out = r;
+}
+
 // Selection of the pixels [x0, x1) of image row y (Eq. 9 and the left-right check), by one block.
 // The right-view keys of the row (per column xr, the (S << 9 | d) minimum over the pixels
 // x = xr + d whose window holds d) are reached through `part`: keymin(xr, key) (an atomic minimum
@@ -1616,77 +1687,34 @@ __device__ __forceinline__ void select_part(
     if (threadIdx.x == 0) n_wide = 0;
     part.sync();
 
-    // ---- narrow windows: one thread per pixel
-    for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+    // ---- narrow windows: one thread per pixel, the labels unrolled to the widest narrow window
+    // of the warp's pixels (8, 12 or 16)
+    for (int xb = x0 + (threadIdx.x & ~31); xb < x1; xb += blockDim.x) {
+        const int x = xb + lane;
+        const bool in = x < x1;
         const int i = y * W + x;
-        const uint2 dsc = desc[i];
+        const uint2 dsc = in ? desc[i] : make_uint2(0u, 0u);
         const uint32_t o = dsc.x;
         const int a = (int)(dsc.y & 0xFFFFu);
         const int w = (int)(dsc.y >> 16);
-        if (w > kSelNarrow) {
+        if (in && w > kSelNarrow) {
             if (split)
                 ds[x - x0] = -1;
             else
                 wideq[atomicAdd(&n_wide, 1)] = (int16_t)(x - x0);
-            continue;
         }
-        uint32_t sp[kSelNarrow / 2];  // S as u16x2 pairs
-#pragma unroll
-        for (int q = 0; q < kSelNarrow / 4; ++q) {
-            if (4 * q < w) {
-                sum_paths<NPATHS>(Lvol, vol_stride, o, 4 * q, sp[2 * q], sp[2 * q + 1]);
-                if (S_out) *reinterpret_cast<uint2*>(S_out + o + 4 * q) = make_uint2(sp[2 * q], sp[2 * q + 1]);
-            } else {
-                sp[2 * q] = 0xFFFFFFFFu;
-                sp[2 * q + 1] = 0xFFFFFFFFu;
-            }
-        }
-        int sv[kSelNarrow];
-#pragma unroll
-        for (int j = 0; j < kSelNarrow; ++j)
-            sv[j] = (j < w) ? (int)((j & 1) ? (sp[j >> 1] >> 16) : (sp[j >> 1] & 0xFFFFu)) : 0x7FFFFFFF;
-        int js = 0, s0 = sv[0];
-#pragma unroll
-        for (int j = 1; j < kSelNarrow; ++j)
-            if (sv[j] < s0) {
-                s0 = sv[j];
-                js = j;
-            }
-        int sm = 0, spv = 0;
-#pragma unroll
-        for (int j = 0; j < kSelNarrow; ++j) {
-            if (j == js - 1) sm = sv[j];
-            if (j == js + 1) spv = sv[j];
-            if (j < w) {
-                const int xr = x - (a + j);
-                if (xr >= 0) part.keymin(xr, ((uint32_t)sv[j] << 9) | (uint32_t)(a + j));
-            }
-        }
-        float delta = 0.0f;
-        if (js >= 1 && js + 1 < w) {
-            const int den = 2 * (sm - 2 * s0 + spv);
-            if (den > 0) delta = __fdiv_rn((float)(sm - spv), (float)den);
-        }
-        // counts: running sums outwards from d*; walking labels in order of distance keeps the
-        // sums growing, so every label whose sum is below the threshold is in the counted run
-        int nl = 0, nr = 0, acc = 0;
-#pragma unroll
-        for (int j = kSelNarrow - 1; j >= 0; --j) {
-            if (j < js) {
-                acc += sv[j] - s0;
-                nl += ((float)acc < s_thr) ? 1 : 0;
-            }
-        }
-        acc = 0;
-#pragma unroll
-        for (int j = 0; j < kSelNarrow; ++j) {
-            if (j > js && j < w) {
-                acc += sv[j] - s0;
-                nr += ((float)acc < s_thr) ? 1 : 0;
-            }
-        }
-        float r = (float)(nl + nr);
-        if (r < r_min) r = r_min;
+        const bool narrow = in && w <= kSelNarrow;
+        const int wmax = (int)__reduce_max_sync(kFull, narrow ? (unsigned)w : 0u);
+        if (!narrow) continue;
+        auto km = [&](int xr, uint32_t k) { part.keymin(xr, k); };
+        int js;
+        float delta, r;
+        if (wmax <= 8)
+            select_narrow<NPATHS, 8>(Lvol, vol_stride, o, a, w, x, s_thr, r_min, S_out, km, js, delta, r);
+        else if (wmax <= 12)
+            select_narrow<NPATHS, 12>(Lvol, vol_stride, o, a, w, x, s_thr, r_min, S_out, km, js, delta, r);
+        else
+            select_narrow<NPATHS, 16>(Lvol, vol_stride, o, a, w, x, s_thr, r_min, S_out, km, js, delta, r);
         ds[x - x0] = (int16_t)(a + js);
         dzs[x - x0] = __fadd_rn((float)(a + js), delta);
         rzs[x - x0] = r;
