@@ -389,6 +389,12 @@ def bench_serving(duration_s: float, budget_gb: float):
             "max_in_flight": st["max_in_flight"], "hbm_budget_gb": budget_gb}
 
 
+# DRAM bytes (read + write) of one aggregation launch, averaged over the ten launches of one step of
+# the sequence (one full-range frame, nine reduced), from ncu's dram__bytes_read.sum and
+# dram__bytes_write.sum (profiles/k_sgm_kitti_1242x375_reduced.md); None once k_sgm changes.
+SGM_DRAM_BYTES_PER_LAUNCH = 114_681_728
+
+
 def algorithmic_sgm_bytes(cells: int, px: int) -> int:
     """Bytes the aggregation kernel must move once: the ragged cost C read (1 B/cell), the
     aggregated S written (2 B/cell), window bounds and offsets read (8 B/px)."""
@@ -582,7 +588,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
         "roofline": {"bound": "hbm", "kernel": "k_sgm (path aggregation)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "traffic": None,
+                     "peak_kind": peak_kind, "traffic": SGM_DRAM_BYTES_PER_LAUNCH,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_us": agg_avg_s * 1e6},
         "cpu_baseline": {"value": N_FRAMES / cpu_s, "unit": "frames/s", "cores": 1,
