@@ -256,6 +256,7 @@ tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* righ
                               keep ? ctx->lrvalid : nullptr, ctx->wq, ctx->gkeys, ctx->wds,
                               ctx->stream),
             "select");
+    ++ctx->launches;  // launch_select enqueues two kernels (wide windows, then the rows)
     stage_end(ctx, TSGM_STAGE_SELECT);
     return TSGM_OK;
 }
