@@ -76,6 +76,12 @@ class Params:
     gamma_f: float = 1.0       # Eq. 8 similarity threshold (value not given)
     edge_reject: bool = False  # Sec. 2.2, reject predicted pixels near disparity discontinuities
     edge_thr: float = 1.0      # discontinuity threshold of the edge rejection (value not given)
+    pred_lr_check: bool = False  # Sec. 2.2 / Fig. 3(d), left-right check of the prediction
+    pred_lr_tol: float = 1.0     # its similarity threshold (value not given)
+    sad_check: bool = False      # Sec. 2.4, SAD check of the updated map on the two images
+    sad_w: int = 5               # patch (odd sizes; not given)
+    sad_h: int = 5
+    sad_thr: float = 20.0        # mean absolute difference per patch pixel (value not given)
 
     @property
     def D(self) -> int:
@@ -136,6 +142,29 @@ def edge_reject(Dp, Pp, edge_thr: float):
     D = np.array(Dp, dtype=np.float32, copy=True)
     P = np.array(Pp, dtype=np.float32, copy=True)
     lib.oracle_edge_reject(W, Hh, ctypes.c_float(edge_thr), _p(D), _p(P))
+    return D, P
+
+
+def pred_lr_check(Dp, Pp, tol: float):
+    """Sec. 2.2 / Fig. 3(d): left-right consistency check of the prediction against the right
+    view's prediction formed from it (nearest surface per right pixel); copies."""
+    lib = _load()
+    Hh, W = Dp.shape
+    D = np.array(Dp, dtype=np.float32, copy=True)
+    P = np.array(Pp, dtype=np.float32, copy=True)
+    lib.oracle_pred_lr_check(W, Hh, ctypes.c_float(tol), _p(D), _p(P))
+    return D, P
+
+
+def sad_check(left, right, D, P, sw: int, sh: int, sad_thr: float):
+    """Sec. 2.4: reject pixels of the updated map whose left/right patch SAD exceeds sad_thr per
+    patch pixel; copies."""
+    lib = _load()
+    Hh, W = D.shape
+    D = np.array(D, dtype=np.float32, copy=True)
+    P = np.array(P, dtype=np.float32, copy=True)
+    lib.oracle_sad_check(W, Hh, int(sw), int(sh), ctypes.c_float(sad_thr),
+                         _p(_c(left, np.uint8)), _p(_c(right, np.uint8)), _p(D), _p(P))
     return D, P
 
 
@@ -289,9 +318,14 @@ class Tracker:
                 Dp, Pp = edge_reject(Dp, Pp, prm.edge_thr)
             if prm.fill_gaps:
                 Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)
+            if prm.pred_lr_check:
+                Dp, Pp = pred_lr_check(Dp, Pp, prm.pred_lr_tol)
         lo, hi, off, n_cells = windows(Dp, Pp, prm.D, prm.sigma_mult)
         m = match(left, right, lo, hi, prm, keep=True)
         D, P = kalman(Dp, Pp, m["Dz"], m["rz"])
+        if prm.sad_check:
+            out["D_unchecked"], out["P_unchecked"] = D, P
+            D, P = sad_check(left, right, D, P, prm.sad_w, prm.sad_h, prm.sad_thr)
         self.D, self.P = D, P
         if keep:
             out.update(m)

@@ -203,6 +203,75 @@ void oracle_edge_reject(int W, int Hh, float edge_thr, float* D, float* P) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Sec. 2.2 and Sec. 3 (Fig. 3(d)): left-right consistency check of the prediction. The right
+// view's prediction is formed from the left one: a valid predicted pixel (x, y, d) lands on the
+// right view's pixel x_r = x - round(d) of its row, round(d) = floor(d + 1/2) in binary32, and the
+// right view keeps the largest disparity landing on each pixel (the nearest surface). A left pixel
+// stays valid when x_r lies inside the image and the right prediction there differs from d by at
+// most tol; otherwise D and P become -1 (seen by one camera only, or hidden in the right view
+// behind a nearer surface). In place.
+// ------------------------------------------------------------------------------------------
+static inline int right_column(int x, float d) {
+    const float rf = std::floor(d + 0.5f);
+    return rf > (float)x ? -1 : x - (int)rf;
+}
+
+void oracle_pred_lr_check(int W, int Hh, float tol, float* D, float* P) {
+    std::vector<float> R(W);
+    for (int y = 0; y < Hh; ++y) {
+        float* d = D + (size_t)y * W;
+        float* p = P + (size_t)y * W;
+        for (int x = 0; x < W; ++x) R[x] = -1.0f;
+        for (int x = 0; x < W; ++x) {
+            if (!(finite_nonneg(d[x]) && finite_nonneg(p[x]))) continue;
+            const int r = right_column(x, d[x]);
+            if (r >= 0 && d[x] > R[r]) R[r] = d[x];
+        }
+        for (int x = 0; x < W; ++x) {
+            if (!(finite_nonneg(d[x]) && finite_nonneg(p[x]))) continue;
+            const int r = right_column(x, d[x]);
+            if (!(r >= 0 && std::fabs(d[x] - R[r]) <= tol)) {
+                d[x] = -1.0f;
+                p[x] = -1.0f;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Sec. 2.4 (disparity consistency check), the SAD check on the left and right images: the sum of
+// absolute differences between the sw x sh patch of the left image around (x, y) and the right
+// image's patch around (x - round(d), y), every coordinate clamped into the image. A pixel whose
+// SAD exceeds sad_thr times the patch area (binary32) is rejected (D = P = -1), so that the next
+// image searches it over the whole range. Applied to the updated map, in place.
+// ------------------------------------------------------------------------------------------
+void oracle_sad_check(int W, int Hh, int sw, int sh, float sad_thr, const uint8_t* L,
+                      const uint8_t* R, float* D, float* P) {
+    const float lim = sad_thr * (float)(sw * sh);
+    const int hw = sw / 2, hh = sh / 2;
+    auto clampi = [](int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); };
+    for (int y = 0; y < Hh; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int i = y * W + x;
+            if (!(finite_nonneg(D[i]) && finite_nonneg(P[i]))) continue;
+            const float rf = std::floor(D[i] + 0.5f);
+            const int dx = rf > (float)(2 * W) ? 2 * W : (int)rf;  // beyond the image either way
+            int sad = 0;
+            for (int v = -hh; v <= hh; ++v)
+                for (int u = -hw; u <= hw; ++u) {
+                    const int yy = clampi(y + v, 0, Hh - 1);
+                    const int xl = clampi(x + u, 0, W - 1);
+                    const int xr = clampi(x - dx + u, 0, W - 1);
+                    sad += std::abs((int)L[yy * W + xl] - (int)R[yy * W + xr]);
+                }
+            if ((float)sad > lim) {
+                D[i] = -1.0f;
+                P[i] = -1.0f;
+            }
+        }
+}
+
+// ------------------------------------------------------------------------------------------
 // Sec. 2.3: reduced search interval [d - 3 sqrt(p), d + 3 sqrt(p)] (multiplier k = sigma_mult),
 // rounded outwards to integers and clipped to [0, D-1]. A pixel without a valid prediction
 // (d < 0, p < 0, NaN or inf), or whose interval misses [0, D-1], is searched over the whole

@@ -661,3 +661,112 @@ def test_edge_reject_runs_before_gap_filling_in_the_tracker():
     swapped = oracle.edge_reject(*oracle.fill_gaps(*raw, 1.0), 1.0)
     assert np.array_equal(ref[0], pd1) and np.array_equal(ref[1], outs[True]["Ppred"])
     assert not np.array_equal(swapped[0], pd1)       # the order matters on this scene
+
+
+def test_pred_lr_check_hand_cases():
+    """Sec. 2.2 / Fig. 3(d): the prediction's left-right check against the right view formed from
+    it (each predicted pixel lands on x - round(d); the right view keeps the nearest surface)."""
+    I = -1.0
+    # one row worked by hand: landing columns 1, 1, 0, 2, 2, 6, 0 for x = 1..7
+    d = np.array([[I, 0.4, 1.0, 3.0, 2.0, 2.6, 0.0, 7.2]], np.float32)
+    p = np.where(d >= 0, 1.0, -1.0).astype(np.float32)
+    De, Pe = oracle.pred_lr_check(d, p, 0.5)
+    # right view: col 0 <- max(3.0, 7.2) = 7.2, col 1 <- max(0.4, 1.0) = 1.0, col 2 <- 2.6, col 6 <- 0
+    expect = np.array([[I, I, 1.0, I, I, 2.6, 0.0, 7.2]], np.float32)
+    assert np.array_equal(De, expect)
+    assert np.array_equal(Pe, np.where(expect >= 0, 1.0, -1.0).astype(np.float32))
+    # the same row with a looser threshold: 0.6 apart is now consistent, 4.2 apart still not
+    De2, _ = oracle.pred_lr_check(d, p, 0.6)
+    assert np.array_equal(De2, np.array([[I, 0.4, 1.0, I, 2.0, 2.6, 0.0, 7.2]], np.float32))
+    # a difference equal to the threshold is consistent: x=2 (2.0) and x=3 (2.5, rounds to 3)
+    # land on column 0 with x=0 (0.0), which the nearer 2.5 hides; x=1 (0.0) keeps column 1
+    e = np.array([[0, 0, 2.0, 2.5]], np.float32)
+    Ee, _ = oracle.pred_lr_check(e, np.ones_like(e), 0.5)
+    assert np.array_equal(Ee, np.array([[I, 0, 2.0, 2.5]], np.float32))
+    Ee2, _ = oracle.pred_lr_check(e, np.ones_like(e), 0.49)
+    assert np.array_equal(Ee2, np.array([[I, 0, I, 2.5]], np.float32))
+
+
+def test_pred_lr_check_geometry():
+    """Closed forms: a fronto-parallel plane at disparity d is seen by both cameras exactly where
+    x >= round(d) (the left-border band of Fig. 3(d)); a nearer block hides from the right camera
+    the band of background of width (d_F - d_B) just left of it, and nothing else."""
+    W, H = 40, 3
+    for dv in (0.0, 3.0, 7.49, 7.5, 12.2):
+        D = np.full((H, W), dv, np.float32)
+        De, _ = oracle.pred_lr_check(D, np.ones_like(D), 0.25)
+        k = int(math.floor(dv + 0.5))
+        assert np.all(De[:, :k] == -1) and np.array_equal(De[:, k:], D[:, k:])
+    dB, dF, a, b = 4.0, 10.0, 20, 30
+    D = np.full((1, W), dB, np.float32)
+    D[0, a:b] = dF
+    De, _ = oracle.pred_lr_check(D, np.ones_like(D), 0.5)
+    hidden = np.zeros(W, bool)
+    hidden[:4] = True                                   # background not seen by the right camera
+    hidden[a - int(dF - dB):a] = True                   # background behind the block
+    assert np.all(De[0, hidden] == -1)
+    assert np.array_equal(De[0, ~hidden], D[0, ~hidden])
+
+
+def test_sad_check_hand_cases():
+    """Sec. 2.4: a pixel of the updated map is rejected when its left/right patch SAD exceeds the
+    threshold times the patch area; coordinates clamp at the image border."""
+    I = -1.0
+    L = np.array([[10, 20, 30, 40, 50]], np.uint8)
+    R = np.array([[20, 30, 40, 50, 99]], np.uint8)  # the left row moved one pixel left
+    D = np.array([[1.0, 1.0, 1.0, 0.0, I]], np.float32)
+    P = np.where(D >= 0, 1.0, -1.0).astype(np.float32)
+    # 3 x 1 patches. x=0, d=1: left (10,10,20) vs right cols clamp(-2..0) = (20,20,20): SAD 30;
+    # x=1, d=1: (10,20,30) vs (20,20,30): 10; x=2, d=1: (20,30,40) vs (20,30,40): 0;
+    # x=3, d=0: (30,40,50) vs (40,50,99): 10 + 10 + 49 = 69
+    De, Pe = oracle.sad_check(L, R, D, P, 3, 1, 10.0)   # limit 30: 30 stays (not above), 69 goes
+    assert np.array_equal(De, np.array([[1.0, 1.0, 1.0, I, I]], np.float32))
+    assert np.array_equal(Pe, np.array([[1.0, 1.0, 1.0, I, I]], np.float32))
+    De2, _ = oracle.sad_check(L, R, D, P, 3, 1, 3.0)    # limit 9: only the exact match stays
+    assert np.array_equal(De2, np.array([[I, I, 1.0, I, I]], np.float32))
+    # rounding of the disparity: 1.49 uses 1, 1.5 uses 2 (x=2: right cols 0..2 = (20,30,40) vs
+    # cols -1..1 clamped = (20,20,30))
+    D3 = np.array([[I, I, 1.49, I, I]], np.float32)
+    assert oracle.sad_check(L, R, D3, np.abs(D3), 3, 1, 0.0)[0][0, 2] == 1.49
+    D4 = np.array([[I, I, 1.5, I, I]], np.float32)
+    assert oracle.sad_check(L, R, D4, np.abs(D4), 3, 1, 6.6)[0][0, 2] == -1   # SAD 20 > 19.8
+    assert oracle.sad_check(L, R, D4, np.abs(D4), 3, 1, 6.7)[0][0, 2] == 1.5  # 20 <= 20.1
+
+
+def test_sad_check_shifted_texture():
+    """A right image that is the left one shifted by s: every pixel far enough from the borders
+    passes at d = s with SAD 0 and fails at a wrong disparity."""
+    rng = np.random.default_rng(3)
+    W, H, s = 48, 9, 5
+    L = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    R = np.zeros_like(L)
+    R[:, :W - s] = L[:, s:]
+    D = np.full((H, W), float(s), np.float32)
+    De, _ = oracle.sad_check(L, R, D, np.ones_like(D), 5, 5, 0.0)
+    inner = (slice(2, H - 2), slice(s + 2, W - s - 2))
+    assert np.all(De[inner] == s)
+    Dw = np.full((H, W), float(s + 3), np.float32)
+    Dwe, _ = oracle.sad_check(L, R, Dw, np.ones_like(Dw), 5, 5, 20.0)
+    assert np.all(Dwe[inner] == -1)
+
+
+def test_pred_lr_and_sad_checks_in_the_tracker():
+    """The tracker checks the prediction after gap filling (Fig. 3(c) then (d)) and the updated
+    map with the SAD check after the Kalman update; both only ever invalidate pixels."""
+    seq = synth.small_pair(1)
+    W, H = seq.cam.W, seq.cam.H
+    base = dict(d_max=63, census_w=5, census_h=5, n_paths=4, fill_gaps=True)
+    prm = oracle.Params(W, H, pred_lr_check=True, sad_check=True, **base)
+    tr = oracle.Tracker(prm)
+    tr.frame(seq.left[0], seq.right[0], None, None, seq.K, seq.cam.b)
+    out = tr.frame(seq.left[1], seq.right[1], seq.R[1], seq.t[1], seq.K, seq.cam.b, keep=True)
+    raw = (out["Dpred_raw"], out["Ppred_raw"])
+    ref = oracle.pred_lr_check(*oracle.fill_gaps(*raw, prm.gamma_f), prm.pred_lr_tol)
+    assert np.array_equal(ref[0], out["Dpred"]) and np.array_equal(ref[1], out["Ppred"])
+    filled = oracle.fill_gaps(*raw, prm.gamma_f)[0]
+    assert (out["Dpred"] < 0).sum() > (filled < 0).sum()     # the left border band goes
+    chk = oracle.sad_check(seq.left[1], seq.right[1], out["D_unchecked"], out["P_unchecked"],
+                           prm.sad_w, prm.sad_h, prm.sad_thr)
+    assert np.array_equal(chk[0], out["D"]) and np.array_equal(chk[1], out["P"])
+    changed = out["D"] != out["D_unchecked"]
+    assert np.all(out["D"][changed] == -1)
