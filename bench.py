@@ -436,6 +436,9 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     ctx_plain = make(0)  # the prediction without gap filling, for comparison
     # the prediction with its edges rejected (Sec. 2.2) before the gap filling, for comparison
     ctx_edge = make(tsgm.FLAG_FILL_GAPS | tsgm.FLAG_EDGE_REJECT)
+    # the prediction's left-right check (Sec. 2.2, Fig. 3(d)) and the SAD check of the updated
+    # map (Sec. 2.4) on top of the gap filling, for comparison
+    ctx_chk = make(tsgm.FLAG_FILL_GAPS | tsgm.FLAG_PRED_LR_CHECK | tsgm.FLAG_SAD_CHECK)
     Dout = torch.empty((H, W), dtype=torch.float32, device=dev)
     Pout = torch.empty_like(Dout)
 
@@ -469,6 +472,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     cells_full, bad_full = characterise(ctx_full)
     cells_plain, bad_plain = characterise(ctx_plain)
     cells_edge, bad_edge = characterise(ctx_edge)
+    cells_chk, bad_chk = characterise(ctx_chk)
 
     def timed(c, K_steps, W_steps, profile):
         for _ in range(W_steps):
@@ -505,6 +509,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     k_full = max(1, args.steps // 2)
     t_plain, _, _, stages_plain = timed(ctx_plain, k_full, 3, profile=True)
     t_edge, _, _, _ = timed(ctx_edge, k_full, 3, profile=False)
+    t_chk, _, _, _ = timed(ctx_chk, k_full, 3, profile=False)
 
     # end to end through the host-buffer entry point (pinned host memory)
     hl = [torch.from_numpy(x).pin_memory() for x in seq.left]
@@ -583,6 +588,9 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
         "with_edge_rejection": {"fps": N_FRAMES * k_full / (t_edge / 1000.0),
                                 "search_space_frac": [c / (n * 128) for c in cells_edge],
                                 "bad3px_updated": bad_edge},
+        "with_consistency_checks": {"fps": N_FRAMES * k_full / (t_chk / 1000.0),
+                                    "search_space_frac": [c / (n * 128) for c in cells_chk],
+                                    "bad3px_updated": bad_chk},
         "search_space_frac": [c / (n * 128) for c in cells_red],
         "bad3px": {"reduced_updated": bad_red, "full_range_updated": bad_full},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},

@@ -61,6 +61,10 @@ typedef enum {
 #define TSGM_FLAG_EDGE_REJECT 8u     /* tsgm_frame rejects predicted pixels next to a disparity
                                         discontinuity (Sec. 2.2, disparity refinement), before
                                         the gap filling */
+#define TSGM_FLAG_PRED_LR_CHECK 16u  /* tsgm_frame checks the prediction against the right view's
+                                        prediction (Sec. 2.2, Fig. 3(d)), after the gap filling */
+#define TSGM_FLAG_SAD_CHECK 32u      /* tsgm_frame rejects pixels of the updated map whose left /
+                                        right patch SAD is high (Sec. 2.4), after the update */
 
 typedef struct {
     int32_t width, height;       /* image size, 1 <= width <= 13000, 1 <= height */
@@ -76,10 +80,14 @@ typedef struct {
     uint32_t flags;              /* TSGM_FLAG_* */
     float gamma_f;               /* similarity threshold of the gap filling (Eq. 8), px */
     float edge_thr;              /* discontinuity threshold of the edge rejection, px */
+    float pred_lr_tol;           /* similarity threshold of the prediction's left-right check, px */
+    int32_t sad_w, sad_h;        /* SAD check patch, odd sizes 1 .. 31 */
+    float sad_thr;               /* SAD check: mean absolute difference per patch pixel, grey levels */
 } tsgm_params;
 
 /* Fill *p with the defaults: d_max 127, census 9x7, 8 paths, P1 8, P2 32, sigma_mult 3,
- * q 0.25, S_max 10, r_min 0.5, lr_tol 1, flags 0, gamma_f 1, edge_thr 1. */
+ * q 0.25, S_max 10, r_min 0.5, lr_tol 1, flags 0, gamma_f 1, edge_thr 1, pred_lr_tol 1,
+ * SAD patch 5x5, sad_thr 30. */
 void tsgm_default_params(tsgm_params* p, int32_t width, int32_t height);
 
 /* Create a context. `cuda_stream` is the cudaStream_t every call of the context is enqueued on
@@ -123,6 +131,24 @@ tsgm_status tsgm_fill_gaps(tsgm_ctx* ctx, float* pred_D, float* pred_P);
  * becomes invalid (-1 in both maps); invalid neighbours do not count. The pass reads the map as it
  * was before it. Uses the context's D_z/r_z buffers as scratch. */
 tsgm_status tsgm_edge_reject(tsgm_ctx* ctx, float* pred_D, float* pred_P);
+
+/* Left-right consistency check of a prediction (Sec. 2.2, Sec. 3 and Fig. 3(d); the paper leaves
+ * the right view's propagation open: here it is formed from the left prediction). In place on
+ * the device maps pred_D, pred_P (W x H, row-major, -1 = invalid). Every valid pixel (x, y, d)
+ * lands on the right view's pixel x - round(d) of its row, round(d) = floor(d + 1/2) in binary32,
+ * and the right view keeps the largest disparity landing on each pixel; a valid pixel stays valid
+ * when its landing pixel is inside the image and holds a disparity within pred_lr_tol of its own,
+ * else it becomes -1 in both maps (seen by one camera only, or hidden behind a nearer surface). */
+tsgm_status tsgm_pred_lr_check(tsgm_ctx* ctx, float* pred_D, float* pred_P);
+
+/* SAD check (Sec. 2.4, disparity consistency check) on an updated map, in place on the device
+ * maps D, P with the device images left, right (uint8, W x H): the sum of absolute differences
+ * between the sad_w x sad_h patch of the left image around (x, y) and the right image's patch
+ * around (x - round(d), y), coordinates clamped into the image; a valid pixel whose SAD is above
+ * sad_thr * sad_w * sad_h (binary32) becomes -1 in both maps, so that the next image searches it
+ * over the whole range. */
+tsgm_status tsgm_sad_check(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right, float* D,
+                           float* P);
 
 /* Reduced search space (Sec. 2.3): d_lo = max(0, floor(d - k sqrt(p))), d_hi = min(d_max,
  * ceil(d + k sqrt(p))) with k = sigma_mult, binary32; the whole range [0, d_max] where the

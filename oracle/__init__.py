@@ -81,7 +81,7 @@ class Params:
     sad_check: bool = False      # Sec. 2.4, SAD check of the updated map on the two images
     sad_w: int = 5               # patch (odd sizes; not given)
     sad_h: int = 5
-    sad_thr: float = 20.0        # mean absolute difference per patch pixel (value not given)
+    sad_thr: float = 30.0        # mean absolute difference per patch pixel (value not given)
 
     @property
     def D(self) -> int:

@@ -87,6 +87,19 @@ tsgm_status check_params(const tsgm_params* p, std::string& why) {
         why = "edge_thr must be finite and >= 0";
         return TSGM_ERR_INVALID_ARG;
     }
+    if (!(p->pred_lr_tol >= 0.0f) || !std::isfinite(p->pred_lr_tol)) {
+        why = "pred_lr_tol must be finite and >= 0";
+        return TSGM_ERR_INVALID_ARG;
+    }
+    if (p->sad_w < 1 || p->sad_w > 31 || p->sad_w % 2 == 0 || p->sad_h < 1 || p->sad_h > 31 ||
+        p->sad_h % 2 == 0) {
+        why = "sad_w and sad_h must be odd, 1 .. 31";
+        return TSGM_ERR_INVALID_ARG;
+    }
+    if (!(p->sad_thr >= 0.0f) || !std::isfinite(p->sad_thr)) {
+        why = "sad_thr must be finite and >= 0";
+        return TSGM_ERR_INVALID_ARG;
+    }
     if (!(p->gamma_f >= 0.0f) || !std::isfinite(p->gamma_f)) {
         why = "gamma_f must be finite and >= 0";
         return TSGM_ERR_INVALID_ARG;
@@ -191,6 +204,28 @@ tsgm_status warp_stage(tsgm_ctx* ctx, const float* prevD, const float* prevP, co
     return TSGM_OK;
 }
 
+// Sec. 2.2 / Fig. 3(d): the prediction's left-right check, in place.
+tsgm_status pred_lr_stage(tsgm_ctx* ctx, float* D, float* P) {
+    stage_begin(ctx, TSGM_STAGE_WARP);
+    TSGM_LAUNCH(launch_pred_lr(D, P, ctx->W, ctx->H, ctx->prm.pred_lr_tol, ctx->stream),
+                "prediction left-right check");
+    stage_end(ctx, TSGM_STAGE_WARP);
+    return TSGM_OK;
+}
+
+// Sec. 2.4: SAD check of an updated map, in place on (D, P) and (D2, P2) when given.
+tsgm_status sad_stage(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right, float* D, float* P,
+                      float* D2, float* P2) {
+    const tsgm_params& p = ctx->prm;
+    const float lim = p.sad_thr * (float)(p.sad_w * p.sad_h);
+    stage_begin(ctx, TSGM_STAGE_KALMAN);
+    TSGM_LAUNCH(launch_sad_check(left, right, ctx->W, ctx->H, p.sad_w, p.sad_h, lim, D, P, D2, P2,
+                                 ctx->stream),
+                "SAD check");
+    stage_end(ctx, TSGM_STAGE_KALMAN);
+    return TSGM_OK;
+}
+
 // Sec. 2.2 edge rejection, in place on (D, P) through the D_z/r_z scratch.
 tsgm_status edge_reject_stage(tsgm_ctx* ctx, float* D, float* P) {
     stage_begin(ctx, TSGM_STAGE_WARP);
@@ -284,6 +319,10 @@ void tsgm_default_params(tsgm_params* p, int32_t width, int32_t height) {
     p->flags = 0;
     p->gamma_f = 1.0f;
     p->edge_thr = 1.0f;
+    p->pred_lr_tol = 1.0f;
+    p->sad_w = 5;
+    p->sad_h = 5;
+    p->sad_thr = 30.0f;
 }
 
 tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out) {
@@ -409,6 +448,21 @@ tsgm_status tsgm_edge_reject(tsgm_ctx* ctx, float* pred_D, float* pred_P) {
     return edge_reject_stage(ctx, pred_D, pred_P);
 }
 
+tsgm_status tsgm_pred_lr_check(tsgm_ctx* ctx, float* pred_D, float* pred_P) {
+    if (!ctx) return TSGM_ERR_INVALID_ARG;
+    if (!pred_D || !pred_P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_pred_lr_check: null pointer");
+    if (pred_D == pred_P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_pred_lr_check: maps alias");
+    return pred_lr_stage(ctx, pred_D, pred_P);
+}
+
+tsgm_status tsgm_sad_check(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right, float* D,
+                           float* P) {
+    if (!ctx) return TSGM_ERR_INVALID_ARG;
+    if (!left || !right || !D || !P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_sad_check: null pointer");
+    if (D == P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_sad_check: maps alias");
+    return sad_stage(ctx, left, right, D, P, nullptr, nullptr);
+}
+
 tsgm_status tsgm_windows(tsgm_ctx* ctx, const float* pred_D, const float* pred_P, int16_t* d_lo,
                          int16_t* d_hi, uint64_t* n_cells_host) {
     if (!ctx) return TSGM_ERR_INVALID_ARG;
@@ -460,6 +514,7 @@ tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
         TSGM_TRY(warp_stage(ctx, ctx->stateD, ctx->stateP, R, t, K, baseline, ctx->predD, ctx->predP));
         if (ctx->prm.flags & TSGM_FLAG_EDGE_REJECT) TSGM_TRY(edge_reject_stage(ctx, ctx->predD, ctx->predP));
         if (ctx->prm.flags & TSGM_FLAG_FILL_GAPS) TSGM_TRY(fill_gaps_stage(ctx, ctx->predD, ctx->predP));
+        if (ctx->prm.flags & TSGM_FLAG_PRED_LR_CHECK) TSGM_TRY(pred_lr_stage(ctx, ctx->predD, ctx->predP));
     } else {
         TSGM_LAUNCH(launch_fill(ctx->predD, -1.0f, ctx->n, ctx->stream), "fill");
         TSGM_LAUNCH(launch_fill(ctx->predP, -1.0f, ctx->n, ctx->stream), "fill");
@@ -477,6 +532,8 @@ tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
                           ctx->stateP, ctx->stream),
             "kalman");
     stage_end(ctx, TSGM_STAGE_KALMAN);
+    if (ctx->prm.flags & TSGM_FLAG_SAD_CHECK)
+        TSGM_TRY(sad_stage(ctx, left, right, D, P, ctx->stateD, ctx->stateP));
     ctx->has_prev = 1;
     return TSGM_OK;
 }

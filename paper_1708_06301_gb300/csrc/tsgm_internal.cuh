@@ -43,6 +43,12 @@ cudaError_t launch_offsets(const int16_t* lo, const int16_t* hi, const uint32_t*
                            const uint32_t* rowcells, int W, int Hh, uint32_t* off, uint2* desc,
                            uint32_t* cells_total, uint32_t* wq, cudaStream_t st);
 cudaError_t launch_fill(float* a, float v, int n, cudaStream_t st);
+// left-right check of a prediction, in place, one block per row
+cudaError_t launch_pred_lr(float* D, float* P, int W, int Hh, float tol, cudaStream_t st);
+// SAD check of an updated map, in place on (D, P) and, when given, on (D2, P2)
+cudaError_t launch_sad_check(const uint8_t* left, const uint8_t* right, int W, int Hh, int sw,
+                             int sh, float lim, float* D, float* P, float* D2, float* P2,
+                             cudaStream_t st);
 cudaError_t launch_edge_reject(const float* Din, const float* Pin, int W, int Hh, float thr,
                                float* Dout, float* Pout, cudaStream_t st);
 cudaError_t launch_fill_gaps(const float* Din, const float* Pin, int W, int Hh, float gamma_f,

@@ -255,6 +255,83 @@ __global__ void __launch_bounds__(256) k_edge_reject(const float* __restrict__ D
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Left-right check of the prediction (Sec. 2.2, Fig. 3(d)), one block per row, in place: the
+// right view's prediction of the row in shared memory (every valid pixel lands on x - round(d),
+// round(d) = floor(d + 1/2) in binary32, and the right pixel keeps the largest disparity, by an
+// atomic maximum on the bit patterns of non-negative floats), then a pixel stays valid where its
+// landing pixel lies in the image and holds a disparity within tol of its own.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int right_col(int x, float d) {
+    const float rf = floorf(__fadd_rn(d, 0.5f));
+    return rf > (float)x ? -1 : x - (int)rf;
+}
+
+__global__ void __launch_bounds__(512) k_pred_lr(float* __restrict__ D, float* __restrict__ P,
+                                                 int W, float tol) {
+    extern __shared__ unsigned int rbits[];  // W right pixels (0 = +0.0f, below any landing)
+    float* const d = D + (size_t)blockIdx.x * W;
+    float* const p = P + (size_t)blockIdx.x * W;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) rbits[x] = 0u;
+    __syncthreads();
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const float dv = d[x];
+        if (!(valid_value(dv) && valid_value(p[x]))) continue;
+        const int r = right_col(x, dv);
+        if (r >= 0) atomicMax(rbits + r, __float_as_uint(dv));
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const float dv = d[x];
+        if (!(valid_value(dv) && valid_value(p[x]))) continue;
+        const int r = right_col(x, dv);
+        if (!(r >= 0 && fabsf(__fsub_rn(dv, __uint_as_float(rbits[r]))) <= tol)) {
+            d[x] = -1.0f;
+            p[x] = -1.0f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// SAD check of an updated map (Sec. 2.4), one thread per pixel, in place: the left patch around
+// (x, y) against the right patch around (x - round(d), y), coordinates clamped into the image; a
+// valid pixel whose SAD is above lim is rejected in (D, P) and, when given, in (D2, P2).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sad_check(const uint8_t* __restrict__ L,
+                                                   const uint8_t* __restrict__ R, int W, int Hh,
+                                                   int sw, int sh, float lim,
+                                                   float* __restrict__ D, float* __restrict__ P,
+                                                   float* __restrict__ D2, float* __restrict__ P2) {
+    const int n = W * Hh;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float dv = D[i];
+    if (!(valid_value(dv) && valid_value(P[i]))) return;
+    const int y = i / W, x = i - y * W;
+    const float rf = floorf(__fadd_rn(dv, 0.5f));
+    const int dx = rf > (float)(2 * W) ? 2 * W : (int)rf;  // beyond the image either way
+    const int hw = sw / 2, hh = sh / 2;
+    int sad = 0;
+    for (int v = -hh; v <= hh; ++v) {
+        const int yy = min(max(y + v, 0), Hh - 1);
+        const uint8_t* const lrow = L + (size_t)yy * W;
+        const uint8_t* const rrow = R + (size_t)yy * W;
+        for (int u = -hw; u <= hw; ++u) {
+            const int xl = min(max(x + u, 0), W - 1);
+            const int xr = min(max(x - dx + u, 0), W - 1);
+            sad += abs((int)__ldg(lrow + xl) - (int)__ldg(rrow + xr));
+        }
+    }
+    if ((float)sad > lim) {
+        D[i] = -1.0f;
+        P[i] = -1.0f;
+        if (D2) {
+            D2[i] = -1.0f;
+            P2[i] = -1.0f;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_warp_scatter(const float* Dprev, const float* Pprev, const float* H, float cx,
@@ -272,6 +349,25 @@ cudaError_t launch_warp_gather(const unsigned long long* keys, const float* Dpre
                                const float* Pprev, float q, int n, float* Dpred, float* Ppred,
                                cudaStream_t st) {
     k_warp_gather<<<grid_for(n, 256), 256, 0, st>>>(keys, Dprev, Pprev, q, n, Dpred, Ppred);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pred_lr(float* D, float* P, int W, int Hh, float tol, cudaStream_t st) {
+    const size_t smem = (size_t)W * sizeof(unsigned int);
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_pred_lr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_pred_lr<<<Hh, 512, smem, st>>>(D, P, W, tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sad_check(const uint8_t* left, const uint8_t* right, int W, int Hh, int sw,
+                             int sh, float lim, float* D, float* P, float* D2, float* P2,
+                             cudaStream_t st) {
+    const int n = W * Hh;
+    k_sad_check<<<(n + 255) / 256, 256, 0, st>>>(left, right, W, Hh, sw, sh, lim, D, P, D2, P2);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,8 @@ FLAG_KEEP_INTERNALS = 1
 FLAG_FULL_RANGE = 2
 FLAG_FILL_GAPS = 4
 FLAG_EDGE_REJECT = 8
+FLAG_PRED_LR_CHECK = 16
+FLAG_SAD_CHECK = 32
 N_STAGES = 8
 STAGES = ["warp", "windows", "census", "cost", "sgm", "select", "kalman", "offsets"]
 BUF = dict(census_l=0, census_r=1, offsets=2, cost=3, S=4, dstar=5, dright=6, lr_valid=7,
@@ -41,7 +43,10 @@ class Params(ctypes.Structure):
                 ("sigma_mult", ctypes.c_float), ("q", ctypes.c_float), ("S_max", ctypes.c_float),
                 ("r_min", ctypes.c_float), ("lr_tol", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("gamma_f", ctypes.c_float),
-                ("edge_thr", ctypes.c_float)]
+                ("edge_thr", ctypes.c_float),
+                ("pred_lr_tol", ctypes.c_float),
+                ("sad_w", ctypes.c_int32), ("sad_h", ctypes.c_int32),
+                ("sad_thr", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,6 +75,8 @@ _SIGS = {
     "tsgm_census": (ctypes.c_int, [_vp, _vp, _vp]),
     "tsgm_fill_gaps": (ctypes.c_int, [_vp, _vp, _vp]),
     "tsgm_edge_reject": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tsgm_pred_lr_check": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tsgm_sad_check": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "tsgm_inspect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64]),
     "tsgm_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -297,6 +304,14 @@ class Context:
     def edge_reject(self, pred_D, pred_P):
         self._check(self.lib.tsgm_edge_reject(self.h, _ptr(pred_D), _ptr(pred_P)),
                     "tsgm_edge_reject")
+
+    def pred_lr_check(self, pred_D, pred_P):
+        self._check(self.lib.tsgm_pred_lr_check(self.h, _ptr(pred_D), _ptr(pred_P)),
+                    "tsgm_pred_lr_check")
+
+    def sad_check(self, left, right, D, P):
+        self._check(self.lib.tsgm_sad_check(self.h, _ptr(left), _ptr(right), _ptr(D), _ptr(P)),
+                    "tsgm_sad_check")
 
     def census(self, img, codes):
         self._check(self.lib.tsgm_census(self.h, _ptr(img), _ptr(codes)), "tsgm_census")

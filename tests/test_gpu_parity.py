@@ -323,6 +323,9 @@ def test_errors_are_status_codes(tsgm):
         tsgm.Context(tsgm.default_params(64, 32, n_paths=5))
     with pytest.raises(tsgm.TsgmError):
         tsgm.Context(tsgm.default_params(64, 32, d_max=300))
+    for bad in (dict(sad_w=4), dict(sad_h=33), dict(sad_thr=-1.0), dict(pred_lr_tol=float("nan"))):
+        with pytest.raises(tsgm.TsgmError):
+            tsgm.Context(tsgm.default_params(64, 32, **bad))
     with make_ctx(tsgm, 64, 32) as ctx:
         with pytest.raises(tsgm.TsgmError) as e:
             ctx.match(0, 0, 0, 0, 0, 0)
@@ -407,6 +410,88 @@ def test_frames_with_edge_rejection_and_gap_filling(tsgm):
     W, H = seq.cam.W, seq.cam.H
     g = run_sequence(tsgm, seq, n, 63, 5, 5, 4, flags=1 | 4 | 8)
     tr = oracle.Tracker(oparams(W, H, d_max=63, fill_gaps=True, edge_reject=True))
+    for k in range(n):
+        o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
+        assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
+        assert_maps(g[k]["D"], g[k]["P"], o["D"], o["P"])
+
+
+@pytest.mark.parametrize("tol", [0.5, 1.0])
+def test_pred_lr_check_bitexact(tsgm, tol):
+    """The prediction's left-right check (Sec. 2.2, Fig. 3(d)) of a warped, gap-filled
+    prediction: the GPU pass equals the oracle's and removes the band seen by the left camera
+    only, plus the occluded background."""
+    W, H = 1242, 375
+    seq = synth.kitti_like(2, n_frames=2)
+    D = seq.gt_disp[0].astype(np.float32)
+    P = np.full_like(D, 0.5)
+    D[::97, ::13] = -1.0
+    K = synth.Camera(W, H, 721.0, 0.54).K
+    with make_ctx(tsgm, W, H, d_max=127, pred_lr_tol=tol) as ctx:
+        pD, pP = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.warp_predict(dev(D), dev(P), seq.R[1], seq.t[1], K, f32(0.54), pD, pP)
+        ctx.fill_gaps(pD, pP)
+        Dw, Pw = host(pD, np.float32), host(pP, np.float32)
+        ctx.pred_lr_check(pD, pP)
+        Dg, Pg = host(pD, np.float32), host(pP, np.float32)
+    Do, Po = oracle.pred_lr_check(Dw, Pw, tol)
+    assert np.array_equal(Dg, Do) and np.array_equal(Pg, Po)
+    assert (Do < 0).sum() > (Dw < 0).sum()
+    # every pixel kept lands inside the right image
+    ys, xs = np.nonzero(Do >= 0)
+    assert np.all(xs >= np.floor(Do[ys, xs] + np.float32(0.5)))
+
+
+def test_pred_lr_check_small_and_large_disparities(tsgm):
+    """Rows narrower than the disparities (landing columns far outside the image), huge values,
+    holes and invalid variances, on a 7 x 3 image."""
+    rng = np.random.default_rng(11)
+    W, H = 7, 3
+    D = rng.uniform(0, 12, (H, W)).astype(np.float32)
+    D[0, 3] = 3.0e38
+    D[1, 1] = -1.0
+    P = np.full_like(D, 1.0)
+    P[2, 5] = -1.0
+    with make_ctx(tsgm, W, H, d_max=63, pred_lr_tol=2.0) as ctx:
+        pD, pP = dev(D), dev(P)
+        ctx.pred_lr_check(pD, pP)
+        Dg, Pg = host(pD, np.float32), host(pP, np.float32)
+    Do, Po = oracle.pred_lr_check(D, P, 2.0)
+    assert np.array_equal(Dg, Do) and np.array_equal(Pg, Po)
+
+
+@pytest.mark.parametrize("sw,sh,thr", [(5, 5, 20.0), (3, 7, 8.0), (1, 1, 0.0), (9, 3, 12.5)])
+def test_sad_check_bitexact(tsgm, sw, sh, thr):
+    """SAD check (Sec. 2.4) of a map near the true disparities with noise, outliers and holes,
+    on a rendered pair: the GPU pass equals the oracle's."""
+    seq = synth.kitti_like(2, n_frames=1)
+    W, H = seq.cam.W, seq.cam.H
+    rng = np.random.default_rng(sw * 100 + sh)
+    D = (seq.gt_disp[0] + rng.normal(0, 0.7, (H, W))).astype(np.float32)
+    out = rng.random((H, W)) < 0.05
+    D[out] = rng.uniform(0, 127, out.sum()).astype(np.float32)
+    D[rng.random((H, W)) < 0.02] = -1.0
+    D[D < 0] = -1.0
+    P = np.where(D >= 0, 0.7, -1.0).astype(np.float32)
+    with make_ctx(tsgm, W, H, d_max=127, sad_w=sw, sad_h=sh, sad_thr=thr) as ctx:
+        gD, gP = dev(D), dev(P)
+        ctx.sad_check(dev(seq.left[0]), dev(seq.right[0]), gD, gP)
+        Dg, Pg = host(gD, np.float32), host(gP, np.float32)
+    Do, Po = oracle.sad_check(seq.left[0], seq.right[0], D, P, sw, sh, thr)
+    assert np.array_equal(Dg, Do) and np.array_equal(Pg, Po)
+    if thr > 0:
+        assert 0 < (Do < 0).sum() - (D < 0).sum() < 0.5 * D.size
+
+
+def test_frames_with_prediction_checks(tsgm):
+    """Whole frames with gap filling, the prediction's left-right check and the SAD check of the
+    updated map (flags 4 | 16 | 32): windows and maps equal the oracle tracker's."""
+    seq = synth.make_sequence(5, 320, 96, 721.0, 0.54, n_frames=3, n_boxes=4, step_range=(0.4, 0.6),
+                              yaw_deg=1.0, noise_sigma=1.0)
+    n = 3
+    W, H = seq.cam.W, seq.cam.H
+    g = run_sequence(tsgm, seq, n, 63, 5, 5, 4, flags=1 | 4 | 16 | 32)
+    tr = oracle.Tracker(oparams(W, H, d_max=63, fill_gaps=True, pred_lr_check=True, sad_check=True))
     for k in range(n):
         o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
         assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
