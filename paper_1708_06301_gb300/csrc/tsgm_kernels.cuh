@@ -247,24 +247,38 @@ __device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int
     out[y * W + x] = code;
 }
 
-// pixels g, g + ngroups, ... of one image, each walked by a group of 8 lanes (lane `sub`)
+// pixels g, g + ngroups, ... of one image, each walked by a group of 8 lanes (lane `sub`); the
+// row and column advance by the stride's quotient and remainder (no division per pixel), and the
+// next pixel's descriptor and left code are loaded while the current one's cells are computed
 __device__ __forceinline__ void cost_pixels(const uint64_t* __restrict__ cl,
                                             const uint64_t* __restrict__ cr,
                                             const uint2* __restrict__ desc, int W, int n, int Bc,
                                             uint8_t* __restrict__ C, int g, int sub, int ngroups) {
+    const int dy = ngroups / W, dx = ngroups - dy * W;
+    int y = g / W, x = g - y * W;
+    uint2 dnext = g < n ? desc[g] : make_uint2(0u, 0u);
+    uint64_t cnext = g < n ? cl[g] : 0ull;
     for (int i = g; i < n; i += ngroups) {
-        const int y = i / W;
-        const int x = i - y * W;
-        const uint2 dsc = desc[i];
+        const uint2 dsc = dnext;
+        const uint64_t c0 = cnext;
+        if (i + ngroups < n) {
+            dnext = desc[i + ngroups];
+            cnext = cl[i + ngroups];
+        }
         const uint32_t o = dsc.x;
         const int a = (int)(dsc.y & 0xFFFFu);
         const int w = (int)(dsc.y >> 16);
-        const uint64_t c0 = cl[i];
         const uint64_t* row = cr + (size_t)y * W;
         for (int j = sub; j < w; j += 8) {
             const int xr = x - (a + j);
             const int c = xr >= 0 ? __popcll(c0 ^ row[xr]) : Bc;
             C[o + j] = (uint8_t)c;
+        }
+        y += dy;
+        x += dx;
+        if (x >= W) {
+            x -= W;
+            ++y;
         }
     }
 }
