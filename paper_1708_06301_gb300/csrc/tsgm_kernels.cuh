@@ -1672,10 +1672,13 @@ __device__ __forceinline__ void select_narrow(const uint8_t* __restrict__ Lvol, 
 // Selection of the pixels [x0, x1) of image row y (Eq. 9 and the left-right check), by one block.
 // The right-view keys of the row (per column xr, the (S << 9 | d) minimum over the pixels
 // x = xr + d whose window holds d) are reached through `part`: keymin(xr, key) (an atomic minimum
-// from one of this block's pixels), key(xr) (the row's final key, after sync()), own_keys() and
-// nkeys (this block's key array, to initialise) and sync() (every block working on the row).
-// `smem` holds this block's keys and the per-pixel state of its pixels, then the per-warp scratch;
-// `n_wide` is block-shared.
+// from one of this block's pixels), key(xr) (the row's final key, after sync()), own_keys(),
+// nkeys and key_base() (this block's key array and the column of its first key) and sync()
+// (every block working on the row). Narrow windows: one thread each. Wide ones: when the image
+// is split (select_split over the queue wq), already selected by select_wide, whose winners are
+// in wds and whose keys this block merges from gkeys_row (and resets for the next image);
+// otherwise queued in the block and taken one warp each. `smem` holds this block's keys and the
+// per-pixel state of its pixels, then the per-warp scratch; `n_wide` is block-shared.
 template <int NPATHS, int NCH, class Part>
 __device__ __forceinline__ void select_part(
     const uint8_t* __restrict__ Lvol, uint64_t vol_stride, const uint2* __restrict__ desc, int W,

@@ -62,9 +62,10 @@ __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restric
 
 // Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the
 // row's pixels (seg columns from x0). Every block keeps the right-view keys its own pixels can
-// reach, columns x0 - (D - 1) .. x0 + seg - 1, with atomics in its own shared memory; after the
-// cluster barrier the key of column xr is the minimum over the (at most few) blocks whose pixels
-// reach it, read through distributed shared memory.
+// reach, columns x0 - (D - 1) .. x0 + seg - 1, with atomics in its own shared memory (merging the
+// keys of the wide windows that k_select_wide took); after the cluster barrier the key of column
+// xr is the minimum over the (at most few) blocks whose pixels reach it, read through distributed
+// shared memory.
 constexpr int kSelCluster = 4;
 constexpr int kSelThreadsCl = 256;
 

@@ -496,3 +496,37 @@ def test_frames_with_prediction_checks(tsgm):
         o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
         assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
         assert_maps(g[k]["D"], g[k]["P"], o["D"], o["P"])
+
+
+@pytest.mark.parametrize("extra", [0, 1])
+def test_selection_split_boundary(tsgm, extra):
+    """The wide windows (> 16 labels) are selected apart from their rows while they are at most a
+    quarter of the image, and by their rows beyond: exactly a quarter and one more both equal the
+    oracle (the two selection kernels take the same decision)."""
+    W, H, D = 96, 40, 64
+    n = W * H
+    lo, hi = synth.mixed_windows(21, W, H, D, (2, 12), (17, 64), 0.0, 0.0)
+    lo = lo.copy()
+    hi = hi.copy()
+    rng = np.random.default_rng(4)
+    idx = rng.permutation(n)[: n // 4 + extra]
+    wl, wh = lo.reshape(-1), hi.reshape(-1)
+    wl[idx] = 0
+    wh[idx] = rng.integers(17, D, idx.size)               # 18 .. D labels: every one wide
+    assert int(((hi.astype(np.int64) - lo + 1) > 16).sum()) == n // 4 + extra
+    left, right = synth.random_images(77, W, H)
+    right = np.roll(left, -3, axis=1)
+    with make_ctx(tsgm, W, H, d_max=D - 1, n_paths=8) as ctx:
+        Dz, rz = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.match(dev(left), dev(right), dev(lo), dev(hi), Dz, rz)
+        ds, dr, va = empty((H, W), np.int16), empty((H, W), np.int16), empty((H, W), np.uint8)
+        ctx.inspect("dstar", ds, n)
+        ctx.inspect("dright", dr, n)
+        ctx.inspect("lr_valid", va, n)
+        g = dict(ds=host(ds, np.int16), dr=host(dr, np.int16), va=host(va, np.uint8),
+                 Dz=host(Dz, np.float32), rz=host(rz, np.float32))
+    o = oracle.match(left, right, lo, hi, oparams(W, H, d_max=D - 1, n_paths=8), keep=True)
+    assert np.array_equal(g["ds"].astype(np.int32), o["dstar"])
+    assert np.array_equal(g["dr"].astype(np.int32), o["dright"])
+    assert np.array_equal(g["va"], o["valid"])
+    assert_maps(g["Dz"], g["rz"], o["Dz"], o["rz"])
