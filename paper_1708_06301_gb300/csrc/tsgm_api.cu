@@ -127,22 +127,24 @@ void timing_resolve(tsgm_ctx* c) {
     c->ev_used = 0;
 }
 
-void stage_begin(tsgm_ctx* c, int s) {
+void stage_begin(tsgm_ctx* c, int s, cudaStream_t st) {
     if (!c->prof || c->ev_pool.size() < 2) return;
     if (c->ev_used + 2 > c->ev_pool.size()) timing_resolve(c);
     tsgm_ctx::EventRec r;
     r.stage = s;
     r.a = c->ev_pool[c->ev_used++];
     r.b = c->ev_pool[c->ev_used++];
-    cudaEventRecord(r.a, c->stream);
+    cudaEventRecord(r.a, st);
     c->ev_recs.push_back(r);
 }
+void stage_begin(tsgm_ctx* c, int s) { stage_begin(c, s, c->stream); }
 
-void stage_end(tsgm_ctx* c, int s) {
+void stage_end(tsgm_ctx* c, int s, cudaStream_t st) {
     if (!c->prof || c->ev_recs.empty()) return;
     tsgm_ctx::EventRec& r = c->ev_recs.back();
-    if (r.stage == s) cudaEventRecord(r.b, c->stream);
+    if (r.stage == s) cudaEventRecord(r.b, st);
 }
+void stage_end(tsgm_ctx* c, int s) { stage_end(c, s, c->stream); }
 
 template <typename T>
 cudaError_t alloc(T** p, size_t count) {
@@ -160,6 +162,11 @@ void free_all(tsgm_ctx* c) {
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    c->ev_fork = c->ev_join = nullptr;
+    c->aux = nullptr;
 }
 
 // H = Gamma T Gamma^{-1} (Eq. 1-4) in binary64; x, y relative to the principal point.
@@ -263,15 +270,28 @@ tsgm_status windows_stage(tsgm_ctx* ctx, const float* pD, const float* pP, int16
     return TSGM_OK;
 }
 
-// Matching on windows whose offsets are already in ctx->off.
-tsgm_status match_stages(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
-                         const int16_t* lo, const int16_t* hi, float* Dz, float* rz) {
+// The census of both images on the context's second stream, forked from its stream here; the cost
+// (match_stages) joins it. The census reads only the images, so it runs beside the prediction and
+// window stages enqueued in between.
+tsgm_status census_fork(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right) {
     const tsgm_params& p = ctx->prm;
-    stage_begin(ctx, TSGM_STAGE_CENSUS);
+    TSGM_CK(cudaEventRecord(ctx->ev_fork, ctx->stream), "census fork");
+    TSGM_CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0), "census fork");
+    stage_begin(ctx, TSGM_STAGE_CENSUS, ctx->aux);
     TSGM_LAUNCH(launch_census(left, right, ctx->W, ctx->H, p.census_w, p.census_h, ctx->censusL,
-                          ctx->censusR, ctx->stream),
-            "census");
-    stage_end(ctx, TSGM_STAGE_CENSUS);
+                              ctx->censusR, ctx->aux),
+                "census");
+    stage_end(ctx, TSGM_STAGE_CENSUS, ctx->aux);
+    TSGM_CK(cudaEventRecord(ctx->ev_join, ctx->aux), "census join");
+    return TSGM_OK;
+}
+
+// Matching on windows whose offsets are already in ctx->off and census codes forked by
+// census_fork.
+tsgm_status match_stages(tsgm_ctx* ctx, const int16_t* lo, const int16_t* hi, float* Dz,
+                         float* rz) {
+    const tsgm_params& p = ctx->prm;
+    TSGM_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "census join");
     stage_begin(ctx, TSGM_STAGE_COST);
     TSGM_LAUNCH(launch_cost(ctx->censusL, ctx->censusR, ctx->desc, ctx->W, ctx->H, ctx->Bc, ctx->C,
                             ctx->stream),
@@ -347,6 +367,9 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ctx->stream = (cudaStream_t)cuda_stream;  // NULL: the legacy default stream
     const size_t n = (size_t)ctx->n;
     bool ok = true;
+    ok = ok && cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && alloc(&ctx->censusL, n) == cudaSuccess;
     ok = ok && alloc(&ctx->censusR, n) == cudaSuccess;
     ok = ok && alloc(&ctx->keys, n) == cudaSuccess;
@@ -478,6 +501,7 @@ tsgm_status tsgm_match(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
     if (!ctx) return TSGM_ERR_INVALID_ARG;
     if (!left || !right || !d_lo || !d_hi || !D_z || !r_z)
         return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_match: null pointer");
+    TSGM_TRY(census_fork(ctx, left, right));
     // the caller's windows are copied, clamped into [0, d_max], into the context's buffers
     stage_begin(ctx, TSGM_STAGE_OFFSETS);
     TSGM_LAUNCH(launch_sanitize(d_lo, d_hi, ctx->W, ctx->H, ctx->D, ctx->lo, ctx->hi, ctx->rowsum,
@@ -487,7 +511,7 @@ tsgm_status tsgm_match(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
                                ctx->desc, ctx->cells, ctx->wq, ctx->stream),
                 "offsets");
     stage_end(ctx, TSGM_STAGE_OFFSETS);
-    return match_stages(ctx, left, right, ctx->lo, ctx->hi, D_z, r_z);
+    return match_stages(ctx, ctx->lo, ctx->hi, D_z, r_z);
 }
 
 tsgm_status tsgm_kalman_update(tsgm_ctx* ctx, const float* pred_D, const float* pred_P,
@@ -510,6 +534,7 @@ tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
     if (D == P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: D and P alias");
     if (ctx->has_prev && (!R || !t))
         return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: pose required after the first frame");
+    TSGM_TRY(census_fork(ctx, left, right));
     if (ctx->has_prev) {
         TSGM_TRY(warp_stage(ctx, ctx->stateD, ctx->stateP, R, t, K, baseline, ctx->predD, ctx->predP));
         if (ctx->prm.flags & TSGM_FLAG_EDGE_REJECT) TSGM_TRY(edge_reject_stage(ctx, ctx->predD, ctx->predP));
@@ -526,7 +551,7 @@ tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
     } else {
         TSGM_TRY(windows_stage(ctx, ctx->predD, ctx->predP, ctx->lo, ctx->hi));
     }
-    TSGM_TRY(match_stages(ctx, left, right, ctx->lo, ctx->hi, ctx->Dz, ctx->rz));
+    TSGM_TRY(match_stages(ctx, ctx->lo, ctx->hi, ctx->Dz, ctx->rz));
     stage_begin(ctx, TSGM_STAGE_KALMAN);
     TSGM_LAUNCH(launch_kalman(ctx->predD, ctx->predP, ctx->Dz, ctx->rz, ctx->n, D, P, ctx->stateD,
                           ctx->stateP, ctx->stream),

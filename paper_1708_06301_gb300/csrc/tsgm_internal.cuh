@@ -75,6 +75,10 @@ struct tsgm_ctx {
     int W = 0, H = 0, D = 0, n = 0, Bc = 0;
     uint64_t max_cells = 0;
     cudaStream_t stream = nullptr;
+    // second stream: the census of both images runs there beside the prediction and the windows
+    // (forked from `stream` by ev_fork, joined before the cost by ev_join)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // device scratch, all sized at create time
     uint64_t* censusL = nullptr;
