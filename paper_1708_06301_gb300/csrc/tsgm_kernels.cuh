@@ -254,7 +254,7 @@ __device__ __forceinline__ void cost_pixels(const uint64_t* __restrict__ cl,
                                             const uint64_t* __restrict__ cr,
                                             const uint2* __restrict__ desc, int W, int n, int Bc,
                                             uint8_t* __restrict__ C, int g, int sub, int ngroups) {
-    const int dy = ngroups / W, dx = ngroups - dy * W;
+    const int dy = g + ngroups < n ? ngroups / W : 0, dx = ngroups - dy * W;  // one pixel: unused
     int y = g / W, x = g - y * W;
     uint2 dnext = g < n ? desc[g] : make_uint2(0u, 0u);
     uint64_t cnext = g < n ? cl[g] : 0ull;
