@@ -190,6 +190,19 @@ tsgm_status tsgm_frame_host(tsgm_ctx* ctx, const uint8_t* left_host, const uint8
                             const float R[9], const float t[3], const float K[9],
                             float baseline, float* D_host, float* P_host);
 
+/* tsgm_frame_host without waiting: the input copies, the step and the output copies are
+ * enqueued and the call returns. The copies run on two transfer streams of the context and the
+ * context has two device staging slots, used in turn, so that one frame's copies overlap the
+ * computation of the frames before and after it. left_host/right_host must not change, and
+ * D_host/P_host must not be read, until tsgm_wait returns; host buffers must be pinned
+ * (page-locked). Frames complete in call order. */
+tsgm_status tsgm_frame_host_async(tsgm_ctx* ctx, const uint8_t* left_host,
+                                  const uint8_t* right_host, const float R[9], const float t[3],
+                                  const float K[9], float baseline, float* D_host, float* P_host);
+
+/* Wait for every frame and copy enqueued on the context. */
+tsgm_status tsgm_wait(tsgm_ctx* ctx);
+
 /* Forget the previous frame: the next tsgm_frame searches the whole range. */
 tsgm_status tsgm_reset(tsgm_ctx* ctx);
 

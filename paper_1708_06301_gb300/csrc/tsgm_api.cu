@@ -157,11 +157,21 @@ void free_all(tsgm_ctx* c) {
                     c->dright,  c->lrvalid, c->off,    c->rowsum, c->C,       c->S,
                     c->rowcells, c->cells,  c->desc,  c->Lvol,  c->adj_partials,
                     c->wq,      c->gkeys,   c->wds,
-                    c->d_left,  c->d_right, c->d_outD, c->d_outP};
+                    c->d_left,  c->d_right, c->d_outD, c->d_outP,
+                    c->d_left1, c->d_right1, c->d_outD1, c->d_outP1};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
+    for (int k = 0; k < 2; ++k) {
+        if (c->ev_slot_in[k]) cudaEventDestroy(c->ev_slot_in[k]);
+        if (c->ev_slot_used[k]) cudaEventDestroy(c->ev_slot_used[k]);
+        if (c->ev_slot_out[k]) cudaEventDestroy(c->ev_slot_out[k]);
+        c->ev_slot_in[k] = c->ev_slot_used[k] = c->ev_slot_out[k] = nullptr;
+    }
+    if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+    if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+    c->s_h2d = c->s_d2h = nullptr;
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -403,6 +413,17 @@ tsgm_status tsgm_create(const tsgm_params* p, void* cuda_stream, tsgm_ctx** out)
     ok = ok && alloc(&ctx->d_right, n) == cudaSuccess;
     ok = ok && alloc(&ctx->d_outD, n) == cudaSuccess;
     ok = ok && alloc(&ctx->d_outP, n) == cudaSuccess;
+    ok = ok && alloc(&ctx->d_left1, n) == cudaSuccess;
+    ok = ok && alloc(&ctx->d_right1, n) == cudaSuccess;
+    ok = ok && alloc(&ctx->d_outD1, n) == cudaSuccess;
+    ok = ok && alloc(&ctx->d_outP1, n) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&ctx->s_h2d, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+        ok = ok && cudaEventCreateWithFlags(&ctx->ev_slot_in[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&ctx->ev_slot_used[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&ctx->ev_slot_out[k], cudaEventDisableTiming) == cudaSuccess;
+    }
     if (!ok) {
         cudaGetLastError();
         free_all(ctx);
@@ -570,11 +591,56 @@ tsgm_status tsgm_frame_host(tsgm_ctx* ctx, const uint8_t* left_host, const uint8
     if (!left_host || !right_host || !D_host || !P_host)
         return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame_host: null pointer");
     const size_t n = (size_t)ctx->n;
+    // copies still pending from tsgm_frame_host_async use the same staging
+    TSGM_CK(cudaStreamSynchronize(ctx->s_h2d), "synchronize");
+    TSGM_CK(cudaStreamSynchronize(ctx->s_d2h), "synchronize");
     TSGM_CK(cudaMemcpyAsync(ctx->d_left, left_host, n, cudaMemcpyHostToDevice, ctx->stream), "h2d left");
     TSGM_CK(cudaMemcpyAsync(ctx->d_right, right_host, n, cudaMemcpyHostToDevice, ctx->stream), "h2d right");
     TSGM_TRY(tsgm_frame(ctx, ctx->d_left, ctx->d_right, R, t, K, baseline, ctx->d_outD, ctx->d_outP));
     TSGM_CK(cudaMemcpyAsync(D_host, ctx->d_outD, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "d2h D");
     TSGM_CK(cudaMemcpyAsync(P_host, ctx->d_outP, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream), "d2h P");
+    TSGM_CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_frame_host_async(tsgm_ctx* ctx, const uint8_t* left_host,
+                                  const uint8_t* right_host, const float R[9], const float t[3],
+                                  const float K[9], float baseline, float* D_host, float* P_host) {
+    if (!ctx) return TSGM_ERR_INVALID_ARG;
+    if (!left_host || !right_host || !D_host || !P_host)
+        return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame_host_async: null pointer");
+    if (D_host == P_host) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame_host_async: D and P alias");
+    if (ctx->has_prev && (!R || !t))
+        return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame_host_async: pose required after the first frame");
+    const size_t n = (size_t)ctx->n;
+    const int s = ctx->hslot;
+    ctx->hslot ^= 1;
+    uint8_t* const dl = s ? ctx->d_left1 : ctx->d_left;
+    uint8_t* const dr = s ? ctx->d_right1 : ctx->d_right;
+    float* const dD = s ? ctx->d_outD1 : ctx->d_outD;
+    float* const dP = s ? ctx->d_outP1 : ctx->d_outP;
+    // inputs: once the frame that used this slot two calls ago is done with it
+    TSGM_CK(cudaStreamWaitEvent(ctx->s_h2d, ctx->ev_slot_used[s], 0), "wait");
+    TSGM_CK(cudaMemcpyAsync(dl, left_host, n, cudaMemcpyHostToDevice, ctx->s_h2d), "h2d left");
+    TSGM_CK(cudaMemcpyAsync(dr, right_host, n, cudaMemcpyHostToDevice, ctx->s_h2d), "h2d right");
+    TSGM_CK(cudaEventRecord(ctx->ev_slot_in[s], ctx->s_h2d), "record");
+    // the step: after its inputs, and after the slot's outputs of two calls ago were copied out
+    TSGM_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_slot_in[s], 0), "wait");
+    TSGM_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_slot_out[s], 0), "wait");
+    TSGM_TRY(tsgm_frame(ctx, dl, dr, R, t, K, baseline, dD, dP));
+    TSGM_CK(cudaEventRecord(ctx->ev_slot_used[s], ctx->stream), "record");
+    // outputs: after the step, beside the next one
+    TSGM_CK(cudaStreamWaitEvent(ctx->s_d2h, ctx->ev_slot_used[s], 0), "wait");
+    TSGM_CK(cudaMemcpyAsync(D_host, dD, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->s_d2h), "d2h D");
+    TSGM_CK(cudaMemcpyAsync(P_host, dP, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->s_d2h), "d2h P");
+    TSGM_CK(cudaEventRecord(ctx->ev_slot_out[s], ctx->s_d2h), "record");
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_wait(tsgm_ctx* ctx) {
+    if (!ctx) return TSGM_ERR_INVALID_ARG;
+    TSGM_CK(cudaStreamSynchronize(ctx->s_d2h), "synchronize");
+    TSGM_CK(cudaStreamSynchronize(ctx->s_h2d), "synchronize");
     TSGM_CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     return TSGM_OK;
 }

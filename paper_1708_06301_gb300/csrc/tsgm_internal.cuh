@@ -112,6 +112,18 @@ struct tsgm_ctx {
     uint8_t* d_right = nullptr;
     float* d_outD = nullptr;
     float* d_outP = nullptr;
+    // tsgm_frame_host_async: two staging slots (slot 0 is the buffers above), used in turn; input
+    // copies on s_h2d, output copies on s_d2h; per slot: inputs copied (ev_slot_in), frame done with
+    // the slot (ev_slot_used), outputs copied out (ev_slot_out)
+    uint8_t* d_left1 = nullptr;
+    uint8_t* d_right1 = nullptr;
+    float* d_outD1 = nullptr;
+    float* d_outP1 = nullptr;
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_slot_in[2] = {nullptr, nullptr};
+    cudaEvent_t ev_slot_used[2] = {nullptr, nullptr};
+    cudaEvent_t ev_slot_out[2] = {nullptr, nullptr};
+    int hslot = 0;
 
     int has_prev = 0;
     uint64_t launches = 0;  // kernels enqueued by this context (for launch accounting)

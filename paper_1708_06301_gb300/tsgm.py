@@ -76,6 +76,8 @@ _SIGS = {
     "tsgm_fill_gaps": (ctypes.c_int, [_vp, _vp, _vp]),
     "tsgm_edge_reject": (ctypes.c_int, [_vp, _vp, _vp]),
     "tsgm_pred_lr_check": (ctypes.c_int, [_vp, _vp, _vp]),
+    "tsgm_frame_host_async": (ctypes.c_int, [_vp, _vp, _vp, _fp, _fp, _fp, ctypes.c_float, _vp, _vp]),
+    "tsgm_wait": (ctypes.c_int, [_vp]),
     "tsgm_sad_check": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "tsgm_inspect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64]),
     "tsgm_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -280,6 +282,23 @@ class Context:
         self._check(self.lib.tsgm_frame_host(self.h, hp(left), hp(right), Rp, tp, Kp,
                                              ctypes.c_float(baseline), hp(D), hp(P)),
                     "tsgm_frame_host")
+
+    def frame_host_async(self, left, right, R, t, K, baseline, D, P):
+        """Pinned host buffers in and out; returns at once (see tsgm_frame_host_async). The arrays
+        (and the pose arrays' copies kept here) must stay alive until wait()."""
+        def hp(a):
+            if hasattr(a, "data_ptr"):
+                return a.data_ptr()
+            return a.ctypes.data
+        Ra, Rp = _host_f32(R, 9)
+        ta, tp = _host_f32(t, 3)
+        Ka, Kp = _host_f32(K, 9)
+        self._check(self.lib.tsgm_frame_host_async(self.h, hp(left), hp(right), Rp, tp, Kp,
+                                                   ctypes.c_float(baseline), hp(D), hp(P)),
+                    "tsgm_frame_host_async")
+
+    def wait(self):
+        self._check(self.lib.tsgm_wait(self.h), "tsgm_wait")
 
     def reset(self):
         self._check(self.lib.tsgm_reset(self.h), "tsgm_reset")

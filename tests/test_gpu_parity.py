@@ -282,6 +282,34 @@ def test_frame_host_equals_device(tsgm):
             assert np.array_equal(D, g[k]["D"]) and np.array_equal(P, g[k]["P"])
 
 
+def test_frame_host_async_equals_device(tsgm):
+    """Frames enqueued with pinned host buffers and no wait in between (copies on the transfer
+    streams, two staging slots in turn), then one wait: every frame's maps equal the device
+    path's; a blocking call afterwards still works on the same context."""
+    import torch
+    seq = synth.make_sequence(7, 320, 96, 721.0, 0.54, n_frames=5, n_boxes=4, step_range=(0.4, 0.6),
+                              yaw_deg=1.0, noise_sigma=1.0)
+    W, H, n = 320, 96, 5
+    b = f32(seq.cam.b)
+    g = run_sequence(tsgm, seq, n, 63, 5, 5, 4)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    L = [pin(seq.left[k]) for k in range(n)]
+    R = [pin(seq.right[k]) for k in range(n)]
+    D = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(n)]
+    P = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(n)]
+    with make_ctx(tsgm, W, H) as ctx:
+        for k in range(n):
+            ctx.frame_host_async(L[k], R[k], seq.R[k], seq.t[k], seq.K, b, D[k], P[k])
+        ctx.wait()
+        for k in range(n):
+            assert np.array_equal(D[k].numpy(), g[k]["D"]) and np.array_equal(P[k].numpy(), g[k]["P"])
+        ctx.reset()
+        Dh = np.empty((H, W), np.float32)
+        Ph = np.empty((H, W), np.float32)
+        ctx.frame_host(seq.left[0], seq.right[0], seq.R[0], seq.t[0], seq.K, b, Dh, Ph)
+        assert np.array_equal(Dh, g[0]["D"]) and np.array_equal(Ph, g[0]["P"])
+
+
 def test_state_export_import_resume(tsgm):
     seq = synth.small_pair(1)
     W, H = 320, 96
@@ -530,3 +558,26 @@ def test_selection_split_boundary(tsgm, extra):
     assert np.array_equal(g["dr"].astype(np.int32), o["dright"])
     assert np.array_equal(g["va"], o["valid"])
     assert_maps(g["Dz"], g["rz"], o["Dz"], o["rz"])
+
+
+@pytest.mark.parametrize("W,H", [(1, 9), (13, 1), (3, 2)])
+def test_consistency_checks_degenerate_shapes(tsgm, W, H):
+    """One-pixel-wide and one-row images, and patches larger than the image (every coordinate
+    clamps): both checks equal the oracle."""
+    rng = np.random.default_rng(W * 31 + H)
+    D = rng.uniform(0, 6, (H, W)).astype(np.float32)
+    D[rng.random((H, W)) < 0.2] = -1.0
+    P = np.where(D >= 0, 1.0, -1.0).astype(np.float32)
+    L = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    R = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    with make_ctx(tsgm, W, H, d_max=15, pred_lr_tol=0.5, sad_w=31, sad_h=5, sad_thr=60.0) as ctx:
+        gD, gP = dev(D), dev(P)
+        ctx.pred_lr_check(gD, gP)
+        Dg, Pg = host(gD, np.float32), host(gP, np.float32)
+        sD, sP = dev(D), dev(P)
+        ctx.sad_check(dev(L), dev(R), sD, sP)
+        Sg, SPg = host(sD, np.float32), host(sP, np.float32)
+    Do, Po = oracle.pred_lr_check(D, P, 0.5)
+    assert np.array_equal(Dg, Do) and np.array_equal(Pg, Po)
+    So, SPo = oracle.sad_check(L, R, D, P, 31, 5, 60.0)
+    assert np.array_equal(Sg, So) and np.array_equal(SPg, SPo)
