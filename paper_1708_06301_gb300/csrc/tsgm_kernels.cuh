@@ -1702,7 +1702,7 @@ __device__ __forceinline__ void select_part(
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int t = threadIdx.x; t < part.nkeys; t += blockDim.x) drk[t] = 0xFFFFFFFFu;
     if (threadIdx.x == 0) n_wide = 0;
-    part.sync();
+    __syncthreads();  // keymin touches only this block's keys until the row's barrier below
 
     // ---- narrow windows: one thread per pixel, the labels unrolled to the widest narrow window
     // of the warp's pixels (8, 12 or 16)

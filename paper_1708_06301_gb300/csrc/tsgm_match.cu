@@ -229,7 +229,7 @@ cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths,
                         (size_t)(kSelThreadsCl / 32) * DP * sizeof(uint16_t);
     auto wide = n_paths == 8 ? (D <= 128 ? k_select_wide<8, 1> : k_select_wide<8, 2>)
                              : (D <= 128 ? k_select_wide<4, 1> : k_select_wide<4, 2>);
-    wide<<<152 * 4, 256, 0, st>>>(Lvol, vol_stride, desc, W, n, s_thr, r_min, Dz, rz, S, wds,
+    wide<<<152 * 8, 256, 0, st>>>(Lvol, vol_stride, desc, W, n, s_thr, r_min, Dz, rz, S, wds,
                                   gkeys, wq);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
