@@ -78,6 +78,9 @@ _SIGS = {
     "tsgm_pred_lr_check": (ctypes.c_int, [_vp, _vp, _vp]),
     "tsgm_frame_host_async": (ctypes.c_int, [_vp, _vp, _vp, _fp, _fp, _fp, ctypes.c_float, _vp, _vp]),
     "tsgm_wait": (ctypes.c_int, [_vp]),
+    "tsgm_warp_predict_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _fp, _fp,
+                                                 _fp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp,
+                                                 ctypes.c_char_p, ctypes.c_size_t]),
     "tsgm_sad_check": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "tsgm_inspect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64]),
     "tsgm_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -284,8 +287,9 @@ class Context:
                     "tsgm_frame_host")
 
     def frame_host_async(self, left, right, R, t, K, baseline, D, P):
-        """Pinned host buffers in and out; returns at once (see tsgm_frame_host_async). The arrays
-        (and the pose arrays' copies kept here) must stay alive until wait()."""
+        """Pinned host buffers in and out; returns at once (see tsgm_frame_host_async). The image
+        and map buffers must stay alive and untouched until wait(); R, t, K are read during the
+        call."""
         def hp(a):
             if hasattr(a, "data_ptr"):
                 return a.data_ptr()

@@ -36,11 +36,21 @@ def test_default_params(tsgm):
     p = tsgm.default_params(1242, 375)
     assert (p.d_max, p.census_w, p.census_h, p.n_paths, p.P1, p.P2) == (127, 9, 7, 8, 8, 32)
     assert (p.sigma_mult, p.q, p.S_max, p.r_min, p.lr_tol) == (3.0, 0.25, 10.0, 0.5, 1)
+    assert (p.flags, p.gamma_f, p.edge_thr, p.pred_lr_tol) == (0, 1.0, 1.0, 1.0)
+    assert (p.sad_w, p.sad_h, p.sad_thr) == (5, 5, 30.0)
+
+
+def test_binding_covers_the_header(tsgm):
+    """Every function the header declares has a ctypes signature in the binding."""
+    missing = [s for s in tsgm.header_symbols() if s not in tsgm._SIGS]
+    assert not missing, missing
 
 
 @pytest.mark.parametrize("bad", [dict(n_paths=5), dict(d_max=256), dict(census_w=4),
                                  dict(census_w=11, census_h=7), dict(P1=40, P2=30),
-                                 dict(P2=200), dict(width=0), dict(q=-1.0)])
+                                 dict(P2=200), dict(width=0), dict(q=-1.0), dict(sad_w=4),
+                                 dict(sad_h=0), dict(sad_w=33), dict(sad_thr=-0.5),
+                                 dict(pred_lr_tol=float("inf")), dict(edge_thr=float("nan"))])
 def test_create_rejects_bad_params_before_touching_the_gpu(tsgm, bad):
     p = tsgm.default_params(64, 32)
     for k, v in bad.items():
