@@ -253,16 +253,18 @@ tsgm_status tsgm_cells(tsgm_ctx* ctx, uint64_t* n_cells);
  * z-buffer memset are not counted). */
 tsgm_status tsgm_launches(tsgm_ctx* ctx, uint64_t* n);
 
-/* Stage timing with CUDA events on the context stream. When enabled, each call records events
+/* Stage timing with CUDA events on the context's streams. When enabled, each call records events
  * around its stages; tsgm_stage_times returns the accumulated milliseconds per stage since the
- * last enable (synchronises) and the number of times each was recorded. Stage ids: */
-#define TSGM_STAGE_WARP 0      /* scatter + gather */
+ * last enable (synchronises) and the number of times each was recorded. The events add a little
+ * time to the calls that record them. Stage ids: */
+#define TSGM_STAGE_WARP 0      /* scatter + gather, and the prediction's refinements (edge
+                                  rejection, gap filling, left-right check) */
 #define TSGM_STAGE_WINDOWS 1   /* windows + offsets */
-#define TSGM_STAGE_CENSUS 2
+#define TSGM_STAGE_CENSUS 2    /* on the context's second stream, beside the stages before the cost */
 #define TSGM_STAGE_COST 3
 #define TSGM_STAGE_SGM 4       /* path aggregation */
-#define TSGM_STAGE_SELECT 5    /* WTA, sub-pixel, r, LR check */
-#define TSGM_STAGE_KALMAN 6
+#define TSGM_STAGE_SELECT 5    /* WTA, sub-pixel, r, LR check (both selection kernels) */
+#define TSGM_STAGE_KALMAN 6    /* the update, and the SAD check of the updated map */
 #define TSGM_STAGE_OFFSETS 7   /* offsets of caller windows in tsgm_match */
 #define TSGM_N_STAGES 8
 tsgm_status tsgm_profile(tsgm_ctx* ctx, int32_t enable);
