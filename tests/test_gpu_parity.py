@@ -581,3 +581,42 @@ def test_consistency_checks_degenerate_shapes(tsgm, W, H):
     assert np.array_equal(Dg, Do) and np.array_equal(Pg, Po)
     So, SPo = oracle.sad_check(L, R, D, P, 31, 5, 60.0)
     assert np.array_equal(Sg, So) and np.array_equal(SPg, SPo)
+
+
+def test_frames_full_size_every_refinement(tsgm):
+    """The benchmark's workload at full size with every refinement on (edge rejection, gap
+    filling, the prediction's left-right check, the SAD check of the updated map; flags
+    4 | 8 | 16 | 32): windows and maps of three frames equal the oracle tracker's."""
+    seq = synth.kitti_like(2, n_frames=3)
+    g = run_sequence(tsgm, seq, 3, 127, 9, 7, 8, flags=1 | 4 | 8 | 16 | 32)
+    tr = oracle.Tracker(oparams(1242, 375, d_max=127, cw=9, ch=7, n_paths=8, fill_gaps=True,
+                                edge_reject=True, pred_lr_check=True, sad_check=True))
+    for k in range(3):
+        o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, f32(seq.cam.b), keep=True)
+        assert np.array_equal(g[k]["lo"], o["lo"]) and np.array_equal(g[k]["hi"], o["hi"])
+        assert_maps(g[k]["D"], g[k]["P"], o["D"], o["P"])
+
+
+def test_selection_split_with_256_labels(tsgm):
+    """Wide windows of up to 256 labels (two chunks of 128 per lane set) selected apart from their
+    rows (a few percent of the pixels wide): equal to the oracle."""
+    W, H, D = 160, 48, 256
+    lo, hi = synth.mixed_windows(33, W, H, D, (2, 14), (17, 256), 0.06, 0.04)
+    n = W * H
+    assert 0 < int(((hi.astype(np.int64) - lo + 1) > 16).sum()) <= n // 4
+    left, _ = synth.random_images(91, W, H)
+    right = np.roll(left, -9, axis=1)
+    with make_ctx(tsgm, W, H, d_max=D - 1, n_paths=8) as ctx:
+        Dz, rz = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.match(dev(left), dev(right), dev(lo), dev(hi), Dz, rz)
+        ds, dr, va = empty((H, W), np.int16), empty((H, W), np.int16), empty((H, W), np.uint8)
+        ctx.inspect("dstar", ds, n)
+        ctx.inspect("dright", dr, n)
+        ctx.inspect("lr_valid", va, n)
+        g = dict(ds=host(ds, np.int16), dr=host(dr, np.int16), va=host(va, np.uint8),
+                 Dz=host(Dz, np.float32), rz=host(rz, np.float32))
+    o = oracle.match(left, right, lo, hi, oparams(W, H, d_max=D - 1, n_paths=8), keep=True)
+    assert np.array_equal(g["ds"].astype(np.int32), o["dstar"])
+    assert np.array_equal(g["dr"].astype(np.int32), o["dright"])
+    assert np.array_equal(g["va"], o["valid"])
+    assert_maps(g["Dz"], g["rz"], o["Dz"], o["rz"])
