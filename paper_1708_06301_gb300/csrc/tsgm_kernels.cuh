@@ -1425,18 +1425,21 @@ __device__ __forceinline__ void sgm_pair_dense(const uint8_t* __restrict__ C,
 }
 
 // One pair of lines of one image: scan the windows of the (common) geometric line once. Lines
-// whose windows are all the full range are walked together by twin 0 with the paired full-range
+// whose windows are all the full range are walked together by one twin with the paired full-range
 // walker (two interleaved recurrences per warp); other lines are walked one per twin, line A by
 // twin 0 and line B by twin 1: with the branch-free narrow walker when no window is wider than 32
 // labels; the general walker when more than one pixel in 8 has a window of 33 .. D - 1 labels;
 // the narrow walker when at most one pixel in 8 is wide and the wide ones are scattered (runs
 // shorter than 8 on average); else the mixed walker (narrow and full-range runs at full speed). twin < 0: this warp walks the
-// whole pair alone. The choice changes the work, never the result.
+// whole pair alone. dense_twin: which twin walks an all-full-range pair (the launch alternates it
+// so that the walking warps of a block fall on all four SM sub-partitions). The choice changes
+// the work, never the result.
 template <int LPL>
 __device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
                                          const uint2* __restrict__ desc, int W, int Hh, int D,
                                          int P1, int P2, int codeA, int lA, uint8_t* __restrict__ LvA,
-                                         uint8_t* __restrict__ LvB, uint32_t* const wsm, int twin) {
+                                         uint8_t* __restrict__ LvB, uint32_t* const wsm, int twin,
+                                         int dense_twin = 0) {
     const int lane = threadIdx.x & 31;
     const int codeB = codeA + 1;
     const int lB = partner_line(codeA, lA, codeB, W, Hh);
@@ -1460,7 +1463,7 @@ __device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
     runs = (int)__reduce_add_sync(kFull, (unsigned)runs);
     const int other = wide - (D > 32 ? full : 0);  // windows of 33 .. D - 1 labels
     if (full == len && D > 32) {
-        if (twin == 1) return;
+        if (twin >= 0 && twin != dense_twin) return;
         const int code[2] = {codeA, codeB};
         const int l[2] = {lA, lB};
         uint8_t* const Lv[2] = {LvA, LvB};

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
 // Path aggregation of one image: all lines of all directions in one launch, two twin warps per
 // pair of opposite directions on one geometric line (see sgm_pair; horizontal pairs first: they
 // are the longest chains). `lines` lists the first direction of each pair (codes 0, 2, 4, 6) and
-// its line counts.
+// its line counts. The twin that walks an all-full-range pair is warp 0, 2, 5 or 7 of the block:
+// one on each of the four SM sub-partitions (warp index mod 4), not two on each of two.
 template <int LPL>
 __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restrict__ C,
                                                         const uint2* __restrict__ desc, int W,
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restric
     const int code = lines.code[slot];
     sgm_pair<LPL>(C, desc, W, Hh, D, P1, P2, code, pair - lines.start[slot],
                   Lvol + (size_t)code * vol_stride, Lvol + (size_t)(code + 1) * vol_stride,
-                  sgm_smem32 + wib * sgm_pair_words<LPL>(), gw & 1);
+                  sgm_smem32 + wib * sgm_pair_words<LPL>(), gw & 1, (pair >> 1) & 1);
 }
 
 // Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the
