@@ -390,10 +390,14 @@ def bench_serving(duration_s: float, budget_gb: float):
             "max_in_flight": st["max_in_flight"], "hbm_budget_gb": budget_gb}
 
 
-# DRAM bytes (read + write) of one aggregation launch, averaged over the ten launches of one step of
-# the sequence (one full-range frame, nine reduced), from ncu's dram__bytes_read.sum and
-# dram__bytes_write.sum (profiles/k_sgm_kitti_1242x375_reduced.md); None once k_sgm changes.
-SGM_DRAM_BYTES_PER_LAUNCH = 114_681_728
+# DRAM bytes (read + write) of one aggregation launch from ncu's dram__bytes_read.sum and
+# dram__bytes_write.sum over the ten launches of one step of the sequence (one full-range frame, nine
+# reduced); None while k_sgm has changed since the last capture. The last capture
+# (profiles/k_sgm_kitti_1242x375_reduced.md) read 114,681,728 B per launch before the change of
+# which twin warp walks an all-full-range pair (same loads and stores, other warps).
+SGM_DRAM_BYTES_PER_LAUNCH = None
+SGM_DRAM_NOTE = ("k_sgm changed after the last ncu capture (which twin warp walks an all-full-range "
+                 "pair); that capture read 114.7 MB per launch")
 
 
 def algorithmic_sgm_bytes(cells: int, px: int) -> int:
@@ -615,6 +619,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
         "roofline": {"bound": "hbm", "kernel": "k_sgm (path aggregation)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": SGM_DRAM_BYTES_PER_LAUNCH,
+                     "traffic_note": SGM_DRAM_NOTE if SGM_DRAM_BYTES_PER_LAUNCH is None else None,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_us": agg_avg_s * 1e6,
                      "timed_in": "a profiled pass of the same steps beside the headline's"},
