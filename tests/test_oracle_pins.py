@@ -590,6 +590,11 @@ def test_fill_gaps_hand_cases():
     assert Df2[1, 0] == 4.25
     assert Df2[1, 1] == -1                             # |4 - 9| >= gamma_f
     assert Df2[1, 2] == np.float32((np.float32(4) + np.float32(4.2)) * np.float32(0.5))
+    # similarity is strict (Eq. 8): neighbours exactly gamma_f apart do not fill the gap
+    E = np.array([[5, I, 6]], np.float32)
+    EP = np.where(E >= 0, 1.0, -1.0).astype(np.float32)
+    assert oracle.fill_gaps(E, EP, 1.0)[0][0, 1] == -1
+    assert oracle.fill_gaps(E, EP, 1.5)[0][0, 1] == 5.5
 
 
 def test_fill_gaps_horizontal_pass_comes_first():
@@ -634,6 +639,13 @@ def test_edge_reject_hand_cases():
     He, _ = oracle.edge_reject(H, HP, 1.0)
     assert He[1, 1] == -1 and He[2, 1] == -1         # 7 vs 40 (below): both rejected
     assert He[1, 2] == 30                            # invalid pixels are left as they are
+    # a valid pixel whose neighbours are all holes stays, and so does one whose only valid-looking
+    # neighbour, far away in disparity, has an invalid variance
+    O = np.array([[I, I, I], [I, 7, I], [I, I, I]], np.float32)
+    assert oracle.edge_reject(O, np.where(O >= 0, 1.0, -1.0).astype(np.float32), 1.0)[0][1, 1] == 7
+    V = np.array([[I, I, I], [I, 7, 30], [I, I, I]], np.float32)
+    VP = np.array([[I, I, I], [I, 1, I], [I, I, I]], np.float32)
+    assert oracle.edge_reject(V, VP, 1.0)[0][1, 1] == 7
     G = np.array([[I, I, I], [I, 7, I], [I, I, 90]], np.float32)
     Ge, _ = oracle.edge_reject(G, np.where(G >= 0, 1.0, -1.0).astype(np.float32), 1.0)
     assert Ge[1, 1] == -1 and Ge[2, 2] == -1         # diagonal neighbours: an edge
@@ -731,6 +743,15 @@ def test_sad_check_hand_cases():
     D4 = np.array([[I, I, 1.5, I, I]], np.float32)
     assert oracle.sad_check(L, R, D4, np.abs(D4), 3, 1, 6.6)[0][0, 2] == -1   # SAD 20 > 19.8
     assert oracle.sad_check(L, R, D4, np.abs(D4), 3, 1, 6.7)[0][0, 2] == 1.5  # 20 <= 20.1
+    # the limit scales with the patch area sw * sh: 3 x 5 patches of two constant images 2 apart
+    # have SAD 30, which a threshold of 2 (limit 30) keeps and one of 1.99 (limit 29.85) rejects
+    L5 = np.full((5, 5), 10, np.uint8)
+    R5 = np.full((5, 5), 12, np.uint8)
+    D5 = np.full((5, 5), I, np.float32)
+    D5[2, 2] = 0.0
+    P5 = np.abs(D5)
+    assert oracle.sad_check(L5, R5, D5, P5, 3, 5, 2.0)[0][2, 2] == 0.0
+    assert oracle.sad_check(L5, R5, D5, P5, 3, 5, 1.99)[0][2, 2] == -1
 
 
 def test_sad_check_shifted_texture():
