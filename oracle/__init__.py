@@ -19,12 +19,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# TSGM_ORACLE_SRC names a mutated copy of the arithmetic (tests/test_oracle_mutants.py), built
-# beside the copy and loaded in place of the oracle's own.
-_ALT_SRC = os.environ.get("TSGM_ORACLE_SRC")
-_SRC = _ALT_SRC or os.path.join(_HERE, "tsgm_oracle.cpp")
-_OUT = (os.path.join(os.path.dirname(os.path.abspath(_ALT_SRC)), "liboracle.so") if _ALT_SRC
-        else os.path.join(_HERE, "_build", "liboracle.so"))
+_SRC = os.path.join(_HERE, "tsgm_oracle.cpp")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 

@@ -1,11 +1,13 @@
 """Mutation check of the oracle's pins (CPU only).
 
-Each mutant plants one plausible mistake in a copy of the oracle's arithmetic: a dropped term, a
-wrong sign or index, a transposed operand, a threshold taken with the wrong comparison, a tie
-broken the other way, a rounding or clamping rule changed. The copy is built beside itself and
-`tests/test_oracle_pins.py` runs against it (the oracle loads the copy named by
-TSGM_ORACLE_SRC). Every mutant must fail at least one pin, and the unmodified copy must pass, so
-that a pin that stopped checking what it claims is noticed. No mutant writes outside its buffers.
+Each mutant plants one plausible mistake in a copy of the oracle package (its C++ arithmetic or
+its Python composition and binary64 adjoint references): a dropped term, a wrong sign or index, a
+transposed operand, a threshold taken with the wrong comparison, a tie broken the other way, a
+rounding or clamping rule changed, two stages run in the wrong order. The pins
+(`tests/test_oracle_pins.py`, `tests/test_oracle_adjoint.py`) run against the copy, which the
+test conftest imports in place of the oracle when TSGM_ORACLE_ROOT names its folder. Every mutant
+must fail at least one pin, and the unmodified copy must pass, so that a pin that stopped
+checking what it claims is noticed. No mutant writes outside its buffers.
 """
 import concurrent.futures as cf
 import os
@@ -14,11 +16,13 @@ import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "oracle", "tsgm_oracle.cpp")
+CPP = os.path.join(ROOT, "oracle", "tsgm_oracle.cpp")
+PY = os.path.join(ROOT, "oracle", "__init__.py")
 WORK = os.path.join(ROOT, "oracle", "_build", "mutants")
+PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_adjoint.py")]
 
-# (name, text of the oracle, replacement); each text occurs exactly once in the oracle
-MUTANTS = [
+# (name, text of tsgm_oracle.cpp, replacement); each text occurs exactly once in the file
+CPP_MUTANTS = [
     # Eq. 1-4: disparity-space homography
     ("H_t_sign", "{R[0], R[1], R[2], t[0]}", "{R[0], R[1], R[2], -t[0]}"),
     ("H_R_transposed", "{R[0], R[1], R[2], t[0]},\n                      {R[3], R[4], R[5], t[1]}",
@@ -91,32 +95,70 @@ MUTANTS = [
      "            D[i] = Dz[i];\n            P[i] = Pp[i];"),
 ]
 
+# (name, text of __init__.py, replacement): parameters, the per-frame composition (Sec. 2) and
+# the binary64 adjoint references
+PY_MUTANTS = [
+    ("Bc_counts_the_centre", "return self.census_w * self.census_h - 1", "return self.census_w * self.census_h"),
+    ("s_thr_not_per_path", "return float(np.float32(self.S_max) * np.float32(self.n_paths))",
+     "return float(np.float32(self.S_max))"),
+    ("K_cx_cy_swapped", "return float(K[0, 0]), float(K[0, 2]), float(K[1, 2])",
+     "return float(K[0, 0]), float(K[1, 2]), float(K[0, 2])"),
+    ("tracker_q_dropped", "np.float32(cx), np.float32(cy), prm.q)", "np.float32(cx), np.float32(cy), 0.0)"),
+    ("tracker_fill_before_edge",
+     "            if prm.edge_reject:\n                Dp, Pp = edge_reject(Dp, Pp, prm.edge_thr)\n"
+     "            if prm.fill_gaps:\n                Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)\n",
+     "            if prm.fill_gaps:\n                Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)\n"
+     "            if prm.edge_reject:\n                Dp, Pp = edge_reject(Dp, Pp, prm.edge_thr)\n"),
+    ("tracker_pred_lr_before_fill",
+     "            if prm.fill_gaps:\n                Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)\n"
+     "            if prm.pred_lr_check:\n                Dp, Pp = pred_lr_check(Dp, Pp, prm.pred_lr_tol)\n",
+     "            if prm.pred_lr_check:\n                Dp, Pp = pred_lr_check(Dp, Pp, prm.pred_lr_tol)\n"
+     "            if prm.fill_gaps:\n                Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)\n"),
+    ("tracker_sad_skipped", "            D, P = sad_check(left, right, D, P, prm.sad_w, prm.sad_h, prm.sad_thr)\n",
+     "            pass\n"),
+    ("rodrigues_sign", "return np.eye(3) + np.sin(th) * Kx + (1 - np.cos(th)) * (Kx @ Kx)",
+     "return np.eye(3) - np.sin(th) * Kx + (1 - np.cos(th)) * (Kx @ Kx)"),
+    ("adj_forward_phi_not_squared", "pp = (dp / d) ** 2 * p + q             # Eq. 5-6",
+     "pp = (dp / d) * p + q             # Eq. 5-6"),
+    ("adj_forward_gain_swapped", "Kg = Pp[both] / (Pp[both] + r[both])   # Eq. 10",
+     "Kg = r[both] / (Pp[both] + r[both])   # Eq. 10"),
+    ("adj_forward_measurement_only_unscaled", "D[mo], P[mo] = dz[mo], r[mo]", "D[mo], P[mo] = dz[mo], rr[mo]"),
+    ("adj_grad_dP_dpp", "dP_dpp = np.where(mv, (r / den) ** 2, 1.0)", "dP_dpp = np.where(mv, r / den, 1.0)"),
+    ("adj_grad_phi_chain", "dL_ddp = gd * dD_ddp + dL_dpp * 2 * p * dp / d ** 2",
+     "dL_ddp = gd * dD_ddp + dL_dpp * p * dp / d ** 2"),
+    ("adj_grad_t2_baseline", "g_t2 = np.sum(dL_dw3 * d / (f * b))", "g_t2 = np.sum(dL_dw3 * d / f)"),
+    ("adj_grad_measurement_only_dropped",
+     "g_sr += np.sum(gP.reshape(-1)[mo].astype(np.float64) * rall[mo])", "g_sr += 0.0"),
+]
 
-def _run_pins(name: str, text: str) -> tuple[str, int, str]:
-    d = os.path.join(WORK, name)
-    os.makedirs(d, exist_ok=True)
-    src = os.path.join(d, "tsgm_oracle.cpp")
-    with open(src, "w") as f:
-        f.write(text)
-    env = dict(os.environ, TSGM_ORACLE_SRC=src)
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        "-x", "-q", "-p", "no:cacheprovider"],
+
+def _run_pins(name: str, cpp: str, py: str) -> tuple[str, int, str]:
+    pkg = os.path.join(WORK, name, "oracle")
+    os.makedirs(pkg, exist_ok=True)
+    for fname, text in (("tsgm_oracle.cpp", cpp), ("__init__.py", py)):
+        with open(os.path.join(pkg, fname), "w") as f:
+            f.write(text)
+    env = dict(os.environ, TSGM_ORACLE_ROOT=os.path.dirname(pkg))
+    r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p", "no:cacheprovider"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     tail = (r.stdout.strip().splitlines() or [""])[-1]
     return name, r.returncode, tail
 
 
 def test_every_mutant_text_occurs_once():
-    orig = open(SRC).read()
-    names = [m[0] for m in MUTANTS]
+    names = [m[0] for m in CPP_MUTANTS + PY_MUTANTS]
     assert len(set(names)) == len(names)
-    for name, a, _ in MUTANTS:
-        assert orig.count(a) == 1, name
+    for path, mutants in ((CPP, CPP_MUTANTS), (PY, PY_MUTANTS)):
+        orig = open(path).read()
+        for name, a, _ in mutants:
+            assert orig.count(a) == 1, name
 
 
 def test_every_planted_mistake_fails_a_pin():
-    orig = open(SRC).read()
-    jobs = [("unmodified", orig)] + [(name, orig.replace(a, b, 1)) for name, a, b in MUTANTS]
+    cpp, py = open(CPP).read(), open(PY).read()
+    jobs = ([("unmodified", cpp, py)] +
+            [(name, cpp.replace(a, b, 1), py) for name, a, b in CPP_MUTANTS] +
+            [(name, cpp, py.replace(a, b, 1)) for name, a, b in PY_MUTANTS])
     workers = max(1, min(8, os.cpu_count() or 1))
     try:
         with cf.ThreadPoolExecutor(workers) as ex:

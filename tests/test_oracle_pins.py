@@ -273,6 +273,16 @@ def _popcount(v):
     return bin(int(v)).count("1")
 
 
+def test_border_cost_is_the_census_bit_count():
+    """B_c, the cost of a disparity that leaves the image, is the largest Hamming distance two
+    census codes can have: the bit count of a local maximum's code (every neighbour darker)."""
+    for cw, ch in ((3, 3), (5, 5), (9, 7)):
+        img = np.zeros((ch + 2, cw + 2), np.uint8)
+        img[ch // 2 + 1, cw // 2 + 1] = 200
+        code = oracle.census(img, cw, ch)[ch // 2 + 1, cw // 2 + 1]
+        assert oracle.Params(8, 8, census_w=cw, census_h=ch).Bc == _popcount(code)
+
+
 def test_cost_hamming_and_border():
     a, b = synth.random_images(12, 21, 6)
     D = 8
@@ -466,6 +476,20 @@ def test_select_argmin_bruteforce():
         assert d[y, x] == lo[y, x] + int(np.argmin(S[off[i]:off[i + 1]]))
 
 
+def test_matching_variance_threshold_is_per_path():
+    """Eq. 9's threshold S_max is read as per path: on the aggregated cost of n paths it is
+    n * S_max. On a 1 x 1 image every path is its own first pixel, so each path cost is the
+    matching cost and S = n C; the count must then equal Eq. 9 evaluated on C with S_max. Equal
+    left and right pixels give C = (0, B_c, B_c, ...) (a disparity > 0 leaves the image), so with
+    B_c = 24 < S_max = 30 < 2 B_c one neighbour of d* = 0 is counted."""
+    for n_paths in (4, 8):
+        prm = oracle.Params(1, 1, d_max=7, n_paths=n_paths, S_max=30.0, r_min=0.0)
+        tr = oracle.Tracker(prm)
+        img = np.array([[90]], np.uint8)
+        D, P = tr.frame(img, img, None, None, np.eye(3), 0.5)
+        assert D[0, 0] == 0.0 and P[0, 0] == 1.0
+
+
 # ----------------------------------------------------------------------------------------------
 # Left-right check (Sec. 2.4)
 # ----------------------------------------------------------------------------------------------
@@ -546,6 +570,21 @@ def test_kalman_limits_and_missing_sides():
 # ----------------------------------------------------------------------------------------------
 # Whole pipeline properties
 # ----------------------------------------------------------------------------------------------
+
+def test_tracker_prediction_adds_the_ego_motion_variance():
+    """With an identity pose the warp moves nothing and Phi = 1 (Eq. 5), so the tracker's raw
+    prediction of frame 2 is frame 1's map, with its variance raised by q (Eq. 6)."""
+    seq = synth.small_pair(1)
+    prm = oracle.Params(320, 96, q=0.75)
+    tr = oracle.Tracker(prm)
+    D1, P1 = tr.frame(seq.left[0], seq.right[0], seq.R[0], seq.t[0], seq.K, B)
+    o = tr.frame(seq.left[0], seq.right[0], np.eye(3), np.zeros(3), seq.K, B, keep=True)
+    v = (D1 > 0) & (P1 >= 0)
+    assert v.mean() > 0.5
+    assert np.array_equal(o["Dpred_raw"][v], D1[v])
+    assert np.array_equal(o["Ppred_raw"][v], (P1[v] + np.float32(0.75)).astype(np.float32))
+    assert np.all(o["Dpred_raw"][~v] == -1)
+
 
 def test_pipeline_small_pair_reduced_vs_full():
     """Frame 2 of the 320x96 pair: the reduced search considers a fraction of the cells and is at
