@@ -1430,10 +1430,10 @@ __device__ __forceinline__ void sgm_pair_dense(const uint8_t* __restrict__ C,
 // twin 0 and line B by twin 1: with the branch-free narrow walker when no window is wider than 32
 // labels; the general walker when more than one pixel in 8 has a window of 33 .. D - 1 labels;
 // the narrow walker when at most one pixel in 8 is wide and the wide ones are scattered (runs
-// shorter than 8 on average); else the mixed walker (narrow and full-range runs at full speed). twin < 0: this warp walks the
-// whole pair alone. dense_twin: which twin walks an all-full-range pair (the launch alternates it
-// so that the walking warps of a block fall on all four SM sub-partitions). The choice changes
-// the work, never the result.
+// shorter than 8 on average); else the mixed walker (narrow and full-range runs at full speed).
+// twin < 0: this warp walks the whole pair alone. dense_twin: which twin walks an
+// all-full-range pair (the launch alternates it so that the walking warps of a block fall on all
+// four SM sub-partitions). The choice changes the work, never the result.
 template <int LPL>
 __device__ __forceinline__ void sgm_pair(const uint8_t* __restrict__ C,
                                          const uint2* __restrict__ desc, int W, int Hh, int D,
