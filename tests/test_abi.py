@@ -106,3 +106,14 @@ def test_product_and_oracle_are_independent():
             assert "paper_1708_06301_gb300" not in _imports(os.path.join(od, f)), f
         if f.endswith((".cpp", ".h")):
             assert "tsgm.h" not in open(os.path.join(od, f)).read()
+
+
+def test_missing_library_fails_loudly(tsgm):
+    """No fallback: without the built CUDA library the binding raises and says how to build it."""
+    saved = tsgm._lib
+    tsgm._lib = None
+    try:
+        with pytest.raises(ImportError, match="build"):
+            tsgm.load(os.path.join(ROOT, "paper_1708_06301_gb300", "_build", "no_such_libtsgm.so"))
+    finally:
+        tsgm._lib = saved
