@@ -53,6 +53,28 @@ def _c(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+def _same_shape(shape, **arrays):
+    """The C functions trust the sizes they are given: every array a call reads or writes must
+    have the shape the call takes its sizes from, or it would be read past its end."""
+    for name, a in arrays.items():
+        if np.shape(a) != tuple(shape):
+            raise ValueError(f"{name} has shape {np.shape(a)}, expected {tuple(shape)}")
+
+
+def _ragged(lo, hi, off, **volumes):
+    """A ragged volume is indexed through off: it must be the exclusive scan of the window
+    lengths of lo, hi (inside [0, 2^15)), and every volume must hold off[n] cells."""
+    _same_shape(np.shape(lo), hi=hi)
+    if np.any(np.asarray(lo) < 0) or np.any(np.asarray(hi) < np.asarray(lo)):
+        raise ValueError("windows need 0 <= lo <= hi")
+    if not np.array_equal(np.asarray(off).reshape(-1), offsets(lo, hi)):
+        raise ValueError("off is not the exclusive scan of the window lengths")
+    cells = int(np.asarray(off).reshape(-1)[-1])
+    for name, a in volumes.items():
+        if np.size(a) != cells:
+            raise ValueError(f"{name} has {np.size(a)} cells, expected {cells}")
+
+
 # ----------------------------------------------------------------------------------------------
 # Parameters (defaults are the readings listed in the design notes)
 # ----------------------------------------------------------------------------------------------
@@ -103,7 +125,7 @@ class Params:
 def build_H(R, t, f: float, b: float):
     """Eq. 4 in binary64; returns (H64, H32) row-major 4x4."""
     lib = _load()
-    R64 = _c(np.asarray(R, dtype=np.float64).reshape(9), np.float64)
+    R64 = _c(np.asarray(R, dtype=np.float64).reshape(9), np.float64)   # reshape checks the sizes
     t64 = _c(np.asarray(t, dtype=np.float64).reshape(3), np.float64)
     H = np.zeros(16, dtype=np.float64)
     lib.oracle_build_H(_p(R64), _p(t64), ctypes.c_double(f), ctypes.c_double(b), _p(H))
@@ -113,6 +135,7 @@ def build_H(R, t, f: float, b: float):
 def warp_predict(Dprev, Pprev, H32, cx: float, cy: float, q: float):
     lib = _load()
     Hh, W = Dprev.shape
+    _same_shape((Hh, W), Pprev=Pprev)
     Dprev = _c(Dprev, np.float32)
     Pprev = _c(Pprev, np.float32)
     Hm = _c(H32, np.float32).reshape(16)
@@ -128,6 +151,7 @@ def fill_gaps(Dp, Pp, gamma_f: float):
     """Eq. 7-8: horizontal then vertical one-pixel gap filling of a prediction (copies)."""
     lib = _load()
     Hh, W = Dp.shape
+    _same_shape((Hh, W), Pp=Pp)
     D = np.array(Dp, dtype=np.float32, copy=True)
     P = np.array(Pp, dtype=np.float32, copy=True)
     lib.oracle_fill_gaps(W, Hh, ctypes.c_float(gamma_f), _p(D), _p(P))
@@ -139,6 +163,7 @@ def edge_reject(Dp, Pp, edge_thr: float):
     (8-neighbourhood, |d - d_n| >= edge_thr with a valid neighbour; copies)."""
     lib = _load()
     Hh, W = Dp.shape
+    _same_shape((Hh, W), Pp=Pp)
     D = np.array(Dp, dtype=np.float32, copy=True)
     P = np.array(Pp, dtype=np.float32, copy=True)
     lib.oracle_edge_reject(W, Hh, ctypes.c_float(edge_thr), _p(D), _p(P))
@@ -150,6 +175,7 @@ def pred_lr_check(Dp, Pp, tol: float):
     view's prediction formed from it (nearest surface per right pixel); copies."""
     lib = _load()
     Hh, W = Dp.shape
+    _same_shape((Hh, W), Pp=Pp)
     D = np.array(Dp, dtype=np.float32, copy=True)
     P = np.array(Pp, dtype=np.float32, copy=True)
     lib.oracle_pred_lr_check(W, Hh, ctypes.c_float(tol), _p(D), _p(P))
@@ -161,6 +187,7 @@ def sad_check(left, right, D, P, sw: int, sh: int, sad_thr: float):
     patch pixel; copies."""
     lib = _load()
     Hh, W = D.shape
+    _same_shape((Hh, W), P=P, left=left, right=right)
     D = np.array(D, dtype=np.float32, copy=True)
     P = np.array(P, dtype=np.float32, copy=True)
     lib.oracle_sad_check(W, Hh, int(sw), int(sh), ctypes.c_float(sad_thr),
@@ -171,6 +198,7 @@ def sad_check(left, right, D, P, sw: int, sh: int, sad_thr: float):
 def windows(Dp, Pp, D: int, sigma_mult: float):
     lib = _load()
     Hh, W = Dp.shape
+    _same_shape((Hh, W), Pp=Pp)
     Dp = _c(Dp, np.float32)
     Pp = _c(Pp, np.float32)
     lo = np.empty((Hh, W), np.int16)
@@ -202,6 +230,8 @@ def census(img, cw: int, ch: int):
 def cost(cl, cr, lo, hi, off, Bc: int):
     lib = _load()
     Hh, W = cl.shape
+    _same_shape((Hh, W), cr=cr, lo=lo)
+    _ragged(lo, hi, off)
     C = np.empty(int(off[-1]), np.uint8)
     lib.oracle_cost(W, Hh, Bc, _p(_c(cl, np.uint64)), _p(_c(cr, np.uint64)), _p(_c(lo, np.int16)),
                     _p(_c(hi, np.int16)), _p(_c(off, np.uint32)), _p(C))
@@ -211,6 +241,7 @@ def cost(cl, cr, lo, hi, off, Bc: int):
 def sgm_path(C, lo, hi, off, direction: int, P1: int, P2: int):
     lib = _load()
     Hh, W = lo.shape
+    _ragged(lo, hi, off, C=C)
     L = np.empty(int(off[-1]), np.uint16)
     lib.oracle_sgm_path(W, Hh, direction, P1, P2, _p(_c(C, np.uint8)), _p(_c(lo, np.int16)),
                         _p(_c(hi, np.int16)), _p(_c(off, np.uint32)), _p(L))
@@ -220,6 +251,7 @@ def sgm_path(C, lo, hi, off, direction: int, P1: int, P2: int):
 def sgm(C, lo, hi, off, n_paths: int, P1: int, P2: int):
     lib = _load()
     Hh, W = lo.shape
+    _ragged(lo, hi, off, C=C)
     S = np.empty(int(off[-1]), np.uint16)
     lib.oracle_sgm(W, Hh, n_paths, P1, P2, _p(_c(C, np.uint8)), _p(_c(lo, np.int16)),
                    _p(_c(hi, np.int16)), _p(_c(off, np.uint32)), _p(S))
@@ -229,6 +261,7 @@ def sgm(C, lo, hi, off, n_paths: int, P1: int, P2: int):
 def select(S, lo, hi, off, s_thr: float, r_min: float):
     lib = _load()
     Hh, W = lo.shape
+    _ragged(lo, hi, off, S=S)
     dstar = np.empty((Hh, W), np.int32)
     Dz = np.empty((Hh, W), np.float32)
     rz = np.empty((Hh, W), np.float32)
@@ -242,6 +275,8 @@ def lr_check(S, lo, hi, off, dstar, D: int, tol: int, Dz, rz):
     """Returns (dright, valid, Dz_masked, rz_masked); inputs Dz, rz are not modified."""
     lib = _load()
     Hh, W = lo.shape
+    _ragged(lo, hi, off, S=S)
+    _same_shape((Hh, W), dstar=dstar, Dz=Dz, rz=rz)
     dright = np.empty((Hh, W), np.int32)
     valid = np.empty((Hh, W), np.uint8)
     Dz = np.array(Dz, dtype=np.float32, copy=True)
@@ -255,6 +290,7 @@ def lr_check(S, lo, hi, off, dstar, D: int, tol: int, Dz, rz):
 def kalman(Dp, Pp, Dz, rz):
     lib = _load()
     shape = np.shape(Dp)
+    _same_shape(shape, Pp=Pp, Dz=Dz, rz=rz)
     n = int(np.prod(shape))
     D = np.empty(shape, np.float32)
     P = np.empty(shape, np.float32)

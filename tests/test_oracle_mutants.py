@@ -93,6 +93,24 @@ CPP_MUTANTS = [
     ("kalman_variance_K", "const float omk = 1.0f - K;", "const float omk = K;"),
     ("kalman_measurement_only_keeps_p", "            D[i] = Dz[i];\n            P[i] = rz[i];",
      "            D[i] = Dz[i];\n            P[i] = Pp[i];"),
+    # window edges and validity tests (each off by one label, one pixel or one condition)
+    ("valid_accepts_inf", "return v >= 0.0f && v <= FLT_MAX;", "return v >= 0.0f;"),
+    ("warp_drops_last_column", "fx <= (float)(W - 1)", "fx < (float)(W - 1)"),
+    ("predlr_drops_column_0", "return rf > (float)x ? -1 : x - (int)rf;", "return rf >= (float)x ? -1 : x - (int)rf;"),
+    ("window_top_label_is_a_miss", "if (lo_f <= (float)(D - 1) && hi_f >= 0.0f) {",
+     "if (lo_f < (float)(D - 1) && hi_f >= 0.0f) {"),
+    ("census_left_clamp_to_1", "int qx = std::min(std::max(x + dx, 0), W - 1);",
+     "int qx = std::min(std::max(x + dx, 1), W - 1);"),
+    ("sgm_m_misses_top_label", "for (int k = lo[j]; k <= hi[j]; ++k) m = std::min(m, (int)L[off[j] + (k - lo[j])]);",
+     "for (int k = lo[j]; k < hi[j]; ++k) m = std::min(m, (int)L[off[j] + (k - lo[j])]);"),
+    ("sgm_upper_neighbour_at_edge", "if (d + 1 >= lo[j] && d + 1 <= hi[j]) best",
+     "if (d + 1 >= lo[j] && d + 1 < hi[j]) best"),
+    ("subpixel_needs_two_above", "if (best - 1 >= a && best + 1 <= b) {", "if (best - 1 >= a && best + 1 < b) {"),
+    ("lr_window_top_excluded", "if (d < lo[i] || d > hi[i]) continue;", "if (d < lo[i] || d >= hi[i]) continue;"),
+    ("kalman_measurement_ignores_r", "const bool mv = finite_nonneg(Dz[i]) && finite_nonneg(rz[i]);",
+     "const bool mv = finite_nonneg(Dz[i]);"),
+    ("kalman_prediction_ignores_p", "const bool pv = finite_nonneg(Dp[i]) && finite_nonneg(Pp[i]);",
+     "const bool pv = finite_nonneg(Dp[i]);"),
 ]
 
 # (name, text of __init__.py, replacement): parameters, the per-frame composition (Sec. 2) and
@@ -141,8 +159,9 @@ def _run_pins(name: str, cpp: str, py: str) -> tuple[str, int, str]:
     env = dict(os.environ, TSGM_ORACLE_ROOT=os.path.dirname(pkg))
     r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p", "no:cacheprovider"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
-    tail = (r.stdout.strip().splitlines() or [""])[-1]
-    return name, r.returncode, tail
+    lines = r.stdout.strip().splitlines() or [""]
+    failed = [ln for ln in lines if ln.startswith(("FAILED", "ERROR"))]
+    return name, r.returncode, "; ".join(failed[:1] + lines[-1:])
 
 
 def test_every_mutant_text_occurs_once():

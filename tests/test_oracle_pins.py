@@ -137,6 +137,30 @@ def test_warp_forward_motion_fronto_parallel_wall():
     assert np.all(np.abs(y_land - tv) <= 0.5 + 1e-4)
 
 
+def test_wrappers_reject_inputs_that_do_not_match_their_sizes():
+    """The C functions trust the sizes they are given; the wrappers refuse a map of another shape
+    (it would be read past its end) and a ragged layout that is not the scan of its windows."""
+    D = np.ones((4, 6), np.float32)
+    H = np.eye(4, dtype=np.float32)
+    with pytest.raises(ValueError):
+        oracle.warp_predict(D, np.ones((4, 1), np.float32), H, 2.5, 1.5, 0.0)
+    with pytest.raises(ValueError):
+        oracle.kalman(D, D, D, D[:, :5])
+    with pytest.raises(ValueError):
+        oracle.fill_gaps(D, D.T, 1.0)
+    lo = np.zeros((4, 6), np.int16)
+    hi = np.full((4, 6), 3, np.int16)
+    off = oracle.offsets(lo, hi)
+    with pytest.raises(ValueError):
+        oracle.sgm(np.zeros(int(off[-1]) - 1, np.uint8), lo, hi, off, 4, 8, 32)
+    bad = off.copy()
+    bad[3] += 1
+    with pytest.raises(ValueError):
+        oracle.sgm(np.zeros(int(off[-1]), np.uint8), lo, hi, bad, 4, 8, 32)
+    with pytest.raises(ValueError):
+        oracle.sgm(np.zeros(int(off[-1]), np.uint8), hi, lo, off, 4, 8, 32)
+
+
 def test_warp_zbuffer_tie_goes_to_lowest_source():
     """Moving backwards from a fronto-parallel wall shrinks the image: several sources with the
     same predicted disparity land on one target; the lowest source index must win. Landing
@@ -174,7 +198,7 @@ def test_warp_ground_plane_against_renderer():
     _, Z1 = synth.render(scene, cam, np.eye(3), np.array([0, 0, s]))
     D0 = (F * B / Z0).astype(np.float32)
     D1 = (F * B / Z1).astype(np.float32)
-    ground = np.arange(H)[:, None] > cam.cy + 2
+    ground = np.broadcast_to(np.arange(H)[:, None] > cam.cy + 2, (H, W))
     D0 = np.where(ground, D0, -1.0).astype(np.float32)
     P0 = np.where(ground, 1.0, -1.0).astype(np.float32)
     _, H32 = oracle.build_H(np.eye(3), np.array([0, 0, -s]), F, B)
@@ -207,6 +231,9 @@ def test_warp_ground_plane_against_renderer():
     (10.0, float("inf"), 64, (0, 63)),
     (100.0, 1.0, 64, (0, 63)),       # interval entirely above the range: whole range
     (0.0, 0.01, 64, (0, 1)),
+    (63.0, 0.0, 64, (63, 63)),       # the top label alone is inside the range
+    (0.0, 0.0, 64, (0, 0)),          # the bottom label alone
+    (64.0, 0.0, 64, (0, 63)),        # one label above the range: a miss, whole range
 ])
 def test_window_hand_cases(d, p, D, exp):
     lo, hi, off, n = oracle.windows(np.array([[d]], np.float32), np.array([[p]], np.float32), D, 3.0)
@@ -446,6 +473,10 @@ def test_select_parabola_vertex_exact():
     assert _select_one(s[5:12], lo=5)[:2] == (7, 7.25)
     # minimum on the window edge: no sub-pixel step
     assert _select_one([4, 9, 12], lo=3)[:2] == (3, 3.0)
+    # minimum one label inside either edge: both neighbours exist, the parabola applies
+    # (delta = (4 - 3) / (2 (4 - 2 + 3)) = 0.1 and its mirror image)
+    assert _select_one([4, 1, 3])[:2] == (1, float(np.float32(1) + np.float32(1) / np.float32(10)))
+    assert _select_one([3, 1, 4])[:2] == (1, float(np.float32(1) + np.float32(-1) / np.float32(10)))
 
 
 def test_select_matching_variance_hand_cases():
@@ -565,6 +596,17 @@ def test_kalman_limits_and_missing_sides():
     assert D[3] == 12 and P[3] == 3          # no prediction: take the measurement
     assert D[4] == 11 and P[4] == 1          # equal variances: midpoint, half variance
     assert D[5] == -1 and P[5] == -1
+    # validity needs both the value and its variance: a prediction with an invalid or infinite
+    # variance is no prediction (the p -> inf limit takes the measurement and its variance),
+    # a measurement with an invalid variance is no measurement
+    dp = np.array([10, 10, 10], np.float32)
+    pp = np.array([np.inf, -1, 1], np.float32)
+    dz = np.array([12, 12, 12], np.float32)
+    rz = np.array([2, 2, -1], np.float32)
+    D, P = oracle.kalman(dp, pp, dz, rz)
+    assert D[0] == 12 and P[0] == 2
+    assert D[1] == 12 and P[1] == 2
+    assert D[2] == 10 and P[2] == 1
 
 
 # ----------------------------------------------------------------------------------------------
