@@ -2,8 +2,10 @@
 
 Every step of the path runs in the CUDA library `_build/libtsgm.so`; this module loads it with
 ctypes and passes device pointers (torch tensors' `data_ptr()` or plain integers), host arrays
-for poses and calibration, and the current torch CUDA stream. There is no fallback: if the
-library is missing, loading fails with an error that says how to build it.
+for poses and calibration, and the current torch CUDA stream. The kernels trust the sizes a
+context was created with, so every tensor or host array is checked against them (element count
+and element size) before the call; raw integer pointers are passed on unchecked. There is no
+fallback: if the library is missing, loading fails with an error that says how to build it.
 """
 from __future__ import annotations
 
@@ -168,6 +170,47 @@ def _ptr(x) -> int:
     raise TypeError(f"cannot take a device pointer of {type(x)}")
 
 
+def _dptr(x, n: int, esize: int, what: str) -> int:
+    """Device pointer of a buffer that a call reads or writes as n elements of esize bytes. The
+    kernels trust the sizes the context was created with, so a CUDA tensor must be at least that
+    large, with elements of that size. A raw integer pointer, or None where the call allows it,
+    is passed on unchecked."""
+    p = _ptr(x)
+    if hasattr(x, "numel") and hasattr(x, "element_size"):
+        if x.element_size() != esize:
+            raise ValueError(f"{what}: expected elements of {esize} bytes, got {x.element_size()}")
+        if x.numel() < n:
+            raise ValueError(f"{what}: expected at least {n} elements, got {x.numel()}")
+    return p
+
+
+def _hptr(a, n: int, esize: int, what: str) -> int:
+    """Address of a host buffer (a numpy array or a CPU tensor, pinned for the asynchronous
+    calls) of at least n contiguous elements of esize bytes."""
+    if hasattr(a, "data_ptr"):
+        if getattr(a, "is_cuda", False):
+            raise ValueError(f"{what}: expected a host buffer, got a CUDA tensor")
+        if not a.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous tensor")
+        size, item, ptr = a.numel(), a.element_size(), a.data_ptr()
+    elif isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{what}: expected a contiguous array")
+        size, item, ptr = a.size, a.itemsize, a.ctypes.data
+    else:
+        raise TypeError(f"{what}: cannot take a host address of {type(a)}")
+    if item != esize:
+        raise ValueError(f"{what}: expected elements of {esize} bytes, got {item}")
+    if size < n:
+        raise ValueError(f"{what}: expected at least {n} elements, got {size}")
+    return ptr
+
+
+# element bytes of the internal buffers that tsgm_inspect copies out
+_BUF_BYTES = dict(census_l=8, census_r=8, offsets=4, cost=1, S=2, dstar=2, dright=2, lr_valid=1,
+                  zkeys=8, windows_lo=2, windows_hi=2, pred_d=4, pred_p=4, counts=4)
+
+
 def _host_f32(a, n: int):
     if a is None:
         return None, None
@@ -246,59 +289,69 @@ class Context:
         Ra, Rp = _host_f32(R, 9)
         ta, tp = _host_f32(t, 3)
         Ka, Kp = _host_f32(K, 9)
-        self._check(self.lib.tsgm_warp_predict(self.h, _ptr(prev_D), _ptr(prev_P), Rp, tp, Kp,
-                                               ctypes.c_float(baseline), _ptr(pred_D),
-                                               _ptr(pred_P)), "tsgm_warp_predict")
+        n = self.n
+        self._check(self.lib.tsgm_warp_predict(self.h, _dptr(prev_D, n, 4, "prev_D"),
+                                               _dptr(prev_P, n, 4, "prev_P"), Rp, tp, Kp,
+                                               ctypes.c_float(baseline), _dptr(pred_D, n, 4, "pred_D"),
+                                               _dptr(pred_P, n, 4, "pred_P")), "tsgm_warp_predict")
 
     def windows(self, pred_D, pred_P, d_lo, d_hi, want_cells: bool = False):
         cells = ctypes.c_uint64(0)
-        self._check(self.lib.tsgm_windows(self.h, _ptr(pred_D), _ptr(pred_P), _ptr(d_lo), _ptr(d_hi),
+        n = self.n
+        self._check(self.lib.tsgm_windows(self.h, _dptr(pred_D, n, 4, "pred_D"),
+                                          _dptr(pred_P, n, 4, "pred_P"), _dptr(d_lo, n, 2, "d_lo"),
+                                          _dptr(d_hi, n, 2, "d_hi"),
                                           ctypes.byref(cells) if want_cells else None),
                     "tsgm_windows")
         return int(cells.value) if want_cells else None
 
     def match(self, left, right, d_lo, d_hi, D_z, r_z):
-        self._check(self.lib.tsgm_match(self.h, _ptr(left), _ptr(right), _ptr(d_lo), _ptr(d_hi),
-                                        _ptr(D_z), _ptr(r_z)), "tsgm_match")
+        n = self.n
+        self._check(self.lib.tsgm_match(self.h, _dptr(left, n, 1, "left"), _dptr(right, n, 1, "right"),
+                                        _dptr(d_lo, n, 2, "d_lo"), _dptr(d_hi, n, 2, "d_hi"),
+                                        _dptr(D_z, n, 4, "D_z"), _dptr(r_z, n, 4, "r_z")),
+                    "tsgm_match")
 
     def kalman_update(self, pred_D, pred_P, D_z, r_z, D, P):
-        self._check(self.lib.tsgm_kalman_update(self.h, _ptr(pred_D), _ptr(pred_P), _ptr(D_z),
-                                                _ptr(r_z), _ptr(D), _ptr(P)), "tsgm_kalman_update")
+        n = self.n
+        self._check(self.lib.tsgm_kalman_update(self.h, _dptr(pred_D, n, 4, "pred_D"),
+                                                _dptr(pred_P, n, 4, "pred_P"), _dptr(D_z, n, 4, "D_z"),
+                                                _dptr(r_z, n, 4, "r_z"), _dptr(D, n, 4, "D"),
+                                                _dptr(P, n, 4, "P")), "tsgm_kalman_update")
 
     def frame(self, left, right, R, t, K, baseline, D, P):
         Ra, Rp = _host_f32(R, 9)
         ta, tp = _host_f32(t, 3)
         Ka, Kp = _host_f32(K, 9)
-        self._check(self.lib.tsgm_frame(self.h, _ptr(left), _ptr(right), Rp, tp, Kp,
-                                        ctypes.c_float(baseline), _ptr(D), _ptr(P)), "tsgm_frame")
+        n = self.n
+        self._check(self.lib.tsgm_frame(self.h, _dptr(left, n, 1, "left"), _dptr(right, n, 1, "right"),
+                                        Rp, tp, Kp, ctypes.c_float(baseline), _dptr(D, n, 4, "D"),
+                                        _dptr(P, n, 4, "P")), "tsgm_frame")
 
     def frame_host(self, left: np.ndarray, right: np.ndarray, R, t, K, baseline, D: np.ndarray,
                    P: np.ndarray):
         """Host buffers (numpy or pinned torch CPU tensors) in and out; synchronises."""
-        def hp(a):
-            if hasattr(a, "data_ptr"):
-                return a.data_ptr()
-            return a.ctypes.data
         Ra, Rp = _host_f32(R, 9)
         ta, tp = _host_f32(t, 3)
         Ka, Kp = _host_f32(K, 9)
-        self._check(self.lib.tsgm_frame_host(self.h, hp(left), hp(right), Rp, tp, Kp,
-                                             ctypes.c_float(baseline), hp(D), hp(P)),
+        n = self.n
+        self._check(self.lib.tsgm_frame_host(self.h, _hptr(left, n, 1, "left"), _hptr(right, n, 1, "right"),
+                                             Rp, tp, Kp, ctypes.c_float(baseline),
+                                             _hptr(D, n, 4, "D"), _hptr(P, n, 4, "P")),
                     "tsgm_frame_host")
 
     def frame_host_async(self, left, right, R, t, K, baseline, D, P):
         """Pinned host buffers in and out; returns at once (see tsgm_frame_host_async). The image
         and map buffers must stay alive and untouched until wait(); R, t, K are read during the
         call."""
-        def hp(a):
-            if hasattr(a, "data_ptr"):
-                return a.data_ptr()
-            return a.ctypes.data
         Ra, Rp = _host_f32(R, 9)
         ta, tp = _host_f32(t, 3)
         Ka, Kp = _host_f32(K, 9)
-        self._check(self.lib.tsgm_frame_host_async(self.h, hp(left), hp(right), Rp, tp, Kp,
-                                                   ctypes.c_float(baseline), hp(D), hp(P)),
+        n = self.n
+        self._check(self.lib.tsgm_frame_host_async(self.h, _hptr(left, n, 1, "left"),
+                                                   _hptr(right, n, 1, "right"), Rp, tp, Kp,
+                                                   ctypes.c_float(baseline), _hptr(D, n, 4, "D"),
+                                                   _hptr(P, n, 4, "P")),
                     "tsgm_frame_host_async")
 
     def wait(self):
@@ -318,28 +371,39 @@ class Context:
     def state_import(self, D, P, has_prev: bool = True):
         D = np.ascontiguousarray(D, np.float32)
         P = np.ascontiguousarray(P, np.float32)
-        self._check(self.lib.tsgm_state_import(self.h, D.ctypes.data, P.ctypes.data, int(has_prev)),
+        self._check(self.lib.tsgm_state_import(self.h, _hptr(D, self.n, 4, "D"),
+                                               _hptr(P, self.n, 4, "P"), int(has_prev)),
                     "tsgm_state_import")
 
     def fill_gaps(self, pred_D, pred_P):
-        self._check(self.lib.tsgm_fill_gaps(self.h, _ptr(pred_D), _ptr(pred_P)), "tsgm_fill_gaps")
+        self._check(self.lib.tsgm_fill_gaps(self.h, _dptr(pred_D, self.n, 4, "pred_D"),
+                                            _dptr(pred_P, self.n, 4, "pred_P")), "tsgm_fill_gaps")
 
     def edge_reject(self, pred_D, pred_P):
-        self._check(self.lib.tsgm_edge_reject(self.h, _ptr(pred_D), _ptr(pred_P)),
+        self._check(self.lib.tsgm_edge_reject(self.h, _dptr(pred_D, self.n, 4, "pred_D"),
+                                              _dptr(pred_P, self.n, 4, "pred_P")),
                     "tsgm_edge_reject")
 
     def pred_lr_check(self, pred_D, pred_P):
-        self._check(self.lib.tsgm_pred_lr_check(self.h, _ptr(pred_D), _ptr(pred_P)),
+        self._check(self.lib.tsgm_pred_lr_check(self.h, _dptr(pred_D, self.n, 4, "pred_D"),
+                                                _dptr(pred_P, self.n, 4, "pred_P")),
                     "tsgm_pred_lr_check")
 
     def sad_check(self, left, right, D, P):
-        self._check(self.lib.tsgm_sad_check(self.h, _ptr(left), _ptr(right), _ptr(D), _ptr(P)),
+        n = self.n
+        self._check(self.lib.tsgm_sad_check(self.h, _dptr(left, n, 1, "left"), _dptr(right, n, 1, "right"),
+                                            _dptr(D, n, 4, "D"), _dptr(P, n, 4, "P")),
                     "tsgm_sad_check")
 
     def census(self, img, codes):
-        self._check(self.lib.tsgm_census(self.h, _ptr(img), _ptr(codes)), "tsgm_census")
+        self._check(self.lib.tsgm_census(self.h, _dptr(img, self.n, 1, "img"),
+                                         _dptr(codes, self.n, 8, "codes")), "tsgm_census")
 
     def inspect(self, which: str, dst, count: int):
+        need = int(count) * _BUF_BYTES[which]
+        if hasattr(dst, "numel") and dst.numel() * dst.element_size() < need:
+            raise ValueError(f"inspect {which}: dst holds {dst.numel() * dst.element_size()} bytes, "
+                             f"{need} needed")
         self._check(self.lib.tsgm_inspect(self.h, BUF[which], _ptr(dst), int(count)), "tsgm_inspect")
 
     def cells(self) -> int:
@@ -350,20 +414,26 @@ class Context:
     def adjoint_forward(self, prev_D, prev_P, pose6, K, baseline, q, r_scale, D_z, r_z, D, P):
         p6 = (ctypes.c_double * 6)(*[float(v) for v in np.asarray(pose6, np.float64).reshape(6)])
         Ka, Kp = _host_f32(K, 9)
-        self._check(self.lib.tsgm_adjoint_forward(self.h, _ptr(prev_D), _ptr(prev_P), p6, Kp,
+        n = self.n
+        self._check(self.lib.tsgm_adjoint_forward(self.h, _dptr(prev_D, n, 4, "prev_D"),
+                                                  _dptr(prev_P, n, 4, "prev_P"), p6, Kp,
                                                   ctypes.c_float(baseline), ctypes.c_float(q),
-                                                  ctypes.c_float(r_scale), _ptr(D_z), _ptr(r_z),
-                                                  _ptr(D), _ptr(P)), "tsgm_adjoint_forward")
+                                                  ctypes.c_float(r_scale), _dptr(D_z, n, 4, "D_z"),
+                                                  _dptr(r_z, n, 4, "r_z"), _dptr(D, n, 4, "D"),
+                                                  _dptr(P, n, 4, "P")), "tsgm_adjoint_forward")
 
     def adjoint_backward(self, prev_D, prev_P, pose6, K, baseline, q, r_scale, D_z, r_z, grad_D,
                          grad_P) -> np.ndarray:
         p6 = (ctypes.c_double * 6)(*[float(v) for v in np.asarray(pose6, np.float64).reshape(6)])
         Ka, Kp = _host_f32(K, 9)
         g = (ctypes.c_double * 8)()
-        self._check(self.lib.tsgm_adjoint_backward(self.h, _ptr(prev_D), _ptr(prev_P), p6, Kp,
+        n = self.n
+        self._check(self.lib.tsgm_adjoint_backward(self.h, _dptr(prev_D, n, 4, "prev_D"),
+                                                   _dptr(prev_P, n, 4, "prev_P"), p6, Kp,
                                                    ctypes.c_float(baseline), ctypes.c_float(q),
-                                                   ctypes.c_float(r_scale), _ptr(D_z), _ptr(r_z),
-                                                   _ptr(grad_D), _ptr(grad_P), g),
+                                                   ctypes.c_float(r_scale), _dptr(D_z, n, 4, "D_z"),
+                                                   _dptr(r_z, n, 4, "r_z"), _dptr(grad_D, n, 4, "grad_D"),
+                                                   _dptr(grad_P, n, 4, "grad_P"), g),
                     "tsgm_adjoint_backward")
         return np.array(list(g), dtype=np.float64)
 
@@ -402,21 +472,28 @@ class Batch:
             msg = self.lib.tsgm_batch_last_error(self.h)
             raise TsgmError(st, f"{what}: {msg.decode() if msg else ''}")
 
-    @staticmethod
-    def _arr(xs):
-        return (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+    def _arr(self, xs, esize: int, what: str):
+        """Per-stream device pointers, each buffer checked against its stream's image size."""
+        xs = list(xs)
+        if len(xs) != self.n:
+            raise ValueError(f"{what}: expected {self.n} buffers, got {len(xs)}")
+        ptrs = [_dptr(x, int(p.width) * int(p.height), esize, f"{what}[{i}]")
+                for i, (x, p) in enumerate(zip(xs, self.params))]
+        return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+    def _arrs(self, lefts, rights, los, his, Dzs, rzs):
+        return (self._arr(lefts, 1, "lefts"), self._arr(rights, 1, "rights"), self._arr(los, 2, "los"),
+                self._arr(his, 2, "his"), self._arr(Dzs, 4, "Dzs"), self._arr(rzs, 4, "rzs"))
 
     def match(self, lefts, rights, los, his, Dzs, rzs):
-        self._check(self.lib.tsgm_batch_match(self.h, self._arr(lefts), self._arr(rights),
-                                              self._arr(los), self._arr(his), self._arr(Dzs),
-                                              self._arr(rzs)), "tsgm_batch_match")
+        self._check(self.lib.tsgm_batch_match(self.h, *self._arrs(lefts, rights, los, his, Dzs, rzs)),
+                    "tsgm_batch_match")
 
     def autotune(self, lefts, rights, los, his, Dzs, rzs, reps: int = 3):
         ms = ctypes.c_double(0)
         shape = ctypes.c_int32(0)
-        self._check(self.lib.tsgm_batch_autotune(self.h, self._arr(lefts), self._arr(rights),
-                                                 self._arr(los), self._arr(his), self._arr(Dzs),
-                                                 self._arr(rzs), int(reps), ctypes.byref(ms),
+        self._check(self.lib.tsgm_batch_autotune(self.h, *self._arrs(lefts, rights, los, his, Dzs, rzs),
+                                                 int(reps), ctypes.byref(ms),
                                                  ctypes.byref(shape)), "tsgm_batch_autotune")
         return float(ms.value), int(shape.value)
 
@@ -435,9 +512,8 @@ class Batch:
     def profile(self, lefts, rights, los, his, Dzs, rzs):
         """(aggregation ms, whole step ms) of one step with direct launches."""
         a, z = ctypes.c_float(0), ctypes.c_float(0)
-        self._check(self.lib.tsgm_batch_profile(self.h, self._arr(lefts), self._arr(rights),
-                                                self._arr(los), self._arr(his), self._arr(Dzs),
-                                                self._arr(rzs), ctypes.byref(a), ctypes.byref(z)),
+        self._check(self.lib.tsgm_batch_profile(self.h, *self._arrs(lefts, rights, los, his, Dzs, rzs),
+                                                ctypes.byref(a), ctypes.byref(z)),
                     "tsgm_batch_profile")
         return float(a.value), float(z.value)
 
@@ -482,9 +558,13 @@ class Server:
         ta, tp = _host_f32(t, 3)
         Ka, Kp = _host_f32(K, 9)
         tk = ctypes.c_uint64(0)
-        st = self.lib.tsgm_server_submit(self.h, int(stream), left.ctypes.data, right.ctypes.data,
-                                         Rp, tp, Kp, ctypes.c_float(baseline), D_out.ctypes.data,
-                                         P_out.ctypes.data, ctypes.byref(tk))
+        if not 0 <= int(stream) < len(self.params):
+            raise ValueError(f"stream {stream} out of range")
+        n = int(self.params[int(stream)].width) * int(self.params[int(stream)].height)
+        st = self.lib.tsgm_server_submit(self.h, int(stream), _hptr(left, n, 1, "left"),
+                                         _hptr(right, n, 1, "right"), Rp, tp, Kp,
+                                         ctypes.c_float(baseline), _hptr(D_out, n, 4, "D_out"),
+                                         _hptr(P_out, n, 4, "P_out"), ctypes.byref(tk))
         if st != OK:
             raise TsgmError(st, "tsgm_server_submit failed")
         self._keep[int(tk.value)] = (D_out, P_out)

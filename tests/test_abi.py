@@ -117,3 +117,67 @@ def test_missing_library_fails_loudly(tsgm):
             tsgm.load(os.path.join(ROOT, "paper_1708_06301_gb300", "_build", "no_such_libtsgm.so"))
     finally:
         tsgm._lib = saved
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor on a machine without a GPU: only what the binding reads."""
+
+    is_cuda = True
+
+    def __init__(self, numel, esize, contiguous=True):
+        self._n, self._e, self._c = numel, esize, contiguous
+
+    def numel(self):
+        return self._n
+
+    def element_size(self):
+        return self._e
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        return 0x7F0000000000
+
+
+def test_binding_checks_device_buffer_sizes(tsgm):
+    """Kernels trust the context's sizes: the binding refuses a device buffer that is smaller than
+    the call needs or has another element size, before anything reaches the GPU."""
+    assert tsgm._dptr(_FakeCudaTensor(12, 4), 12, 4, "D") == 0x7F0000000000
+    assert tsgm._dptr(_FakeCudaTensor(20, 4), 12, 4, "D") == 0x7F0000000000
+    assert tsgm._dptr(None, 12, 4, "D") == 0
+    assert tsgm._dptr(1234, 12, 4, "D") == 1234          # a raw pointer: the caller vouches
+    with pytest.raises(ValueError, match="at least 12"):
+        tsgm._dptr(_FakeCudaTensor(11, 4), 12, 4, "D")
+    with pytest.raises(ValueError, match="4 bytes"):
+        tsgm._dptr(_FakeCudaTensor(12, 8), 12, 4, "D")
+    with pytest.raises(ValueError, match="contiguous"):
+        tsgm._dptr(_FakeCudaTensor(12, 4, contiguous=False), 12, 4, "D")
+
+
+def test_binding_checks_host_buffer_sizes(tsgm):
+    a = np.zeros((3, 4), np.float32)
+    assert tsgm._hptr(a, 12, 4, "D") == a.ctypes.data
+    with pytest.raises(ValueError, match="at least 13"):
+        tsgm._hptr(a, 13, 4, "D")
+    with pytest.raises(ValueError, match="4 bytes"):
+        tsgm._hptr(a.astype(np.float64), 12, 4, "D")
+    with pytest.raises(ValueError, match="contiguous"):
+        tsgm._hptr(np.zeros((4, 6), np.float32)[:, ::2], 12, 4, "D")
+    with pytest.raises(ValueError, match="host buffer"):
+        tsgm._hptr(_FakeCudaTensor(12, 4), 12, 4, "D")
+    import torch
+    t = torch.zeros((3, 4), dtype=torch.float32)
+    assert tsgm._hptr(t, 12, 4, "D") == t.data_ptr()
+
+
+def test_batch_checks_each_stream_against_its_size(tsgm):
+    b = object.__new__(tsgm.Batch)
+    b.params = [tsgm.default_params(8, 4), tsgm.default_params(16, 2)]
+    b.n = 2
+    imgs = [_FakeCudaTensor(32, 1), _FakeCudaTensor(32, 1)]
+    assert len(b._arr(imgs, 1, "lefts")) == 2
+    with pytest.raises(ValueError, match=r"lefts\[1\]"):
+        b._arr([_FakeCudaTensor(32, 1), _FakeCudaTensor(31, 1)], 1, "lefts")
+    with pytest.raises(ValueError, match="expected 2 buffers"):
+        b._arr(imgs[:1], 1, "lefts")
