@@ -21,7 +21,8 @@
 //   * a window is [lo, hi] (inclusive, int16) inside [0, D-1]; the ragged volume stores the
 //     cells of pixel i at off[i] .. off[i+1]-1, cell j <-> disparity lo[i] + j.
 //
-// Parity status: every function below is pinned by a `-m "not gpu"` test (tests/test_oracle_pins.py).
+// Parity status: every function below is pinned by a `-m "not gpu"` test (tests/test_oracle_pins.py),
+// and tests/test_oracle_mutants.py checks that a planted mistake in any of them fails a pin.
 
 #include <cmath>
 #include <cstdint>
