@@ -379,14 +379,17 @@ tsgm_status tsgm_server_stats(tsgm_server* s, double* p50_ms, double* p99_ms, ui
  * held by every GPU that loads the library until the process exits. It calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *   prev_D, prev_P, pred_D, pred_P: device maps of width*height floats, as in tsgm_warp_predict;
- *   q: variance added by the prediction (Eq. 5); cuda_stream: stream to enqueue on (NULL: the
- *   legacy default stream); errbuf: optional buffer of errbuf_len bytes for a message.
- * Returns INVALID_ARG (nothing launched) for null pointers, a bad pose or calibration, or
- * width * height > TSGM_NOALLOC_MAX_PIXELS; CUDA if a launch fails.
+ *   q: variance added to every predicted pixel, finite and >= 0; cuda_stream: stream to enqueue
+ *   on (NULL: the legacy default stream); errbuf: optional buffer of errbuf_len bytes for a
+ *   message.
+ * Returns INVALID_ARG (nothing launched) for null pointers, outputs that alias inputs, a q that
+ * is negative, infinite or NaN, a bad pose or calibration, or width * height >
+ * TSGM_NOALLOC_MAX_PIXELS; CUDA if a launch fails.
  * The first call on a device looks up the array's device address on that device (a one-time
- * set-up); make that first call before any stream capture. Every call shares the one array and
- * resets the keys it uses, so calls whose work overlaps on the GPU (other streams, other host
- * threads) race and must be serialised by the caller. */
+ * set-up); make that first call before any stream capture. The address is kept for the life of
+ * the device's context: do not use this call across a cudaDeviceReset. Every call shares the
+ * one array and resets the keys it uses, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
 #define TSGM_NOALLOC_MAX_PIXELS 2097152
 tsgm_status tsgm_warp_predict_noalloc(const float* prev_D, const float* prev_P, int32_t width,
                                       int32_t height, const float R[9], const float t[3],

@@ -8,6 +8,7 @@
 // point does the same work as tsgm_warp_predict with the scratch taken from a file-scope device
 // array; it calls no cudaMalloc, cudaFree or other allocating routine.
 
+#include <cfloat>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -33,6 +34,9 @@ void put_error(char* buf, size_t len, const char* msg) {
 
 // Device address of the key array on the current device, resolved once per device. In host
 // code the array's name is only a host-side stand-in, so the kernels get this address instead.
+// The cached address belongs to the device's current context: after cudaDeviceReset (or any
+// other teardown of the primary context) the module is loaded again and may sit elsewhere, so
+// the entry point is not to be used across a device reset.
 cudaError_t keys_on_current_device(unsigned long long** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -61,6 +65,12 @@ extern "C" tsgm_status tsgm_warp_predict_noalloc(const float* prev_D, const floa
         put_error(errbuf, errbuf_len, "tsgm_warp_predict_noalloc: null pointer");
         return TSGM_ERR_INVALID_ARG;
     }
+    // the gather writes pred_D[i], pred_P[i] while other threads still read the winners' source
+    // values from prev_D, prev_P: outputs that alias inputs would race
+    if (pred_D == prev_D || pred_P == prev_P || pred_D == prev_P || pred_P == prev_D) {
+        put_error(errbuf, errbuf_len, "tsgm_warp_predict_noalloc: outputs alias inputs");
+        return TSGM_ERR_INVALID_ARG;
+    }
     if (width < 1 || height < 1 ||
         (int64_t)width * (int64_t)height > (int64_t)TSGM_NOALLOC_MAX_PIXELS) {
         char msg[200];
@@ -71,8 +81,8 @@ extern "C" tsgm_status tsgm_warp_predict_noalloc(const float* prev_D, const floa
         put_error(errbuf, errbuf_len, msg);
         return TSGM_ERR_INVALID_ARG;
     }
-    if (!(q >= 0.0f)) {
-        put_error(errbuf, errbuf_len, "tsgm_warp_predict_noalloc: q must be >= 0");
+    if (!(q >= 0.0f && q <= FLT_MAX)) {
+        put_error(errbuf, errbuf_len, "tsgm_warp_predict_noalloc: q must be finite and >= 0");
         return TSGM_ERR_INVALID_ARG;
     }
     float H32[16];

@@ -91,3 +91,48 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
                                        x.data_ptr(), None, err, 256)
     assert st == tsgm.ERR_INVALID_ARG
     assert "exceeds" in err.value.decode()
+
+
+def test_noalloc_refuses_aliased_outputs_and_bad_q(lib):
+    """Outputs that alias inputs would race inside the gather, and an infinite q would make every
+    predicted variance infinite: both are refused before anything is enqueued."""
+    from paper_1708_06301_gb300 import tsgm
+    W, H = 64, 32
+    K = synth.Camera(W, H, 721.0, 0.54).K
+    D, P = synth.random_maps(7, W, H)
+    dD, dP = dev(D), dev(P)
+    o = empty((H, W), np.float32)
+    for outD, outP in ((dD, o), (o, dP), (dP, o), (o, dD)):
+        st, msg = call_noalloc(lib, dD, dP, np.eye(3), np.zeros(3), K, 0.54, 0.25, outD, outP)
+        assert st == tsgm.ERR_INVALID_ARG and "alias" in msg
+    o2 = empty((H, W), np.float32)
+    for q in (float("inf"), float("nan"), -1.0):
+        st, msg = call_noalloc(lib, dD, dP, np.eye(3), np.zeros(3), K, 0.54, q, o, o2)
+        assert st == tsgm.ERR_INVALID_ARG and "q must be" in msg
+
+
+def test_noalloc_at_exactly_its_maximum_size(lib):
+    """An image of exactly TSGM_NOALLOC_MAX_PIXELS pixels (2048 x 1024), where an off-by-one in
+    the bound or in the reset of the key array would show, equals the context entry point."""
+    from paper_1708_06301_gb300 import tsgm
+    W, H = 2048, 1024
+    K = synth.Camera(W, H, 721.0, 0.54).K
+    b = f32(0.54)
+    ctx = tsgm.Context(tsgm.default_params(W, H))
+    for seed in (11, 12):  # a moved pose, then the identity (every key of the array in use)
+        D, P = synth.random_maps(seed, W, H, d_range=(1.0, 20.0), invalid_frac=0.05)
+        R, t = (synth.random_pose(seed) if seed == 11 else (np.eye(3), np.zeros(3)))
+        dD, dP = dev(D), dev(P)
+        outD, outP = empty((H, W), np.float32), empty((H, W), np.float32)
+        st, msg = call_noalloc(lib, dD, dP, R, t, K, b, 0.25, outD, outP)
+        assert st == 0, msg
+        refD, refP = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.warp_predict(dD, dP, R, t, K, b, refD, refP)
+        gD, gP = host(outD, np.float32), host(outP, np.float32)
+        eD, eP = host(refD, np.float32), host(refP, np.float32)
+        assert np.array_equal(gD < 0, eD < 0)
+        v = eD >= 0
+        assert v.mean() > 0.3
+        assert np.max(np.abs(gD[v] - eD[v])) <= 1e-4
+        assert np.max(np.abs(gP[v] - eP[v]) / eP[v]) <= 1e-5
+    ctx.close()
