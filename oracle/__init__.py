@@ -319,6 +319,12 @@ def match(left, right, lo, hi, prm: Params, keep: bool = False):
                 dright=dright, valid=valid, Dz=Dz, rz=rz)
 
 
+def _finite_nonneg(a):
+    """The validity test of a disparity or variance: finite and >= 0 (NaN, inf, -1 invalid)."""
+    a = np.asarray(a, np.float32)
+    return (a >= 0) & (a <= np.finfo(np.float32).max)
+
+
 def K_fbc(K):
     K = np.asarray(K, dtype=np.float64).reshape(3, 3)
     return float(K[0, 0]), float(K[0, 2]), float(K[1, 2])
@@ -362,10 +368,17 @@ class Tracker:
         if prm.sad_check:
             out["D_unchecked"], out["P_unchecked"] = D, P
             D, P = sad_check(left, right, D, P, prm.sad_w, prm.sad_h, prm.sad_thr)
-        self.D, self.P = D, P
+        # Sec. 2.4, disparity consistency check: where the matched disparity was rejected, the
+        # true minimum may lie outside the reduced window, so the next frame searches the whole
+        # range there. The updated map still carries the prediction (Sec. 3: it combines the
+        # matched and the predicted map), but the state passed to the next frame keeps no value.
+        meas = _finite_nonneg(m["Dz"]) & _finite_nonneg(m["rz"])
+        self.D = np.where(meas, D, np.float32(-1.0)).astype(np.float32)
+        self.P = np.where(meas, P, np.float32(-1.0)).astype(np.float32)
         if keep:
             out.update(m)
-            out.update(Dpred=Dp, Ppred=Pp, lo=lo, hi=hi, n_cells=n_cells, D=D, P=P)
+            out.update(Dpred=Dp, Ppred=Pp, lo=lo, hi=hi, n_cells=n_cells, D=D, P=P,
+                       D_state=self.D, P_state=self.P)
             return out
         return D, P
 

@@ -628,6 +628,35 @@ def test_tracker_prediction_adds_the_ego_motion_variance():
     assert np.all(o["Dpred_raw"][~v] == -1)
 
 
+def test_tracker_rejected_measurement_is_searched_in_full_next_frame():
+    """Sec. 2.4 (disparity consistency check): the true minimum may lie outside a reduced window,
+    so where the matched disparity was rejected the next frame searches the whole range. The
+    updated map itself still carries the prediction there (Sec. 3: it combines the matched and
+    the predicted map). With identity poses every pixel predicts only itself, so the pixels
+    rejected in frame 2 are exactly the ones without a prediction in frame 3."""
+    seq = synth.small_pair(1)
+    prm = oracle.Params(320, 96)
+    tr = oracle.Tracker(prm)
+    I3, z3 = np.eye(3, dtype=np.float32), np.zeros(3, np.float32)
+    tr.frame(seq.left[0], seq.right[0], seq.R[0], seq.t[0], seq.K, B)
+    noise, _ = synth.random_images(5, 320, 96)
+    # frame 2: an unrelated right view, so that many matches fail the left-right check
+    o2 = tr.frame(seq.left[0], noise, I3, z3, seq.K, B, keep=True)
+    pv = o2["Dpred"] >= 0
+    rej = pv & (o2["Dz"] < 0)
+    acc = pv & (o2["Dz"] >= 0)
+    assert rej.sum() > 1000 and acc.sum() > 100
+    assert np.array_equal(o2["D"][rej], o2["Dpred"][rej])
+    assert np.array_equal(o2["P"][rej], o2["Ppred"][rej])
+    assert np.all(o2["D_state"][rej] == -1) and np.all(o2["P_state"][rej] == -1)
+    assert np.array_equal(o2["D_state"][acc], o2["D"][acc])
+    o3 = tr.frame(seq.left[0], seq.right[0], I3, z3, seq.K, B, keep=True)
+    assert np.all(o3["Dpred_raw"][rej] == -1)
+    assert np.all(o3["lo"][rej] == 0) and np.all(o3["hi"][rej] == prm.D - 1)
+    w3 = o3["hi"].astype(np.int64) - o3["lo"] + 1
+    assert np.all(w3[acc] < prm.D)
+
+
 def test_pipeline_small_pair_reduced_vs_full():
     """Frame 2 of the 320x96 pair: the reduced search considers a fraction of the cells and is at
     least as accurate (bad-3px over ground truth) as full-range SGM on the same frame."""
