@@ -177,8 +177,11 @@ tsgm_status tsgm_kalman_update(tsgm_ctx* ctx, const float* pred_D, const float* 
 
 /* One time step (Sec. 2): predict from the context's previous state with the pose, choose the
  * windows, match, update; the result is written to D, P (device) and kept as the next
- * frame's previous state. The first call after create/reset has no prediction and searches
- * the whole range (Sec. 3); its R, t may be NULL. */
+ * frame's previous state, except where the matched disparity was rejected (left-right check):
+ * there D, P carry the prediction, but the state keeps no value, so that the next frame
+ * searches the whole range at that pixel (Sec. 2.4, disparity consistency check). The first
+ * call after create/reset has no prediction and searches the whole range (Sec. 3); its R, t
+ * may be NULL. */
 tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
                        const float R[9], const float t[3], const float K[9], float baseline,
                        float* D, float* P);
@@ -207,7 +210,8 @@ tsgm_status tsgm_wait(tsgm_ctx* ctx);
 tsgm_status tsgm_reset(tsgm_ctx* ctx);
 
 /* Checkpoint of the per-stream state (previous D, P and whether it exists) through host
- * buffers of width*height floats. Export synchronises the stream. */
+ * buffers of width*height floats: the last frame's D, P without the pixels whose match was
+ * rejected (see tsgm_frame). Export synchronises the stream. */
 tsgm_status tsgm_state_export(tsgm_ctx* ctx, float* D_host, float* P_host, int32_t* has_prev);
 tsgm_status tsgm_state_import(tsgm_ctx* ctx, const float* D_host, const float* P_host,
                               int32_t has_prev);

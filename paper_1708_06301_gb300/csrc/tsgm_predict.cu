@@ -177,8 +177,11 @@ __global__ void __launch_bounds__(256) k_kalman(const float* __restrict__ Dp,
         D[i] = d;
         P[i] = p;
         if (D2) {
-            D2[i] = d;
-            P2[i] = p;
+            // the state for the next frame keeps only measured pixels: where the match was
+            // rejected the true minimum may lie outside the window, so the next frame searches
+            // the whole range there (Sec. 2.4, disparity consistency check)
+            D2[i] = mv ? d : -1.0f;
+            P2[i] = mv ? p : -1.0f;
         }
     }
 }
