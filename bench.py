@@ -159,6 +159,55 @@ def oracle_frames(seq, frames):
     return times
 
 
+def _oracle_worker(frames_data, reps):
+    """One host thread's share of the threaded CPU baseline: the whole sequence `reps` times with
+    its own tracker (frames of different sequences are independent)."""
+    import oracle
+    left, right, Rs, ts, K, b = frames_data
+    prm = oracle.Params(1242, 375, d_max=127, census_w=9, census_h=7, n_paths=8, fill_gaps=True)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        tr = oracle.Tracker(prm)
+        for k in range(len(left)):
+            tr.frame(left[k], right[k], Rs[k], ts[k], K, b)
+    return len(left) * reps, time.perf_counter() - t0
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_threaded(seq, threads: int):
+    """The oracle (itself single-threaded, as it stands) run as `threads` independent copies of
+    the 10-frame sequence in a spawn process pool, one per host core: aggregate frames/s."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    data = (list(seq.left), list(seq.right), list(seq.R), list(seq.t), seq.K,
+            np.float32(seq.cam.b))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(threads) as pool:
+        pool.map(_oracle_worker, [(data, 0)] * threads)  # start-up (imports) outside the clock
+        t0 = time.perf_counter()
+        res = pool.starmap(_oracle_worker, [(data, 1)] * threads)
+        wall = time.perf_counter() - t0
+    return sum(r[0] for r in res) / wall
+
+
 def run_reference(args, ws, rank):
     """The oracle on the host cores: step s processes frame s mod 10 of the sequence (so ten
     steps have the same full-range/reduced mix as one GPU step)."""
@@ -583,6 +632,9 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
         extra["batched"] = bench_batched(dev, max(3, args.steps // 2), 2)
         extra["serving"] = bench_serving(args.serving_seconds, 64.0)
     cpu_s = sum(oracle_frames(seq, list(range(N_FRAMES))))
+    n_threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cpu_fps_threaded = oracle_threaded(seq, n_threads)
+    cpu_name = cpu_model()
     line = {
         "metric": METRIC,
         "value": fps,
@@ -624,9 +676,14 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
                      "avg_launch_us": agg_avg_s * 1e6,
                      "timed_in": "a profiled pass of the same steps beside the headline's"},
         "cpu_baseline": {"value": N_FRAMES / cpu_s, "unit": "frames/s", "cores": 1,
-                         "kind": "oracle",
+                         "kind": "oracle", "cpu": cpu_name,
                          "sample": "one step: the 10-frame sequence (1 full-range, 9 reduced), "
-                                   "single thread"},
+                                   "single thread",
+                         "threaded": {"value": cpu_fps_threaded, "unit": "frames/s",
+                                      "cores": n_threads, "cpu": cpu_name,
+                                      "sample": f"{n_threads} independent copies of the 10-frame "
+                                                "sequence at once, one process per core (the "
+                                                "oracle itself is single-threaded)"}},
         "e2e": {"value": frames / (e2e_max / 1000.0), "unit": "frames/s",
                 "h2d_bytes_per_step": N_FRAMES * 2 * n,
                 "d2h_bytes_per_step": N_FRAMES * 2 * 4 * n,
