@@ -201,7 +201,7 @@ def oracle_threaded(seq, threads: int):
             np.float32(seq.cam.b))
     ctx = mp.get_context("spawn")
     with ctx.Pool(threads) as pool:
-        pool.map(_oracle_worker, [(data, 0)] * threads)  # start-up (imports) outside the clock
+        pool.starmap(_oracle_worker, [(data, 0)] * threads)  # start-up outside the clock
         t0 = time.perf_counter()
         res = pool.starmap(_oracle_worker, [(data, 1)] * threads)
         wall = time.perf_counter() - t0

@@ -104,6 +104,7 @@ class Params:
     sad_w: int = 5               # patch (odd sizes; not given)
     sad_h: int = 5
     sad_thr: float = 30.0        # mean absolute difference per patch pixel (value not given)
+    full_range: bool = False     # search [0, D-1] everywhere (prediction and update as usual)
 
     @property
     def D(self) -> int:
@@ -362,7 +363,12 @@ class Tracker:
                 Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)
             if prm.pred_lr_check:
                 Dp, Pp = pred_lr_check(Dp, Pp, prm.pred_lr_tol)
-        lo, hi, off, n_cells = windows(Dp, Pp, prm.D, prm.sigma_mult)
+        if prm.full_range:
+            lo = np.zeros((Hh, W), np.int16)
+            hi = np.full((Hh, W), prm.D - 1, np.int16)
+            n_cells = W * Hh * prm.D
+        else:
+            lo, hi, off, n_cells = windows(Dp, Pp, prm.D, prm.sigma_mult)
         m = match(left, right, lo, hi, prm, keep=True)
         D, P = kalman(Dp, Pp, m["Dz"], m["rz"])
         if prm.sad_check:

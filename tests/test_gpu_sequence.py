@@ -36,29 +36,12 @@ def _oracle_sequence(mode: str, n_frames: int):
     W, H = seq.cam.W, seq.cam.H
     b = float(np.float32(seq.cam.b))
     prm = oracle.Params(W, H, d_max=127, census_w=9, census_h=7, n_paths=8,
-                        fill_gaps=(mode == "reduced"))
+                        fill_gaps=(mode == "reduced"), full_range=(mode == "full"))
+    tr = oracle.Tracker(prm)
     out = []
-    if mode == "reduced":
-        tr = oracle.Tracker(prm)
-        for k in range(n_frames):
-            o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, b, keep=True)
-            out.append(dict(D=o["D"], P=o["P"], lo=o["lo"], hi=o["hi"]))
-        return out
-    lo = np.zeros((H, W), np.int16)
-    hi = np.full((H, W), prm.D - 1, np.int16)
-    f, cx, cy = oracle.K_fbc(np.asarray(seq.K, np.float32))
-    D = P = None
     for k in range(n_frames):
-        if D is None:
-            Dp = np.full((H, W), -1.0, np.float32)
-            Pp = Dp.copy()
-        else:
-            _, H32 = oracle.build_H(np.asarray(seq.R[k], np.float32),
-                                    np.asarray(seq.t[k], np.float32), f, b)
-            Dp, Pp, _ = oracle.warp_predict(D, P, H32, np.float32(cx), np.float32(cy), prm.q)
-        Dz, rz = oracle.match(seq.left[k], seq.right[k], lo, hi, prm)
-        D, P = oracle.kalman(Dp, Pp, Dz, rz)
-        out.append(dict(D=D, P=P, lo=lo, hi=hi))
+        o = tr.frame(seq.left[k], seq.right[k], seq.R[k], seq.t[k], seq.K, b, keep=True)
+        out.append(dict(D=o["D"], P=o["P"], lo=o["lo"], hi=o["hi"]))
     return out
 
 

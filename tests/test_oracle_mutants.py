@@ -134,6 +134,8 @@ PY_MUTANTS = [
      "            if prm.fill_gaps:\n                Dp, Pp = fill_gaps(Dp, Pp, prm.gamma_f)\n"),
     ("tracker_state_keeps_rejected", "meas = _finite_nonneg(m[\"Dz\"]) & _finite_nonneg(m[\"rz\"])",
      "meas = np.ones(D.shape, bool)"),
+    ("tracker_full_range_ignored", "        if prm.full_range:\n            lo = np.zeros((Hh, W), np.int16)",
+     "        if False:\n            lo = np.zeros((Hh, W), np.int16)"),
     ("tracker_sad_skipped", "            D, P = sad_check(left, right, D, P, prm.sad_w, prm.sad_h, prm.sad_thr)\n",
      "            pass\n"),
     ("rodrigues_sign", "return np.eye(3) + np.sin(th) * Kx + (1 - np.cos(th)) * (Kx @ Kx)",

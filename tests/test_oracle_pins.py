@@ -657,6 +657,22 @@ def test_tracker_rejected_measurement_is_searched_in_full_next_frame():
     assert np.all(w3[acc] < prm.D)
 
 
+def test_tracker_full_range_option():
+    """full_range searches [0, D-1] everywhere and keeps the prediction and the update: frame 2
+    equals the Kalman update (Eq. 10-12) of the warped prediction with a full-range match."""
+    seq = synth.small_pair(1)
+    prm = oracle.Params(320, 96, full_range=True)
+    tr = oracle.Tracker(prm)
+    tr.frame(seq.left[0], seq.right[0], seq.R[0], seq.t[0], seq.K, B)
+    o = tr.frame(seq.left[1], seq.right[1], seq.R[1], seq.t[1], seq.K, B, keep=True)
+    assert np.all(o["lo"] == 0) and np.all(o["hi"] == 63) and o["n_cells"] == 320 * 96 * 64
+    assert (o["Dpred"] >= 0).mean() > 0.5
+    lo, hi = np.zeros((96, 320), np.int16), np.full((96, 320), 63, np.int16)
+    Dz, rz = oracle.match(seq.left[1], seq.right[1], lo, hi, prm)
+    D, P = oracle.kalman(o["Dpred"], o["Ppred"], Dz, rz)
+    assert np.array_equal(o["D"], D) and np.array_equal(o["P"], P)
+
+
 def test_pipeline_small_pair_reduced_vs_full():
     """Frame 2 of the 320x96 pair: the reduced search considers a fraction of the cells and is at
     least as accurate (bad-3px over ground truth) as full-range SGM on the same frame."""
