@@ -309,7 +309,7 @@ tsgm_status match_stages(tsgm_ctx* ctx, const int16_t* lo, const int16_t* hi, fl
     stage_end(ctx, TSGM_STAGE_COST);
     stage_begin(ctx, TSGM_STAGE_SGM);
     TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->Lvol,
-                           ctx->max_cells, ctx->stream),
+                           ctx->max_cells, ctx->wq, ctx->stream),
                 "sgm");
     stage_end(ctx, TSGM_STAGE_SGM);
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "tsgm_kernels.cuh"
+#include "tsgm_sgm.cuh"
 
 namespace {
 
@@ -54,11 +55,11 @@ struct BTable {
     int tile_base[kMaxStreams + 1];  // prefix of census tiles (one image)
     int px_base[kMaxStreams + 1];    // prefix of pixels
     int tiles_x[kMaxStreams];
-    // pairs of opposite path lines, direction-major: slot s holds the lines of directions 2s and
-    // 2s + 1; items of stream i in slot s are [slot_base[s][i], slot_base[s][i+1]);
-    // slot_base[s][ns] == slot_base[s+1][0]
-    int slot_base[4][kMaxStreams + 1];
-    int total_lines;
+    // groups of path lines (the lines one warp walks together), direction-major: slot s holds the
+    // lines of direction code s; items of stream i in slot s are [slot_base[s][i],
+    // slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]
+    int slot_base[8][kMaxStreams + 1];
+    int total_items;
 };
 
 __device__ __forceinline__ int find_stream(const int* base, int ns, int item) {
@@ -114,30 +115,32 @@ __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
     }
 }
 
-// persistent path aggregation: warps take items from a global counter until none is left; each
-// pair of opposite path lines (one geometric line) is two items, its twins (see sgm_pair)
-template <int LPL, int WARPS>
+// persistent path aggregation: warps take items from a global counter until none is left; an item
+// is the NG = 32 / GL lines of one direction of one stream that a warp walks together (see
+// sgm_group_lines), every stream's horizontal lines first
+template <int LPLW, int GL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__ st,
-                                                     const BTable* __restrict__ tb, int n_pairs,
+                                                     const BTable* __restrict__ tb, int n_slots,
                                                      int P1, int P2, int* __restrict__ counter) {
+    constexpr int NG = 32 / GL;
     extern __shared__ uint32_t sgm_smem32[];
-    uint32_t* wsm = sgm_smem32 + (threadIdx.x >> 5) * sgm_pair_words<LPL>();
+    uint32_t* wsm = sgm_smem32 + (threadIdx.x >> 5) * grp_words_ng<LPLW, NG>();
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(counter, 1);
         item = __shfl_sync(kFull, item, 0);
-        if (item >= 2 * tb->total_lines) return;
-        const int pitem = item >> 1;  // two items (twins) per pair of lines
+        if (item >= tb->total_items) return;
         int slot = 0;
-        while (slot + 1 < n_pairs && pitem >= tb->slot_base[slot + 1][0]) ++slot;
-        const int s = find_stream(tb->slot_base[slot], tb->ns, pitem);
+        while (slot + 1 < n_slots && item >= tb->slot_base[slot + 1][0]) ++slot;
+        const int s = find_stream(tb->slot_base[slot], tb->ns, item);
         const BStream& b = st[s];
         if (*b.status != 0u) continue;
-        const int code = 2 * slot;
-        sgm_pair<LPL>(b.C, b.desc, b.W, b.H, b.D, P1, P2, code, pitem - tb->slot_base[slot][s],
-                      b.Lvol + (size_t)code * b.capacity, b.Lvol + (size_t)(code + 1) * b.capacity,
-                      wsm, item & 1);
+        const int code = slot;
+        const int nlines = code <= 1 ? b.H : (code <= 3 ? b.W : b.W + b.H - 1);
+        sgm_group_lines<LPLW, GL>(b.C, b.desc, b.W, b.H, P1, P2, code,
+                                  (item - tb->slot_base[slot][s]) * NG, nlines,
+                                  b.Lvol + (size_t)code * b.capacity, wsm);
     }
 }
 
@@ -170,24 +173,32 @@ constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 using SgmKernel = void (*)(const BStream*, const BTable*, int, int, int, int*);
 
-int lpl_for(int maxD) { return maxD <= 64 ? 2 : (maxD <= 128 ? 4 : 8); }
+int lplw_for(int maxD) { return maxD <= 64 ? 2 : (maxD <= 128 ? 4 : 8); }
 
-template <int LPL>
-SgmKernel sgm_kernel_l(int warps) {
-    return warps == 4 ? kb_sgm<LPL, 4> : (warps == 8 ? kb_sgm<LPL, 8> : kb_sgm<LPL, 16>);
+template <int LPLW, int GL>
+SgmKernel sgm_kernel_lg(int warps) {
+    return warps == 4 ? kb_sgm<LPLW, GL, 4> : (warps == 8 ? kb_sgm<LPLW, GL, 8> : kb_sgm<LPLW, GL, 16>);
 }
 
-SgmKernel sgm_kernel(int maxD, int warps) {
-    switch (lpl_for(maxD)) {
-        case 2: return sgm_kernel_l<2>(warps);
-        case 4: return sgm_kernel_l<4>(warps);
-        default: return sgm_kernel_l<8>(warps);
+template <int LPLW>
+SgmKernel sgm_kernel_l(int gl, int warps) {
+    return gl == 4 ? sgm_kernel_lg<LPLW, 4>(warps) : sgm_kernel_lg<LPLW, 8>(warps);
+}
+
+SgmKernel sgm_kernel(int maxD, int gl, int warps) {
+    switch (lplw_for(maxD)) {
+        case 2: return sgm_kernel_l<2>(gl, warps);
+        case 4: return sgm_kernel_l<4>(gl, warps);
+        default: return sgm_kernel_l<8>(gl, warps);
     }
 }
 
-size_t sgm_smem_bytes(int maxD, int warps) {
-    const int L = lpl_for(maxD);
-    const int words = L == 2 ? sgm_pair_words<2>() : (L == 4 ? sgm_pair_words<4>() : sgm_pair_words<8>());
+template <int LPLW>
+int sgm_words(int gl) { return gl == 4 ? grp_words_ng<LPLW, 8>() : grp_words_ng<LPLW, 4>(); }
+
+size_t sgm_smem_bytes(int maxD, int gl, int warps) {
+    const int L = lplw_for(maxD);
+    const int words = L == 2 ? sgm_words<2>(gl) : (L == 4 ? sgm_words<4>(gl) : sgm_words<8>(gl));
     return (size_t)warps * words * sizeof(uint32_t);
 }
 
@@ -208,6 +219,8 @@ struct tsgm_batch {
     BTable* d_table = nullptr;
     int* d_counter = nullptr;
     int shape = 3;  // index into kShapes
+    int gl = 8;     // lanes per path line in the aggregation (4: windows up to 16 labels in one step)
+    bool shape_ok[kNumShapes] = {};  // the shape's shared memory fits a block
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev_sgm_a = nullptr, ev_sgm_b = nullptr;  // around the aggregation (profiled steps)
     uint64_t launches = 0;
@@ -262,8 +275,9 @@ cudaError_t enqueue_step(tsgm_batch* b, int shape, bool timed = false) {
     if (timed && (e = cudaEventRecord(b->ev_sgm_a, st)) != cudaSuccess) return e;
     const SgmShape sh = kShapes[shape];
     const int grid = b->sms * sh.blocks;
-    sgm_kernel(b->maxD, sh.warps)<<<grid, sh.warps * 32, sgm_smem_bytes(b->maxD, sh.warps), st>>>(
-        b->d_streams, b->d_table, p.n_paths / 2, p.P1, p.P2, b->d_counter);
+    sgm_kernel(b->maxD, b->gl, sh.warps)<<<grid, sh.warps * 32,
+                                           sgm_smem_bytes(b->maxD, b->gl, sh.warps), st>>>(
+        b->d_streams, b->d_table, p.n_paths, p.P1, p.P2, b->d_counter);
     if (timed && (e = cudaEventRecord(b->ev_sgm_b, st)) != cudaSuccess) return e;
     const int DP = 256;
     const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * DP * 2;
@@ -390,26 +404,39 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
             t.tile_base[i + 1] = t.tile_base[i] + t.tiles_x[i] * ((s.H + kCtH - 1) / kCtH);
             t.px_base[i + 1] = t.px_base[i] + s.n;
         }
+        // lines per warp: windows of up to 16 labels fit the 4-lane groups (8 lines per warp),
+        // wider ones (up to 32 in one step) the 8-lane groups
+        b->gl = (max_labels > 0 && max_labels <= 16) ? 4 : 8;
+        const int NG = 32 / b->gl;
         // direction-major line order: every stream's horizontal lines first
         int item = 0;
-        for (int slot = 0; slot < p0.n_paths / 2; ++slot) {
+        for (int slot = 0; slot < p0.n_paths; ++slot) {
             for (int i = 0; i < n_streams; ++i) {
                 t.slot_base[slot][i] = item;
                 const BStream& s = b->h_streams[i];
-                const int code = 2 * slot;
-                item += code <= 1 ? s.H : (code <= 3 ? s.W : s.W + s.H - 1);
+                const int code = slot;
+                const int nl = code <= 1 ? s.H : (code <= 3 ? s.W : s.W + s.H - 1);
+                item += (nl + NG - 1) / NG;
             }
             t.slot_base[slot][n_streams] = item;
         }
-        t.total_lines = item;
+        t.total_items = item;
         ok = ok && cudaMemcpy(b->d_table, b->h_table, sizeof(BTable), cudaMemcpyHostToDevice) == cudaSuccess;
+        int smem_max = 48 * 1024;
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        int first_ok = -1;
         for (int k = 0; ok && k < kNumShapes; ++k) {
-            const size_t sm = sgm_smem_bytes(b->maxD, kShapes[k].warps);
+            const size_t sm = sgm_smem_bytes(b->maxD, b->gl, kShapes[k].warps);
+            if (sm > (size_t)smem_max) continue;  // does not fit: never launched
             if (sm > 48 * 1024)
-                ok = cudaFuncSetAttribute(sgm_kernel(b->maxD, kShapes[k].warps),
+                ok = cudaFuncSetAttribute(sgm_kernel(b->maxD, b->gl, kShapes[k].warps),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sm) == cudaSuccess;
+            b->shape_ok[k] = ok;
+            if (ok && first_ok < 0) first_ok = k;
         }
+        if (first_ok < 0) ok = false;
+        if (ok && !b->shape_ok[b->shape]) b->shape = first_ok;
         const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * 256 * 2;
         if (ok && sel_smem > 48 * 1024) {
             ok = cudaFuncSetAttribute(kb_select<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -480,6 +507,7 @@ tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
     double best = 1e30;
     int best_i = b->shape;
     for (int i = 0; i < kNumShapes; ++i) {
+        if (!b->shape_ok[i]) continue;
         e = enqueue_step(b, i);  // warm-up
         if (e != cudaSuccess) break;
         cudaEventRecord(a, b->exec);

@@ -13,6 +13,7 @@
 #include <cfloat>
 
 #include "tsgm_kernels.cuh"
+#include "tsgm_sgm.cuh"
 
 namespace tsgm {
 namespace {
@@ -37,28 +38,34 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
                 threadIdx.x & 7, (gridDim.x * blockDim.x) >> 3);
 }
 
-// Path aggregation of one image: all lines of all directions in one launch, two twin warps per
-// pair of opposite directions on one geometric line (see sgm_pair; horizontal pairs first: they
-// are the longest chains). `lines` lists the first direction of each pair (codes 0, 2, 4, 6) and
-// its line counts. The twin that walks an all-full-range pair is warp 0, 2, 5 or 7 of the block:
-// one on each of the four SM sub-partitions (warp index mod 4), not two on each of two.
-template <int LPL>
-__global__ void __launch_bounds__(kSgmWarps * 32) k_sgm(const uint8_t* __restrict__ C,
+// Path aggregation of one image: all lines of all directions in one launch, NG lines of one
+// direction per warp (see sgm_group_lines; horizontal lines first: they are the longest chains).
+// The lines' groups are 4 lanes wide (windows of up to 16 labels in straight-line code, 8 lines
+// per warp) unless more than one pixel in 16 has a wider window (wq[0], the count of windows
+// wider than kSelNarrow = 16 labels, written by the offsets pass): then 8 lanes (up to 32 labels,
+// 4 lines per warp). The launch has enough warps for the second form; in the first, the warps
+// past the last line return at once.
+constexpr int kGrpWarps = 4;
+
+template <int LPLW>
+__global__ void __launch_bounds__(kGrpWarps * 32) k_sgm(const uint8_t* __restrict__ C,
                                                         const uint2* __restrict__ desc, int W,
-                                                        int Hh, int D, int P1, int P2,
-                                                        SgmLines lines, uint8_t* __restrict__ Lvol,
-                                                        uint64_t vol_stride) {
+                                                        int Hh, int P1, int P2, GrpLines lines,
+                                                        uint8_t* __restrict__ Lvol,
+                                                        uint64_t vol_stride,
+                                                        const uint32_t* __restrict__ wq, int n) {
     extern __shared__ uint32_t sgm_smem32[];
     const int wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * kSgmWarps + wib;
-    const int pair = gw >> 1;
-    if (pair >= lines.start[lines.nslots]) return;
-    int slot = 0;
-    while (pair >= lines.start[slot + 1]) ++slot;
-    const int code = lines.code[slot];
-    sgm_pair<LPL>(C, desc, W, Hh, D, P1, P2, code, pair - lines.start[slot],
-                  Lvol + (size_t)code * vol_stride, Lvol + (size_t)(code + 1) * vol_stride,
-                  sgm_smem32 + wib * sgm_pair_words<LPL>(), gw & 1, (pair >> 1) & 1);
+    const int gw = blockIdx.x * kGrpWarps + wib;
+    uint32_t* const wsm = sgm_smem32 + wib * grp_words<LPLW>();
+    const bool eight = 16ull * wq[0] > (unsigned long long)n;
+    int code, first, nlines;
+    if (!grp_warp_lines(lines, eight ? 4 : 8, gw, code, first, nlines)) return;
+    uint8_t* const Lv = Lvol + (size_t)code * vol_stride;
+    if (eight)
+        sgm_group_lines<LPLW, 8>(C, desc, W, Hh, P1, P2, code, first, nlines, Lv, wsm);
+    else
+        sgm_group_lines<LPLW, 4>(C, desc, W, Hh, P1, P2, code, first, nlines, Lv, wsm);
 }
 
 // Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the
@@ -185,37 +192,36 @@ cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* des
     return cudaGetLastError();
 }
 
-template <int LPL>
-static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int Hh, int D,
-                                int P1, int P2, const SgmLines& L, uint8_t* Lvol,
-                                uint64_t vol_stride, cudaStream_t st) {
-    const int nwarps = 2 * L.start[L.nslots];  // twin warps per pair
-    const size_t smem = (size_t)kSgmWarps * sgm_pair_words<LPL>() * sizeof(uint32_t);
+template <int LPLW>
+static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int Hh, int P1, int P2,
+                                const GrpLines& L, uint8_t* Lvol, uint64_t vol_stride,
+                                const uint32_t* wq, cudaStream_t st) {
+    int nwarps = 0;  // warps of the 4-lines-per-warp form, the larger count
+    for (int s = 0; s < L.nslots; ++s) nwarps += (L.count[s] + 3) / 4;
+    const size_t smem = (size_t)kGrpWarps * grp_words<LPLW>() * sizeof(uint32_t);
     if (smem > 48 * 1024) {
         const cudaError_t e =
-            cudaFuncSetAttribute(k_sgm<LPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_sgm<LPLW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_sgm<LPL><<<(nwarps + kSgmWarps - 1) / kSgmWarps, kSgmWarps * 32, smem, st>>>(
-        C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride);
+    k_sgm<LPLW><<<(nwarps + kGrpWarps - 1) / kGrpWarps, kGrpWarps * 32, smem, st>>>(
+        C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, W * Hh);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
-                       int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, cudaStream_t st) {
-    // pairs of opposite directions, longest lines first: horizontal, vertical, then diagonals
-    SgmLines L;
-    L.nslots = n_paths / 2;
-    L.start[0] = 0;
-    for (int s = 0; s < L.nslots; ++s) {
-        const int code = 2 * s;
-        L.code[s] = code;
-        const int cnt = code <= 1 ? Hh : (code <= 3 ? W : W + Hh - 1);
-        L.start[s + 1] = L.start[s] + cnt;
+                       int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, const uint32_t* wq,
+                       cudaStream_t st) {
+    // direction codes: horizontal (0, 1), vertical (2, 3), then the diagonals
+    GrpLines L;
+    L.nslots = n_paths;
+    for (int code = 0; code < n_paths; ++code) {
+        L.code[code] = code;
+        L.count[code] = code <= 1 ? Hh : (code <= 3 ? W : W + Hh - 1);
     }
-    if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
-    if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
-    return launch_sgm_t<8>(C, desc, W, Hh, D, P1, P2, L, Lvol, vol_stride, st);
+    if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
+    if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
+    return launch_sgm_t<8>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
 }
 
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,

@@ -79,3 +79,63 @@ def test_results_alone_equal_results_in_the_mix(tsgm, budget):
     for (i, k), (D, P) in outs.items():
         assert np.array_equal(D, ref[i][k][0]), (i, k)
         assert np.array_equal(P, ref[i][k][1]), (i, k)
+
+
+def frames_alone(tsgm, seq, ks):
+    """The stream's frames ks (in order, each with its own pose) through a plain context."""
+    W, H = seq.cam.W, seq.cam.H
+    out = {}
+    with tsgm.Context(params_for(tsgm, seq)) as ctx:
+        D, P = empty((H, W), np.float32), empty((H, W), np.float32)
+        for i, k in enumerate(ks):
+            ctx.frame(dev(seq.left[k]), dev(seq.right[k]), seq.R[k] if i else None,
+                      seq.t[k] if i else None, seq.K, f32(seq.cam.b), D, P)
+            out[k] = (host(D, np.float32), host(P, np.float32))
+    return out
+
+
+def test_a_failing_frame_leaves_the_other_streams_untouched(tsgm):
+    """Frames that cannot run are refused on their own while the others go on: a zero baseline
+    (no disparity-space homography, Eq. 1-4) and a later frame without a pose. Each such ticket
+    reports INVALID_ARG; its stream keeps the state of its last good frame (its next frame is the
+    one a context gives when the refused frame is left out); every other stream's results equal
+    its results alone."""
+    seqs = camera_streams()
+    ref = [alone(tsgm, s) for s in seqs]
+    bad = {(1, 2): "zero baseline", (3, 1): "no pose"}
+    rng = np.random.default_rng(11)
+    with tsgm.Server([params_for(tsgm, s) for s in seqs], hbm_budget_bytes=1 << 40) as srv:
+        nxt = [0] * len(seqs)
+        order = [i for i in range(len(seqs)) for _ in range(4)]
+        rng.shuffle(order)
+        outs, tickets = {}, {}
+        for i in order:
+            k = nxt[i]
+            nxt[i] += 1
+            s = seqs[i]
+            D = np.empty((s.cam.H, s.cam.W), np.float32)
+            P = np.empty_like(D)
+            R, t, b = (s.R[k], s.t[k], f32(s.cam.b)) if k else (None, None, f32(s.cam.b))
+            if bad.get((i, k)) == "zero baseline":
+                b = f32(0.0)
+            elif bad.get((i, k)) == "no pose":
+                R = t = None
+            tickets[(i, k)] = srv.submit(i, s.left[k], s.right[k], R, t, s.K, b, D, P)
+            outs[(i, k)] = (D, P)
+        for key, tk in tickets.items():
+            if key in bad:
+                with pytest.raises(tsgm.TsgmError) as e:
+                    srv.wait(tk)
+                assert e.value.status == tsgm.ERR_INVALID_ARG, bad[key]
+            else:
+                srv.wait(tk)
+        assert srv.stats()["completed"] == len(order)
+    for i in (0, 2, 4):
+        for k in range(4):
+            assert np.array_equal(outs[(i, k)][0], ref[i][k][0]), (i, k)
+            assert np.array_equal(outs[(i, k)][1], ref[i][k][1]), (i, k)
+    for i, ks in ((1, [0, 1, 3]), (3, [0, 2, 3])):
+        skipped = frames_alone(tsgm, seqs[i], ks)
+        for k in ks:
+            assert np.array_equal(outs[(i, k)][0], skipped[k][0]), (i, k)
+            assert np.array_equal(outs[(i, k)][1], skipped[k][1]), (i, k)

@@ -81,14 +81,16 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     """An image larger than the fixed scratch is refused before anything is launched."""
     from paper_1708_06301_gb300 import tsgm
     W, H = 2049, 1024  # 2,098,176 pixels > TSGM_NOALLOC_MAX_PIXELS = 2,097,152
-    x = torch.empty(8, dtype=torch.float32, device="cuda")
+    # four distinct buffers (never read: the call is refused first), so that the size is what
+    # is refused and not an aliasing of outputs and inputs
+    x = [torch.empty(8, dtype=torch.float32, device="cuda") for _ in range(4)]
     Ra, Rp = _host(np.eye(3))
     ta, tp = _host(np.zeros(3))
     Ka, Kp = _host(synth.Camera(W, H, 721.0, 0.54).K)
     err = ctypes.create_string_buffer(256)
-    st = lib.tsgm_warp_predict_noalloc(x.data_ptr(), x.data_ptr(), W, H, Rp, tp, Kp,
-                                       ctypes.c_float(0.54), ctypes.c_float(0.25), x.data_ptr(),
-                                       x.data_ptr(), None, err, 256)
+    st = lib.tsgm_warp_predict_noalloc(x[0].data_ptr(), x[1].data_ptr(), W, H, Rp, tp, Kp,
+                                       ctypes.c_float(0.54), ctypes.c_float(0.25), x[2].data_ptr(),
+                                       x[3].data_ptr(), None, err, 256)
     assert st == tsgm.ERR_INVALID_ARG
     assert "exceeds" in err.value.decode()
 
