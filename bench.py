@@ -358,9 +358,9 @@ def bench_batched(dev, steps: int, warmup: int):
     sgm_s = float(np.mean(sgm_ms)) / 1000.0
     peak, kind = peaks()
     agg_bytes = algorithmic_sgm_bytes(cells, px)
-    # whole-step algorithmic bytes: images 2, census 16 (write+read), windows 4 read + 4 copy,
-    # descriptors 8 + offsets 4, outputs 8 per pixel; C 1 write + 1 read, S 2 per cell
-    step_bytes = 46 * px + 4 * cells
+    # matching step (no prediction or update): 4 B/cell; per pixel images 2, census re-read 32,
+    # windows 4, offsets 4, D_z + r 8 out
+    step_bytes = 4 * cells + 50 * px
     return {"workload": "32 streams: 11x 640x480 D=64, 11x 1242x375 D=128, 10x 1920x1080 D=256; "
                         "windows 4-24 labels around ground truth; inputs larger than L2",
             "px_per_step": px, "cells_per_step": cells, "overflowed_streams": over,
@@ -449,10 +449,21 @@ SGM_DRAM_NOTE = ("k_sgm changed after the last ncu capture (which twin warp walk
                  "pair); that capture read 114.7 MB per launch")
 
 
-def algorithmic_sgm_bytes(cells: int, px: int) -> int:
-    """Bytes the aggregation kernel must move once: the ragged cost C read (1 B/cell), the
-    aggregated S written (2 B/cell), window bounds and offsets read (8 B/px)."""
-    return 3 * cells + 8 * px
+def algorithmic_sgm_bytes(cells: int, px: int, census_bytes: int = 8) -> int:
+    """Bytes the path aggregation must move once (the method's minimum, not this kernel's
+    layout): the directions cannot all be walked in one pass, so a 16-bit partial sum crosses
+    from a forward to a backward sweep, 2 B written + 2 B read per window cell; per pixel the
+    census codes of both images are read in both sweeps (2 x 2 x census_bytes) and the window
+    bounds and ragged offsets once (4 + 4 B): 4 B/cell + 40 B/px with the 9x7 census."""
+    return 4 * cells + (2 * 2 * census_bytes + 8) * px
+
+
+def algorithmic_step_bytes(cells: int, px: int, census_bytes: int = 8) -> int:
+    """Bytes of a whole time step (prediction, windows, matching, update): 4 B/cell as above;
+    per pixel: images 2, census re-read 2 x 2 x census_bytes, windows 4, offsets 4, D_z + r 8
+    out; warp: D, P in 8, z-buffer key read-modify-write 16, predicted D, P out 8; Kalman: 16 in,
+    8 out (106 B/px with the 9x7 census)."""
+    return 4 * cells + (2 + 4 * census_bytes + 4 + 4 + 8 + 8 + 16 + 8 + 16 + 8) * px
 
 
 def run_ours(args, ws, rank, local):

@@ -116,8 +116,9 @@ __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
 }
 
 // persistent path aggregation: warps take items from a global counter until none is left; an item
-// is the NG = 32 / GL lines of one direction of one stream that a warp walks together (see
-// sgm_group_lines), every stream's horizontal lines first
+// is what a warp walks together, NG = 32 / GL groups of lanes on lines (or segments of long
+// horizontal lines) of one direction of one stream (see sgm_group_lines), every stream's
+// horizontal lines first
 template <int LPLW, int GL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__ st,
                                                      const BTable* __restrict__ tb, int n_slots,
@@ -138,8 +139,9 @@ __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__
         if (*b.status != 0u) continue;
         const int code = slot;
         const int nlines = code <= 1 ? b.H : (code <= 3 ? b.W : b.W + b.H - 1);
+        const int seg = code <= 1 ? grp_hseg(b.W, b.H) : 1;
         sgm_group_lines<LPLW, GL>(b.C, b.desc, b.W, b.H, P1, P2, code,
-                                  (item - tb->slot_base[slot][s]) * NG, nlines,
+                                  (item - tb->slot_base[slot][s]) * (NG / seg), nlines, seg,
                                   b.Lvol + (size_t)code * b.capacity, wsm);
     }
 }
@@ -416,7 +418,8 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
                 const BStream& s = b->h_streams[i];
                 const int code = slot;
                 const int nl = code <= 1 ? s.H : (code <= 3 ? s.W : s.W + s.H - 1);
-                item += (nl + NG - 1) / NG;
+                const int per = NG / (code <= 1 ? grp_hseg(s.W, s.H) : 1);
+                item += (nl + per - 1) / per;
             }
             t.slot_base[slot][n_streams] = item;
         }

@@ -38,8 +38,9 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
                 threadIdx.x & 7, (gridDim.x * blockDim.x) >> 3);
 }
 
-// Path aggregation of one image: all lines of all directions in one launch, NG lines of one
-// direction per warp (see sgm_group_lines; horizontal lines first: they are the longest chains).
+// Path aggregation of one image: all lines of all directions in one launch, NG groups of lanes
+// per warp, each on a line of one direction or on a segment of a long horizontal line (see
+// sgm_group_lines; horizontal lines first: they are the longest chains).
 // The lines' groups are 4 lanes wide (windows of up to 16 labels in straight-line code, 8 lines
 // per warp) unless more than one pixel in 16 has a wider window (wq[0], the count of windows
 // wider than kSelNarrow = 16 labels, written by the offsets pass): then 8 lanes (up to 32 labels,
@@ -59,13 +60,13 @@ __global__ void __launch_bounds__(kGrpWarps * 32) k_sgm(const uint8_t* __restric
     const int gw = blockIdx.x * kGrpWarps + wib;
     uint32_t* const wsm = sgm_smem32 + wib * grp_words<LPLW>();
     const bool eight = 16ull * wq[0] > (unsigned long long)n;
-    int code, first, nlines;
-    if (!grp_warp_lines(lines, eight ? 4 : 8, gw, code, first, nlines)) return;
+    int code, first, nlines, seg;
+    if (!grp_warp_lines(lines, eight ? 4 : 8, gw, code, first, nlines, seg)) return;
     uint8_t* const Lv = Lvol + (size_t)code * vol_stride;
     if (eight)
-        sgm_group_lines<LPLW, 8>(C, desc, W, Hh, P1, P2, code, first, nlines, Lv, wsm);
+        sgm_group_lines<LPLW, 8>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
     else
-        sgm_group_lines<LPLW, 4>(C, desc, W, Hh, P1, P2, code, first, nlines, Lv, wsm);
+        sgm_group_lines<LPLW, 4>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
 }
 
 // Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the
@@ -196,8 +197,11 @@ template <int LPLW>
 static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int Hh, int P1, int P2,
                                 const GrpLines& L, uint8_t* Lvol, uint64_t vol_stride,
                                 const uint32_t* wq, cudaStream_t st) {
-    int nwarps = 0;  // warps of the 4-lines-per-warp form, the larger count
-    for (int s = 0; s < L.nslots; ++s) nwarps += (L.count[s] + 3) / 4;
+    int nwarps = 0;  // warps of the 4-groups-per-warp form, the larger count
+    for (int s = 0; s < L.nslots; ++s) {
+        const int per = 4 / L.seg[s];
+        nwarps += (L.count[s] + per - 1) / per;
+    }
     const size_t smem = (size_t)kGrpWarps * grp_words<LPLW>() * sizeof(uint32_t);
     if (smem > 48 * 1024) {
         const cudaError_t e =
@@ -218,6 +222,7 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
     for (int code = 0; code < n_paths; ++code) {
         L.code[code] = code;
         L.count[code] = code <= 1 ? Hh : (code <= 3 ? W : W + Hh - 1);
+        L.seg[code] = code <= 1 ? grp_hseg(W, Hh) : 1;  // long horizontal lines in segments
     }
     if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
     if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);

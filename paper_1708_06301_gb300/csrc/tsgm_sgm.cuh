@@ -15,13 +15,25 @@
 // reduction. A window wider than 4 GL labels is taken by the whole warp (LPLW labels per lane,
 // m by redux.sync), one such group after the other.
 //
+// Long lines in segments. A line's steps form one dependent chain, and the longest lines bound
+// the launch. A line can be cut into S segments walked at once by S groups: segment 0 starts at
+// the line's start; every other one starts as if a line began there (L = C), which is a guess.
+// The recursion forgets its start fast (a window that shares no label with its predecessor's,
+// or P2 capping every difference, makes L independent of what came before), so the guess and
+// the true state agree after a few steps. The guess is then checked exactly: each later segment
+// is walked again from the true end state of the segment before it for kGFix steps, and its
+// state there is compared with the state the first walk had at the same pixel (a checkpoint).
+// Equal states give equal values from there on, so the first walk's later values stand; a
+// difference makes the second walk go on to the segment's end (and the next segment is walked
+// again from that end, and so on), so the result is the sequential recurrence's in every case.
+//
 // State. Each line keeps its last L as a row of 16-bit labels in shared memory, indexed relative
 // to the window's lo, with +inf padding on both sides; two rows per line, used in turn. A step
 // reads the predecessor's labels d - 1 .. d + 1 at the offset lo - lo(q), clamped into the padding
 // (so that no range test is needed): this makes every change of window, narrow or wide, one code
 // path. The costs of the step PF ahead are in flight into a ring of shared-memory slots
-// (cp.async, issued by the group's own lanes), and the window descriptors come in blocks of 32
-// steps per line (cp.async), two blocks in the ring.
+// (cp.async, issued by the group's own lanes), and the window descriptors come in blocks of
+// kGBlk steps per line (cp.async), two blocks in the ring.
 //
 // Each direction writes its path costs L (<= census bits + P2 <= 255) as bytes into its own
 // ragged volume; the selection sums the directions.
@@ -34,7 +46,8 @@ namespace dev {
 
 constexpr int kGPadL = 16, kGPadR = 16;  // +inf labels before and after a state row
 constexpr int kGSlots = 8, kGPref = 6;   // cost ring slots per line and prefetch distance (steps)
-constexpr int kGBlk = 32;                // steps per descriptor block
+constexpr int kGBlk = 16;                // steps per descriptor block
+constexpr int kGFix = 64;                // steps a segment is walked again before the check
 constexpr int kGSkew = 16;               // bytes between the cost rings of two lines (bank skew)
 
 // labels of the wide (whole-warp) form: LPLW per lane, >= D
@@ -43,12 +56,12 @@ __host__ __device__ constexpr int grp_dp() { return 32 * LPLW; }
 // 16-bit entries of one state row
 template <int LPLW>
 __host__ __device__ constexpr int grp_row() { return kGPadL + grp_dp<LPLW>() + kGPadR; }
-// shared memory of one warp in 32-bit words, for NG lines: state rows (2 per line), cost ring,
-// descriptor ring
+// shared memory of one warp in 32-bit words, for NG lines: state rows (2 per line), checkpoints
+// (one state per line), cost ring, descriptor ring
 template <int LPLW, int NG>
 __host__ __device__ constexpr int grp_words_ng() {
-    return NG * (grp_row<LPLW>() + 32) + NG * (kGSlots * grp_dp<LPLW>() + kGSkew) / 4 +
-           2 * kGBlk * NG * 2;
+    return NG * (grp_row<LPLW>() + 32) + NG * grp_dp<LPLW>() / 2 +
+           NG * (kGSlots * grp_dp<LPLW>() + kGSkew) / 4 + 2 * kGBlk * NG * 2;
 }
 
 // Word offset of line g's two state rows (ROW / 2 words each, inside the line's ROW + 32 words).
@@ -83,13 +96,15 @@ __device__ __forceinline__ uint32_t grp_t(uint32_t a0, uint32_t a1, uint32_t P1x
     return vmin2(t, mP2);
 }
 
-// NG lines of direction `code`, lines first_line .. first_line + NG - 1 (those < nlines), one
-// group of GL lanes each. Lv: the direction's volume; wsm: this warp's shared memory.
+// NG / S lines of direction `code`, lines first_line .. (those < nlines), S segments each (S
+// divides NG; the caller keeps every line at least 16 S steps long when S > 1), one group of GL
+// lanes per segment: group g walks segment g % S of line first_line + g / S. Lv: the direction's
+// volume; wsm: this warp's shared memory (grp_words_ng<LPLW, NG>).
 template <int LPLW, int GL>
 __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                                                 const uint2* __restrict__ desc, int W, int Hh,
                                                 int P1, int P2, int code, int first_line,
-                                                int nlines, uint8_t* __restrict__ Lv,
+                                                int nlines, int S, uint8_t* __restrict__ Lv,
                                                 uint32_t* const wsm) {
     static_assert(GL == 4 || GL == 8, "lanes per line");
     static_assert(LPLW == 2 || LPLW == 4 || LPLW == 8, "labels per lane of the wide form");
@@ -97,42 +112,54 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     constexpr int CAPN = 4 * GL;          // labels of the narrow form
     constexpr int DP = grp_dp<LPLW>();    // labels of the wide form
     constexpr int ROW = grp_row<LPLW>();  // entries of a state row
+    constexpr int CKW = DP / 2;           // words of a checkpoint
     constexpr int PF = kGPref, NS = kGSlots;
     constexpr int PER = kGBlk / GL;       // descriptors each lane loads per block
     static_assert(CAPN + 16 <= DP + kGPadR, "narrow padding inside the row");
+    static_assert(kGBlk - PF > PF, "descriptor blocks arrive in time");
     const int lane = threadIdx.x & 31;
     const int g = lane / GL, j = lane % GL;
+    const unsigned gmask = ((1u << GL) - 1u) << (g * GL);
 
     // state rows: line g's two rows start at word grp_row_base(g) (bank-skewed, 4-byte aligned)
     auto row_of = [&](int gi, int which) -> uint16_t* {
         return reinterpret_cast<uint16_t*>(wsm + grp_row_base<LPLW, NG>(gi) + which * (ROW / 2));
     };
-    constexpr int RS = NS * DP + kGSkew;  // bytes of one line's cost ring
-    uint8_t* const ring = reinterpret_cast<uint8_t*>(wsm + NG * (ROW + 32));  // [NG][RS]
-    uint2* const dring = reinterpret_cast<uint2*>(ring + NG * RS);       // [2][kGBlk][NG]
+    uint32_t* const ckpt = wsm + NG * (ROW + 32) + g * CKW;  // this group's checkpoint
+    constexpr int RS = NS * DP + kGSkew;  // bytes of one group's cost ring
+    uint8_t* const ring = reinterpret_cast<uint8_t*>(wsm + NG * (ROW + 32) + NG * CKW);
+    uint2* const dring = reinterpret_cast<uint2*>(ring + NG * RS);  // [2][kGBlk][NG]
 
-    const int l = first_line + g;
-    int i0 = 0, stp = 0, len = 0;
-    if (l < nlines) line_geometry(code, l, W, Hh, i0, stp, len);
-    const int maxlen = (int)__reduce_max_sync(kFull, (unsigned)len);
-    if (maxlen == 0) return;
+    const int li = first_line + g / S, sg = g % S;
+    int i0 = 0, stp = 0, llen = 0;
+    if (li < nlines) line_geometry(code, li, W, Hh, i0, stp, llen);
+    // segment 0 is the shortest, so that every later one ends at the same step
+    int slen = llen, p0 = i0;
+    if (S > 1 && llen > 0) {
+        const int Lseg = (llen + S - 1) / S, len0 = llen - (S - 1) * Lseg;
+        slen = sg == 0 ? len0 : Lseg;
+        p0 = i0 + (sg == 0 ? 0 : len0 + (sg - 1) * Lseg) * stp;
+    }
+    if (__reduce_max_sync(kFull, (unsigned)slen) == 0u) return;
+    // the step after which a later segment's state is saved (first walk) or compared (again)
+    const int cstep = (S > 1 && sg > 0) ? min(kGFix, slen) - 1 : -1;
 
     for (int t = lane; t < NG * (ROW + 32); t += 32) wsm[t] = kInf2;
 
     auto dslot = [&](int s) -> uint2* {
-        return dring + (((s >> 5) & 1) * kGBlk + (s & 31)) * NG + g;
+        return dring + (((s / kGBlk) & 1) * kGBlk + (s % kGBlk)) * NG + g;
     };
     auto load_block = [&](int b) {
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int s = b * kGBlk + j * PER + q;
-            if (s < len) cp_async8(dslot(s), desc + (i0 + s * stp));
+            if (s < slen) cp_async8(dslot(s), desc + (p0 + s * stp));
         }
     };
-    // the costs of step s (its whole window, whole 4-byte words) into the line's ring slot; one
+    // the costs of step s (its whole window, whole 4-byte words) into the group's ring slot; one
     // commit group per call
-    auto issue = [&](int s) {
-        if (s < len) {
+    auto issue = [&](int s, bool walking) {
+        if (walking && s < slen) {
             const uint2 ds = *dslot(s);
             const int nw = ((int)(ds.y >> 16) + 3) >> 2;
             uint8_t* const slot = ring + g * RS + (s % NS) * DP;
@@ -141,144 +168,258 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         cp_async_commit();
     };
 
-    load_block(0);
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncwarp();
-    load_block(1);
-    for (int s = 0; s < PF; ++s) issue(s);
-
     const uint32_t P1x2 = ((uint32_t)P1 << 16) | (uint32_t)P1;
     const uint32_t P2x2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
-    // predecessor of the first step: all +inf, m = 0 and no P2 term, so that L = C
-    int lo_old = 0, cap_old = 0;
+    // predecessor of a first step: all +inf, m = 0 and no P2 term, so that L = C
+    int lo_old = 0, w_old = 0, cap_old = 0;  // the state's window and its row's labels
     uint32_t mm2 = 0u, mP2 = 0u;
-    int cur = 0;
+    int cur = 0;             // which of the group's rows holds its state
+    int pg = g, pw = 0;      // the row holding the predecessor of the next step (group, which)
+    int ck_lo = 0, ck_w = 0;
+    bool walker = slen > 0;  // this group walks in the current pass
 
-    for (int k = 0; k < maxlen; ++k) {
-        if (k > 0 && (k & 31) == 0) load_block((k >> 5) + 1);
-        issue(k + PF);
-        cp_async_wait<PF>();  // this lane's copies of step k (and older) have landed
-        __syncwarp();         // ... and every lane's
-        const bool act = k < len;
-        const uint2 ds = act ? *dslot(k) : make_uint2(0u, 0u);
-        const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
-        const bool wide = w > CAPN;
-
-        // ---- narrow step of this lane's line (computed everywhere, stored where it applies) ----
-        {
-            const uint16_t* const rold = row_of(g, cur);
-            uint16_t* const rnew = row_of(g, cur ^ 1);
-            const int e = min(max(lo - lo_old + 4 * j - 1, -6), cap_old);
-            const int b = kGPadL + e;
-            const uint32_t* r32 = reinterpret_cast<const uint32_t*>(rold) + (b >> 1);
-            const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
-            const uint32_t w0 = r32[0], w1 = r32[1], w2 = r32[2], w3 = r32[3];
-            const uint32_t A0 = __byte_perm(w0, w1, sel), A1 = __byte_perm(w1, w2, sel),
-                           A2 = __byte_perm(w2, w3, sel);
-            const uint32_t cw =
-                *reinterpret_cast<const uint32_t*>(ring + g * RS + (k % NS) * DP + 4 * j);
-            const int rem = w - 4 * j;
-            const uint32_t k0 = pair_keep(rem), k1 = pair_keep(rem - 2);
-            uint32_t L0 = (__byte_perm(cw, 0u, 0x4140) + grp_t(A0, A1, P1x2, mP2)) - mm2;
-            uint32_t L1 = (__byte_perm(cw, 0u, 0x4342) + grp_t(A1, A2, P1x2, mP2)) - mm2;
-            L0 = (L0 & k0) | (kInf2 & ~k0);
-            L1 = (L1 & k1) | (kInf2 & ~k1);
-            const uint32_t pm = vmin2(L0, L1);
-            int m = (int)min(pm & 0xFFFFu, pm >> 16);
-#pragma unroll
-            for (int s = 1; s < GL; s <<= 1) m = min(m, __shfl_xor_sync(kFull, m, s));
-            if (act && !wide) {
-                uint32_t* const rw = reinterpret_cast<uint32_t*>(rnew + kGPadL);
-                rw[2 * j] = L0;
-                rw[2 * j + 1] = L1;
-                if (j < 4) {
-                    rw[CAPN / 2 + 2 * j] = kInf2;
-                    rw[CAPN / 2 + 2 * j + 1] = kInf2;
+    for (int pass = 0;; ++pass) {
+        load_block(0);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        load_block(1);
+        for (int s = 0; s < PF; ++s) issue(s, walker);
+        bool stop = false;      // the walk of this pass ended at the check (the states agreed)
+        bool changed = false;   // this pass changed the segment's end state
+        for (int k = 0;; ++k) {
+            // the check after step cstep: save the state (first walk) or compare with it
+            if (__any_sync(kFull, walker && k == cstep + 1)) {
+                const bool mine = walker && k == cstep + 1;
+                const uint32_t* const rw =
+                    reinterpret_cast<const uint32_t*>(row_of(g, cur) + kGPadL);
+                // the state is L over the window (lo, w); entries past w are +inf in every row
+                bool eq = lo_old == ck_lo && w_old == ck_w;
+                if (mine) {
+                    for (int t = j; t < (w_old + 1) / 2; t += GL) {
+                        if (pass == 0) ckpt[t] = rw[t];
+                        else eq = eq && ckpt[t] == rw[t];
+                    }
+                    if (pass == 0) {
+                        ck_lo = lo_old;
+                        ck_w = w_old;
+                    }
                 }
-                if (rem > 0)
-                    *reinterpret_cast<uint32_t*>(Lv + ds.x + 4 * j) = __byte_perm(L0, L1, 0x6420);
-                lo_old = lo;
-                cap_old = CAPN;
-                mm2 = (uint32_t)m * 0x10001u;
-                mP2 = mm2 + P2x2;
+                const bool same = (__ballot_sync(kFull, !eq) & gmask) == 0u;
+                if (mine && pass > 0) {
+                    stop = same;
+                    changed = !same;
+                }
+            }
+            const bool go = walker && !stop && k < slen;
+            if (!__any_sync(kFull, go)) break;
+            if (k > 0 && (k % kGBlk) == 0) load_block(k / kGBlk + 1);
+            issue(k + PF, walker && !stop);
+            cp_async_wait<PF>();  // this lane's copies of step k (and older) have landed
+            __syncwarp();         // ... and every lane's
+            const uint2 ds = go ? *dslot(k) : make_uint2(0u, 0u);
+            const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
+            const bool wide = w > CAPN;
+            const unsigned wb0 = __ballot_sync(kFull, go && wide && j == 0);
+
+            if (__popc(wb0) >= 2) {
+                // ---- dense step: every group its own window with its own lanes, DP / GL labels
+                // per lane, in chunks of 8 (several wide windows at once: the full-range band at
+                // the image border, a full-range frame)
+                constexpr int LPD = DP / GL;
+                const uint16_t* const rold = row_of(pg, pw);
+                uint32_t* const rw = reinterpret_cast<uint32_t*>(row_of(g, cur ^ 1) + kGPadL);
+                const uint8_t* const cs = ring + g * RS + (k % NS) * DP;
+                uint32_t pm = kInf2;
+#pragma unroll
+                for (int c = 0; c < LPD / 8; ++c) {
+                    const int base = LPD * j + 8 * c;  // first label of the chunk, from lo
+                    const int e = min(max(lo - lo_old + base - 1, -10), cap_old);
+                    const int b = kGPadL + e;
+                    const uint32_t* r32 = reinterpret_cast<const uint32_t*>(rold) + (b >> 1);
+                    const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
+                    uint32_t wv[6], A[5];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) wv[i] = r32[i];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel);
+                    const uint32_t c4a = *reinterpret_cast<const uint32_t*>(cs + base);
+                    const uint32_t c4b = *reinterpret_cast<const uint32_t*>(cs + base + 4);
+                    const uint32_t cp[4] = {__byte_perm(c4a, 0u, 0x4140), __byte_perm(c4a, 0u, 0x4342),
+                                            __byte_perm(c4b, 0u, 0x4140), __byte_perm(c4b, 0u, 0x4342)};
+                    const int rem = w - base;
+                    uint32_t Lc[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t kp = pair_keep(rem - 2 * i);
+                        const uint32_t v = (cp[i] + grp_t(A[i], A[i + 1], P1x2, mP2)) - mm2;
+                        Lc[i] = (v & kp) | (kInf2 & ~kp);
+                        pm = vmin2(pm, Lc[i]);
+                    }
+                    if (go) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) rw[base / 2 + i] = Lc[i];
+                        if (rem > 0)
+                            *reinterpret_cast<uint32_t*>(Lv + ds.x + base) = __byte_perm(Lc[0], Lc[1], 0x6420);
+                        if (rem > 4)
+                            *reinterpret_cast<uint32_t*>(Lv + ds.x + base + 4) =
+                                __byte_perm(Lc[2], Lc[3], 0x6420);
+                    }
+                }
+                int m = (int)min(pm & 0xFFFFu, pm >> 16);
+#pragma unroll
+                for (int s = 1; s < GL; s <<= 1) m = min(m, __shfl_xor_sync(kFull, m, s));
+                if (go) {
+                    lo_old = lo;
+                    w_old = w;
+                    cap_old = DP;
+                    mm2 = (uint32_t)m * 0x10001u;
+                    mP2 = mm2 + P2x2;
+                }
+            } else {
+            // ---- narrow step of this group's line (computed everywhere, stored where it applies)
+            {
+                const uint16_t* const rold = row_of(pg, pw);
+                uint16_t* const rnew = row_of(g, cur ^ 1);
+                const int e = min(max(lo - lo_old + 4 * j - 1, -6), cap_old);
+                const int b = kGPadL + e;
+                const uint32_t* r32 = reinterpret_cast<const uint32_t*>(rold) + (b >> 1);
+                const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
+                const uint32_t w0 = r32[0], w1 = r32[1], w2 = r32[2], w3 = r32[3];
+                const uint32_t A0 = __byte_perm(w0, w1, sel), A1 = __byte_perm(w1, w2, sel),
+                               A2 = __byte_perm(w2, w3, sel);
+                const uint32_t cw =
+                    *reinterpret_cast<const uint32_t*>(ring + g * RS + (k % NS) * DP + 4 * j);
+                const int rem = w - 4 * j;
+                const uint32_t k0 = pair_keep(rem), k1 = pair_keep(rem - 2);
+                uint32_t L0 = (__byte_perm(cw, 0u, 0x4140) + grp_t(A0, A1, P1x2, mP2)) - mm2;
+                uint32_t L1 = (__byte_perm(cw, 0u, 0x4342) + grp_t(A1, A2, P1x2, mP2)) - mm2;
+                L0 = (L0 & k0) | (kInf2 & ~k0);
+                L1 = (L1 & k1) | (kInf2 & ~k1);
+                const uint32_t pm = vmin2(L0, L1);
+                int m = (int)min(pm & 0xFFFFu, pm >> 16);
+#pragma unroll
+                for (int s = 1; s < GL; s <<= 1) m = min(m, __shfl_xor_sync(kFull, m, s));
+                if (go && !wide) {
+                    uint32_t* const rw = reinterpret_cast<uint32_t*>(rnew + kGPadL);
+                    rw[2 * j] = L0;
+                    rw[2 * j + 1] = L1;
+                    if (j < 4) {
+                        rw[CAPN / 2 + 2 * j] = kInf2;
+                        rw[CAPN / 2 + 2 * j + 1] = kInf2;
+                    }
+                    if (rem > 0)
+                        *reinterpret_cast<uint32_t*>(Lv + ds.x + 4 * j) = __byte_perm(L0, L1, 0x6420);
+                    lo_old = lo;
+                    w_old = w;
+                    cap_old = CAPN;
+                    mm2 = (uint32_t)m * 0x10001u;
+                    mP2 = mm2 + P2x2;
+                }
+            }
+
+            // ---- a single wide window: the whole warp ----
+            unsigned wb = wb0;
+            while (wb) {
+                const int gg = (__ffs(wb) - 1) / GL;
+                wb &= wb - 1;
+                const int src = gg * GL;
+                const int lo_g = __shfl_sync(kFull, lo, src), w_g = __shfl_sync(kFull, w, src);
+                const uint32_t o_g = __shfl_sync(kFull, ds.x, src);
+                const int lo_old_g = __shfl_sync(kFull, lo_old, src);
+                const int cap_old_g = __shfl_sync(kFull, cap_old, src);
+                const uint32_t mm2_g = __shfl_sync(kFull, mm2, src);
+                const uint32_t mP2_g = __shfl_sync(kFull, mP2, src);
+                const int pg_g = __shfl_sync(kFull, pg, src), pw_g = __shfl_sync(kFull, pw, src);
+                const int cur_g = __shfl_sync(kFull, cur, src);
+                const uint16_t* const rold = row_of(pg_g, pw_g);
+                uint16_t* const rnew = row_of(gg, cur_g ^ 1);
+                constexpr int NPW = LPLW / 2;  // packed pairs per lane
+                const int e = min(max(lo_g - lo_old_g + LPLW * lane - 1, -(LPLW + 2)), cap_old_g);
+                const int b = kGPadL + e;
+                const uint32_t* r32 = reinterpret_cast<const uint32_t*>(rold) + (b >> 1);
+                const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
+                uint32_t wv[NPW + 2], A[NPW + 1];
+#pragma unroll
+                for (int i = 0; i < NPW + 2; ++i) wv[i] = r32[i];
+#pragma unroll
+                for (int i = 0; i < NPW + 1; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel);
+                const uint8_t* const cs = ring + gg * RS + (k % NS) * DP + LPLW * lane;
+                uint32_t cpk[NPW];
+                if constexpr (LPLW == 2) {
+                    cpk[0] = __byte_perm((uint32_t)*reinterpret_cast<const uint16_t*>(cs), 0u, 0x4140);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < LPLW / 4; ++q) {
+                        const uint32_t c4 = reinterpret_cast<const uint32_t*>(cs)[q];
+                        cpk[2 * q] = __byte_perm(c4, 0u, 0x4140);
+                        cpk[2 * q + 1] = __byte_perm(c4, 0u, 0x4342);
+                    }
+                }
+                const int rem = w_g - LPLW * lane;
+                uint32_t Lw[NPW];
+                uint32_t pm = kInf2;
+#pragma unroll
+                for (int i = 0; i < NPW; ++i) {
+                    const uint32_t kp = pair_keep(rem - 2 * i);
+                    const uint32_t v = (cpk[i] + grp_t(A[i], A[i + 1], P1x2, mP2_g)) - mm2_g;
+                    Lw[i] = (v & kp) | (kInf2 & ~kp);
+                    pm = vmin2(pm, Lw[i]);
+                }
+                const int mg = (int)__reduce_min_sync(kFull, min(pm & 0xFFFFu, pm >> 16));
+                uint16_t* const dst = rnew + kGPadL + LPLW * lane;
+                if constexpr (LPLW == 2) {
+                    *reinterpret_cast<uint32_t*>(dst) = Lw[0];
+                    if (rem > 0)
+                        *reinterpret_cast<uint16_t*>(Lv + o_g + 2 * lane) =
+                            (uint16_t)__byte_perm(Lw[0], 0u, 0x0020);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < LPLW / 4; ++q) {
+                        reinterpret_cast<uint32_t*>(dst)[2 * q] = Lw[2 * q];
+                        reinterpret_cast<uint32_t*>(dst)[2 * q + 1] = Lw[2 * q + 1];
+                        if (rem > 4 * q)
+                            *reinterpret_cast<uint32_t*>(Lv + o_g + LPLW * lane + 4 * q) =
+                                __byte_perm(Lw[2 * q], Lw[2 * q + 1], 0x6420);
+                    }
+                }
+                if (g == gg) {
+                    lo_old = lo_g;
+                    w_old = w_g;
+                    cap_old = DP;
+                    mm2 = (uint32_t)mg * 0x10001u;
+                    mP2 = mm2 + P2x2;
+                }
+            }
+            }
+            if (go) {
+                cur ^= 1;
+                pg = g;
+                pw = cur;
             }
         }
-
-        // ---- wide windows: the whole warp, one line after the other ----
-        unsigned wb = __ballot_sync(kFull, act && wide && j == 0);
-        while (wb) {
-            const int gg = (__ffs(wb) - 1) / GL;
-            wb &= wb - 1;
-            const int src = gg * GL;
-            const int lo_g = __shfl_sync(kFull, lo, src), w_g = __shfl_sync(kFull, w, src);
-            const uint32_t o_g = __shfl_sync(kFull, ds.x, src);
-            const int lo_old_g = __shfl_sync(kFull, lo_old, src);
-            const int cap_old_g = __shfl_sync(kFull, cap_old, src);
-            const uint32_t mm2_g = __shfl_sync(kFull, mm2, src);
-            const uint32_t mP2_g = __shfl_sync(kFull, mP2, src);
-            const uint16_t* const rold = row_of(gg, cur);
-            uint16_t* const rnew = row_of(gg, cur ^ 1);
-            constexpr int NPW = LPLW / 2;  // packed pairs per lane
-            const int e = min(max(lo_g - lo_old_g + LPLW * lane - 1, -(LPLW + 2)), cap_old_g);
-            const int b = kGPadL + e;
-            const uint32_t* r32 = reinterpret_cast<const uint32_t*>(rold) + (b >> 1);
-            const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
-            uint32_t wv[NPW + 2], A[NPW + 1];
-#pragma unroll
-            for (int i = 0; i < NPW + 2; ++i) wv[i] = r32[i];
-#pragma unroll
-            for (int i = 0; i < NPW + 1; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel);
-            const uint8_t* const cs = ring + gg * RS + (k % NS) * DP + LPLW * lane;
-            uint32_t cpk[NPW];
-            if constexpr (LPLW == 2) {
-                cpk[0] = __byte_perm((uint32_t)*reinterpret_cast<const uint16_t*>(cs), 0u, 0x4140);
-            } else {
-#pragma unroll
-                for (int q = 0; q < LPLW / 4; ++q) {
-                    const uint32_t c4 = reinterpret_cast<const uint32_t*>(cs)[q];
-                    cpk[2 * q] = __byte_perm(c4, 0u, 0x4140);
-                    cpk[2 * q + 1] = __byte_perm(c4, 0u, 0x4342);
-                }
-            }
-            const int rem = w_g - LPLW * lane;
-            uint32_t Lw[NPW];
-            uint32_t pm = kInf2;
-#pragma unroll
-            for (int i = 0; i < NPW; ++i) {
-                const uint32_t kp = pair_keep(rem - 2 * i);
-                const uint32_t v = (cpk[i] + grp_t(A[i], A[i + 1], P1x2, mP2_g)) - mm2_g;
-                Lw[i] = (v & kp) | (kInf2 & ~kp);
-                pm = vmin2(pm, Lw[i]);
-            }
-            const int mg = (int)__reduce_min_sync(kFull, min(pm & 0xFFFFu, pm >> 16));
-            uint16_t* const dst = rnew + kGPadL + LPLW * lane;
-            if constexpr (LPLW == 2) {
-                *reinterpret_cast<uint32_t*>(dst) = Lw[0];
-                if (rem > 0)
-                    *reinterpret_cast<uint16_t*>(Lv + o_g + 2 * lane) =
-                        (uint16_t)__byte_perm(Lw[0], 0u, 0x0020);
-            } else {
-#pragma unroll
-                for (int q = 0; q < LPLW / 4; ++q) {
-                    reinterpret_cast<uint32_t*>(dst)[2 * q] = Lw[2 * q];
-                    reinterpret_cast<uint32_t*>(dst)[2 * q + 1] = Lw[2 * q + 1];
-                    if (rem > 4 * q)
-                        *reinterpret_cast<uint32_t*>(Lv + o_g + LPLW * lane + 4 * q) =
-                            __byte_perm(Lw[2 * q], Lw[2 * q + 1], 0x6420);
-                }
-            }
-            if (g == gg) {
-                lo_old = lo_g;
-                cap_old = DP;
-                mm2 = (uint32_t)mg * 0x10001u;
-                mP2 = mm2 + P2x2;
-            }
+        cp_async_wait<0>();
+        __syncwarp();
+        // the next pass: the later segments (first walk done), then every segment whose
+        // predecessor's end state changed in this pass, from that end state
+        const int src = (sg > 0 ? g - 1 : g) * GL;
+        const bool pchanged = __shfl_sync(kFull, (int)changed, src) != 0;
+        const int plo = __shfl_sync(kFull, lo_old, src), pcap = __shfl_sync(kFull, cap_old, src);
+        const int pwid = __shfl_sync(kFull, w_old, src);
+        const uint32_t pmm2 = __shfl_sync(kFull, mm2, src), pmP2 = __shfl_sync(kFull, mP2, src);
+        const int pcur = __shfl_sync(kFull, cur, src);
+        walker = sg > 0 && slen > 0 && (pass == 0 || pchanged);
+        if (!__any_sync(kFull, walker)) break;
+        if (walker) {
+            lo_old = plo;
+            w_old = pwid;
+            cap_old = pcap;
+            mm2 = pmm2;
+            mP2 = pmP2;
+            pg = g - 1;
+            pw = pcur;
         }
-        cur ^= 1;
     }
-    cp_async_wait<0>();
-    __syncwarp();
 }
 
 // Lines of one image for the grouped walker: direction codes in launch order (horizontal pairs
@@ -286,20 +427,33 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
 struct GrpLines {
     int code[8];
     int count[8];
+    int seg[8];  // segments per line (1, 2 or 4)
     int nslots;
 };
 
-// Map warp gw of the launch to (direction code, first line, line count) for NG lines per warp;
-// false when gw is past the last line.
+// Segments per horizontal line of a W x Hh image: the lines are cut so that a segment (plus its
+// second walk) is about as long as the other directions' lines, at most 4 and only where every
+// segment stays at least 64 steps long.
+__host__ __device__ __forceinline__ int grp_hseg(int W, int Hh) {
+    const int target = Hh > 256 ? Hh : 256;
+    int S = 1;
+    while (S < 4 && W > S * target && W >= 2 * S * 64) S *= 2;
+    return S;
+}
+
+// Map warp gw of the launch to (direction code, first line, line count, segments) for NG groups
+// per warp (NG / seg lines); false when gw is past the last line.
 __device__ __forceinline__ bool grp_warp_lines(const GrpLines& L, int NG, int gw, int& code,
-                                               int& first, int& nlines) {
+                                               int& first, int& nlines, int& seg) {
     int base = 0;
     for (int s = 0; s < L.nslots; ++s) {
-        const int nw = (L.count[s] + NG - 1) / NG;
+        const int per = NG / L.seg[s];
+        const int nw = (L.count[s] + per - 1) / per;
         if (gw < base + nw) {
             code = L.code[s];
-            first = (gw - base) * NG;
+            first = (gw - base) * per;
             nlines = L.count[s];
+            seg = L.seg[s];
             return true;
         }
         base += nw;

@@ -149,6 +149,15 @@ CASES = [
     (45, 17, 64, (5, 5), 4, ("rand", 1, 1, 1.0)),
     (33, 9, 37, (5, 5), 8, ("rand", 1, 1, 1.0)),
     (40, 12, 200, (9, 7), 8, ("rand", 1, 1, 1.0)),
+    # long horizontal lines walked in segments from guessed starts (2 or 4 per line): with the
+    # 3x3 census the costs are small against P1, P2, so a guessed start often does not agree
+    # with the true state within the re-walk and the correction goes on to the segment's end and
+    # into the next segment (several passes)
+    (600, 8, 64, (3, 3), 8, ("rand", 1, 1, 1.0)),
+    (700, 12, 128, (3, 3), 4, ("mixed", (1, 16), (17, 40), 0.02, 0.03)),
+    (300, 20, 128, (9, 7), 8, ("mixed", (3, 12), (17, 32), 0.0, 0.0)),
+    (1300, 6, 256, (5, 5), 4, ("rand", 1, 1, 1.0)),
+    (1242, 16, 128, (9, 7), 8, ("border", (3, 12), 35)),
 ]
 
 
