@@ -115,20 +115,22 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     constexpr int CKW = DP / 2;           // words of a checkpoint
     constexpr int PF = kGPref, NS = kGSlots;
     constexpr int PER = kGBlk / GL;       // descriptors each lane loads per block
+    constexpr int RS = NS * DP + kGSkew;  // bytes of one group's cost ring
     static_assert(CAPN + 16 <= DP + kGPadR, "narrow padding inside the row");
-    static_assert(kGBlk - PF > PF, "descriptor blocks arrive in time");
+    static_assert(kGBlk - PF > PF + 1, "descriptor blocks arrive in time");
+    static_assert(2 * kGBlk == 32 && NS == 8, "ring indices are masks");
     const int lane = threadIdx.x & 31;
     const int g = lane / GL, j = lane % GL;
     const unsigned gmask = ((1u << GL) - 1u) << (g * GL);
 
-    // state rows: line g's two rows start at word grp_row_base(g) (bank-skewed, 4-byte aligned)
-    auto row_of = [&](int gi, int which) -> uint16_t* {
-        return reinterpret_cast<uint16_t*>(wsm + grp_row_base<LPLW, NG>(gi) + which * (ROW / 2));
-    };
-    uint32_t* const ckpt = wsm + NG * (ROW + 32) + g * CKW;  // this group's checkpoint
-    constexpr int RS = NS * DP + kGSkew;  // bytes of one group's cost ring
+    // shared memory of this group: two state rows (bank-skewed), checkpoint, cost ring slots,
+    // descriptor ring column (entry s at dcol[(s & 31) * NG])
+    uint32_t* const rowA = wsm + grp_row_base<LPLW, NG>(g);
+    uint32_t* const rowB = rowA + ROW / 2;
+    uint32_t* const ckpt = wsm + NG * (ROW + 32) + g * CKW;
     uint8_t* const ring = reinterpret_cast<uint8_t*>(wsm + NG * (ROW + 32) + NG * CKW);
-    uint2* const dring = reinterpret_cast<uint2*>(ring + NG * RS);  // [2][kGBlk][NG]
+    uint8_t* const cring = ring + g * RS;
+    uint2* const dcol = reinterpret_cast<uint2*>(ring + NG * RS) + g;
 
     const int li = first_line + g / S, sg = g % S;
     int i0 = 0, stp = 0, llen = 0;
@@ -140,31 +142,32 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         slen = sg == 0 ? len0 : Lseg;
         p0 = i0 + (sg == 0 ? 0 : len0 + (sg - 1) * Lseg) * stp;
     }
-    if (__reduce_max_sync(kFull, (unsigned)slen) == 0u) return;
-    // the step after which a later segment's state is saved (first walk) or compared (again)
+    const int maxslen = (int)__reduce_max_sync(kFull, (unsigned)slen);
+    if (maxslen == 0) return;
+    // the step after which a later segment's state is saved (first walk) or compared (again);
+    // all later segments of the warp's lines have the same length, so the check is one step
     const int cstep = (S > 1 && sg > 0) ? min(kGFix, slen) - 1 : -1;
+    const int cchk = (int)__reduce_max_sync(kFull, (unsigned)(cstep + 1));  // 0: no check
 
     for (int t = lane; t < NG * (ROW + 32); t += 32) wsm[t] = kInf2;
 
-    auto dslot = [&](int s) -> uint2* {
-        return dring + (((s / kGBlk) & 1) * kGBlk + (s % kGBlk)) * NG + g;
-    };
     auto load_block = [&](int b) {
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int s = b * kGBlk + j * PER + q;
-            if (s < slen) cp_async8(dslot(s), desc + (p0 + s * stp));
+            if (s < slen) cp_async8(dcol + (s & 31) * NG, desc + (p0 + s * stp));
         }
     };
-    // the costs of step s (its whole window, whole 4-byte words) into the group's ring slot; one
-    // commit group per call
-    auto issue = [&](int s, bool walking) {
-        if (walking && s < slen) {
-            const uint2 ds = *dslot(s);
-            const int nw = ((int)(ds.y >> 16) + 3) >> 2;
-            uint8_t* const slot = ring + g * RS + (s % NS) * DP;
-            for (int t = j; t < nw; t += GL) cp_async4(slot + 4 * t, C + ds.x + 4 * t);
-        }
+    auto dread = [&](int s, bool walking) -> uint2 {
+        return (walking && s < slen) ? dcol[(s & 31) * NG] : make_uint2(0u, 0u);
+    };
+    // the costs of a step with descriptor dsc (its whole window, whole 4-byte words) into ring
+    // slot `slot`; one commit group per call
+    auto issue = [&](uint2 dsc, int slot) {
+        const int nw = ((int)(dsc.y >> 16) + 3) >> 2;
+        uint8_t* const dst = cring + slot * DP;
+        if (j < nw) cp_async4(dst + 4 * j, C + dsc.x + 4 * j);
+        for (int t = j + GL; t < nw; t += GL) cp_async4(dst + 4 * t, C + dsc.x + 4 * t);
         cp_async_commit();
     };
 
@@ -173,8 +176,8 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     // predecessor of a first step: all +inf, m = 0 and no P2 term, so that L = C
     int lo_old = 0, w_old = 0, cap_old = 0;  // the state's window and its row's labels
     uint32_t mm2 = 0u, mP2 = 0u;
-    int cur = 0;             // which of the group's rows holds its state
-    int pg = g, pw = 0;      // the row holding the predecessor of the next step (group, which)
+    const uint32_t* prow = rowA;  // the predecessor of the next step
+    uint32_t* nrow = rowB;        // the row the next step writes
     int ck_lo = 0, ck_w = 0;
     bool walker = slen > 0;  // this group walks in the current pass
 
@@ -184,21 +187,25 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         cp_async_wait<0>();
         __syncwarp();
         load_block(1);
-        for (int s = 0; s < PF; ++s) issue(s, walker);
-        bool stop = false;      // the walk of this pass ended at the check (the states agreed)
-        bool changed = false;   // this pass changed the segment's end state
+        for (int t = 0; t < PF; ++t) issue(dread(t, walker), t);
+        bool stop = false;     // the walk of this pass ended at the check (the states agreed)
+        bool changed = false;  // this pass changed the segment's end state
+        int kend = pass == 0 ? maxslen : cchk;
+        // software pipeline: the next step's descriptor (dn) and wide vote (wbn), and the
+        // descriptor of the step whose costs are issued next (dp)
+        uint2 dn = dread(0, walker), dp = dread(PF, walker);
+        unsigned wbn = __ballot_sync(kFull, walker && (int)(dn.y >> 16) > CAPN && j == 0);
         for (int k = 0;; ++k) {
-            // the check after step cstep: save the state (first walk) or compare with it
-            if (__any_sync(kFull, walker && k == cstep + 1)) {
-                const bool mine = walker && k == cstep + 1;
-                const uint32_t* const rw =
-                    reinterpret_cast<const uint32_t*>(row_of(g, cur) + kGPadL);
-                // the state is L over the window (lo, w); entries past w are +inf in every row
+            if (k == cchk) {
+                // the check after step cstep: save the state (first walk) or compare with it;
+                // the state is L over the window (lo, w), entries past w are +inf in every row
+                const bool mine = walker && cstep + 1 == k;
                 bool eq = lo_old == ck_lo && w_old == ck_w;
                 if (mine) {
                     for (int t = j; t < (w_old + 1) / 2; t += GL) {
-                        if (pass == 0) ckpt[t] = rw[t];
-                        else eq = eq && ckpt[t] == rw[t];
+                        const uint32_t v = prow[kGPadL / 2 + t];
+                        if (pass == 0) ckpt[t] = v;
+                        else eq = eq && ckpt[t] == v;
                     }
                     if (pass == 0) {
                         ck_lo = lo_old;
@@ -210,41 +217,44 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     stop = same;
                     changed = !same;
                 }
+                if (pass > 0 && __any_sync(kFull, changed)) kend = maxslen;
             }
+            if (k >= kend) break;
             const bool go = walker && !stop && k < slen;
-            if (!__any_sync(kFull, go)) break;
-            if (k > 0 && (k % kGBlk) == 0) load_block(k / kGBlk + 1);
-            issue(k + PF, walker && !stop);
+            const uint2 ds = dn;
+            unsigned wb0 = wbn;                               // voted a step ahead ...
+            if (k == cchk) wb0 &= __ballot_sync(kFull, go);   // ... before a walk stopped here
+            if (k > 0 && (k & (kGBlk - 1)) == 0) load_block(k / kGBlk + 1);
+            issue(dp, (k + PF) & (NS - 1));
+            dp = dread(k + PF + 1, walker && !stop);
             cp_async_wait<PF>();  // this lane's copies of step k (and older) have landed
             __syncwarp();         // ... and every lane's
-            const uint2 ds = go ? *dslot(k) : make_uint2(0u, 0u);
+            dn = dread(k + 1, walker && !stop);
+            wbn = __ballot_sync(kFull, walker && !stop && k + 1 < slen &&
+                                           (int)(dn.y >> 16) > CAPN && j == 0);
             const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
-            const bool wide = w > CAPN;
-            const unsigned wb0 = __ballot_sync(kFull, go && wide && j == 0);
+            const uint8_t* const cslot = cring + (k & (NS - 1)) * DP;
 
             if (__popc(wb0) >= 2) {
                 // ---- dense step: every group its own window with its own lanes, DP / GL labels
                 // per lane, in chunks of 8 (several wide windows at once: the full-range band at
                 // the image border, a full-range frame)
                 constexpr int LPD = DP / GL;
-                const uint16_t* const rold = row_of(pg, pw);
-                uint32_t* const rw = reinterpret_cast<uint32_t*>(row_of(g, cur ^ 1) + kGPadL);
-                const uint8_t* const cs = ring + g * RS + (k % NS) * DP;
                 uint32_t pm = kInf2;
 #pragma unroll
                 for (int c = 0; c < LPD / 8; ++c) {
                     const int base = LPD * j + 8 * c;  // first label of the chunk, from lo
                     const int e = min(max(lo - lo_old + base - 1, -10), cap_old);
                     const int b = kGPadL + e;
-                    const uint32_t* r32 = reinterpret_cast<const uint32_t*>(rold) + (b >> 1);
+                    const uint32_t* r32 = prow + (b >> 1);
                     const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
                     uint32_t wv[6], A[5];
 #pragma unroll
                     for (int i = 0; i < 6; ++i) wv[i] = r32[i];
 #pragma unroll
                     for (int i = 0; i < 5; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel);
-                    const uint32_t c4a = *reinterpret_cast<const uint32_t*>(cs + base);
-                    const uint32_t c4b = *reinterpret_cast<const uint32_t*>(cs + base + 4);
+                    const uint32_t c4a = *reinterpret_cast<const uint32_t*>(cslot + base);
+                    const uint32_t c4b = *reinterpret_cast<const uint32_t*>(cslot + base + 4);
                     const uint32_t cp[4] = {__byte_perm(c4a, 0u, 0x4140), __byte_perm(c4a, 0u, 0x4342),
                                             __byte_perm(c4b, 0u, 0x4140), __byte_perm(c4b, 0u, 0x4342)};
                     const int rem = w - base;
@@ -258,7 +268,7 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     }
                     if (go) {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) rw[base / 2 + i] = Lc[i];
+                        for (int i = 0; i < 4; ++i) nrow[kGPadL / 2 + base / 2 + i] = Lc[i];
                         if (rem > 0)
                             *reinterpret_cast<uint32_t*>(Lv + ds.x + base) = __byte_perm(Lc[0], Lc[1], 0x6420);
                         if (rem > 4)
@@ -268,7 +278,7 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 }
                 int m = (int)min(pm & 0xFFFFu, pm >> 16);
 #pragma unroll
-                for (int s = 1; s < GL; s <<= 1) m = min(m, __shfl_xor_sync(kFull, m, s));
+                for (int t = 1; t < GL; t <<= 1) m = min(m, __shfl_xor_sync(kFull, m, t));
                 if (go) {
                     lo_old = lo;
                     w_old = w;
@@ -277,19 +287,17 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     mP2 = mm2 + P2x2;
                 }
             } else {
-            // ---- narrow step of this group's line (computed everywhere, stored where it applies)
-            {
-                const uint16_t* const rold = row_of(pg, pw);
-                uint16_t* const rnew = row_of(g, cur ^ 1);
+                // ---- narrow step of this group's line (computed everywhere, stored where it
+                // applies)
+                const bool wide = w > CAPN;
                 const int e = min(max(lo - lo_old + 4 * j - 1, -6), cap_old);
                 const int b = kGPadL + e;
-                const uint32_t* r32 = reinterpret_cast<const uint32_t*>(rold) + (b >> 1);
+                const uint32_t* r32 = prow + (b >> 1);
                 const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
                 const uint32_t w0 = r32[0], w1 = r32[1], w2 = r32[2], w3 = r32[3];
                 const uint32_t A0 = __byte_perm(w0, w1, sel), A1 = __byte_perm(w1, w2, sel),
                                A2 = __byte_perm(w2, w3, sel);
-                const uint32_t cw =
-                    *reinterpret_cast<const uint32_t*>(ring + g * RS + (k % NS) * DP + 4 * j);
+                const uint32_t cw = *reinterpret_cast<const uint32_t*>(cslot + 4 * j);
                 const int rem = w - 4 * j;
                 const uint32_t k0 = pair_keep(rem), k1 = pair_keep(rem - 2);
                 uint32_t L0 = (__byte_perm(cw, 0u, 0x4140) + grp_t(A0, A1, P1x2, mP2)) - mm2;
@@ -299,12 +307,12 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 const uint32_t pm = vmin2(L0, L1);
                 int m = (int)min(pm & 0xFFFFu, pm >> 16);
 #pragma unroll
-                for (int s = 1; s < GL; s <<= 1) m = min(m, __shfl_xor_sync(kFull, m, s));
+                for (int t = 1; t < GL; t <<= 1) m = min(m, __shfl_xor_sync(kFull, m, t));
                 if (go && !wide) {
-                    uint32_t* const rw = reinterpret_cast<uint32_t*>(rnew + kGPadL);
+                    uint32_t* const rw = nrow + kGPadL / 2;
                     rw[2 * j] = L0;
                     rw[2 * j + 1] = L1;
-                    if (j < 4) {
+                    if (GL == 4 || j < 4) {
                         rw[CAPN / 2 + 2 * j] = kInf2;
                         rw[CAPN / 2 + 2 * j + 1] = kInf2;
                     }
@@ -316,86 +324,81 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     mm2 = (uint32_t)m * 0x10001u;
                     mP2 = mm2 + P2x2;
                 }
-            }
 
-            // ---- a single wide window: the whole warp ----
-            unsigned wb = wb0;
-            while (wb) {
-                const int gg = (__ffs(wb) - 1) / GL;
-                wb &= wb - 1;
-                const int src = gg * GL;
-                const int lo_g = __shfl_sync(kFull, lo, src), w_g = __shfl_sync(kFull, w, src);
-                const uint32_t o_g = __shfl_sync(kFull, ds.x, src);
-                const int lo_old_g = __shfl_sync(kFull, lo_old, src);
-                const int cap_old_g = __shfl_sync(kFull, cap_old, src);
-                const uint32_t mm2_g = __shfl_sync(kFull, mm2, src);
-                const uint32_t mP2_g = __shfl_sync(kFull, mP2, src);
-                const int pg_g = __shfl_sync(kFull, pg, src), pw_g = __shfl_sync(kFull, pw, src);
-                const int cur_g = __shfl_sync(kFull, cur, src);
-                const uint16_t* const rold = row_of(pg_g, pw_g);
-                uint16_t* const rnew = row_of(gg, cur_g ^ 1);
-                constexpr int NPW = LPLW / 2;  // packed pairs per lane
-                const int e = min(max(lo_g - lo_old_g + LPLW * lane - 1, -(LPLW + 2)), cap_old_g);
-                const int b = kGPadL + e;
-                const uint32_t* r32 = reinterpret_cast<const uint32_t*>(rold) + (b >> 1);
-                const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
-                uint32_t wv[NPW + 2], A[NPW + 1];
+                // ---- a single wide window: the whole warp ----
+                if (wb0) {
+                    const int gg = (__ffs(wb0) - 1) / GL;
+                    const int src = gg * GL;
+                    const int lo_g = __shfl_sync(kFull, lo, src), w_g = __shfl_sync(kFull, w, src);
+                    const uint32_t o_g = __shfl_sync(kFull, ds.x, src);
+                    const int lo_old_g = __shfl_sync(kFull, lo_old, src);
+                    const int cap_old_g = __shfl_sync(kFull, cap_old, src);
+                    const uint32_t mm2_g = __shfl_sync(kFull, mm2, src);
+                    const uint32_t mP2_g = __shfl_sync(kFull, mP2, src);
+                    const uint32_t* const rold = reinterpret_cast<const uint32_t*>(
+                        __shfl_sync(kFull, (unsigned long long)prow, src));
+                    uint32_t* const rnew =
+                        reinterpret_cast<uint32_t*>(__shfl_sync(kFull, (unsigned long long)nrow, src));
+                    constexpr int NPW = LPLW / 2;  // packed pairs per lane
+                    const int e2 = min(max(lo_g - lo_old_g + LPLW * lane - 1, -(LPLW + 2)), cap_old_g);
+                    const int b2 = kGPadL + e2;
+                    const uint32_t* q32 = rold + (b2 >> 1);
+                    const uint32_t sel2 = (b2 & 1) ? 0x5432u : 0x3210u;
+                    uint32_t wv[NPW + 2], A[NPW + 1];
 #pragma unroll
-                for (int i = 0; i < NPW + 2; ++i) wv[i] = r32[i];
+                    for (int i = 0; i < NPW + 2; ++i) wv[i] = q32[i];
 #pragma unroll
-                for (int i = 0; i < NPW + 1; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel);
-                const uint8_t* const cs = ring + gg * RS + (k % NS) * DP + LPLW * lane;
-                uint32_t cpk[NPW];
-                if constexpr (LPLW == 2) {
-                    cpk[0] = __byte_perm((uint32_t)*reinterpret_cast<const uint16_t*>(cs), 0u, 0x4140);
-                } else {
+                    for (int i = 0; i < NPW + 1; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel2);
+                    const uint8_t* const cs = ring + gg * RS + (k & (NS - 1)) * DP + LPLW * lane;
+                    uint32_t cpk[NPW];
+                    if constexpr (LPLW == 2) {
+                        cpk[0] = __byte_perm((uint32_t)*reinterpret_cast<const uint16_t*>(cs), 0u, 0x4140);
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < LPLW / 4; ++q) {
-                        const uint32_t c4 = reinterpret_cast<const uint32_t*>(cs)[q];
-                        cpk[2 * q] = __byte_perm(c4, 0u, 0x4140);
-                        cpk[2 * q + 1] = __byte_perm(c4, 0u, 0x4342);
+                        for (int q = 0; q < LPLW / 4; ++q) {
+                            const uint32_t c4 = reinterpret_cast<const uint32_t*>(cs)[q];
+                            cpk[2 * q] = __byte_perm(c4, 0u, 0x4140);
+                            cpk[2 * q + 1] = __byte_perm(c4, 0u, 0x4342);
+                        }
+                    }
+                    const int rem2 = w_g - LPLW * lane;
+                    uint32_t Lw[NPW];
+                    uint32_t pw2 = kInf2;
+#pragma unroll
+                    for (int i = 0; i < NPW; ++i) {
+                        const uint32_t kp = pair_keep(rem2 - 2 * i);
+                        const uint32_t v = (cpk[i] + grp_t(A[i], A[i + 1], P1x2, mP2_g)) - mm2_g;
+                        Lw[i] = (v & kp) | (kInf2 & ~kp);
+                        pw2 = vmin2(pw2, Lw[i]);
+                    }
+                    const int mg = (int)__reduce_min_sync(kFull, min(pw2 & 0xFFFFu, pw2 >> 16));
+                    uint32_t* const dst = rnew + kGPadL / 2 + LPLW * lane / 2;
+#pragma unroll
+                    for (int i = 0; i < NPW; ++i) dst[i] = Lw[i];
+                    if constexpr (LPLW == 2) {
+                        if (rem2 > 0)
+                            *reinterpret_cast<uint16_t*>(Lv + o_g + 2 * lane) =
+                                (uint16_t)__byte_perm(Lw[0], 0u, 0x0020);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < LPLW / 4; ++q)
+                            if (rem2 > 4 * q)
+                                *reinterpret_cast<uint32_t*>(Lv + o_g + LPLW * lane + 4 * q) =
+                                    __byte_perm(Lw[2 * q], Lw[2 * q + 1], 0x6420);
+                    }
+                    if (g == gg) {
+                        lo_old = lo_g;
+                        w_old = w_g;
+                        cap_old = DP;
+                        mm2 = (uint32_t)mg * 0x10001u;
+                        mP2 = mm2 + P2x2;
                     }
                 }
-                const int rem = w_g - LPLW * lane;
-                uint32_t Lw[NPW];
-                uint32_t pm = kInf2;
-#pragma unroll
-                for (int i = 0; i < NPW; ++i) {
-                    const uint32_t kp = pair_keep(rem - 2 * i);
-                    const uint32_t v = (cpk[i] + grp_t(A[i], A[i + 1], P1x2, mP2_g)) - mm2_g;
-                    Lw[i] = (v & kp) | (kInf2 & ~kp);
-                    pm = vmin2(pm, Lw[i]);
-                }
-                const int mg = (int)__reduce_min_sync(kFull, min(pm & 0xFFFFu, pm >> 16));
-                uint16_t* const dst = rnew + kGPadL + LPLW * lane;
-                if constexpr (LPLW == 2) {
-                    *reinterpret_cast<uint32_t*>(dst) = Lw[0];
-                    if (rem > 0)
-                        *reinterpret_cast<uint16_t*>(Lv + o_g + 2 * lane) =
-                            (uint16_t)__byte_perm(Lw[0], 0u, 0x0020);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < LPLW / 4; ++q) {
-                        reinterpret_cast<uint32_t*>(dst)[2 * q] = Lw[2 * q];
-                        reinterpret_cast<uint32_t*>(dst)[2 * q + 1] = Lw[2 * q + 1];
-                        if (rem > 4 * q)
-                            *reinterpret_cast<uint32_t*>(Lv + o_g + LPLW * lane + 4 * q) =
-                                __byte_perm(Lw[2 * q], Lw[2 * q + 1], 0x6420);
-                    }
-                }
-                if (g == gg) {
-                    lo_old = lo_g;
-                    w_old = w_g;
-                    cap_old = DP;
-                    mm2 = (uint32_t)mg * 0x10001u;
-                    mP2 = mm2 + P2x2;
-                }
-            }
             }
             if (go) {
-                cur ^= 1;
-                pg = g;
-                pw = cur;
+                const uint32_t* const t = nrow;
+                nrow = const_cast<uint32_t*>(prow == rowA || prow == rowB ? prow : (nrow == rowA ? rowB : rowA));
+                prow = t;
             }
         }
         cp_async_wait<0>();
@@ -407,7 +410,8 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         const int plo = __shfl_sync(kFull, lo_old, src), pcap = __shfl_sync(kFull, cap_old, src);
         const int pwid = __shfl_sync(kFull, w_old, src);
         const uint32_t pmm2 = __shfl_sync(kFull, mm2, src), pmP2 = __shfl_sync(kFull, mP2, src);
-        const int pcur = __shfl_sync(kFull, cur, src);
+        const uint32_t* const pprow =
+            reinterpret_cast<const uint32_t*>(__shfl_sync(kFull, (unsigned long long)prow, src));
         walker = sg > 0 && slen > 0 && (pass == 0 || pchanged);
         if (!__any_sync(kFull, walker)) break;
         if (walker) {
@@ -416,8 +420,9 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
             cap_old = pcap;
             mm2 = pmm2;
             mP2 = pmP2;
-            pg = g - 1;
-            pw = pcur;
+            // the first step reads the predecessor's row; this group's own rows are both free
+            prow = pprow;
+            nrow = rowA;
         }
     }
 }
