@@ -184,7 +184,8 @@ SgmKernel sgm_kernel_lg(int warps) {
 
 template <int LPLW>
 SgmKernel sgm_kernel_l(int gl, int warps) {
-    return gl == 4 ? sgm_kernel_lg<LPLW, 4>(warps) : sgm_kernel_lg<LPLW, 8>(warps);
+    if constexpr (LPLW == 8) return sgm_kernel_lg<LPLW, 8>(warps);  // see the 256-label rule
+    else return gl == 4 ? sgm_kernel_lg<LPLW, 4>(warps) : sgm_kernel_lg<LPLW, 8>(warps);
 }
 
 SgmKernel sgm_kernel(int maxD, int gl, int warps) {
@@ -408,7 +409,8 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
         }
         // lines per warp: windows of up to 16 labels fit the 4-lane groups (8 lines per warp),
         // wider ones (up to 32 in one step) the 8-lane groups
-        b->gl = (max_labels > 0 && max_labels <= 16) ? 4 : 8;
+        // (256 labels: always the 8-lane groups, as in the single-image aggregation)
+        b->gl = (max_labels > 0 && max_labels <= 16 && b->maxD <= 128) ? 4 : 8;
         const int NG = 32 / b->gl;
         // direction-major line order: every stream's horizontal lines first
         int item = 0;

@@ -59,14 +59,20 @@ __global__ void __launch_bounds__(kGrpWarps * 32) k_sgm(const uint8_t* __restric
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kGrpWarps + wib;
     uint32_t* const wsm = sgm_smem32 + wib * grp_words<LPLW>();
-    const bool eight = 16ull * wq[0] > (unsigned long long)n;
+    // 256 labels: always the 8-lane groups (the 4-lane form's dense step would hold 64 labels
+    // of costs per lane)
+    const bool eight = LPLW == 8 || 16ull * wq[0] > (unsigned long long)n;
     int code, first, nlines, seg;
     if (!grp_warp_lines(lines, eight ? 4 : 8, gw, code, first, nlines, seg)) return;
     uint8_t* const Lv = Lvol + (size_t)code * vol_stride;
-    if (eight)
+    if constexpr (LPLW == 8) {
         sgm_group_lines<LPLW, 8>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
-    else
-        sgm_group_lines<LPLW, 4>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
+    } else {
+        if (eight)
+            sgm_group_lines<LPLW, 8>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
+        else
+            sgm_group_lines<LPLW, 4>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
+    }
 }
 
 // Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the

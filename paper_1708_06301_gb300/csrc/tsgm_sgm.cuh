@@ -31,9 +31,11 @@
 // to the window's lo, with +inf padding on both sides; two rows per line, used in turn. A step
 // reads the predecessor's labels d - 1 .. d + 1 at the offset lo - lo(q), clamped into the padding
 // (so that no range test is needed): this makes every change of window, narrow or wide, one code
-// path. The costs of the step PF ahead are in flight into a ring of shared-memory slots
-// (cp.async, issued by the group's own lanes), and the window descriptors come in blocks of
-// kGBlk steps per line (cp.async), two blocks in the ring.
+// path. The window descriptors come in blocks of kGBlk steps per line (cp.async into a small
+// shared-memory ring, two blocks deep); the costs of the next step are loaded into registers
+// during the current one (two register sets, used in turn), in the form the next step takes:
+// each lane its own word (narrow), the lanes' share of one wide window (whole warp), or each
+// lane its share of its own line's wide window (dense).
 //
 // Each direction writes its path costs L (<= census bits + P2 <= 255) as bytes into its own
 // ragged volume; the selection sums the directions.
@@ -45,10 +47,8 @@ namespace tsgm {
 namespace dev {
 
 constexpr int kGPadL = 16, kGPadR = 16;  // +inf labels before and after a state row
-constexpr int kGSlots = 8, kGPref = 6;   // cost ring slots per line and prefetch distance (steps)
 constexpr int kGBlk = 16;                // steps per descriptor block
 constexpr int kGFix = 64;                // steps a segment is walked again before the check
-constexpr int kGSkew = 16;               // bytes between the cost rings of two lines (bank skew)
 
 // labels of the wide (whole-warp) form: LPLW per lane, >= D
 template <int LPLW>
@@ -57,11 +57,10 @@ __host__ __device__ constexpr int grp_dp() { return 32 * LPLW; }
 template <int LPLW>
 __host__ __device__ constexpr int grp_row() { return kGPadL + grp_dp<LPLW>() + kGPadR; }
 // shared memory of one warp in 32-bit words, for NG lines: state rows (2 per line), checkpoints
-// (one state per line), cost ring, descriptor ring
+// (one state per line), descriptor ring
 template <int LPLW, int NG>
 __host__ __device__ constexpr int grp_words_ng() {
-    return NG * (grp_row<LPLW>() + 32) + NG * grp_dp<LPLW>() / 2 +
-           NG * (kGSlots * grp_dp<LPLW>() + kGSkew) / 4 + 2 * kGBlk * NG * 2;
+    return NG * (grp_row<LPLW>() + 32) + NG * grp_dp<LPLW>() / 2 + 2 * kGBlk * NG * 2;
 }
 
 // Word offset of line g's two state rows (ROW / 2 words each, inside the line's ROW + 32 words).
@@ -113,24 +112,22 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     constexpr int DP = grp_dp<LPLW>();    // labels of the wide form
     constexpr int ROW = grp_row<LPLW>();  // entries of a state row
     constexpr int CKW = DP / 2;           // words of a checkpoint
-    constexpr int PF = kGPref, NS = kGSlots;
     constexpr int PER = kGBlk / GL;       // descriptors each lane loads per block
-    constexpr int RS = NS * DP + kGSkew;  // bytes of one group's cost ring
+    constexpr int LPD = DP / GL;          // labels per lane of the dense step
+    constexpr int NWD = LPD / 4;          // its cost words
+    constexpr int NWC = LPLW >= 4 ? LPLW / 4 : 1;  // cost words per lane of the whole-warp step
     static_assert(CAPN + 16 <= DP + kGPadR, "narrow padding inside the row");
-    static_assert(kGBlk - PF > PF + 1, "descriptor blocks arrive in time");
-    static_assert(2 * kGBlk == 32 && NS == 8, "ring indices are masks");
+    static_assert(2 * kGBlk == 32, "the descriptor ring index is a mask");
     const int lane = threadIdx.x & 31;
     const int g = lane / GL, j = lane % GL;
     const unsigned gmask = ((1u << GL) - 1u) << (g * GL);
 
-    // shared memory of this group: two state rows (bank-skewed), checkpoint, cost ring slots,
-    // descriptor ring column (entry s at dcol[(s & 31) * NG])
+    // shared memory of this group: two state rows (bank-skewed), checkpoint, descriptor ring
+    // column (entry s at dcol[(s & 31) * NG])
     uint32_t* const rowA = wsm + grp_row_base<LPLW, NG>(g);
     uint32_t* const rowB = rowA + ROW / 2;
     uint32_t* const ckpt = wsm + NG * (ROW + 32) + g * CKW;
-    uint8_t* const ring = reinterpret_cast<uint8_t*>(wsm + NG * (ROW + 32) + NG * CKW);
-    uint8_t* const cring = ring + g * RS;
-    uint2* const dcol = reinterpret_cast<uint2*>(ring + NG * RS) + g;
+    uint2* const dcol = reinterpret_cast<uint2*>(wsm + NG * (ROW + 32) + NG * CKW) + g;
 
     const int li = first_line + g / S, sg = g % S;
     int i0 = 0, stp = 0, llen = 0;
@@ -157,18 +154,10 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
             const int s = b * kGBlk + j * PER + q;
             if (s < slen) cp_async8(dcol + (s & 31) * NG, desc + (p0 + s * stp));
         }
+        cp_async_commit();
     };
     auto dread = [&](int s, bool walking) -> uint2 {
         return (walking && s < slen) ? dcol[(s & 31) * NG] : make_uint2(0u, 0u);
-    };
-    // the costs of a step with descriptor dsc (its whole window, whole 4-byte words) into ring
-    // slot `slot`; one commit group per call
-    auto issue = [&](uint2 dsc, int slot) {
-        const int nw = ((int)(dsc.y >> 16) + 3) >> 2;
-        uint8_t* const dst = cring + slot * DP;
-        if (j < nw) cp_async4(dst + 4 * j, C + dsc.x + 4 * j);
-        for (int t = j + GL; t < nw; t += GL) cp_async4(dst + 4 * t, C + dsc.x + 4 * t);
-        cp_async_commit();
     };
 
     const uint32_t P1x2 = ((uint32_t)P1 << 16) | (uint32_t)P1;
@@ -181,21 +170,52 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     int ck_lo = 0, ck_w = 0;
     bool walker = slen > 0;  // this group walks in the current pass
 
+    // costs of a step, in the form the step takes (two sets, used in turn)
+    uint32_t cn[2], cw[2][NWC], cd[2][NWD];
+    // load the costs of a step whose descriptor is dsc (this lane's group) and whose wide vote is
+    // wb (lanes GL g of the wide groups) into set q
+    auto fetch = [&](int q, uint2 dsc, unsigned wb) {
+        const int w_ = (int)(dsc.y >> 16);
+        const uint8_t* const c0 = C + dsc.x;
+        const int nwide = __popc(wb);
+        if (nwide >= 2) {
+#pragma unroll
+            for (int i = 0; i < NWD; ++i)
+                cd[q][i] = (LPD * j + 4 * i < w_) ? __ldg(reinterpret_cast<const uint32_t*>(c0 + LPD * j) + i) : 0u;
+        } else {
+            cn[q] = (4 * j < w_) ? __ldg(reinterpret_cast<const uint32_t*>(c0) + j) : 0u;
+            if (nwide == 1) {
+                const int src = __ffs(wb) - 1;
+                const unsigned o_g = __shfl_sync(kFull, dsc.x, src);
+                const int w_g = (int)(__shfl_sync(kFull, dsc.y, src) >> 16);
+                const uint8_t* const cg = C + o_g + LPLW * lane;
+                if constexpr (LPLW == 2) {
+                    cw[q][0] = (2 * lane < w_g) ? (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(cg)) : 0u;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NWC; ++i)
+                        cw[q][i] = (LPLW * lane + 4 * i < w_g) ? __ldg(reinterpret_cast<const uint32_t*>(cg) + i) : 0u;
+                }
+            }
+        }
+    };
+
     for (int pass = 0;; ++pass) {
         load_block(0);
-        cp_async_commit();
         cp_async_wait<0>();
         __syncwarp();
         load_block(1);
-        for (int t = 0; t < PF; ++t) issue(dread(t, walker), t);
         bool stop = false;     // the walk of this pass ended at the check (the states agreed)
         bool changed = false;  // this pass changed the segment's end state
         int kend = pass == 0 ? maxslen : cchk;
-        // software pipeline: the next step's descriptor (dn) and wide vote (wbn), and the
-        // descriptor of the step whose costs are issued next (dp)
-        uint2 dn = dread(0, walker), dp = dread(PF, walker);
-        unsigned wbn = __ballot_sync(kFull, walker && (int)(dn.y >> 16) > CAPN && j == 0);
-        for (int k = 0;; ++k) {
+        // the pipeline: step k's descriptor (dcur) and wide vote (wcur) are known one step ahead,
+        // its costs were loaded during step k - 1
+        uint2 dcur = dread(0, walker);
+        unsigned wcur = __ballot_sync(kFull, walker && (int)(dcur.y >> 16) > CAPN && j == 0);
+        fetch(0, dcur, wcur);
+
+        // one step; q: the cost set of this step (the next step's costs go to the other set)
+        auto step = [&](int k, int q) -> bool {
             if (k == cchk) {
                 // the check after step cstep: save the state (first walk) or compare with it;
                 // the state is L over the window (lo, w), entries past w are +inf in every row
@@ -219,27 +239,28 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 }
                 if (pass > 0 && __any_sync(kFull, changed)) kend = maxslen;
             }
-            if (k >= kend) break;
+            if (k >= kend) return false;
             const bool go = walker && !stop && k < slen;
-            const uint2 ds = dn;
-            unsigned wb0 = wbn;                               // voted a step ahead ...
-            if (k == cchk) wb0 &= __ballot_sync(kFull, go);   // ... before a walk stopped here
+            const uint2 ds = dcur;
+            // voted a step ahead (a line whose walk stops at this step's check may still be in
+            // it: its wide step then recomputes the values it already holds, which is harmless)
+            const unsigned wb0 = wcur;
+            // descriptor blocks: block b + 1 is requested at step 16 b and complete before its
+            // first entry is read (step 16 b + 15)
+            if ((k & (kGBlk - 1)) == kGBlk - 1) cp_async_wait<0>();
+            __syncwarp();  // the rows of the last step (and the descriptors) are visible
             if (k > 0 && (k & (kGBlk - 1)) == 0) load_block(k / kGBlk + 1);
-            issue(dp, (k + PF) & (NS - 1));
-            dp = dread(k + PF + 1, walker && !stop);
-            cp_async_wait<PF>();  // this lane's copies of step k (and older) have landed
-            __syncwarp();         // ... and every lane's
-            dn = dread(k + 1, walker && !stop);
-            wbn = __ballot_sync(kFull, walker && !stop && k + 1 < slen &&
-                                           (int)(dn.y >> 16) > CAPN && j == 0);
+            // the next step: descriptor, wide vote, costs
+            dcur = dread(k + 1, walker && !stop);
+            wcur = __ballot_sync(kFull, walker && !stop && k + 1 < slen &&
+                                            (int)(dcur.y >> 16) > CAPN && j == 0);
+            fetch(q ^ 1, dcur, wcur);
             const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
-            const uint8_t* const cslot = cring + (k & (NS - 1)) * DP;
 
             if (__popc(wb0) >= 2) {
-                // ---- dense step: every group its own window with its own lanes, DP / GL labels
-                // per lane, in chunks of 8 (several wide windows at once: the full-range band at
-                // the image border, a full-range frame)
-                constexpr int LPD = DP / GL;
+                // ---- dense step: every group its own window with its own lanes, LPD labels per
+                // lane, in chunks of 8 (several wide windows at once: the full-range band at the
+                // image border, a full-range frame)
                 uint32_t pm = kInf2;
 #pragma unroll
                 for (int c = 0; c < LPD / 8; ++c) {
@@ -253,8 +274,7 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     for (int i = 0; i < 6; ++i) wv[i] = r32[i];
 #pragma unroll
                     for (int i = 0; i < 5; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel);
-                    const uint32_t c4a = *reinterpret_cast<const uint32_t*>(cslot + base);
-                    const uint32_t c4b = *reinterpret_cast<const uint32_t*>(cslot + base + 4);
+                    const uint32_t c4a = cd[q][2 * c], c4b = cd[q][2 * c + 1];
                     const uint32_t cp[4] = {__byte_perm(c4a, 0u, 0x4140), __byte_perm(c4a, 0u, 0x4342),
                                             __byte_perm(c4b, 0u, 0x4140), __byte_perm(c4b, 0u, 0x4342)};
                     const int rem = w - base;
@@ -297,11 +317,11 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 const uint32_t w0 = r32[0], w1 = r32[1], w2 = r32[2], w3 = r32[3];
                 const uint32_t A0 = __byte_perm(w0, w1, sel), A1 = __byte_perm(w1, w2, sel),
                                A2 = __byte_perm(w2, w3, sel);
-                const uint32_t cw = *reinterpret_cast<const uint32_t*>(cslot + 4 * j);
+                const uint32_t cwd = cn[q];
                 const int rem = w - 4 * j;
                 const uint32_t k0 = pair_keep(rem), k1 = pair_keep(rem - 2);
-                uint32_t L0 = (__byte_perm(cw, 0u, 0x4140) + grp_t(A0, A1, P1x2, mP2)) - mm2;
-                uint32_t L1 = (__byte_perm(cw, 0u, 0x4342) + grp_t(A1, A2, P1x2, mP2)) - mm2;
+                uint32_t L0 = (__byte_perm(cwd, 0u, 0x4140) + grp_t(A0, A1, P1x2, mP2)) - mm2;
+                uint32_t L1 = (__byte_perm(cwd, 0u, 0x4342) + grp_t(A1, A2, P1x2, mP2)) - mm2;
                 L0 = (L0 & k0) | (kInf2 & ~k0);
                 L1 = (L1 & k1) | (kInf2 & ~k1);
                 const uint32_t pm = vmin2(L0, L1);
@@ -327,8 +347,8 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
 
                 // ---- a single wide window: the whole warp ----
                 if (wb0) {
-                    const int gg = (__ffs(wb0) - 1) / GL;
-                    const int src = gg * GL;
+                    const int src = __ffs(wb0) - 1;
+                    const int gg = src / GL;
                     const int lo_g = __shfl_sync(kFull, lo, src), w_g = __shfl_sync(kFull, w, src);
                     const uint32_t o_g = __shfl_sync(kFull, ds.x, src);
                     const int lo_old_g = __shfl_sync(kFull, lo_old, src);
@@ -349,16 +369,14 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     for (int i = 0; i < NPW + 2; ++i) wv[i] = q32[i];
 #pragma unroll
                     for (int i = 0; i < NPW + 1; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel2);
-                    const uint8_t* const cs = ring + gg * RS + (k & (NS - 1)) * DP + LPLW * lane;
                     uint32_t cpk[NPW];
                     if constexpr (LPLW == 2) {
-                        cpk[0] = __byte_perm((uint32_t)*reinterpret_cast<const uint16_t*>(cs), 0u, 0x4140);
+                        cpk[0] = __byte_perm(cw[q][0], 0u, 0x4140);
                     } else {
 #pragma unroll
-                        for (int q = 0; q < LPLW / 4; ++q) {
-                            const uint32_t c4 = reinterpret_cast<const uint32_t*>(cs)[q];
-                            cpk[2 * q] = __byte_perm(c4, 0u, 0x4140);
-                            cpk[2 * q + 1] = __byte_perm(c4, 0u, 0x4342);
+                        for (int i = 0; i < NWC; ++i) {
+                            cpk[2 * i] = __byte_perm(cw[q][i], 0u, 0x4140);
+                            cpk[2 * i + 1] = __byte_perm(cw[q][i], 0u, 0x4342);
                         }
                     }
                     const int rem2 = w_g - LPLW * lane;
@@ -381,10 +399,10 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                                 (uint16_t)__byte_perm(Lw[0], 0u, 0x0020);
                     } else {
 #pragma unroll
-                        for (int q = 0; q < LPLW / 4; ++q)
-                            if (rem2 > 4 * q)
-                                *reinterpret_cast<uint32_t*>(Lv + o_g + LPLW * lane + 4 * q) =
-                                    __byte_perm(Lw[2 * q], Lw[2 * q + 1], 0x6420);
+                        for (int i = 0; i < NWC; ++i)
+                            if (rem2 > 4 * i)
+                                *reinterpret_cast<uint32_t*>(Lv + o_g + LPLW * lane + 4 * i) =
+                                    __byte_perm(Lw[2 * i], Lw[2 * i + 1], 0x6420);
                     }
                     if (g == gg) {
                         lo_old = lo_g;
@@ -400,6 +418,11 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 nrow = const_cast<uint32_t*>(prow == rowA || prow == rowB ? prow : (nrow == rowA ? rowB : rowA));
                 prow = t;
             }
+            return true;
+        };
+        for (int k = 0;; k += 2) {
+            if (!step(k, 0)) break;
+            if (!step(k + 1, 1)) break;
         }
         cp_async_wait<0>();
         __syncwarp();
