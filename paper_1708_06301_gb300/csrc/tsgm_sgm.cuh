@@ -47,7 +47,7 @@ namespace tsgm {
 namespace dev {
 
 constexpr int kGPadL = 16, kGPadR = 16;  // +inf labels before and after a state row
-constexpr int kGBlk = 16;                // steps per descriptor block
+constexpr int kGBlk = 8;                 // steps per descriptor block (4 blocks in the ring)
 constexpr int kGFix = 64;                // steps a segment is walked again before the check
 
 // labels of the wide (whole-warp) form: LPLW per lane, >= D
@@ -57,10 +57,10 @@ __host__ __device__ constexpr int grp_dp() { return 32 * LPLW; }
 template <int LPLW>
 __host__ __device__ constexpr int grp_row() { return kGPadL + grp_dp<LPLW>() + kGPadR; }
 // shared memory of one warp in 32-bit words, for NG lines: state rows (2 per line), checkpoints
-// (one state per line), descriptor ring
+// (one state per line), descriptor ring (4 blocks)
 template <int LPLW, int NG>
 __host__ __device__ constexpr int grp_words_ng() {
-    return NG * (grp_row<LPLW>() + 32) + NG * grp_dp<LPLW>() / 2 + 2 * kGBlk * NG * 2;
+    return NG * (grp_row<LPLW>() + 32) + NG * grp_dp<LPLW>() / 2 + 4 * kGBlk * NG * 2;
 }
 
 // Word offset of line g's two state rows (ROW / 2 words each, inside the line's ROW + 32 words).
@@ -76,6 +76,22 @@ __device__ __forceinline__ int grp_row_base(int g) {
 // the most any lane-group width needs (4 lanes per line: 8 lines)
 template <int LPLW>
 __host__ __device__ constexpr int grp_words() { return grp_words_ng<LPLW, 8>(); }
+
+// 32-bit shared-memory accesses by address (the rows are addressed by 32-bit offsets: no 64-bit
+// pointer arithmetic in the step)
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint2 lds64(uint32_t a) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
@@ -117,17 +133,20 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     constexpr int NWD = LPD / 4;          // its cost words
     constexpr int NWC = LPLW >= 4 ? LPLW / 4 : 1;  // cost words per lane of the whole-warp step
     static_assert(CAPN + 16 <= DP + kGPadR, "narrow padding inside the row");
-    static_assert(2 * kGBlk == 32, "the descriptor ring index is a mask");
+    static_assert(4 * kGBlk == 32 && PER >= 1, "the descriptor ring index is a mask");
     const int lane = threadIdx.x & 31;
     const int g = lane / GL, j = lane % GL;
     const unsigned gmask = ((1u << GL) - 1u) << (g * GL);
 
-    // shared memory of this group: two state rows (bank-skewed), checkpoint, descriptor ring
-    // column (entry s at dcol[(s & 31) * NG])
-    uint32_t* const rowA = wsm + grp_row_base<LPLW, NG>(g);
-    uint32_t* const rowB = rowA + ROW / 2;
+    // shared memory of this group, by 32-bit address: two state rows (bank-skewed), checkpoint,
+    // descriptor ring column (entry s at dcol + 8 NG (s & 31))
+    const uint32_t wsm_s = static_cast<uint32_t>(__cvta_generic_to_shared(wsm));
+    const uint32_t rowA = wsm_s + 4u * (uint32_t)grp_row_base<LPLW, NG>(g);
+    const uint32_t rowB = rowA + 2u * ROW;
     uint32_t* const ckpt = wsm + NG * (ROW + 32) + g * CKW;
-    uint2* const dcol = reinterpret_cast<uint2*>(wsm + NG * (ROW + 32) + NG * CKW) + g;
+    uint2* const dcol_g = reinterpret_cast<uint2*>(wsm + NG * (ROW + 32) + NG * CKW) + g;
+    const uint32_t dcol = static_cast<uint32_t>(__cvta_generic_to_shared(dcol_g));
+    auto gptr = [&](uint32_t a) -> uint32_t* { return wsm + ((a - wsm_s) >> 2); };
 
     const int li = first_line + g / S, sg = g % S;
     int i0 = 0, stp = 0, llen = 0;
@@ -152,21 +171,21 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int s = b * kGBlk + j * PER + q;
-            if (s < slen) cp_async8(dcol + (s & 31) * NG, desc + (p0 + s * stp));
+            if (s < slen) cp_async8(dcol_g + (s & 31) * NG, desc + (p0 + s * stp));
         }
         cp_async_commit();
     };
     auto dread = [&](int s, bool walking) -> uint2 {
-        return (walking && s < slen) ? dcol[(s & 31) * NG] : make_uint2(0u, 0u);
+        return (walking && s < slen) ? lds64(dcol + 8u * NG * (uint32_t)(s & 31)) : make_uint2(0u, 0u);
     };
 
     const uint32_t P1x2 = ((uint32_t)P1 << 16) | (uint32_t)P1;
     const uint32_t P2x2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
     // predecessor of a first step: all +inf, m = 0 and no P2 term, so that L = C
     int lo_old = 0, w_old = 0, cap_old = 0;  // the state's window and its row's labels
-    uint32_t mm2 = 0u, mP2 = 0u;
-    const uint32_t* prow = rowA;  // the predecessor of the next step
-    uint32_t* nrow = rowB;        // the row the next step writes
+    int mm = 0, mP = 0;                      // m and m + P2 of the state
+    uint32_t prow = rowA;                    // the predecessor of the next step
+    uint32_t nrow = rowB;                    // the row the next step writes
     int ck_lo = 0, ck_w = 0;
     bool walker = slen > 0;  // this group walks in the current pass
 
@@ -200,6 +219,48 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         }
     };
 
+    // narrow step of this group's line: lane j's labels lo + 4j .. lo + 4j + 3 in 32-bit
+    // arithmetic (computed everywhere; stored and taken as the new state where `keep`)
+    auto narrow = [&](uint2 ds, uint32_t cwd, bool keep) {
+        const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
+        const int e = min(max(lo - lo_old + 4 * j - 1, -6), cap_old);
+        const uint32_t ba = prow + 2u * (uint32_t)(kGPadL + e);  // entry e of the predecessor
+        const uint32_t wa = ba & ~3u, sh = (ba & 2u) << 3;
+        const uint32_t w0 = lds32(wa), w1 = lds32(wa + 4), w2 = lds32(wa + 8), w3 = lds32(wa + 12);
+        const uint32_t q0 = __funnelshift_r(w0, w1, sh), q1 = __funnelshift_r(w1, w2, sh),
+                       q2 = __funnelshift_r(w2, w3, sh);
+        const int v[6] = {(int)(q0 & 0xFFFFu), (int)(q0 >> 16), (int)(q1 & 0xFFFFu),
+                          (int)(q1 >> 16),     (int)(q2 & 0xFFFFu), (int)(q2 >> 16)};
+        int L[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int t = min(min(v[i], v[i + 2]) + P1, v[i + 1]);
+            t = min(t, mP);
+            const int c = (int)((cwd >> (8 * i)) & 0xFFu);
+            L[i] = (4 * j + i < w) ? c + t - mm : kInf;
+        }
+        int m = min(min(L[0], L[1]), min(L[2], L[3]));
+#pragma unroll
+        for (int t = 1; t < GL; t <<= 1) m = min(m, __shfl_xor_sync(kFull, m, t));
+        if (keep) {
+            const uint32_t pk0 = (uint32_t)L[0] | ((uint32_t)L[1] << 16);
+            const uint32_t pk1 = (uint32_t)L[2] | ((uint32_t)L[3] << 16);
+            const uint32_t rw = nrow + 2u * kGPadL + 8u * j;
+            sts32(rw, pk0);
+            sts32(rw + 4, pk1);
+            if (GL == 4 || j < 4) {
+                sts32(rw + 2u * CAPN, kInf2);
+                sts32(rw + 2u * CAPN + 4, kInf2);
+            }
+            if (4 * j < w) *reinterpret_cast<uint32_t*>(Lv + ds.x + 4 * j) = __byte_perm(pk0, pk1, 0x6420);
+            lo_old = lo;
+            w_old = w;
+            cap_old = CAPN;
+            mm = m;
+            mP = m + P2;
+        }
+    };
+
     for (int pass = 0;; ++pass) {
         load_block(0);
         cp_async_wait<0>();
@@ -222,8 +283,9 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 const bool mine = walker && cstep + 1 == k;
                 bool eq = lo_old == ck_lo && w_old == ck_w;
                 if (mine) {
+                    const uint32_t* const pr = gptr(prow);
                     for (int t = j; t < (w_old + 1) / 2; t += GL) {
-                        const uint32_t v = prow[kGPadL / 2 + t];
+                        const uint32_t v = pr[kGPadL / 2 + t];
                         if (pass == 0) ckpt[t] = v;
                         else eq = eq && ckpt[t] == v;
                     }
@@ -245,29 +307,38 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
             // voted a step ahead (a line whose walk stops at this step's check may still be in
             // it: its wide step then recomputes the values it already holds, which is harmless)
             const unsigned wb0 = wcur;
-            // descriptor blocks: block b + 1 is requested at step 16 b and complete before its
-            // first entry is read (step 16 b + 15)
-            if ((k & (kGBlk - 1)) == kGBlk - 1) cp_async_wait<0>();
-            __syncwarp();  // the rows of the last step (and the descriptors) are visible
-            if (k > 0 && (k & (kGBlk - 1)) == 0) load_block(k / kGBlk + 1);
+            // descriptor blocks: block b + 1 (requested at step 8 (b - 1)) is complete at step
+            // 8 b, when block b + 2 is requested; the next step's descriptor is in block b or b + 1
+            if ((k & (kGBlk - 1)) == 0) {
+                cp_async_wait<0>();
+                __syncwarp();
+                load_block(k / kGBlk + 2);
+            } else {
+                __syncwarp();  // the rows of the last step are visible
+            }
             // the next step: descriptor, wide vote, costs
             dcur = dread(k + 1, walker && !stop);
             wcur = __ballot_sync(kFull, walker && !stop && k + 1 < slen &&
                                             (int)(dcur.y >> 16) > CAPN && j == 0);
             fetch(q ^ 1, dcur, wcur);
-            const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
 
-            if (__popc(wb0) >= 2) {
+            if (wb0 == 0u) {
+                narrow(ds, cn[q], go);
+            } else if (__popc(wb0) >= 2) {
                 // ---- dense step: every group its own window with its own lanes, LPD labels per
                 // lane, in chunks of 8 (several wide windows at once: the full-range band at the
                 // image border, a full-range frame)
+                const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
+                const uint32_t mm2 = (uint32_t)mm * 0x10001u, mP2 = (uint32_t)mP * 0x10001u;
+                const uint32_t* const pr = gptr(prow);
+                uint32_t* const nr = gptr(nrow);
                 uint32_t pm = kInf2;
 #pragma unroll
                 for (int c = 0; c < LPD / 8; ++c) {
                     const int base = LPD * j + 8 * c;  // first label of the chunk, from lo
                     const int e = min(max(lo - lo_old + base - 1, -10), cap_old);
                     const int b = kGPadL + e;
-                    const uint32_t* r32 = prow + (b >> 1);
+                    const uint32_t* r32 = pr + (b >> 1);
                     const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
                     uint32_t wv[6], A[5];
 #pragma unroll
@@ -288,7 +359,7 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     }
                     if (go) {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) nrow[kGPadL / 2 + base / 2 + i] = Lc[i];
+                        for (int i = 0; i < 4; ++i) nr[kGPadL / 2 + base / 2 + i] = Lc[i];
                         if (rem > 0)
                             *reinterpret_cast<uint32_t*>(Lv + ds.x + base) = __byte_perm(Lc[0], Lc[1], 0x6420);
                         if (rem > 4)
@@ -303,119 +374,80 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     lo_old = lo;
                     w_old = w;
                     cap_old = DP;
-                    mm2 = (uint32_t)m * 0x10001u;
-                    mP2 = mm2 + P2x2;
+                    mm = m;
+                    mP = m + P2;
                 }
             } else {
-                // ---- narrow step of this group's line (computed everywhere, stored where it
-                // applies)
-                const bool wide = w > CAPN;
-                const int e = min(max(lo - lo_old + 4 * j - 1, -6), cap_old);
-                const int b = kGPadL + e;
-                const uint32_t* r32 = prow + (b >> 1);
-                const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
-                const uint32_t w0 = r32[0], w1 = r32[1], w2 = r32[2], w3 = r32[3];
-                const uint32_t A0 = __byte_perm(w0, w1, sel), A1 = __byte_perm(w1, w2, sel),
-                               A2 = __byte_perm(w2, w3, sel);
-                const uint32_t cwd = cn[q];
-                const int rem = w - 4 * j;
-                const uint32_t k0 = pair_keep(rem), k1 = pair_keep(rem - 2);
-                uint32_t L0 = (__byte_perm(cwd, 0u, 0x4140) + grp_t(A0, A1, P1x2, mP2)) - mm2;
-                uint32_t L1 = (__byte_perm(cwd, 0u, 0x4342) + grp_t(A1, A2, P1x2, mP2)) - mm2;
-                L0 = (L0 & k0) | (kInf2 & ~k0);
-                L1 = (L1 & k1) | (kInf2 & ~k1);
-                const uint32_t pm = vmin2(L0, L1);
-                int m = (int)min(pm & 0xFFFFu, pm >> 16);
+                // ---- one wide window: the other lines' narrow steps, then the whole warp ----
+                const int w = (int)(ds.y >> 16);
+                narrow(ds, cn[q], go && w <= CAPN);
+                const int src = __ffs(wb0) - 1;
+                const int gg = src / GL;
+                const int lo_g = (int)(__shfl_sync(kFull, ds.y, src) & 0xFFFFu);
+                const int w_g = (int)(__shfl_sync(kFull, ds.y, src) >> 16);
+                const uint32_t o_g = __shfl_sync(kFull, ds.x, src);
+                const int lo_old_g = __shfl_sync(kFull, lo_old, src);
+                const int cap_old_g = __shfl_sync(kFull, cap_old, src);
+                const uint32_t mm2_g = (uint32_t)__shfl_sync(kFull, mm, src) * 0x10001u;
+                const uint32_t mP2_g = (uint32_t)__shfl_sync(kFull, mP, src) * 0x10001u;
+                const uint32_t* const rold = gptr(__shfl_sync(kFull, prow, src));
+                uint32_t* const rnew = gptr(__shfl_sync(kFull, nrow, src));
+                constexpr int NPW = LPLW / 2;  // packed pairs per lane
+                const int e2 = min(max(lo_g - lo_old_g + LPLW * lane - 1, -(LPLW + 2)), cap_old_g);
+                const int b2 = kGPadL + e2;
+                const uint32_t* q32 = rold + (b2 >> 1);
+                const uint32_t sel2 = (b2 & 1) ? 0x5432u : 0x3210u;
+                uint32_t wv[NPW + 2], A[NPW + 1];
 #pragma unroll
-                for (int t = 1; t < GL; t <<= 1) m = min(m, __shfl_xor_sync(kFull, m, t));
-                if (go && !wide) {
-                    uint32_t* const rw = nrow + kGPadL / 2;
-                    rw[2 * j] = L0;
-                    rw[2 * j + 1] = L1;
-                    if (GL == 4 || j < 4) {
-                        rw[CAPN / 2 + 2 * j] = kInf2;
-                        rw[CAPN / 2 + 2 * j + 1] = kInf2;
+                for (int i = 0; i < NPW + 2; ++i) wv[i] = q32[i];
+#pragma unroll
+                for (int i = 0; i < NPW + 1; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel2);
+                uint32_t cpk[NPW];
+                if constexpr (LPLW == 2) {
+                    cpk[0] = __byte_perm(cw[q][0], 0u, 0x4140);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NWC; ++i) {
+                        cpk[2 * i] = __byte_perm(cw[q][i], 0u, 0x4140);
+                        cpk[2 * i + 1] = __byte_perm(cw[q][i], 0u, 0x4342);
                     }
-                    if (rem > 0)
-                        *reinterpret_cast<uint32_t*>(Lv + ds.x + 4 * j) = __byte_perm(L0, L1, 0x6420);
-                    lo_old = lo;
-                    w_old = w;
-                    cap_old = CAPN;
-                    mm2 = (uint32_t)m * 0x10001u;
-                    mP2 = mm2 + P2x2;
                 }
-
-                // ---- a single wide window: the whole warp ----
-                if (wb0) {
-                    const int src = __ffs(wb0) - 1;
-                    const int gg = src / GL;
-                    const int lo_g = __shfl_sync(kFull, lo, src), w_g = __shfl_sync(kFull, w, src);
-                    const uint32_t o_g = __shfl_sync(kFull, ds.x, src);
-                    const int lo_old_g = __shfl_sync(kFull, lo_old, src);
-                    const int cap_old_g = __shfl_sync(kFull, cap_old, src);
-                    const uint32_t mm2_g = __shfl_sync(kFull, mm2, src);
-                    const uint32_t mP2_g = __shfl_sync(kFull, mP2, src);
-                    const uint32_t* const rold = reinterpret_cast<const uint32_t*>(
-                        __shfl_sync(kFull, (unsigned long long)prow, src));
-                    uint32_t* const rnew =
-                        reinterpret_cast<uint32_t*>(__shfl_sync(kFull, (unsigned long long)nrow, src));
-                    constexpr int NPW = LPLW / 2;  // packed pairs per lane
-                    const int e2 = min(max(lo_g - lo_old_g + LPLW * lane - 1, -(LPLW + 2)), cap_old_g);
-                    const int b2 = kGPadL + e2;
-                    const uint32_t* q32 = rold + (b2 >> 1);
-                    const uint32_t sel2 = (b2 & 1) ? 0x5432u : 0x3210u;
-                    uint32_t wv[NPW + 2], A[NPW + 1];
+                const int rem2 = w_g - LPLW * lane;
+                uint32_t Lw[NPW];
+                uint32_t pw2 = kInf2;
 #pragma unroll
-                    for (int i = 0; i < NPW + 2; ++i) wv[i] = q32[i];
+                for (int i = 0; i < NPW; ++i) {
+                    const uint32_t kp = pair_keep(rem2 - 2 * i);
+                    const uint32_t v = (cpk[i] + grp_t(A[i], A[i + 1], P1x2, mP2_g)) - mm2_g;
+                    Lw[i] = (v & kp) | (kInf2 & ~kp);
+                    pw2 = vmin2(pw2, Lw[i]);
+                }
+                const int mg = (int)__reduce_min_sync(kFull, min(pw2 & 0xFFFFu, pw2 >> 16));
+                uint32_t* const dst = rnew + kGPadL / 2 + LPLW * lane / 2;
 #pragma unroll
-                    for (int i = 0; i < NPW + 1; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel2);
-                    uint32_t cpk[NPW];
-                    if constexpr (LPLW == 2) {
-                        cpk[0] = __byte_perm(cw[q][0], 0u, 0x4140);
-                    } else {
+                for (int i = 0; i < NPW; ++i) dst[i] = Lw[i];
+                if constexpr (LPLW == 2) {
+                    if (rem2 > 0)
+                        *reinterpret_cast<uint16_t*>(Lv + o_g + 2 * lane) =
+                            (uint16_t)__byte_perm(Lw[0], 0u, 0x0020);
+                } else {
 #pragma unroll
-                        for (int i = 0; i < NWC; ++i) {
-                            cpk[2 * i] = __byte_perm(cw[q][i], 0u, 0x4140);
-                            cpk[2 * i + 1] = __byte_perm(cw[q][i], 0u, 0x4342);
-                        }
-                    }
-                    const int rem2 = w_g - LPLW * lane;
-                    uint32_t Lw[NPW];
-                    uint32_t pw2 = kInf2;
-#pragma unroll
-                    for (int i = 0; i < NPW; ++i) {
-                        const uint32_t kp = pair_keep(rem2 - 2 * i);
-                        const uint32_t v = (cpk[i] + grp_t(A[i], A[i + 1], P1x2, mP2_g)) - mm2_g;
-                        Lw[i] = (v & kp) | (kInf2 & ~kp);
-                        pw2 = vmin2(pw2, Lw[i]);
-                    }
-                    const int mg = (int)__reduce_min_sync(kFull, min(pw2 & 0xFFFFu, pw2 >> 16));
-                    uint32_t* const dst = rnew + kGPadL / 2 + LPLW * lane / 2;
-#pragma unroll
-                    for (int i = 0; i < NPW; ++i) dst[i] = Lw[i];
-                    if constexpr (LPLW == 2) {
-                        if (rem2 > 0)
-                            *reinterpret_cast<uint16_t*>(Lv + o_g + 2 * lane) =
-                                (uint16_t)__byte_perm(Lw[0], 0u, 0x0020);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < NWC; ++i)
-                            if (rem2 > 4 * i)
-                                *reinterpret_cast<uint32_t*>(Lv + o_g + LPLW * lane + 4 * i) =
-                                    __byte_perm(Lw[2 * i], Lw[2 * i + 1], 0x6420);
-                    }
-                    if (g == gg) {
-                        lo_old = lo_g;
-                        w_old = w_g;
-                        cap_old = DP;
-                        mm2 = (uint32_t)mg * 0x10001u;
-                        mP2 = mm2 + P2x2;
-                    }
+                    for (int i = 0; i < NWC; ++i)
+                        if (rem2 > 4 * i)
+                            *reinterpret_cast<uint32_t*>(Lv + o_g + LPLW * lane + 4 * i) =
+                                __byte_perm(Lw[2 * i], Lw[2 * i + 1], 0x6420);
+                }
+                if (g == gg) {
+                    lo_old = lo_g;
+                    w_old = w_g;
+                    cap_old = DP;
+                    mm = mg;
+                    mP = mg + P2;
                 }
             }
             if (go) {
-                const uint32_t* const t = nrow;
-                nrow = const_cast<uint32_t*>(prow == rowA || prow == rowB ? prow : (nrow == rowA ? rowB : rowA));
+                const uint32_t t = nrow;
+                nrow = (prow == rowA || prow == rowB) ? prow : (nrow == rowA ? rowB : rowA);
                 prow = t;
             }
             return true;
@@ -432,17 +464,16 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         const bool pchanged = __shfl_sync(kFull, (int)changed, src) != 0;
         const int plo = __shfl_sync(kFull, lo_old, src), pcap = __shfl_sync(kFull, cap_old, src);
         const int pwid = __shfl_sync(kFull, w_old, src);
-        const uint32_t pmm2 = __shfl_sync(kFull, mm2, src), pmP2 = __shfl_sync(kFull, mP2, src);
-        const uint32_t* const pprow =
-            reinterpret_cast<const uint32_t*>(__shfl_sync(kFull, (unsigned long long)prow, src));
+        const int pmm = __shfl_sync(kFull, mm, src), pmP = __shfl_sync(kFull, mP, src);
+        const uint32_t pprow = __shfl_sync(kFull, prow, src);
         walker = sg > 0 && slen > 0 && (pass == 0 || pchanged);
         if (!__any_sync(kFull, walker)) break;
         if (walker) {
             lo_old = plo;
             w_old = pwid;
             cap_old = pcap;
-            mm2 = pmm2;
-            mP2 = pmP2;
+            mm = pmm;
+            mP = pmP;
             // the first step reads the predecessor's row; this group's own rows are both free
             prow = pprow;
             nrow = rowA;
