@@ -77,21 +77,6 @@ __device__ __forceinline__ int grp_row_base(int g) {
 template <int LPLW>
 __host__ __device__ constexpr int grp_words() { return grp_words_ng<LPLW, 8>(); }
 
-// 32-bit shared-memory accesses by address (the rows are addressed by 32-bit offsets: no 64-bit
-// pointer arithmetic in the step)
-__device__ __forceinline__ uint32_t lds32(uint32_t a) {
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint2 lds64(uint32_t a) {
-    uint2 v;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
-    return v;
-}
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
@@ -138,15 +123,14 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     const int g = lane / GL, j = lane % GL;
     const unsigned gmask = ((1u << GL) - 1u) << (g * GL);
 
-    // shared memory of this group, by 32-bit address: two state rows (bank-skewed), checkpoint,
-    // descriptor ring column (entry s at dcol + 8 NG (s & 31))
-    const uint32_t wsm_s = static_cast<uint32_t>(__cvta_generic_to_shared(wsm));
-    const uint32_t rowA = wsm_s + 4u * (uint32_t)grp_row_base<LPLW, NG>(g);
-    const uint32_t rowB = rowA + 2u * ROW;
+    // shared memory of this group, by word index into wsm: two state rows (bank-skewed),
+    // checkpoint, descriptor ring column (entry s at word dcol + 2 NG (s & 31))
+    const int rowA = grp_row_base<LPLW, NG>(g);
+    const int rowB = rowA + ROW / 2;
     uint32_t* const ckpt = wsm + NG * (ROW + 32) + g * CKW;
-    uint2* const dcol_g = reinterpret_cast<uint2*>(wsm + NG * (ROW + 32) + NG * CKW) + g;
-    const uint32_t dcol = static_cast<uint32_t>(__cvta_generic_to_shared(dcol_g));
-    auto gptr = [&](uint32_t a) -> uint32_t* { return wsm + ((a - wsm_s) >> 2); };
+    const int dcol0 = NG * (ROW + 32) + NG * CKW;  // the ring
+    const int dcol = dcol0 + 2 * g;
+    uint2* const dcol_g = reinterpret_cast<uint2*>(wsm + dcol);
 
     const int li = first_line + g / S, sg = g % S;
     int i0 = 0, stp = 0, llen = 0;
@@ -166,6 +150,10 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     const int cchk = (int)__reduce_max_sync(kFull, (unsigned)(cstep + 1));  // 0: no check
 
     for (int t = lane; t < NG * (ROW + 32); t += 32) wsm[t] = kInf2;
+    // every ring entry holds a valid descriptor at all times (an empty window until written), so
+    // that the descriptor reads and the cost loads they address need no guard
+    for (int t = lane; t < 4 * kGBlk * NG * 2; t += 32) wsm[dcol0 + t] = 0u;
+    __syncwarp();  // before any lane's copies land in the ring
 
     auto load_block = [&](int b) {
 #pragma unroll
@@ -175,8 +163,9 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         }
         cp_async_commit();
     };
-    auto dread = [&](int s, bool walking) -> uint2 {
-        return (walking && s < slen) ? lds64(dcol + 8u * NG * (uint32_t)(s & 31)) : make_uint2(0u, 0u);
+    // (entries past the walk hold stale but valid descriptors; what they feed is not stored)
+    auto dread = [&](int s) -> uint2 {
+        return *reinterpret_cast<const uint2*>(wsm + dcol + 2 * NG * (s & 31));
     };
 
     const uint32_t P1x2 = ((uint32_t)P1 << 16) | (uint32_t)P1;
@@ -184,8 +173,8 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     // predecessor of a first step: all +inf, m = 0 and no P2 term, so that L = C
     int lo_old = 0, w_old = 0, cap_old = 0;  // the state's window and its row's labels
     int mm = 0, mP = 0;                      // m and m + P2 of the state
-    uint32_t prow = rowA;                    // the predecessor of the next step
-    uint32_t nrow = rowB;                    // the row the next step writes
+    int prow = rowA;                         // the predecessor of the next step (word index)
+    int nrow = rowB;                         // the row the next step writes
     int ck_lo = 0, ck_w = 0;
     bool walker = slen > 0;  // this group walks in the current pass
 
@@ -193,27 +182,33 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     uint32_t cn[2], cw[2][NWC], cd[2][NWD];
     // load the costs of a step whose descriptor is dsc (this lane's group) and whose wide vote is
     // wb (lanes GL g of the wide groups) into set q
+    // (every load is unconditional, from the cost word itself or, past the window, from C[0]:
+    // the value is masked later, and no instruction waits on a load in the step that issues it)
     auto fetch = [&](int q, uint2 dsc, unsigned wb) {
         const int w_ = (int)(dsc.y >> 16);
-        const uint8_t* const c0 = C + dsc.x;
+        const uint32_t* const C32 = reinterpret_cast<const uint32_t*>(C);
         const int nwide = __popc(wb);
         if (nwide >= 2) {
 #pragma unroll
-            for (int i = 0; i < NWD; ++i)
-                cd[q][i] = (LPD * j + 4 * i < w_) ? __ldg(reinterpret_cast<const uint32_t*>(c0 + LPD * j) + i) : 0u;
+            for (int i = 0; i < NWD; ++i) {
+                const int t = LPD * j + 4 * i;
+                cd[q][i] = __ldg(C32 + (t < w_ ? (dsc.x + t) >> 2 : 0u));
+            }
         } else {
-            cn[q] = (4 * j < w_) ? __ldg(reinterpret_cast<const uint32_t*>(c0) + j) : 0u;
+            cn[q] = __ldg(C32 + (4 * j < w_ ? (dsc.x >> 2) + j : 0u));
             if (nwide == 1) {
                 const int src = __ffs(wb) - 1;
                 const unsigned o_g = __shfl_sync(kFull, dsc.x, src);
                 const int w_g = (int)(__shfl_sync(kFull, dsc.y, src) >> 16);
-                const uint8_t* const cg = C + o_g + LPLW * lane;
                 if constexpr (LPLW == 2) {
-                    cw[q][0] = (2 * lane < w_g) ? (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(cg)) : 0u;
+                    const uint16_t* const C16 = reinterpret_cast<const uint16_t*>(C);
+                    cw[q][0] = (uint32_t)__ldg(C16 + (2 * lane < w_g ? (o_g >> 1) + lane : 0u));
                 } else {
 #pragma unroll
-                    for (int i = 0; i < NWC; ++i)
-                        cw[q][i] = (LPLW * lane + 4 * i < w_g) ? __ldg(reinterpret_cast<const uint32_t*>(cg) + i) : 0u;
+                    for (int i = 0; i < NWC; ++i) {
+                        const int t = LPLW * lane + 4 * i;
+                        cw[q][i] = __ldg(C32 + (t < w_g ? (o_g + t) >> 2 : 0u));
+                    }
                 }
             }
         }
@@ -224,9 +219,10 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     auto narrow = [&](uint2 ds, uint32_t cwd, bool keep) {
         const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
         const int e = min(max(lo - lo_old + 4 * j - 1, -6), cap_old);
-        const uint32_t ba = prow + 2u * (uint32_t)(kGPadL + e);  // entry e of the predecessor
-        const uint32_t wa = ba & ~3u, sh = (ba & 2u) << 3;
-        const uint32_t w0 = lds32(wa), w1 = lds32(wa + 4), w2 = lds32(wa + 8), w3 = lds32(wa + 12);
+        const int ea = kGPadL + e;  // entry e of the predecessor row
+        const uint32_t* const r32 = wsm + prow + (ea >> 1);
+        const uint32_t sh = (uint32_t)(ea & 1) << 4;
+        const uint32_t w0 = r32[0], w1 = r32[1], w2 = r32[2], w3 = r32[3];
         const uint32_t q0 = __funnelshift_r(w0, w1, sh), q1 = __funnelshift_r(w1, w2, sh),
                        q2 = __funnelshift_r(w2, w3, sh);
         const int v[6] = {(int)(q0 & 0xFFFFu), (int)(q0 >> 16), (int)(q1 & 0xFFFFu),
@@ -245,12 +241,12 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         if (keep) {
             const uint32_t pk0 = (uint32_t)L[0] | ((uint32_t)L[1] << 16);
             const uint32_t pk1 = (uint32_t)L[2] | ((uint32_t)L[3] << 16);
-            const uint32_t rw = nrow + 2u * kGPadL + 8u * j;
-            sts32(rw, pk0);
-            sts32(rw + 4, pk1);
+            uint32_t* const rw = wsm + nrow + kGPadL / 2 + 2 * j;
+            rw[0] = pk0;
+            rw[1] = pk1;
             if (GL == 4 || j < 4) {
-                sts32(rw + 2u * CAPN, kInf2);
-                sts32(rw + 2u * CAPN + 4, kInf2);
+                rw[CAPN / 2] = kInf2;
+                rw[CAPN / 2 + 1] = kInf2;
             }
             if (4 * j < w) *reinterpret_cast<uint32_t*>(Lv + ds.x + 4 * j) = __byte_perm(pk0, pk1, 0x6420);
             lo_old = lo;
@@ -271,7 +267,7 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         int kend = pass == 0 ? maxslen : cchk;
         // the pipeline: step k's descriptor (dcur) and wide vote (wcur) are known one step ahead,
         // its costs were loaded during step k - 1
-        uint2 dcur = dread(0, walker);
+        uint2 dcur = dread(0);
         unsigned wcur = __ballot_sync(kFull, walker && (int)(dcur.y >> 16) > CAPN && j == 0);
         fetch(0, dcur, wcur);
 
@@ -283,7 +279,7 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 const bool mine = walker && cstep + 1 == k;
                 bool eq = lo_old == ck_lo && w_old == ck_w;
                 if (mine) {
-                    const uint32_t* const pr = gptr(prow);
+                    const uint32_t* const pr = wsm + prow;
                     for (int t = j; t < (w_old + 1) / 2; t += GL) {
                         const uint32_t v = pr[kGPadL / 2 + t];
                         if (pass == 0) ckpt[t] = v;
@@ -316,11 +312,10 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
             } else {
                 __syncwarp();  // the rows of the last step are visible
             }
-            // the next step: descriptor, wide vote, costs
-            dcur = dread(k + 1, walker && !stop);
-            wcur = __ballot_sync(kFull, walker && !stop && k + 1 < slen &&
-                                            (int)(dcur.y >> 16) > CAPN && j == 0);
-            fetch(q ^ 1, dcur, wcur);
+            // the next step's descriptor now; its wide vote and cost loads after this step's
+            // work, so that neither waits in front of it
+            const bool nxt = walker && !stop && k + 1 < slen;
+            dcur = dread(k + 1);
 
             if (wb0 == 0u) {
                 narrow(ds, cn[q], go);
@@ -330,8 +325,8 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 // image border, a full-range frame)
                 const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
                 const uint32_t mm2 = (uint32_t)mm * 0x10001u, mP2 = (uint32_t)mP * 0x10001u;
-                const uint32_t* const pr = gptr(prow);
-                uint32_t* const nr = gptr(nrow);
+                const uint32_t* const pr = wsm + prow;
+                uint32_t* const nr = wsm + nrow;
                 uint32_t pm = kInf2;
 #pragma unroll
                 for (int c = 0; c < LPD / 8; ++c) {
@@ -390,8 +385,8 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 const int cap_old_g = __shfl_sync(kFull, cap_old, src);
                 const uint32_t mm2_g = (uint32_t)__shfl_sync(kFull, mm, src) * 0x10001u;
                 const uint32_t mP2_g = (uint32_t)__shfl_sync(kFull, mP, src) * 0x10001u;
-                const uint32_t* const rold = gptr(__shfl_sync(kFull, prow, src));
-                uint32_t* const rnew = gptr(__shfl_sync(kFull, nrow, src));
+                const uint32_t* const rold = wsm + __shfl_sync(kFull, prow, src);
+                uint32_t* const rnew = wsm + __shfl_sync(kFull, nrow, src);
                 constexpr int NPW = LPLW / 2;  // packed pairs per lane
                 const int e2 = min(max(lo_g - lo_old_g + LPLW * lane - 1, -(LPLW + 2)), cap_old_g);
                 const int b2 = kGPadL + e2;
@@ -445,8 +440,10 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                     mP = mg + P2;
                 }
             }
+            wcur = __ballot_sync(kFull, nxt && (int)(dcur.y >> 16) > CAPN && j == 0);
+            fetch(q ^ 1, dcur, wcur);
             if (go) {
-                const uint32_t t = nrow;
+                const int t = nrow;
                 nrow = (prow == rowA || prow == rowB) ? prow : (nrow == rowA ? rowB : rowA);
                 prow = t;
             }
@@ -465,7 +462,7 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         const int plo = __shfl_sync(kFull, lo_old, src), pcap = __shfl_sync(kFull, cap_old, src);
         const int pwid = __shfl_sync(kFull, w_old, src);
         const int pmm = __shfl_sync(kFull, mm, src), pmP = __shfl_sync(kFull, mP, src);
-        const uint32_t pprow = __shfl_sync(kFull, prow, src);
+        const int pprow = __shfl_sync(kFull, prow, src);
         walker = sg > 0 && slen > 0 && (pass == 0 || pchanged);
         if (!__any_sync(kFull, walker)) break;
         if (walker) {
