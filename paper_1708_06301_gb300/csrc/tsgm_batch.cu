@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__
         if (*b.status != 0u) continue;
         const int code = slot;
         const int nlines = code <= 1 ? b.H : (code <= 3 ? b.W : b.W + b.H - 1);
-        const int seg = code <= 1 ? grp_hseg(b.W, b.H) : 1;
+        const int seg = min(grp_seg(code <= 1 ? b.W : (code <= 3 ? b.H : min(b.W, b.H))), NG);
         sgm_group_lines<LPLW, GL>(b.C, b.desc, b.W, b.H, P1, P2, code,
                                   (item - tb->slot_base[slot][s]) * (NG / seg), nlines, seg,
                                   b.Lvol + (size_t)code * b.capacity, wsm);
@@ -420,7 +420,8 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
                 const BStream& s = b->h_streams[i];
                 const int code = slot;
                 const int nl = code <= 1 ? s.H : (code <= 3 ? s.W : s.W + s.H - 1);
-                const int per = NG / (code <= 1 ? grp_hseg(s.W, s.H) : 1);
+                const int seg = grp_seg(code <= 1 ? s.W : (code <= 3 ? s.H : std::min(s.W, s.H)));
+                const int per = NG / std::min(seg, NG);
                 item += (nl + per - 1) / per;
             }
             t.slot_base[slot][n_streams] = item;

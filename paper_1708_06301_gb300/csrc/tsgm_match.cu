@@ -205,7 +205,7 @@ static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int 
                                 const uint32_t* wq, cudaStream_t st) {
     int nwarps = 0;  // warps of the 4-groups-per-warp form, the larger count
     for (int s = 0; s < L.nslots; ++s) {
-        const int per = 4 / L.seg[s];
+        const int per = 4 / (L.seg[s] < 4 ? L.seg[s] : 4);
         nwarps += (L.count[s] + per - 1) / per;
     }
     const size_t smem = (size_t)kGrpWarps * grp_words<LPLW>() * sizeof(uint32_t);
@@ -228,7 +228,8 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
     for (int code = 0; code < n_paths; ++code) {
         L.code[code] = code;
         L.count[code] = code <= 1 ? Hh : (code <= 3 ? W : W + Hh - 1);
-        L.seg[code] = code <= 1 ? grp_hseg(W, Hh) : 1;  // long horizontal lines in segments
+        // long lines in segments
+        L.seg[code] = grp_seg(code <= 1 ? W : (code <= 3 ? Hh : (W < Hh ? W : Hh)));
     }
     if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
     if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);

@@ -135,12 +135,17 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     const int li = first_line + g / S, sg = g % S;
     int i0 = 0, stp = 0, llen = 0;
     if (li < nlines) line_geometry(code, li, W, Hh, i0, stp, llen);
-    // segment 0 is the shortest, so that every later one ends at the same step
+    // segment 0 is the shortest, so that every later one ends at the same step; a line too short
+    // to cut (a diagonal near a corner) is walked whole by its first group
     int slen = llen, p0 = i0;
     if (S > 1 && llen > 0) {
-        const int Lseg = (llen + S - 1) / S, len0 = llen - (S - 1) * Lseg;
-        slen = sg == 0 ? len0 : Lseg;
-        p0 = i0 + (sg == 0 ? 0 : len0 + (sg - 1) * Lseg) * stp;
+        if (llen >= 16 * S) {
+            const int Lseg = (llen + S - 1) / S, len0 = llen - (S - 1) * Lseg;
+            slen = sg == 0 ? len0 : Lseg;
+            p0 = i0 + (sg == 0 ? 0 : len0 + (sg - 1) * Lseg) * stp;
+        } else if (sg > 0) {
+            slen = 0;
+        }
     }
     const int maxslen = (int)__reduce_max_sync(kFull, (unsigned)slen);
     if (maxslen == 0) return;
@@ -483,17 +488,17 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
 struct GrpLines {
     int code[8];
     int count[8];
-    int seg[8];  // segments per line (1, 2 or 4)
+    int seg[8];  // segments per line (a power of two; the kernel takes at most its groups)
     int nslots;
 };
 
-// Segments per horizontal line of a W x Hh image: the lines are cut so that a segment (plus its
-// second walk) is about as long as the other directions' lines, at most 4 and only where every
-// segment stays at least 64 steps long.
-__host__ __device__ __forceinline__ int grp_hseg(int W, int Hh) {
-    const int target = Hh > 256 ? Hh : 256;
+// Segments per line for lines of up to `len` steps: as many (a power of two, at most 8) as keep
+// every segment at least kGSegMin steps long, so that the longest chain of the launch, a segment
+// plus its second walk, is short.
+constexpr int kGSegMin = 128;
+__host__ __device__ __forceinline__ int grp_seg(int len) {
     int S = 1;
-    while (S < 4 && W > S * target && W >= 2 * S * 64) S *= 2;
+    while (S < 8 && len >= 2 * S * kGSegMin) S *= 2;
     return S;
 }
 
@@ -503,13 +508,13 @@ __device__ __forceinline__ bool grp_warp_lines(const GrpLines& L, int NG, int gw
                                                int& first, int& nlines, int& seg) {
     int base = 0;
     for (int s = 0; s < L.nslots; ++s) {
-        const int per = NG / L.seg[s];
+        const int per = NG / min(L.seg[s], NG);
         const int nw = (L.count[s] + per - 1) / per;
         if (gw < base + nw) {
             code = L.code[s];
             first = (gw - base) * per;
             nlines = L.count[s];
-            seg = L.seg[s];
+            seg = min(L.seg[s], NG);
             return true;
         }
         base += nw;
