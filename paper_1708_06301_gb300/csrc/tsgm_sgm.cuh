@@ -280,7 +280,9 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         auto step = [&](int k, int q) -> bool {
             if (k == cchk) {
                 // the check after step cstep: save the state (first walk) or compare with it;
-                // the state is L over the window (lo, w), entries past w are +inf in every row
+                // the state is L over the window (lo, w), entries past w are +inf in every row.
+                // The rows of the last step were written by other lanes: synchronise first.
+                __syncwarp();
                 const bool mine = walker && cstep + 1 == k;
                 bool eq = lo_old == ck_lo && w_old == ck_w;
                 if (mine) {
@@ -299,6 +301,14 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 if (mine && pass > 0) {
                     stop = same;
                     changed = !same;
+                    // the walk goes on and rewrites the values after this step: they now follow
+                    // this state, so it becomes the reference of the next comparison
+                    if (!same) {
+                        const uint32_t* const pr = wsm + prow;
+                        for (int t = j; t < (w_old + 1) / 2; t += GL) ckpt[t] = pr[kGPadL / 2 + t];
+                        ck_lo = lo_old;
+                        ck_w = w_old;
+                    }
                 }
                 if (pass > 0 && __any_sync(kFull, changed)) kend = maxslen;
             }
@@ -476,9 +486,11 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
             cap_old = pcap;
             mm = pmm;
             mP = pmP;
-            // the first step reads the predecessor's row; this group's own rows are both free
+            // the first step reads the predecessor's row and writes the row of this group that
+            // does not hold its end state: the next segment, walking again in the same pass, may
+            // read that end state in this same step
+            nrow = prow == rowA ? rowB : rowA;
             prow = pprow;
-            nrow = rowA;
         }
     }
 }

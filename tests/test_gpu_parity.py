@@ -158,6 +158,11 @@ CASES = [
     (300, 20, 128, (9, 7), 8, ("mixed", (3, 12), (17, 32), 0.0, 0.0)),
     (1300, 6, 256, (5, 5), 4, ("rand", 1, 1, 1.0)),
     (1242, 16, 128, (9, 7), 8, ("border", (3, 12), 35)),
+    # vertical and diagonal lines in segments too, with slow agreement (3x3 census): several
+    # correction passes, where a segment walking again reads the end state of a predecessor
+    # that walks again in the same pass
+    (48, 600, 64, (3, 3), 8, ("rand", 1, 1, 1.0)),
+    (520, 520, 64, (3, 3), 8, ("mixed", (1, 16), (17, 40), 0.05, 0.05)),
 ]
 
 
