@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__
         if (*b.status != 0u) continue;
         const int code = slot;
         const int nlines = code <= 1 ? b.H : (code <= 3 ? b.W : b.W + b.H - 1);
-        const int seg = min(grp_seg(code <= 1 ? b.W : (code <= 3 ? b.H : min(b.W, b.H))), NG);
+        int seg = min(grp_seg(code <= 1 ? b.W : (code <= 3 ? b.H : min(b.W, b.H))), NG);
+        if (NG == 4 && code > 1) seg = 1;  // as grp_slot_seg
         sgm_group_lines<LPLW, GL>(b.C, b.desc, b.W, b.H, P1, P2, code,
                                   (item - tb->slot_base[slot][s]) * (NG / seg), nlines, seg,
                                   b.Lvol + (size_t)code * b.capacity, wsm);
@@ -420,8 +421,9 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
                 const BStream& s = b->h_streams[i];
                 const int code = slot;
                 const int nl = code <= 1 ? s.H : (code <= 3 ? s.W : s.W + s.H - 1);
-                const int seg = grp_seg(code <= 1 ? s.W : (code <= 3 ? s.H : std::min(s.W, s.H)));
-                const int per = NG / std::min(seg, NG);
+                int seg = std::min(grp_seg(code <= 1 ? s.W : (code <= 3 ? s.H : std::min(s.W, s.H))), NG);
+                if (NG == 4 && code > 1) seg = 1;  // as grp_slot_seg
+                const int per = NG / seg;
                 item += (nl + per - 1) / per;
             }
             t.slot_base[slot][n_streams] = item;

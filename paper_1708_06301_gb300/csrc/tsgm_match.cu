@@ -203,10 +203,14 @@ template <int LPLW>
 static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int Hh, int P1, int P2,
                                 const GrpLines& L, uint8_t* Lvol, uint64_t vol_stride,
                                 const uint32_t* wq, cudaStream_t st) {
-    int nwarps = 0;  // warps of the 4-groups-per-warp form, the larger count
-    for (int s = 0; s < L.nslots; ++s) {
-        const int per = 4 / (L.seg[s] < 4 ? L.seg[s] : 4);
-        nwarps += (L.count[s] + per - 1) / per;
+    int nwarps = 0;  // the larger count of the two forms (4 or 8 groups per warp)
+    for (int NG = 4; NG <= 8; NG *= 2) {
+        int nw = 0;
+        for (int s = 0; s < L.nslots; ++s) {
+            const int per = NG / grp_slot_seg(L, s, NG);
+            nw += (L.count[s] + per - 1) / per;
+        }
+        nwarps = nw > nwarps ? nw : nwarps;
     }
     const size_t smem = (size_t)kGrpWarps * grp_words<LPLW>() * sizeof(uint32_t);
     if (smem > 48 * 1024) {
