@@ -339,57 +339,45 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 // lane, in chunks of 8 (several wide windows at once: the full-range band at the
                 // image border, a full-range frame)
                 const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
+                const uint32_t mm2 = (uint32_t)mm * 0x10001u, mP2 = (uint32_t)mP * 0x10001u;
                 const uint32_t* const pr = wsm + prow;
                 uint32_t* const nr = wsm + nrow;
-                int mloc = kInf;
-                // one chunk at a time (few live registers); its two cost words are always the
-                // first two of the set, which shifts down by two after each chunk
-#pragma unroll 1
+                uint32_t pm = kInf2;
+#pragma unroll
                 for (int c = 0; c < LPD / 8; ++c) {
-                    // labels base .. base + 7 (from lo), in 32-bit arithmetic as in the narrow
-                    // step: the predecessor's entries e .. e + 9
-                    const int base = LPD * j + 8 * c;
+                    const int base = LPD * j + 8 * c;  // first label of the chunk, from lo
                     const int e = min(max(lo - lo_old + base - 1, -10), cap_old);
-                    const int ea = kGPadL + e;
-                    const uint32_t* const r32 = pr + (ea >> 1);
-                    const uint32_t sh = (uint32_t)(ea & 1) << 4;
-                    uint32_t wv[6];
+                    const int b = kGPadL + e;
+                    const uint32_t* r32 = pr + (b >> 1);
+                    const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
+                    uint32_t wv[6], A[5];
 #pragma unroll
                     for (int i = 0; i < 6; ++i) wv[i] = r32[i];
-                    int v[10];
 #pragma unroll
-                    for (int i = 0; i < 5; ++i) {
-                        const uint32_t pq = __funnelshift_r(wv[i], wv[i + 1], sh);
-                        v[2 * i] = (int)(pq & 0xFFFFu);
-                        v[2 * i + 1] = (int)(pq >> 16);
-                    }
-                    const uint32_t c4[2] = {cd[q][0], cd[q][1]};
+                    for (int i = 0; i < 5; ++i) A[i] = __byte_perm(wv[i], wv[i + 1], sel);
+                    const uint32_t c4a = cd[q][2 * c], c4b = cd[q][2 * c + 1];
+                    const uint32_t cp[4] = {__byte_perm(c4a, 0u, 0x4140), __byte_perm(c4a, 0u, 0x4342),
+                                            __byte_perm(c4b, 0u, 0x4140), __byte_perm(c4b, 0u, 0x4342)};
+                    const int rem = w - base;
+                    uint32_t Lc[4];
 #pragma unroll
-                    for (int i = 0; i + 2 < NWD; ++i) cd[q][i] = cd[q][i + 2];
-                    int L[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        int t = min(min(v[i], v[i + 2]) + P1, v[i + 1]);
-                        t = min(t, mP);
-                        const int cc = (int)((c4[i >> 2] >> (8 * (i & 3))) & 0xFFu);
-                        L[i] = (base + i < w) ? cc + t - mm : kInf;
-                        mloc = min(mloc, L[i]);
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t kp = pair_keep(rem - 2 * i);
+                        const uint32_t v = (cp[i] + grp_t(A[i], A[i + 1], P1x2, mP2)) - mm2;
+                        Lc[i] = (v & kp) | (kInf2 & ~kp);
+                        pm = vmin2(pm, Lc[i]);
                     }
                     if (go) {
-                        uint32_t pk[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            pk[i] = (uint32_t)L[2 * i] | ((uint32_t)L[2 * i + 1] << 16);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) nr[kGPadL / 2 + base / 2 + i] = pk[i];
-                        if (base < w)
-                            *reinterpret_cast<uint32_t*>(Lv + ds.x + base) = __byte_perm(pk[0], pk[1], 0x6420);
-                        if (base + 4 < w)
+                        for (int i = 0; i < 4; ++i) nr[kGPadL / 2 + base / 2 + i] = Lc[i];
+                        if (rem > 0)
+                            *reinterpret_cast<uint32_t*>(Lv + ds.x + base) = __byte_perm(Lc[0], Lc[1], 0x6420);
+                        if (rem > 4)
                             *reinterpret_cast<uint32_t*>(Lv + ds.x + base + 4) =
-                                __byte_perm(pk[2], pk[3], 0x6420);
+                                __byte_perm(Lc[2], Lc[3], 0x6420);
                     }
                 }
-                int m = mloc;
+                int m = (int)min(pm & 0xFFFFu, pm >> 16);
 #pragma unroll
                 for (int t = 1; t < GL; t <<= 1) m = min(m, __shfl_xor_sync(kFull, m, t));
                 if (go) {
