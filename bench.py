@@ -239,18 +239,14 @@ def run_reference(args, ws, rank):
 
 def mix_shape(i: int):
     """Stream i of the multi-stream workloads: 640x480 D=64, 1242x375 D=128, 1920x1080 D=256."""
-    return [(640, 480, 64), (1242, 375, 128), (1920, 1080, 256)][i % 3]
+    from paper_1708_06301_gb300 import synth
+    return synth.mix_shape(i)
 
 
 def render_mix(n_frames: int):
     """One rendered driving-shaped sequence per image size (focal length scaled with the width)."""
     from paper_1708_06301_gb300 import synth
-    out = {}
-    for k in range(3):
-        W, H, D = mix_shape(k)
-        out[(W, H)] = synth.make_sequence(100 + k, W, H, 721.0 * W / 1242.0, 0.54,
-                                          n_frames=n_frames, n_boxes=20, noise_sigma=2.0)
-    return out
+    return synth.camera_mix(n_frames)
 
 
 def bench_adjoint(dev, steps: int):
@@ -373,6 +369,82 @@ def bench_batched(dev, steps: int, warmup: int):
                              "peak_kind": kind, "avg_launch_us": sgm_s * 1e6,
                              "algorithmic_bytes_per_launch": agg_bytes},
             "step_hbm_frac": step_bytes / step_s / 1e9 / peak}
+
+
+BATCH_FRAMES = 4
+
+
+def bench_batched_frame(dev, steps: int, warmup: int):
+    """The whole time step of 32 camera streams (same size mix; streams of one size see the scene
+    from principal points 7 px apart) in one graph replay per step: prediction with gap filling,
+    windows, matching and update of every stream. The frames go back and forth through a
+    4-frame sequence (0 1 2 3 2 1 0 1 ...) with the true relative pose of each move; the first
+    step (no previous state) runs in the warm-up."""
+    import torch
+    from paper_1708_06301_gb300 import synth, tsgm
+    seqs = render_mix(BATCH_FRAMES)
+    NS = BATCH_STREAMS
+    params, Ls, Rs_img, Ks, bs, Ds, Ps = [], [], [], [], [], [], []
+    views = []
+    px = 0
+    for i in range(NS):
+        W, H, D = mix_shape(i)
+        sq = seqs[(W, H)]
+        left, right, K = synth.shifted_view(sq, 7 * (i // 3))
+        views.append(sq)
+        params.append(tsgm.default_params(W, H, d_max=D - 1, flags=tsgm.FLAG_FILL_GAPS))
+        Ls.append([torch.from_numpy(x).to(dev) for x in left])
+        Rs_img.append([torch.from_numpy(x).to(dev) for x in right])
+        Ks.append(K)
+        bs.append(np.float32(sq.cam.b))
+        Ds.append(torch.empty((H, W), dtype=torch.float32, device=dev))
+        Ps.append(torch.empty((H, W), dtype=torch.float32, device=dev))
+        px += W * H
+    Ks = np.stack(Ks)
+    bs = np.array(bs, np.float32)
+    cyc = list(range(BATCH_FRAMES)) + list(range(BATCH_FRAMES - 2, 0, -1))
+    order = [cyc[s_ % len(cyc)] for s_ in range(1 + warmup + steps)]
+    poses = {}
+    for a, b in zip(order[:-1], order[1:]):
+        if (a, b) not in poses:
+            per = [views[i].pose_between(a, b) for i in range(NS)]
+            poses[(a, b)] = (np.stack([x[0] for x in per]), np.stack([x[1] for x in per]))
+    st = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ms, cells = [], []
+    with tsgm.Batch(params, stream=st.cuda_stream) as bt:
+        def step(j):
+            f = order[j]
+            R, t = poses[(order[j - 1], f)] if j else (None, None)
+            bt.frame([x[f] for x in Ls], [x[f] for x in Rs_img], R, t, Ks, bs, Ds, Ps)
+        for j in range(1 + warmup):
+            step(j)
+        torch.cuda.synchronize()
+        l0 = bt.launches()
+        for j in range(1 + warmup, 1 + warmup + steps):
+            flush.fill_(float(j))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            step(j)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            cells.append(bt.cells()[0])
+        launches = bt.launches() - l0
+    step_s = float(np.mean(ms)) / 1000.0
+    mean_cells = float(np.mean(cells))
+    peak, kind = peaks()
+    step_bytes = algorithmic_step_bytes(int(mean_cells), px)
+    return {"workload": "32 streams: 11x 640x480 D=64, 11x 1242x375 D=128, 10x 1920x1080 D=256; "
+                        "rendered 4-frame driving sequences played back and forth; whole time step "
+                        "(prediction, gap filling, windows, matching, Kalman update); inputs larger "
+                        "than L2",
+            "px_per_step": px, "mean_cells_per_step": mean_cells,
+            "searched_fraction": mean_cells / sum(p.width * p.height * (p.d_max + 1) for p in params),
+            "ms_per_step": step_s * 1000.0, "frames_per_s": NS / step_s,
+            "kernels_per_step": launches / max(steps, 1),
+            "step_hbm_frac": step_bytes / step_s / 1e9 / peak, "peak_kind": kind,
+            "algorithmic_bytes_per_step": step_bytes}
 
 
 def bench_serving(duration_s: float, budget_gb: float):
@@ -641,6 +713,7 @@ def run_ours_on_stream(args, ws, rank, local, dev, stream):
     if not args.skip_forms:
         extra["adjoint"] = bench_adjoint(dev, 10)
         extra["batched"] = bench_batched(dev, max(3, args.steps // 2), 2)
+        extra["batched_frame"] = bench_batched_frame(dev, max(3, args.steps // 2), 3)
         extra["serving"] = bench_serving(args.serving_seconds, 64.0)
     cpu_s = sum(oracle_frames(seq, list(range(N_FRAMES))))
     n_threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()

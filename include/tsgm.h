@@ -329,8 +329,8 @@ tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
                                 const int16_t* const* d_hi, float* const* D_z, float* const* r_z,
                                 int32_t reps, double* best_ms, int32_t* best_shape);
 
-/* Total window cells of the last step over all streams, and how many streams were skipped for
- * lack of storage. Synchronises. */
+/* Total window cells of the last step over the streams that ran it, and how many of them were
+ * skipped for lack of storage. Synchronises. */
 tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed);
 
 /* One step run with direct launches instead of the graph, timed with CUDA events on the batch's
@@ -339,6 +339,35 @@ tsgm_status tsgm_batch_profile(tsgm_batch* b, const uint8_t* const* left,
                                const uint8_t* const* right, const int16_t* const* d_lo,
                                const int16_t* const* d_hi, float* const* D_z, float* const* r_z,
                                float* sgm_ms, float* step_ms);
+
+/* One time step of every stream (Sec. 2, the per-frame loop of tsgm_frame run for all streams at
+ * once): pose warp of the stream's previous state with the z-buffer (Eq. 3-6), gap filling
+ * (Eq. 7-8, with TSGM_FLAG_FILL_GAPS), the +-k sigma windows (Sec. 2.3; the whole range with
+ * TSGM_FLAG_FULL_RANGE), census, cost, aggregation, selection with the left-right check
+ * (Sec. 2.4, Eq. 9) and the Kalman update (Eq. 10-12). The previous state of each stream stays
+ * on the device inside the batch, so stream i's outputs equal those of a tsgm_frame context fed
+ * the same frames. The whole step is one CUDA graph (captured by the first call, replayed after).
+ *   left, right : host arrays of n_streams device pointers to W_i x H_i u8 images; a stream whose
+ *                 left and right are both NULL sits the step out (its state is kept)
+ *   R, t        : host arrays, n_streams x 9 and n_streams x 3 floats, the motion from the
+ *                 stream's previous frame to this one (Eq. 1-4); unread for a stream's first
+ *                 frame and for streams sitting out; may be NULL when no stream needs them
+ *   K, baseline : host arrays, n_streams x 9 floats (row-major intrinsics) and n_streams floats
+ *   D, P        : host arrays of n_streams device pointers to W_i x H_i f32 outputs (updated
+ *                 disparity and variance; -1 where neither a prediction nor a match exists)
+ * Stream parameters: flags, gamma_f and sigma_mult must be equal across streams and q finite
+ * >= 0; TSGM_FLAG_EDGE_REJECT, _PRED_LR_CHECK and _SAD_CHECK are not in the batched step
+ * (UNIMPLEMENTED); TSGM_FLAG_KEEP_INTERNALS is ignored. All arguments are checked before
+ * anything is enqueued: INVALID_ARG (null pointer of an active stream, D[i] == P[i], invalid
+ * pose or calibration, poses missing) leaves every stream's state as it was. Ordered on the
+ * batch's CUDA stream like tsgm_batch_match; a call waits for the previous step to finish. */
+tsgm_status tsgm_batch_frame(tsgm_batch* b, const uint8_t* const* left,
+                             const uint8_t* const* right, const float* R, const float* t,
+                             const float* K, const float* baseline, float* const* D,
+                             float* const* P);
+
+/* Forget every stream's previous state: the next tsgm_batch_frame is a first frame for all. */
+tsgm_status tsgm_batch_reset(tsgm_batch* b);
 
 /* Kernels launched by this batch (graph steps count their kernels). */
 tsgm_status tsgm_batch_launches(tsgm_batch* b, uint64_t* n);

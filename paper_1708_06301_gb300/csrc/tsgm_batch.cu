@@ -1,12 +1,17 @@
-// Batched matching over many camera streams of different sizes and disparity ranges (Sec. 2.3-2.4
-// applied to every stream): every stage is one launch over the work units of all streams (rows,
-// census tiles, pixels, path lines); the path aggregation is a persistent kernel whose warps pull
-// path lines from one global queue, ordered direction-major so that the long horizontal chains of
-// every stream start first and large and small streams balance; the whole step is captured once
-// in a CUDA graph and replayed. The launch shape of the aggregation is chosen by an autotuner that
-// times the candidates on the caller's data.
+// Batched processing of many camera streams of different sizes and disparity ranges: the
+// matching of caller windows (tsgm_batch_match, Sec. 2.3-2.4 applied to every stream) and the
+// whole time step (tsgm_batch_frame, Sec. 2: prediction, gap filling, windows, matching, update,
+// with every stream's state kept on the device). Every stage is one launch over the work units
+// of all streams (pixels, rows, census tiles, path lines); the path aggregation is a persistent
+// kernel whose warps pull path lines from one global queue, ordered direction-major so that the
+// long horizontal chains of every stream start first and large and small streams balance; each
+// form of the step is captured once in a CUDA graph and replayed. A stream can sit a step out
+// (tsgm_batch_frame with no images for it): its blocks return at once and its state stays. The
+// launch shape of the aggregation is chosen by an autotuner that times the candidates on the
+// caller's data.
 
 #include <algorithm>
+#include <cfloat>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -14,6 +19,7 @@
 #include <vector>
 
 #include "tsgm_kernels.cuh"
+#include "tsgm_predict.cuh"
 #include "tsgm_sgm.cuh"
 
 namespace {
@@ -47,6 +53,22 @@ struct BStream {
     uint8_t* C;
     uint8_t* Lvol;
     uint64_t capacity;  // cells of storage per volume (C and each direction of Lvol)
+    int active;         // 0: the stream sits this step out (time-step form)
+    // time-step form: the previous state, the prediction and its scratch, the matched maps
+    int has_prev;
+    WarpParams wp;
+    float q;
+    unsigned long long* keys;  // z-buffer, all empty between steps (the gather empties them)
+    float* stateD;
+    float* stateP;
+    float* predD;
+    float* predP;
+    float* tmpD;
+    float* tmpP;
+    float* Dm;  // matched disparity and variance (the form's own D_z, r_z)
+    float* rm;
+    float* outD;  // caller outputs of this step
+    float* outP;
 };
 
 struct BTable {
@@ -55,6 +77,7 @@ struct BTable {
     int tile_base[kMaxStreams + 1];  // prefix of census tiles (one image)
     int px_base[kMaxStreams + 1];    // prefix of pixels
     int tiles_x[kMaxStreams];
+    int pblk_base[kMaxStreams + 1];  // prefix of 256-pixel blocks
     // groups of path lines (the lines one warp walks together), direction-major: slot s holds the
     // lines of direction code s; items of stream i in slot s are [slot_base[s][i],
     // slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]
@@ -75,6 +98,7 @@ __global__ void __launch_bounds__(256) kb_sanitize(const BStream* __restrict__ s
                                                    const BTable* __restrict__ tb) {
     const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
     const BStream& b = st[s];
+    if (!b.active) return;
     sanitize_row(b.lo_in, b.hi_in, b.W, b.D, blockIdx.x - tb->row_base[s], b.lo, b.hi, b.rowsum,
                  b.rowcells, b.rowcells + b.H);
 }
@@ -83,6 +107,7 @@ __global__ void __launch_bounds__(512) kb_offsets(const BStream* __restrict__ st
                                                   const BTable* __restrict__ tb) {
     const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
     const BStream& b = st[s];
+    if (!b.active) return;
     const int y = blockIdx.x - tb->row_base[s];
     offsets_row(b.lo, b.hi, b.rowsum, b.rowcells, b.rowcells + b.H, b.W, b.H, y, b.off, b.desc,
                 b.cells, nullptr);
@@ -96,6 +121,7 @@ __global__ void __launch_bounds__(kCtW* kCtH) kb_census(const BStream* __restric
                                                          int ch) {
     const int s = find_stream(tb->tile_base, tb->ns, blockIdx.x);
     const BStream& b = st[s];
+    if (!b.active) return;
     const int t = blockIdx.x - tb->tile_base[s];
     const int tx = t % tb->tiles_x[s], ty = t / tb->tiles_x[s];
     census_tile<CW, CH>(blockIdx.z ? b.right : b.left, b.W, b.H, cw, ch, tx * kCtW, ty * kCtH,
@@ -110,7 +136,7 @@ __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
     for (int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 3; gi < total; gi += ngroups) {
         const int s = find_stream(tb->px_base, tb->ns, gi);
         const BStream& b = st[s];
-        if (*b.status != 0u) continue;
+        if (!b.active || *b.status != 0u) continue;
         cost_pixels(b.censusL, b.censusR, b.desc, b.W, b.n, Bc, b.C, gi - tb->px_base[s], sub, b.n);
     }
 }
@@ -136,7 +162,7 @@ __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__
         while (slot + 1 < n_slots && item >= tb->slot_base[slot + 1][0]) ++slot;
         const int s = find_stream(tb->slot_base[slot], tb->ns, item);
         const BStream& b = st[s];
-        if (*b.status != 0u) continue;
+        if (!b.active || *b.status != 0u) continue;
         const int code = slot;
         const int nlines = code <= 1 ? b.H : (code <= 3 ? b.W : b.W + b.H - 1);
         int seg = min(grp_seg(code <= 1 ? b.W : (code <= 3 ? b.H : min(b.W, b.H))), NG);
@@ -156,6 +182,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) kb_select(const BStream* __res
     const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
     const BStream& b = st[s];
     const int y = blockIdx.x - tb->row_base[s];
+    if (!b.active) return;
     if (*b.status != 0u) {
         for (int x = threadIdx.x; x < b.W; x += blockDim.x) {
             b.Dz[y * b.W + x] = -1.0f;
@@ -165,6 +192,85 @@ __global__ void __launch_bounds__(kSelThreads, 2) kb_select(const BStream* __res
     }
     select_row<NPATHS>(b.Lvol, b.capacity, b.desc, b.W, y, DP, s_thr, r_min, lr_tol, b.Dz, b.rz,
                        nullptr, nullptr, nullptr, nullptr, sel_smem, n_wide);
+}
+
+// ---- time-step form: one launch per stage over the pixels (256 per block) or rows of every
+// active stream
+
+// block b's stream and first pixel, or -1 when the stream sits the step out
+__device__ __forceinline__ int px_block(const BStream* __restrict__ st, const BTable* __restrict__ tb,
+                                        int& s) {
+    s = find_stream(tb->pblk_base, tb->ns, blockIdx.x);
+    return st[s].active ? (blockIdx.x - tb->pblk_base[s]) * 256 : -1;
+}
+
+// Prediction, scatter (Eq. 3, z-buffer): streams with a previous state only.
+__global__ void __launch_bounds__(256) kb_scatter(const BStream* __restrict__ st,
+                                                  const BTable* __restrict__ tb) {
+    int s;
+    const int p0 = px_block(st, tb, s);
+    const BStream& b = st[s];
+    const int i = p0 + threadIdx.x;
+    if (p0 < 0 || !b.has_prev || i >= b.n) return;
+    warp_scatter_px(i, b.W, b.H, b.stateD, b.stateP, b.wp, b.keys);
+}
+
+// Prediction, gather and variance (Eq. 5-6); empties the z-buffer for the next step. Without a
+// previous state: no prediction.
+__global__ void __launch_bounds__(256) kb_gather(const BStream* __restrict__ st,
+                                                 const BTable* __restrict__ tb) {
+    int s;
+    const int p0 = px_block(st, tb, s);
+    const BStream& b = st[s];
+    const int i = p0 + threadIdx.x;
+    if (p0 < 0 || i >= b.n) return;
+    if (b.has_prev) {
+        const unsigned long long key = b.keys[i];
+        b.keys[i] = kEmptyKey;
+        warp_gather_px(i, key, b.stateD, b.stateP, b.q, b.predD, b.predP);
+    } else {
+        b.predD[i] = -1.0f;
+        b.predP[i] = -1.0f;
+    }
+}
+
+// Gap filling of the prediction (Eq. 7-8): the horizontal pass into the scratch maps, then the
+// vertical one back into the prediction.
+__global__ void __launch_bounds__(256) kb_fill_gaps(const BStream* __restrict__ st,
+                                                    const BTable* __restrict__ tb, float gamma_f,
+                                                    int vertical) {
+    int s;
+    const int p0 = px_block(st, tb, s);
+    const BStream& b = st[s];
+    const int i = p0 + threadIdx.x;
+    if (p0 < 0 || !b.has_prev || i >= b.n) return;
+    if (vertical)
+        fill_gaps_px(i, b.W, b.H, b.tmpD, b.tmpP, gamma_f, 1, b.predD, b.predP);
+    else
+        fill_gaps_px(i, b.W, b.H, b.predD, b.predP, gamma_f, 0, b.tmpD, b.tmpP);
+}
+
+// Windows (Sec. 2.3), one block per row; full: every window the whole range.
+__global__ void __launch_bounds__(256) kb_windows(const BStream* __restrict__ st,
+                                                  const BTable* __restrict__ tb, float k,
+                                                  int full) {
+    const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
+    const BStream& b = st[s];
+    if (!b.active) return;
+    const int y = blockIdx.x - tb->row_base[s];
+    windows_row(b.predD, b.predP, b.W, b.D, k, y, b.lo, b.hi, b.rowsum, b.rowcells,
+                b.rowcells + b.H, full != 0);
+}
+
+// Kalman update (Eq. 10-12) into the caller's maps and the stream's state.
+__global__ void __launch_bounds__(256) kb_kalman(const BStream* __restrict__ st,
+                                                 const BTable* __restrict__ tb) {
+    int s;
+    const int p0 = px_block(st, tb, s);
+    const BStream& b = st[s];
+    const int i = p0 + threadIdx.x;
+    if (p0 < 0 || i >= b.n) return;
+    kalman_px(i, b.predD, b.predP, b.Dm, b.rm, b.outD, b.outP, b.stateD, b.stateP);
 }
 
 struct SgmShape {
@@ -222,6 +328,8 @@ struct tsgm_batch {
     BTable* h_table = nullptr;
     BTable* d_table = nullptr;
     int* d_counter = nullptr;
+    cudaGraphExec_t fgraph = nullptr;  // the time-step form
+    std::string step_err;  // why the time-step form cannot run on these streams ("" if it can)
     int shape = 3;  // index into kShapes
     int gl = 8;     // lanes per path line in the aggregation (4: windows up to 16 labels in one step)
     bool shape_ok[kNumShapes] = {};  // the shape's shared memory fits a block
@@ -316,6 +424,80 @@ tsgm_status capture(tsgm_batch* b) {
     return TSGM_OK;
 }
 
+// enqueue every stage of one time step of all streams (Sec. 2) on b->exec: prediction (warp,
+// gap filling), windows, census, cost, aggregation, selection, Kalman update
+cudaError_t enqueue_frame_step(tsgm_batch* b, int shape) {
+    const tsgm_params& p = b->prm;
+    cudaStream_t st = b->exec;
+    const BTable& t = *b->h_table;
+    cudaError_t e = cudaMemcpyAsync(b->d_streams, b->h_streams, sizeof(BStream) * b->ns,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    const int rows = t.row_base[b->ns];
+    const int pblocks = t.pblk_base[b->ns];
+    kb_scatter<<<pblocks, 256, 0, st>>>(b->d_streams, b->d_table);
+    kb_gather<<<pblocks, 256, 0, st>>>(b->d_streams, b->d_table);
+    if (p.flags & TSGM_FLAG_FILL_GAPS) {
+        kb_fill_gaps<<<pblocks, 256, 0, st>>>(b->d_streams, b->d_table, p.gamma_f, 0);
+        kb_fill_gaps<<<pblocks, 256, 0, st>>>(b->d_streams, b->d_table, p.gamma_f, 1);
+    }
+    kb_windows<<<rows, 256, 0, st>>>(b->d_streams, b->d_table, p.sigma_mult,
+                                     (p.flags & TSGM_FLAG_FULL_RANGE) ? 1 : 0);
+    kb_offsets<<<rows, 512, 0, st>>>(b->d_streams, b->d_table);
+    {
+        const dim3 cg(t.tile_base[b->ns], 1, 2), cb(kCtW, kCtH);
+        if (p.census_w == 9 && p.census_h == 7)
+            kb_census<9, 7><<<cg, cb, 0, st>>>(b->d_streams, b->d_table, p.census_w, p.census_h);
+        else if (p.census_w == 5 && p.census_h == 5)
+            kb_census<5, 5><<<cg, cb, 0, st>>>(b->d_streams, b->d_table, p.census_w, p.census_h);
+        else
+            kb_census<0, 0><<<cg, cb, 0, st>>>(b->d_streams, b->d_table, p.census_w, p.census_h);
+    }
+    kb_cost<<<b->sms * 8, 256, 0, st>>>(b->d_streams, b->d_table, p.census_w * p.census_h - 1);
+    if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+    const SgmShape sh = kShapes[shape];
+    sgm_kernel(b->maxD, b->gl, sh.warps)<<<b->sms * sh.blocks, sh.warps * 32,
+                                           sgm_smem_bytes(b->maxD, b->gl, sh.warps), st>>>(
+        b->d_streams, b->d_table, p.n_paths, p.P1, p.P2, b->d_counter);
+    const int DP = 256;
+    const size_t sel_smem = (size_t)((4 * b->maxW + 1) & ~1) * 4 + (size_t)(kSelThreads / 32) * DP * 2;
+    const float s_thr = p.S_max * (float)p.n_paths;
+    if (p.n_paths == 8)
+        kb_select<8><<<rows, kSelThreads, sel_smem, st>>>(b->d_streams, b->d_table, DP, s_thr,
+                                                          p.r_min, p.lr_tol);
+    else
+        kb_select<4><<<rows, kSelThreads, sel_smem, st>>>(b->d_streams, b->d_table, DP, s_thr,
+                                                          p.r_min, p.lr_tol);
+    kb_kalman<<<pblocks, 256, 0, st>>>(b->d_streams, b->d_table);
+    return cudaGetLastError();
+}
+
+// kernels of one time step (the census counts as one: both images in one launch)
+int frame_kernels(const tsgm_batch* b) {
+    return 9 + ((b->prm.flags & TSGM_FLAG_FILL_GAPS) ? 2 : 0);
+}
+
+tsgm_status capture_frame(tsgm_batch* b) {
+    if (b->fgraph) {
+        cudaGraphExecDestroy(b->fgraph);
+        b->fgraph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->exec, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "begin capture");
+    cudaError_t e2 = enqueue_frame_step(b, b->shape);
+    e = cudaStreamEndCapture(b->exec, &g);
+    if (e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bcuda(b, e2, "capture time step");
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "end capture");
+    e = cudaGraphInstantiate(&b->fgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bcuda(b, e, "instantiate graph");
+    return TSGM_OK;
+}
+
 tsgm_status set_io(tsgm_batch* b, const uint8_t* const* left, const uint8_t* const* right,
                    const int16_t* const* d_lo, const int16_t* const* d_hi, float* const* D_z,
                    float* const* r_z) {
@@ -332,6 +514,7 @@ tsgm_status set_io(tsgm_batch* b, const uint8_t* const* left, const uint8_t* con
         s.hi_in = d_hi[i];
         s.Dz = D_z[i];
         s.rz = r_z[i];
+        s.active = 1;
     }
     return TSGM_OK;
 }
@@ -364,6 +547,14 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
     tsgm_batch* b = new (std::nothrow) tsgm_batch();
     if (!b) return TSGM_ERR_OUT_OF_MEMORY;
     b->prm = p0;
+    // the time-step form runs one prediction and window rule over all streams
+    for (int i = 0; i < n_streams && b->step_err.empty(); ++i) {
+        const tsgm_params& p = streams[i];
+        if (p.flags != p0.flags || p.gamma_f != p0.gamma_f || p.sigma_mult != p0.sigma_mult)
+            b->step_err = "tsgm_batch_frame: flags, gamma_f and sigma_mult differ across streams";
+        else if (!(p.q >= 0.0f && p.q <= FLT_MAX) || !(p.sigma_mult >= 0.0f && p.sigma_mult <= FLT_MAX))
+            b->step_err = "tsgm_batch_frame: q and sigma_mult must be finite and >= 0";
+    }
     b->ns = n_streams;
     b->user = (cudaStream_t)cuda_stream;
     int dev = 0;
@@ -402,11 +593,18 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
                  balloc(b, &s.rowsum, (size_t)s.H) && balloc(b, &s.rowcells, 2 * (size_t)s.H) &&
                  balloc(b, &s.cells, 2) && balloc(b, &s.status, 1) &&
                  balloc(b, &s.C, (size_t)s.capacity + 64) &&
-                 balloc(b, &s.Lvol, (size_t)s.capacity * p0.n_paths + 64);
+                 balloc(b, &s.Lvol, (size_t)s.capacity * p0.n_paths + 64) &&
+                 // time-step form: z-buffer, state, prediction and its scratch, matched maps
+                 balloc(b, &s.keys, n) && balloc(b, &s.stateD, n) && balloc(b, &s.stateP, n) &&
+                 balloc(b, &s.predD, n) && balloc(b, &s.predP, n) && balloc(b, &s.tmpD, n) &&
+                 balloc(b, &s.tmpP, n) && balloc(b, &s.Dm, n) && balloc(b, &s.rm, n) &&
+                 cudaMemset(s.keys, 0xFF, n * sizeof(unsigned long long)) == cudaSuccess;
+            s.q = p.q;
             t.row_base[i + 1] = t.row_base[i] + s.H;
             t.tiles_x[i] = (s.W + kCtW - 1) / kCtW;
             t.tile_base[i + 1] = t.tile_base[i] + t.tiles_x[i] * ((s.H + kCtH - 1) / kCtH);
             t.px_base[i + 1] = t.px_base[i] + s.n;
+            t.pblk_base[i + 1] = t.pblk_base[i] + (s.n + 255) / 256;
         }
         // lines per warp: windows of up to 16 labels fit the 4-lane groups (8 lines per warp),
         // wider ones (up to 32 in one step) the 8-lane groups
@@ -466,6 +664,7 @@ void tsgm_batch_destroy(tsgm_batch* b) {
     if (!b) return;
     if (b->exec) cudaStreamSynchronize(b->exec);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
     for (void* q : b->allocs) cudaFree(q);
     if (b->h_streams) cudaFreeHost(b->h_streams);
     if (b->h_table) cudaFreeHost(b->h_table);
@@ -483,11 +682,12 @@ tsgm_status tsgm_batch_match(tsgm_batch* b, const uint8_t* const* left,
                              const uint8_t* const* right, const int16_t* const* d_lo,
                              const int16_t* const* d_hi, float* const* D_z, float* const* r_z) {
     if (!b) return TSGM_ERR_INVALID_ARG;
-    tsgm_status s = set_io(b, left, right, d_lo, d_hi, D_z, r_z);
-    if (s != TSGM_OK) return s;
-    // the graph reads the pinned table when it runs: wait for the previous replay first
+    // the graph reads the pinned table when it runs: wait for the previous replay before
+    // rewriting it
     cudaError_t e = cudaEventSynchronize(b->ev_out);
     if (e != cudaSuccess) return bcuda(b, e, "previous batch step");
+    tsgm_status s = set_io(b, left, right, d_lo, d_hi, D_z, r_z);
+    if (s != TSGM_OK) return s;
     if (!b->graph && (s = capture(b)) != TSGM_OK) return s;
     if ((e = cudaEventRecord(b->ev_in, b->user)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(b->exec, b->ev_in, 0)) != cudaSuccess ||
@@ -533,6 +733,10 @@ tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
     cudaEventDestroy(z);
     if (e != cudaSuccess) return bcuda(b, e, "autotune");
     b->shape = best_i;
+    if (b->fgraph) {  // the time-step form is captured again with the new shape when next used
+        cudaGraphExecDestroy(b->fgraph);
+        b->fgraph = nullptr;
+    }
     if ((s = capture(b)) != TSGM_OK) return s;
     if (best_ms) *best_ms = best;
     if (best_shape) *best_shape = best_i;
@@ -546,6 +750,7 @@ tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed
     uint64_t tot = 0;
     int32_t over = 0;
     for (int i = 0; i < b->ns; ++i) {
+        if (!b->h_streams[i].active) continue;  // sat the last step out
         uint32_t c = 0, st = 0;
         if (cudaMemcpy(&c, b->h_streams[i].cells, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(&st, b->h_streams[i].status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -579,6 +784,79 @@ tsgm_status tsgm_batch_profile(tsgm_batch* b, const uint8_t* const* left,
     if (z) cudaEventDestroy(z);
     if (e != cudaSuccess) return bcuda(b, e, "tsgm_batch_profile");
     b->launches += 6;
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_batch_frame(tsgm_batch* b, const uint8_t* const* left,
+                             const uint8_t* const* right, const float* R, const float* t,
+                             const float* K, const float* baseline, float* const* D,
+                             float* const* P) {
+    if (!b) return TSGM_ERR_INVALID_ARG;
+    const tsgm_params& p = b->prm;
+    if (!b->step_err.empty()) return bfail(b, TSGM_ERR_INVALID_ARG, b->step_err);
+    if (p.flags & (TSGM_FLAG_EDGE_REJECT | TSGM_FLAG_PRED_LR_CHECK | TSGM_FLAG_SAD_CHECK))
+        return bfail(b, TSGM_ERR_UNIMPLEMENTED,
+                     "tsgm_batch_frame: edge rejection and the consistency checks of the "
+                     "prediction and update are not in the batched step");
+    if (!left || !right || !K || !baseline || !D || !P)
+        return bfail(b, TSGM_ERR_INVALID_ARG, "tsgm_batch_frame: null pointer array");
+    // every argument is checked before anything is changed or enqueued
+    std::vector<WarpParams> wps((size_t)b->ns);
+    for (int i = 0; i < b->ns; ++i) {
+        if (!left[i] && !right[i]) continue;  // this stream sits the step out
+        if (!left[i] || !right[i] || !D[i] || !P[i])
+            return bfail(b, TSGM_ERR_INVALID_ARG,
+                         "tsgm_batch_frame: null pointer for stream " + std::to_string(i));
+        if (D[i] == P[i])
+            return bfail(b, TSGM_ERR_INVALID_ARG,
+                         "tsgm_batch_frame: D and P alias for stream " + std::to_string(i));
+        const BStream& hs = b->h_streams[i];
+        const float* Ki = K + 9 * i;
+        wps[i].cx = Ki[2];
+        wps[i].cy = Ki[5];
+        if (hs.has_prev) {
+            if (!R || !t)
+                return bfail(b, TSGM_ERR_INVALID_ARG,
+                             "tsgm_batch_frame: poses required after a stream's first frame");
+            if (tsgm_build_H(R + 9 * i, t + 3 * i, Ki, baseline[i], wps[i].h) != TSGM_OK)
+                return bfail(b, TSGM_ERR_INVALID_ARG,
+                             "tsgm_batch_frame: invalid pose or calibration for stream " +
+                                 std::to_string(i));
+        }
+    }
+    cudaError_t e = cudaEventSynchronize(b->ev_out);
+    if (e != cudaSuccess) return bcuda(b, e, "previous batch step");
+    for (int i = 0; i < b->ns; ++i) {
+        BStream& hs = b->h_streams[i];
+        hs.active = left[i] ? 1 : 0;
+        if (!hs.active) continue;
+        hs.left = left[i];
+        hs.right = right[i];
+        hs.outD = D[i];
+        hs.outP = P[i];
+        hs.Dz = hs.Dm;
+        hs.rz = hs.rm;
+        hs.wp = wps[i];
+    }
+    tsgm_status s;
+    if (!b->fgraph && (s = capture_frame(b)) != TSGM_OK) return s;
+    if ((e = cudaEventRecord(b->ev_in, b->user)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->exec, b->ev_in, 0)) != cudaSuccess ||
+        (e = cudaGraphLaunch(b->fgraph, b->exec)) != cudaSuccess ||
+        (e = cudaEventRecord(b->ev_out, b->exec)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->user, b->ev_out, 0)) != cudaSuccess)
+        return bcuda(b, e, "batch time step");
+    b->launches += frame_kernels(b);
+    for (int i = 0; i < b->ns; ++i)
+        if (b->h_streams[i].active) b->h_streams[i].has_prev = 1;
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_batch_reset(tsgm_batch* b) {
+    if (!b) return TSGM_ERR_INVALID_ARG;
+    cudaError_t e = cudaEventSynchronize(b->ev_out);
+    if (e != cudaSuccess) return bcuda(b, e, "previous batch step");
+    for (int i = 0; i < b->ns; ++i) b->h_streams[i].has_prev = 0;
     return TSGM_OK;
 }
 

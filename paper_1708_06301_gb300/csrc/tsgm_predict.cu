@@ -8,6 +8,7 @@
 #include <cfloat>
 
 #include "tsgm_kernels.cuh"
+#include "tsgm_predict.cuh"
 
 namespace tsgm {
 namespace {
@@ -20,45 +21,13 @@ using namespace dev;
 // value, so the complement makes atomicMin keep the largest d') above the source index (equal
 // d' -> lowest index).
 // ---------------------------------------------------------------------------------------------
-struct WarpParams {
-    float h[16];
-    float cx, cy;
-};
-
 __global__ void __launch_bounds__(256) k_warp_scatter(const float* __restrict__ Dprev,
                                                       const float* __restrict__ Pprev,
                                                       WarpParams wp, int W, int Hh,
                                                       unsigned long long* __restrict__ keys) {
     const int n = W * Hh;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float d = Dprev[i];
-        const float p = Pprev[i];
-        if (!(d > 0.0f && d <= FLT_MAX && valid_value(p))) continue;
-        const int v = i / W;
-        const int u = i - v * W;
-        const float xt = __fsub_rn((float)u, wp.cx);
-        const float yt = __fsub_rn((float)v, wp.cy);
-        float w[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float* h = wp.h + 4 * r;
-            float s = __fadd_rn(__fmul_rn(h[0], xt), __fmul_rn(h[1], yt));
-            s = __fadd_rn(s, __fmul_rn(h[2], d));
-            w[r] = __fadd_rn(s, h[3]);
-        }
-        if (!(w[3] > 0.0f)) continue;
-        const float xp = __fdiv_rn(w[0], w[3]);
-        const float yp = __fdiv_rn(w[1], w[3]);
-        const float dp = __fdiv_rn(w[2], w[3]);
-        if (!(dp > 0.0f && dp <= FLT_MAX)) continue;
-        const float fx = floorf(__fadd_rn(__fadd_rn(xp, wp.cx), 0.5f));
-        const float fy = floorf(__fadd_rn(__fadd_rn(yp, wp.cy), 0.5f));
-        if (!(fx >= 0.0f && fx <= (float)(W - 1) && fy >= 0.0f && fy <= (float)(Hh - 1))) continue;
-        const int tgt = (int)fy * W + (int)fx;
-        const unsigned long long key =
-            ((unsigned long long)(~__float_as_uint(dp)) << 32) | (unsigned long long)(unsigned)i;
-        atomicMin(keys + tgt, key);
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        warp_scatter_px(i, W, Hh, Dprev, Pprev, wp, keys);
 }
 
 // Warp gather + variance prediction (Eq. 5-6): p' = (d'/d)^2 p + q.
@@ -67,19 +36,8 @@ __global__ void __launch_bounds__(256) k_warp_gather(const unsigned long long* _
                                                      const float* __restrict__ Pprev, float q,
                                                      int n, float* __restrict__ Dpred,
                                                      float* __restrict__ Ppred) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const unsigned long long key = keys[i];
-        float dp = -1.0f, pp = -1.0f;
-        if (key != kEmptyKey) {
-            const unsigned src = (unsigned)(key & 0xFFFFFFFFull);
-            dp = __uint_as_float(~(unsigned)(key >> 32));
-            const float phi = __fdiv_rn(dp, Dprev[src]);
-            const float phi2 = __fmul_rn(phi, phi);
-            pp = __fadd_rn(__fmul_rn(phi2, Pprev[src]), q);
-        }
-        Dpred[i] = dp;
-        Ppred[i] = pp;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        warp_gather_px(i, keys[i], Dprev, Pprev, q, Dpred, Ppred);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -95,31 +53,9 @@ __global__ void __launch_bounds__(256) k_windows(const float* __restrict__ Dp,
                                                  uint32_t* __restrict__ rowcells,
                                                  uint32_t* __restrict__ rowwide,
                                                  uint32_t* __restrict__ wq) {
-    __shared__ uint32_t sh[33];
     const int y = blockIdx.x;
     if (y == 0 && threadIdx.x == 0) wq[0] = 0u;  // the offsets pass queues this image's wide pixels
-    uint32_t acc = 0, acc_true = 0, acc_wide = 0;
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const int i = y * W + x;
-        const float d = Dp[i], p = Pp[i];
-        int a = 0, b = D - 1;
-        if (valid_value(d) && valid_value(p)) {
-            const float s = __fsqrt_rn(p);
-            const float r = __fmul_rn(k, s);
-            const float lo_f = floorf(__fsub_rn(d, r));
-            const float hi_f = ceilf(__fadd_rn(d, r));
-            if (lo_f <= (float)(D - 1) && hi_f >= 0.0f) {
-                a = lo_f < 0.0f ? 0 : (int)lo_f;
-                b = hi_f > (float)(D - 1) ? D - 1 : (int)hi_f;
-            }
-        }
-        lo[i] = (int16_t)a;
-        hi[i] = (int16_t)b;
-        acc_true += (uint32_t)(b - a + 1);
-        acc += block_cells(b - a + 1);
-        acc_wide += (b - a + 1 > kNarrowMax) ? 1u : 0u;
-    }
-    row_totals(acc, acc_true, acc_wide, y, sh, rowsum, rowcells, rowwide);
+    windows_row(Dp, Pp, W, D, k, y, lo, hi, rowsum, rowcells, rowwide);
 }
 
 // Caller-supplied windows, clamped copies and row totals (see sanitize_row).
@@ -155,35 +91,8 @@ __global__ void __launch_bounds__(256) k_kalman(const float* __restrict__ Dp,
                                                 const float* __restrict__ Dz,
                                                 const float* __restrict__ rz, int n,
                                                 float* D, float* P, float* D2, float* P2) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float dp = Dp[i], pp = Pp[i], dz = Dz[i], r = rz[i];
-        const bool pv = valid_value(dp) && valid_value(pp);
-        const bool mv = valid_value(dz) && valid_value(r);
-        float d, p;
-        if (pv && mv) {
-            const float K = __fdiv_rn(pp, __fadd_rn(pp, r));
-            d = __fadd_rn(dp, __fmul_rn(K, __fsub_rn(dz, dp)));
-            p = __fmul_rn(__fsub_rn(1.0f, K), pp);
-        } else if (mv) {
-            d = dz;
-            p = r;
-        } else if (pv) {
-            d = dp;
-            p = pp;
-        } else {
-            d = -1.0f;
-            p = -1.0f;
-        }
-        D[i] = d;
-        P[i] = p;
-        if (D2) {
-            // the state for the next frame keeps only measured pixels: where the match was
-            // rejected the true minimum may lie outside the window, so the next frame searches
-            // the whole range there (Sec. 2.4, disparity consistency check)
-            D2[i] = mv ? d : -1.0f;
-            P2[i] = mv ? p : -1.0f;
-        }
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        kalman_px(i, Dp, Pp, Dz, rz, D, P, D2, P2);
 }
 
 // Gap filling (Eq. 7-8), one pass: horizontal (vertical == 0) or vertical neighbours, reading
@@ -194,25 +103,8 @@ __global__ void __launch_bounds__(256) k_fill_gaps(const float* __restrict__ Din
                                                    float* __restrict__ Dout,
                                                    float* __restrict__ Pout) {
     const int n = W * Hh;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float d = Din[i], p = Pin[i];
-        if (!(valid_value(d) && valid_value(p))) {
-            const int y = i / W, x = i - y * W;
-            const bool inner = vertical ? (y > 0 && y < Hh - 1) : (x > 0 && x < W - 1);
-            if (inner) {
-                const int a = vertical ? i - W : i - 1;
-                const int b = vertical ? i + W : i + 1;
-                const float da = Din[a], db = Din[b], pa = Pin[a], pb = Pin[b];
-                if (valid_value(da) && valid_value(pa) && valid_value(db) && valid_value(pb) &&
-                    fabsf(__fsub_rn(da, db)) < gamma_f) {
-                    d = __fmul_rn(__fadd_rn(da, db), 0.5f);
-                    p = __fmul_rn(__fadd_rn(pa, pb), 0.5f);
-                }
-            }
-        }
-        Dout[i] = d;
-        Pout[i] = p;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        fill_gaps_px(i, W, Hh, Din, Pin, gamma_f, vertical, Dout, Pout);
 }
 
 __global__ void __launch_bounds__(256) k_fill(float* __restrict__ a, float v, int n) {

@@ -298,6 +298,37 @@ def kitti_like(seed: int = 2, n_frames: int = 10) -> Sequence:
                          step_range=(0.5, 1.5), yaw_deg=2.0, noise_sigma=2.0)
 
 
+MIX_SHAPES = [(640, 480, 64), (1242, 375, 128), (1920, 1080, 256)]
+
+
+def mix_shape(i: int):
+    """(W, H, D) of stream i of the multi-camera workloads: 640x480 D=64, 1242x375 D=128,
+    1920x1080 D=256 in turn."""
+    return MIX_SHAPES[i % 3]
+
+
+def camera_mix(n_frames: int) -> dict:
+    """One driving-shaped sequence per image size of the multi-camera workloads, keyed (W, H):
+    ground + 20 boxes, noise sigma 2, focal length 721 px scaled with the width, baseline 0.54 m."""
+    out = {}
+    for k, (W, H, _) in enumerate(MIX_SHAPES):
+        out[(W, H)] = make_sequence(100 + k, W, H, 721.0 * W / 1242.0, 0.54, n_frames=n_frames,
+                                    n_boxes=20, noise_sigma=2.0)
+    return out
+
+
+def shifted_view(seq: Sequence, shift: int):
+    """The sequence seen by a camera whose principal point sits `shift` pixels further right:
+    both views of every frame rolled right by `shift` columns (the wrapped columns are the only
+    pixels not consistent with the geometry) and the intrinsics' cx moved with them. Gives
+    streams of one size distinct images with the same motion."""
+    K = seq.K.astype(np.float32).copy()
+    K[0, 2] += shift
+    left = [np.ascontiguousarray(np.roll(x, shift, axis=1)) for x in seq.left]
+    right = [np.ascontiguousarray(np.roll(x, shift, axis=1)) for x in seq.right]
+    return left, right, K
+
+
 def random_maps(seed: int, W: int, H: int, d_range=(1.0, 127.0), p_range=(0.1, 4.0),
                 invalid_frac: float = 0.0):
     """Random previous disparity/variance maps (float32), optionally with invalid (-1) pixels."""

@@ -99,6 +99,8 @@ _SIGS = {
     "tsgm_batch_cells": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_int32)]),
     "tsgm_batch_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "tsgm_batch_frame": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tsgm_batch_reset": (ctypes.c_int, [_vp]),
     "tsgm_batch_profile": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_float)]),
@@ -488,6 +490,43 @@ class Batch:
     def match(self, lefts, rights, los, his, Dzs, rzs):
         self._check(self.lib.tsgm_batch_match(self.h, *self._arrs(lefts, rights, los, his, Dzs, rzs)),
                     "tsgm_batch_match")
+
+    def frame(self, lefts, rights, Rs, ts, Ks, baselines, Ds, Ps):
+        """One time step of every stream (tsgm_batch_frame). lefts[i] = rights[i] = None: stream i
+        sits the step out. Rs (n x 3 x 3), ts (n x 3) may be None when no stream has a previous
+        frame; Ks (n x 3 x 3), baselines (n) float32."""
+        lefts, rights = list(lefts), list(rights)
+        if len(lefts) != self.n or len(rights) != self.n:
+            raise ValueError(f"expected {self.n} image pairs")
+        act = [l is not None for l in lefts]
+        if any((r is not None) != a for r, a in zip(rights, act)):
+            raise ValueError("left and right must both be given or both be None")
+
+        def arr(xs, esize, what):
+            xs = list(xs)
+            if len(xs) != self.n:
+                raise ValueError(f"{what}: expected {self.n} buffers, got {len(xs)}")
+            ptrs = [_dptr(x, int(p.width) * int(p.height), esize, f"{what}[{i}]") if a else None
+                    for i, (x, p, a) in enumerate(zip(xs, self.params, act))]
+            return (ctypes.c_void_p * self.n)(*ptrs)
+
+        def host(x, shape):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(x, np.float32).reshape(shape))
+            return a
+
+        R = host(Rs, (self.n, 9))
+        t = host(ts, (self.n, 3))
+        K = host(Ks, (self.n, 9))
+        b = host(baselines, (self.n,))
+        fp = lambda a: None if a is None else a.ctypes.data_as(_vp)
+        self._check(self.lib.tsgm_batch_frame(self.h, arr(lefts, 1, "lefts"), arr(rights, 1, "rights"),
+                                              fp(R), fp(t), fp(K), fp(b), arr(Ds, 4, "Ds"),
+                                              arr(Ps, 4, "Ps")), "tsgm_batch_frame")
+
+    def reset(self):
+        self._check(self.lib.tsgm_batch_reset(self.h), "tsgm_batch_reset")
 
     def autotune(self, lefts, rights, los, his, Dzs, rzs, reps: int = 3):
         ms = ctypes.c_double(0)
