@@ -302,13 +302,17 @@ tsgm_status tsgm_adjoint_backward(tsgm_ctx* ctx, const float* prev_D, const floa
  * ------------------------------------------------------------------------------------------- */
 typedef struct tsgm_batch tsgm_batch;
 
-/* streams[i] gives width, height and d_max of stream i (n_streams <= 128); the matching
- * parameters (census window, paths, P1, P2, S_max, r_min, lr_tol) must be equal across streams.
- * max_labels > 0 sizes every stream's ragged volumes for windows of that many labels on average
- * (0: d_max + 1, never too small); a call whose windows need more cells than a stream's storage
- * skips that stream and writes -1 to its outputs (reported by tsgm_batch_cells). The batch works
- * on its own CUDA stream, ordered after and before `cuda_stream` (NULL: legacy default stream)
- * with events. Errors: INVALID_ARG, OUT_OF_MEMORY. */
+/* streams[i] gives width, height and d_max of stream i (n_streams <= 128, W x H x (d_max + 1)
+ * below 2^32); the matching parameters (census window, paths, P1, P2, S_max, r_min, lr_tol) must
+ * be equal across streams. The ragged cost and path volumes of all streams live in one pool of
+ * sum_i W_i x H_i x L_i cells per volume, L_i = max_labels (or d_max + 1 if smaller or if
+ * max_labels is 0) rounded up to 4. Every step each stream that runs reserves the padded cells of
+ * its windows from the pool, streams refused at the previous step first, then in stream order;
+ * a stream that does not fit the cells left is refused for this step (tsgm_batch_stream_status):
+ * tsgm_batch_match writes -1 to its outputs, tsgm_batch_frame leaves its outputs and state as
+ * they were. With max_labels = 0 every stream always fits. The batch works on its own CUDA
+ * stream, ordered after and before `cuda_stream` (NULL: legacy default stream) with events.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY. */
 tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int32_t max_labels,
                               void* cuda_stream, tsgm_batch** out);
 void tsgm_batch_destroy(tsgm_batch* b);
@@ -329,8 +333,8 @@ tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
                                 const int16_t* const* d_hi, float* const* D_z, float* const* r_z,
                                 int32_t reps, double* best_ms, int32_t* best_shape);
 
-/* Total window cells of the last step over the streams that ran it, and how many of them were
- * skipped for lack of storage. Synchronises. */
+/* Total window cells of the last step over the streams that ran it, and how many streams were
+ * refused for lack of pool cells. Synchronises. */
 tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed);
 
 /* One step run with direct launches instead of the graph, timed with CUDA events on the batch's
@@ -355,8 +359,13 @@ tsgm_status tsgm_batch_profile(tsgm_batch* b, const uint8_t* const* left,
  *   K, baseline : host arrays, n_streams x 9 floats (row-major intrinsics) and n_streams floats
  *   D, P        : host arrays of n_streams device pointers to W_i x H_i f32 outputs (updated
  *                 disparity and variance; -1 where neither a prediction nor a match exists)
+ * A stream refused by the volume pool (see tsgm_batch_create) keeps its state and outputs; the
+ * caller runs that frame again in a later step. R and t are required for every stream that was
+ * active in an earlier step since create or reset (they are unread while the stream holds no
+ * state yet, e.g. when its first frame was refused).
  * Stream parameters: flags, gamma_f and sigma_mult must be equal across streams and q finite
- * >= 0; TSGM_FLAG_EDGE_REJECT, _PRED_LR_CHECK and _SAD_CHECK are not in the batched step
+ * >= 0, and the pool must hold the largest stream at full range (max_labels = 0 does);
+ * TSGM_FLAG_EDGE_REJECT, _PRED_LR_CHECK and _SAD_CHECK are not in the batched step
  * (UNIMPLEMENTED); TSGM_FLAG_KEEP_INTERNALS is ignored. All arguments are checked before
  * anything is enqueued: INVALID_ARG (null pointer of an active stream, D[i] == P[i], invalid
  * pose or calibration, poses missing) leaves every stream's state as it was. Ordered on the
@@ -369,20 +378,32 @@ tsgm_status tsgm_batch_frame(tsgm_batch* b, const uint8_t* const* left,
 /* Forget every stream's previous state: the next tsgm_batch_frame is a first frame for all. */
 tsgm_status tsgm_batch_reset(tsgm_batch* b);
 
+/* Per stream, what the last step did with it: 0 ran, 1 sat the step out (tsgm_batch_frame with
+ * no images for it), 2 refused for lack of pool cells. status: host array of n_streams.
+ * Synchronises. */
+tsgm_status tsgm_batch_stream_status(tsgm_batch* b, int32_t* status);
+
+/* Cells of the volume pool (per volume) and the cells of the largest stream at full range. */
+tsgm_status tsgm_batch_pool(tsgm_batch* b, uint64_t* pool_cells, uint64_t* largest_full_range);
+
 /* Kernels launched by this batch (graph steps count their kernels). */
 tsgm_status tsgm_batch_launches(tsgm_batch* b, uint64_t* n);
 
 /* ---------------------------------------------------------------------------------------------
  * Serving: many camera streams each sending frames at their own rate. The per-stream state
- * (previous D, P) stays on the device. A scheduler thread admits a frame as soon as its stream
- * has no frame in flight and an execution slot of its image size is free (continuous batching:
- * frames arriving while others run start on their own CUDA stream and overlap with them).
- * Slots hold a context's scratch; they are created per image size, at least one each and more
- * while the HBM budget allows, never more than that size has streams.
+ * (previous D, P) stays on the device. A scheduler thread runs ticks of the batched time step
+ * (tsgm_batch_frame): each tick takes the oldest waiting frame of every stream that has one and
+ * runs them all in one graph replay; frames arriving meanwhile go into the next tick (continuous
+ * batching). The ragged volumes of all streams share one pool sized by the HBM budget (at least
+ * the largest stream at full range); a stream that does not fit the cells left in a tick keeps
+ * its state and its frame runs in a later tick, so the budget bounds memory and drops nothing.
  * ------------------------------------------------------------------------------------------- */
 typedef struct tsgm_server tsgm_server;
 
-/* streams[i]: parameters of camera stream i (frames of a stream must have its size). */
+/* streams[i]: parameters of camera stream i (frames of a stream must have its size); the
+ * matching parameters, flags, gamma_f and sigma_mult must be equal across streams (INVALID_ARG)
+ * and TSGM_FLAG_EDGE_REJECT, _PRED_LR_CHECK and _SAD_CHECK are not served (UNIMPLEMENTED).
+ * hbm_budget_bytes bounds the device memory of the server (state, scratch, pool). */
 tsgm_status tsgm_server_create(const tsgm_params* streams, int32_t n_streams,
                                uint64_t hbm_budget_bytes, tsgm_server** out);
 /* Finishes every submitted frame, then releases everything. */
@@ -396,8 +417,8 @@ tsgm_status tsgm_server_submit(tsgm_server* s, int32_t stream, const uint8_t* le
                                uint64_t* ticket);
 /* Block until the ticket's frame is done; returns its status and its latency (submit to result). */
 tsgm_status tsgm_server_wait(tsgm_server* s, uint64_t ticket, double* latency_ms);
-/* Latency percentiles over all finished frames, their number, the number of slots and the
- * largest number of frames that were on the GPU at once. */
+/* Latency percentiles over all finished frames, their number, the number of streams whose
+ * full-range step the pool holds at once (n_slots) and the most frames run in one tick. */
 tsgm_status tsgm_server_stats(tsgm_server* s, double* p50_ms, double* p99_ms, uint64_t* completed,
                               int32_t* n_slots, uint64_t* max_in_flight);
 

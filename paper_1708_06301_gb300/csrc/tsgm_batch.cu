@@ -49,13 +49,12 @@ struct BStream {
     uint32_t* rowsum;
     uint32_t* rowcells;  // true cells per row, then (at + H) pixels wider than kNarrowMax per row
     uint32_t* cells;     // [0] true cells, [1] pixels wider than kNarrowMax
-    uint32_t* status;  // 0 ok, 1: the windows need more cells than the stream's storage
-    uint8_t* C;
-    uint8_t* Lvol;
-    uint64_t capacity;  // cells of storage per volume (C and each direction of Lvol)
-    int active;         // 0: the stream sits this step out (time-step form)
+    uint32_t* status;  // 0 ok, 1: the windows did not fit the free part of the volume pool
+    uint8_t* C;         // the batch's volume pool (shared by all streams; each step a stream's
+    uint8_t* Lvol;      // volumes start at its reserved base cell)
+    uint64_t capacity;  // cells of the pool per volume (C and each direction of Lvol)
+    int active;         // 0: the stream sits this step out
     // time-step form: the previous state, the prediction and its scratch, the matched maps
-    int has_prev;
     WarpParams wp;
     float q;
     unsigned long long* keys;  // z-buffer, all empty between steps (the gather empties them)
@@ -83,6 +82,11 @@ struct BTable {
     // slot_base[s][i+1]); slot_base[s][ns] == slot_base[s+1][0]
     int slot_base[8][kMaxStreams + 1];
     int total_items;
+    // volume pool: every step each active stream reserves the cells of its windows, in order of
+    // how many steps in a row it has been refused (then stream order); device arrays
+    uint64_t* base;     // first pool cell of the stream's volumes this step
+    uint32_t* age;      // consecutive steps the stream was refused for lack of pool cells
+    int* has_prev;      // time-step form: the stream holds a state from an earlier step
 };
 
 __device__ __forceinline__ int find_stream(const int* base, int ns, int item) {
@@ -107,12 +111,54 @@ __global__ void __launch_bounds__(512) kb_offsets(const BStream* __restrict__ st
                                                   const BTable* __restrict__ tb) {
     const int s = find_stream(tb->row_base, tb->ns, blockIdx.x);
     const BStream& b = st[s];
-    if (!b.active) return;
+    if (!b.active || *b.status != 0u) return;
     const int y = blockIdx.x - tb->row_base[s];
     offsets_row(b.lo, b.hi, b.rowsum, b.rowcells, b.rowcells + b.H, b.W, b.H, y, b.off, b.desc,
                 b.cells, nullptr);
-    if (y == b.H - 1 && threadIdx.x == 0)
-        *b.status = (uint64_t)b.off[(size_t)b.W * b.H] > b.capacity ? 1u : 0u;
+}
+
+// Reservation of the volume pool, one block of kMaxStreams threads: each active stream needs the
+// padded cells of its windows (the sum of its row totals), rounded up to 256 so that every
+// stream's volumes stay 256-byte aligned; the streams are served longest-refused first (then in
+// stream order), each taking the next free cells if they suffice and being refused otherwise
+// (status 1: the step skips the stream).
+__global__ void __launch_bounds__(kMaxStreams) kb_reserve(const BStream* __restrict__ st,
+                                                          const BTable* __restrict__ tb) {
+    __shared__ uint64_t need[kMaxStreams];
+    __shared__ int order[kMaxStreams];
+    __shared__ int n_active;
+    const int ns = tb->ns, i = threadIdx.x;
+    if (i == 0) n_active = 0;
+    __syncthreads();
+    const bool act = i < ns && st[i].active;
+    if (act) {
+        const BStream& b = st[i];
+        uint64_t c = 0;
+        for (int y = 0; y < b.H; ++y) c += b.rowsum[y];
+        need[i] = (c + 255) & ~255ull;
+        atomicAdd(&n_active, 1);
+        const uint32_t a = tb->age[i];
+        int r = 0;
+        for (int j = 0; j < ns; ++j) {
+            if (j == i || !st[j].active) continue;
+            const uint32_t aj = tb->age[j];
+            r += (aj > a || (aj == a && j < i)) ? 1 : 0;
+        }
+        order[r] = i;
+    }
+    __syncthreads();
+    if (i == 0) {
+        const uint64_t cap = st[0].capacity;
+        uint64_t used = 0;
+        for (int r = 0; r < n_active; ++r) {
+            const int k = order[r];
+            const bool fit = need[k] <= cap - used;
+            *st[k].status = fit ? 0u : 1u;
+            tb->base[k] = fit ? used : 0;
+            tb->age[k] = fit ? 0u : tb->age[k] + 1u;
+            if (fit) used += need[k];
+        }
+    }
 }
 
 template <int CW, int CH>
@@ -137,7 +183,8 @@ __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
         const int s = find_stream(tb->px_base, tb->ns, gi);
         const BStream& b = st[s];
         if (!b.active || *b.status != 0u) continue;
-        cost_pixels(b.censusL, b.censusR, b.desc, b.W, b.n, Bc, b.C, gi - tb->px_base[s], sub, b.n);
+        cost_pixels(b.censusL, b.censusR, b.desc, b.W, b.n, Bc, b.C + tb->base[s],
+                    gi - tb->px_base[s], sub, b.n);
     }
 }
 
@@ -167,9 +214,10 @@ __global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__
         const int nlines = code <= 1 ? b.H : (code <= 3 ? b.W : b.W + b.H - 1);
         int seg = min(grp_seg(code <= 1 ? b.W : (code <= 3 ? b.H : min(b.W, b.H))), NG);
         if (NG == 4 && code > 1) seg = 1;  // as grp_slot_seg
-        sgm_group_lines<LPLW, GL>(b.C, b.desc, b.W, b.H, P1, P2, code,
+        const uint64_t base = tb->base[s];
+        sgm_group_lines<LPLW, GL>(b.C + base, b.desc, b.W, b.H, P1, P2, code,
                                   (item - tb->slot_base[slot][s]) * (NG / seg), nlines, seg,
-                                  b.Lvol + (size_t)code * b.capacity, wsm);
+                                  b.Lvol + (size_t)code * b.capacity + base, wsm);
     }
 }
 
@@ -190,7 +238,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) kb_select(const BStream* __res
         }
         return;
     }
-    select_row<NPATHS>(b.Lvol, b.capacity, b.desc, b.W, y, DP, s_thr, r_min, lr_tol, b.Dz, b.rz,
+    select_row<NPATHS>(b.Lvol + tb->base[s], b.capacity, b.desc, b.W, y, DP, s_thr, r_min, lr_tol, b.Dz, b.rz,
                        nullptr, nullptr, nullptr, nullptr, sel_smem, n_wide);
 }
 
@@ -201,7 +249,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) kb_select(const BStream* __res
 __device__ __forceinline__ int px_block(const BStream* __restrict__ st, const BTable* __restrict__ tb,
                                         int& s) {
     s = find_stream(tb->pblk_base, tb->ns, blockIdx.x);
-    return st[s].active ? (blockIdx.x - tb->pblk_base[s]) * 256 : -1;
+    return st[s].active ? ((int)blockIdx.x - tb->pblk_base[s]) * 256 : -1;
 }
 
 // Prediction, scatter (Eq. 3, z-buffer): streams with a previous state only.
@@ -211,7 +259,7 @@ __global__ void __launch_bounds__(256) kb_scatter(const BStream* __restrict__ st
     const int p0 = px_block(st, tb, s);
     const BStream& b = st[s];
     const int i = p0 + threadIdx.x;
-    if (p0 < 0 || !b.has_prev || i >= b.n) return;
+    if (p0 < 0 || !tb->has_prev[s] || i >= b.n) return;
     warp_scatter_px(i, b.W, b.H, b.stateD, b.stateP, b.wp, b.keys);
 }
 
@@ -224,7 +272,7 @@ __global__ void __launch_bounds__(256) kb_gather(const BStream* __restrict__ st,
     const BStream& b = st[s];
     const int i = p0 + threadIdx.x;
     if (p0 < 0 || i >= b.n) return;
-    if (b.has_prev) {
+    if (tb->has_prev[s]) {
         const unsigned long long key = b.keys[i];
         b.keys[i] = kEmptyKey;
         warp_gather_px(i, key, b.stateD, b.stateP, b.q, b.predD, b.predP);
@@ -243,7 +291,7 @@ __global__ void __launch_bounds__(256) kb_fill_gaps(const BStream* __restrict__ 
     const int p0 = px_block(st, tb, s);
     const BStream& b = st[s];
     const int i = p0 + threadIdx.x;
-    if (p0 < 0 || !b.has_prev || i >= b.n) return;
+    if (p0 < 0 || !tb->has_prev[s] || i >= b.n) return;
     if (vertical)
         fill_gaps_px(i, b.W, b.H, b.tmpD, b.tmpP, gamma_f, 1, b.predD, b.predP);
     else
@@ -262,15 +310,17 @@ __global__ void __launch_bounds__(256) kb_windows(const BStream* __restrict__ st
                 b.rowcells + b.H, full != 0);
 }
 
-// Kalman update (Eq. 10-12) into the caller's maps and the stream's state.
+// Kalman update (Eq. 10-12) into the caller's maps and the stream's state. A stream refused by
+// the pool keeps its state and its outputs as they were (its frame runs again in a later step).
 __global__ void __launch_bounds__(256) kb_kalman(const BStream* __restrict__ st,
                                                  const BTable* __restrict__ tb) {
     int s;
     const int p0 = px_block(st, tb, s);
     const BStream& b = st[s];
     const int i = p0 + threadIdx.x;
-    if (p0 < 0 || i >= b.n) return;
+    if (p0 < 0 || *b.status != 0u || i >= b.n) return;
     kalman_px(i, b.predD, b.predP, b.Dm, b.rm, b.outD, b.outP, b.stateD, b.stateP);
+    if (i == 0) tb->has_prev[s] = 1;
 }
 
 struct SgmShape {
@@ -329,6 +379,9 @@ struct tsgm_batch {
     BTable* d_table = nullptr;
     int* d_counter = nullptr;
     cudaGraphExec_t fgraph = nullptr;  // the time-step form
+    uint64_t pool_cells = 0;             // cells of the volume pool (per volume)
+    uint64_t full_need = 0, max_need = 0;  // cells of every stream / of the largest one at full range
+    std::vector<uint8_t> seen;           // stream was active in a time step since create / reset
     std::string step_err;  // why the time-step form cannot run on these streams ("" if it can)
     int shape = 3;  // index into kShapes
     int gl = 8;     // lanes per path line in the aggregation (4: windows up to 16 labels in one step)
@@ -372,6 +425,7 @@ cudaError_t enqueue_step(tsgm_batch* b, int shape, bool timed = false) {
     if (e != cudaSuccess) return e;
     const int rows = t.row_base[b->ns];
     kb_sanitize<<<rows, 256, 0, st>>>(b->d_streams, b->d_table);
+    kb_reserve<<<1, kMaxStreams, 0, st>>>(b->d_streams, b->d_table);
     kb_offsets<<<rows, 512, 0, st>>>(b->d_streams, b->d_table);
     {
         const dim3 cg(t.tile_base[b->ns], 1, 2), cb(kCtW, kCtH);
@@ -443,6 +497,7 @@ cudaError_t enqueue_frame_step(tsgm_batch* b, int shape) {
     }
     kb_windows<<<rows, 256, 0, st>>>(b->d_streams, b->d_table, p.sigma_mult,
                                      (p.flags & TSGM_FLAG_FULL_RANGE) ? 1 : 0);
+    kb_reserve<<<1, kMaxStreams, 0, st>>>(b->d_streams, b->d_table);
     kb_offsets<<<rows, 512, 0, st>>>(b->d_streams, b->d_table);
     {
         const dim3 cg(t.tile_base[b->ns], 1, 2), cb(kCtW, kCtH);
@@ -474,7 +529,7 @@ cudaError_t enqueue_frame_step(tsgm_batch* b, int shape) {
 
 // kernels of one time step (the census counts as one: both images in one launch)
 int frame_kernels(const tsgm_batch* b) {
-    return 9 + ((b->prm.flags & TSGM_FLAG_FILL_GAPS) ? 2 : 0);
+    return 10 + ((b->prm.flags & TSGM_FLAG_FILL_GAPS) ? 2 : 0);
 }
 
 tsgm_status capture_frame(tsgm_batch* b) {
@@ -521,10 +576,10 @@ tsgm_status set_io(tsgm_batch* b, const uint8_t* const* left, const uint8_t* con
 
 }  // namespace
 
-extern "C" {
+namespace tsgm {
 
-tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int32_t max_labels,
-                              void* cuda_stream, tsgm_batch** out) {
+tsgm_status batch_create(const tsgm_params* streams, int32_t n_streams, int32_t max_labels,
+                         uint64_t hbm_budget_bytes, void* cuda_stream, tsgm_batch** out) {
     if (!out) return TSGM_ERR_INVALID_ARG;
     *out = nullptr;
     if (!streams || n_streams < 1 || n_streams > kMaxStreams) return TSGM_ERR_INVALID_ARG;
@@ -543,7 +598,12 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
             p.census_w > 15 || p.census_h > 15 || p.census_w * p.census_h - 1 > 64 ||
             (p.n_paths != 4 && p.n_paths != 8))
             return TSGM_ERR_INVALID_ARG;
+        // a stream's cell offsets are 32-bit
+        if ((uint64_t)p.width * p.height * (uint64_t)((p.d_max + 4) & ~3) > 0xFFFFFF00ull)
+            return TSGM_ERR_INVALID_ARG;
     }
+    size_t free0 = 0, total0 = 0;
+    cudaMemGetInfo(&free0, &total0);
     tsgm_batch* b = new (std::nothrow) tsgm_batch();
     if (!b) return TSGM_ERR_OUT_OF_MEMORY;
     b->prm = p0;
@@ -573,6 +633,7 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
         std::memset(b->h_table, 0, sizeof(BTable));
         BTable& t = *b->h_table;
         t.ns = n_streams;
+        uint64_t full_need = 0, max_need = 0;
         for (int i = 0; i < n_streams && ok; ++i) {
             const tsgm_params& p = streams[i];
             BStream& s = b->h_streams[i];
@@ -581,7 +642,10 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
             s.D = p.d_max + 1;
             s.n = p.width * p.height;
             const int lab = (max_labels > 0 && max_labels < s.D) ? max_labels : s.D;
-            s.capacity = (uint64_t)s.n * (uint64_t)((lab + 3) & ~3);
+            const uint64_t full_i = ((uint64_t)s.n * (uint64_t)((s.D + 3) & ~3) + 255) & ~255ull;
+            b->pool_cells += ((uint64_t)s.n * (uint64_t)((lab + 3) & ~3) + 255) & ~255ull;
+            full_need += full_i;
+            max_need = std::max<uint64_t>(max_need, full_i);
             b->W.push_back(s.W);
             b->H.push_back(s.H);
             b->D.push_back(s.D);
@@ -592,8 +656,6 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
                  balloc(b, &s.censusR, n) && balloc(b, &s.desc, n) && balloc(b, &s.off, n + 1) &&
                  balloc(b, &s.rowsum, (size_t)s.H) && balloc(b, &s.rowcells, 2 * (size_t)s.H) &&
                  balloc(b, &s.cells, 2) && balloc(b, &s.status, 1) &&
-                 balloc(b, &s.C, (size_t)s.capacity + 64) &&
-                 balloc(b, &s.Lvol, (size_t)s.capacity * p0.n_paths + 64) &&
                  // time-step form: z-buffer, state, prediction and its scratch, matched maps
                  balloc(b, &s.keys, n) && balloc(b, &s.stateD, n) && balloc(b, &s.stateP, n) &&
                  balloc(b, &s.predD, n) && balloc(b, &s.predP, n) && balloc(b, &s.tmpD, n) &&
@@ -627,6 +689,35 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
             t.slot_base[slot][n_streams] = item;
         }
         t.total_items = item;
+        // the volume pool: with a budget, what the budget leaves after everything above (at
+        // least one full-range stream, at most all streams at full range)
+        b->full_need = full_need;
+        b->max_need = max_need;
+        if (ok && hbm_budget_bytes > 0) {
+            size_t f1 = 0, t1 = 0;
+            cudaMemGetInfo(&f1, &t1);
+            const uint64_t used = free0 > f1 ? (uint64_t)(free0 - f1) : 0;
+            const uint64_t left = hbm_budget_bytes > used ? hbm_budget_bytes - used : 0;
+            b->pool_cells = (left / (uint64_t)(1 + p0.n_paths)) & ~255ull;
+            b->pool_cells = std::min(std::max(b->pool_cells, max_need), full_need);
+        }
+        uint8_t* pool_C = nullptr;
+        uint8_t* pool_L = nullptr;
+        ok = ok && balloc(b, &pool_C, (size_t)b->pool_cells + 64) &&
+             balloc(b, &pool_L, (size_t)b->pool_cells * p0.n_paths + 64) &&
+             balloc(b, &t.base, (size_t)n_streams) && balloc(b, &t.age, (size_t)n_streams) &&
+             balloc(b, &t.has_prev, (size_t)n_streams) &&
+             cudaMemset(t.age, 0, sizeof(uint32_t) * n_streams) == cudaSuccess &&
+             cudaMemset(t.has_prev, 0, sizeof(int) * n_streams) == cudaSuccess &&
+             cudaMemset(t.base, 0, sizeof(uint64_t) * n_streams) == cudaSuccess;
+        for (int i = 0; i < n_streams && ok; ++i) {
+            BStream& s = b->h_streams[i];
+            s.C = pool_C;
+            s.Lvol = pool_L;
+            s.capacity = b->pool_cells;
+            ok = cudaMemset(s.status, 0, sizeof(uint32_t)) == cudaSuccess;
+        }
+        b->seen.assign((size_t)n_streams, 0);
         ok = ok && cudaMemcpy(b->d_table, b->h_table, sizeof(BTable), cudaMemcpyHostToDevice) == cudaSuccess;
         int smem_max = 48 * 1024;
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -658,6 +749,15 @@ tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int
     }
     *out = b;
     return TSGM_OK;
+}
+
+}  // namespace tsgm
+
+extern "C" {
+
+tsgm_status tsgm_batch_create(const tsgm_params* streams, int32_t n_streams, int32_t max_labels,
+                              void* cuda_stream, tsgm_batch** out) {
+    return tsgm::batch_create(streams, n_streams, max_labels, 0, cuda_stream, out);
 }
 
 void tsgm_batch_destroy(tsgm_batch* b) {
@@ -695,7 +795,7 @@ tsgm_status tsgm_batch_match(tsgm_batch* b, const uint8_t* const* left,
         (e = cudaEventRecord(b->ev_out, b->exec)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(b->user, b->ev_out, 0)) != cudaSuccess)
         return bcuda(b, e, "batch step");
-    b->launches += 6;
+    b->launches += 7;
     return TSGM_OK;
 }
 
@@ -752,14 +852,39 @@ tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed
     for (int i = 0; i < b->ns; ++i) {
         if (!b->h_streams[i].active) continue;  // sat the last step out
         uint32_t c = 0, st = 0;
-        if (cudaMemcpy(&c, b->h_streams[i].cells, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(&st, b->h_streams[i].status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        if (cudaMemcpy(&st, b->h_streams[i].status, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            (st == 0u &&
+             cudaMemcpy(&c, b->h_streams[i].cells, 4, cudaMemcpyDeviceToHost) != cudaSuccess))
             return bfail(b, TSGM_ERR_CUDA, "tsgm_batch_cells: copy");
         tot += c;
         over += st != 0u;
     }
     *cells = tot;
     if (overflowed) *overflowed = over;
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_batch_stream_status(tsgm_batch* b, int32_t* status) {
+    if (!b || !status) return TSGM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->exec);
+    if (e != cudaSuccess) return bcuda(b, e, "synchronize");
+    for (int i = 0; i < b->ns; ++i) {
+        uint32_t st = 0;
+        if (!b->h_streams[i].active) {
+            status[i] = 1;
+            continue;
+        }
+        if (cudaMemcpy(&st, b->h_streams[i].status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bfail(b, TSGM_ERR_CUDA, "tsgm_batch_stream_status: copy");
+        status[i] = st ? 2 : 0;
+    }
+    return TSGM_OK;
+}
+
+tsgm_status tsgm_batch_pool(tsgm_batch* b, uint64_t* pool_cells, uint64_t* largest_full_range) {
+    if (!b || !pool_cells) return TSGM_ERR_INVALID_ARG;
+    *pool_cells = b->pool_cells;
+    if (largest_full_range) *largest_full_range = b->max_need;
     return TSGM_OK;
 }
 
@@ -783,7 +908,7 @@ tsgm_status tsgm_batch_profile(tsgm_batch* b, const uint8_t* const* left,
     if (a) cudaEventDestroy(a);
     if (z) cudaEventDestroy(z);
     if (e != cudaSuccess) return bcuda(b, e, "tsgm_batch_profile");
-    b->launches += 6;
+    b->launches += 7;
     return TSGM_OK;
 }
 
@@ -794,6 +919,10 @@ tsgm_status tsgm_batch_frame(tsgm_batch* b, const uint8_t* const* left,
     if (!b) return TSGM_ERR_INVALID_ARG;
     const tsgm_params& p = b->prm;
     if (!b->step_err.empty()) return bfail(b, TSGM_ERR_INVALID_ARG, b->step_err);
+    if (b->pool_cells < b->max_need)
+        return bfail(b, TSGM_ERR_INVALID_ARG,
+                     "tsgm_batch_frame: the volume pool cannot hold the largest stream at full "
+                     "range (a first frame); create the batch with max_labels = 0");
     if (p.flags & (TSGM_FLAG_EDGE_REJECT | TSGM_FLAG_PRED_LR_CHECK | TSGM_FLAG_SAD_CHECK))
         return bfail(b, TSGM_ERR_UNIMPLEMENTED,
                      "tsgm_batch_frame: edge rejection and the consistency checks of the "
@@ -810,11 +939,10 @@ tsgm_status tsgm_batch_frame(tsgm_batch* b, const uint8_t* const* left,
         if (D[i] == P[i])
             return bfail(b, TSGM_ERR_INVALID_ARG,
                          "tsgm_batch_frame: D and P alias for stream " + std::to_string(i));
-        const BStream& hs = b->h_streams[i];
         const float* Ki = K + 9 * i;
         wps[i].cx = Ki[2];
         wps[i].cy = Ki[5];
-        if (hs.has_prev) {
+        if (b->seen[i]) {
             if (!R || !t)
                 return bfail(b, TSGM_ERR_INVALID_ARG,
                              "tsgm_batch_frame: poses required after a stream's first frame");
@@ -848,7 +976,7 @@ tsgm_status tsgm_batch_frame(tsgm_batch* b, const uint8_t* const* left,
         return bcuda(b, e, "batch time step");
     b->launches += frame_kernels(b);
     for (int i = 0; i < b->ns; ++i)
-        if (b->h_streams[i].active) b->h_streams[i].has_prev = 1;
+        if (b->h_streams[i].active) b->seen[i] = 1;
     return TSGM_OK;
 }
 
@@ -856,7 +984,10 @@ tsgm_status tsgm_batch_reset(tsgm_batch* b) {
     if (!b) return TSGM_ERR_INVALID_ARG;
     cudaError_t e = cudaEventSynchronize(b->ev_out);
     if (e != cudaSuccess) return bcuda(b, e, "previous batch step");
-    for (int i = 0; i < b->ns; ++i) b->h_streams[i].has_prev = 0;
+    e = cudaMemsetAsync(b->h_table->has_prev, 0, sizeof(int) * b->ns, b->exec);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->exec);
+    if (e != cudaSuccess) return bcuda(b, e, "tsgm_batch_reset");
+    std::fill(b->seen.begin(), b->seen.end(), 0);
     return TSGM_OK;
 }
 

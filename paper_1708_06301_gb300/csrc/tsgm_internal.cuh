@@ -69,6 +69,12 @@ cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths,
                           float* rz, uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
                           const uint32_t* wq, uint32_t* gkeys, int16_t* wds, cudaStream_t st);
 
+// A batch (tsgm_batch_create) whose volume pool is sized by an HBM budget instead of labels per
+// pixel: whatever the budget leaves after the per-stream buffers, at least the largest stream at
+// full range and at most every stream at full range (hbm_budget_bytes = 0: as tsgm_batch_create).
+tsgm_status batch_create(const tsgm_params* streams, int32_t n_streams, int32_t max_labels,
+                         uint64_t hbm_budget_bytes, void* cuda_stream, tsgm_batch** out);
+
 }  // namespace tsgm
 
 // The opaque context of the public ABI.

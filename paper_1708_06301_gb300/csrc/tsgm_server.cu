@@ -2,12 +2,15 @@
 // own odometry) at its own rate; the per-stream state of the method (previous disparity and
 // variance maps, Sec. 2.2's D^{k-1}, P^{k-1}) stays on the device between frames.
 //
-// Continuous batching: a scheduler thread admits a frame as soon as its stream has no frame in
-// flight and an execution slot of its image size is free, so frames that arrive while others
-// are on the GPU start on their own CUDA stream and overlap with them. Slots (a context with its
-// scratch and a CUDA stream) are created per image size as far as the HBM budget allows, at least
-// one per size. A slot runs the time step on the stream's own state buffers, so admitting a
-// stream moves no maps.
+// Continuous batching on the batched time step: one batch (tsgm_batch) holds every stream's
+// state, scratch and a shared volume pool sized by the HBM budget. A scheduler thread runs ticks:
+// each tick takes the oldest waiting frame of every stream that has one, copies their images in,
+// runs ONE replay of the batched time-step graph over those streams (the others sit the tick
+// out) and copies the results out. Frames that arrive while a tick runs go into the next one.
+// A stream whose windows do not fit the pool cells left in a tick is refused by the step with
+// its state untouched and its frame stays first in line (refused streams are served first next
+// tick), so the budget bounds memory without dropping frames. Copies from the pinned result
+// buffers into the callers' arrays run on helper threads while the next tick is on the GPU.
 
 #include <algorithm>
 #include <chrono>
@@ -20,7 +23,6 @@
 #include <new>
 #include <string>
 #include <thread>
-#include <tuple>
 #include <vector>
 
 #include "tsgm_internal.cuh"
@@ -29,10 +31,15 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+constexpr int kPinnedInputs = 3;  // pinned image buffers per stream (frames waiting at once)
+constexpr int kCopyThreads = 4;
+
 struct Req {
     uint64_t ticket = 0;
     int stream = 0;
-    std::vector<uint8_t> left, right;
+    uint8_t* img = nullptr;     // left then right, pinned (from the stream's free list) or heap
+    bool img_pinned = false;
+    std::vector<uint8_t> heap;  // images when no pinned buffer was free
     float R[9], t[3], K[9];
     float baseline = 0.0f;
     bool has_pose = false;
@@ -45,143 +52,197 @@ struct Req {
 };
 
 struct SrvStream {
-    int W = 0, H = 0, D = 0;
-    int cls = 0;  // slot class (image size)
-    float* stateD = nullptr;
-    float* stateP = nullptr;
-    int has_prev = 0;
-    bool busy = false;
+    int W = 0, H = 0;
+    size_t n = 0;
+    std::deque<std::shared_ptr<Req>> queue;  // waiting frames, in submission order
+    std::vector<uint8_t*> free_img;           // pinned image buffers not in use
+    std::vector<uint8_t*> all_img;
+    bool ran = false;                         // a frame of this stream has run (it has a state)
+    uint8_t* d_img = nullptr;                 // device left, right
+    float* d_out = nullptr;                   // device D, P
+    float* pin_out[2] = {nullptr, nullptr};   // pinned D, P of even / odd ticks
 };
 
-struct Slot {
-    tsgm_ctx* ctx = nullptr;
-    cudaStream_t st = nullptr;
-    uint8_t* pin_l = nullptr;
-    uint8_t* pin_r = nullptr;
-    float* pin_D = nullptr;
-    float* pin_P = nullptr;
-    cudaEvent_t done = nullptr;
-    std::shared_ptr<Req> req;
-    int cls = 0;
+struct CopyTask {
+    std::shared_ptr<Req> r;
+    const float* src = nullptr;  // pinned D then P
+    size_t n = 0;
+    int parity = 0;
 };
 
 }  // namespace
 
 struct tsgm_server {
+    tsgm_batch* batch = nullptr;
     std::vector<SrvStream> streams;
-    std::vector<Slot> slots;
-    std::vector<tsgm_params> cls_params;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<std::shared_ptr<Req>> pending;
+    std::condition_variable cv_work, cv_done, cv_copy;
     std::map<uint64_t, std::shared_ptr<Req>> tickets;
     std::vector<double> latencies;
     uint64_t next_ticket = 1;
     uint64_t completed = 0;
     uint64_t max_in_flight = 0;
+    int32_t slots = 0;
     bool stop = false;
     std::thread worker;
-    std::string err;
-    int device = 0;
+    std::vector<std::thread> copiers;
+    std::deque<CopyTask> copy_q;
+    int copies_pending[2] = {0, 0};
+    bool copy_stop = false;
 };
 
 namespace {
 
-// Enqueue one frame of r on slot s (called by the worker with the lock held).
-tsgm_status launch_on(tsgm_server* S, Slot& s, const std::shared_ptr<Req>& r) {
-    SrvStream& ss = S->streams[r->stream];
-    tsgm_ctx* ctx = s.ctx;
-    const size_t n = (size_t)ss.W * ss.H;
-    std::memcpy(s.pin_l, r->left.data(), n);
-    std::memcpy(s.pin_r, r->right.data(), n);
-    cudaError_t e = cudaMemcpyAsync(ctx->d_left, s.pin_l, n, cudaMemcpyHostToDevice, s.st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_right, s.pin_r, n, cudaMemcpyHostToDevice, s.st);
-    if (e != cudaSuccess) return TSGM_ERR_CUDA;
-    // run the step on this stream's own state
-    float* keepD = ctx->stateD;
-    float* keepP = ctx->stateP;
-    ctx->stateD = ss.stateD;
-    ctx->stateP = ss.stateP;
-    ctx->has_prev = ss.has_prev;
-    const tsgm_status st = tsgm_frame(ctx, ctx->d_left, ctx->d_right, r->has_pose ? r->R : nullptr,
-                                      r->has_pose ? r->t : nullptr, r->K, r->baseline, ctx->d_outD,
-                                      ctx->d_outP);
-    ctx->stateD = keepD;
-    ctx->stateP = keepP;
-    if (st != TSGM_OK) return st;
-    ss.has_prev = 1;
-    e = cudaMemcpyAsync(s.pin_D, ctx->d_outD, n * sizeof(float), cudaMemcpyDeviceToHost, s.st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.pin_P, ctx->d_outP, n * sizeof(float), cudaMemcpyDeviceToHost, s.st);
-    if (e == cudaSuccess) e = cudaEventRecord(s.done, s.st);
-    return e == cudaSuccess ? TSGM_OK : TSGM_ERR_CUDA;
-}
-
-void finish(tsgm_server* S, Slot& s, tsgm_status st) {
-    std::shared_ptr<Req> r = s.req;
-    SrvStream& ss = S->streams[r->stream];
-    if (st == TSGM_OK) {
-        const size_t n = (size_t)ss.W * ss.H;
-        std::memcpy(r->outD, s.pin_D, n * sizeof(float));
-        std::memcpy(r->outP, s.pin_P, n * sizeof(float));
-    }
+// Complete a request (lock held).
+void finish_locked(tsgm_server* S, const std::shared_ptr<Req>& r, tsgm_status st) {
     r->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
     r->status = st;
     r->done = true;
     S->latencies.push_back(r->latency_ms);
     ++S->completed;
-    ss.busy = false;
-    s.req.reset();
+    SrvStream& ss = S->streams[r->stream];
+    if (r->img_pinned) ss.free_img.push_back(r->img);
+    r->img = nullptr;
+    r->img_pinned = false;
+    r->heap.clear();
+    r->heap.shrink_to_fit();
+}
+
+void copier_loop(tsgm_server* S) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        S->cv_copy.wait(lk, [&] { return S->copy_stop || !S->copy_q.empty(); });
+        if (S->copy_q.empty()) return;  // stop requested and nothing left
+        CopyTask t = S->copy_q.front();
+        S->copy_q.pop_front();
+        lk.unlock();
+        std::memcpy(t.r->outD, t.src, t.n * sizeof(float));
+        std::memcpy(t.r->outP, t.src + t.n, t.n * sizeof(float));
+        lk.lock();
+        finish_locked(S, t.r, TSGM_OK);
+        --S->copies_pending[t.parity];
+        S->cv_done.notify_all();
+        S->cv_copy.notify_all();
+    }
+}
+
+bool any_waiting(const tsgm_server* S) {
+    for (const SrvStream& ss : S->streams)
+        if (!ss.queue.empty()) return true;
+    return false;
 }
 
 void worker_loop(tsgm_server* S) {
-    cudaSetDevice(S->device);
+    const int ns = (int)S->streams.size();
+    std::vector<const uint8_t*> L(ns), Rimg(ns);
+    std::vector<float*> Dp(ns), Pp(ns);
+    std::vector<float> Rm(9 * ns), tv(3 * ns), Km(9 * ns), bl(ns);
+    std::vector<std::shared_ptr<Req>> tick(ns);
+    std::vector<int32_t> status(ns);
+    static const float kEye[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    int parity = 0;
     std::unique_lock<std::mutex> lk(S->mu);
-    while (true) {
-        bool progress = false;
-        // completions
-        for (Slot& s : S->slots) {
-            if (!s.req) continue;
-            const cudaError_t q = cudaEventQuery(s.done);
-            if (q == cudaErrorNotReady) continue;
-            finish(S, s, q == cudaSuccess ? TSGM_OK : TSGM_ERR_CUDA);
-            progress = true;
-        }
-        if (progress) S->cv_done.notify_all();
-        // admissions, oldest request first; a stream's frames stay in order
-        for (auto it = S->pending.begin(); it != S->pending.end();) {
-            std::shared_ptr<Req> r = *it;
-            SrvStream& ss = S->streams[r->stream];
-            if (ss.busy) {
-                ++it;
-                continue;
-            }
-            Slot* free_slot = nullptr;
-            for (Slot& s : S->slots)
-                if (!s.req && s.cls == ss.cls) {
-                    free_slot = &s;
+    for (;;) {
+        S->cv_work.wait(lk, [&] { return S->stop || any_waiting(S); });
+        if (!any_waiting(S)) break;  // stop requested and every frame is done
+        // the oldest waiting frame of every stream; frames that cannot run are refused alone
+        int n_tick = 0;
+        for (int i = 0; i < ns; ++i) {
+            SrvStream& ss = S->streams[i];
+            tick[i].reset();
+            while (!ss.queue.empty()) {
+                std::shared_ptr<Req> r = ss.queue.front();
+                float H[16];
+                const bool ok = !ss.ran || (r->has_pose && tsgm_build_H(r->R, r->t, r->K,
+                                                                       r->baseline, H) == TSGM_OK);
+                if (ok) {
+                    tick[i] = r;
+                    ++n_tick;
                     break;
                 }
-            if (!free_slot) {
-                ++it;
+                ss.queue.pop_front();
+                finish_locked(S, r, TSGM_ERR_INVALID_ARG);
+                S->cv_done.notify_all();
+            }
+        }
+        if (n_tick == 0) continue;
+        // the pinned result buffers of this parity were handed to the copiers two ticks ago
+        S->cv_copy.wait(lk, [&] { return S->copies_pending[parity] == 0; });
+        lk.unlock();
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < ns; ++i) {
+            SrvStream& ss = S->streams[i];
+            const std::shared_ptr<Req>& r = tick[i];
+            L[i] = Rimg[i] = nullptr;
+            Dp[i] = Pp[i] = nullptr;
+            if (!r) continue;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ss.d_img, r->img, 2 * ss.n, cudaMemcpyHostToDevice, S->st);
+            L[i] = ss.d_img;
+            Rimg[i] = ss.d_img + ss.n;
+            Dp[i] = ss.d_out;
+            Pp[i] = ss.d_out + ss.n;
+            // a stream without a state does not read its pose: identity, valid intrinsics
+            const bool warp = ss.ran;
+            std::memcpy(&Rm[9 * i], warp ? r->R : kEye, 9 * sizeof(float));
+            for (int k = 0; k < 3; ++k) tv[3 * i + k] = warp ? r->t[k] : 0.0f;
+            std::memcpy(&Km[9 * i], warp ? r->K : kEye, 9 * sizeof(float));
+            bl[i] = warp ? r->baseline : 1.0f;
+        }
+        tsgm_status fst = e == cudaSuccess ? TSGM_OK : TSGM_ERR_CUDA;
+        if (fst == TSGM_OK)
+            fst = tsgm_batch_frame(S->batch, L.data(), Rimg.data(), Rm.data(), tv.data(), Km.data(),
+                                   bl.data(), Dp.data(), Pp.data());
+        for (int i = 0; i < ns && fst == TSGM_OK; ++i) {
+            if (!tick[i]) continue;
+            SrvStream& ss = S->streams[i];
+            if (cudaMemcpyAsync(ss.pin_out[parity], ss.d_out, 2 * ss.n * sizeof(float),
+                                cudaMemcpyDeviceToHost, S->st) != cudaSuccess)
+                fst = TSGM_ERR_CUDA;
+        }
+        if (fst == TSGM_OK &&
+            (cudaEventRecord(S->ev, S->st) != cudaSuccess || cudaEventSynchronize(S->ev) != cudaSuccess))
+            fst = TSGM_ERR_CUDA;
+        if (fst == TSGM_OK) fst = tsgm_batch_stream_status(S->batch, status.data());
+        lk.lock();
+        int ran = 0;
+        for (int i = 0; i < ns; ++i) {
+            if (!tick[i]) continue;
+            SrvStream& ss = S->streams[i];
+            if (fst != TSGM_OK) {  // the whole tick failed: its frames fail
+                ss.queue.pop_front();
+                finish_locked(S, tick[i], fst);
                 continue;
             }
-            free_slot->req = r;
-            ss.busy = true;
-            const tsgm_status st = launch_on(S, *free_slot, r);
-            if (st != TSGM_OK) finish(S, *free_slot, st);
-            it = S->pending.erase(it);
-            progress = true;
+            if (status[i] != 0) continue;  // refused by the pool: first in line next tick
+            ss.queue.pop_front();
+            ss.ran = true;
+            ++ran;
+            S->copy_q.push_back(CopyTask{tick[i], ss.pin_out[parity], ss.n, parity});
+            ++S->copies_pending[parity];
         }
-        uint64_t in_flight = 0;
-        for (Slot& s : S->slots) in_flight += s.req ? 1 : 0;
-        S->max_in_flight = std::max<uint64_t>(S->max_in_flight, in_flight);
-        if (S->stop && S->pending.empty() && in_flight == 0) break;
-        if (!progress) {
-            // nothing new: wait for a submission or poll the GPU again shortly
-            S->cv_work.wait_for(lk, std::chrono::microseconds(in_flight ? 50 : 2000));
-        }
+        S->max_in_flight = std::max<uint64_t>(S->max_in_flight, (uint64_t)ran);
+        S->cv_copy.notify_all();
+        S->cv_done.notify_all();
+        parity ^= 1;
     }
+}
+
+void release(tsgm_server* S) {
+    if (S->st) cudaStreamSynchronize(S->st);
+    if (S->batch) tsgm_batch_destroy(S->batch);
+    for (SrvStream& ss : S->streams) {
+        for (uint8_t* p : ss.all_img) cudaFreeHost(p);
+        for (float* p : ss.pin_out)
+            if (p) cudaFreeHost(p);
+        if (ss.d_img) cudaFree(ss.d_img);
+        if (ss.d_out) cudaFree(ss.d_out);
+    }
+    if (S->ev) cudaEventDestroy(S->ev);
+    if (S->st) cudaStreamDestroy(S->st);
+    delete S;
 }
 
 }  // namespace
@@ -193,94 +254,71 @@ tsgm_status tsgm_server_create(const tsgm_params* streams, int32_t n_streams,
     if (!out) return TSGM_ERR_INVALID_ARG;
     *out = nullptr;
     if (!streams || n_streams < 1) return TSGM_ERR_INVALID_ARG;
-    tsgm_server* S = new (std::nothrow) tsgm_server();
-    if (!S) return TSGM_ERR_OUT_OF_MEMORY;
-    cudaGetDevice(&S->device);
-    // slot classes: one per distinct (width, height, d_max) with the first stream's parameters
-    std::map<std::tuple<int, int, int>, int> cls_of;
-    std::vector<int> cls_count;
+    // one batched time step serves every stream: one prediction and window rule for all
     for (int i = 0; i < n_streams; ++i) {
         const tsgm_params& p = streams[i];
-        auto key = std::make_tuple(p.width, p.height, p.d_max);
-        if (!cls_of.count(key)) {
-            cls_of[key] = (int)S->cls_params.size();
-            tsgm_params q = p;
-            q.flags &= ~(uint32_t)TSGM_FLAG_KEEP_INTERNALS;
-            S->cls_params.push_back(q);
-            cls_count.push_back(0);
-        }
-        const int c = cls_of[key];
-        ++cls_count[c];
-        SrvStream ss;
-        ss.W = p.width;
-        ss.H = p.height;
-        ss.D = p.d_max + 1;
-        ss.cls = c;
-        const size_t n = (size_t)p.width * p.height;
-        if (cudaMalloc((void**)&ss.stateD, n * sizeof(float)) != cudaSuccess ||
-            cudaMalloc((void**)&ss.stateP, n * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            S->streams.push_back(ss);
-            tsgm_server_destroy(S);
-            return TSGM_ERR_OUT_OF_MEMORY;
-        }
-        S->streams.push_back(ss);
+        if (p.flags & (TSGM_FLAG_EDGE_REJECT | TSGM_FLAG_PRED_LR_CHECK | TSGM_FLAG_SAD_CHECK))
+            return TSGM_ERR_UNIMPLEMENTED;
+        if (((p.flags ^ streams[0].flags) & ~(uint32_t)TSGM_FLAG_KEEP_INTERNALS) ||
+            p.gamma_f != streams[0].gamma_f || p.sigma_mult != streams[0].sigma_mult ||
+            !(p.q >= 0.0f && p.q <= 3.0e38f) || !(p.sigma_mult >= 0.0f && p.sigma_mult <= 3.0e38f))
+            return TSGM_ERR_INVALID_ARG;
     }
-    // bytes of one slot of each class: measured from the free memory a context takes
-    auto make_slot = [&](int c) -> bool {
-        Slot s;
-        s.cls = c;
-        const tsgm_params& p = S->cls_params[c];
-        const size_t n = (size_t)p.width * p.height;
-        if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess) return false;
-        if (tsgm_create(&p, s.st, &s.ctx) != TSGM_OK) {
-            cudaStreamDestroy(s.st);
-            return false;
-        }
-        if (cudaMallocHost((void**)&s.pin_l, n) != cudaSuccess ||
-            cudaMallocHost((void**)&s.pin_r, n) != cudaSuccess ||
-            cudaMallocHost((void**)&s.pin_D, n * sizeof(float)) != cudaSuccess ||
-            cudaMallocHost((void**)&s.pin_P, n * sizeof(float)) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
-            S->slots.push_back(s);
-            return false;
-        }
-        S->slots.push_back(s);
-        return true;
-    };
-    uint64_t used = 0;
-    bool ok = true;
-    std::vector<uint64_t> cls_bytes(S->cls_params.size(), 0);
-    for (size_t c = 0; c < S->cls_params.size() && ok; ++c) {
-        size_t f0 = 0, f1 = 0, total = 0;
-        cudaMemGetInfo(&f0, &total);
-        ok = make_slot((int)c);
-        cudaMemGetInfo(&f1, &total);
-        cls_bytes[c] = f0 > f1 ? (uint64_t)(f0 - f1) : 1;
-        used += cls_bytes[c];
-    }
-    // more slots, round-robin over the classes in proportion to their streams, within budget
-    bool grew = true;
-    while (ok && grew) {
-        grew = false;
-        for (size_t c = 0; c < S->cls_params.size(); ++c) {
-            int have = 0;
-            for (const Slot& s : S->slots) have += s.cls == (int)c;
-            if (have >= cls_count[c]) continue;  // never more slots than streams of the class
-            if (used + cls_bytes[c] > hbm_budget_bytes) continue;
-            if (!make_slot((int)c)) {
-                ok = false;
-                break;
+    tsgm_server* S = new (std::nothrow) tsgm_server();
+    if (!S) return TSGM_ERR_OUT_OF_MEMORY;
+    std::vector<tsgm_params> prm(streams, streams + n_streams);
+    for (tsgm_params& p : prm) p.flags &= ~(uint32_t)TSGM_FLAG_KEEP_INTERNALS;
+    size_t f0 = 0, f1 = 0, total = 0;
+    cudaMemGetInfo(&f0, &total);
+    bool ok = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) == cudaSuccess;
+    S->streams.resize((size_t)n_streams);
+    for (int i = 0; i < n_streams && ok; ++i) {
+        SrvStream& ss = S->streams[i];
+        ss.W = prm[i].width;
+        ss.H = prm[i].height;
+        ss.n = (size_t)ss.W * ss.H;
+        ok = cudaMalloc((void**)&ss.d_img, 2 * ss.n) == cudaSuccess &&
+             cudaMalloc((void**)&ss.d_out, 2 * ss.n * sizeof(float)) == cudaSuccess &&
+             cudaMallocHost((void**)&ss.pin_out[0], 2 * ss.n * sizeof(float)) == cudaSuccess &&
+             cudaMallocHost((void**)&ss.pin_out[1], 2 * ss.n * sizeof(float)) == cudaSuccess;
+        for (int k = 0; k < kPinnedInputs && ok; ++k) {
+            uint8_t* p = nullptr;
+            ok = cudaMallocHost((void**)&p, 2 * ss.n) == cudaSuccess;
+            if (ok) {
+                ss.all_img.push_back(p);
+                ss.free_img.push_back(p);
             }
-            used += cls_bytes[c];
-            grew = true;
+        }
+    }
+    tsgm_status st = TSGM_OK;
+    if (ok) {
+        cudaMemGetInfo(&f1, &total);
+        const uint64_t used = f0 > f1 ? (uint64_t)(f0 - f1) : 0;
+        const uint64_t left = hbm_budget_bytes > used ? hbm_budget_bytes - used : 1;
+        st = tsgm::batch_create(prm.data(), n_streams, 0, left, S->st, &S->batch);
+        ok = st == TSGM_OK;
+    }
+    if (ok) {
+        // streams whose full-range step fits the pool at once (in stream order)
+        uint64_t pool = 0, largest = 0, used = 0;
+        tsgm_batch_pool(S->batch, &pool, &largest);
+        for (int i = 0; i < n_streams; ++i) {
+            const uint64_t need =
+                ((uint64_t)prm[i].width * prm[i].height * (uint64_t)((prm[i].d_max + 4) & ~3) + 255) &
+                ~255ull;
+            if (need <= pool - used) {
+                used += need;
+                ++S->slots;
+            }
         }
     }
     if (!ok) {
         cudaGetLastError();
-        tsgm_server_destroy(S);
-        return TSGM_ERR_OUT_OF_MEMORY;
+        release(S);
+        return st == TSGM_ERR_INVALID_ARG ? TSGM_ERR_INVALID_ARG : TSGM_ERR_OUT_OF_MEMORY;
     }
+    for (int k = 0; k < kCopyThreads; ++k) S->copiers.emplace_back(copier_loop, S);
     S->worker = std::thread(worker_loop, S);
     *out = S;
     return TSGM_OK;
@@ -296,21 +334,14 @@ void tsgm_server_destroy(tsgm_server* S) {
         S->cv_work.notify_all();
         S->worker.join();
     }
-    for (Slot& s : S->slots) {
-        if (s.st) cudaStreamSynchronize(s.st);
-        if (s.ctx) tsgm_destroy(s.ctx);
-        if (s.st) cudaStreamDestroy(s.st);
-        if (s.pin_l) cudaFreeHost(s.pin_l);
-        if (s.pin_r) cudaFreeHost(s.pin_r);
-        if (s.pin_D) cudaFreeHost(s.pin_D);
-        if (s.pin_P) cudaFreeHost(s.pin_P);
-        if (s.done) cudaEventDestroy(s.done);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->copy_stop = true;
     }
-    for (SrvStream& ss : S->streams) {
-        if (ss.stateD) cudaFree(ss.stateD);
-        if (ss.stateP) cudaFree(ss.stateP);
-    }
-    delete S;
+    S->cv_copy.notify_all();
+    for (std::thread& t : S->copiers)
+        if (t.joinable()) t.join();
+    release(S);
 }
 
 tsgm_status tsgm_server_submit(tsgm_server* S, int32_t stream, const uint8_t* left_host,
@@ -321,11 +352,23 @@ tsgm_status tsgm_server_submit(tsgm_server* S, int32_t stream, const uint8_t* le
         return TSGM_ERR_INVALID_ARG;
     if (stream < 0 || stream >= (int32_t)S->streams.size()) return TSGM_ERR_INVALID_ARG;
     auto r = std::make_shared<Req>();
-    const SrvStream& ss = S->streams[stream];
-    const size_t n = (size_t)ss.W * ss.H;
+    SrvStream& ss = S->streams[stream];
+    const size_t n = ss.n;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (!ss.free_img.empty()) {
+            r->img = ss.free_img.back();
+            ss.free_img.pop_back();
+            r->img_pinned = true;
+        }
+    }
+    if (!r->img) {
+        r->heap.resize(2 * n);
+        r->img = r->heap.data();
+    }
+    std::memcpy(r->img, left_host, n);
+    std::memcpy(r->img + n, right_host, n);
     r->stream = stream;
-    r->left.assign(left_host, left_host + n);
-    r->right.assign(right_host, right_host + n);
     r->has_pose = R && t;
     if (r->has_pose) {
         std::memcpy(r->R, R, sizeof(r->R));
@@ -340,7 +383,7 @@ tsgm_status tsgm_server_submit(tsgm_server* S, int32_t stream, const uint8_t* le
         std::lock_guard<std::mutex> lk(S->mu);
         r->ticket = S->next_ticket++;
         S->tickets[r->ticket] = r;
-        S->pending.push_back(r);
+        ss.queue.push_back(r);
         *ticket = r->ticket;
     }
     S->cv_work.notify_all();
@@ -355,7 +398,7 @@ tsgm_status tsgm_server_wait(tsgm_server* S, uint64_t ticket, double* latency_ms
     std::shared_ptr<Req> r = it->second;
     S->cv_done.wait(lk, [&] { return r->done; });
     if (latency_ms) *latency_ms = r->latency_ms;
-    S->tickets.erase(it);
+    S->tickets.erase(ticket);
     return r->status;
 }
 
@@ -373,7 +416,7 @@ tsgm_status tsgm_server_stats(tsgm_server* S, double* p50_ms, double* p99_ms, ui
     if (p50_ms) *p50_ms = pct(0.50);
     if (p99_ms) *p99_ms = pct(0.99);
     if (completed) *completed = S->completed;
-    if (n_slots) *n_slots = (int32_t)S->slots.size();
+    if (n_slots) *n_slots = S->slots;
     if (max_in_flight) *max_in_flight = S->max_in_flight;
     return TSGM_OK;
 }

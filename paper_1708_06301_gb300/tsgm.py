@@ -101,6 +101,9 @@ _SIGS = {
     "tsgm_batch_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_batch_frame": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tsgm_batch_reset": (ctypes.c_int, [_vp]),
+    "tsgm_batch_stream_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "tsgm_batch_pool": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_uint64)]),
     "tsgm_batch_profile": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_float)]),
@@ -527,6 +530,21 @@ class Batch:
 
     def reset(self):
         self._check(self.lib.tsgm_batch_reset(self.h), "tsgm_batch_reset")
+
+    RAN, SAT_OUT, REFUSED = 0, 1, 2
+
+    def stream_status(self):
+        """Per stream, what the last step did with it: RAN, SAT_OUT or REFUSED (no pool cells)."""
+        st = (ctypes.c_int32 * self.n)()
+        self._check(self.lib.tsgm_batch_stream_status(self.h, st), "tsgm_batch_stream_status")
+        return [int(x) for x in st]
+
+    def pool(self):
+        """(cells of the volume pool, cells of the largest stream at full range)."""
+        c, m = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        self._check(self.lib.tsgm_batch_pool(self.h, ctypes.byref(c), ctypes.byref(m)),
+                    "tsgm_batch_pool")
+        return int(c.value), int(m.value)
 
     def autotune(self, lefts, rights, los, his, Dzs, rzs, reps: int = 3):
         ms = ctypes.c_double(0)

@@ -105,14 +105,44 @@ def test_batch_small_streams_against_oracle(tsgm):
         assert np.array_equal(rzs[k][v], ro[v])
 
 
-def test_batch_skips_streams_without_enough_storage(tsgm):
+def test_batch_refuses_streams_the_pool_cannot_hold(tsgm):
+    """Storage for 2 labels per pixel (a pool of sum W x H x 4 cells), windows of up to 24: the
+    streams reserve their padded cells in stream order and those that do not fit the cells left
+    are refused (-1 outputs); the others still equal the single-image path. A refused stream is
+    served first at the next step."""
     data = inputs(5)
-    with tsgm.Batch(params(tsgm), max_labels=2) as batch:  # 4 cells per pixel, windows need more
+    need = [((int((((x[3].astype(np.int64) - x[2] + 1) + 3) & ~3).sum()) + 255) & ~255)
+            for x in data]
+    with tsgm.Batch(params(tsgm), max_labels=2) as batch:
+        pool, _ = batch.pool()
+        assert pool == sum(((W * H * 4) + 255) & ~255 for (W, H, _) in SHAPES)
+        expect, used = [], 0
+        for k in range(len(SHAPES)):
+            fit = need[k] <= pool - used
+            expect.append(tsgm.Batch.RAN if fit else tsgm.Batch.REFUSED)
+            used += need[k] if fit else 0
+        assert tsgm.Batch.REFUSED in expect and tsgm.Batch.RAN in expect
         Dzs, rzs, _ = run_batch(tsgm, batch, data)
+        st = batch.stream_status()
         cells, over = batch.cells()
-    assert over == len(SHAPES)
-    for k in range(len(SHAPES)):
-        assert np.all(Dzs[k] == -1) and np.all(rzs[k] == -1)
+        assert st == expect
+        assert over == expect.count(tsgm.Batch.REFUSED)
+        # the next step serves the refused streams first
+        run_batch(tsgm, batch, data)
+        st2 = batch.stream_status()
+    for k, (W, H, D) in enumerate(SHAPES):
+        if st[k] == tsgm.Batch.REFUSED:
+            assert np.all(Dzs[k] == -1) and np.all(rzs[k] == -1)
+        else:
+            Ds, rs = single(tsgm, W, H, D, data[k])
+            assert np.array_equal(Dzs[k], Ds), k
+            assert np.array_equal(rzs[k], rs), k
+    first = [k for k in range(len(SHAPES)) if st[k] == tsgm.Batch.REFUSED]
+    used = 0
+    for k in first + [k for k in range(len(SHAPES)) if k not in first]:
+        fit = need[k] <= pool - used
+        assert st2[k] == (tsgm.Batch.RAN if fit else tsgm.Batch.REFUSED), k
+        used += need[k] if fit else 0
 
 
 @pytest.mark.slow

@@ -89,8 +89,8 @@ def test_32_stream_mix_equals_single_contexts_for_3_frames(tsgm):
             for i in range(NS):
                 got[i].append((host(Ds[i], np.float32), host(Ps[i], np.float32)))
         # one graph per step: prediction (scatter, gather, two gap-filling passes), windows,
-        # offsets, census, cost, aggregation, selection, update
-        assert (bt.launches() - l0) == 11 * N_FRAMES
+        # pool reservation, offsets, census, cost, aggregation, selection, update
+        assert (bt.launches() - l0) == 12 * N_FRAMES
     for i, s in enumerate(streams):
         ref = alone(tsgm, s, tsgm.FLAG_FILL_GAPS)
         for k in range(N_FRAMES):
@@ -100,8 +100,7 @@ def test_32_stream_mix_equals_single_contexts_for_3_frames(tsgm):
         assert np.mean(got[i][-1][0] >= 0) > 0.5, i
 
 
-def small_streams(n_frames=4):
-    specs = [(160, 64, 41), (224, 72, 42), (160, 64, 43), (96, 40, 44)]
+def small_streams(n_frames=4, specs=((160, 64, 41), (224, 72, 42), (160, 64, 43), (96, 40, 44))):
     out = []
     for (W, H, seed) in specs:
         sq = synth.make_sequence(seed, W, H, 400.0, 0.54, n_frames=n_frames, n_boxes=3,
@@ -144,6 +143,48 @@ def test_sitting_out_and_a_refused_call_keep_the_state(tsgm):
         for j, k in enumerate(ks):
             assert np.array_equal(outs[(i, k)][0], ref[j][0]), (i, k)
             assert np.array_equal(outs[(i, k)][1], ref[j][1]), (i, k)
+
+
+def test_frames_refused_by_the_pool_run_in_a_later_step(tsgm):
+    """A pool that holds one stream at full range (max_labels = 16 of 64 labels, four streams of
+    one size): the first frames are full range, so each step runs some streams and refuses the
+    others, which keep their state and get the same frame again at the next step (longest
+    refused first). Every stream's outputs, frame by frame, equal its context's."""
+    streams = small_streams(4, [(160, 64, 51), (160, 64, 52), (160, 64, 53), (160, 64, 54)])
+    flags = tsgm.FLAG_FILL_GAPS
+    n = len(streams)
+    with tsgm.Batch(batch_params(tsgm, streams, flags), max_labels=16) as bt:
+        pool, largest = bt.pool()
+        assert pool == largest == 160 * 64 * 64
+        nxt = [0] * n
+        outs = [[] for _ in range(n)]
+        refused = 0
+        for _ in range(40):
+            if min(nxt) >= 4:
+                break
+            active = [k < 4 for k in nxt]
+            poses = [(s["R"][k], s["t"][k]) if k < 4 else None for s, k in zip(streams, nxt)]
+            L = [dev(s["left"][k]) if a else None for s, k, a in zip(streams, nxt, active)]
+            Rr = [dev(s["right"][k]) if a else None for s, k, a in zip(streams, nxt, active)]
+            Ds = [empty((s["H"], s["W"]), np.float32) if a else None for s, a in zip(streams, active)]
+            Ps = [empty((s["H"], s["W"]), np.float32) if a else None for s, a in zip(streams, active)]
+            eye = (np.eye(3, dtype=np.float32), np.zeros(3, np.float32))
+            bt.frame(L, Rr, np.stack([(p or eye)[0] for p in poses]),
+                     np.stack([(p or eye)[1] for p in poses]), np.stack([s["K"] for s in streams]),
+                     np.array([s["b"] for s in streams], np.float32), Ds, Ps)
+            st = bt.stream_status()
+            for i in range(n):
+                if st[i] == tsgm.Batch.RAN:
+                    outs[i].append((host(Ds[i], np.float32), host(Ps[i], np.float32)))
+                    nxt[i] += 1
+                elif st[i] == tsgm.Batch.REFUSED:
+                    refused += 1
+        assert min(nxt) == 4 and refused > 0
+    for i, s in enumerate(streams):
+        ref = alone(tsgm, s, flags)
+        for k in range(4):
+            assert np.array_equal(outs[i][k][0], ref[k][0]), (i, k)
+            assert np.array_equal(outs[i][k][1], ref[k][1]), (i, k)
 
 
 def test_full_range_and_reset(tsgm):

@@ -1,6 +1,8 @@
-"""Serving loop: frames of several camera streams submitted interleaved (many in flight at once)
-must give exactly the results each stream gets alone through a plain context, and the loop must
-actually overlap frames on the device when the HBM budget allows several slots."""
+"""Serving loop: frames of several camera streams submitted interleaved (many waiting at once)
+must give exactly the results each stream gets alone through a plain context; ticks of the
+batched time step must run several streams' frames together when the HBM budget allows, and
+with the smallest budget (the volume pool holds one full-range stream) frames refused by the
+pool must run in a later tick, never be dropped."""
 import numpy as np
 import pytest
 
@@ -72,10 +74,10 @@ def test_results_alone_equal_results_in_the_mix(tsgm, budget):
         st = srv.stats()
     assert st["completed"] == len(order)
     assert all(x > 0 for x in lat) and st["p99_ms"] >= st["p50_ms"] > 0
-    if budget > 1:
+    if budget > 1:  # the pool holds every stream at full range; ticks run several frames
         assert st["slots"] == len(seqs) and st["max_in_flight"] >= 2
-    else:
-        assert st["slots"] == 2  # one per image size when the budget admits nothing more
+    else:  # the smallest pool: the largest stream at full range
+        assert 1 <= st["slots"] < len(seqs)
     for (i, k), (D, P) in outs.items():
         assert np.array_equal(D, ref[i][k][0]), (i, k)
         assert np.array_equal(P, ref[i][k][1]), (i, k)
