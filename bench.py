@@ -448,8 +448,10 @@ def bench_batched_frame(dev, steps: int, warmup: int):
 
 
 def bench_serving(duration_s: float, budget_gb: float):
-    """64 camera streams (same size mix), each sending frames as a Poisson process at 10-30 Hz for
-    `duration_s` seconds; latency from submission to result, aggregate frames/s."""
+    """64 camera streams (same size mix), each sending frames as a Poisson process at 10-30 Hz.
+    Every stream's first frame (full range: no previous state) is served before the clock starts;
+    then frames arrive for `duration_s` seconds and are measured: served frames/s = frames done /
+    time from the first arrival to the last result, latency from submission to result."""
     import queue
     from paper_1708_06301_gb300 import synth, tsgm
     F = 6
@@ -458,13 +460,13 @@ def bench_serving(duration_s: float, budget_gb: float):
     params = []
     for i in range(NS):
         W, H, D = mix_shape(i)
-        params.append(tsgm.default_params(W, H, d_max=D - 1))
+        params.append(tsgm.default_params(W, H, d_max=D - 1, flags=tsgm.FLAG_FILL_GAPS))
     rs = synth.Stream(11, 0x5E7)
     events = []
     for i in range(NS):
         rate = rs.uniform(10.0, 30.0)
         tcur = rs.uniform(0.0, 1.0 / rate)
-        k = 0
+        k = 1
         while tcur < duration_s:
             events.append((tcur, i, k))
             k += 1
@@ -480,7 +482,24 @@ def bench_serving(duration_s: float, budget_gb: float):
                 return
             lat.append(srv.wait(item[0]))
 
+    def frame_of(k):  # frames go back and forth through the F rendered ones
+        cyc = list(range(F)) + list(range(F - 2, 0, -1))
+        return cyc[k % len(cyc)]
+
+    def submit(srv, i, k):
+        W, H, D = mix_shape(i)
+        sq = seqs[(W, H)]
+        f = frame_of(k)
+        Rm, tv = (None, None) if k == 0 else sq.pose_between(frame_of(k - 1), f)
+        Dout = np.empty((H, W), np.float32)
+        Pout = np.empty((H, W), np.float32)
+        return srv.submit(i, sq.left[f], sq.right[f], Rm, tv, sq.K, np.float32(sq.cam.b), Dout,
+                          Pout), Dout, Pout
+
     with tsgm.Server(params, hbm_budget_bytes=int(budget_gb * (1 << 30))) as srv:
+        first = [submit(srv, i, 0) for i in range(NS)]
+        for tk, _, _ in first:
+            srv.wait(tk)
         th = threading.Thread(target=waiter, args=(srv,), daemon=True)
         th.start()
         t0 = time.perf_counter()
@@ -488,27 +507,22 @@ def bench_serving(duration_s: float, budget_gb: float):
             now = time.perf_counter() - t0
             if ta > now:
                 time.sleep(ta - now)
-            W, H, D = mix_shape(i)
-            sq = seqs[(W, H)]
-            f = k % F
-            if k == 0:
-                Rm, tv = None, None
-            else:
-                Rm, tv = sq.pose_between((k - 1) % F, f)
-            Dout = np.empty((H, W), np.float32)
-            Pout = np.empty((H, W), np.float32)
-            tk = srv.submit(i, sq.left[f], sq.right[f], Rm, tv, sq.K, np.float32(sq.cam.b), Dout, Pout)
-            done_q.put((tk, Dout, Pout))
+            done_q.put(submit(srv, i, k))
         done_q.put(None)
         th.join()
         t_end = time.perf_counter() - t0
         st = srv.stats()
-    return {"workload": "64 camera streams (11/11/10 mix x2: 640x480 D=64, 1242x375 D=128, "
-                        "1920x1080 D=256), Poisson frame arrivals at 10-30 Hz per stream",
+    lat_ms = np.array(lat)
+    return {"workload": "64 camera streams (22x 640x480 D=64, 22x 1242x375 D=128, 20x 1920x1080 "
+                        "D=256), Poisson frame arrivals at 10-30 Hz per stream, frames going back "
+                        "and forth through 6 rendered ones with the true relative poses",
             "duration_s": duration_s, "frames": len(events), "frames_per_s": len(events) / t_end,
             "offered_frames_per_s": len(events) / duration_s,
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "slots": st["slots"],
-            "max_in_flight": st["max_in_flight"], "hbm_budget_gb": budget_gb}
+            "served_over_offered": (len(events) / t_end) / (len(events) / duration_s),
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "warmup": "every stream's first (full-range) frame served before the clock starts",
+            "slots_full_range": st["slots"], "max_frames_per_tick": st["max_in_flight"],
+            "hbm_budget_gb": budget_gb}
 
 
 # DRAM bytes (read + write) of one aggregation launch from ncu's dram__bytes_read.sum and
@@ -792,7 +806,7 @@ def main():
                     help="run only the reduced-window steps (for profiler captures)")
     ap.add_argument("--skip-forms", action="store_true",
                     help="skip the adjoint, batched and serving measurements")
-    ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-seconds", type=float, default=5.0)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
