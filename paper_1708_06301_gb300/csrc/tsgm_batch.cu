@@ -380,6 +380,8 @@ struct tsgm_batch {
     int* d_counter = nullptr;
     cudaGraphExec_t fgraph = nullptr;  // the time-step form
     uint64_t pool_cells = 0;             // cells of the volume pool (per volume)
+    uint32_t* d_status = nullptr;        // the streams' statuses (device), one array
+    uint32_t* h_status = nullptr;        // pinned copy
     uint64_t full_need = 0, max_need = 0;  // cells of every stream / of the largest one at full range
     std::vector<uint8_t> seen;           // stream was active in a time step since create / reset
     std::string step_err;  // why the time-step form cannot run on these streams ("" if it can)
@@ -634,6 +636,9 @@ tsgm_status batch_create(const tsgm_params* streams, int32_t n_streams, int32_t 
         BTable& t = *b->h_table;
         t.ns = n_streams;
         uint64_t full_need = 0, max_need = 0;
+        // the streams' step statuses side by side (read back with one copy)
+        ok = balloc(b, &b->d_status, (size_t)n_streams) &&
+             cudaMallocHost((void**)&b->h_status, sizeof(uint32_t) * n_streams) == cudaSuccess;
         for (int i = 0; i < n_streams && ok; ++i) {
             const tsgm_params& p = streams[i];
             BStream& s = b->h_streams[i];
@@ -652,10 +657,11 @@ tsgm_status batch_create(const tsgm_params* streams, int32_t n_streams, int32_t 
             b->maxW = std::max(b->maxW, s.W);
             b->maxD = std::max(b->maxD, s.D);
             const size_t n = (size_t)s.n;
+            s.status = b->d_status + i;
             ok = balloc(b, &s.lo, n) && balloc(b, &s.hi, n) && balloc(b, &s.censusL, n) &&
                  balloc(b, &s.censusR, n) && balloc(b, &s.desc, n) && balloc(b, &s.off, n + 1) &&
                  balloc(b, &s.rowsum, (size_t)s.H) && balloc(b, &s.rowcells, 2 * (size_t)s.H) &&
-                 balloc(b, &s.cells, 2) && balloc(b, &s.status, 1) &&
+                 balloc(b, &s.cells, 2) &&
                  // time-step form: z-buffer, state, prediction and its scratch, matched maps
                  balloc(b, &s.keys, n) && balloc(b, &s.stateD, n) && balloc(b, &s.stateP, n) &&
                  balloc(b, &s.predD, n) && balloc(b, &s.predP, n) && balloc(b, &s.tmpD, n) &&
@@ -768,6 +774,7 @@ void tsgm_batch_destroy(tsgm_batch* b) {
     for (void* q : b->allocs) cudaFree(q);
     if (b->h_streams) cudaFreeHost(b->h_streams);
     if (b->h_table) cudaFreeHost(b->h_table);
+    if (b->h_status) cudaFreeHost(b->h_status);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->ev_sgm_a) cudaEventDestroy(b->ev_sgm_a);
@@ -866,18 +873,12 @@ tsgm_status tsgm_batch_cells(tsgm_batch* b, uint64_t* cells, int32_t* overflowed
 
 tsgm_status tsgm_batch_stream_status(tsgm_batch* b, int32_t* status) {
     if (!b || !status) return TSGM_ERR_INVALID_ARG;
-    cudaError_t e = cudaStreamSynchronize(b->exec);
-    if (e != cudaSuccess) return bcuda(b, e, "synchronize");
-    for (int i = 0; i < b->ns; ++i) {
-        uint32_t st = 0;
-        if (!b->h_streams[i].active) {
-            status[i] = 1;
-            continue;
-        }
-        if (cudaMemcpy(&st, b->h_streams[i].status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-            return bfail(b, TSGM_ERR_CUDA, "tsgm_batch_stream_status: copy");
-        status[i] = st ? 2 : 0;
-    }
+    cudaError_t e = cudaMemcpyAsync(b->h_status, b->d_status, sizeof(uint32_t) * b->ns,
+                                    cudaMemcpyDeviceToHost, b->exec);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->exec);
+    if (e != cudaSuccess) return bcuda(b, e, "tsgm_batch_stream_status");
+    for (int i = 0; i < b->ns; ++i)
+        status[i] = !b->h_streams[i].active ? 1 : (b->h_status[i] ? 2 : 0);
     return TSGM_OK;
 }
 

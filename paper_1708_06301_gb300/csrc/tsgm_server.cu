@@ -9,8 +9,12 @@
 // out) and copies the results out. Frames that arrive while a tick runs go into the next one.
 // A stream whose windows do not fit the pool cells left in a tick is refused by the step with
 // its state untouched and its frame stays first in line (refused streams are served first next
-// tick), so the budget bounds memory without dropping frames. Copies from the pinned result
-// buffers into the callers' arrays run on helper threads while the next tick is on the GPU.
+// tick), so the budget bounds memory without dropping frames.
+//
+// Ticks are pipelined: images and results live in two device buffers per stream used in turn,
+// so a tick's results go back to pinned memory on a copy stream while the next tick computes,
+// and helper threads copy them into the callers' arrays meanwhile; the scheduler only waits for
+// a tick's compute (to learn which streams the pool refused) before it starts the next.
 
 #include <algorithm>
 #include <chrono>
@@ -58,8 +62,8 @@ struct SrvStream {
     std::vector<uint8_t*> free_img;           // pinned image buffers not in use
     std::vector<uint8_t*> all_img;
     bool ran = false;                         // a frame of this stream has run (it has a state)
-    uint8_t* d_img = nullptr;                 // device left, right
-    float* d_out = nullptr;                   // device D, P
+    uint8_t* d_img[2] = {nullptr, nullptr};   // device left, right of even / odd ticks
+    float* d_out[2] = {nullptr, nullptr};     // device D, P of even / odd ticks
     float* pin_out[2] = {nullptr, nullptr};   // pinned D, P of even / odd ticks
 };
 
@@ -68,6 +72,7 @@ struct CopyTask {
     const float* src = nullptr;  // pinned D then P
     size_t n = 0;
     int parity = 0;
+    cudaEvent_t ready = nullptr;  // the copy into src has finished
 };
 
 }  // namespace
@@ -75,8 +80,11 @@ struct CopyTask {
 struct tsgm_server {
     tsgm_batch* batch = nullptr;
     std::vector<SrvStream> streams;
-    cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaStream_t st = nullptr;      // the batch's steps
+    cudaStream_t s_in = nullptr;    // images in
+    cudaStream_t s_out = nullptr;   // results out
+    cudaEvent_t e_in[2] = {nullptr, nullptr}, e_done[2] = {nullptr, nullptr},
+                e_out[2] = {nullptr, nullptr};
     std::mutex mu;
     std::condition_variable cv_work, cv_done, cv_copy;
     std::map<uint64_t, std::shared_ptr<Req>> tickets;
@@ -91,6 +99,7 @@ struct tsgm_server {
     std::deque<CopyTask> copy_q;
     int copies_pending[2] = {0, 0};
     bool copy_stop = false;
+    int device = 0;  // the CUDA device of the server (its threads work on it)
 };
 
 namespace {
@@ -111,6 +120,7 @@ void finish_locked(tsgm_server* S, const std::shared_ptr<Req>& r, tsgm_status st
 }
 
 void copier_loop(tsgm_server* S) {
+    cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         S->cv_copy.wait(lk, [&] { return S->copy_stop || !S->copy_q.empty(); });
@@ -118,10 +128,13 @@ void copier_loop(tsgm_server* S) {
         CopyTask t = S->copy_q.front();
         S->copy_q.pop_front();
         lk.unlock();
-        std::memcpy(t.r->outD, t.src, t.n * sizeof(float));
-        std::memcpy(t.r->outP, t.src + t.n, t.n * sizeof(float));
+        const bool ok = cudaEventSynchronize(t.ready) == cudaSuccess;
+        if (ok) {
+            std::memcpy(t.r->outD, t.src, t.n * sizeof(float));
+            std::memcpy(t.r->outP, t.src + t.n, t.n * sizeof(float));
+        }
         lk.lock();
-        finish_locked(S, t.r, TSGM_OK);
+        finish_locked(S, t.r, ok ? TSGM_OK : TSGM_ERR_CUDA);
         --S->copies_pending[t.parity];
         S->cv_done.notify_all();
         S->cv_copy.notify_all();
@@ -143,6 +156,7 @@ void worker_loop(tsgm_server* S) {
     std::vector<int32_t> status(ns);
     static const float kEye[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     int parity = 0;
+    cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         S->cv_work.wait(lk, [&] { return S->stop || any_waiting(S); });
@@ -171,6 +185,8 @@ void worker_loop(tsgm_server* S) {
         // the pinned result buffers of this parity were handed to the copiers two ticks ago
         S->cv_copy.wait(lk, [&] { return S->copies_pending[parity] == 0; });
         lk.unlock();
+        // images in (on the input stream), then the step after them and after the copy out of
+        // the results this tick's buffers held two ticks ago
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < ns; ++i) {
             SrvStream& ss = S->streams[i];
@@ -179,11 +195,12 @@ void worker_loop(tsgm_server* S) {
             Dp[i] = Pp[i] = nullptr;
             if (!r) continue;
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(ss.d_img, r->img, 2 * ss.n, cudaMemcpyHostToDevice, S->st);
-            L[i] = ss.d_img;
-            Rimg[i] = ss.d_img + ss.n;
-            Dp[i] = ss.d_out;
-            Pp[i] = ss.d_out + ss.n;
+                e = cudaMemcpyAsync(ss.d_img[parity], r->img, 2 * ss.n, cudaMemcpyHostToDevice,
+                                    S->s_in);
+            L[i] = ss.d_img[parity];
+            Rimg[i] = ss.d_img[parity] + ss.n;
+            Dp[i] = ss.d_out[parity];
+            Pp[i] = ss.d_out[parity] + ss.n;
             // a stream without a state does not read its pose: identity, valid intrinsics
             const bool warp = ss.ran;
             std::memcpy(&Rm[9 * i], warp ? r->R : kEye, 9 * sizeof(float));
@@ -191,21 +208,30 @@ void worker_loop(tsgm_server* S) {
             std::memcpy(&Km[9 * i], warp ? r->K : kEye, 9 * sizeof(float));
             bl[i] = warp ? r->baseline : 1.0f;
         }
+        if (e == cudaSuccess) e = cudaEventRecord(S->e_in[parity], S->s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st, S->e_in[parity], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st, S->e_out[parity], 0);
         tsgm_status fst = e == cudaSuccess ? TSGM_OK : TSGM_ERR_CUDA;
         if (fst == TSGM_OK)
             fst = tsgm_batch_frame(S->batch, L.data(), Rimg.data(), Rm.data(), tv.data(), Km.data(),
                                    bl.data(), Dp.data(), Pp.data());
-        for (int i = 0; i < ns && fst == TSGM_OK; ++i) {
-            if (!tick[i]) continue;
-            SrvStream& ss = S->streams[i];
-            if (cudaMemcpyAsync(ss.pin_out[parity], ss.d_out, 2 * ss.n * sizeof(float),
-                                cudaMemcpyDeviceToHost, S->st) != cudaSuccess)
-                fst = TSGM_ERR_CUDA;
-        }
         if (fst == TSGM_OK &&
-            (cudaEventRecord(S->ev, S->st) != cudaSuccess || cudaEventSynchronize(S->ev) != cudaSuccess))
+            (cudaEventRecord(S->e_done[parity], S->st) != cudaSuccess ||
+             cudaEventSynchronize(S->e_done[parity]) != cudaSuccess))
             fst = TSGM_ERR_CUDA;
         if (fst == TSGM_OK) fst = tsgm_batch_stream_status(S->batch, status.data());
+        // results of the streams that ran back to pinned memory, beside the next tick
+        if (fst == TSGM_OK && cudaStreamWaitEvent(S->s_out, S->e_done[parity], 0) != cudaSuccess)
+            fst = TSGM_ERR_CUDA;
+        for (int i = 0; i < ns && fst == TSGM_OK; ++i) {
+            if (!tick[i] || status[i] != 0) continue;
+            SrvStream& ss = S->streams[i];
+            if (cudaMemcpyAsync(ss.pin_out[parity], ss.d_out[parity], 2 * ss.n * sizeof(float),
+                                cudaMemcpyDeviceToHost, S->s_out) != cudaSuccess)
+                fst = TSGM_ERR_CUDA;
+        }
+        if (fst == TSGM_OK && cudaEventRecord(S->e_out[parity], S->s_out) != cudaSuccess)
+            fst = TSGM_ERR_CUDA;
         lk.lock();
         int ran = 0;
         for (int i = 0; i < ns; ++i) {
@@ -220,7 +246,7 @@ void worker_loop(tsgm_server* S) {
             ss.queue.pop_front();
             ss.ran = true;
             ++ran;
-            S->copy_q.push_back(CopyTask{tick[i], ss.pin_out[parity], ss.n, parity});
+            S->copy_q.push_back(CopyTask{tick[i], ss.pin_out[parity], ss.n, parity, S->e_out[parity]});
             ++S->copies_pending[parity];
         }
         S->max_in_flight = std::max<uint64_t>(S->max_in_flight, (uint64_t)ran);
@@ -231,17 +257,22 @@ void worker_loop(tsgm_server* S) {
 }
 
 void release(tsgm_server* S) {
-    if (S->st) cudaStreamSynchronize(S->st);
+    for (cudaStream_t q : {S->st, S->s_in, S->s_out})
+        if (q) cudaStreamSynchronize(q);
     if (S->batch) tsgm_batch_destroy(S->batch);
     for (SrvStream& ss : S->streams) {
         for (uint8_t* p : ss.all_img) cudaFreeHost(p);
-        for (float* p : ss.pin_out)
-            if (p) cudaFreeHost(p);
-        if (ss.d_img) cudaFree(ss.d_img);
-        if (ss.d_out) cudaFree(ss.d_out);
+        for (int b = 0; b < 2; ++b) {
+            if (ss.pin_out[b]) cudaFreeHost(ss.pin_out[b]);
+            if (ss.d_img[b]) cudaFree(ss.d_img[b]);
+            if (ss.d_out[b]) cudaFree(ss.d_out[b]);
+        }
     }
-    if (S->ev) cudaEventDestroy(S->ev);
-    if (S->st) cudaStreamDestroy(S->st);
+    for (int b = 0; b < 2; ++b)
+        for (cudaEvent_t ev : {S->e_in[b], S->e_done[b], S->e_out[b]})
+            if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t q : {S->st, S->s_in, S->s_out})
+        if (q) cudaStreamDestroy(q);
     delete S;
 }
 
@@ -266,22 +297,30 @@ tsgm_status tsgm_server_create(const tsgm_params* streams, int32_t n_streams,
     }
     tsgm_server* S = new (std::nothrow) tsgm_server();
     if (!S) return TSGM_ERR_OUT_OF_MEMORY;
+    cudaGetDevice(&S->device);
     std::vector<tsgm_params> prm(streams, streams + n_streams);
     for (tsgm_params& p : prm) p.flags &= ~(uint32_t)TSGM_FLAG_KEEP_INTERNALS;
     size_t f0 = 0, f1 = 0, total = 0;
     cudaMemGetInfo(&f0, &total);
     bool ok = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) == cudaSuccess;
+              cudaStreamCreateWithFlags(&S->s_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&S->s_out, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaEventCreateWithFlags(&S->e_in[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&S->e_done[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&S->e_out[b], cudaEventDisableTiming) == cudaSuccess &&
+             // recorded once, so that the first ticks' waits on them are satisfied
+             cudaEventRecord(S->e_out[b], S->s_out) == cudaSuccess;
     S->streams.resize((size_t)n_streams);
     for (int i = 0; i < n_streams && ok; ++i) {
         SrvStream& ss = S->streams[i];
         ss.W = prm[i].width;
         ss.H = prm[i].height;
         ss.n = (size_t)ss.W * ss.H;
-        ok = cudaMalloc((void**)&ss.d_img, 2 * ss.n) == cudaSuccess &&
-             cudaMalloc((void**)&ss.d_out, 2 * ss.n * sizeof(float)) == cudaSuccess &&
-             cudaMallocHost((void**)&ss.pin_out[0], 2 * ss.n * sizeof(float)) == cudaSuccess &&
-             cudaMallocHost((void**)&ss.pin_out[1], 2 * ss.n * sizeof(float)) == cudaSuccess;
+        for (int b = 0; b < 2 && ok; ++b)
+            ok = cudaMalloc((void**)&ss.d_img[b], 2 * ss.n) == cudaSuccess &&
+                 cudaMalloc((void**)&ss.d_out[b], 2 * ss.n * sizeof(float)) == cudaSuccess &&
+                 cudaMallocHost((void**)&ss.pin_out[b], 2 * ss.n * sizeof(float)) == cudaSuccess;
         for (int k = 0; k < kPinnedInputs && ok; ++k) {
             uint8_t* p = nullptr;
             ok = cudaMallocHost((void**)&p, 2 * ss.n) == cudaSuccess;
