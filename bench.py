@@ -566,9 +566,24 @@ def run_ours(args, ws, rank, local):
         run_ours_on_stream(args, ws, rank, local, dev, stream)
 
 
+def run_only(args, dev):
+    """One of the extra measurements alone, printed as one JSON line."""
+    k = max(3, args.steps // 2)
+    fn = {"adjoint": lambda: bench_adjoint(dev, 10),
+          "batched": lambda: bench_batched(dev, k, 2),
+          "batched_frame": lambda: bench_batched_frame(dev, k, 3),
+          "serving": lambda: bench_serving(args.serving_seconds, 64.0)}[args.only]
+    print(json.dumps({"only": args.only, args.only: fn()}), flush=True)
+
+
 def run_ours_on_stream(args, ws, rank, local, dev, stream):
     import torch
     from paper_1708_06301_gb300 import synth, tsgm
+
+    if args.only:
+        if rank == 0:
+            run_only(args, dev)
+        return
 
     seq = synth.kitti_like(2, n_frames=N_FRAMES)
     W, H = seq.cam.W, seq.cam.H
@@ -807,6 +822,9 @@ def main():
     ap.add_argument("--skip-forms", action="store_true",
                     help="skip the adjoint, batched and serving measurements")
     ap.add_argument("--serving-seconds", type=float, default=5.0)
+    ap.add_argument("--only", choices=["adjoint", "batched", "batched_frame", "serving"],
+                    help="run one of the multi-stream or adjoint measurements alone (one JSON "
+                         "line with that measurement; for profiler captures)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

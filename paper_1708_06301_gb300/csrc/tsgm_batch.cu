@@ -176,10 +176,10 @@ __global__ void __launch_bounds__(kCtW* kCtH) kb_census(const BStream* __restric
 
 __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
                                                const BTable* __restrict__ tb, int Bc) {
-    const int ngroups = (gridDim.x * blockDim.x) >> 3;
-    const int sub = threadIdx.x & 7;
+    const int ngroups = (gridDim.x * blockDim.x) / kCostLanes;
+    const int sub = threadIdx.x % kCostLanes;
     const int total = tb->px_base[tb->ns];
-    for (int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 3; gi < total; gi += ngroups) {
+    for (int gi = (blockIdx.x * blockDim.x + threadIdx.x) / kCostLanes; gi < total; gi += ngroups) {
         const int s = find_stream(tb->px_base, tb->ns, gi);
         const BStream& b = st[s];
         if (!b.active || *b.status != 0u) continue;

@@ -247,9 +247,13 @@ __device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int
     out[y * W + x] = code;
 }
 
-// pixels g, g + ngroups, ... of one image, each walked by a group of 8 lanes (lane `sub`); the
-// row and column advance by the stride's quotient and remainder (no division per pixel), and the
-// next pixel's descriptor and left code are loaded while the current one's cells are computed
+// pixels g, g + ngroups, ... of one image, each walked by a group of kCostLanes = 4 lanes (lane
+// `sub` takes cells 4 sub .. 4 sub + 3 of every 16, one 32-bit store; a pixel's block is a multiple of 4
+// cells, so the last word's cells past the window are padding); the row and column advance by the
+// stride's quotient and remainder (no division per pixel), and the next pixel's descriptor and
+// left code are loaded while the current one's cells are computed
+constexpr int kCostLanes = 4;  // lanes per pixel of the cost computation
+
 __device__ __forceinline__ void cost_pixels(const uint64_t* __restrict__ cl,
                                             const uint64_t* __restrict__ cr,
                                             const uint2* __restrict__ desc, int W, int n, int Bc,
@@ -269,10 +273,15 @@ __device__ __forceinline__ void cost_pixels(const uint64_t* __restrict__ cl,
         const int a = (int)(dsc.y & 0xFFFFu);
         const int w = (int)(dsc.y >> 16);
         const uint64_t* row = cr + (size_t)y * W;
-        for (int j = sub; j < w; j += 8) {
-            const int xr = x - (a + j);
-            const int c = xr >= 0 ? __popcll(c0 ^ row[xr]) : Bc;
-            C[o + j] = (uint8_t)c;
+        for (int j = 4 * sub; j < w; j += 4 * kCostLanes) {
+            const int xr = x - (a + j);  // cells j .. j + 3 match columns xr .. xr - 3
+            uint32_t word = 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = xr - q >= 0 ? __popcll(c0 ^ row[xr - q]) : Bc;
+                word |= (uint32_t)c << (8 * q);
+            }
+            *reinterpret_cast<uint32_t*>(C + o + j) = word;
         }
         y += dy;
         x += dx;

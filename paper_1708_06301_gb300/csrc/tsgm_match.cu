@@ -34,8 +34,8 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
                                               const uint64_t* __restrict__ cr,
                                               const uint2* __restrict__ desc, int W, int n,
                                               int Bc, uint8_t* __restrict__ C) {
-    cost_pixels(cl, cr, desc, W, n, Bc, C, (blockIdx.x * blockDim.x + threadIdx.x) >> 3,
-                threadIdx.x & 7, (gridDim.x * blockDim.x) >> 3);
+    cost_pixels(cl, cr, desc, W, n, Bc, C, (blockIdx.x * blockDim.x + threadIdx.x) / kCostLanes,
+                threadIdx.x % kCostLanes, (gridDim.x * blockDim.x) / kCostLanes);
 }
 
 // Path aggregation of one image: all lines of all directions in one launch, NG groups of lanes
@@ -193,7 +193,7 @@ cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int H
 cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* desc, int W, int Hh,
                         int Bc, uint8_t* C, cudaStream_t st) {
     const int n = W * Hh;
-    int blocks = (n * 8 + 255) / 256;
+    int blocks = (n * kCostLanes + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     k_cost<<<blocks, 256, 0, st>>>(cl, cr, desc, W, n, Bc, C);
     return cudaGetLastError();
