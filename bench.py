@@ -525,14 +525,11 @@ def bench_serving(duration_s: float, budget_gb: float):
             "hbm_budget_gb": budget_gb}
 
 
-# DRAM bytes (read + write) of one aggregation launch from ncu's dram__bytes_read.sum and
-# dram__bytes_write.sum over the ten launches of one step of the sequence (one full-range frame, nine
-# reduced); None while k_sgm has changed since the last capture. The last capture
-# (profiles/k_sgm_kitti_1242x375_reduced.md) read 114,681,728 B per launch before the change of
-# which twin warp walks an all-full-range pair (same loads and stores, other warps).
-SGM_DRAM_BYTES_PER_LAUNCH = None
-SGM_DRAM_NOTE = ("k_sgm changed after the last ncu capture (which twin warp walks an all-full-range "
-                 "pair); that capture read 114.7 MB per launch")
+# DRAM bytes (read + write) of one aggregation launch: the mean over the ten launches of one step
+# of the sequence (one full-range frame, 620 MB; nine reduced, 10-20 MB each) from ncu's
+# dram__bytes_read.sum + dram__bytes_write.sum (profiles/k_sgm_kitti_1242x375_reduced.md).
+SGM_DRAM_BYTES_PER_LAUNCH = 74693734
+SGM_DRAM_NOTE = None
 
 
 def algorithmic_sgm_bytes(cells: int, px: int, census_bytes: int = 8) -> int:

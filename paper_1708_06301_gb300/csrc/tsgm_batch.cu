@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) kb_cost(const BStream* __restrict__ st,
 // horizontal lines) of one direction of one stream (see sgm_group_lines), every stream's
 // horizontal lines first
 template <int LPLW, int GL, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) kb_sgm(const BStream* __restrict__ st,
+__global__ void __launch_bounds__(WARPS * 32, GL == 8 ? 24 / WARPS : 1) kb_sgm(const BStream* __restrict__ st,
                                                      const BTable* __restrict__ tb, int n_slots,
                                                      int P1, int P2, int* __restrict__ counter) {
     constexpr int NG = 32 / GL;

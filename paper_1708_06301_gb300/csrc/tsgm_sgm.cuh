@@ -21,11 +21,14 @@
 // The recursion forgets its start fast (a window that shares no label with its predecessor's,
 // or P2 capping every difference, makes L independent of what came before), so the guess and
 // the true state agree after a few steps. The guess is then checked exactly: each later segment
-// is walked again from the true end state of the segment before it for kGFix steps, and its
-// state there is compared with the state the first walk had at the same pixel (a checkpoint).
-// Equal states give equal values from there on, so the first walk's later values stand; a
-// difference makes the second walk go on to the segment's end (and the next segment is walked
-// again from that end, and so on), so the result is the sequential recurrence's in every case.
+// is walked again from the true end state of the segment before it, and before its steps 16, 32
+// and kGFix its state is compared with the state the first walk had at the same pixel (three
+// checkpoints; the first two only for windows of the narrow form). Equal states give equal
+// values from there on, so the walk stops at the first check that agrees and the first walk's
+// later values stand; a difference at the last check makes the walk go on to the segment's end
+// (and the next segment is walked again from that end, and so on), so the result is the
+// sequential recurrence's in every case. Lines of different lengths in one warp check at their
+// own steps.
 //
 // State. Each line keeps its last L as a row of 16-bit labels in shared memory, indexed relative
 // to the window's lo, with +inf padding on both sides; two rows per line, used in turn. A step
@@ -57,10 +60,11 @@ __host__ __device__ constexpr int grp_dp() { return 32 * LPLW; }
 template <int LPLW>
 __host__ __device__ constexpr int grp_row() { return kGPadL + grp_dp<LPLW>() + kGPadR; }
 // shared memory of one warp in 32-bit words, for NG lines: state rows (2 per line), checkpoints
-// (one state per line), descriptor ring (4 blocks)
+// (one wide state and two narrow states, 4 (32 / NG) labels, per line), descriptor ring (4 blocks)
 template <int LPLW, int NG>
 __host__ __device__ constexpr int grp_words_ng() {
-    return NG * (grp_row<LPLW>() + 32) + NG * grp_dp<LPLW>() / 2 + 4 * kGBlk * NG * 2;
+    return NG * (grp_row<LPLW>() + 32) + NG * grp_dp<LPLW>() / 2 + 2 * 4 * 32 / 2 +
+           4 * kGBlk * NG * 2;
 }
 
 // Word offset of line g's two state rows (ROW / 2 words each, inside the line's ROW + 32 words).
@@ -127,8 +131,10 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     // checkpoint, descriptor ring column (entry s at word dcol + 2 NG (s & 31))
     const int rowA = grp_row_base<LPLW, NG>(g);
     const int rowB = rowA + ROW / 2;
-    uint32_t* const ckpt = wsm + NG * (ROW + 32) + g * CKW;
-    const int dcol0 = NG * (ROW + 32) + NG * CKW;  // the ring
+    uint32_t* const ckpt = wsm + NG * (ROW + 32) + g * CKW;  // the last check's (any window)
+    uint32_t* const ckn0 = wsm + NG * (ROW + 32) + NG * CKW + g * (CAPN / 2);  // the narrow ones
+    uint32_t* const ckn1 = ckn0 + NG * (CAPN / 2);
+    const int dcol0 = NG * (ROW + 32) + NG * CKW + 2 * NG * (CAPN / 2);  // the ring
     const int dcol = dcol0 + 2 * g;
     uint2* const dcol_g = reinterpret_cast<uint2*>(wsm + dcol);
 
@@ -149,10 +155,17 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     }
     const int maxslen = (int)__reduce_max_sync(kFull, (unsigned)slen);
     if (maxslen == 0) return;
-    // the step after which a later segment's state is saved (first walk) or compared (again);
-    // all later segments of the warp's lines have the same length, so the check is one step
-    const int cstep = (S > 1 && sg > 0) ? min(kGFix, slen) - 1 : -1;
-    const int cchk = (int)__reduce_max_sync(kFull, (unsigned)(cstep + 1));  // 0: no check
+    // the steps before which a later segment's state is saved (first walk) or compared (again);
+    // the last (kc2) may coincide with the others in a short segment, and then wins
+    const bool later = S > 1 && sg > 0 && slen > 0;
+    const int kc0 = later ? min(16, slen) : -1, kc2 = later ? min(kGFix, slen) : -1;
+    static_assert(kGFix <= 64, "check steps 16 .. kGFix as bits k - 1 of one word");
+    // the steps at which some group of the warp checks (bit k - 1), so that a step tests a
+    // register instead of voting
+    uint64_t cbits =
+        later ? (1ull << (kc0 - 1)) | (1ull << (min(32, slen) - 1)) | (1ull << (kc2 - 1)) : 0ull;
+    cbits = ((uint64_t)__reduce_or_sync(kFull, (unsigned)(cbits >> 32)) << 32) |
+            (uint64_t)__reduce_or_sync(kFull, (unsigned)cbits);
 
     for (int t = lane; t < NG * (ROW + 32); t += 32) wsm[t] = kInf2;
     // every ring entry holds a valid descriptor at all times (an empty window until written), so
@@ -180,7 +193,8 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     int mm = 0, mP = 0;                      // m and m + P2 of the state
     int prow = rowA;                         // the predecessor of the next step (word index)
     int nrow = rowB;                         // the row the next step writes
-    int ck_lo = 0, ck_w = 0;
+    // the windows of the three checkpoints, lo << 16 | w (w = 0xFFFF: a state too wide to save)
+    int ckw2 = 0, ckw0 = 0, ckw1 = 0;
     bool walker = slen > 0;  // this group walks in the current pass
 
     // costs of a step, in the form the step takes (two sets, used in turn)
@@ -267,9 +281,11 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         cp_async_wait<0>();
         __syncwarp();
         load_block(1);
-        bool stop = false;     // the walk of this pass ended at the check (the states agreed)
+        bool stop = false;     // the walk of this pass ended at a check (the states agreed)
         bool changed = false;  // this pass changed the segment's end state
-        int kend = pass == 0 ? maxslen : cchk;
+        // the step the warp's walk ends at: every segment's end in the first walk; in a walk
+        // again the end of the segments still walking, updated at every check
+        int kend = pass == 0 ? maxslen : (int)__reduce_max_sync(kFull, walker ? (unsigned)slen : 0u);
         // the pipeline: step k's descriptor (dcur) and wide vote (wcur) are known one step ahead,
         // its costs were loaded during step k - 1
         uint2 dcur = dread(0);
@@ -278,39 +294,44 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
 
         // one step; q: the cost set of this step (the next step's costs go to the other set)
         auto step = [&](int k, int q) -> bool {
-            if (k == cchk) {
-                // the check after step cstep: save the state (first walk) or compare with it;
-                // the state is L over the window (lo, w), entries past w are +inf in every row.
-                // The rows of the last step were written by other lanes: synchronise first.
+            if (k >= 1 && k <= 64 && ((cbits >> (k - 1)) & 1ull)) {
+                const bool at = walker && !stop && (k == kc0 || k == min(32, slen) || k == kc2);
+                // a check: save the state (first walk) or compare with it; the state is L over
+                // the window (lo, w), entries past w are +inf in every row. The rows of the last
+                // step were written by other lanes: synchronise first.
                 __syncwarp();
-                const bool mine = walker && cstep + 1 == k;
-                bool eq = lo_old == ck_lo && w_old == ck_w;
-                if (mine) {
-                    const uint32_t* const pr = wsm + prow;
+                const int ci = k == kc2 ? 2 : (k == min(32, slen) ? 1 : 0);
+                uint32_t* const ck = ci == 2 ? ckpt : (ci == 1 ? ckn1 : ckn0);
+                const int cap = ci == 2 ? DP : CAPN;  // a wider state is never equal here
+                const int cwin = ci == 2 ? ckw2 : (ci == 1 ? ckw1 : ckw0);
+                const bool fits = w_old <= cap;
+                bool eq = cwin == ((lo_old << 16) | w_old) && fits;
+                const uint32_t* const pr = wsm + prow;
+                if (at && fits) {
                     for (int t = j; t < (w_old + 1) / 2; t += GL) {
                         const uint32_t v = pr[kGPadL / 2 + t];
-                        if (pass == 0) ckpt[t] = v;
-                        else eq = eq && ckpt[t] == v;
-                    }
-                    if (pass == 0) {
-                        ck_lo = lo_old;
-                        ck_w = w_old;
+                        if (pass == 0) ck[t] = v;
+                        else eq = eq && ck[t] == v;
                     }
                 }
                 const bool same = (__ballot_sync(kFull, !eq) & gmask) == 0u;
-                if (mine && pass > 0) {
+                // the first walk saves; a walk again stops where the states agree, and where
+                // they differ goes on and rewrites the values after this step: they now follow
+                // this state, so it becomes the reference of the next comparison
+                const bool save = at && (pass == 0 || !same);
+                if (at && pass > 0) {
                     stop = same;
-                    changed = !same;
-                    // the walk goes on and rewrites the values after this step: they now follow
-                    // this state, so it becomes the reference of the next comparison
-                    if (!same) {
-                        const uint32_t* const pr = wsm + prow;
-                        for (int t = j; t < (w_old + 1) / 2; t += GL) ckpt[t] = pr[kGPadL / 2 + t];
-                        ck_lo = lo_old;
-                        ck_w = w_old;
-                    }
+                    changed = !same && ci == 2;
+                    if (!same && fits)
+                        for (int t = j; t < (w_old + 1) / 2; t += GL) ck[t] = pr[kGPadL / 2 + t];
                 }
-                if (pass > 0 && __any_sync(kFull, changed)) kend = maxslen;
+                if (save) {
+                    const int nwin = (lo_old << 16) | (fits ? w_old : 0xFFFF);
+                    if (ci == 2) ckw2 = nwin;
+                    else if (ci == 1) ckw1 = nwin;
+                    else ckw0 = nwin;
+                }
+                if (pass > 0) kend = (int)__reduce_max_sync(kFull, (walker && !stop) ? (unsigned)slen : 0u);
             }
             if (k >= kend) return false;
             const bool go = walker && !stop && k < slen;
