@@ -528,7 +528,7 @@ def bench_serving(duration_s: float, budget_gb: float):
 # DRAM bytes (read + write) of one aggregation launch: the mean over the ten launches of one step
 # of the sequence (one full-range frame, 620 MB; nine reduced, 10-20 MB each) from ncu's
 # dram__bytes_read.sum + dram__bytes_write.sum (profiles/k_sgm_kitti_1242x375_reduced.md).
-SGM_DRAM_BYTES_PER_LAUNCH = 74693734
+SGM_DRAM_BYTES_PER_LAUNCH = 74331469
 SGM_DRAM_NOTE = None
 
 
