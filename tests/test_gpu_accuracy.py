@@ -52,5 +52,9 @@ def test_reduced_no_worse_than_full_range_for_30_frames(tsgm):
     bad_full, frac_full = _run(tsgm, seq, tsgm.FLAG_FULL_RANGE)
     assert np.all(frac_full == 1.0)
     assert frac_red[0] == 1.0 and np.all(frac_red[1:] < 0.5)
+    # the per-frame table (shown with pytest -s)
+    print("\nframe  searched  bad3px_reduced  bad3px_full")
+    for k in range(N_FRAMES):
+        print(f"{k + 1:5d}  {frac_red[k]:8.4f}  {100 * bad_red[k]:14.3f}  {100 * bad_full[k]:11.3f}")
     worse = [(k + 1, bad_red[k], bad_full[k]) for k in range(N_FRAMES) if bad_red[k] > bad_full[k]]
     assert not worse, f"frames where the reduced search is less accurate: {worse}"
