@@ -528,7 +528,7 @@ struct GrpLines {
 // Segments per line for lines of up to `len` steps: as many (a power of two, at most 8) as keep
 // every segment at least kGSegMin steps long, so that the longest chain of the launch, a segment
 // plus its second walk, is short.
-constexpr int kGSegMin = 128;
+constexpr int kGSegMin = 64;
 __host__ __device__ __forceinline__ int grp_seg(int len) {
     int S = 1;
     while (S < 8 && len >= 2 * S * kGSegMin) S *= 2;
