@@ -599,8 +599,8 @@ __device__ __forceinline__ void select_part(
     }
     __syncthreads();
 
-    // ---- wide windows: one warp per pixel, the next pixel's path costs loaded during this one
-    // (NCH chunks of 128 labels cover the widest window)
+    // ---- wide windows: one warp per pixel, the path costs of the next two pixels loaded during
+    // this one (NCH chunks of 128 labels cover the widest window)
     uint16_t* scr = scr_all + wid * DP;
     const int nwide = n_wide;
     auto load_wide = [&](int q, uint32_t (&v)[NCH * NPATHS], uint2& dsc) {
@@ -608,11 +608,12 @@ __device__ __forceinline__ void select_part(
         dsc = desc[y * W + x0 + wideq[q]];
         load_wide_costs<NPATHS, NCH>(Lvol, vol_stride, dsc, v);
     };
-    uint32_t vcur[NCH * NPATHS], vnext[NCH * NPATHS];
-    uint2 dcur = make_uint2(0u, 0u), dnext = make_uint2(0u, 0u);
+    uint32_t vcur[NCH * NPATHS], vnext[NCH * NPATHS], vnext2[NCH * NPATHS];
+    uint2 dcur = make_uint2(0u, 0u), dnext = make_uint2(0u, 0u), dnext2 = make_uint2(0u, 0u);
     load_wide(wid, vcur, dcur);
+    load_wide(wid + nw, vnext, dnext);
     for (int q = wid; q < nwide; q += nw) {
-        load_wide(q + nw, vnext, dnext);
+        load_wide(q + 2 * nw, vnext2, dnext2);
         const int x = x0 + wideq[q];
         int dsr;
         float dzr, rr;
@@ -624,8 +625,12 @@ __device__ __forceinline__ void select_part(
             rzs[x - x0] = rr;
         }
 #pragma unroll
-        for (int t = 0; t < NCH * NPATHS; ++t) vcur[t] = vnext[t];
+        for (int t = 0; t < NCH * NPATHS; ++t) {
+            vcur[t] = vnext[t];
+            vnext[t] = vnext2[t];
+        }
         dcur = dnext;
+        dnext = dnext2;
     }
     if (split) {
         __syncthreads();  // this block's key atomics are done

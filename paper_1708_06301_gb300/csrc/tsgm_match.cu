@@ -142,20 +142,26 @@ __global__ void __launch_bounds__(256) k_select_wide(const uint8_t* __restrict__
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nwarps = gridDim.x * 8;
     uint16_t* const scr = scr_all[wid];
-    uint32_t vcur[NCH * NPATHS], vnext[NCH * NPATHS];
-    uint2 dcur = make_uint2(0u, 0u), dnext = make_uint2(0u, 0u);
+    // the path costs of the next two pixels are loaded during the current one
+    uint32_t vcur[NCH * NPATHS], vnext[NCH * NPATHS], vnext2[NCH * NPATHS];
+    uint2 dcur = make_uint2(0u, 0u), dnext = make_uint2(0u, 0u), dnext2 = make_uint2(0u, 0u);
     int t = blockIdx.x * 8 + wid;
-    int icur = 0, inext = 0;
+    int icur = 0, inext = 0, inext2 = 0;
     if (t < count) {
         icur = (int)wq[1 + t];
         dcur = desc[icur];
         load_wide_costs<NPATHS, NCH>(Lvol, vol_stride, dcur, vcur);
     }
+    if (t + nwarps < count) {
+        inext = (int)wq[1 + t + nwarps];
+        dnext = desc[inext];
+        load_wide_costs<NPATHS, NCH>(Lvol, vol_stride, dnext, vnext);
+    }
     for (; t < count; t += nwarps) {
-        if (t + nwarps < count) {
-            inext = (int)wq[1 + t + nwarps];
-            dnext = desc[inext];
-            load_wide_costs<NPATHS, NCH>(Lvol, vol_stride, dnext, vnext);
+        if (t + 2 * nwarps < count) {
+            inext2 = (int)wq[1 + t + 2 * nwarps];
+            dnext2 = desc[inext2];
+            load_wide_costs<NPATHS, NCH>(Lvol, vol_stride, dnext2, vnext2);
         }
         const int y = icur / W, x = icur - y * W;
         uint32_t* const grow = gkeys + (size_t)y * W;
@@ -169,9 +175,14 @@ __global__ void __launch_bounds__(256) k_select_wide(const uint8_t* __restrict__
             rz[icur] = rr;
         }
 #pragma unroll
-        for (int q = 0; q < NCH * NPATHS; ++q) vcur[q] = vnext[q];
+        for (int q = 0; q < NCH * NPATHS; ++q) {
+            vcur[q] = vnext[q];
+            vnext[q] = vnext2[q];
+        }
         dcur = dnext;
+        dnext = dnext2;
         icur = inext;
+        inext = inext2;
     }
 }
 
