@@ -43,36 +43,31 @@ __global__ void __launch_bounds__(256) k_cost(const uint64_t* __restrict__ cl,
 // sgm_group_lines; horizontal lines first: they are the longest chains).
 // The lines' groups are 4 lanes wide (windows of up to 16 labels in straight-line code, 8 lines
 // per warp) unless more than one pixel in 16 has a wider window (wq[0], the count of windows
-// wider than kSelNarrow = 16 labels, written by the offsets pass): then 8 lanes (up to 32 labels,
-// 4 lines per warp). The launch has enough warps for the second form; in the first, the warps
-// past the last line return at once.
+// wider than kSelNarrow = 16 labels, written by the offsets pass) or D > 128: then 8 lanes (up to
+// 32 labels, 4 lines per warp). Each form is its own kernel (so that each gets its own register
+// allocation: the 8-lane form needs fewer registers, and a full-range frame's 3000 warps then
+// fit on the GPU at once); both are launched, and the one that is not the frame's form returns
+// at once.
 constexpr int kGrpWarps = 4;
 
-template <int LPLW>
-__global__ void __launch_bounds__(kGrpWarps * 32) k_sgm(const uint8_t* __restrict__ C,
-                                                        const uint2* __restrict__ desc, int W,
-                                                        int Hh, int P1, int P2, GrpLines lines,
-                                                        uint8_t* __restrict__ Lvol,
-                                                        uint64_t vol_stride,
-                                                        const uint32_t* __restrict__ wq, int n) {
+template <int LPLW, int GL>
+__global__ void __launch_bounds__(kGrpWarps * 32, GL == 8 ? (LPLW == 8 ? 6 : 8) : 5) k_sgm(
+    const uint8_t* __restrict__ C, const uint2* __restrict__ desc, int W, int Hh, int P1, int P2,
+    GrpLines lines, uint8_t* __restrict__ Lvol, uint64_t vol_stride,
+    const uint32_t* __restrict__ wq, int n) {
     extern __shared__ uint32_t sgm_smem32[];
+    constexpr int NG = 32 / GL;
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kGrpWarps + wib;
-    uint32_t* const wsm = sgm_smem32 + wib * grp_words<LPLW>();
+    uint32_t* const wsm = sgm_smem32 + wib * grp_words_ng<LPLW, NG>();
     // 256 labels: always the 8-lane groups (the 4-lane form's dense step would hold 64 labels
     // of costs per lane)
     const bool eight = LPLW == 8 || 16ull * wq[0] > (unsigned long long)n;
+    if (eight != (GL == 8)) return;
     int code, first, nlines, seg;
-    if (!grp_warp_lines(lines, eight ? 4 : 8, gw, code, first, nlines, seg)) return;
+    if (!grp_warp_lines(lines, NG, gw, code, first, nlines, seg)) return;
     uint8_t* const Lv = Lvol + (size_t)code * vol_stride;
-    if constexpr (LPLW == 8) {
-        sgm_group_lines<LPLW, 8>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
-    } else {
-        if (eight)
-            sgm_group_lines<LPLW, 8>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
-        else
-            sgm_group_lines<LPLW, 4>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
-    }
+    sgm_group_lines<LPLW, GL>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
 }
 
 // Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the
@@ -210,28 +205,39 @@ cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* des
     return cudaGetLastError();
 }
 
+template <int LPLW, int GL>
+static cudaError_t launch_sgm_form(const uint8_t* C, const uint2* desc, int W, int Hh, int P1,
+                                   int P2, const GrpLines& L, uint8_t* Lvol, uint64_t vol_stride,
+                                   const uint32_t* wq, cudaStream_t st) {
+    constexpr int NG = 32 / GL;
+    int nwarps = 0;
+    for (int s = 0; s < L.nslots; ++s) {
+        const int per = NG / grp_slot_seg(L, s, NG);
+        nwarps += (L.count[s] + per - 1) / per;
+    }
+    const size_t smem = (size_t)kGrpWarps * grp_words_ng<LPLW, NG>() * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_sgm<LPLW, GL>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_sgm<LPLW, GL><<<(nwarps + kGrpWarps - 1) / kGrpWarps, kGrpWarps * 32, smem, st>>>(
+        C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, W * Hh);
+    return cudaGetLastError();
+}
+
+// both forms for D <= 128 (the 8-lane one first: on a full-range frame it does the work), the
+// 8-lane form alone beyond
 template <int LPLW>
 static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int Hh, int P1, int P2,
                                 const GrpLines& L, uint8_t* Lvol, uint64_t vol_stride,
                                 const uint32_t* wq, cudaStream_t st) {
-    int nwarps = 0;  // the larger count of the two forms (4 or 8 groups per warp)
-    for (int NG = 4; NG <= 8; NG *= 2) {
-        int nw = 0;
-        for (int s = 0; s < L.nslots; ++s) {
-            const int per = NG / grp_slot_seg(L, s, NG);
-            nw += (L.count[s] + per - 1) / per;
-        }
-        nwarps = nw > nwarps ? nw : nwarps;
+    cudaError_t e = launch_sgm_form<LPLW, 8>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
+    if constexpr (LPLW < 8) {
+        if (e == cudaSuccess)
+            e = launch_sgm_form<LPLW, 4>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
     }
-    const size_t smem = (size_t)kGrpWarps * grp_words<LPLW>() * sizeof(uint32_t);
-    if (smem > 48 * 1024) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_sgm<LPLW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_sgm<LPLW><<<(nwarps + kGrpWarps - 1) / kGrpWarps, kGrpWarps * 32, smem, st>>>(
-        C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, W * Hh);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
