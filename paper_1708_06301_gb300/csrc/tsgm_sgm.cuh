@@ -233,8 +233,8 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         }
     };
 
-    // narrow step of this group's line: lane j's labels lo + 4j .. lo + 4j + 3 in 32-bit
-    // arithmetic (computed everywhere; stored and taken as the new state where `keep`)
+    // narrow step of this group's line: lane j's labels lo + 4j .. lo + 4j + 3 as two packed
+    // 16-bit pairs (computed everywhere; stored and taken as the new state where `keep`)
     auto narrow = [&](uint2 ds, uint32_t cwd, bool keep) {
         const int lo = (int)(ds.y & 0xFFFFu), w = (int)(ds.y >> 16);
         const int e = min(max(lo - lo_old + 4 * j - 1, -6), cap_old);
@@ -242,24 +242,20 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
         const uint32_t* const r32 = wsm + prow + (ea >> 1);
         const uint32_t sh = (uint32_t)(ea & 1) << 4;
         const uint32_t w0 = r32[0], w1 = r32[1], w2 = r32[2], w3 = r32[3];
+        // predecessor entries e .. e + 5 as three pairs
         const uint32_t q0 = __funnelshift_r(w0, w1, sh), q1 = __funnelshift_r(w1, w2, sh),
                        q2 = __funnelshift_r(w2, w3, sh);
-        const int v[6] = {(int)(q0 & 0xFFFFu), (int)(q0 >> 16), (int)(q1 & 0xFFFFu),
-                          (int)(q1 >> 16),     (int)(q2 & 0xFFFFu), (int)(q2 >> 16)};
-        int L[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int t = min(min(v[i], v[i + 2]) + P1, v[i + 1]);
-            t = min(t, mP);
-            const int c = (int)((cwd >> (8 * i)) & 0xFFu);
-            L[i] = (4 * j + i < w) ? c + t - mm : kInf;
-        }
-        int m = min(min(L[0], L[1]), min(L[2], L[3]));
+        const uint32_t mm2 = (uint32_t)mm * 0x10001u, mP2 = (uint32_t)mP * 0x10001u;
+        const int rem = w - 4 * j;
+        const uint32_t k0 = pair_keep(rem), k1 = pair_keep(rem - 2);
+        const uint32_t v0 = (__byte_perm(cwd, 0u, 0x4140) + grp_t(q0, q1, P1x2, mP2)) - mm2;
+        const uint32_t v1 = (__byte_perm(cwd, 0u, 0x4342) + grp_t(q1, q2, P1x2, mP2)) - mm2;
+        const uint32_t pk0 = (v0 & k0) | (kInf2 & ~k0), pk1 = (v1 & k1) | (kInf2 & ~k1);
+        const uint32_t pm = vmin2(pk0, pk1);
+        int m = (int)min(pm & 0xFFFFu, pm >> 16);
 #pragma unroll
         for (int t = 1; t < GL; t <<= 1) m = min(m, __shfl_xor_sync(kFull, m, t));
         if (keep) {
-            const uint32_t pk0 = (uint32_t)L[0] | ((uint32_t)L[1] << 16);
-            const uint32_t pk1 = (uint32_t)L[2] | ((uint32_t)L[3] << 16);
             uint32_t* const rw = wsm + nrow + kGPadL / 2 + 2 * j;
             rw[0] = pk0;
             rw[1] = pk1;
@@ -267,7 +263,7 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
                 rw[CAPN / 2] = kInf2;
                 rw[CAPN / 2 + 1] = kInf2;
             }
-            if (4 * j < w) *reinterpret_cast<uint32_t*>(Lv + ds.x + 4 * j) = __byte_perm(pk0, pk1, 0x6420);
+            if (rem > 0) *reinterpret_cast<uint32_t*>(Lv + ds.x + 4 * j) = __byte_perm(pk0, pk1, 0x6420);
             lo_old = lo;
             w_old = w;
             cap_old = CAPN;
