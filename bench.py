@@ -525,10 +525,11 @@ def bench_serving(duration_s: float, budget_gb: float):
             "hbm_budget_gb": budget_gb}
 
 
-# DRAM bytes (read + write) of one aggregation launch: the mean over the ten launches of one step
-# of the sequence (one full-range frame, 620 MB; nine reduced, 10-20 MB each) from ncu's
+# DRAM bytes (read + write) of one frame's aggregation (its two launches: the lane-group form that
+# does the work and the other, which returns at once), mean over the ten frames of one step of the
+# sequence (one full-range frame, 621 MB; nine reduced, 11-21 MB each) from ncu's
 # dram__bytes_read.sum + dram__bytes_write.sum (profiles/k_sgm_kitti_1242x375_reduced.md).
-SGM_DRAM_BYTES_PER_LAUNCH = 74331469
+SGM_DRAM_BYTES_PER_LAUNCH = 75608474
 SGM_DRAM_NOTE = None
 
 
