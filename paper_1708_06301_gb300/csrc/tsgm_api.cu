@@ -311,6 +311,7 @@ tsgm_status match_stages(tsgm_ctx* ctx, const int16_t* lo, const int16_t* hi, fl
     TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->Lvol,
                            ctx->max_cells, ctx->wq, ctx->stream),
                 "sgm");
+    if (ctx->D <= 128) ++ctx->launches;  // launch_sgm enqueues both lane-group forms
     stage_end(ctx, TSGM_STAGE_SGM);
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;
     const float s_thr = p.S_max * (float)p.n_paths;
