@@ -326,8 +326,10 @@ tsgm_status tsgm_batch_match(tsgm_batch* b, const uint8_t* const* left,
                              const int16_t* const* d_hi, float* const* D_z, float* const* r_z);
 
 /* Time every candidate launch shape of the path aggregation (warps per block x blocks per SM)
- * on these inputs, `reps` steps each, keep the fastest and re-capture the graph. Outputs the
- * best mean step time (ms) and the chosen shape index. Synchronises. */
+ * on these inputs, `reps` steps each, keep the fastest; then, with that shape, every candidate
+ * grid of the cost kernel (2, 4, 8 or 16 blocks per SM); re-capture the graph (both step forms
+ * use the result). Outputs the best mean step time (ms) and the chosen aggregation shape index.
+ * Synchronises. */
 tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
                                 const uint8_t* const* right, const int16_t* const* d_lo,
                                 const int16_t* const* d_hi, float* const* D_z, float* const* r_z,

@@ -7,8 +7,8 @@
 // long horizontal chains of every stream start first and large and small streams balance; each
 // form of the step is captured once in a CUDA graph and replayed. A stream can sit a step out
 // (tsgm_batch_frame with no images for it): its blocks return at once and its state stays. The
-// launch shape of the aggregation is chosen by an autotuner that times the candidates on the
-// caller's data.
+// launch shape of the aggregation and the grid of the cost kernel are chosen by an autotuner
+// that times the candidates on the caller's data.
 
 #include <algorithm>
 #include <cfloat>
@@ -385,6 +385,7 @@ struct tsgm_batch {
     std::vector<uint8_t> seen;           // stream was active in a time step since create / reset
     std::string step_err;  // why the time-step form cannot run on these streams ("" if it can)
     int shape = 3;  // index into kShapes
+    int cost_blocks = 8;  // blocks per SM of the cost kernel
     int gl = 8;     // lanes per path line in the aggregation (4: windows up to 16 labels in one step)
     bool shape_ok[kNumShapes] = {};  // the shape's shared memory fits a block
     cudaGraphExec_t graph = nullptr;
@@ -437,7 +438,8 @@ cudaError_t enqueue_step(tsgm_batch* b, int shape, bool timed = false) {
         else
             kb_census<0, 0><<<cg, cb, 0, st>>>(b->d_streams, b->d_table, p.census_w, p.census_h);
     }
-    kb_cost<<<b->sms * 8, 256, 0, st>>>(b->d_streams, b->d_table, p.census_w * p.census_h - 1);
+    kb_cost<<<b->sms * b->cost_blocks, 256, 0, st>>>(b->d_streams, b->d_table,
+                                                     p.census_w * p.census_h - 1);
     if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecord(b->ev_sgm_a, st)) != cudaSuccess) return e;
     const SgmShape sh = kShapes[shape];
@@ -509,7 +511,8 @@ cudaError_t enqueue_frame_step(tsgm_batch* b, int shape) {
         else
             kb_census<0, 0><<<cg, cb, 0, st>>>(b->d_streams, b->d_table, p.census_w, p.census_h);
     }
-    kb_cost<<<b->sms * 8, 256, 0, st>>>(b->d_streams, b->d_table, p.census_w * p.census_h - 1);
+    kb_cost<<<b->sms * b->cost_blocks, 256, 0, st>>>(b->d_streams, b->d_table,
+                                                     p.census_w * p.census_h - 1);
     if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
     const SgmShape sh = kShapes[shape];
     sgm_kernel(b->maxD, b->gl, sh.warps)<<<b->sms * sh.blocks, sh.warps * 32,
@@ -832,10 +835,29 @@ tsgm_status tsgm_batch_autotune(tsgm_batch* b, const uint8_t* const* left,
             best_i = i;
         }
     }
+    b->shape = best_i;
+    // then the cost kernel's grid (blocks per SM), with the chosen aggregation shape
+    int best_c = b->cost_blocks;
+    for (int cb : {2, 4, 8, 16}) {
+        if (e != cudaSuccess) break;
+        b->cost_blocks = cb;
+        e = enqueue_step(b, best_i);  // warm-up
+        if (e != cudaSuccess) break;
+        cudaEventRecord(a, b->exec);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue_step(b, best_i);
+        cudaEventRecord(z, b->exec);
+        if (e == cudaSuccess) e = cudaEventSynchronize(z);
+        float ms = 0.0f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, z);
+        if (e == cudaSuccess && ms / reps < best) {
+            best = ms / reps;
+            best_c = cb;
+        }
+    }
+    b->cost_blocks = best_c;
     cudaEventDestroy(a);
     cudaEventDestroy(z);
     if (e != cudaSuccess) return bcuda(b, e, "autotune");
-    b->shape = best_i;
     if (b->fgraph) {  // the time-step form is captured again with the new shape when next used
         cudaGraphExecDestroy(b->fgraph);
         b->fgraph = nullptr;
