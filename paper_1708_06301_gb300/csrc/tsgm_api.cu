@@ -163,6 +163,8 @@ void free_all(tsgm_ctx* c) {
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
+    if (c->fexec) cudaGraphExecDestroy(c->fexec);
+    c->fexec = nullptr;
     for (int k = 0; k < 2; ++k) {
         if (c->ev_slot_in[k]) cudaEventDestroy(c->ev_slot_in[k]);
         if (c->ev_slot_used[k]) cudaEventDestroy(c->ev_slot_used[k]);
@@ -548,14 +550,14 @@ tsgm_status tsgm_kalman_update(tsgm_ctx* ctx, const float* pred_D, const float* 
     return TSGM_OK;
 }
 
-tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right, const float R[9],
-                       const float t[3], const float K[9], float baseline, float* D, float* P) {
-    if (!ctx) return TSGM_ERR_INVALID_ARG;
-    if (!left || !right || !K || !D || !P)
-        return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: null pointer");
-    if (D == P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: D and P alias");
-    if (ctx->has_prev && (!R || !t))
-        return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: pose required after the first frame");
+}  // extern "C"
+
+namespace {
+
+// Every stage of one time step, enqueued on the context's streams (the census on the second).
+tsgm_status frame_enqueue(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
+                          const float R[9], const float t[3], const float K[9], float baseline,
+                          float* D, float* P) {
     TSGM_TRY(census_fork(ctx, left, right));
     if (ctx->has_prev) {
         TSGM_TRY(warp_stage(ctx, ctx->stateD, ctx->stateP, R, t, K, baseline, ctx->predD, ctx->predP));
@@ -583,6 +585,88 @@ tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
         TSGM_TRY(sad_stage(ctx, left, right, D, P, ctx->stateD, ctx->stateP));
     ctx->has_prev = 1;
     return TSGM_OK;
+}
+
+// The step as a CUDA graph: captured from the context's stream, then either used to update the
+// instantiated graph of the last step in place (same kernels, new pointers and pose: the usual
+// case from the second frame on) or instantiated anew, and launched. A step of ~20 small kernels
+// runs with shorter gaps between them this way. Not for the legacy default streams (they cannot
+// be captured) nor while stage timing is on; a capture that fails leaves the context on the
+// direct path for good. Returns false when the step was not run (the caller runs it directly).
+bool frame_graph(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right, const float R[9],
+                 const float t[3], const float K[9], float baseline, float* D, float* P,
+                 tsgm_status* st) {
+    if (ctx->graph_off || ctx->prof || ctx->stream == nullptr || ctx->stream == cudaStreamLegacy ||
+        ctx->stream == cudaStreamPerThread)
+        return false;
+    // the caller may be capturing the stream itself: then the kernels go into its capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->graph_off = true;
+        return false;
+    }
+    const int had_prev = ctx->has_prev;
+    const uint64_t launches = ctx->launches;
+    const tsgm_status s = frame_enqueue(ctx, left, right, R, t, K, baseline, D, P);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (s != TSGM_OK || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        ctx->has_prev = had_prev;
+        ctx->launches = launches;
+        if (s != TSGM_OK) {  // an argument or launch error: nothing ran, report it
+            *st = s;
+            return true;
+        }
+        ctx->graph_off = true;  // the capture itself failed: run this step directly
+        return false;
+    }
+    bool ok = true;
+    if (ctx->fexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ctx->fexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(ctx->fexec);
+            ctx->fexec = nullptr;
+        }
+    }
+    if (!ctx->fexec) ok = cudaGraphInstantiate(&ctx->fexec, g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    if (ok) ok = cudaGraphLaunch(ctx->fexec, ctx->stream) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (ctx->fexec) cudaGraphExecDestroy(ctx->fexec);
+        ctx->fexec = nullptr;
+        ctx->graph_off = true;
+        ctx->has_prev = had_prev;
+        ctx->launches = launches;
+        return false;
+    }
+    *st = TSGM_OK;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right, const float R[9],
+                       const float t[3], const float K[9], float baseline, float* D, float* P) {
+    if (!ctx) return TSGM_ERR_INVALID_ARG;
+    if (!left || !right || !K || !D || !P)
+        return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: null pointer");
+    if (D == P) return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: D and P alias");
+    if (ctx->has_prev && (!R || !t))
+        return fail(ctx, TSGM_ERR_INVALID_ARG, "tsgm_frame: pose required after the first frame");
+    tsgm_status st = TSGM_OK;
+    if (frame_graph(ctx, left, right, R, t, K, baseline, D, P, &st)) return st;
+    return frame_enqueue(ctx, left, right, R, t, K, baseline, D, P);
 }
 
 tsgm_status tsgm_frame_host(tsgm_ctx* ctx, const uint8_t* left_host, const uint8_t* right_host,

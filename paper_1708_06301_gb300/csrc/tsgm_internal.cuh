@@ -134,6 +134,8 @@ struct tsgm_ctx {
     int hslot = 0;
 
     int has_prev = 0;
+    cudaGraphExec_t fexec = nullptr;  // the last time step as a graph (tsgm_frame)
+    bool graph_off = false;           // tsgm_frame launches its kernels directly
     uint64_t launches = 0;  // kernels enqueued by this context (for launch accounting)
     std::string err;
 

@@ -115,3 +115,39 @@ def test_timed_sequence_full_range_every_frame(tsgm, oracle_runs):
     for k in range(N_FRAMES):
         assert np.all(g[k]["lo"] == 0) and np.all(g[k]["hi"] == 127)
         _compare(g[k], o[k], k)
+
+
+@pytest.mark.slow
+def test_timed_sequence_on_a_stream_of_its_own_equals_the_default_stream(tsgm):
+    """On a non-default CUDA stream tsgm_frame launches each step as a CUDA graph (captured,
+    then updated in place frame after frame); on the legacy default stream it launches the
+    kernels one by one. Both give the same maps, bit for bit, on every frame, also after a reset
+    (a first frame again: another graph) and with stage timing switched on mid-sequence (back to
+    direct launches)."""
+    seq = synth.kitti_like(2, n_frames=N_FRAMES)
+    W, H = seq.cam.W, seq.cam.H
+    b = f32(seq.cam.b)
+    left = [dev(x) for x in seq.left]
+    right = [dev(x) for x in seq.right]
+
+    def run(stream, profile_from=None):
+        out = []
+        with tsgm.Context(tsgm.default_params(W, H, flags=tsgm.FLAG_FILL_GAPS),
+                          stream=stream) as ctx:
+            D, P = empty((H, W), np.float32), empty((H, W), np.float32)
+            for rep in range(2):
+                ctx.reset()
+                for k in range(N_FRAMES):
+                    if profile_from is not None and rep == 1 and k == profile_from:
+                        ctx.profile(True)
+                    ctx.frame(left[k], right[k], seq.R[k], seq.t[k], seq.K, b, D, P)
+                    out.append((host(D, np.float32), host(P, np.float32)))
+        return out
+
+    ref = run(0)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        got = run(s.cuda_stream, profile_from=6)
+    for k, ((Dg, Pg), (Dr, Pr)) in enumerate(zip(got, ref)):
+        assert np.array_equal(Dg, Dr), k
+        assert np.array_equal(Pg, Pr), k
