@@ -187,7 +187,6 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     };
 
     const uint32_t P1x2 = ((uint32_t)P1 << 16) | (uint32_t)P1;
-    const uint32_t P2x2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
     // predecessor of a first step: all +inf, m = 0 and no P2 term, so that L = C
     int lo_old = 0, w_old = 0, cap_old = 0;  // the state's window and its row's labels
     int mm = 0, mP = 0;                      // m and m + P2 of the state
