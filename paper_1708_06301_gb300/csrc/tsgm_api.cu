@@ -163,8 +163,10 @@ void free_all(tsgm_ctx* c) {
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
-    if (c->fexec) cudaGraphExecDestroy(c->fexec);
-    c->fexec = nullptr;
+    for (cudaGraphExec_t& x : c->fexec) {
+        if (x) cudaGraphExecDestroy(x);
+        x = nullptr;
+    }
     for (int k = 0; k < 2; ++k) {
         if (c->ev_slot_in[k]) cudaEventDestroy(c->ev_slot_in[k]);
         if (c->ev_slot_used[k]) cudaEventDestroy(c->ev_slot_used[k]);
@@ -301,7 +303,7 @@ tsgm_status census_fork(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right
 // Matching on windows whose offsets are already in ctx->off and census codes forked by
 // census_fork.
 tsgm_status match_stages(tsgm_ctx* ctx, const int16_t* lo, const int16_t* hi, float* Dz,
-                         float* rz) {
+                         float* rz, bool full) {
     const tsgm_params& p = ctx->prm;
     TSGM_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "census join");
     stage_begin(ctx, TSGM_STAGE_COST);
@@ -311,9 +313,9 @@ tsgm_status match_stages(tsgm_ctx* ctx, const int16_t* lo, const int16_t* hi, fl
     stage_end(ctx, TSGM_STAGE_COST);
     stage_begin(ctx, TSGM_STAGE_SGM);
     TSGM_LAUNCH(launch_sgm(ctx->C, ctx->desc, ctx->W, ctx->H, ctx->D, p.n_paths, p.P1, p.P2, ctx->Lvol,
-                           ctx->max_cells, ctx->wq, ctx->stream),
+                           ctx->max_cells, ctx->wq, full, ctx->stream),
                 "sgm");
-    if (ctx->D <= 128) ++ctx->launches;  // launch_sgm enqueues both lane-group forms
+    if (ctx->D <= 128 && !full) ++ctx->launches;  // launch_sgm enqueues both lane-group forms
     stage_end(ctx, TSGM_STAGE_SGM);
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;
     const float s_thr = p.S_max * (float)p.n_paths;
@@ -535,7 +537,7 @@ tsgm_status tsgm_match(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
                                ctx->desc, ctx->cells, ctx->wq, ctx->stream),
                 "offsets");
     stage_end(ctx, TSGM_STAGE_OFFSETS);
-    return match_stages(ctx, ctx->lo, ctx->hi, D_z, r_z);
+    return match_stages(ctx, ctx->lo, ctx->hi, D_z, r_z, false);
 }
 
 tsgm_status tsgm_kalman_update(tsgm_ctx* ctx, const float* pred_D, const float* pred_P,
@@ -575,7 +577,9 @@ tsgm_status frame_enqueue(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* rig
     } else {
         TSGM_TRY(windows_stage(ctx, ctx->predD, ctx->predP, ctx->lo, ctx->hi));
     }
-    TSGM_TRY(match_stages(ctx, ctx->lo, ctx->hi, ctx->Dz, ctx->rz));
+    // every window is the whole range on a first frame and in the full-range mode
+    const bool full = !ctx->has_prev || (ctx->prm.flags & TSGM_FLAG_FULL_RANGE) != 0;
+    TSGM_TRY(match_stages(ctx, ctx->lo, ctx->hi, ctx->Dz, ctx->rz, full));
     stage_begin(ctx, TSGM_STAGE_KALMAN);
     TSGM_LAUNCH(launch_kalman(ctx->predD, ctx->predP, ctx->Dz, ctx->rz, ctx->n, D, P, ctx->stateD,
                           ctx->stateP, ctx->stream),
@@ -587,9 +591,9 @@ tsgm_status frame_enqueue(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* rig
     return TSGM_OK;
 }
 
-// The step as a CUDA graph: captured from the context's stream, then either used to update the
-// instantiated graph of the last step in place (same kernels, new pointers and pose: the usual
-// case from the second frame on) or instantiated anew, and launched. A step of ~20 small kernels
+// The step as a CUDA graph: captured from the context's stream, then either used to update in
+// place the instantiated graph of the last step of its kind (a first frame, or a frame with a
+// previous state: the same kernels, new pointers and pose) or instantiated anew, and launched. A step of ~20 small kernels
 // runs with shorter gaps between them this way. Not for the legacy default streams (they cannot
 // be captured) nor while stage timing is on; a capture that fails leaves the context on the
 // direct path for good. Returns false when the step was not run (the caller runs it directly).
@@ -628,21 +632,22 @@ bool frame_graph(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right, const
         return false;
     }
     bool ok = true;
-    if (ctx->fexec) {
+    cudaGraphExec_t& ex = ctx->fexec[had_prev ? 1 : 0];
+    if (ex) {
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(ctx->fexec, g, &info) != cudaSuccess) {
+        if (cudaGraphExecUpdate(ex, g, &info) != cudaSuccess) {
             cudaGetLastError();
-            cudaGraphExecDestroy(ctx->fexec);
-            ctx->fexec = nullptr;
+            cudaGraphExecDestroy(ex);
+            ex = nullptr;
         }
     }
-    if (!ctx->fexec) ok = cudaGraphInstantiate(&ctx->fexec, g, 0) == cudaSuccess;
+    if (!ex) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
     cudaGraphDestroy(g);
-    if (ok) ok = cudaGraphLaunch(ctx->fexec, ctx->stream) == cudaSuccess;
+    if (ok) ok = cudaGraphLaunch(ex, ctx->stream) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        if (ctx->fexec) cudaGraphExecDestroy(ctx->fexec);
-        ctx->fexec = nullptr;
+        if (ex) cudaGraphExecDestroy(ex);
+        ex = nullptr;
         ctx->graph_off = true;
         ctx->has_prev = had_prev;
         ctx->launches = launches;

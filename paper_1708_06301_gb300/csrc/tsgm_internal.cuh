@@ -60,10 +60,11 @@ cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int H
                           uint64_t* outA, uint64_t* outB, cudaStream_t st);
 cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* desc, int W, int Hh,
                         int Bc, uint8_t* C, cudaStream_t st);
-// wq: the queue of wide pixels written by launch_offsets (its count picks the lane groups)
+// wq: the queue of wide pixels written by launch_offsets (its count picks the lane groups);
+// full: every window is [0, D - 1] (one launch of the full-range kernel, desc and wq unread)
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
                        int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, const uint32_t* wq,
-                       cudaStream_t st);
+                       bool full, cudaStream_t st);
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
                           int W, int Hh, int D, float s_thr, float r_min, int lr_tol, float* Dz,
                           float* rz, uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,
@@ -134,7 +135,8 @@ struct tsgm_ctx {
     int hslot = 0;
 
     int has_prev = 0;
-    cudaGraphExec_t fexec = nullptr;  // the last time step as a graph (tsgm_frame)
+    // the time step as a graph (tsgm_frame): [0] a full-range step, [1] a reduced one
+    cudaGraphExec_t fexec[2] = {nullptr, nullptr};
     bool graph_off = false;           // tsgm_frame launches its kernels directly
     uint64_t launches = 0;  // kernels enqueued by this context (for launch accounting)
     std::string err;

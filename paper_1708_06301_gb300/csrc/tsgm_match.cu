@@ -70,6 +70,26 @@ __global__ void __launch_bounds__(kGrpWarps * 32, GL == 8 ? (LPLW == 8 ? 6 : 8) 
     sgm_group_lines<LPLW, GL>(C, desc, W, Hh, P1, P2, code, first, nlines, seg, Lv, wsm);
 }
 
+// Path aggregation of an image whose windows are all the full range (every block rD = D rounded
+// up to 4 cells, pixel i's at cell i rD): one warp per line (sgm_full_line), lines in the same
+// direction-major order, no descriptors read.
+constexpr int kFullWarps = 8;
+
+template <int LPLW>
+__global__ void __launch_bounds__(kFullWarps * 32, LPLW == 8 ? 6 : 8) k_sgm_full(const uint8_t* __restrict__ C, int W,
+                                                              int Hh, int D, int P1, int P2,
+                                                              GrpLines lines,
+                                                              uint8_t* __restrict__ Lvol,
+                                                              uint64_t vol_stride) {
+    __shared__ uint32_t ring[kFullWarps * kFullRing * 32 * full_words<LPLW>()];
+    const int gw = blockIdx.x * kFullWarps + (threadIdx.x >> 5);
+    int code, first, nlines, seg;
+    if (!grp_warp_lines(lines, 1, gw, code, first, nlines, seg)) return;
+    sgm_full_line<LPLW>(C, W, Hh, D, (D + 3) & ~3, P1, P2, code, first,
+                        Lvol + (size_t)code * vol_stride,
+                        ring + (threadIdx.x >> 5) * kFullRing * 32 * full_words<LPLW>());
+}
+
 // Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the
 // row's pixels (seg columns from x0). Every block keeps the right-view keys its own pixels can
 // reach, columns x0 - (D - 1) .. x0 + seg - 1, with atomics in its own shared memory (merging the
@@ -242,7 +262,7 @@ static cudaError_t launch_sgm_t(const uint8_t* C, const uint2* desc, int W, int 
 
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
                        int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, const uint32_t* wq,
-                       cudaStream_t st) {
+                       bool full, cudaStream_t st) {
     // direction codes: horizontal (0, 1), vertical (2, 3), then the diagonals
     GrpLines L;
     L.nslots = n_paths;
@@ -251,6 +271,18 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
         L.count[code] = code <= 1 ? Hh : (code <= 3 ? W : W + Hh - 1);
         // long lines in segments
         L.seg[code] = grp_seg(code <= 1 ? W : (code <= 3 ? Hh : (W < Hh ? W : Hh)));
+    }
+    if (full) {
+        int nwarps = 0;
+        for (int code = 0; code < n_paths; ++code) nwarps += L.count[code];
+        const int blocks = (nwarps + kFullWarps - 1) / kFullWarps;
+        if (D <= 64)
+            k_sgm_full<2><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, L, Lvol, vol_stride);
+        else if (D <= 128)
+            k_sgm_full<4><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, L, Lvol, vol_stride);
+        else
+            k_sgm_full<8><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, L, Lvol, vol_stride);
+        return cudaGetLastError();
     }
     if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
     if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);

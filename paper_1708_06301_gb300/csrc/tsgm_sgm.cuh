@@ -511,6 +511,109 @@ __device__ __forceinline__ void sgm_group_lines(const uint8_t* __restrict__ C,
     }
 }
 
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// Cost ring of the full-range walker: kFullRing steps of 32 lanes x full_words<LPLW>() words per
+// warp, filled kFullAhead steps ahead (a slot is refilled kFullRing - kFullAhead steps after its
+// last read, whose value the walk has consumed by then).
+constexpr int kFullRing = 16;
+constexpr int kFullAhead = 12;
+template <int LPLW>
+__host__ __device__ constexpr int full_words() { return LPLW == 8 ? 2 : 1; }
+
+// One path line whose windows are all the full range [0, D - 1] (a first frame, or the
+// full-range mode: known before the launch), one warp, lane j holding labels LPLW j .. LPLW j +
+// LPLW - 1 of the state in registers as packed 16-bit pairs: the neighbours d - 1 and d + 1 across
+// lanes come by shuffle, m by redux.sync. The costs of a step (every pixel's block of rD = D
+// rounded up to 4 cells, 4-byte aligned) reach this lane's words of the ring by cp.async,
+// kFullAhead steps ahead, so that a long line is not bound by the load latency. Labels from D on
+// are +inf. Same recurrence and first step (L = C) as sgm_group_lines. ring: this warp's
+// kFullRing * 32 * full_words<LPLW>() words of shared memory.
+template <int LPLW>
+__device__ __forceinline__ void sgm_full_line(const uint8_t* __restrict__ C, int W, int Hh, int D,
+                                              int rD, int P1, int P2, int code, int line,
+                                              uint8_t* __restrict__ Lv, uint32_t* const ring) {
+    static_assert(LPLW == 2 || LPLW == 4 || LPLW == 8, "labels per lane");
+    static_assert((kFullRing & (kFullRing - 1)) == 0 && kFullAhead + 4 <= kFullRing, "ring");
+    constexpr int NP = LPLW / 2;              // packed pairs per lane
+    constexpr int NW = full_words<LPLW>();    // ring words per lane and step
+    const int lane = threadIdx.x & 31;
+    int i0 = 0, stp = 0, len = 0;
+    line_geometry(code, line, W, Hh, i0, stp, len);
+    const int base = LPLW * lane;  // this lane's first label
+    uint32_t kp[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) kp[k] = pair_keep(D - (base + 2 * k));
+    const uint32_t P1x2 = ((uint32_t)P1 << 16) | (uint32_t)P1;
+    // the 4-byte words a lane copies: its own (two lanes share one word when LPLW = 2)
+    const int cb = LPLW == 2 ? 4 * (lane >> 1) : base;
+    const uint32_t psel = LPLW == 2 && (lane & 1) ? 0x4342u : 0x4140u;
+    uint32_t* const slot0 = ring + lane * NW;
+    auto issue = [&](int s) {
+        if (s < len && base < D) {
+            const uint8_t* const src = C + (size_t)(i0 + s * stp) * rD + cb;
+            uint32_t* const dst = slot0 + (s & (kFullRing - 1)) * 32 * NW;
+#pragma unroll
+            for (int g = 0; g < NW; ++g)
+                if (base + 4 * g < D) cp_async4(dst + g, src + 4 * g);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int s = 0; s < kFullAhead; ++s) issue(s);
+
+    uint32_t P[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) P[k] = kInf2;
+    uint32_t mm2 = 0u, mP2 = 0u;  // a first step: no predecessor, L = C
+    for (int s = 0; s < len; ++s) {
+        cp_async_wait<kFullAhead - 1>();  // this step's copy (the oldest group) has landed
+        uint32_t cw[NW];
+#pragma unroll
+        for (int g = 0; g < NW; ++g) cw[g] = slot0[(s & (kFullRing - 1)) * 32 * NW + g];
+        issue(s + kFullAhead);
+        uint32_t cp[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+            cp[k] = __byte_perm(cw[k >> 1], 0u, LPLW == 2 ? psel : ((k & 1) ? 0x4342u : 0x4140u));
+        uint32_t up = __shfl_up_sync(kFull, P[NP - 1], 1);
+        uint32_t dn = __shfl_down_sync(kFull, P[0], 1);
+        if (lane == 0) up = kInf2;
+        if (lane == 31) dn = kInf2;
+        // X[k]: the pair (label base + 2k - 1, base + 2k) of the predecessor
+        uint32_t X[NP + 1];
+        X[0] = __byte_perm(up, P[0], 0x5432);
+#pragma unroll
+        for (int k = 1; k < NP; ++k) X[k] = __byte_perm(P[k - 1], P[k], 0x5432);
+        X[NP] = __byte_perm(P[NP - 1], dn, 0x5432);
+        uint32_t pm = kInf2;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const uint32_t v = (cp[k] + grp_t(X[k], X[k + 1], P1x2, mP2)) - mm2;
+            P[k] = (v & kp[k]) | (kInf2 & ~kp[k]);
+            pm = vmin2(pm, P[k]);
+        }
+        const unsigned m = __reduce_min_sync(kFull, min(pm & 0xFFFFu, pm >> 16));
+        mm2 = m * 0x10001u;
+        mP2 = (m + (unsigned)P2) * 0x10001u;
+        if (base < D) {
+            uint8_t* const dst = Lv + (size_t)(i0 + s * stp) * rD + base;
+            if constexpr (LPLW == 2) {
+                *reinterpret_cast<uint16_t*>(dst) = (uint16_t)__byte_perm(P[0], 0u, 0x0020);
+            } else {
+#pragma unroll
+                for (int g = 0; g < NW; ++g)
+                    if (base + 4 * g < D)
+                        reinterpret_cast<uint32_t*>(dst)[g] = __byte_perm(P[2 * g], P[2 * g + 1], 0x6420);
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // Lines of one image for the grouped walker: direction codes in launch order (horizontal pairs
 // first: the longest chains) and their line counts.
 struct GrpLines {

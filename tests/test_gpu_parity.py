@@ -226,6 +226,64 @@ def test_match_stages_bitexact(tsgm, case):
     assert_maps(g["Dz"], g["rz"], o["Dz"], o["rz"])
 
 
+# First frames: every window is [0, D - 1], and the aggregation runs its full-range kernel (one
+# warp per line, labels in registers); D ragged against the lanes' labels (41, 101, 201), exact
+# (64, 128, 256), a single label, lines shorter than a warp and long horizontal lines.
+FULL_CASES = [
+    # W, H, D, census, paths
+    (97, 45, 41, (5, 5), 4),
+    (64, 33, 64, (5, 5), 8),
+    (131, 37, 101, (9, 7), 8),
+    (300, 20, 128, (9, 7), 8),
+    (1242, 16, 128, (3, 3), 8),
+    (40, 12, 201, (9, 7), 8),
+    (1300, 6, 256, (5, 5), 4),
+    (5, 3, 1, (3, 3), 8),
+    (1, 9, 16, (5, 5), 8),
+    (13, 1, 33, (5, 5), 8),
+    (3, 2, 128, (3, 3), 8),
+]
+
+
+@pytest.mark.parametrize("case", FULL_CASES)
+def test_first_frame_full_range_bitexact(tsgm, case):
+    W, H, D, (cw, ch), npaths = case
+    seq_l, seq_r = synth.random_images(W * 5 + H + D, W, H)
+    right = np.roll(seq_l, -min(5, D - 1), axis=1)
+    right[:, -5:] = seq_r[:, -5:]
+    K = np.array([[0.9 * W, 0, W / 2], [0, 0.9 * W, H / 2], [0, 0, 1]], np.float32)
+    with make_ctx(tsgm, W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths) as ctx:
+        Dg, Pg = empty((H, W), np.float32), empty((H, W), np.float32)
+        ctx.frame(dev(seq_l), dev(right), None, None, K, f32(0.5), Dg, Pg)
+        off = empty((W * H + 1,), np.uint32)
+        ctx.inspect("offsets", off, W * H + 1)
+        offg = host(off, np.uint32)
+        storage = int(offg[-1])
+        C = empty((storage,), np.uint8)
+        S = empty((storage,), np.uint16)
+        ctx.inspect("cost", C, storage)
+        ctx.inspect("S", S, storage)
+        ds, dr, va = empty((H, W), np.int16), empty((H, W), np.int16), empty((H, W), np.uint8)
+        ctx.inspect("dstar", ds, W * H)
+        ctx.inspect("dright", dr, W * H)
+        ctx.inspect("lr_valid", va, W * H)
+        lo = np.zeros((H, W), np.int16)
+        hi = np.full((H, W), D - 1, np.int16)
+        g = dict(C=compact(host(C, np.uint8), offg, lo, hi), S=compact(host(S, np.uint16), offg, lo, hi),
+                 ds=host(ds, np.int16), dr=host(dr, np.int16), va=host(va, np.uint8),
+                 D=host(Dg, np.float32), P=host(Pg, np.float32))
+    o = oracle.match(seq_l, right, lo, hi, oparams(W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths),
+                     keep=True)
+    assert storage == W * H * ((D + 3) // 4 * 4)
+    assert np.array_equal(g["C"], o["C"])
+    assert np.array_equal(g["S"], o["S"])
+    assert np.array_equal(g["ds"].astype(np.int32), o["dstar"])
+    assert np.array_equal(g["dr"].astype(np.int32), o["dright"])
+    assert np.array_equal(g["va"], o["valid"])
+    # no prediction on a first frame: the Kalman update passes the measurement through
+    assert_maps(g["D"], g["P"], o["Dz"], o["rz"])
+
+
 def test_kalman_elementwise(tsgm):
     W, H = 257, 3
     n = W * H
