@@ -75,19 +75,49 @@ __global__ void __launch_bounds__(kGrpWarps * 32, GL == 8 ? (LPLW == 8 ? 6 : 8) 
 // direction-major order, no descriptors read.
 constexpr int kFullWarps = 8;
 
-template <int LPLW>
-__global__ void __launch_bounds__(kFullWarps * 32, LPLW == 8 ? 6 : 8) k_sgm_full(const uint8_t* __restrict__ C, int W,
-                                                              int Hh, int D, int P1, int P2,
-                                                              GrpLines lines,
-                                                              uint8_t* __restrict__ Lvol,
-                                                              uint64_t vol_stride) {
-    __shared__ uint32_t ring[kFullWarps * kFullRing * 32 * full_words<LPLW>()];
+// Warp gw's line: direction codes 0 .. n_paths - 1 in turn (horizontal, vertical, diagonal).
+__device__ __forceinline__ bool full_warp_line(int n_paths, int W, int Hh, int gw, int& code,
+                                               int& line) {
+    int base = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (c < n_paths) {
+            const int cnt = c <= 1 ? Hh : (c <= 3 ? W : W + Hh - 1);
+            if (gw < base + cnt) {
+                code = c;
+                line = gw - base;
+                return true;
+            }
+            base += cnt;
+        }
+    }
+    return false;
+}
+
+template <int LPLW, bool V16, bool EXACT>
+__global__ void __launch_bounds__(kFullWarps * 32, LPLW == 8 ? (EXACT ? 6 : 5) : (EXACT ? 8 : 6)) k_sgm_full(
+    const uint8_t* __restrict__ C, int W, int Hh, int D, int P1, int P2, int n_paths,
+    uint8_t* __restrict__ Lvol, uint64_t vol_stride) {
+    __shared__ __align__(16) uint32_t ring[kFullWarps * kFullRing * 8 * LPLW];
     const int gw = blockIdx.x * kFullWarps + (threadIdx.x >> 5);
-    int code, first, nlines, seg;
-    if (!grp_warp_lines(lines, 1, gw, code, first, nlines, seg)) return;
-    sgm_full_line<LPLW>(C, W, Hh, D, (D + 3) & ~3, P1, P2, code, first,
-                        Lvol + (size_t)code * vol_stride,
-                        ring + (threadIdx.x >> 5) * kFullRing * 32 * full_words<LPLW>());
+    int code = 0, line = 0;
+    if (!full_warp_line(n_paths, W, Hh, gw, code, line)) return;
+    sgm_full_line<LPLW, V16, EXACT>(C, W, Hh, D, (D + 3) & ~3, P1, P2, code, line,
+                                    Lvol + (size_t)code * vol_stride,
+                                    ring + (threadIdx.x >> 5) * kFullRing * 8 * LPLW);
+}
+
+template <int LPLW>
+static void launch_sgm_full_t(const uint8_t* C, int W, int Hh, int D, int P1, int P2, int n_paths,
+                              int nwarps, uint8_t* Lvol, uint64_t vol_stride, cudaStream_t st) {
+    const int blocks = (nwarps + kFullWarps - 1) / kFullWarps;
+    const int rD = (D + 3) & ~3;
+    if (D == 32 * LPLW)
+        k_sgm_full<LPLW, true, true><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, n_paths, Lvol, vol_stride);
+    else if (rD == 32 * LPLW)
+        k_sgm_full<LPLW, true, false><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, n_paths, Lvol, vol_stride);
+    else
+        k_sgm_full<LPLW, false, false><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, n_paths, Lvol, vol_stride);
 }
 
 // Selection of one image: a cluster of kSelCluster blocks per row, each block a quarter of the
@@ -275,13 +305,12 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
     if (full) {
         int nwarps = 0;
         for (int code = 0; code < n_paths; ++code) nwarps += L.count[code];
-        const int blocks = (nwarps + kFullWarps - 1) / kFullWarps;
         if (D <= 64)
-            k_sgm_full<2><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, L, Lvol, vol_stride);
+            launch_sgm_full_t<2>(C, W, Hh, D, P1, P2, n_paths, nwarps, Lvol, vol_stride, st);
         else if (D <= 128)
-            k_sgm_full<4><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, L, Lvol, vol_stride);
+            launch_sgm_full_t<4>(C, W, Hh, D, P1, P2, n_paths, nwarps, Lvol, vol_stride, st);
         else
-            k_sgm_full<8><<<blocks, kFullWarps * 32, 0, st>>>(C, W, Hh, D, P1, P2, L, Lvol, vol_stride);
+            launch_sgm_full_t<8>(C, W, Hh, D, P1, P2, n_paths, nwarps, Lvol, vol_stride, st);
         return cudaGetLastError();
     }
     if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);

@@ -515,70 +515,102 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) 
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 
-// Cost ring of the full-range walker: kFullRing steps of 32 lanes x full_words<LPLW>() words per
-// warp, filled kFullAhead steps ahead (a slot is refilled kFullRing - kFullAhead steps after its
-// last read, whose value the walk has consumed by then).
+// Cost ring of the full-range walker: kFullRing steps of one pixel's cost slice each (32 LPLW
+// bytes, the slice's layout in the volume), copied in blocks of kFullBlk steps, kFullAhead blocks
+// ahead of the walk (the block a copy overwrites was read in the iteration before).
+constexpr int kFullBlk = 4;
 constexpr int kFullRing = 16;
-constexpr int kFullAhead = 12;
-template <int LPLW>
-__host__ __device__ constexpr int full_words() { return LPLW == 8 ? 2 : 1; }
+constexpr int kFullAhead = 3;
+static_assert(kFullRing == (kFullAhead + 1) * kFullBlk, "ring of the blocks in flight + the one read");
 
 // One path line whose windows are all the full range [0, D - 1] (a first frame, or the
 // full-range mode: known before the launch), one warp, lane j holding labels LPLW j .. LPLW j +
 // LPLW - 1 of the state in registers as packed 16-bit pairs: the neighbours d - 1 and d + 1 across
-// lanes come by shuffle, m by redux.sync. The costs of a step (every pixel's block of rD = D
-// rounded up to 4 cells, 4-byte aligned) reach this lane's words of the ring by cp.async,
-// kFullAhead steps ahead, so that a long line is not bound by the load latency. Labels from D on
-// are +inf. Same recurrence and first step (L = C) as sgm_group_lines. ring: this warp's
-// kFullRing * 32 * full_words<LPLW>() words of shared memory.
-template <int LPLW>
+// lanes come by shuffle, m by redux.sync (on the lane minimum held in both halves, so that the
+// result is m in both halves). Labels from D on are +inf. Same recurrence and first step (L = C)
+// as sgm_group_lines.
+// The costs of a step (pixel i's block of rD = D rounded up to 4 cells, at cell i rD) reach the
+// ring by cp.async, kFullAhead blocks of kFullBlk steps ahead, so that a long line is not bound
+// by the load latency: with V16 (rD = 32 LPLW, a multiple of 16 bytes) in 16-byte pieces of the
+// block's slices spread over the lanes, else each lane copies the 4-byte words of its labels.
+// EXACT: D = 32 LPLW (no label of any lane past the range). ring: this warp's kFullRing * 8 * LPLW
+// words of shared memory.
+template <int LPLW, bool V16, bool EXACT>
 __device__ __forceinline__ void sgm_full_line(const uint8_t* __restrict__ C, int W, int Hh, int D,
                                               int rD, int P1, int P2, int code, int line,
                                               uint8_t* __restrict__ Lv, uint32_t* const ring) {
     static_assert(LPLW == 2 || LPLW == 4 || LPLW == 8, "labels per lane");
-    static_assert((kFullRing & (kFullRing - 1)) == 0 && kFullAhead + 4 <= kFullRing, "ring");
-    constexpr int NP = LPLW / 2;              // packed pairs per lane
-    constexpr int NW = full_words<LPLW>();    // ring words per lane and step
+    constexpr int NP = LPLW / 2;          // packed pairs per lane
+    constexpr int SLOT = 32 * LPLW;       // bytes of a ring slot
+    constexpr int NCH = kFullBlk * SLOT / 16;  // 16-byte pieces of a block
     const int lane = threadIdx.x & 31;
     int i0 = 0, stp = 0, len = 0;
     line_geometry(code, line, W, Hh, i0, stp, len);
     const int base = LPLW * lane;  // this lane's first label
     uint32_t kp[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) kp[k] = pair_keep(D - (base + 2 * k));
+    for (int k = 0; k < NP; ++k) kp[k] = EXACT ? 0xFFFFFFFFu : pair_keep(D - (base + 2 * k));
     const uint32_t P1x2 = ((uint32_t)P1 << 16) | (uint32_t)P1;
-    // the 4-byte words a lane copies: its own (two lanes share one word when LPLW = 2)
-    const int cb = LPLW == 2 ? 4 * (lane >> 1) : base;
-    const uint32_t psel = LPLW == 2 && (lane & 1) ? 0x4342u : 0x4140u;
-    uint32_t* const slot0 = ring + lane * NW;
-    auto issue = [&](int s) {
-        if (s < len && base < D) {
-            const uint8_t* const src = C + (size_t)(i0 + s * stp) * rD + cb;
-            uint32_t* const dst = slot0 + (s & (kFullRing - 1)) * 32 * NW;
+    const uint32_t P2x2 = ((uint32_t)P2 << 16) | (uint32_t)P2;
+    uint8_t* const ring8 = reinterpret_cast<uint8_t*>(ring);
+
+    // copies of block b (steps kFullBlk b ..) into ring slots (kFullBlk b ..) mod kFullRing
+    auto issue = [&](int b) {
+        if constexpr (V16) {
 #pragma unroll
-            for (int g = 0; g < NW; ++g)
-                if (base + 4 * g < D) cp_async4(dst + g, src + 4 * g);
+            for (int r = 0; r < (NCH + 31) / 32; ++r) {
+                const int c = lane + 32 * r;
+                const int q = c / (SLOT / 16), o = 16 * (c % (SLOT / 16));
+                const int s = kFullBlk * b + q;
+                if ((NCH % 32 == 0 || c < NCH) && s < len)
+                    cp_async16(ring8 + (s & (kFullRing - 1)) * SLOT + o,
+                               C + (size_t)(i0 + s * stp) * rD + o);
+            }
+        } else {
+            // the 4-byte words of this lane's labels (one word of two lanes when LPLW = 2)
+            const int wb = LPLW == 2 ? 4 * (lane >> 1) : base;
+            const bool owner = LPLW != 2 || (lane & 1) == 0;
+#pragma unroll
+            for (int q = 0; q < kFullBlk; ++q) {
+                const int s = kFullBlk * b + q;
+                if (s < len && owner) {
+#pragma unroll
+                    for (int g = 0; g < (LPLW == 8 ? 2 : 1); ++g)
+                        if (wb + 4 * g < D)
+                            cp_async4(ring8 + (s & (kFullRing - 1)) * SLOT + wb + 4 * g,
+                                      C + (size_t)(i0 + s * stp) * rD + wb + 4 * g);
+                }
+            }
         }
         cp_async_commit();
     };
 #pragma unroll
-    for (int s = 0; s < kFullAhead; ++s) issue(s);
+    for (int b = 0; b < kFullAhead; ++b) issue(b);
 
     uint32_t P[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) P[k] = kInf2;
     uint32_t mm2 = 0u, mP2 = 0u;  // a first step: no predecessor, L = C
-    for (int s = 0; s < len; ++s) {
-        cp_async_wait<kFullAhead - 1>();  // this step's copy (the oldest group) has landed
-        uint32_t cw[NW];
-#pragma unroll
-        for (int g = 0; g < NW; ++g) cw[g] = slot0[(s & (kFullRing - 1)) * 32 * NW + g];
-        issue(s + kFullAhead);
+    const bool live = EXACT || base < D;
+    // step s: costs from ring slot s mod kFullRing, result to pixel i0 + s stp
+    auto step = [&](int s) {
+        const uint8_t* const sl = ring8 + (s & (kFullRing - 1)) * SLOT + base;
         uint32_t cp[NP];
+        if constexpr (LPLW == 2) {
+            cp[0] = __byte_perm((uint32_t)*reinterpret_cast<const uint16_t*>(sl), 0u, 0x4140);
+        } else {
 #pragma unroll
-        for (int k = 0; k < NP; ++k)
-            cp[k] = __byte_perm(cw[k >> 1], 0u, LPLW == 2 ? psel : ((k & 1) ? 0x4342u : 0x4140u));
+            for (int g = 0; g < LPLW / 4; ++g) {
+                const uint32_t w = reinterpret_cast<const uint32_t*>(sl)[g];
+                cp[2 * g] = __byte_perm(w, 0u, 0x4140);
+                cp[2 * g + 1] = __byte_perm(w, 0u, 0x4342);
+            }
+        }
         uint32_t up = __shfl_up_sync(kFull, P[NP - 1], 1);
         uint32_t dn = __shfl_down_sync(kFull, P[0], 1);
         if (lane == 0) up = kInf2;
@@ -589,27 +621,44 @@ __device__ __forceinline__ void sgm_full_line(const uint8_t* __restrict__ C, int
 #pragma unroll
         for (int k = 1; k < NP; ++k) X[k] = __byte_perm(P[k - 1], P[k], 0x5432);
         X[NP] = __byte_perm(P[NP - 1], dn, 0x5432);
-        uint32_t pm = kInf2;
+        uint32_t pm = 0u;
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            const uint32_t v = (cp[k] + grp_t(X[k], X[k + 1], P1x2, mP2)) - mm2;
-            P[k] = (v & kp[k]) | (kInf2 & ~kp[k]);
-            pm = vmin2(pm, P[k]);
+            // as grp_t, with the pair (L(d), L(d + 1)) taken from P[k] itself
+            const uint32_t t = vmin2(vmin2(vmin2(X[k], X[k + 1]) + P1x2, P[k]), mP2);
+            const uint32_t v = (cp[k] + t) - mm2;
+            P[k] = EXACT ? v : (v & kp[k]) | (kInf2 & ~kp[k]);
+            pm = k == 0 ? P[0] : vmin2(pm, P[k]);
         }
-        const unsigned m = __reduce_min_sync(kFull, min(pm & 0xFFFFu, pm >> 16));
-        mm2 = m * 0x10001u;
-        mP2 = (m + (unsigned)P2) * 0x10001u;
-        if (base < D) {
-            uint8_t* const dst = Lv + (size_t)(i0 + s * stp) * rD + base;
+        // the lane's minimum in both halves, then the warp's: m in both halves
+        mm2 = __reduce_min_sync(kFull, vmin2(pm, __byte_perm(pm, 0u, 0x1032)));
+        mP2 = mm2 + P2x2;
+        if (live) {
+            uint8_t* const dst = Lv + (size_t)(unsigned)(i0 + s * stp) * (unsigned)rD + base;
             if constexpr (LPLW == 2) {
                 *reinterpret_cast<uint16_t*>(dst) = (uint16_t)__byte_perm(P[0], 0u, 0x0020);
             } else {
 #pragma unroll
-                for (int g = 0; g < NW; ++g)
-                    if (base + 4 * g < D)
+                for (int g = 0; g < LPLW / 4; ++g)
+                    if (EXACT || base + 4 * g < D)
                         reinterpret_cast<uint32_t*>(dst)[g] = __byte_perm(P[2 * g], P[2 * g + 1], 0x6420);
             }
         }
+    };
+    const int nfull = len / kFullBlk;
+    for (int b = 0; b < nfull; ++b) {
+        cp_async_wait<kFullAhead - 1>();  // block b (the oldest in flight) has landed
+        __syncwarp();                     // ... for every lane (pieces copied by other lanes)
+        issue(b + kFullAhead);
+#pragma unroll
+        for (int q = 0; q < kFullBlk; ++q) step(kFullBlk * b + q);
+    }
+    if (nfull * kFullBlk < len) {
+        cp_async_wait<kFullAhead - 1>();
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kFullBlk; ++q)
+            if (kFullBlk * nfull + q < len) step(kFullBlk * nfull + q);
     }
     cp_async_wait<0>();
 }
