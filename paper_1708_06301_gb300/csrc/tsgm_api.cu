@@ -320,13 +320,22 @@ tsgm_status match_stages(tsgm_ctx* ctx, const int16_t* lo, const int16_t* hi, fl
     const bool keep = (p.flags & TSGM_FLAG_KEEP_INTERNALS) != 0;
     const float s_thr = p.S_max * (float)p.n_paths;
     stage_begin(ctx, TSGM_STAGE_SELECT);
-    TSGM_LAUNCH(launch_select(ctx->Lvol, ctx->max_cells, p.n_paths, ctx->desc, ctx->W, ctx->H, ctx->D,
-                              s_thr, p.r_min, p.lr_tol, Dz, rz, keep ? ctx->S : nullptr,
-                              keep ? ctx->dstar : nullptr, keep ? ctx->dright : nullptr,
-                              keep ? ctx->lrvalid : nullptr, ctx->wq, ctx->gkeys, ctx->wds,
-                              ctx->stream),
-            "select");
-    ++ctx->launches;  // launch_select enqueues two kernels (wide windows, then the rows)
+    if (full) {
+        TSGM_LAUNCH(launch_select_full(ctx->Lvol, ctx->max_cells, p.n_paths, ctx->W, ctx->H, ctx->D,
+                                       ctx->Bc, p.P2, s_thr, p.r_min, p.lr_tol, Dz, rz,
+                                       keep ? ctx->S : nullptr, keep ? ctx->dstar : nullptr,
+                                       keep ? ctx->dright : nullptr, keep ? ctx->lrvalid : nullptr,
+                                       ctx->stream),
+                    "select");
+    } else {
+        TSGM_LAUNCH(launch_select(ctx->Lvol, ctx->max_cells, p.n_paths, ctx->desc, ctx->W, ctx->H, ctx->D,
+                                  s_thr, p.r_min, p.lr_tol, Dz, rz, keep ? ctx->S : nullptr,
+                                  keep ? ctx->dstar : nullptr, keep ? ctx->dright : nullptr,
+                                  keep ? ctx->lrvalid : nullptr, ctx->wq, ctx->gkeys, ctx->wds,
+                                  ctx->stream),
+                    "select");
+        ++ctx->launches;  // launch_select enqueues two kernels (wide windows, then the rows)
+    }
     stage_end(ctx, TSGM_STAGE_SELECT);
     return TSGM_OK;
 }

@@ -65,6 +65,11 @@ cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* des
 cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D, int n_paths,
                        int P1, int P2, uint8_t* Lvol, uint64_t vol_stride, const uint32_t* wq,
                        bool full, cudaStream_t st);
+// every window [0, D - 1]: one kernel, desc and the wide queue unread (Bc: census bits)
+cudaError_t launch_select_full(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, int W, int Hh,
+                               int D, int Bc, int P2, float s_thr, float r_min, int lr_tol,
+                               float* Dz, float* rz, uint16_t* S, int16_t* dstar, int16_t* dright,
+                               uint8_t* valid, cudaStream_t st);
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,
                           int W, int Hh, int D, float s_thr, float r_min, int lr_tol, float* Dz,
                           float* rz, uint16_t* S, int16_t* dstar, int16_t* dright, uint8_t* valid,

@@ -459,6 +459,111 @@ __device__ __forceinline__ void load_wide_costs(const uint8_t* __restrict__ Lvol
     }
 }
 
+// Full-range selection (every window [0, D - 1], pixel i's block of rD cells at cell i rD): lane
+// j's cost words of pixel i, labels LPL j .. LPL j + LPL - 1 of each of the NPATHS volumes (words
+// past D read as 0).
+template <int NPATHS, int LPL>
+__device__ __forceinline__ void load_full_costs(const uint8_t* __restrict__ Lvol, uint64_t stride,
+                                                size_t o, int D, uint32_t (&v)[NPATHS * (LPL >= 4 ? LPL / 4 : 1)]) {
+    constexpr int NW = LPL >= 4 ? LPL / 4 : 1;
+    const int base = LPL * (int)(threadIdx.x & 31);
+#pragma unroll
+    for (int r = 0; r < NPATHS; ++r) {
+        const uint8_t* const src = Lvol + r * stride + o + base;
+        if constexpr (LPL == 2) {
+            v[r] = base < D ? (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(src)) : 0u;
+        } else {
+#pragma unroll
+            for (int g = 0; g < NW; ++g)
+                v[r * NW + g] = base + 4 * g < D ? __ldg(reinterpret_cast<const uint32_t*>(src) + g) : 0u;
+        }
+    }
+}
+
+// One full-range pixel by a whole warp (Eq. 9 and the right-view keys), v from load_full_costs:
+// the sums S(d) of the path costs (with `bytesum`, when every path cost is below 128, two volumes'
+// words are added bytewise first), every label's right-view key to keymin(xr, S << 9 | d) for
+// xr = x - d >= 0, and the winner d* (least S, then least d; the same keys order both), its
+// sub-pixel offset and the matching variance, as select_wide. scr: this warp's D labels of
+// scratch.
+template <int NPATHS, int LPL, class KeyMin>
+__device__ __forceinline__ void select_full_px(const uint32_t (&v)[NPATHS * (LPL >= 4 ? LPL / 4 : 1)],
+                                               int D, bool bytesum, int x, size_t o, float s_thr,
+                                               float r_min, uint16_t* scr,
+                                               uint16_t* __restrict__ S_out, const KeyMin& keymin,
+                                               int& dstar, float& dz, float& rr) {
+    constexpr int NW = LPL >= 4 ? LPL / 4 : 1;
+    constexpr int NP = LPL / 2;
+    const int lane = threadIdx.x & 31;
+    const int base = LPL * lane;
+    // S as packed pairs (labels base + 2k, base + 2k + 1)
+    uint32_t S[NP];
+#pragma unroll
+    for (int g = 0; g < NW; ++g) {
+        uint32_t p0 = 0u, p1 = 0u;
+        if (bytesum && NPATHS % 2 == 0) {
+#pragma unroll
+            for (int r = 0; r < NPATHS; r += 2) {
+                const uint32_t b = v[r * NW + g] + v[(r + 1) * NW + g];  // bytes < 256: no carry
+                p0 += __byte_perm(b, 0u, 0x4140);
+                p1 += __byte_perm(b, 0u, 0x4342);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < NPATHS; ++r) {
+                p0 += __byte_perm(v[r * NW + g], 0u, 0x4140);
+                p1 += __byte_perm(v[r * NW + g], 0u, 0x4342);
+            }
+        }
+        S[2 * g] = p0;
+        if (2 * g + 1 < NP) S[2 * g + 1] = p1;
+    }
+    if constexpr (LPL == 2) {
+        if (base < D) {
+            *reinterpret_cast<uint32_t*>(scr + base) = S[0];
+            if (S_out) *reinterpret_cast<uint32_t*>(S_out + o + base) = S[0];
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < NW; ++g) {
+            if (base + 4 * g < D) {
+                *reinterpret_cast<uint2*>(scr + base + 4 * g) = make_uint2(S[2 * g], S[2 * g + 1]);
+                if (S_out) *reinterpret_cast<uint2*>(S_out + o + base + 4 * g) = make_uint2(S[2 * g], S[2 * g + 1]);
+            }
+        }
+    }
+    unsigned best = 0xFFFFFFFFu;
+    const bool all_xr = x >= D - 1;  // every label's right-view column inside the image
+#pragma unroll
+    for (int t = 0; t < LPL; ++t) {
+        const int d = base + t;
+        if (d < D) {
+            const unsigned sv = (t & 1) ? (S[t >> 1] >> 16) : (S[t >> 1] & 0xFFFFu);
+            const unsigned key = (sv << 9) | (unsigned)d;
+            best = min(best, key);
+            if (all_xr || x - d >= 0) keymin(x - d, key);
+        }
+    }
+    __syncwarp();
+    best = __reduce_min_sync(kFull, best);
+    const int js = (int)(best & 0x1FFu);
+    const int s0 = (int)(best >> 9);
+    float delta = 0.0f;
+    if (js >= 1 && js + 1 < D) {
+        const int smv = scr[js - 1], spv = scr[js + 1];
+        const int den = 2 * (smv - 2 * s0 + spv);
+        if (den > 0) delta = __fdiv_rn((float)(smv - spv), (float)den);
+    }
+    const int nl = count_side(scr, js - 1, -1, 0, D - 1, s0, s_thr, lane);
+    const int nr = count_side(scr, js + 1, +1, 0, D - 1, s0, s_thr, lane);
+    float r = (float)(nl + nr);
+    if (r < r_min) r = r_min;
+    dstar = js;
+    dz = __fadd_rn((float)js, delta);
+    rr = r;
+    __syncwarp();  // the scratch is free for the next pixel
+}
+
 // One window of at most NL (a multiple of 4, <= kSelNarrow) labels by one thread: its aggregated
 // costs (to S_out when given), every label's right-view key to keymin(xr, key), the winner's index
 // js in the window, its sub-pixel offset delta and the matching variance r (Eq. 9).

@@ -167,6 +167,83 @@ __global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(kSelThread
                              gkeys + (size_t)y * W, wds);
 }
 
+// Selection of an image whose windows are all the full range: a cluster of kSelCluster blocks per
+// row as k_select (the right-view keys of a block's pixels in its shared memory, merged across the
+// cluster), every pixel by one warp (select_full_px), the path costs of a warp's next pixel loaded
+// during the current one. bytesum: census bits + P2 < 128 (every path cost below 128).
+template <int NPATHS, int LPL>
+__global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(kSelThreadsCl) k_select_full(
+    const uint8_t* __restrict__ Lvol, uint64_t vol_stride, int W, int D, int bytesum, float s_thr,
+    float r_min, int lr_tol, float* __restrict__ Dz, float* __restrict__ rz,
+    uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
+    int16_t* __restrict__ dright_out, uint8_t* __restrict__ valid_out) {
+    constexpr int NW = LPL >= 4 ? LPL / 4 : 1;
+    extern __shared__ uint32_t sel_smem[];
+    const int rank = (int)cooperative_groups::this_cluster().block_rank();
+    const int y = blockIdx.x / kSelCluster;
+    const int seg = (W + kSelCluster - 1) / kSelCluster;
+    const int x0 = min(W, rank * seg), x1 = min(W, x0 + seg);
+    const int npx = x1 - x0;
+    const int rD = (D + 3) & ~3;
+    ClusterPart part{sel_smem, seg + D - 1, seg, D, W, rank * seg - (D - 1)};
+    uint32_t* const drk = part.own_keys();
+    float* const dzs = reinterpret_cast<float*>(sel_smem + part.nkeys);
+    float* const rzs = dzs + seg;
+    int16_t* const ds = reinterpret_cast<int16_t*>(rzs + seg);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint16_t* const scr = reinterpret_cast<uint16_t*>(sel_smem + ((part.nkeys + 3 * seg + 1) & ~1)) +
+                          wid * ((D + 7) & ~7);
+    for (int t = threadIdx.x; t < part.nkeys; t += blockDim.x) drk[t] = 0xFFFFFFFFu;
+    __syncthreads();
+
+    auto px = [&](const uint32_t (&v)[NPATHS * NW], int q) {
+        const int x = x0 + q;
+        const size_t o = (size_t)(y * W + x) * rD;
+        int dsr;
+        float dzr, rr;
+        select_full_px<NPATHS, LPL>(v, D, bytesum != 0, x, o, s_thr, r_min, scr, S_out,
+                                    [&](int xr, uint32_t k) { part.keymin(xr, k); }, dsr, dzr, rr);
+        if (lane == 0) {
+            ds[q] = (int16_t)dsr;
+            dzs[q] = dzr;
+            rzs[q] = rr;
+        }
+    };
+    // two register sets in turn: the next pixel's costs load during the current one
+    uint32_t va[NPATHS * NW], vb[NPATHS * NW];
+    auto load = [&](uint32_t (&v)[NPATHS * NW], int q) {
+        load_full_costs<NPATHS, LPL>(Lvol, vol_stride, (size_t)(y * W + x0 + q) * rD, D, v);
+    };
+    if (wid < npx) load(va, wid);
+    for (int q = wid; q < npx; q += 2 * nw) {
+        if (q + nw < npx) load(vb, q + nw);
+        px(va, q);
+        if (q + nw >= npx) break;
+        if (q + 2 * nw < npx) load(va, q + 2 * nw);
+        px(vb, q + nw);
+    }
+    part.sync();  // every key of the row is final
+    for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+        const int i = y * W + x;
+        const int d = ds[x - x0];
+        const int xr = x - d;
+        bool ok = false;
+        if (xr >= 0) {
+            const uint32_t kk = part.key(xr);
+            ok = kk != 0xFFFFFFFFu && abs(d - (int)(kk & 0x1FFu)) <= lr_tol;
+        }
+        Dz[i] = ok ? dzs[x - x0] : -1.0f;
+        rz[i] = ok ? rzs[x - x0] : -1.0f;
+        if (dstar_out) {
+            dstar_out[i] = (int16_t)d;
+            const uint32_t kx = part.key(x);
+            dright_out[i] = kx == 0xFFFFFFFFu ? (int16_t)-1 : (int16_t)(kx & 0x1FFu);
+            valid_out[i] = ok ? 1 : 0;
+        }
+    }
+    part.sync();  // no block leaves while another may still read its keys
+}
+
 // The wide windows of the queue wq (see select_split), one warp per pixel (pixel t of the queue by
 // warp t mod the launch's warps, the next one's path costs loaded during the current one): winner,
 // sub-pixel disparity and matching variance into wds, Dz and rz (the row's selection clears Dz and
@@ -316,6 +393,51 @@ cudaError_t launch_sgm(const uint8_t* C, const uint2* desc, int W, int Hh, int D
     if (D <= 64) return launch_sgm_t<2>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
     if (D <= 128) return launch_sgm_t<4>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
     return launch_sgm_t<8>(C, desc, W, Hh, P1, P2, L, Lvol, vol_stride, wq, st);
+}
+
+template <int NPATHS, int LPL>
+static cudaError_t launch_select_full_t(const uint8_t* Lvol, uint64_t vol_stride, int W, int Hh,
+                                        int D, int bytesum, float s_thr, float r_min, int lr_tol,
+                                        float* Dz, float* rz, uint16_t* S, int16_t* dstar,
+                                        int16_t* dright, uint8_t* valid, cudaStream_t st) {
+    const int seg = (W + kSelCluster - 1) / kSelCluster;
+    const size_t smem = (size_t)((seg + D - 1 + 3 * seg + 1) & ~1) * 4 +
+                        (size_t)(kSelThreadsCl / 32) * ((D + 7) & ~7) * sizeof(uint16_t);
+    auto kern = k_select_full<NPATHS, LPL>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<Hh * kSelCluster, kSelThreadsCl, smem, st>>>(Lvol, vol_stride, W, D, bytesum, s_thr, r_min,
+                                                        lr_tol, Dz, rz, S, dstar, dright, valid);
+    return cudaGetLastError();
+}
+
+template <int NPATHS>
+static cudaError_t launch_select_full_p(const uint8_t* Lvol, uint64_t vol_stride, int W, int Hh,
+                                        int D, int bytesum, float s_thr, float r_min, int lr_tol,
+                                        float* Dz, float* rz, uint16_t* S, int16_t* dstar,
+                                        int16_t* dright, uint8_t* valid, cudaStream_t st) {
+    if (D <= 64)
+        return launch_select_full_t<NPATHS, 2>(Lvol, vol_stride, W, Hh, D, bytesum, s_thr, r_min,
+                                               lr_tol, Dz, rz, S, dstar, dright, valid, st);
+    if (D <= 128)
+        return launch_select_full_t<NPATHS, 4>(Lvol, vol_stride, W, Hh, D, bytesum, s_thr, r_min,
+                                               lr_tol, Dz, rz, S, dstar, dright, valid, st);
+    return launch_select_full_t<NPATHS, 8>(Lvol, vol_stride, W, Hh, D, bytesum, s_thr, r_min,
+                                           lr_tol, Dz, rz, S, dstar, dright, valid, st);
+}
+
+cudaError_t launch_select_full(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, int W, int Hh,
+                               int D, int Bc, int P2, float s_thr, float r_min, int lr_tol,
+                               float* Dz, float* rz, uint16_t* S, int16_t* dstar, int16_t* dright,
+                               uint8_t* valid, cudaStream_t st) {
+    const int bytesum = Bc + P2 < 128 ? 1 : 0;
+    return n_paths == 8
+               ? launch_select_full_p<8>(Lvol, vol_stride, W, Hh, D, bytesum, s_thr, r_min, lr_tol,
+                                         Dz, rz, S, dstar, dright, valid, st)
+               : launch_select_full_p<4>(Lvol, vol_stride, W, Hh, D, bytesum, s_thr, r_min, lr_tol,
+                                         Dz, rz, S, dstar, dright, valid, st);
 }
 
 cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths, const uint2* desc,

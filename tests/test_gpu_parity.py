@@ -226,12 +226,16 @@ def test_match_stages_bitexact(tsgm, case):
     assert_maps(g["Dz"], g["rz"], o["Dz"], o["rz"])
 
 
-# First frames: every window is [0, D - 1], and the aggregation runs its full-range kernel (one
-# warp per line, labels in registers); D ragged against the lanes' labels (41, 101, 201), exact
-# (64, 128, 256), a single label, lines shorter than a warp and long horizontal lines.
+# First frames: every window is [0, D - 1], and the aggregation and the selection run their
+# full-range kernels (one warp per line or pixel); D ragged against the lanes' labels (41, 101,
+# 201), exact (64, 128, 256), a single label, lines shorter than a warp and long horizontal lines.
 FULL_CASES = [
-    # W, H, D, census, paths
+    # W, H, D, census, paths[, P1, P2]; with census bits + P2 >= 128 the selection sums the path
+    # costs without the bytewise pairing
     (97, 45, 41, (5, 5), 4),
+    (131, 37, 101, (9, 7), 8, 10, 90),
+    (150, 21, 128, (9, 7), 4, 20, 120),
+    (70, 19, 256, (9, 7), 8, 8, 66),
     (64, 33, 64, (5, 5), 8),
     (131, 37, 101, (9, 7), 8),
     (300, 20, 128, (9, 7), 8),
@@ -247,12 +251,13 @@ FULL_CASES = [
 
 @pytest.mark.parametrize("case", FULL_CASES)
 def test_first_frame_full_range_bitexact(tsgm, case):
-    W, H, D, (cw, ch), npaths = case
+    W, H, D, (cw, ch), npaths = case[:5]
+    pen = dict(P1=case[5], P2=case[6]) if len(case) > 5 else {}
     seq_l, seq_r = synth.random_images(W * 5 + H + D, W, H)
     right = np.roll(seq_l, -min(5, D - 1), axis=1)
     right[:, -5:] = seq_r[:, -5:]
     K = np.array([[0.9 * W, 0, W / 2], [0, 0.9 * W, H / 2], [0, 0, 1]], np.float32)
-    with make_ctx(tsgm, W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths) as ctx:
+    with make_ctx(tsgm, W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths, **pen) as ctx:
         Dg, Pg = empty((H, W), np.float32), empty((H, W), np.float32)
         ctx.frame(dev(seq_l), dev(right), None, None, K, f32(0.5), Dg, Pg)
         off = empty((W * H + 1,), np.uint32)
@@ -272,8 +277,8 @@ def test_first_frame_full_range_bitexact(tsgm, case):
         g = dict(C=compact(host(C, np.uint8), offg, lo, hi), S=compact(host(S, np.uint16), offg, lo, hi),
                  ds=host(ds, np.int16), dr=host(dr, np.int16), va=host(va, np.uint8),
                  D=host(Dg, np.float32), P=host(Pg, np.float32))
-    o = oracle.match(seq_l, right, lo, hi, oparams(W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths),
-                     keep=True)
+    o = oracle.match(seq_l, right, lo, hi,
+                     oparams(W, H, d_max=D - 1, cw=cw, ch=ch, n_paths=npaths, **pen), keep=True)
     assert storage == W * H * ((D + 3) // 4 * 4)
     assert np.array_equal(g["C"], o["C"])
     assert np.array_equal(g["S"], o["S"])
