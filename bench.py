@@ -525,11 +525,12 @@ def bench_serving(duration_s: float, budget_gb: float):
             "hbm_budget_gb": budget_gb}
 
 
-# DRAM bytes (read + write) of one frame's aggregation (its two launches: the lane-group form that
-# does the work and the other, which returns at once), mean over the ten frames of one step of the
-# sequence (one full-range frame, 621 MB; nine reduced, 11-21 MB each) from ncu's
-# dram__bytes_read.sum + dram__bytes_write.sum (profiles/k_sgm_kitti_1242x375_reduced.md).
-SGM_DRAM_BYTES_PER_LAUNCH = 75608474
+# DRAM bytes (read + write) of one frame's aggregation, mean over the ten frames of one step of the
+# sequence from ncu's dram__bytes_read.sum + dram__bytes_write.sum
+# (profiles/k_sgm_kitti_1242x375_reduced.md): the full-range frame, one launch of k_sgm_full, 676
+# MB; nine reduced frames, two launches each (the lane-group form that does the work and the
+# other, which returns at once), 11-22 MB.
+SGM_DRAM_BYTES_PER_LAUNCH = 80998682
 SGM_DRAM_NOTE = None
 
 
