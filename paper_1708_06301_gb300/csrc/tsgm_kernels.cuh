@@ -346,8 +346,16 @@ __device__ __forceinline__ void cp_async_wait() {
 
 constexpr int kSelThreads = 512;
 
+// The Eq. 9 threshold as an integer. A running sum n of in-window labels is below 2^20 (at most
+// 256 labels of S <= 8 x 255), and for such n, (float)n < thr exactly when n < count_limit(thr):
+// the least integer not below thr, capped at 2^20 (none for thr <= 0 or NaN). count_side's
+// out-of-window sentinel (2^20) is then never counted, whatever thr.
+__device__ __forceinline__ int count_limit(float thr) {
+    return thr > 0.0f ? (thr >= 1048576.0f ? 1048576 : (int)ceilf(thr)) : 0;
+}
+
 __device__ __forceinline__ int count_side(const uint16_t* __restrict__ s, int start, int dirn,
-                                          int lo_idx, int hi_idx, int s0, float thr, int lane) {
+                                          int lo_idx, int hi_idx, int s0, int lim, int lane) {
     int carry = 0, count = 0;
     for (int t0 = 0;; t0 += 32) {
         const int jj = start + dirn * (t0 + lane);
@@ -358,7 +366,7 @@ __device__ __forceinline__ int count_side(const uint16_t* __restrict__ s, int st
             const int u = __shfl_up_sync(kFull, v, o);
             if (lane >= o) v += u;
         }
-        const unsigned ok = __ballot_sync(kFull, (float)(carry + v) < thr);
+        const unsigned ok = __ballot_sync(kFull, carry + v < lim);
         const int c = __popc(ok);
         count += c;
         const int tot = __shfl_sync(kFull, v, 31);
@@ -433,8 +441,9 @@ __device__ __forceinline__ void select_wide(const uint32_t (&v)[NCH * NPATHS], u
         const int den = 2 * (smv - 2 * s0 + spv);
         if (den > 0) delta = __fdiv_rn((float)(smv - spv), (float)den);
     }
-    const int nl = count_side(scr, js - 1, -1, 0, w - 1, s0, s_thr, lane);
-    const int nr = count_side(scr, js + 1, +1, 0, w - 1, s0, s_thr, lane);
+    const int lim = count_limit(s_thr);
+    const int nl = count_side(scr, js - 1, -1, 0, w - 1, s0, lim, lane);
+    const int nr = count_side(scr, js + 1, +1, 0, w - 1, s0, lim, lane);
     float r = (float)(nl + nr);
     if (r < r_min) r = r_min;
     dstar = a + js;
@@ -554,8 +563,9 @@ __device__ __forceinline__ void select_full_px(const uint32_t (&v)[NPATHS * (LPL
         const int den = 2 * (smv - 2 * s0 + spv);
         if (den > 0) delta = __fdiv_rn((float)(smv - spv), (float)den);
     }
-    const int nl = count_side(scr, js - 1, -1, 0, D - 1, s0, s_thr, lane);
-    const int nr = count_side(scr, js + 1, +1, 0, D - 1, s0, s_thr, lane);
+    const int lim = count_limit(s_thr);
+    const int nl = count_side(scr, js - 1, -1, 0, D - 1, s0, lim, lane);
+    const int nr = count_side(scr, js + 1, +1, 0, D - 1, s0, lim, lane);
     float r = (float)(nl + nr);
     if (r < r_min) r = r_min;
     dstar = js;
@@ -612,12 +622,13 @@ __device__ __forceinline__ void select_narrow(const uint8_t* __restrict__ Lvol, 
     }
     // counts: running sums outwards from d*; walking labels in order of distance keeps the
     // sums growing, so every label whose sum is below the threshold is in the counted run
+    const int lim = count_limit(s_thr);
     int nl = 0, nr = 0, acc = 0;
 #pragma unroll
     for (int j = NL - 1; j >= 0; --j) {
         if (j < js) {
             acc += sv[j] - s0;
-            nl += ((float)acc < s_thr) ? 1 : 0;
+            nl += acc < lim ? 1 : 0;
         }
     }
     acc = 0;
@@ -625,7 +636,7 @@ __device__ __forceinline__ void select_narrow(const uint8_t* __restrict__ Lvol, 
     for (int j = 0; j < NL; ++j) {
         if (j > js && j < w) {
             acc += sv[j] - s0;
-            nr += ((float)acc < s_thr) ? 1 : 0;
+            nr += acc < lim ? 1 : 0;
         }
     }
     float r = (float)(nl + nr);

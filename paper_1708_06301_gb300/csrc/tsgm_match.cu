@@ -10,6 +10,7 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cfloat>
 
 #include "tsgm_kernels.cuh"
@@ -128,6 +129,9 @@ static void launch_sgm_full_t(const uint8_t* C, int W, int Hh, int D, int P1, in
 // shared memory.
 constexpr int kSelCluster = 4;
 constexpr int kSelThreadsCl = 256;
+// k_select's blocks: a thread per pixel of the block's quarter row (rounded up to whole warps), at
+// most this many (then a thread takes several)
+constexpr int kSelThreadsMax = 512;
 
 struct ClusterPart {
     uint32_t* keys;
@@ -148,7 +152,7 @@ struct ClusterPart {
 };
 
 template <int NPATHS, int NCH>
-__global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(kSelThreadsCl) k_select(
+__global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(kSelThreadsMax) k_select(
     const uint8_t* __restrict__ Lvol, uint64_t vol_stride, const uint2* __restrict__ desc, int W,
     int DP, int DPim, float s_thr, float r_min, int lr_tol, float* __restrict__ Dz,
     float* __restrict__ rz, uint16_t* __restrict__ S_out, int16_t* __restrict__ dstar_out,
@@ -448,8 +452,9 @@ cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths,
     const int DP = 256;
     const int n = W * Hh;
     const int seg = (W + kSelCluster - 1) / kSelCluster;
+    const int threads = std::min(kSelThreadsMax, std::max(64, (seg + 31) & ~31));
     const size_t smem = (size_t)((seg + D - 1 + 3 * seg + 1) & ~1) * 4 +
-                        (size_t)(kSelThreadsCl / 32) * DP * sizeof(uint16_t);
+                        (size_t)(threads / 32) * DP * sizeof(uint16_t);
     auto wide = n_paths == 8 ? (D <= 128 ? k_select_wide<8, 1> : k_select_wide<8, 2>)
                              : (D <= 128 ? k_select_wide<4, 1> : k_select_wide<4, 2>);
     wide<<<152 * 8, 256, 0, st>>>(Lvol, vol_stride, desc, W, n, s_thr, r_min, Dz, rz, S, wds,
@@ -462,9 +467,9 @@ cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths,
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<Hh * kSelCluster, kSelThreadsCl, smem, st>>>(Lvol, vol_stride, desc, W, DP, D, s_thr,
-                                                         r_min, lr_tol, Dz, rz, S, dstar, dright,
-                                                         valid, n, wq, gkeys, wds);
+    kern<<<Hh * kSelCluster, threads, smem, st>>>(Lvol, vol_stride, desc, W, DP, D, s_thr, r_min,
+                                                   lr_tol, Dz, rz, S, dstar, dright, valid, n, wq,
+                                                   gkeys, wds);
     return cudaGetLastError();
 }
 
