@@ -181,11 +181,14 @@ tsgm_status tsgm_kalman_update(tsgm_ctx* ctx, const float* pred_D, const float* 
  * there D, P carry the prediction, but the state keeps no value, so that the next frame
  * searches the whole range at that pixel (Sec. 2.4, disparity consistency check). The first
  * call after create/reset has no prediction and searches the whole range (Sec. 3); its R, t
- * may be NULL. On a context created with a non-default CUDA stream, while stage timing is off
+ * may be NULL. Such a frame, and every frame with TSGM_FLAG_FULL_RANGE, is aggregated and
+ * selected by kernels for full windows (the same results as the windowed ones on windows
+ * [0, d_max]). On a context created with a non-default CUDA stream, while stage timing is off
  * and the caller is not capturing that stream, the step's ~20 kernels are launched as one CUDA
- * graph (captured each call; the instantiated graph of the last call is updated in place), which
- * shortens the gaps between them; the results are the same either way. An argument error found
- * while enqueueing (an invalid pose) then leaves nothing enqueued. */
+ * graph (captured each call; the instantiated graph of the last call of the same kind, a first
+ * frame or a later one, is updated in place), which shortens the gaps between them; the results
+ * are the same either way. An argument error found while enqueueing (an invalid pose) then
+ * leaves nothing enqueued. */
 tsgm_status tsgm_frame(tsgm_ctx* ctx, const uint8_t* left, const uint8_t* right,
                        const float R[9], const float t[3], const float K[9], float baseline,
                        float* D, float* P);
