@@ -329,9 +329,11 @@ cudaError_t launch_census(const uint8_t* imgA, const uint8_t* imgB, int W, int H
 
 cudaError_t launch_cost(const uint64_t* cl, const uint64_t* cr, const uint2* desc, int W, int Hh,
                         int Bc, uint8_t* C, cudaStream_t st) {
+    // a group of lanes per pixel: blocks retire as their pixels' windows are done, so that the
+    // few wide windows of a reduced frame spread over the launch instead of lengthening the
+    // loops of a fixed grid
     const int n = W * Hh;
-    int blocks = (n * kCostLanes + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    const int blocks = (int)(((size_t)n * kCostLanes + 255) / 256);
     k_cost<<<blocks, 256, 0, st>>>(cl, cr, desc, W, n, Bc, C);
     return cudaGetLastError();
 }
