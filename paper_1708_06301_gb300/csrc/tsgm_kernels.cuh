@@ -748,6 +748,10 @@ __device__ __forceinline__ void select_part(
         dcur = dnext;
         dnext = dnext2;
     }
+    // the kernel that selected the wide pixels apart (k_select_wide) may still be running when
+    // this one was launched as its programmatic dependent: wait for its grid and its writes
+    // (winners, outputs, keys) before reading them; without such a launch this returns at once
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (split) {
         __syncthreads();  // this block's key atomics are done
         const int kb = part.key_base();

@@ -263,6 +263,9 @@ __global__ void __launch_bounds__(256) k_select_wide(const uint8_t* __restrict__
                                                      uint32_t* __restrict__ gkeys,
                                                      const uint32_t* __restrict__ wq) {
     __shared__ __align__(16) uint16_t scr_all[8][NCH * 128];
+    // k_select, launched next with programmatic serialisation, may start its narrow pixels now:
+    // it waits for this grid (griddepcontrol.wait) before it reads what this kernel writes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int count = (int)wq[0];
     if (!select_split((uint32_t)count, n)) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -469,9 +472,21 @@ cudaError_t launch_select(const uint8_t* Lvol, uint64_t vol_stride, int n_paths,
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<Hh * kSelCluster, threads, smem, st>>>(Lvol, vol_stride, desc, W, DP, D, s_thr, r_min,
-                                                   lr_tol, Dz, rz, S, dstar, dright, valid, n, wq,
-                                                   gkeys, wds);
+    // programmatic dependent launch: the row clusters select their narrow pixels while
+    // k_select_wide still runs, and wait for it before they merge its keys and winners
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(Hh * kSelCluster));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, Lvol, vol_stride, desc, W, DP, D, s_thr, r_min, lr_tol, Dz, rz,
+                           S, dstar, dright, valid, n, wq, gkeys, wds);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
