@@ -494,6 +494,13 @@ def test_select_matching_variance_hand_cases():
     assert _select_one([20, 7, 0, 8, 20], s_thr=8.0)[2] == 1.0
     # r floored at r_min
     assert _select_one([9, 0, 9], s_thr=8.0, r_min=0.5)[2] == 0.5
+    # a threshold between integers: a running sum of 7 is below 7.5 but not below 7.0
+    assert _select_one([20, 7, 0, 1, 20], s_thr=7.5)[2] == 2.0
+    assert _select_one([20, 7, 0, 1, 20], s_thr=7.0)[2] == 1.0
+    # a threshold above every running sum: the count stops at the window's edges, every other
+    # label of the window counted (here 2 + 2), in a window that starts at 40 as well
+    assert _select_one([5, 3, 0, 4, 9], s_thr=1.0e9)[2] == 4.0
+    assert _select_one([5, 3, 0, 4, 9], lo=40, s_thr=3.0e7)[2] == 4.0
 
 
 def test_select_argmin_bruteforce():
